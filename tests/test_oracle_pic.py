@@ -1,0 +1,328 @@
+"""Pins for oracle.pic: deposit/gather, push, initial state and whole-step invariants.
+
+Each test checks the oracle against something fixed outside it: hand-computed
+spline weights, exact conservation sums, closed-form particle motion, the cold
+plasma frequency, and the paper's time-consistency theorems (section 3).
+"""
+import numpy as np
+import pytest
+
+from oracle import pic, spectral, steppers
+from paper_2410_18414_gb300 import workloads
+
+from test_oracle_bspline import closed_form
+
+
+def _cfg(**kw):
+    base = dict(nx=8, ny=6, lx=1.3, ly=0.9, dt=0.01, p=2, stepper="bdf", bdf_order=1, w=0.37)
+    base.update(kw)
+    return pic.Config(**base)
+
+
+# ------------------------------------------------------------------ deposit --
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_deposit_single_particle_brute_force(p):
+    cfg = _cfg(p=p)
+    # A particle near the corner, so the stencil wraps in both directions.
+    x, y = np.array([0.05]), np.array([0.88])
+    grid = pic.deposit(cfg, x, y, np.array([2.0]))
+    expect = np.zeros((cfg.nx, cfg.ny))
+    for i in range(-cfg.nx, 2 * cfg.nx):
+        for j in range(-cfg.ny, 2 * cfg.ny):
+            wgt = closed_form(x[0] / cfg.dx - i, p) * closed_form(y[0] / cfg.dy - j, p)
+            expect[i % cfg.nx, j % cfg.ny] += 2.0 * wgt
+    np.testing.assert_allclose(grid, expect / (cfg.dx * cfg.dy), atol=1e-12)
+
+
+def test_deposit_total_and_transpose_identity():
+    rng = np.random.default_rng(0)
+    cfg = _cfg(p=3)
+    n = 500
+    x = rng.uniform(0, cfg.lx, n)
+    y = rng.uniform(0, cfg.ly, n)
+    val = rng.standard_normal(n)
+    grid = pic.deposit(cfg, x, y, val)
+    assert abs(grid.sum() * cfg.dx * cfg.dy - val.sum()) < 1e-12
+    F = rng.standard_normal((cfg.nx, cfg.ny))
+    lhs = np.sum(F * grid) * cfg.dx * cfg.dy
+    rhs = np.sum(val * pic.gather(cfg, x, y, F))
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_gather_reproduces_linear_and_constant_fields():
+    cfg = _cfg(p=4, nx=16, ny=16, lx=1.0, ly=1.0)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0.3, 0.7, 200)
+    y = rng.uniform(0.3, 0.7, 200)
+    gx = (np.arange(16) * cfg.dx)[:, None] * np.ones((1, 16))
+    np.testing.assert_allclose(pic.gather(cfg, x, y, 2.0 + 0 * gx), 2.0, atol=1e-14)
+    # Degree >= 1 splines reproduce linear functions away from the wrap.
+    np.testing.assert_allclose(pic.gather(cfg, x, y, gx), x, atol=1e-13)
+
+
+# --------------------------------------------------------------------- push --
+
+def test_iaem_push_uniform_potential_gradient_closed_form():
+    cfg = _cfg(dt=0.02, q=-1.0, m=1.0)
+    g = {k: np.zeros(1) for k in pic.FIELD_NAMES}
+    g["dphidx"][:] = 0.3
+    g["dphidy"][:] = -0.1
+    st = pic.State(x=np.zeros(1), y=np.zeros(1), px=np.array([0.2]), py=np.array([0.0]),
+                   vx=np.zeros(1), vy=np.zeros(1), vx_old=np.zeros(1), vy_old=np.zeros(1))
+    for n in range(1, 60):
+        pic.iaem_push(cfg, st, g)
+        pxe = 0.2 - cfg.q * 0.3 * cfg.dt * n
+        pye = 0.0 + cfg.q * 0.1 * cfg.dt * n
+        gam = np.sqrt(1 + pxe * pxe + pye * pye)
+        assert abs(st.px[0] - pxe) < 1e-13 and abs(st.py[0] - pye) < 1e-13
+        assert abs(st.vx[0] - pxe / gam) < 1e-13 and abs(st.vy[0] - pye / gam) < 1e-13
+
+
+def test_iaem_push_uniform_vector_potential():
+    # Uniform A: canonical momentum conserved, v = (P - qA)/sqrt(|P - qA|^2 + 1), |v| < c.
+    cfg = _cfg(dt=0.02, q=-1.0)
+    g = {k: np.zeros(3) for k in pic.FIELD_NAMES}
+    g["ax"][:] = [0.5, 3.0, -40.0]
+    g["ay"][:] = [0.1, -2.0, 7.0]
+    p0 = np.array([0.3, -0.4, 1.0])
+    st = pic.State(x=np.zeros(3), y=np.zeros(3), px=p0.copy(), py=-p0.copy(), vx=np.zeros(3),
+                   vy=np.zeros(3), vx_old=np.zeros(3), vy_old=np.zeros(3))
+    pic.iaem_push(cfg, st, g)
+    np.testing.assert_array_equal(st.px, p0)
+    ux, uy = p0 + g["ax"], -p0 + g["ay"]
+    gam = np.sqrt(1 + ux * ux + uy * uy)
+    np.testing.assert_allclose(st.vx, ux / gam, rtol=1e-14)
+    np.testing.assert_allclose(st.vy, uy / gam, rtol=1e-14)
+    assert np.all(st.vx ** 2 + st.vy ** 2 < 1.0)
+
+
+def test_iaem_uses_extrapolated_velocity_in_grad_a_term():
+    # dP_x/dt = q (dAx/dx v*_x + dAy/dx v*_y) with v* = 2 v^n - v^{n-1}.
+    cfg = _cfg(dt=0.1, q=2.0)
+    g = {k: np.zeros(1) for k in pic.FIELD_NAMES}
+    g["daxdx"][:] = 0.7
+    g["daydx"][:] = -0.2
+    g["daxdy"][:] = 0.4
+    g["daydy"][:] = 0.9
+    st = pic.State(x=np.zeros(1), y=np.zeros(1), px=np.zeros(1), py=np.zeros(1),
+                   vx=np.array([0.3]), vy=np.array([0.1]), vx_old=np.array([0.2]),
+                   vy_old=np.array([0.25]))
+    pic.iaem_push(cfg, st, g)
+    vs = np.array([0.4, -0.05])
+    assert abs(st.px[0] - 0.2 * (0.7 * vs[0] - 0.2 * vs[1])) < 1e-15
+    assert abs(st.py[0] - 0.2 * (0.4 * vs[0] + 0.9 * vs[1])) < 1e-15
+    assert st.vx_old[0] == 0.3 and st.vy_old[0] == 0.1
+
+
+def test_taylor_back_velocity_matches_exact_uniform_field_motion():
+    # Exact: p(t) = p0 + q E t, v = p / sqrt(m^2 + |p|^2/c^2) (c = m = 1).
+    E = np.array([0.4, -0.7])
+    v0 = np.array([0.5, 0.3])
+    g0 = 1.0 / np.sqrt(1.0 - v0 @ v0)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        cfg = _cfg(dt=dt, q=-1.0)
+        vb = np.array(pic.taylor_back_velocity(cfg, v0[:1], v0[1:], E[:1], E[1:])).ravel()
+        p = g0 * v0 - cfg.q * E * dt
+        errs.append(np.linalg.norm(vb - p / np.sqrt(1 + p @ p)))
+    assert errs[0] < 5e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+# ------------------------------------------------------------ initial state --
+
+@pytest.mark.parametrize("stepper", ["bdf", "cdf2", "dirk"])
+def test_initial_state_poisson_and_projection(stepper):
+    wl = workloads.drifting_cloud(n=3000, nx=16, ny=12)
+    cfg = pic.Config(nx=16, ny=12, lx=1.0, ly=1.0, dt=wl.dt, p=2, stepper=stepper,
+                     w=wl.weight, dirk=steppers.DIRK2_QIN_ZHANG)
+    st = pic.initial_state(cfg, wl.x, wl.y, wl.vx, wl.vy)
+    kx, ky, K = spectral.wavenumber_grid(16, 12, 1.0, 1.0)
+    raw = spectral.dft2(pic.deposit(cfg, st.x, st.y, np.full(len(st.x), cfg.w * cfg.q)))
+    rho_hat = spectral.dft2(st.grids["rho"])
+    phi_hat = spectral.dft2(st.grids["phi"])
+    np.testing.assert_allclose(rho_hat[K > 0], raw[K > 0], atol=1e-9)
+    assert np.max(np.abs(rho_hat[K == 0])) < 1e-9
+    np.testing.assert_allclose(K * phi_hat, rho_hat, atol=1e-8)     # -Lap phi = rho/eps0
+    np.testing.assert_allclose(st.px, st.vx / np.sqrt(1 - st.vx ** 2 - st.vy ** 2), rtol=1e-14)
+
+
+# ----------------------------------------------------------- free streaming --
+
+def test_free_streaming_with_zero_charge():
+    wl = workloads.weibel(16, 16, 4, 0.5, 0.01, 7, 3, "bdf", 2, 10)
+    cfg = pic.Config(nx=16, ny=16, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=3, stepper="bdf",
+                     bdf_order=2, q=0.0, w=wl.weight)
+    st = pic.run(cfg, wl.x, wl.y, wl.vx, wl.vy, 10)
+    dxp = np.mod(st.x - (wl.x + 10 * wl.dt * wl.vx) + 0.5 * wl.lx, wl.lx) - 0.5 * wl.lx
+    dyp = np.mod(st.y - (wl.y + 10 * wl.dt * wl.vy) + 0.5 * wl.ly, wl.ly) - 0.5 * wl.ly
+    assert np.max(np.abs(dxp)) < 1e-13 and np.max(np.abs(dyp)) < 1e-13
+    np.testing.assert_allclose(st.vx, wl.vx, rtol=1e-13)
+    for name in pic.FIELD_NAMES:
+        assert np.max(np.abs(st.grids[name])) == 0.0
+
+
+# ---------------------------------------------------------- plasma physics --
+
+def _lattice(nx, ny, lx, ly, sub):
+    gx = (np.arange(nx * sub) + 0.5) * lx / (nx * sub)
+    gy = (np.arange(ny * sub) + 0.5) * ly / (ny * sub)
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    return X.ravel(), Y.ravel()
+
+
+def _frequency(t, s):
+    z = np.where(np.sign(s[1:]) != np.sign(s[:-1]))[0]
+    tz = t[z] - s[z] * (t[z + 1] - t[z]) / (s[z + 1] - s[z])
+    return np.pi / np.mean(np.diff(tz))
+
+
+@pytest.mark.parametrize("stepper", ["cdf2", "dirk", "bdf"])
+def test_uniform_mode_oscillates_at_plasma_frequency(stepper):
+    # Every electron drifts with the same small v: the k = 0 mode of A obeys
+    # A'' = mu0 c^2 J = -omega_pe^2 (A + P), so v oscillates at omega_pe = 1.
+    nx = ny = 4
+    x, y = _lattice(nx, ny, 1.0, 1.0, 2)
+    n = len(x)
+    cfg = pic.Config(nx=nx, ny=ny, lx=1.0, ly=1.0, dt=0.05, p=2, stepper=stepper, bdf_order=2,
+                     dirk=steppers.DIRK2_QIN_ZHANG, w=1.0 / n)
+    st = pic.initial_state(cfg, x, y, np.full(n, 0.01), np.zeros(n))
+    t, s = [], []
+    for k in range(300):
+        pic.step(cfg, st)
+        t.append((k + 1) * cfg.dt)
+        s.append(st.vx.mean())
+    w = _frequency(np.array(t), np.array(s))
+    assert abs(w - 1.0) < 0.01, w
+
+
+def test_langmuir_oscillation_frequency():
+    # Cold electrons, velocity perturbation along x with wavenumber 1: the
+    # electrostatic mode oscillates at omega_pe times the deposit/gather transfer
+    # factor S(k) = sinc(k dx / 2)^(p+1) = 0.99519 (p = 2, k dx = 2 pi/32).  IAEM
+    # couples particles and fields at first order in dt, so the measured frequency
+    # carries an O(dt) shift: check the first-order rate and the extrapolation.
+    nx, ny = 32, 4
+    lx = 2 * np.pi
+    ly = lx * ny / nx
+    x, y = _lattice(nx, ny, lx, ly, 2)
+    n = len(x)
+    ws = []
+    for dt in (0.025, 0.0125):
+        cfg = pic.Config(nx=nx, ny=ny, lx=lx, ly=ly, dt=dt, p=2, stepper="cdf2", w=lx * ly / n)
+        st = pic.initial_state(cfg, x, y, 1e-3 * np.sin(x), np.zeros(n))
+        t, s = [], []
+        for k in range(int(round(13.0 / dt))):
+            pic.step(cfg, st)
+            t.append((k + 1) * cfg.dt)
+            s.append(np.sum(st.vx * np.sin(st.x)))
+        ws.append(_frequency(np.array(t), np.array(s)))
+    w0 = 2 * ws[1] - ws[0]
+    sk = (np.sin(np.pi / 32) / (np.pi / 32)) ** 3
+    assert abs(w0 - sk) < 0.004, (ws, w0, sk)
+    assert 1.3 < (ws[0] - w0) / (ws[1] - w0) < 2.7
+
+
+# ------------------------------------------------------- time consistency --
+
+STEPPERS = [
+    ("bdf", 1, None), ("bdf", 2, None), ("bdf", 3, None), ("cdf2", 1, None),
+    ("dirk", 1, steppers.DIRK2_QIN_ZHANG), ("dirk", 1, steppers.DIRK3_MIDPOINT),
+]
+
+
+def _run_cloud(stepper, k, tab, nsteps=25, p=2):
+    wl = workloads.drifting_cloud(n=4000, nx=16, ny=16, seed=4)
+    cfg = pic.Config(nx=16, ny=16, lx=1.0, ly=1.0, dt=wl.dt, p=p, stepper=stepper,
+                     bdf_order=k, dirk=tab, w=wl.weight)
+    st = pic.initial_state(cfg, wl.x, wl.y, wl.vx, wl.vy)
+    hist = []
+    for _ in range(nsteps):
+        pic.step(cfg, st)
+        rho_scale = np.max(np.abs(spectral.dft2(st.grids["rho"])))
+        hist.append((dict(st.res), rho_scale))
+    return cfg, st, hist
+
+
+@pytest.mark.parametrize("stepper,k,tab", STEPPERS)
+def test_gauge_and_continuity_hold_to_roundoff(stepper, k, tab):
+    cfg, st, hist = _run_cloud(stepper, k, tab)
+    for res, rho_scale in hist:
+        assert np.max(np.abs(res["continuity"])) < 1e-12 * rho_scale / cfg.dt
+        gauge_scale = rho_scale / cfg.dt if stepper != "dirk" else rho_scale * cfg.dt
+        assert np.max(np.abs(res["gauge"])) < 1e-11 * gauge_scale
+        if stepper == "dirk":
+            assert np.max(np.abs(res["gauge_dt"])) < 1e-11 * rho_scale
+
+
+@pytest.mark.parametrize("stepper,k,tab", STEPPERS)
+def test_gauss_law(stepper, k, tab):
+    cfg, st, hist = _run_cloud(stepper, k, tab)
+    for res, rho_scale in hist:
+        err = np.max(np.abs(res["gauss"]))
+        if stepper == "dirk":
+            continue
+        assert err < 1e-11 * rho_scale, (err, rho_scale)
+    if stepper == "dirk":
+        # Not a theorem for DIRK (remark at the end of section 3.3.2): it must be visibly nonzero.
+        assert np.max(np.abs(hist[-1][0]["gauss"])) > 1e-8 * hist[-1][1]
+
+
+def test_dirk_gauge_residual_obeys_stepper_recurrence():
+    # Writing X = (phi, v_phi) and Y = (div A, div v_A), both evolve with the same
+    # per-mode DIRK map (section 3.3.1), so the gauge pair E = (eps_1, eps_2) obeys
+    # E^{n+1} = M E^n + (N0 eps_3^n + N1 eps_3^{n+1}) / eps0, driven only by the
+    # continuity residual eps_3.  Plant a continuity violation at n = 0 (rho^0 bumped
+    # after the equilibrium phi^0 was set up): the recurrence then predicts
+    # E^1 = -(N0 + N1) bump / eps0, the response of the wave map to a constant
+    # source bump/eps0 from rest, whatever the particles do.
+    tab = steppers.DIRK2_QIN_ZHANG
+    wl = workloads.drifting_cloud(n=2000, nx=8, ny=8, seed=6)
+    cfg = pic.Config(nx=8, ny=8, lx=1.0, ly=1.0, dt=wl.dt, p=2, stepper="dirk", dirk=tab,
+                     w=wl.weight)
+    st = pic.initial_state(cfg, wl.x, wl.y, wl.vx, wl.vy)
+    _, _, K = spectral.wavenumber_grid(8, 8, 1.0, 1.0)
+    bump = np.zeros((8, 8), complex)
+    bump[1, 2] = 1e-3
+    bump[7, 6] = 1e-3
+    st.hist["rho"] = st.hist["rho"] + bump
+    pic.step(cfg, st)
+    u1, v1 = steppers.dirk_wave_update(np.zeros_like(bump), np.zeros_like(bump), bump, bump,
+                                       K, cfg.c, cfg.dt, tab["A"], tab["b"], tab["c"])
+    np.testing.assert_allclose(st.res["gauge"], -u1 / cfg.eps0, atol=1e-14)
+    np.testing.assert_allclose(st.res["gauge_dt"], -v1 / cfg.eps0, atol=1e-13)
+    assert np.max(np.abs(st.res["gauge"])) > 1e-7
+
+
+def test_planted_continuity_sign_error_breaks_gauge(monkeypatch):
+    # A sign mistake in the BDF continuity update must be caught by the gauge pin.
+    orig = steppers.bdf_continuity
+
+    def wrong(rho_hist, div_j_new, dt, a, beta):
+        return orig(rho_hist, -div_j_new, dt, a, beta)
+
+    monkeypatch.setattr(steppers, "bdf_continuity", wrong)
+    cfg, st, hist = _run_cloud("bdf", 2, None, nsteps=5)
+    res, rho_scale = hist[-1]
+    assert np.max(np.abs(res["gauge"])) > 1e-6 * rho_scale / cfg.dt
+
+
+def test_planted_coefficient_error_breaks_gauge(monkeypatch):
+    orig = steppers.bdf_second_derivative_coefficients
+
+    def wrong(a):
+        C = orig(a)
+        C[2] = C[2] * (1 + 1e-3)
+        return C
+
+    monkeypatch.setattr(steppers, "bdf_second_derivative_coefficients", wrong)
+    cfg, st, hist = _run_cloud("bdf", 2, None, nsteps=8)
+    res, rho_scale = hist[-1]
+    assert np.max(np.abs(res["gauge"])) > 1e-9 * rho_scale / cfg.dt
+
+
+def test_energies_are_finite_and_bounded():
+    cfg, st, _ = _run_cloud("cdf2", 1, None, nsteps=10)
+    e = pic.energies(cfg, st)
+    assert all(np.isfinite(v) and v >= 0 for v in e.values())
