@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Throughput of the gauge-conserving spectral PIC step on GB300 (particle-steps/s).
+
+Default workload: the 128x128 relativistic Weibel set-up -- 64 macro-electrons per
+cell (1,048,576), counter-streaming beams +-0.5c along y, u_th = 0.01c, cubic
+B-splines, dt = 0.4 dx, BDF-2 -- run through the C ABI of libgpic (pic_deposit,
+pic_field_solve, pic_gather_push).  Inputs are the seeded synthetic initial
+conditions of paper_2410_18414_gb300.workloads, resident in HBM before timing.
+
+Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
+events on the library's stream, with a 256 MiB device write between steps
+(outside the events) so that every timed step starts with a cold L2.  With more
+than one GPU (torchrun), every rank runs an independent replica (its own seed):
+weak scaling, no collective on the data path; the timed region is the max over
+ranks.  `--impl reference` times the CPU oracle instead (see run_reference).
+
+One JSON line is printed by rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s"
+STEPPER_NAMES = {"bdf1": ("bdf", 1), "bdf2": ("bdf", 2), "cdf2": ("cdf2", 1), "dirk2": ("dirk", 1),
+                 "dirk3": ("dirk", 1)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default="bdf2")
+    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-steppers", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- workload --
+
+def make_workload(seed):
+    from paper_2410_18414_gb300 import workloads
+    return workloads.weibel(128, 128, 64, 0.5, 0.01, seed, 3, "bdf", 2, 2000)
+
+
+def dirk_tableau(name):
+    # Butcher tableaux of the readings used for DIRK-2 (Qin-Zhang) and DIRK-3.
+    if name == "dirk2":
+        return {"A": [[0.25, 0.0], [0.5, 0.25]], "b": [0.5, 0.5], "c": [0.25, 0.75]}
+    return {"A": [[1 / 6, 0, 0], [1 / 3, 1 / 6, 0], [1 / 3, 1 / 3, 1 / 6]],
+            "b": [1 / 3, 1 / 3, 1 / 3], "c": [1 / 6, 0.5, 5 / 6]}
+
+
+def make_config(wl, stepper_name):
+    from paper_2410_18414_gb300 import pic
+    stepper, k = STEPPER_NAMES[stepper_name]
+    dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
+    return pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper=stepper,
+                           bdf_order=k, dirk=dirk, weight=wl.weight)
+
+
+def workload_desc(wl, stepper_name):
+    return {"workload": f"weibel_{wl.nx}x{wl.ny}_ppc64_cubic_{stepper_name}",
+            "nx": wl.nx, "ny": wl.ny, "particles_per_gpu": wl.n, "spline_order": wl.p,
+            "stepper": stepper_name, "dt": wl.dt, "v_drift": 0.5, "u_th": 0.01}
+
+
+# --------------------------------------------------- algorithmic op counts --
+# Per particle, counted from the arithmetic the method needs (see the design notes):
+# weights of one axis for degree p (incl. x/dx), gather: one weight product and 8
+# FMAs per node, IAEM push 31 flops; deposit: move 4, per node 2 products + 2 adds.
+WEIGHT_FLOPS = {2: 10, 3: 19, 4: 39}
+
+
+def flops_gather_push(p):
+    return 2 * WEIGHT_FLOPS[p] + 17 * (p + 1) ** 2 + 31
+
+
+def flops_move_deposit(p):
+    return 4 + 2 * WEIGHT_FLOPS[p] + 2 * (p + 1) + 4 * (p + 1) ** 2
+
+
+def bytes_gather_push(rsz):
+    return 12 * rsz     # read x, y, Px, Py, v^n, v^{n-1} (8); write Px, Py, v^{n+1} (4)
+
+
+def bytes_move_deposit(rsz):
+    return 6 * rsz      # read x, y, v^n (4); write x, y (2)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "hbm_src": "fallback", "fp64_gflops": 1250.0,
+           "fp64_src": "nominal GB300 FP64 (profiling recipe table)"}
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        out["hbm_gbs"] = float(m["hbm_gbs"])
+        out["hbm_src"] = "measured"
+    except Exception:
+        pass
+    return out
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle --
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import pic as opic
+from paper_2410_18414_gb300 import workloads
+wl = workloads.weibel(128, 128, 64, 0.5, 0.01, {seed}, 3, "bdf", 2, 2000)
+n = {n}
+x, y, vx, vy = wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n]
+cfg = opic.Config(nx=128, ny=128, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=3, stepper={stepper!r},
+                  bdf_order={k}, dirk={dirk!r}, w=wl.lx * wl.ly / n)
+st = opic.initial_state(cfg, x, y, vx, vy)
+for _ in range({warmup}):
+    opic.step(cfg, st)
+times = []
+for _ in range({steps}):
+    t0 = time.perf_counter()
+    opic.step(cfg, st)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times}}))
+"""
+
+
+def run_oracle(stepper_name, n, steps, warmup, seed=2):
+    stepper, k = STEPPER_NAMES[stepper_name]
+    dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
+    code = ORACLE_SNIPPET.format(root=ROOT, seed=seed, n=n, stepper=stepper, k=k, dirk=dirk,
+                                 warmup=warmup, steps=steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    times = json.loads(r.stdout.strip().splitlines()[-1])["times"]
+    return times
+
+
+def cpu_baseline(stepper_name):
+    n = 262144
+    steps = 4
+    times = run_oracle(stepper_name, n, steps, 1)
+    v = n * len(times) / sum(times)
+    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle, single thread, 128x128 grid with the first {n} of the "
+                      f"1,048,576 particles (weight rescaled), {steps} timed steps after 1 warm-up, "
+                      f"{sum(times):.1f} s"}
+
+
+def run_reference(a):
+    """The reference arm: the CPU oracle on the host cores, bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 131072
+    times = run_oracle(a.stepper, n, a.steps, a.warmup)
+    total = sum(times)
+    value = n * len(times) / total
+    wl_desc = workload_desc(make_workload(2), a.stepper)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(wl_desc, form="fp64", sample_particles=n, parallelism="replicas"),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the numpy FP64 oracle on the 128x128 grid with "
+                                       f"the first {n} particles, single thread"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def time_steps(sim, steps, warmup, stream, flush):
+    import torch
+    for _ in range(warmup):
+        sim.step(1)
+        flush.zero_()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        e = ev[k]
+        e[0].record(stream)
+        sim.deposit()
+        e[1].record(stream)
+        sim.field_solve()
+        e[2].record(stream)
+        sim.gather_push()
+        e[3].record(stream)
+        flush.zero_()       # cold L2 for the next step (outside the events)
+    torch.cuda.synchronize()
+    dep = [e[0].elapsed_time(e[1]) for e in ev]
+    fld = [e[1].elapsed_time(e[2]) for e in ev]
+    psh = [e[2].elapsed_time(e[3]) for e in ev]
+    tot = [e[0].elapsed_time(e[3]) for e in ev]
+    return {"deposit_ms": dep, "field_ms": fld, "push_ms": psh, "step_ms": tot}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    from paper_2410_18414_gb300 import pic
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pic.load_library()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    wl = make_workload(2 + rank)
+    cfg = make_config(wl, a.stepper)
+    sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = time_steps(sim, a.steps, a.warmup, stream, flush)
+    clk = clocks.stop()
+    barrier()
+    sim.sync()
+    total_ms = sum(t["step_ms"])
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    n_all = wl.n * world
+    value = n_all * a.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (per-launch averages from the events above)
+    pk = peaks()
+    rsz = 8
+    p = wl.p
+    dep_ms = statistics.mean(t["deposit_ms"])
+    psh_ms = statistics.mean(t["push_ms"])
+    fld_ms = statistics.mean(t["field_ms"])
+    kern = {
+        "gather_push": {"ms": psh_ms, "flops": flops_gather_push(p) * wl.n,
+                        "bytes": bytes_gather_push(rsz) * wl.n},
+        "move_deposit": {"ms": dep_ms, "flops": flops_move_deposit(p) * wl.n,
+                         "bytes": bytes_move_deposit(rsz) * wl.n},
+    }
+    for k in kern.values():
+        k["gflops"] = k["flops"] / (k["ms"] * 1e-3) / 1e9
+        k["gbs"] = k["bytes"] / (k["ms"] * 1e-3) / 1e9
+        k["frac_fp64_alu"] = k["gflops"] / pk["fp64_gflops"]
+        k["frac_hbm"] = k["gbs"] / pk["hbm_gbs"]
+    dom_name = max(kern, key=lambda k: kern[k]["ms"])
+    dom = kern[dom_name]
+    roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
+                "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
+                "frac": dom["gflops"] / pk["fp64_gflops"], "traffic": None,
+                "peak_source": pk["fp64_src"],
+                "hbm": {"achieved_gbs": dom["gbs"], "peak_gbs": pk["hbm_gbs"],
+                        "frac": dom["gbs"] / pk["hbm_gbs"], "peak_source": pk["hbm_src"]}}
+
+    # other steppers of the same workload (shorter runs)
+    by_stepper = {a.stepper: total_ms / a.steps}
+    if not a.no_extra_steppers:
+        for name in ("bdf2", "cdf2", "dirk2"):
+            if name == a.stepper:
+                continue
+            s2 = pic.Simulation(make_config(wl, name), wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+            t2 = time_steps(s2, max(10, a.steps // 5), 3, stream, flush)
+            by_stepper[name] = statistics.mean(t2["step_ms"])
+            s2.close()
+
+    # end to end through the public API with pinned host buffers
+    host = {k: torch.from_numpy(getattr(wl, k).copy()).pin_memory() for k in ("x", "y", "vx", "vy")}
+    outs = {k: torch.empty(wl.n, dtype=torch.float64).pin_memory()
+            for k in ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s3 = pic.Simulation(cfg, host["x"], host["y"], host["vx"], host["vy"], stream=sp)
+    s3.step(a.steps)
+    s3.particles(outs)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s3.close()
+    e2e = {"value": n_all * a.steps / e2e_s if world == 1 else None, "unit": METRIC,
+           "h2d_bytes_per_step": 4 * 8 * wl.n / a.steps,
+           "d2h_bytes_per_step": 8 * 8 * wl.n / a.steps,
+           "includes": "pic_init from pinned host arrays (incl. device allocation and t=0 solve), "
+                       "K steps, read-back of all 8 particle arrays"}
+    if dist:
+        ee = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ee, op=dist.ReduceOp.MAX)
+        e2e["value"] = n_all * a.steps / float(ee.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(a.stepper)
+        except Exception as exc:  # the line still prints; the failure is stated
+            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_desc(wl, a.stepper), form="fp64",
+                           l2="flushed between timed steps (256 MiB device write)",
+                           parallelism="replicas" if world > 1 else "single"),
+            "roofline": roofline,
+            "kernels": {k: {kk: round(vv, 6) if isinstance(vv, float) else vv
+                            for kk, vv in v.items()} for k, v in kern.items()},
+            "phase_ms": {"deposit": dep_ms, "field_solve": fld_ms, "gather_push": psh_ms},
+            "by_stepper_ms_per_step": by_stepper,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": sim.kernels_per_step * a.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * pic.h -- C ABI of the GB300 gauge-conserving spectral PIC library (libgpic.so).
+ *
+ * The library advances the particle-in-cell method of Christlieb, Sands and White,
+ * "A PIC method with a generalized-momentum formulation, Part III: a family of
+ * gauge-conserving methods" (arXiv 2410.18414), on a 2-D doubly periodic grid with
+ * two velocity components, one time step being Algorithm 1 of section 4.2:
+ *
+ *   x^{n+1} = x^n + v^n dt                                   (IAEM, section 4.1)
+ *   J^{n+1} = sum_p q_p v^n_p S(x - x^{n+1}_p)                (section 2.2, section 4)
+ *   rho^{n+1} from the semi-discrete continuity equation     (sections 3.1-3.3, Alg. 1)
+ *   phi, A at the new level from the implicit wave solve of the chosen stepper
+ *     (CDF-2 implicit: section 3.1; BDF-k: section 3.2; s-stage DIRK: section 3.3)
+ *   grad phi~, A, grad A spectrally (section 4), gathered with the same shape S
+ *   P^{n+1} = P^n + q(-grad phi~ + grad A . v*) dt, v* = 2 v^n - v^{n-1};
+ *   v^{n+1} = c^2 (P - qA) / sqrt(c^2 |P - qA|^2 + (m c^2)^2)  (section 4.1)
+ *
+ * Conventions shared by every call:
+ *   - All work runs on one CUDA device, enqueued on the stream given to pic_init
+ *     (0 = the legacy default stream).  Calls that only enqueue work return before
+ *     it finishes; calls that return data to the host synchronize that stream.
+ *   - Pointers named "src"/"dst" may be host or device memory (unified addressing
+ *     decides; pinned host memory is fastest).  The library never keeps them.
+ *   - Device memory for the simulation state is owned by the handle and released
+ *     by pic_destroy.  No call frees memory it did not allocate.
+ *   - Every call returns a pic_status.  Argument errors are reported synchronously
+ *     and leave the handle unchanged.  Errors found on the device (non-finite
+ *     particle data, fixed-point overflow) are latched in a device word and
+ *     reported by the next call that synchronizes (pic_sync, pic_residuals,
+ *     pic_read_particles, pic_get_field).  No call aborts the process;
+ *     pic_last_error gives a one-line description of the last failure.
+ *   - Grid arrays are (nx, ny) row-major with y fastest: node (i, j) at
+ *     (i*dx, j*dy) is element i*ny + j.
+ */
+#ifndef GPIC_PIC_H
+#define GPIC_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_handle pic_handle; /* opaque, owned by the library */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_INVALID_ARG = 1, /* a size, pointer or parameter outside its range     */
+    PIC_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement      */
+    PIC_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed        */
+    PIC_ERR_NONFINITE = 4,   /* a particle momentum or velocity became inf/NaN     */
+    PIC_ERR_OVERFLOW = 5,    /* the int64 fixed-point current would overflow       */
+    PIC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                      */
+    PIC_ERR_STATE = 7        /* the call needs state that is not available yet     */
+} pic_status;
+
+/* Time stepper for the wave equations of phi and A (section 3). */
+typedef enum {
+    PIC_STEPPER_BDF = 0,  /* BDF-k, k = bdf_order in 1..6 (section 3.2)               */
+    PIC_STEPPER_CDF2 = 1, /* implicit centred CDF-2, phi at half levels (section 3.1) */
+    PIC_STEPPER_DIRK = 2  /* s-stage DIRK with the tableau in pic_config (section 3.3) */
+} pic_stepper;
+
+typedef enum {
+    PIC_FP64 = 0,        /* the plain path: everything in FP64                          */
+    PIC_FP32_FIX64 = 1   /* FP32 particles and FFT, current summed in int64 fixed point */
+} pic_precision;
+
+/* Grid quantities readable with pic_get_field (all real nx*ny arrays, FP64). */
+typedef enum {
+    PIC_FIELD_JX = 0, PIC_FIELD_JY = 1,      /* J^{n+1} of the last step                  */
+    PIC_FIELD_RHO = 2,                        /* newest rho (CDF: rho^{n+3/2})             */
+    PIC_FIELD_PHI = 3,                        /* newest phi (CDF: phi^{n+3/2})             */
+    PIC_FIELD_AX = 4, PIC_FIELD_AY = 5,      /* A^{n+1}                                   */
+    PIC_FIELD_BZ = 6,                         /* dAy/dx - dAx/dy at n+1                    */
+    PIC_FIELD_EX = 7, PIC_FIELD_EY = 8,      /* stepper's discrete E (needs diagnostics)  */
+    PIC_FIELD_DPHIDX = 9, PIC_FIELD_DPHIDY = 10,  /* the eight fields the particles      */
+    PIC_FIELD_GAX = 11, PIC_FIELD_GAY = 12,       /* gather: grad phi~, A, grad A        */
+    PIC_FIELD_DAXDX = 13, PIC_FIELD_DAXDY = 14,
+    PIC_FIELD_DAYDX = 15, PIC_FIELD_DAYDY = 16
+} pic_field;
+
+typedef struct {
+    int32_t nx, ny;          /* grid nodes per direction, each 8..4096, of the form 2^a 3^b */
+    int32_t spline_order;    /* B-spline degree p of the particle shape: 2, 3 or 4          */
+    int32_t stepper;         /* pic_stepper                                                 */
+    int32_t bdf_order;       /* k for PIC_STEPPER_BDF (1..6)                                */
+    int32_t dirk_stages;     /* s for PIC_STEPPER_DIRK (1..4)                               */
+    int32_t precision;       /* pic_precision                                               */
+    int32_t sort_interval;   /* re-sort particles by tile every this many steps; 0 = never  */
+    double lx, ly;           /* periodic domain [0,lx) x [0,ly)                             */
+    double c, eps0;          /* speed of light and permittivity; mu0 = 1/(eps0 c^2)         */
+    double dt;               /* time step                                                   */
+    double q, m;             /* charge and mass of one physical particle                    */
+    double weight;           /* macro-particle weight: deposits charge weight*q             */
+    double dirk_a[16];       /* s x s Butcher matrix, row-major (lower triangular)          */
+    double dirk_b[4];        /* Butcher weights                                             */
+    double dirk_c[4];        /* Butcher nodes                                               */
+    int32_t reserved[8];     /* must be zero                                                */
+} pic_config;
+
+/* Initial particle state: positions x^0 (wrapped into the domain by pic_init) and
+ * velocities v^0 (|v^0| < c).  Arrays of n FP64 values, host or device. */
+typedef struct {
+    const double *x, *y, *vx, *vy;
+    int64_t n;
+} pic_particles_in;
+
+/* Diagnostics of the last step that ran with diagnostics enabled (all FP64).
+ * *_rms are grid root-mean-square values (Parseval over all modes). */
+typedef struct {
+    double gauge_rms;      /* Lorenz-gauge residual eps_1 of the stepper (sections 3.1-3.3) */
+    double gauss_rms;      /* div E - rho/eps0 with the stepper's E                         */
+    double continuity_rms; /* semi-discrete continuity residual                             */
+    double gauge_dt_rms;   /* DIRK only: residual of the time-differentiated gauge (eps_2)  */
+    double rho_rms;        /* RMS of rho/eps0 (scale for gauss_rms)                         */
+    double div_a_rms;      /* RMS of div A^{n+1} (scale for gauge_rms)                      */
+    double w_e;            /* eps0/2 sum |E|^2 dx dy                                        */
+    double w_b;            /* 1/(2 mu0) sum B_z^2 dx dy                                     */
+    double kinetic;        /* sum_p weight m c^2 (gamma_p - 1)                              */
+    int64_t step;          /* step index n+1 these values belong to                         */
+} pic_diagnostics;
+
+/* Create a simulation: validate cfg, copy the initial particles to the device and
+ * build the t = 0 state (section 4.2, Algorithm 1 set-up): rho^0 by depositing the
+ * charge with its K = 0 modes removed (neutralising background), phi^0 from
+ * Poisson's equation, A^0 = 0, P^0 = gamma m v^0, v^{-1} by a first-order Taylor
+ * step back in E^0 = -grad phi^0, and every history level at its t = 0 value.
+ * On success *out receives the handle.  The stream must outlive the handle. */
+pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,
+                    pic_handle **out);
+
+/* Algorithm 1, first two lines: move every particle with v^n (wrapping into the
+ * domain) and deposit J^{n+1} with the new positions and v^n.  Re-sorts the
+ * particles first when sort_interval says so. */
+pic_status pic_deposit(pic_handle *h);
+
+/* Algorithm 1, charge and field lines: FFT of J^{n+1}, rho^{n+1} from continuity,
+ * the implicit per-mode wave update of phi and A, and the eight spectral gradient
+ * fields on the grid.  Needs a preceding pic_deposit of the same step. */
+pic_status pic_field_solve(pic_handle *h);
+
+/* Algorithm 1, particle lines: gather the eight fields at x^{n+1}, IAEM momentum
+ * update with v*, new velocity; then shift the time histories (end of the step). */
+pic_status pic_gather_push(pic_handle *h);
+
+/* nsteps complete steps (deposit, field solve, gather/push each). */
+pic_status pic_step(pic_handle *h, int32_t nsteps);
+
+/* Compute diagnostics every `every` steps (0 = never, the default).  They cost one
+ * extra reduction over modes and particles per diagnosed step. */
+pic_status pic_set_diagnostics(pic_handle *h, int32_t every);
+
+/* Copy the diagnostics of the last diagnosed step to *out (synchronizes).
+ * PIC_ERR_STATE if no step has been diagnosed yet. */
+pic_status pic_residuals(pic_handle *h, pic_diagnostics *out);
+
+/* Copy one real nx*ny grid quantity of the last step into dst (FP64, host or
+ * device).  PIC_ERR_STATE for EX/EY unless the last step was diagnosed, and for
+ * every field before the first step except RHO and PHI. Synchronizes. */
+pic_status pic_get_field(pic_handle *h, int32_t which, double *dst);
+
+/* Copy the particle state, in the order the particles were given to pic_init, into
+ * FP64 arrays of n values (host or device).  Any pointer may be NULL to skip it.
+ * x, y: x^n; px, py: P^n; vx, vy: v^n; vx_old, vy_old: v^{n-1}.  Synchronizes. */
+pic_status pic_read_particles(pic_handle *h, double *x, double *y, double *px, double *py,
+                              double *vx, double *vy, double *vx_old, double *vy_old);
+
+/* Wait for all work enqueued by this handle; report latched device errors. */
+pic_status pic_sync(pic_handle *h);
+
+/* Steps completed since pic_init. */
+int64_t pic_step_count(const pic_handle *h);
+
+/* Number of CUDA kernels one step launches (for launch accounting). */
+int32_t pic_kernels_per_step(const pic_handle *h);
+
+/* One-line description of the last failure on this handle (or of the last failed
+ * pic_init when h is NULL).  Valid until the next call on the handle. */
+const char *pic_last_error(const pic_handle *h);
+
+/* Release every device allocation of the handle.  NULL is allowed. */
+void pic_destroy(pic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPIC_PIC_H */

@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of libgpic: kernel
+// launchers and their parameter blocks.  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpic {
+
+constexpr int kMaxRadices = 16;
+constexpr int kMaxBdf = 6;
+constexpr int kMaxDirk = 4;
+
+// 1-D transform description: length n = prod(radix[0..nf-1]), radices in {2,3,4}.
+struct FftDesc {
+    int n;
+    int nf;
+    int radix[kMaxRadices];
+};
+
+// Diagnostic accumulators (device, FP64): sums of |.|^2 over modes and particles.
+enum DiagSlot {
+    D_GAUGE = 0, D_GAUSS, D_CONT, D_GAUGE_DT, D_RHO, D_DIVA, D_WE, D_WB, D_KIN, D_NSLOTS
+};
+
+// Per-mode kernel parameters common to all steppers.
+struct ModeCommon {
+    int nx, ny;
+    double kx_scale, ky_scale;  // 2 pi / L
+    double jscale;              // q_p / (dx dy): raw deposit sums -> current density
+    double inv_n;               // 1 / (nx ny): inverse-FFT normalisation folded in
+    double eps0, mu0, c, dt;
+    int diag;                   // accumulate diagnostics this step
+};
+
+struct BdfParams {
+    int k;
+    double a[kMaxBdf + 1];
+    double C[2 * kMaxBdf + 1];
+    double g;    // (c beta dt)^2
+    double bdt;  // beta dt
+    // history, newest first: hist[d-1] is level n+1-d
+    void* phi[2 * kMaxBdf];
+    void* ax[2 * kMaxBdf];
+    void* ay[2 * kMaxBdf];
+    void* rho[kMaxBdf];
+    // where the new level goes (the slot of the oldest level, read first)
+    void* phi_new;
+    void* ax_new;
+    void* ay_new;
+    void* rho_new;
+};
+
+struct CdfParams {
+    // levels: phi^{n+1/2}, phi^{n-1/2} (new phi^{n+3/2} overwrites phi_prev), same for rho;
+    // A^n, A^{n-1} (new A^{n+1} overwrites *_prev); J^n, J^{n-1} (new J overwrites j_prev)
+    void *phi, *phi_prev, *rho, *rho_prev, *ax, *ax_prev, *ay, *ay_prev;
+    void *jx, *jx_prev, *jy, *jy_prev;
+};
+
+struct DirkParams {
+    int s;
+    double a[kMaxDirk * kMaxDirk];
+    double b[kMaxDirk];
+    double c[kMaxDirk];
+    double r0, r1;
+    // state at level n, updated in place
+    void *phi, *vphi, *ax, *vax, *ay, *vay, *rho, *jx, *jy;
+};
+
+enum StepperKind { K_BDF = 0, K_CDF2 = 1, K_DIRK = 2 };
+
+// ---------------------------------------------------------------- launchers
+
+// In-place or out-of-place 1-D transforms of nb arrays of shape (nx, ny).
+// Along y (contiguous); out_interleave != 0 writes out[(i*ny + j)*nb + b].
+template <typename T>
+cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
+                         const void* twiddle, int sign, int out_interleave, cudaStream_t s);
+// Along x (stride ny).
+template <typename T>
+cudaError_t launch_fft_x(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
+                         const void* twiddle, int sign, cudaStream_t s);
+// exp(-2 pi i m / n), m = 0..n-1, computed in FP64.
+template <typename T>
+cudaError_t launch_twiddles(void* tw, int n, cudaStream_t s);
+
+// Per-mode kernels.
+template <typename T>
+cudaError_t launch_mode_init(const ModeCommon& mc, const void* zq, void* rho_out, void* phi_out,
+                             void* e_packed, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mode_bdf(const ModeCommon& mc, const BdfParams& bp, const void* z, void* f4,
+                            void* e_packed, double* diag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mode_cdf2(const ModeCommon& mc, const CdfParams& cp, const void* z, void* f4,
+                             void* e_packed, double* diag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mode_dirk(const ModeCommon& mc, const DirkParams& dp, const void* z, void* f4,
+                             void* e_packed, double* diag, cudaStream_t s);
+// Pack two spectra a + i b (scaled by inv_n) for an inverse transform to two real fields.
+template <typename T>
+cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,
+                              void* out, cudaStream_t s);
+
+// Particle kernels.
+struct ParticleGeom {
+    int nx, ny;
+    double lx, ly, inv_dx, inv_dy, dt;
+};
+
+template <typename T>
+cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
+                                const T* vy, int64_t n, double2* j, unsigned int* err,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
+                                  double2* j, unsigned int* err, cudaStream_t s);
+// dst[k] = component `comp` of the complex array src (element stride `stride` complex
+// values) times `scale`, as FP64.
+template <typename T>
+cudaError_t launch_extract(const void* src, int stride, int comp, double scale, double* dst,
+                           int64_t n, cudaStream_t s);
+
+struct PushParams {
+    double q, m, c, dt, weight;
+    int diag;
+};
+
+template <typename T>
+cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
+                               const T* y, T* px, T* py, const T* vx, const T* vy, T* vx_old,
+                               T* vy_old, int64_t n, const void* fields4, double* diag,
+                               unsigned int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_particles(int p, const ParticleGeom& g, const PushParams& pp, T* x, T* y,
+                                  T* px, T* py, const T* vx, const T* vy, T* vx_old, T* vy_old,
+                                  int64_t n, const void* e2, unsigned int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_wrap_positions(T* x, T* y, int64_t n, double lx, double ly, cudaStream_t s);
+template <typename Tsrc, typename Tdst>
+cudaError_t launch_convert(const Tsrc* src, Tdst* dst, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, int64_t n,
+                                 cudaStream_t s);
+
+// Device error word bits.
+enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };
+
+}  // namespace gpic

@@ -1,0 +1,664 @@
+// Host side of the C ABI declared in include/pic.h: the simulation handle, argument
+// checks, the t = 0 set-up and the three phases of one step (Algorithm 1, section 4.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gpic_internal.h"
+#include "pic.h"
+
+using namespace gpic;
+
+namespace {
+thread_local std::string g_init_error;
+}
+
+struct pic_handle {
+    pic_config cfg{};
+    cudaStream_t s = nullptr;
+    int device = 0;
+    int64_t n = 0;
+    bool fp32 = false;
+    size_t rsz = 8;
+    int p = 2;
+    int nx = 0, ny = 0;
+    size_t ng = 0;
+    // particle state (FP64 or FP32 by precision); v[buffer][component]
+    void *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr;
+    void* v[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
+    double* stage = nullptr;  // FP64 staging for conversions (n values)
+    // grid buffers
+    double2* J = nullptr;    // deposit accumulator (sum_p v W), FP64
+    void* Z = nullptr;       // spectrum of J (complex)
+    void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
+    void* G = nullptr;       // [node][4] complex: the eight real gather fields
+    void* E = nullptr;       // packed E spectrum of the last diagnosed step
+    void* tmp = nullptr;     // complex scratch (ng)
+    double* tmpd = nullptr;  // real scratch (ng)
+    void *twx = nullptr, *twy = nullptr;
+    FftDesc fx{}, fy{};
+    // time histories (BDF rings; CDF pairs; DIRK state)
+    std::vector<void*> phi_l, ax_l, ay_l, rho_l;
+    int L = 0, Lr = 0, head = 0, head_r = 0;
+    BdfParams bdf{};
+    CdfParams cdf{};
+    DirkParams dirk{};
+    // diagnostics and errors
+    double* diag = nullptr;
+    unsigned int* err = nullptr;
+    int diag_every = 0;
+    bool diag_now = false, diag_valid = false, e_valid = false;
+    int64_t diag_step = -1;
+    int64_t step = 0;
+    int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
+    bool stepped = false;
+    std::vector<void*> allocs;
+    ModeCommon mc{};
+    ParticleGeom geom{};
+    PushParams push{};
+    std::string errmsg;
+};
+
+namespace {
+
+pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->errmsg = buf;
+    else
+        g_init_error = buf;
+    return st;
+}
+
+#define CK(...)                                                                           \
+    do {                                                                                  \
+        cudaError_t e_ = (__VA_ARGS__);                                                        \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, PIC_ERR_CUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool factor_23(int n, FftDesc& d) {
+    d.n = n;
+    d.nf = 0;
+    int m = n;
+    while (m % 4 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 4; m /= 4; }
+    while (m % 2 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 2; m /= 2; }
+    while (m % 3 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 3; m /= 3; }
+    return m == 1;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+pic_status validate(const pic_config* c, const pic_particles_in* in) {
+    pic_handle* h = nullptr;
+    if (!c || !in) return fail(h, PIC_ERR_INVALID_ARG, "cfg and init must not be NULL");
+    for (int i = 0; i < 8; ++i)
+        if (c->reserved[i] != 0) return fail(h, PIC_ERR_INVALID_ARG, "reserved fields must be 0");
+    FftDesc d;
+    for (int n : {c->nx, c->ny})
+        if (n < 8 || n > 1024 || (n & 1) || !factor_23(n, d))
+            return fail(h, PIC_ERR_INVALID_ARG,
+                        "grid size %d must be even, 8..1024 and of the form 2^a 3^b", n);
+    if (c->spline_order < 2 || c->spline_order > 4)
+        return fail(h, PIC_ERR_INVALID_ARG, "spline_order must be 2, 3 or 4");
+    if (!finite_pos(c->lx) || !finite_pos(c->ly) || !finite_pos(c->c) || !finite_pos(c->eps0) ||
+        !finite_pos(c->dt) || !finite_pos(c->m) || !std::isfinite(c->q) ||
+        !std::isfinite(c->weight) || c->weight < 0)
+        return fail(h, PIC_ERR_INVALID_ARG,
+                    "lx, ly, c, eps0, dt, m must be finite and > 0; q finite; weight >= 0");
+    if (c->c * c->dt >= std::fmin(c->lx, c->ly))
+        return fail(h, PIC_ERR_INVALID_ARG, "c*dt must be below the domain size");
+    if (c->stepper == PIC_STEPPER_BDF) {
+        if (c->bdf_order < 1 || c->bdf_order > kMaxBdf)
+            return fail(h, PIC_ERR_INVALID_ARG, "bdf_order must be 1..6");
+    } else if (c->stepper == PIC_STEPPER_DIRK) {
+        const int s = c->dirk_stages;
+        if (s < 1 || s > kMaxDirk) return fail(h, PIC_ERR_INVALID_ARG, "dirk_stages must be 1..4");
+        for (int i = 0; i < s; ++i) {
+            if (!std::isfinite(c->dirk_b[i]) || !std::isfinite(c->dirk_c[i]))
+                return fail(h, PIC_ERR_INVALID_ARG, "DIRK tableau must be finite");
+            for (int j = 0; j < s; ++j) {
+                const double a = c->dirk_a[i * s + j];
+                if (!std::isfinite(a))
+                    return fail(h, PIC_ERR_INVALID_ARG, "DIRK tableau must be finite");
+                if (j > i && a != 0.0)
+                    return fail(h, PIC_ERR_INVALID_ARG, "DIRK matrix must be lower triangular");
+                if (j == i && a < 0.0)
+                    return fail(h, PIC_ERR_INVALID_ARG, "DIRK diagonal must be >= 0");
+            }
+        }
+    } else if (c->stepper != PIC_STEPPER_CDF2) {
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown stepper %d", c->stepper);
+    }
+    if (c->precision != PIC_FP64 && c->precision != PIC_FP32_FIX64)
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+    if (c->precision == PIC_FP32_FIX64)
+        return fail(h, PIC_ERR_UNSUPPORTED, "the FP32 fixed-point form is not built yet");
+    if (c->sort_interval < 0) return fail(h, PIC_ERR_INVALID_ARG, "sort_interval must be >= 0");
+    if (in->n < 0 || in->n > 2147483647LL)
+        return fail(h, PIC_ERR_INVALID_ARG, "particle count must be 0..2^31-1");
+    if (in->n > 0 && (!in->x || !in->y || !in->vx || !in->vy))
+        return fail(h, PIC_ERR_INVALID_ARG, "particle arrays must not be NULL");
+    return PIC_OK;
+}
+
+cudaError_t dalloc(pic_handle* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) h->allocs.push_back(*p);
+    return e;
+}
+
+void free_all(pic_handle* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+// Run f with a value of the storage type (double or float).
+template <typename F>
+cudaError_t by_prec(pic_handle* h, F&& f) {
+    if (h->fp32) return f(float{});
+    return f(double{});
+}
+
+cudaError_t forward_fft(pic_handle* h, const void* in, void* out) {
+    return by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t e = launch_fft_y<T>(in, out, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s);
+        if (e != cudaSuccess) return e;
+        return launch_fft_x<T>(out, out, h->nx, h->ny, 1, h->fx, h->twx, -1, h->s);
+    });
+}
+
+// Inverse transform of nb packed spectra in `buf` (in place along x), then along y
+// into `out` (interleaved by array when nb > 1).
+cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb) {
+    return by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t e = launch_fft_x<T>(buf, buf, h->nx, h->ny, nb, h->fx, h->twx, +1, h->s);
+        if (e != cudaSuccess) return e;
+        return launch_fft_y<T>(buf, out, h->nx, h->ny, nb, h->fy, h->twy, +1, nb > 1, h->s);
+    });
+}
+
+// Newest spectral level: 0 phi, 1 Ax, 2 Ay, 3 rho.
+void* newest(pic_handle* h, int which) {
+    switch (h->cfg.stepper) {
+        case PIC_STEPPER_BDF:
+            if (which == 3) return h->rho_l[h->head_r];
+            return (which == 0 ? h->phi_l : which == 1 ? h->ax_l : h->ay_l)[h->head];
+        case PIC_STEPPER_CDF2:
+            return which == 0 ? h->cdf.phi : which == 1 ? h->cdf.ax : which == 2 ? h->cdf.ay : h->cdf.rho;
+        default:
+            return which == 0 ? h->dirk.phi : which == 1 ? h->dirk.ax : which == 2 ? h->dirk.ay : h->dirk.rho;
+    }
+}
+
+pic_status check_device_error(pic_handle* h) {
+    unsigned int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (e & ERR_OVERFLOW) return fail(h, PIC_ERR_OVERFLOW, "fixed-point current overflow");
+    if (e & ERR_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_NONFINITE)
+        return fail(h, PIC_ERR_NONFINITE, "non-finite or out-of-domain particle data");
+    return PIC_OK;
+}
+
+pic_status alloc_state(pic_handle* h) {
+    const pic_config& c = h->cfg;
+    const size_t cs = 2 * h->rsz;
+    const size_t pn = (size_t)std::max<int64_t>(h->n, 1) * h->rsz;
+    CK(dalloc(h, &h->x, pn));
+    CK(dalloc(h, &h->y, pn));
+    CK(dalloc(h, &h->px, pn));
+    CK(dalloc(h, &h->py, pn));
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->v[b][k], pn));
+    CK(dalloc(h, (void**)&h->stage, (size_t)std::max<int64_t>(h->n, 1) * sizeof(double)));
+    CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
+    CK(dalloc(h, &h->Z, h->ng * cs));
+    CK(dalloc(h, &h->F4, 4 * h->ng * cs));
+    CK(dalloc(h, &h->G, 4 * h->ng * cs));
+    CK(dalloc(h, &h->E, h->ng * cs));
+    CK(dalloc(h, &h->tmp, h->ng * cs));
+    CK(dalloc(h, (void**)&h->tmpd, h->ng * sizeof(double)));
+    CK(dalloc(h, &h->twx, (size_t)c.nx * cs));
+    CK(dalloc(h, &h->twy, (size_t)c.ny * cs));
+    CK(dalloc(h, (void**)&h->diag, D_NSLOTS * sizeof(double)));
+    CK(dalloc(h, (void**)&h->err, sizeof(unsigned int)));
+    CK(cudaMemsetAsync(h->err, 0, sizeof(unsigned int), h->s));
+    CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
+
+    auto spec = [&](void** p) {
+        cudaError_t e = dalloc(h, p, h->ng * cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, h->ng * cs, h->s);
+        return e;
+    };
+    if (c.stepper == PIC_STEPPER_BDF) {
+        const int k = c.bdf_order;
+        h->L = 2 * k;
+        h->Lr = k;
+        h->phi_l.assign(h->L, nullptr);
+        h->ax_l.assign(h->L, nullptr);
+        h->ay_l.assign(h->L, nullptr);
+        h->rho_l.assign(h->Lr, nullptr);
+        for (int i = 0; i < h->L; ++i) {
+            CK(spec(&h->phi_l[i]));
+            CK(spec(&h->ax_l[i]));
+            CK(spec(&h->ay_l[i]));
+        }
+        for (int i = 0; i < h->Lr; ++i) CK(spec(&h->rho_l[i]));
+        // BDF-k with a_0 = 1 (section 3.2) from sum_{j=1..k} (1/j) nabla^j u = dt u'.
+        double alpha[kMaxBdf + 1] = {0};
+        for (int j = 1; j <= k; ++j) {
+            double binom = 1.0;
+            for (int i = 0; i <= j; ++i) {
+                alpha[i] += ((i & 1) ? -binom : binom) / j;
+                binom = binom * (j - i) / (i + 1);
+            }
+        }
+        h->bdf.k = k;
+        for (int i = 0; i <= k; ++i) h->bdf.a[i] = alpha[i] / alpha[0];
+        const double beta = 1.0 / alpha[0];
+        // C = a * a: coefficients of the twice-applied BDF operator (Table 1).
+        for (int d = 0; d <= 2 * k; ++d) {
+            double s = 0;
+            for (int j = 0; j <= d; ++j)
+                if (j <= k && d - j <= k) s += h->bdf.a[j] * h->bdf.a[d - j];
+            h->bdf.C[d] = s;
+        }
+        h->bdf.bdt = beta * c.dt;
+        h->bdf.g = (c.c * beta * c.dt) * (c.c * beta * c.dt);
+    } else if (c.stepper == PIC_STEPPER_CDF2) {
+        void** slots[] = {&h->cdf.phi, &h->cdf.phi_prev, &h->cdf.rho, &h->cdf.rho_prev,
+                          &h->cdf.ax,  &h->cdf.ax_prev,  &h->cdf.ay,  &h->cdf.ay_prev,
+                          &h->cdf.jx,  &h->cdf.jx_prev,  &h->cdf.jy,  &h->cdf.jy_prev};
+        for (void** sl : slots) CK(spec(sl));
+    } else {
+        void** slots[] = {&h->dirk.phi, &h->dirk.vphi, &h->dirk.ax, &h->dirk.vax, &h->dirk.ay,
+                          &h->dirk.vay, &h->dirk.rho,  &h->dirk.jx, &h->dirk.jy};
+        for (void** sl : slots) CK(spec(sl));
+        const int s = c.dirk_stages;
+        h->dirk.s = s;
+        double r0 = 0, r1 = 0;
+        for (int i = 0; i < s; ++i) {
+            for (int j = 0; j < s; ++j) h->dirk.a[i * kMaxDirk + j] = c.dirk_a[i * s + j];
+            h->dirk.b[i] = c.dirk_b[i];
+            h->dirk.c[i] = c.dirk_c[i];
+            r0 += c.dirk_b[i] * (1.0 - c.dirk_c[i]);
+            r1 += c.dirk_b[i] * c.dirk_c[i];
+        }
+        h->dirk.r0 = r0;
+        h->dirk.r1 = r1;
+    }
+    return PIC_OK;
+}
+
+// t = 0 state (Algorithm 1 set-up): wrap x^0, deposit the charge, remove its K = 0
+// modes, solve Poisson for phi^0, gather E^0 = -grad phi^0 for P^0 and v^{-1}, and
+// fill every history level with its t = 0 value.
+pic_status setup(pic_handle* h, const pic_particles_in* in) {
+    const pic_config& c = h->cfg;
+    const size_t cs = 2 * h->rsz;
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t r = launch_twiddles<T>(h->twx, c.nx, h->s);
+        return r != cudaSuccess ? r : launch_twiddles<T>(h->twy, c.ny, h->s);
+    }));
+
+    const int64_t n = h->n;
+    const size_t nb64 = (size_t)n * sizeof(double);
+    const double* src[4] = {in->x, in->y, in->vx, in->vy};
+    void* dst[4] = {h->x, h->y, h->v[0][0], h->v[0][1]};
+    for (int i = 0; i < 4 && n > 0; ++i) {
+        if (h->fp32) {
+            CK(cudaMemcpyAsync(h->stage, src[i], nb64, cudaMemcpyDefault, h->s));
+            CK(launch_convert<double, float>(h->stage, (float*)dst[i], n, h->s));
+        } else {
+            CK(cudaMemcpyAsync(dst[i], src[i], nb64, cudaMemcpyDefault, h->s));
+        }
+    }
+
+    void* rho0 = newest(h, 3);
+    void* phi0 = newest(h, 0);
+    CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    CK(by_prec(h, [&](auto t) -> cudaError_t {
+        using T = decltype(t);
+        cudaError_t r = launch_wrap_positions<T>((T*)h->x, (T*)h->y, n, c.lx, c.ly, h->s);
+        if (r != cudaSuccess) return r;
+        r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n, h->J,
+                                     h->err, h->s);
+        if (r != cudaSuccess) return r;
+        if (h->fp32) {
+            r = launch_convert<double, float>((const double*)h->J, (float*)h->tmp, 2 * h->ng, h->s);
+            if (r != cudaSuccess) return r;
+            r = forward_fft(h, h->tmp, h->Z);
+        } else {
+            r = forward_fft(h, h->J, h->Z);
+        }
+        if (r != cudaSuccess) return r;
+        r = launch_mode_init<T>(h->mc, h->Z, rho0, phi0, h->F4, h->s);
+        if (r != cudaSuccess) return r;
+        r = inverse_fft(h, h->F4, h->tmp, 1);  // grid (Ex, Ey) at t = 0
+        if (r != cudaSuccess) return r;
+        return launch_init_particles<T>(h->p, h->geom, h->push, (T*)h->x, (T*)h->y, (T*)h->px,
+                                        (T*)h->py, (const T*)h->v[0][0], (const T*)h->v[0][1],
+                                        (T*)h->v[1][0], (T*)h->v[1][1], n, h->tmp, h->err, h->s);
+    }));
+    h->vcur = 0;
+
+    const size_t bytes = h->ng * cs;
+    if (c.stepper == PIC_STEPPER_BDF) {
+        for (int i = 1; i < h->L; ++i)
+            CK(cudaMemcpyAsync(h->phi_l[i], phi0, bytes, cudaMemcpyDeviceToDevice, h->s));
+        for (int i = 1; i < h->Lr; ++i)
+            CK(cudaMemcpyAsync(h->rho_l[i], rho0, bytes, cudaMemcpyDeviceToDevice, h->s));
+        h->head = 0;
+        h->head_r = 0;
+    } else if (c.stepper == PIC_STEPPER_CDF2) {
+        CK(cudaMemcpyAsync(h->cdf.phi_prev, phi0, bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->cdf.rho_prev, rho0, bytes, cudaMemcpyDeviceToDevice, h->s));
+    }
+    return check_device_error(h);
+}
+
+bool diag_due(const pic_handle* h) {
+    return h->diag_every > 0 && ((h->step + 1) % h->diag_every) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* stream,
+                    pic_handle** out) {
+    if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    pic_status st = validate(cfg, init);
+    if (st != PIC_OK) return st;
+    pic_handle* h = new pic_handle();
+    h->cfg = *cfg;
+    h->s = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    h->nx = cfg->nx;
+    h->ny = cfg->ny;
+    h->ng = (size_t)cfg->nx * cfg->ny;
+    h->p = cfg->spline_order;
+    h->n = init->n;
+    h->fp32 = cfg->precision == PIC_FP32_FIX64;
+    h->rsz = h->fp32 ? 4 : 8;
+    factor_23(cfg->nx, h->fx);
+    factor_23(cfg->ny, h->fy);
+    const double dx = cfg->lx / cfg->nx, dy = cfg->ly / cfg->ny;
+    h->mc.nx = cfg->nx;
+    h->mc.ny = cfg->ny;
+    h->mc.kx_scale = 2.0 * M_PI / cfg->lx;
+    h->mc.ky_scale = 2.0 * M_PI / cfg->ly;
+    h->mc.jscale = cfg->weight * cfg->q / (dx * dy);
+    h->mc.inv_n = 1.0 / (double)h->ng;
+    h->mc.eps0 = cfg->eps0;
+    h->mc.mu0 = 1.0 / (cfg->eps0 * cfg->c * cfg->c);
+    h->mc.c = cfg->c;
+    h->mc.dt = cfg->dt;
+    h->geom = ParticleGeom{cfg->nx, cfg->ny, cfg->lx, cfg->ly, 1.0 / dx, 1.0 / dy, cfg->dt};
+    h->push = PushParams{cfg->q, cfg->m, cfg->c, cfg->dt, cfg->weight, 0};
+    st = alloc_state(h);
+    if (st == PIC_OK) st = setup(h, init);
+    if (st != PIC_OK) {
+        g_init_error = h->errmsg;
+        cudaStreamSynchronize(h->s);
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_deposit(pic_handle* h) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_deposit: the previous step is not finished");
+    CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        return launch_move_deposit<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
+                                      (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1], h->n,
+                                      h->J, h->err, h->s);
+    }));
+    h->phase = 1;
+    return PIC_OK;
+}
+
+pic_status pic_field_solve(pic_handle* h) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (h->phase != 1) return fail(h, PIC_ERR_STATE, "pic_field_solve needs pic_deposit first");
+    h->diag_now = diag_due(h);
+    h->mc.diag = h->diag_now ? 1 : 0;
+    if (h->diag_now) CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
+    if (h->fp32) {
+        CK(launch_convert<double, float>((const double*)h->J, (float*)h->tmp, 2 * h->ng, h->s));
+        CK(forward_fft(h, h->tmp, h->Z));
+    } else {
+        CK(forward_fft(h, h->J, h->Z));
+    }
+    const int st = h->cfg.stepper;
+    if (st == PIC_STEPPER_BDF) {
+        BdfParams bp = h->bdf;
+        const int k = bp.k;
+        for (int d = 1; d <= 2 * k; ++d) {
+            const int slot = ((h->head - (d - 1)) % h->L + h->L) % h->L;
+            bp.phi[d - 1] = h->phi_l[slot];
+            bp.ax[d - 1] = h->ax_l[slot];
+            bp.ay[d - 1] = h->ay_l[slot];
+        }
+        for (int d = 1; d <= k; ++d) bp.rho[d - 1] = h->rho_l[((h->head_r - (d - 1)) % h->Lr + h->Lr) % h->Lr];
+        const int nslot = (h->head + 1) % h->L, nr = (h->head_r + 1) % h->Lr;
+        bp.phi_new = h->phi_l[nslot];
+        bp.ax_new = h->ax_l[nslot];
+        bp.ay_new = h->ay_l[nslot];
+        bp.rho_new = h->rho_l[nr];
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_mode_bdf<T>(h->mc, bp, h->Z, h->F4, h->E, h->diag, h->s);
+        }));
+        h->head = nslot;
+        h->head_r = nr;
+    } else if (st == PIC_STEPPER_CDF2) {
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_mode_cdf2<T>(h->mc, h->cdf, h->Z, h->F4, h->E, h->diag, h->s);
+        }));
+        std::swap(h->cdf.phi, h->cdf.phi_prev);
+        std::swap(h->cdf.rho, h->cdf.rho_prev);
+        std::swap(h->cdf.ax, h->cdf.ax_prev);
+        std::swap(h->cdf.ay, h->cdf.ay_prev);
+        std::swap(h->cdf.jx, h->cdf.jx_prev);
+        std::swap(h->cdf.jy, h->cdf.jy_prev);
+    } else {
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_mode_dirk<T>(h->mc, h->dirk, h->Z, h->F4, h->E, h->diag, h->s);
+        }));
+    }
+    CK(inverse_fft(h, h->F4, h->G, 4));
+    h->phase = 2;
+    return PIC_OK;
+}
+
+pic_status pic_gather_push(pic_handle* h) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (h->phase != 2) return fail(h, PIC_ERR_STATE, "pic_gather_push needs pic_field_solve first");
+    PushParams pp = h->push;
+    pp.diag = h->diag_now ? 1 : 0;
+    const int vo = 1 - h->vcur;
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        return launch_gather_push<T>(h->p, h->geom, pp, (const T*)h->x, (const T*)h->y,
+                                     (T*)h->px, (T*)h->py, (const T*)h->v[h->vcur][0],
+                                     (const T*)h->v[h->vcur][1], (T*)h->v[vo][0], (T*)h->v[vo][1],
+                                     h->n, h->G, h->diag, h->err, h->s);
+    }));
+    h->vcur = vo;
+    h->step += 1;
+    h->stepped = true;
+    h->e_valid = h->diag_now;
+    if (h->diag_now) {
+        h->diag_valid = true;
+        h->diag_step = h->step;
+    }
+    h->phase = 0;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_handle* h, int32_t nsteps) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (nsteps < 0) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    for (int32_t i = 0; i < nsteps; ++i) {
+        pic_status st = pic_deposit(h);
+        if (st == PIC_OK) st = pic_field_solve(h);
+        if (st == PIC_OK) st = pic_gather_push(h);
+        if (st != PIC_OK) return st;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_set_diagnostics(pic_handle* h, int32_t every) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (every < 0) return fail(h, PIC_ERR_INVALID_ARG, "every must be >= 0");
+    h->diag_every = every;
+    return PIC_OK;
+}
+
+pic_status pic_residuals(pic_handle* h, pic_diagnostics* out) {
+    if (!h || !out) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    double acc[D_NSLOTS];
+    CK(cudaMemcpyAsync(acc, h->diag, sizeof acc, cudaMemcpyDeviceToHost, h->s));
+    pic_status st = check_device_error(h);
+    if (st != PIC_OK) return st;
+    if (!h->diag_valid) return fail(h, PIC_ERR_STATE, "no step has been diagnosed yet");
+    const double N = (double)h->ng;
+    const double area = (h->cfg.lx / h->nx) * (h->cfg.ly / h->ny);
+    // Parseval: grid mean of |f|^2 = (1/N^2) sum_k |f_hat|^2
+    auto rms = [&](double s) { return std::sqrt(s) / N; };
+    out->gauge_rms = rms(acc[D_GAUGE]);
+    out->gauss_rms = rms(acc[D_GAUSS]);
+    out->continuity_rms = rms(acc[D_CONT]);
+    out->gauge_dt_rms = rms(acc[D_GAUGE_DT]);
+    out->rho_rms = rms(acc[D_RHO]);
+    out->div_a_rms = rms(acc[D_DIVA]);
+    out->w_e = 0.5 * h->cfg.eps0 * area * acc[D_WE] / N;
+    out->w_b = 0.5 / h->mc.mu0 * area * acc[D_WB] / N;
+    out->kinetic = acc[D_KIN];
+    out->step = h->diag_step;
+    return PIC_OK;
+}
+
+pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
+    if (!h || !dst) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    if (which < PIC_FIELD_JX || which > PIC_FIELD_DAYDY)
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown field %d", which);
+    if (!h->stepped && which != PIC_FIELD_RHO && which != PIC_FIELD_PHI)
+        return fail(h, PIC_ERR_STATE, "field %d needs a completed step", which);
+    if ((which == PIC_FIELD_EX || which == PIC_FIELD_EY) && !h->e_valid)
+        return fail(h, PIC_ERR_STATE, "E needs diagnostics on the last step");
+    const int64_t n = (int64_t)h->ng;
+    cudaError_t e = by_prec(h, [&](auto t) -> cudaError_t {
+        using T = decltype(t);
+        const size_t cs = sizeof(T) * 2;
+        switch (which) {
+            case PIC_FIELD_JX:
+            case PIC_FIELD_JY:
+                return launch_extract<double>(h->J, 1, which == PIC_FIELD_JY, h->mc.jscale, h->tmpd, n, h->s);
+            case PIC_FIELD_DPHIDX: case PIC_FIELD_DPHIDY: case PIC_FIELD_GAX: case PIC_FIELD_GAY:
+            case PIC_FIELD_DAXDX: case PIC_FIELD_DAXDY: case PIC_FIELD_DAYDX: case PIC_FIELD_DAYDY: {
+                const int f = which - PIC_FIELD_DPHIDX;
+                return launch_extract<T>((const char*)h->G + (f / 2) * cs, 4, f & 1, 1.0, h->tmpd, n, h->s);
+            }
+            default: break;
+        }
+        cudaError_t r;
+        int comp = 0;
+        if (which == PIC_FIELD_EX || which == PIC_FIELD_EY) {
+            r = cudaMemcpyAsync(h->tmp, h->E, h->ng * cs, cudaMemcpyDeviceToDevice, h->s);
+            comp = which == PIC_FIELD_EY;
+        } else if (which == PIC_FIELD_RHO) {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 3), nullptr, 0, h->tmp, h->s);
+        } else if (which == PIC_FIELD_PHI) {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 0), nullptr, 0, h->tmp, h->s);
+        } else if (which == PIC_FIELD_BZ) {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 1), newest(h, 2), 1, h->tmp, h->s);
+        } else {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 1), newest(h, 2), 0, h->tmp, h->s);
+            comp = which == PIC_FIELD_AY;
+        }
+        if (r != cudaSuccess) return r;
+        r = inverse_fft(h, h->tmp, h->tmp, 1);
+        if (r != cudaSuccess) return r;
+        return launch_extract<T>(h->tmp, 1, comp, 1.0, h->tmpd, n, h->s);
+    });
+    CK(e);
+    CK(cudaMemcpyAsync(dst, h->tmpd, h->ng * sizeof(double), cudaMemcpyDefault, h->s));
+    return check_device_error(h);
+}
+
+pic_status pic_read_particles(pic_handle* h, double* x, double* y, double* px, double* py,
+                              double* vx, double* vy, double* vx_old, double* vy_old) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_read_particles inside a step");
+    const void* src[8] = {h->x, h->y, h->px, h->py, h->v[h->vcur][0], h->v[h->vcur][1],
+                          h->v[1 - h->vcur][0], h->v[1 - h->vcur][1]};
+    double* dst[8] = {x, y, px, py, vx, vy, vx_old, vy_old};
+    const size_t nb = (size_t)h->n * sizeof(double);
+    for (int i = 0; i < 8; ++i) {
+        if (!dst[i] || h->n == 0) continue;
+        if (h->fp32) {
+            CK(launch_convert<float, double>((const float*)src[i], h->stage, h->n, h->s));
+            CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
+            CK(cudaStreamSynchronize(h->s));  // the staging buffer is reused
+        } else {
+            CK(cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyDefault, h->s));
+        }
+    }
+    return check_device_error(h);
+}
+
+pic_status pic_sync(pic_handle* h) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->s));
+    return check_device_error(h);
+}
+
+int64_t pic_step_count(const pic_handle* h) { return h ? h->step : -1; }
+
+int32_t pic_kernels_per_step(const pic_handle* h) {
+    if (!h) return 0;
+    // move_deposit, 2 forward FFT passes, per-mode update, 2 inverse FFT passes,
+    // gather_push; the FP32 form adds one conversion kernel.
+    return 7 + (h->fp32 ? 1 : 0);
+}
+
+const char* pic_last_error(const pic_handle* h) {
+    return h ? h->errmsg.c_str() : g_init_error.c_str();
+}
+
+void pic_destroy(pic_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->s);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,230 @@
+"""Python binding of the C ABI in include/pic.h (argument marshalling only).
+
+Every step of the PIC method runs inside libgpic.so's CUDA kernels; this module only
+loads the library, mirrors its structs with ctypes and turns status codes into
+exceptions.  It never computes anything of the method itself, and it refuses to run
+without the compiled library (there is no CPU fallback).
+
+Arrays may be numpy (host) or torch tensors (host or CUDA): the library's copies use
+unified addressing, so a device pointer and a host pointer are both accepted.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpic.so")
+
+# pic_status
+PIC_OK = 0
+STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_INVALID_ARG", 2: "PIC_ERR_UNSUPPORTED", 3: "PIC_ERR_CUDA",
+                4: "PIC_ERR_NONFINITE", 5: "PIC_ERR_OVERFLOW", 6: "PIC_ERR_TIMEOUT",
+                7: "PIC_ERR_STATE"}
+# pic_stepper
+STEPPER_BDF, STEPPER_CDF2, STEPPER_DIRK = 0, 1, 2
+STEPPERS = {"bdf": STEPPER_BDF, "cdf2": STEPPER_CDF2, "dirk": STEPPER_DIRK}
+# pic_precision
+FP64, FP32_FIX64 = 0, 1
+# pic_field
+FIELDS = {"jx": 0, "jy": 1, "rho": 2, "phi": 3, "ax": 4, "ay": 5, "bz": 6, "ex": 7, "ey": 8,
+          "dphidx": 9, "dphidy": 10, "gax": 11, "gay": 12, "daxdx": 13, "daxdy": 14,
+          "daydx": 15, "daydy": 16}
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("spline_order", ctypes.c_int32), ("stepper", ctypes.c_int32),
+        ("bdf_order", ctypes.c_int32), ("dirk_stages", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("sort_interval", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("c", ctypes.c_double), ("eps0", ctypes.c_double), ("dt", ctypes.c_double),
+        ("q", ctypes.c_double), ("m", ctypes.c_double), ("weight", ctypes.c_double),
+        ("dirk_a", ctypes.c_double * 16), ("dirk_b", ctypes.c_double * 4),
+        ("dirk_c", ctypes.c_double * 4),
+        ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+class PicParticlesIn(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("vx", ctypes.c_void_p),
+                ("vy", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class PicDiagnostics(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_double) for name in
+                ("gauge_rms", "gauss_rms", "continuity_rms", "gauge_dt_rms", "rho_rms",
+                 "div_a_rms", "w_e", "w_b", "kinetic")] + [("step", ctypes.c_int64)]
+
+
+EXPORTS = ("pic_init", "pic_deposit", "pic_field_solve", "pic_gather_push", "pic_step",
+           "pic_set_diagnostics", "pic_residuals", "pic_get_field", "pic_read_particles",
+           "pic_sync", "pic_step_count", "pic_kernels_per_step", "pic_last_error", "pic_destroy")
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libgpic.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgpic.so not found at {path}: build it with "
+                           "`python -m paper_2410_18414_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "pic_init": ([ctypes.POINTER(PicConfig), ctypes.POINTER(PicParticlesIn), vp,
+                      ctypes.POINTER(vp)], i32),
+        "pic_deposit": ([vp], i32),
+        "pic_field_solve": ([vp], i32),
+        "pic_gather_push": ([vp], i32),
+        "pic_step": ([vp, i32], i32),
+        "pic_set_diagnostics": ([vp, i32], i32),
+        "pic_residuals": ([vp, ctypes.POINTER(PicDiagnostics)], i32),
+        "pic_get_field": ([vp, i32, vp], i32),
+        "pic_read_particles": ([vp] + [vp] * 8, i32),
+        "pic_sync": ([vp], i32),
+        "pic_step_count": ([vp], i64),
+        "pic_kernels_per_step": ([vp], i32),
+        "pic_last_error": ([vp], ctypes.c_char_p),
+        "pic_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    del dp
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (contiguous float64)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, c=1.0, eps0=1.0,
+                q=-1.0, m=1.0, weight=1.0, precision=FP64, sort_interval=0):
+    cfg = PicConfig()
+    cfg.nx, cfg.ny, cfg.lx, cfg.ly, cfg.dt = nx, ny, lx, ly, dt
+    cfg.spline_order = p
+    cfg.stepper = STEPPERS[stepper] if isinstance(stepper, str) else int(stepper)
+    cfg.bdf_order = bdf_order
+    cfg.c, cfg.eps0, cfg.q, cfg.m, cfg.weight = c, eps0, q, m, weight
+    cfg.precision = precision
+    cfg.sort_interval = sort_interval
+    if dirk is not None:
+        s = len(dirk["b"])
+        cfg.dirk_stages = s
+        for i in range(s):
+            for j in range(s):
+                cfg.dirk_a[i * s + j] = dirk["A"][i][j]
+            cfg.dirk_b[i] = dirk["b"][i]
+            cfg.dirk_c[i] = dirk["c"][i]
+    return cfg
+
+
+class Simulation:
+    """One simulation handle of libgpic (owns its device memory until close())."""
+
+    def __init__(self, cfg, x, y, vx, vy, stream=None):
+        self.lib = load_library()
+        self.cfg = cfg
+        self.n = len(x)
+        self._keep = (x, y, vx, vy)
+        init = PicParticlesIn(_ptr(x), _ptr(y), _ptr(vx), _ptr(vy), self.n)
+        handle = ctypes.c_void_p()
+        st = self.lib.pic_init(ctypes.byref(cfg), ctypes.byref(init),
+                               ctypes.c_void_p(stream or 0), ctypes.byref(handle))
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(None).decode())
+        self.h = handle
+        self._keep = None
+
+    def _check(self, st):
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(self.h).decode())
+
+    def deposit(self):
+        self._check(self.lib.pic_deposit(self.h))
+
+    def field_solve(self):
+        self._check(self.lib.pic_field_solve(self.h))
+
+    def gather_push(self):
+        self._check(self.lib.pic_gather_push(self.h))
+
+    def step(self, nsteps=1):
+        self._check(self.lib.pic_step(self.h, nsteps))
+
+    def set_diagnostics(self, every):
+        self._check(self.lib.pic_set_diagnostics(self.h, every))
+
+    def residuals(self):
+        d = PicDiagnostics()
+        self._check(self.lib.pic_residuals(self.h, ctypes.byref(d)))
+        return {name: getattr(d, name) for name, _ in PicDiagnostics._fields_}
+
+    def field(self, name, out=None):
+        if out is None:
+            out = np.empty((self.cfg.nx, self.cfg.ny), dtype=np.float64)
+        self._check(self.lib.pic_get_field(self.h, FIELDS[name], ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def particles(self, out=None):
+        """Dict of the eight particle arrays (x, y, px, py, vx, vy, vx_old, vy_old), FP64."""
+        names = ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old")
+        if out is None:
+            out = {k: np.empty(self.n, dtype=np.float64) for k in names}
+        ptrs = [ctypes.c_void_p(_ptr(out[k])) if out.get(k) is not None else None for k in names]
+        self._check(self.lib.pic_read_particles(self.h, *ptrs))
+        return out
+
+    def sync(self):
+        self._check(self.lib.pic_sync(self.h))
+
+    @property
+    def step_count(self):
+        return int(self.lib.pic_step_count(self.h))
+
+    @property
+    def kernels_per_step(self):
+        return int(self.lib.pic_kernels_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
