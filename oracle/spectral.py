@@ -23,9 +23,14 @@ import numpy as np
 
 
 def dft_matrix(n, sign=-1):
-    """Dense DFT matrix F[m, j] = exp(sign * 2 pi i m j / n)."""
+    """Dense DFT matrix F[m, j] = exp(sign * 2 pi i m j / n).
+
+    The kernel depends on m j only modulo n, so the exponent is taken at the reduced
+    argument 2 pi ((m j) mod n) / n: evaluating it at m j up to (n-1)^2 would lose
+    about log10(n^2) digits of the phase.
+    """
     idx = np.arange(n)
-    return np.exp(sign * 2j * np.pi * np.outer(idx, idx) / n)
+    return np.exp(sign * 2j * np.pi * (np.outer(idx, idx) % n) / n)
 
 
 def dft2(f):

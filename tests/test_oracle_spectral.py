@@ -12,6 +12,17 @@ def test_dft2_matches_library_fft():
         np.testing.assert_allclose(spectral.idft2(f), np.fft.ifft2(f), atol=1e-13)
 
 
+def test_dft_accuracy_on_offset_signal():
+    # A large mean on top of small fluctuations (as a neutral plasma's charge): the
+    # fluctuation modes must keep full FP64 accuracy relative to the input norm.
+    rng = np.random.default_rng(5)
+    for n in (128, 512):
+        f = 64.0 + rng.standard_normal((n, 4))
+        ref = np.fft.fft2(f)
+        err = np.abs(spectral.dft2(f) - ref)[1:].max()
+        assert err < 2e-15 * np.linalg.norm(f) * np.sqrt(n), (n, err)
+
+
 def test_delta_and_cosine():
     f = np.zeros((8, 4))
     f[0, 0] = 1.0
