@@ -36,8 +36,8 @@ STEPPER_NAMES = {"bdf1": ("bdf", 1), "bdf2": ("bdf", 2), "cdf2": ("cdf2", 1), "d
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default="bdf2")
     ap.add_argument("--precision", choices=["fp64"], default="fp64")
