@@ -183,6 +183,33 @@ const char *pic_last_error(const pic_handle *h);
 /* Release every device allocation of the handle.  NULL is allowed. */
 void pic_destroy(pic_handle *h);
 
+/* Allocation-free move + deposit pass (the first two lines of one step, as pic_deposit
+ * does them) for callers that cannot let a library allocate device memory: hosts whose
+ * GPU memory is owned by their own pool allocator (a hidden cudaMalloc would fail or
+ * bypass the pool), and latency-bound loops that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree imply.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *
+ *   cfg     only nx, ny (nx*ny <= 262144, i.e. up to a 512 x 512 grid; each >= 8), lx, ly,
+ *           dt, c, spline_order, q, weight and precision (must be PIC_FP64) are used.
+ *   x, y    device arrays of n FP64 positions in [0, L), moved in place by v dt and wrapped.
+ *   vx, vy  device arrays of n FP64 velocities v^n.
+ *   jx, jy  device outputs, nx*ny FP64 each (layout as every grid here): J^{n+1} as a
+ *           current density, weight*q*sum_p v_p W W / (dx dy).
+ *
+ * The only scratch is a fixed 4 MiB array inside the library, resident on every device
+ * that loads it until the process exits.  The first call on a device looks up that
+ * array's device address (a one-time set-up, so make that first call before any stream
+ * capture).  Every call shares the array and clears what it uses; calls that overlap on
+ * the GPU (other threads or streams) race on it.  The call enqueues on cuda_stream and
+ * returns once the pass has finished.  Returns PIC_ERR_INVALID_ARG for a grid above the
+ * limit or a bad argument, PIC_ERR_UNSUPPORTED for FP32, PIC_ERR_NONFINITE if a position
+ * was outside the domain or not finite (that particle is skipped), PIC_ERR_CUDA on a
+ * runtime failure.  No call allocates or frees device memory. */
+pic_status pic_move_deposit_noalloc(const pic_config *cfg, int64_t n, double *x, double *y,
+                                    const double *vx, const double *vy, double *jx, double *jy,
+                                    void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
