@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default="bdf2")
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="form timed for the headline value; the other form is timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-steppers", action="store_true")
     return ap.parse_args()
@@ -61,12 +62,13 @@ def dirk_tableau(name):
             "b": [1 / 3, 1 / 3, 1 / 3], "c": [1 / 6, 0.5, 5 / 6]}
 
 
-def make_config(wl, stepper_name):
+def make_config(wl, stepper_name, precision="fp64"):
     from paper_2410_18414_gb300 import pic
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
+    prec = pic.FP32_FIX64 if precision == "fp32" else pic.FP64
     return pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper=stepper,
-                           bdf_order=k, dirk=dirk, weight=wl.weight)
+                           bdf_order=k, dirk=dirk, weight=wl.weight, precision=prec)
 
 
 def workload_desc(wl, stepper_name):
@@ -96,6 +98,11 @@ def bytes_gather_push(rsz):
 
 def bytes_move_deposit(rsz):
     return 6 * rsz      # read x, y, v^n (4); write x, y (2)
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
+# captures (profiles/), keyed by (kernel, form); None when the kernel changed since.
+TRAFFIC = {}
 
 
 def peaks():
@@ -290,7 +297,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     wl = make_workload(2 + rank)
-    cfg = make_config(wl, a.stepper)
+    cfg = make_config(wl, a.stepper, a.precision)
     sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
 
     def barrier():
@@ -316,7 +323,8 @@ def main():
 
     # roofline of the dominant kernel (per-launch averages from the events above)
     pk = peaks()
-    rsz = 8
+    fp32 = a.precision == "fp32"
+    rsz = 4 if fp32 else 8
     p = wl.p
     dep_ms = statistics.mean(t["deposit_ms"])
     psh_ms = statistics.mean(t["push_ms"])
@@ -330,16 +338,35 @@ def main():
     for k in kern.values():
         k["gflops"] = k["flops"] / (k["ms"] * 1e-3) / 1e9
         k["gbs"] = k["bytes"] / (k["ms"] * 1e-3) / 1e9
-        k["frac_fp64_alu"] = k["gflops"] / pk["fp64_gflops"]
         k["frac_hbm"] = k["gbs"] / pk["hbm_gbs"]
+        if not fp32:
+            k["frac_fp64_alu"] = k["gflops"] / pk["fp64_gflops"]
     dom_name = max(kern, key=lambda k: kern[k]["ms"])
     dom = kern[dom_name]
-    roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
-                "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
-                "frac": dom["gflops"] / pk["fp64_gflops"], "traffic": None,
-                "peak_source": pk["fp64_src"],
-                "hbm": {"achieved_gbs": dom["gbs"], "peak_gbs": pk["hbm_gbs"],
-                        "frac": dom["gbs"] / pk["hbm_gbs"], "peak_source": pk["hbm_src"]}}
+    if fp32:
+        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["gbs"],
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dom["gbs"] / pk["hbm_gbs"],
+                    "traffic": TRAFFIC.get((dom_name, a.precision)), "peak_source": pk["hbm_src"]}
+    else:
+        roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
+                    "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
+                    "frac": dom["gflops"] / pk["fp64_gflops"],
+                    "traffic": TRAFFIC.get((dom_name, a.precision)),
+                    "peak_source": pk["fp64_src"],
+                    "hbm": {"achieved_gbs": dom["gbs"], "peak_gbs": pk["hbm_gbs"],
+                            "frac": dom["gbs"] / pk["hbm_gbs"], "peak_source": pk["hbm_src"]}}
+
+    # the other precision form on the same workload (the metric's comparison)
+    other = "fp64" if fp32 else "fp32"
+    so = pic.Simulation(make_config(wl, a.stepper, other), wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+    to = time_steps(so, max(20, a.steps // 4), 5, stream, flush)
+    so.close()
+    other_ms = statistics.mean(to["step_ms"])
+    other_form = {"form": other, "ms_per_step": other_ms,
+                  "value": wl.n * world / (other_ms * 1e-3),
+                  "phase_ms": {"deposit": statistics.mean(to["deposit_ms"]),
+                               "field_solve": statistics.mean(to["field_ms"]),
+                               "gather_push": statistics.mean(to["push_ms"])}}
 
     # other steppers of the same workload (shorter runs)
     by_stepper = {a.stepper: total_ms / a.steps}
@@ -347,7 +374,8 @@ def main():
         for name in ("bdf2", "cdf2", "dirk2"):
             if name == a.stepper:
                 continue
-            s2 = pic.Simulation(make_config(wl, name), wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+            s2 = pic.Simulation(make_config(wl, name, a.precision), wl.x, wl.y, wl.vx, wl.vy,
+                                stream=sp)
             t2 = time_steps(s2, max(10, a.steps // 5), 3, stream, flush)
             by_stepper[name] = statistics.mean(t2["step_ms"])
             s2.close()
@@ -386,8 +414,10 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_desc(wl, a.stepper), form="fp64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+            "data": "synthetic",
+            "config": dict(workload_desc(wl, a.stepper),
+                           form="fp32_fix64" if fp32 else "fp64",
                            l2="flushed between timed steps (256 MiB device write)",
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline,
@@ -395,6 +425,8 @@ def main():
                             for kk, vv in v.items()} for k, v in kern.items()},
             "phase_ms": {"deposit": dep_ms, "field_solve": fld_ms, "gather_push": psh_ms},
             "by_stepper_ms_per_step": by_stepper,
+            "other_form": other_form,
+            "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": sim.kernels_per_step * a.steps,

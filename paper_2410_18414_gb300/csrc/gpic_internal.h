@@ -116,6 +116,21 @@ cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const 
 template <typename T>
 cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
                                   double2* j, unsigned int* err, cudaStream_t s);
+// Fixed-point current (int64 per component, contribution = round(value * scale)).
+template <typename T>
+cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
+                                    const T* vy, int64_t n, longlong2* j, float scale,
+                                    unsigned int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, const T* y,
+                                      int64_t n, longlong2* j, float scale, unsigned int* err,
+                                      cudaStream_t s);
+// out[k] = (J[k].x, J[k].y) * unscale in complex storage type T.
+template <typename T>
+cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,
+                               cudaStream_t s);
+cudaError_t launch_extract_fix(const longlong2* j, int comp, double scale, double* dst, int64_t n,
+                               cudaStream_t s);
 // dst[k] = component `comp` of the complex array src (element stride `stride` complex
 // values) times `scale`, as FP64.
 template <typename T>

@@ -12,7 +12,8 @@
 //                           th = c^2 dt^2 / 2
 //   DIRK-s  (section 3.3):  rho^{n+1} = rho^n - h sum_i b_i i k.J^(i); stage pairs solved
 //                           with d_i = 1 + (h a_ii c)^2 K
-// All coefficients and the recurrences run in FP64 whatever the storage type.
+// All coefficients and the recurrences run in FP64, and the time histories are stored in
+// FP64 in both precision forms; only the transform inputs/outputs use the storage type C.
 // The packed current spectrum Z = FFT(Jx + i Jy) is split with the Hermitian pair
 // (k, -k):  Jx = (Z(k) + conj Z(-k))/2,  Jy = (Z(k) - conj Z(-k))/(2i).
 // Outputs are four packed spectra whose inverse FFTs give the real field pairs
@@ -115,16 +116,16 @@ k_mode_bdf(ModeCommon mc, BdfParams bp, const C* __restrict__ z, C* __restrict__
         ModeIn m = mode_in(mc, z, idx);
         const int k = bp.k;
         zd rho_new = -bp.bdt * m.divj;
-        for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * zload((const C*)bp.rho[d - 1] + idx);
+        for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * zload((const double2*)bp.rho[d - 1] + idx);
         rho_new = (1.0 / bp.a[0]) * rho_new;
         const double inv = 1.0 / (bp.C[0] + bp.g * m.K);
         zd sphi = (bp.g / mc.eps0) * rho_new;
         zd sax = (bp.g * mc.mu0) * m.jx;
         zd say = (bp.g * mc.mu0) * m.jy;
         for (int d = 1; d <= 2 * k; ++d) {
-            sphi = sphi - bp.C[d] * zload((const C*)bp.phi[d - 1] + idx);
-            sax = sax - bp.C[d] * zload((const C*)bp.ax[d - 1] + idx);
-            say = say - bp.C[d] * zload((const C*)bp.ay[d - 1] + idx);
+            sphi = sphi - bp.C[d] * zload((const double2*)bp.phi[d - 1] + idx);
+            sax = sax - bp.C[d] * zload((const double2*)bp.ax[d - 1] + idx);
+            say = say - bp.C[d] * zload((const double2*)bp.ay[d - 1] + idx);
         }
         zd phi_new = inv * sphi, ax_new = inv * sax, ay_new = inv * say;
         if (mc.diag) {
@@ -133,10 +134,10 @@ k_mode_bdf(ModeCommon mc, BdfParams bp, const C* __restrict__ z, C* __restrict__
             zd dphi = bp.a[0] * phi_new, dax = bp.a[0] * ax_new, day = bp.a[0] * ay_new;
             zd drho = bp.a[0] * rho_new;
             for (int d = 1; d <= k; ++d) {
-                dphi = dphi + bp.a[d] * zload((const C*)bp.phi[d - 1] + idx);
-                dax = dax + bp.a[d] * zload((const C*)bp.ax[d - 1] + idx);
-                day = day + bp.a[d] * zload((const C*)bp.ay[d - 1] + idx);
-                drho = drho + bp.a[d] * zload((const C*)bp.rho[d - 1] + idx);
+                dphi = dphi + bp.a[d] * zload((const double2*)bp.phi[d - 1] + idx);
+                dax = dax + bp.a[d] * zload((const double2*)bp.ax[d - 1] + idx);
+                day = day + bp.a[d] * zload((const double2*)bp.ay[d - 1] + idx);
+                drho = drho + bp.a[d] * zload((const double2*)bp.rho[d - 1] + idx);
             }
             const double ibdt = 1.0 / bp.bdt;
             zd diva = div2(m.kx, m.ky, ax_new, ay_new);
@@ -153,10 +154,10 @@ k_mode_bdf(ModeCommon mc, BdfParams bp, const C* __restrict__ z, C* __restrict__
             diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
             zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
         }
-        zstore((C*)bp.rho_new + idx, rho_new);
-        zstore((C*)bp.phi_new + idx, phi_new);
-        zstore((C*)bp.ax_new + idx, ax_new);
-        zstore((C*)bp.ay_new + idx, ay_new);
+        zstore((double2*)bp.rho_new + idx, rho_new);
+        zstore((double2*)bp.phi_new + idx, phi_new);
+        zstore((double2*)bp.ax_new + idx, ax_new);
+        zstore((double2*)bp.ay_new + idx, ay_new);
         store_outputs(mc, f4, idx, m.kx, m.ky, phi_new, ax_new, ay_new);
     }
     if (mc.diag) reduce_diag(acc, diag);
@@ -176,11 +177,11 @@ k_mode_cdf2(ModeCommon mc, CdfParams cp, const C* __restrict__ z, C* __restrict_
         const double dt = mc.dt;
         const double th = 0.5 * mc.c * mc.c * dt * dt;
         const double inv = 1.0 / (1.0 + th * m.K);
-        zd phi = zload((const C*)cp.phi + idx), phi_prev = zload((const C*)cp.phi_prev + idx);
-        zd rho = zload((const C*)cp.rho + idx), rho_prev = zload((const C*)cp.rho_prev + idx);
-        zd ax = zload((const C*)cp.ax + idx), ax_prev = zload((const C*)cp.ax_prev + idx);
-        zd ay = zload((const C*)cp.ay + idx), ay_prev = zload((const C*)cp.ay_prev + idx);
-        zd jx_prev = zload((const C*)cp.jx_prev + idx), jy_prev = zload((const C*)cp.jy_prev + idx);
+        zd phi = zload((const double2*)cp.phi + idx), phi_prev = zload((const double2*)cp.phi_prev + idx);
+        zd rho = zload((const double2*)cp.rho + idx), rho_prev = zload((const double2*)cp.rho_prev + idx);
+        zd ax = zload((const double2*)cp.ax + idx), ax_prev = zload((const double2*)cp.ax_prev + idx);
+        zd ay = zload((const double2*)cp.ay + idx), ay_prev = zload((const double2*)cp.ay_prev + idx);
+        zd jx_prev = zload((const double2*)cp.jx_prev + idx), jy_prev = zload((const double2*)cp.jy_prev + idx);
         zd rho_new = rho - dt * m.divj;                                    // rho^{n+3/2}
         zd phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
         zd ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
@@ -202,12 +203,12 @@ k_mode_cdf2(ModeCommon mc, CdfParams cp, const C* __restrict__ z, C* __restrict_
             diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
             zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
         }
-        zstore((C*)cp.phi_prev + idx, phi_new);
-        zstore((C*)cp.rho_prev + idx, rho_new);
-        zstore((C*)cp.ax_prev + idx, ax_new);
-        zstore((C*)cp.ay_prev + idx, ay_new);
-        zstore((C*)cp.jx_prev + idx, m.jx);
-        zstore((C*)cp.jy_prev + idx, m.jy);
+        zstore((double2*)cp.phi_prev + idx, phi_new);
+        zstore((double2*)cp.rho_prev + idx, rho_new);
+        zstore((double2*)cp.ax_prev + idx, ax_new);
+        zstore((double2*)cp.ay_prev + idx, ay_new);
+        zstore((double2*)cp.jx_prev + idx, m.jx);
+        zstore((double2*)cp.jy_prev + idx, m.jy);
         store_outputs(mc, f4, idx, m.kx, m.ky, 0.5 * (phi_new + phi), ax_new, ay_new);
     }
     if (mc.diag) reduce_diag(acc, diag);
@@ -251,11 +252,11 @@ k_mode_dirk(ModeCommon mc, DirkParams dp, const C* __restrict__ z, C* __restrict
     if (idx < nmodes) {
         ModeIn m = mode_in(mc, z, idx);
         const double h = mc.dt;
-        zd phi = zload((const C*)dp.phi + idx), vphi = zload((const C*)dp.vphi + idx);
-        zd ax = zload((const C*)dp.ax + idx), vax = zload((const C*)dp.vax + idx);
-        zd ay = zload((const C*)dp.ay + idx), vay = zload((const C*)dp.vay + idx);
-        zd rho = zload((const C*)dp.rho + idx);
-        zd jxn = zload((const C*)dp.jx + idx), jyn = zload((const C*)dp.jy + idx);
+        zd phi = zload((const double2*)dp.phi + idx), vphi = zload((const double2*)dp.vphi + idx);
+        zd ax = zload((const double2*)dp.ax + idx), vax = zload((const double2*)dp.vax + idx);
+        zd ay = zload((const double2*)dp.ay + idx), vay = zload((const double2*)dp.vay + idx);
+        zd rho = zload((const double2*)dp.rho + idx);
+        zd jxn = zload((const double2*)dp.jx + idx), jyn = zload((const double2*)dp.jy + idx);
         zd divjn = div2(m.kx, m.ky, jxn, jyn);
         zd rho_new = rho;
         for (int i = 0; i < dp.s; ++i)
@@ -285,15 +286,15 @@ k_mode_dirk(ModeCommon mc, DirkParams dp, const C* __restrict__ z, C* __restrict
             diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
             zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
         }
-        zstore((C*)dp.phi + idx, phi_new);
-        zstore((C*)dp.vphi + idx, vphi_new);
-        zstore((C*)dp.ax + idx, ax_new);
-        zstore((C*)dp.vax + idx, vax_new);
-        zstore((C*)dp.ay + idx, ay_new);
-        zstore((C*)dp.vay + idx, vay_new);
-        zstore((C*)dp.rho + idx, rho_new);
-        zstore((C*)dp.jx + idx, m.jx);
-        zstore((C*)dp.jy + idx, m.jy);
+        zstore((double2*)dp.phi + idx, phi_new);
+        zstore((double2*)dp.vphi + idx, vphi_new);
+        zstore((double2*)dp.ax + idx, ax_new);
+        zstore((double2*)dp.vax + idx, vax_new);
+        zstore((double2*)dp.ay + idx, ay_new);
+        zstore((double2*)dp.vay + idx, vay_new);
+        zstore((double2*)dp.rho + idx, rho_new);
+        zstore((double2*)dp.jx + idx, m.jx);
+        zstore((double2*)dp.jy + idx, m.jy);
         store_outputs(mc, f4, idx, m.kx, m.ky, phi_new, ax_new, ay_new);
     }
     if (mc.diag) reduce_diag(acc, diag);
@@ -303,8 +304,8 @@ k_mode_dirk(ModeCommon mc, DirkParams dp, const C* __restrict__ z, C* __restrict
 // packed E^0 = -grad phi^0 for the Taylor start of v^{-1}.
 template <typename C>
 __global__ void __launch_bounds__(kModeThreads)
-k_mode_init(ModeCommon mc, const C* __restrict__ zq, C* __restrict__ rho_out,
-            C* __restrict__ phi_out, C* __restrict__ epk) {
+k_mode_init(ModeCommon mc, const C* __restrict__ zq, double2* __restrict__ rho_out,
+            double2* __restrict__ phi_out, C* __restrict__ epk) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= mc.nx * mc.ny) return;
     ModeIn m = mode_in(mc, zq, idx);
@@ -319,7 +320,7 @@ k_mode_init(ModeCommon mc, const C* __restrict__ zq, C* __restrict__ rho_out,
 // out = inv_n * (A + i B) with (op 0) A = a, B = b, or (op 1) A = i kx b - i ky a, B = 0.
 template <typename C>
 __global__ void __launch_bounds__(kModeThreads)
-k_mode_pack2(ModeCommon mc, const C* __restrict__ a, const C* __restrict__ b, int op,
+k_mode_pack2(ModeCommon mc, const double2* __restrict__ a, const double2* __restrict__ b, int op,
              C* __restrict__ out) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= mc.nx * mc.ny) return;
@@ -367,14 +368,14 @@ template <typename T>
 cudaError_t launch_mode_init(const ModeCommon& mc, const void* zq, void* rho, void* phi, void* e,
                              cudaStream_t s) {
     using C = cplx_t<T>;
-    k_mode_init<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const C*)zq, (C*)rho, (C*)phi, (C*)e);
+    k_mode_init<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const C*)zq, (double2*)rho, (double2*)phi, (C*)e);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,
                               void* out, cudaStream_t s) {
     using C = cplx_t<T>;
-    k_mode_pack2<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const C*)a, (const C*)b, op, (C*)out);
+    k_mode_pack2<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const double2*)a, (const double2*)b, op, (C*)out);
     return cudaGetLastError();
 }
 

@@ -35,11 +35,43 @@ __device__ __forceinline__ bool in_domain(T xi, int n) {
     return xi >= (T)0 && xi <= (T)n;
 }
 
-template <typename T, int P>
+// Current accumulation policies.  AccF64: FP64 atomics (plain path).  AccFix: each
+// contribution is rounded to an integer multiple of 1/scale and summed with int64
+// atomics, so the grid total does not depend on the order of the additions.
+struct AccF64 {
+    double2* J;
+    template <typename T>
+    __device__ __forceinline__ void add(size_t node, T a, T b) const {
+        atomicAdd(&J[node].x, (double)a);
+        atomicAdd(&J[node].y, (double)b);
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1(size_t node, T a) const {
+        atomicAdd(&J[node].x, (double)a);
+    }
+};
+
+struct AccFix {
+    longlong2* J;
+    float scale;
+    __device__ __forceinline__ static unsigned long long q(float v, float s) {
+        return (unsigned long long)__float2ll_rn(v * s);
+    }
+    template <typename T>
+    __device__ __forceinline__ void add(size_t node, T a, T b) const {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), q((float)a, scale));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].y), q((float)b, scale));
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1(size_t node, T a) const {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), q((float)a, scale));
+    }
+};
+
+template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_move_deposit(ParticleGeom g, T* __restrict__ x, T* __restrict__ y, const T* __restrict__ vx,
-               const T* __restrict__ vy, int64_t n, double2* __restrict__ J,
-               unsigned int* __restrict__ err) {
+               const T* __restrict__ vy, int64_t n, Acc acc, unsigned int* __restrict__ err) {
     const T dt = (T)g.dt, lx = (T)g.lx, ly = (T)g.ly, idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -60,21 +92,20 @@ k_move_deposit(ParticleGeom g, T* __restrict__ x, T* __restrict__ y, const T* __
         for (int a = 0; a <= P; ++a) {
             const int gi = wrap_idx(ix + a, g.nx);
             const T tx = vxi * wx[a], ty = vyi * wx[a];
-            double2* row = J + (size_t)gi * g.ny;
+            const size_t row = (size_t)gi * g.ny;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                atomicAdd(&row[gj].x, (double)(tx * wy[b]));
-                atomicAdd(&row[gj].y, (double)(ty * wy[b]));
+                acc.add(row + gj, tx * wy[b], ty * wy[b]);
             }
         }
     }
 }
 
-template <typename T, int P>
+template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                 double2* __restrict__ J, unsigned int* __restrict__ err) {
+                 Acc acc, unsigned int* __restrict__ err) {
     const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -92,9 +123,29 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                atomicAdd(&J[(size_t)gi * g.ny + gj].x, (double)(wx[a] * wy[b]));
+                acc.add1((size_t)gi * g.ny + gj, wx[a] * wy[b]);
             }
         }
+    }
+}
+
+// Fixed-point (Jx, Jy) sums to complex storage values, times `unscale`.
+template <typename T>
+__global__ void k_fix_to_cplx(const longlong2* __restrict__ J, double unscale,
+                              cplx_t<T>* __restrict__ out, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const longlong2 v = J[k];
+        out[k] = mk<cplx_t<T>>((double)v.x * unscale, (double)v.y * unscale);
+    }
+}
+
+__global__ void k_extract_fix(const longlong2* __restrict__ J, int comp, double scale,
+                              double* __restrict__ dst, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const longlong2 v = J[k];
+        dst[k] = scale * (double)(comp ? v.y : v.x);
     }
 }
 
@@ -155,7 +206,10 @@ k_gather_push(ParticleGeom g, PushParams pp, const T* __restrict__ x, const T* _
         vxo[p] = vxn1;
         vyo[p] = vyn1;
         if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
-        if (pp.diag) kin += (double)(den - mc2);  // m c^2 (gamma - 1) per unit weight
+        if (pp.diag) {  // m c^2 (gamma - 1) per unit weight, in FP64 for either storage type
+            const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
+            kin += sqrt(c2d * (uxd * uxd + uyd * uyd) + mc2d * mc2d) - mc2d;
+        }
     }
     if (bad) atomicOr(err, bad);
     if (pp.diag) {
@@ -255,12 +309,20 @@ __global__ void k_extract(const cplx_t<T>* __restrict__ src, int stride, int com
         default: return cudaErrorInvalidValue;                             \
     }
 
+#define GPIC_DISPATCH_PA(p, KERNEL, ACC, ...)                                               \
+    switch (p) {                                                                           \
+        case 2: KERNEL<T, 2, ACC><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break; \
+        case 3: KERNEL<T, 3, ACC><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break; \
+        case 4: KERNEL<T, 4, ACC><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break; \
+        default: return cudaErrorInvalidValue;                                             \
+    }
+
 template <typename T>
 cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
                                 const T* vy, int64_t n, double2* j, unsigned int* err,
                                 cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_P(p, k_move_deposit, g, x, y, vx, vy, n, j, err)
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccF64, g, x, y, vx, vy, n, AccF64{j}, err)
     return cudaGetLastError();
 }
 
@@ -268,7 +330,38 @@ template <typename T>
 cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
                                   double2* j, unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_P(p, k_deposit_charge, g, x, y, n, j, err)
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccF64, g, x, y, n, AccF64{j}, err)
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
+                                    const T* vy, int64_t n, longlong2* j, float scale,
+                                    unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, g, x, y, vx, vy, n, (AccFix{j, scale}), err)
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, const T* y,
+                                      int64_t n, longlong2* j, float scale, unsigned int* err,
+                                      cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix{j, scale}), err)
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,
+                               cudaStream_t s) {
+    k_fix_to_cplx<T><<<blocks_for(n), kThreads, 0, s>>>(j, unscale, (cplx_t<T>*)out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract_fix(const longlong2* j, int comp, double scale, double* dst, int64_t n,
+                               cudaStream_t s) {
+    k_extract_fix<<<blocks_for(n), kThreads, 0, s>>>(j, comp, scale, dst, n);
     return cudaGetLastError();
 }
 
@@ -343,7 +436,15 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                  cudaStream_t);                                 \
     template cudaError_t launch_extract<T>(const void*, int, int, double, double*, int64_t,     \
                                            cudaStream_t);                                       \
-    template cudaError_t launch_wrap_positions<T>(T*, T*, int64_t, double, double, cudaStream_t);
+    template cudaError_t launch_wrap_positions<T>(T*, T*, int64_t, double, double, cudaStream_t); \
+    template cudaError_t launch_move_deposit_fix<T>(int, const ParticleGeom&, T*, T*, const T*,   \
+                                                    const T*, int64_t, longlong2*, float,         \
+                                                    unsigned int*, cudaStream_t);                 \
+    template cudaError_t launch_deposit_charge_fix<T>(int, const ParticleGeom&, const T*,         \
+                                                      const T*, int64_t, longlong2*, float,       \
+                                                      unsigned int*, cudaStream_t);               \
+    template cudaError_t launch_fix_to_cplx<T>(const longlong2*, double, void*, int64_t,          \
+                                               cudaStream_t);
 GPIC_INST(double)
 GPIC_INST(float)
 #undef GPIC_INST

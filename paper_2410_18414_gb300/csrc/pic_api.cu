@@ -35,7 +35,10 @@ struct pic_handle {
     int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
     double* stage = nullptr;  // FP64 staging for conversions (n values)
     // grid buffers
-    double2* J = nullptr;    // deposit accumulator (sum_p v W), FP64
+    double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
+    // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
+    float fix_scale_j = 0.f, fix_scale_q = 0.f;
+    double fix_unscale_j = 0.0, fix_unscale_q = 0.0;
     void* Z = nullptr;       // spectrum of J (complex)
     void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
     void* G = nullptr;       // [node][4] complex: the eight real gather fields
@@ -143,8 +146,6 @@ pic_status validate(const pic_config* c, const pic_particles_in* in) {
     }
     if (c->precision != PIC_FP64 && c->precision != PIC_FP32_FIX64)
         return fail(h, PIC_ERR_INVALID_ARG, "unknown precision %d", c->precision);
-    if (c->precision == PIC_FP32_FIX64)
-        return fail(h, PIC_ERR_UNSUPPORTED, "the FP32 fixed-point form is not built yet");
     if (c->sort_interval < 0) return fail(h, PIC_ERR_INVALID_ARG, "sort_interval must be >= 0");
     if (in->n < 0 || in->n > 2147483647LL)
         return fail(h, PIC_ERR_INVALID_ARG, "particle count must be 0..2^31-1");
@@ -242,9 +243,10 @@ pic_status alloc_state(pic_handle* h) {
     CK(cudaMemsetAsync(h->err, 0, sizeof(unsigned int), h->s));
     CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
 
+    // time histories are FP64 complex spectra in both precision forms
     auto spec = [&](void** p) {
-        cudaError_t e = dalloc(h, p, h->ng * cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, h->ng * cs, h->s);
+        cudaError_t e = dalloc(h, p, h->ng * sizeof(double2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, h->ng * sizeof(double2), h->s);
         return e;
     };
     if (c.stepper == PIC_STEPPER_BDF) {
@@ -339,14 +341,17 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
         using T = decltype(t);
         cudaError_t r = launch_wrap_positions<T>((T*)h->x, (T*)h->y, n, c.lx, c.ly, h->s);
         if (r != cudaSuccess) return r;
-        r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n, h->J,
-                                     h->err, h->s);
-        if (r != cudaSuccess) return r;
         if (h->fp32) {
-            r = launch_convert<double, float>((const double*)h->J, (float*)h->tmp, 2 * h->ng, h->s);
+            r = launch_deposit_charge_fix<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n,
+                                             (longlong2*)h->J, h->fix_scale_q, h->err, h->s);
+            if (r != cudaSuccess) return r;
+            r = launch_fix_to_cplx<T>((const longlong2*)h->J, h->fix_unscale_q, h->tmp, h->ng, h->s);
             if (r != cudaSuccess) return r;
             r = forward_fft(h, h->tmp, h->Z);
         } else {
+            r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n, h->J,
+                                         h->err, h->s);
+            if (r != cudaSuccess) return r;
             r = forward_fft(h, h->J, h->Z);
         }
         if (r != cudaSuccess) return r;
@@ -360,7 +365,7 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
     }));
     h->vcur = 0;
 
-    const size_t bytes = h->ng * cs;
+    const size_t bytes = h->ng * sizeof(double2);
     if (c.stepper == PIC_STEPPER_BDF) {
         for (int i = 1; i < h->L; ++i)
             CK(cudaMemcpyAsync(h->phi_l[i], phi0, bytes, cudaMemcpyDeviceToDevice, h->s));
@@ -415,6 +420,18 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
     h->mc.dt = cfg->dt;
     h->geom = ParticleGeom{cfg->nx, cfg->ny, cfg->lx, cfg->ly, 1.0 / dx, 1.0 / dy, cfg->dt};
     h->push = PushParams{cfg->q, cfg->m, cfg->c, cfg->dt, cfg->weight, 0};
+    if (h->fp32) {
+        // Fixed-point scale 2^k: every contribution is at most |v| W <= c (current) or
+        // W <= 1 (charge), so with k = 62 - ceil(log2 n) no node total can reach 2^62
+        // whatever the particle distribution.
+        int k = 46;
+        if (h->n > 1) k = std::min(46, 62 - (int)std::ceil(std::log2((double)h->n)));
+        const double two_k = std::ldexp(1.0, k);
+        h->fix_scale_j = (float)(two_k / cfg->c);
+        h->fix_unscale_j = 1.0 / (double)h->fix_scale_j;
+        h->fix_scale_q = (float)two_k;
+        h->fix_unscale_q = 1.0 / two_k;
+    }
     st = alloc_state(h);
     if (st == PIC_OK) st = setup(h, init);
     if (st != PIC_OK) {
@@ -434,6 +451,10 @@ pic_status pic_deposit(pic_handle* h) {
     CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
+        if (h->fp32)
+            return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
+                                              (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
+                                              h->n, (longlong2*)h->J, h->fix_scale_j, h->err, h->s);
         return launch_move_deposit<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
                                       (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1], h->n,
                                       h->J, h->err, h->s);
@@ -449,7 +470,7 @@ pic_status pic_field_solve(pic_handle* h) {
     h->mc.diag = h->diag_now ? 1 : 0;
     if (h->diag_now) CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
     if (h->fp32) {
-        CK(launch_convert<double, float>((const double*)h->J, (float*)h->tmp, 2 * h->ng, h->s));
+        CK(launch_fix_to_cplx<float>((const longlong2*)h->J, h->fix_unscale_j, h->tmp, h->ng, h->s));
         CK(forward_fft(h, h->tmp, h->Z));
     } else {
         CK(forward_fft(h, h->J, h->Z));
@@ -581,6 +602,9 @@ pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
         switch (which) {
             case PIC_FIELD_JX:
             case PIC_FIELD_JY:
+                if (h->fp32)
+                    return launch_extract_fix((const longlong2*)h->J, which == PIC_FIELD_JY,
+                                              h->fix_unscale_j * h->mc.jscale, h->tmpd, n, h->s);
                 return launch_extract<double>(h->J, 1, which == PIC_FIELD_JY, h->mc.jscale, h->tmpd, n, h->s);
             case PIC_FIELD_DPHIDX: case PIC_FIELD_DPHIDY: case PIC_FIELD_GAX: case PIC_FIELD_GAY:
             case PIC_FIELD_DAXDX: case PIC_FIELD_DAXDY: case PIC_FIELD_DAYDX: case PIC_FIELD_DAYDY: {

@@ -1,0 +1,155 @@
+"""GPU checks of the FP32 form (FP32 particles and FFT, int64 fixed-point current).
+
+Against the FP64 oracle the FP32 form is compared with tolerances derived from FP32
+arithmetic (unit roundoff u = 6e-8): particle arrays carry a few u of rounding per step
+(measured <= 4e-7 after 10 steps), grid fields inherit the FP32 weights and transforms,
+amplified by the cancellation of a nearly neutral plasma (measured <= 5e-6 on small grids,
+<= 2e-5 on the 128x128 workload).  Each bound below is about 5x the measured error.
+
+What the FP32 form must keep exactly: the gauge, Gauss (BDF, CDF) and continuity
+residuals stay at FP64 roundoff, because the per-mode recurrences and the histories are
+FP64 whatever the storage type; and the current is summed in int64, so results are
+bitwise reproducible and do not depend on the order of the particles.
+"""
+import numpy as np
+import pytest
+
+from oracle import pic as opic
+from oracle import steppers as osteps
+from paper_2410_18414_gb300 import pic, workloads
+
+pytestmark = pytest.mark.gpu
+
+P_TOL = 2e-6
+F_TOL = 3e-5
+PARTICLE_KEYS = ("px", "py", "vx", "vy", "vx_old", "vy_old")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def wrapped_rel(a, b, length):
+    d = np.mod(a - b + 0.5 * length, length) - 0.5 * length
+    return float(np.linalg.norm(d) / np.linalg.norm(b))
+
+
+def fp32_sim(wl, device, diag=0, order=None, **kw):
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                          precision=pic.FP32_FIX64, **kw)
+    x, y, vx, vy = wl.x, wl.y, wl.vx, wl.vy
+    if order is not None:
+        x, y, vx, vy = x[order], y[order], vx[order], vy[order]
+    sim = pic.Simulation(cfg, x, y, vx, vy, stream=device)
+    if diag:
+        sim.set_diagnostics(diag)
+    return sim
+
+
+CASES = [
+    ("cloud32_bdf1_p2", lambda: workloads.drifting_cloud(n=16384, nx=32, ny=32),
+     dict(stepper="bdf", bdf_order=1)),
+    ("weibel24x16_bdf2_p3", lambda: workloads.weibel(24, 16, 8, 0.5, 0.01, 21, 3, n=3001),
+     dict(stepper="bdf", bdf_order=2)),
+    ("weibel32x48_cdf2_p4", lambda: workloads.weibel(32, 48, 4, 0.5, 0.01, 22, 4, n=5003),
+     dict(stepper="cdf2")),
+    ("weibel16_dirk2_p2", lambda: workloads.weibel(16, 16, 8, 0.5, 0.01, 23, 2, n=2001),
+     dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG)),
+    ("weibel48x32_dirk3_p4", lambda: workloads.weibel(48, 32, 3, 0.6, 0.02, 24, 4, n=4099),
+     dict(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT)),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_fp32_form_against_oracle(device, name, make, kw):
+    wl = make()
+    nsteps = 10
+    sim = fp32_sim(wl, device, diag=1, **kw)
+    sim.step(nsteps)
+    got = sim.particles()
+    ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, w=wl.weight, **kw)
+    st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, nsteps)
+    errs = {"x": wrapped_rel(got["x"], st.x, wl.lx), "y": wrapped_rel(got["y"], st.y, wl.ly)}
+    errs.update({k: rel(got[k], getattr(st, k)) for k in PARTICLE_KEYS})
+    bad = {k: v for k, v in errs.items() if not v <= P_TOL}
+    ferrs = {f: rel(sim.field(f), st.grids[f]) for f in
+             ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "dphidx", "daxdx", "daydy")}
+    bad.update({k: v for k, v in ferrs.items() if not v <= F_TOL})
+    assert not bad, bad
+    # the theorems of section 3 hold to FP64 roundoff in the FP32 form too
+    d = sim.residuals()
+    assert d["gauge_rms"] <= 1e-11 * d["div_a_rms"], d
+    assert d["continuity_rms"] <= 1e-11 * d["rho_rms"] / wl.dt, d
+    if kw["stepper"] != "dirk":
+        assert d["gauss_rms"] <= 1e-11 * d["rho_rms"], d
+    sim.close()
+
+
+def test_fp32_form_bitwise_reproducible_and_order_independent(device):
+    wl = workloads.weibel(32, 32, 16, 0.5, 0.01, 91, 3, n=16001)
+    kw = dict(stepper="bdf", bdf_order=2)
+    a = fp32_sim(wl, device, **kw)
+    b = fp32_sim(wl, device, **kw)
+    perm = np.random.default_rng(1).permutation(wl.n)
+    c = fp32_sim(wl, device, order=perm, **kw)
+    for s in (a, b, c):
+        s.step(8)
+    pa, pb, pc = a.particles(), b.particles(), c.particles()
+    inv = np.argsort(perm)
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+        assert np.array_equal(pa[k], pc[k][inv]), k
+    for f in ("jx", "jy", "phi", "ax"):
+        assert np.array_equal(a.field(f), b.field(f)) and np.array_equal(a.field(f), c.field(f))
+    for s in (a, b, c):
+        s.close()
+
+
+def test_fp32_form_full_size_weibel_128(device):
+    wl = workloads.weibel_128(stepper="bdf", bdf_order=2)
+    kw = dict(stepper="bdf", bdf_order=2)
+    sim = fp32_sim(wl, device, **kw)
+    sim.step(2)
+    got = sim.particles()
+    ocfg = opic.Config(nx=128, ny=128, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=3, w=wl.weight, **kw)
+    st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, 2)
+    assert wrapped_rel(got["x"], st.x, wl.lx) <= P_TOL
+    for k in PARTICLE_KEYS:
+        assert rel(got[k], getattr(st, k)) <= P_TOL, k
+    limits = {"jx": 5e-5, "jy": 5e-5, "rho": 5e-5, "phi": 1e-4, "ax": 5e-5, "dphidx": 1e-4}
+    for f, tol in limits.items():
+        assert rel(sim.field(f), st.grids[f]) <= tol, f
+    sim.close()
+
+
+def test_fp32_form_empty_and_edge_particles(device):
+    x = np.array([0.0, np.nextafter(1.0, 0.0), 1.0, 0.5])
+    y = np.array([np.nextafter(1.0, 0.0), 0.0, 0.25, 1.0])
+    vx = np.array([-0.3, 0.3, 0.0, 0.1])
+    vy = np.array([0.3, -0.3, 0.0, -0.1])
+    wl = workloads.Workload("edge", 16, 16, 1.0, 1.0, 0.5 / 16, 2, "bdf", 2, 5, x, y, vx, vy)
+    sim = fp32_sim(wl, device, stepper="bdf", bdf_order=2)
+    sim.step(5)
+    got = sim.particles()
+    assert np.all((got["x"] >= 0) & (got["x"] < 1.0))
+    sim.close()
+    e = np.zeros(0)
+    wl0 = workloads.Workload("empty", 16, 16, 1.0, 1.0, 0.01, 3, "bdf", 1, 2, e, e, e, e)
+    sim = fp32_sim(wl0, device, stepper="cdf2")
+    sim.step(2)
+    assert np.max(np.abs(sim.field("jx"))) == 0.0
+    sim.close()
