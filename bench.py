@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default="bdf2")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="form timed for the headline value; the other form is timed beside it")
+    ap.add_argument("--sort-interval", type=int, default=8,
+                    help="re-sort particles by tile every this many steps (0 = never)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-steppers", action="store_true")
     return ap.parse_args()
@@ -62,13 +64,14 @@ def dirk_tableau(name):
             "b": [1 / 3, 1 / 3, 1 / 3], "c": [1 / 6, 0.5, 5 / 6]}
 
 
-def make_config(wl, stepper_name, precision="fp64"):
+def make_config(wl, stepper_name, precision="fp64", sort_interval=0):
     from paper_2410_18414_gb300 import pic
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
     prec = pic.FP32_FIX64 if precision == "fp32" else pic.FP64
     return pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper=stepper,
-                           bdf_order=k, dirk=dirk, weight=wl.weight, precision=prec)
+                           bdf_order=k, dirk=dirk, weight=wl.weight, precision=prec,
+                           sort_interval=sort_interval)
 
 
 def workload_desc(wl, stepper_name):
@@ -249,7 +252,7 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm --
 
-def time_steps(sim, steps, warmup, stream, flush):
+def time_steps(sim, steps, warmup, stream, flush, count=None):
     import torch
     for _ in range(warmup):
         sim.step(1)
@@ -265,6 +268,8 @@ def time_steps(sim, steps, warmup, stream, flush):
         e[2].record(stream)
         sim.gather_push()
         e[3].record(stream)
+        if count is not None:
+            count[0] += sim.kernels_per_step
         flush.zero_()       # cold L2 for the next step (outside the events)
     torch.cuda.synchronize()
     dep = [e[0].elapsed_time(e[1]) for e in ev]
@@ -297,7 +302,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     wl = make_workload(2 + rank)
-    cfg = make_config(wl, a.stepper, a.precision)
+    cfg = make_config(wl, a.stepper, a.precision, a.sort_interval)
     sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
 
     def barrier():
@@ -309,7 +314,8 @@ def main():
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    t = time_steps(sim, a.steps, a.warmup, stream, flush)
+    launches = [0]
+    t = time_steps(sim, a.steps, a.warmup, stream, flush, launches)
     clk = clocks.stop()
     barrier()
     sim.sync()
@@ -358,11 +364,15 @@ def main():
 
     # the other precision form on the same workload (the metric's comparison)
     other = "fp64" if fp32 else "fp32"
-    so = pic.Simulation(make_config(wl, a.stepper, other), wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+    # (each form at its own best setting: the FP64 path's global FP64 atomics contend more
+    # on tile-sorted particles, so it runs unsorted)
+    other_sort = a.sort_interval if other == "fp32" else 0
+    so = pic.Simulation(make_config(wl, a.stepper, other, other_sort), wl.x, wl.y, wl.vx,
+                        wl.vy, stream=sp)
     to = time_steps(so, max(20, a.steps // 4), 5, stream, flush)
     so.close()
     other_ms = statistics.mean(to["step_ms"])
-    other_form = {"form": other, "ms_per_step": other_ms,
+    other_form = {"form": other, "ms_per_step": other_ms, "sort_interval": other_sort,
                   "value": wl.n * world / (other_ms * 1e-3),
                   "phase_ms": {"deposit": statistics.mean(to["deposit_ms"]),
                                "field_solve": statistics.mean(to["field_ms"]),
@@ -374,8 +384,8 @@ def main():
         for name in ("bdf2", "cdf2", "dirk2"):
             if name == a.stepper:
                 continue
-            s2 = pic.Simulation(make_config(wl, name, a.precision), wl.x, wl.y, wl.vx, wl.vy,
-                                stream=sp)
+            s2 = pic.Simulation(make_config(wl, name, a.precision, a.sort_interval), wl.x, wl.y,
+                                wl.vx, wl.vy, stream=sp)
             t2 = time_steps(s2, max(10, a.steps // 5), 3, stream, flush)
             by_stepper[name] = statistics.mean(t2["step_ms"])
             s2.close()
@@ -419,6 +429,7 @@ def main():
             "config": dict(workload_desc(wl, a.stepper),
                            form="fp32_fix64" if fp32 else "fp64",
                            l2="flushed between timed steps (256 MiB device write)",
+                           sort_interval=a.sort_interval,
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline,
             "kernels": {k: {kk: round(vv, 6) if isinstance(vv, float) else vv
@@ -429,7 +440,7 @@ def main():
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": sim.kernels_per_step * a.steps,
+            "gpu_launches": launches[0],
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

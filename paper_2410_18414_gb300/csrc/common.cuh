@@ -81,6 +81,26 @@ __device__ __forceinline__ int wrap_idx(int i, int n) {
     return i;
 }
 
+// ------------------------------------------------------------ exact ops -----
+//
+// Round-to-nearest arithmetic that the compiler may not contract or reorder: the shape
+// weights, the move and the current contributions are written with these, so every
+// kernel that evaluates them (tiled or not, FP32 or FP64) produces the same bits.
+
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// x + v dt, wrapped (the IAEM position update)
+template <typename T> __device__ __forceinline__ T move_pos(T x, T v, T dt, T l) {
+    return wrap_pos(rfma(v, dt, x), l);
+}
+
 // ------------------------------------------------------------ shapes ------
 //
 // Centred cardinal B-spline of degree P (unit integral) in closed form.  For a
@@ -90,46 +110,58 @@ __device__ __forceinline__ int wrap_idx(int i, int n) {
 template <int P, typename T> struct Shape;
 
 template <typename T> struct Shape<2, T> {
+    // d in [-1/2, 1/2): w = ((1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2)
     static __device__ __forceinline__ int weights(T xi, T* w) {
-        T f = floor(xi + (T)0.5);
-        T d = xi - f;
-        T hm = (T)0.5 - d, hp = (T)0.5 + d;
-        w[0] = (T)0.5 * hm * hm;
-        w[1] = (T)0.75 - d * d;
-        w[2] = (T)0.5 * hp * hp;
+        const T h = (T)0.5;
+        T f = floor(radd(xi, h));
+        T d = rsub(xi, f);
+        T hm = rsub(h, d), hp = radd(h, d);
+        w[0] = rmul(h, rmul(hm, hm));
+        w[1] = rfma(-d, d, (T)0.75);
+        w[2] = rmul(h, rmul(hp, hp));
         return (int)f - 1;
     }
 };
 
 template <typename T> struct Shape<3, T> {
+    // d in [0, 1), e = 1 - d: w = (e^3/6, 2/3 - d^2 + d^3/2, 2/3 - e^2 + e^3/2, d^3/6)
     static __device__ __forceinline__ int weights(T xi, T* w) {
         T f = floor(xi);
-        T d = xi - f;
-        T e = (T)1 - d;
-        const T s6 = (T)(1.0 / 6.0), t3 = (T)(2.0 / 3.0);
-        w[0] = s6 * e * e * e;
-        w[1] = t3 - d * d + (T)0.5 * d * d * d;
-        w[2] = t3 - e * e + (T)0.5 * e * e * e;
-        w[3] = s6 * d * d * d;
+        T d = rsub(xi, f);
+        T e = rsub((T)1, d);
+        const T s6 = (T)(1.0 / 6.0), t3 = (T)(2.0 / 3.0), h = (T)0.5;
+        T d2 = rmul(d, d), e2 = rmul(e, e);
+        T d3 = rmul(d2, d), e3 = rmul(e2, e);
+        w[0] = rmul(s6, e3);
+        w[1] = rfma(h, d3, rsub(t3, d2));
+        w[2] = rfma(h, e3, rsub(t3, e2));
+        w[3] = rmul(s6, d3);
         return (int)f - 1;
     }
 };
 
 template <typename T> struct Shape<4, T> {
-    static __device__ __forceinline__ T mid(T t) {  // 1/2 <= |t| < 3/2
-        return ((T)55 + t * ((T)20 + t * ((T)-120 + t * ((T)80 - (T)16 * t)))) * (T)(1.0 / 96.0);
+    // |t| in [1/2, 3/2): (55 + 20|t| - 120 t^2 + 80 |t|^3 - 16 t^4)/96, Horner form
+    static __device__ __forceinline__ T mid(T t) {
+        T r = rfma((T)-16, t, (T)80);
+        r = rfma(r, t, (T)-120);
+        r = rfma(r, t, (T)20);
+        r = rfma(r, t, (T)55);
+        return rmul(r, (T)(1.0 / 96.0));
     }
+    // d in [-1/2, 1/2): w = ((1-2d)^4/384, mid(1+d), (115 - 120 d^2 + 48 d^4)/192,
+    //                       mid(1-d), (1+2d)^4/384)
     static __device__ __forceinline__ int weights(T xi, T* w) {
-        T f = floor(xi + (T)0.5);
-        T d = xi - f;
-        T a = (T)1 - (T)2 * d, b = (T)1 + (T)2 * d;
-        T a2 = a * a, b2 = b * b, d2 = d * d;
+        T f = floor(radd(xi, (T)0.5));
+        T d = rsub(xi, f);
+        T a = rfma((T)-2, d, (T)1), b = rfma((T)2, d, (T)1);
+        T a2 = rmul(a, a), b2 = rmul(b, b), d2 = rmul(d, d);
         const T s384 = (T)(1.0 / 384.0);
-        w[0] = s384 * a2 * a2;
-        w[1] = mid((T)1 + d);
-        w[2] = ((T)115 - (T)120 * d2 + (T)48 * d2 * d2) * (T)(1.0 / 192.0);
-        w[3] = mid((T)1 - d);
-        w[4] = s384 * b2 * b2;
+        w[0] = rmul(s384, rmul(a2, a2));
+        w[1] = mid(radd((T)1, d));
+        w[2] = rmul(rfma(rmul((T)48, d2), d2, rfma((T)-120, d2, (T)115)), (T)(1.0 / 192.0));
+        w[3] = mid(rsub((T)1, d));
+        w[4] = rmul(s384, rmul(b2, b2));
         return (int)f - 2;
     }
 };

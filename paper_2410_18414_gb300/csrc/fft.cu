@@ -13,6 +13,7 @@
 //     dst[(j div Ns) Ns R + k + r Ns] = b_r
 // which leaves the transform in natural order after the last pass.
 #include "common.cuh"
+#include "fft_device.cuh"
 #include "gpic_internal.h"
 
 namespace gpic {
@@ -21,93 +22,12 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename C>
-__device__ __forceinline__ void small_dft(C* a, int R, int sign) {
-    if (R == 2) {
-        C t = a[0];
-        a[0] = cadd(t, a[1]);
-        a[1] = csub(t, a[1]);
-    } else if (R == 4) {
-        C t0 = cadd(a[0], a[2]);
-        C t1 = csub(a[0], a[2]);
-        C t2 = cadd(a[1], a[3]);
-        C t3 = cmul_si(csub(a[1], a[3]), sign);
-        a[0] = cadd(t0, t2);
-        a[2] = csub(t0, t2);
-        a[1] = cadd(t1, t3);
-        a[3] = csub(t1, t3);
-    } else {  // R == 3
-        using T = decltype(a[0].x);
-        const T h = (T)0.86602540378443864676;  // sqrt(3)/2
-        C t = cadd(a[1], a[2]);
-        C d = csub(a[1], a[2]);
-        C u = cmul_si(d, sign);
-        u.x *= h;
-        u.y *= h;
-        C m = a[0];
-        m.x -= (T)0.5 * t.x;
-        m.y -= (T)0.5 * t.y;
-        a[0] = cadd(a[0], t);
-        a[1] = cadd(m, u);
-        a[2] = csub(m, u);
-    }
-}
-
-template <typename C>
-__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst,
-                                              int n, int R, int Ns, int lines,
-                                              const C* __restrict__ tw, int sign) {
-    const int nr = n / R;
-    const int twstep = n / (Ns * R);
-    for (int idx = threadIdx.x; idx < lines * nr; idx += blockDim.x) {
-        int line = idx / nr;
-        int j = idx - line * nr;
-        int k = j % Ns;
-        const C* s = src + line * n;
-        C a[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < R) a[r] = s[j + r * nr];
-#pragma unroll
-        for (int r = 1; r < 4; ++r) {
-            if (r < R && k != 0) {
-                C w = __ldg(tw + r * k * twstep);
-                if (sign > 0) w.y = -w.y;
-                a[r] = cmul(a[r], w);
-            }
-        }
-        small_dft(a, R, sign);
-        int base = (j / Ns) * Ns * R + k;
-        C* d = dst + line * n;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < R) d[base + r * Ns] = a[r];
-    }
-}
-
-// Runs all passes; returns the buffer that holds the result.
-template <typename C>
-__device__ C* run_passes(C* b0, C* b1, const FftDesc& d, int lines, const C* tw, int sign) {
-    C* src = b0;
-    C* dst = b1;
-    int Ns = 1;
-    for (int f = 0; f < d.nf; ++f) {
-        int R = d.radix[f];
-        stockham_pass(src, dst, d.n, R, Ns, lines, tw, sign);
-        __syncthreads();
-        C* t = src;
-        src = dst;
-        dst = t;
-        Ns *= R;
-    }
-    return src;
-}
-
 // Transforms along y (contiguous): CTA = `rows` consecutive x-indices of all nb arrays.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, int ny, int nb,
-        int rows, FftDesc d, const cplx_t<T>* __restrict__ tw, int sign, int interleave) {
+        int rows, FftDesc d, const cplx_t<T>* __restrict__ tw, int sign, int interleave,
+        const longlong2* __restrict__ fix_in, double unscale) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* b0 = reinterpret_cast<C*>(smem_raw);
@@ -118,7 +38,13 @@ k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, i
     for (int e = threadIdx.x; e < lines * ny; e += blockDim.x) {
         int l = e / ny, jj = e - l * ny;
         int b = l / rows, r = l - b * rows;
-        b0[e] = in[b * plane + (size_t)(i0 + r) * ny + jj];
+        const size_t src = b * plane + (size_t)(i0 + r) * ny + jj;
+        if (fix_in) {  // fixed-point current sums, converted on load
+            const longlong2 v = fix_in[src];
+            b0[e] = mk<C>((double)v.x * unscale, (double)v.y * unscale);
+        } else {
+            b0[e] = in[src];
+        }
     }
     __syncthreads();
     C* res = run_passes(b0, b1, d, lines, tw, sign);
@@ -181,21 +107,34 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
-                         const void* tw, int sign, int interleave, cudaStream_t s) {
+static cudaError_t fft_y_impl(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
+                              const void* tw, int sign, int interleave, const longlong2* fix_in,
+                              double unscale, cudaStream_t s) {
     using C = cplx_t<T>;
     const size_t per_line = 2 * (size_t)ny * sizeof(C);
-    int rows = 1;
-    while (rows * 2 <= 8 && nx % (rows * 2) == 0 &&
-           (size_t)(rows * 2) * nb * per_line <= kSmemBudget)
-        rows *= 2;
+    // few lines per CTA: these transforms are latency-bound, so favour CTAs (one row of
+    // all nb arrays each, or two rows when there is a single array)
+    int rows = nb == 1 && nx % 2 == 0 ? 2 : 1;
+    if ((size_t)rows * nb * per_line > 200 * 1024) rows = 1;
     if ((size_t)rows * nb * per_line > 200 * 1024) return cudaErrorInvalidValue;
     size_t smem = (size_t)rows * nb * per_line;
     cudaError_t e = set_smem(k_fft_y<T>, smem);
     if (e != cudaSuccess) return e;
     k_fft_y<T><<<nx / rows, kThreads, smem, s>>>((const C*)in, (C*)out, nx, ny, nb, rows, d,
-                                                 (const C*)tw, sign, interleave);
+                                                 (const C*)tw, sign, interleave, fix_in, unscale);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
+                         const void* tw, int sign, int interleave, cudaStream_t s) {
+    return fft_y_impl<T>(in, out, nx, ny, nb, d, tw, sign, interleave, nullptr, 0.0, s);
+}
+
+template <typename T>
+cudaError_t launch_fft_y_from_fix(const longlong2* j, double unscale, void* out, int nx, int ny,
+                                  const FftDesc& d, const void* tw, cudaStream_t s) {
+    return fft_y_impl<T>(nullptr, out, nx, ny, 1, d, tw, -1, 0, j, unscale, s);
 }
 
 template <typename T>
@@ -230,6 +169,10 @@ template cudaError_t launch_fft_x<double>(const void*, void*, int, int, int, con
                                           const void*, int, cudaStream_t);
 template cudaError_t launch_fft_x<float>(const void*, void*, int, int, int, const FftDesc&,
                                          const void*, int, cudaStream_t);
+template cudaError_t launch_fft_y_from_fix<double>(const longlong2*, double, void*, int, int,
+                                                   const FftDesc&, const void*, cudaStream_t);
+template cudaError_t launch_fft_y_from_fix<float>(const longlong2*, double, void*, int, int,
+                                                  const FftDesc&, const void*, cudaStream_t);
 template cudaError_t launch_twiddles<double>(void*, int, cudaStream_t);
 template cudaError_t launch_twiddles<float>(void*, int, cudaStream_t);
 

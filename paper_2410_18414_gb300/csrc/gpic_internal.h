@@ -77,6 +77,10 @@ enum StepperKind { K_BDF = 0, K_CDF2 = 1, K_DIRK = 2 };
 template <typename T>
 cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
                          const void* twiddle, int sign, int out_interleave, cudaStream_t s);
+// Forward transform along y of the fixed-point current (converted on load).
+template <typename T>
+cudaError_t launch_fft_y_from_fix(const longlong2* j, double unscale, void* out, int nx, int ny,
+                                  const FftDesc& d, const void* tw, cudaStream_t s);
 // Along x (stride ny).
 template <typename T>
 cudaError_t launch_fft_x(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
@@ -98,6 +102,18 @@ cudaError_t launch_mode_cdf2(const ModeCommon& mc, const CdfParams& cp, const vo
 template <typename T>
 cudaError_t launch_mode_dirk(const ModeCommon& mc, const DirkParams& dp, const void* z, void* f4,
                              void* e_packed, double* diag, cudaStream_t s);
+// Fused column pass of the field solve (forward transform along x, per-mode update,
+// inverse transforms along x of the four outputs): one CTA per column pair, 16 lines of
+// nx complex values in shared memory.  `kind` is a StepperKind.
+inline size_t field_columns_smem(int nx, size_t complex_bytes) {
+    return 16 * (size_t)nx * complex_bytes;
+}
+constexpr size_t kFieldColumnsSmemMax = 200 * 1024;
+template <typename T>
+cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams& bp,
+                                 const CdfParams& cp, const DirkParams& dp, const void* z,
+                                 void* f4, void* e, double* diag, const FftDesc& fd,
+                                 const void* tw, cudaStream_t s);
 // Pack two spectra a + i b (scaled by inv_n) for an inverse transform to two real fields.
 template <typename T>
 cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,
@@ -158,6 +174,37 @@ cudaError_t launch_convert(const Tsrc* src, Tdst* dst, int64_t n, cudaStream_t s
 template <typename T>
 cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, int64_t n,
                                  cudaStream_t s);
+
+// Tiles for the particle sort and the shared-memory deposit: t x t cells per tile,
+// ntx x nty tiles; a CTA accumulates into an rx x ry node region starting `halo` nodes
+// before its tile's first node (wrapping periodically).
+struct TileGeom {
+    int nx, ny, t, ntx, nty, halo, rx, ry;
+    double inv_dx, inv_dy;
+};
+
+// Particle arrays moved by the sort: x, y, Px, Py, v[0].x, v[0].y, v[1].x, v[1].y, and the
+// particle's index at pic_init.
+template <typename T>
+struct SortArrays {
+    T* a[8];
+    int32_t* id;
+};
+
+template <typename T>
+cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
+                             int* keys, int* keys_out, int* hist, int* off, int* cursor,
+                             cudaStream_t s);
+cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
+
+// Move + deposit over tile-sorted particles: CTA b takes particles [b*chunk, (b+1)*chunk)
+// and accumulates each tile segment in shared memory.  `fix` selects the int64
+// fixed-point accumulation (J is longlong2) with `scale`, else FP64 (J is double2).
+template <typename T>
+cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
+                                      T* y, const T* vx, const T* vy, int64_t n, const int* keys,
+                                      const int* off, void* j, bool fix, float scale,
+                                      unsigned int* err, cudaStream_t s);
 
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };

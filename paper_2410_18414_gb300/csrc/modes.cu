@@ -18,7 +18,13 @@
 // (k, -k):  Jx = (Z(k) + conj Z(-k))/2,  Jy = (Z(k) - conj Z(-k))/(2i).
 // Outputs are four packed spectra whose inverse FFTs give the real field pairs
 // (dphi/dx, dphi/dy), (Ax, Ay), (dAx/dx, dAx/dy), (dAy/dx, dAy/dy).
+//
+// Two drivers share the per-mode code: one thread per mode over a transformed spectrum
+// (k_mode_*), and the fused column kernel k_field_columns, which also performs the
+// forward transform along x before the update and the inverse transforms along x of the
+// four outputs after it, all in shared memory.
 #include "common.cuh"
+#include "fft_device.cuh"
 #include "gpic_internal.h"
 
 namespace gpic {
@@ -28,33 +34,37 @@ namespace {
 constexpr int kModeThreads = 256;
 
 struct ModeIn {
-    int idx;
+    int idx;  // i * ny + j
     double kx, ky, K;
     zd jx, jy, divj;
 };
 
-template <typename C>
-__device__ __forceinline__ ModeIn mode_in(const ModeCommon& mc, const C* z, int idx) {
+// Mode (i, j) from Z(k) = za and Z(-k) = zb.
+__device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, zd za, zd zb) {
     ModeIn m;
-    m.idx = idx;
-    int i = idx / mc.ny, j = idx - i * mc.ny;
-    int ip = (i == 0) ? 0 : mc.nx - i;
-    int jp = (j == 0) ? 0 : mc.ny - j;
+    m.idx = i * mc.ny + j;
     m.kx = wavenumber(i, mc.nx, mc.kx_scale);
     m.ky = wavenumber(j, mc.ny, mc.ky_scale);
     m.K = m.kx * m.kx + m.ky * m.ky;
-    if (z) {
-        zd a = zload(z + idx);
-        zd b = zconj(zload(z + (ip * mc.ny + jp)));
-        double hs = 0.5 * mc.jscale;
-        m.jx = hs * (a + b);
-        zd d = a - b;  // = 2i Jy / jscale
-        m.jy = zd{hs * d.im, -hs * d.re};
-        m.divj = zi(m.kx * m.jx + m.ky * m.jy);
-    } else {
-        m.jx = m.jy = m.divj = zd{0, 0};
-    }
+    const zd b = zconj(zb);
+    const double hs = 0.5 * mc.jscale;
+    m.jx = hs * (za + b);
+    const zd d = za - b;  // = 2i Jy / jscale
+    m.jy = zd{hs * d.im, -hs * d.re};
+    m.divj = zi(m.kx * m.jx + m.ky * m.jy);
     return m;
+}
+
+template <typename C>
+__device__ __forceinline__ ModeIn mode_from_global(const ModeCommon& mc, const C* z, int idx) {
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const int ip = (i == 0) ? 0 : mc.nx - i;
+    const int jp = (j == 0) ? 0 : mc.ny - j;
+    if (!z) {
+        ModeIn m = make_mode(mc, i, j, zd{0, 0}, zd{0, 0});
+        return m;
+    }
+    return make_mode(mc, i, j, zload(z + idx), zload(z + (ip * mc.ny + jp)));
 }
 
 __device__ __forceinline__ zd div2(double kx, double ky, zd ax, zd ay) {
@@ -66,18 +76,17 @@ __device__ __forceinline__ zd grad_packed(double kx, double ky, zd u) {
     return zi(kx * u) - ky * u;
 }
 
-template <typename C>
-__device__ __forceinline__ void store_outputs(const ModeCommon& mc, C* f4, int idx, double kx,
-                                              double ky, zd phit, zd ax, zd ay) {
-    const size_t N = (size_t)mc.nx * mc.ny;
+// The four packed output spectra of one mode, with the inverse-FFT factor 1/(nx ny).
+__device__ __forceinline__ void packed_outputs(const ModeCommon& mc, const ModeIn& m, zd phit,
+                                               zd ax, zd ay, zd* out) {
     const double s = mc.inv_n;
-    zstore(f4 + idx, s * grad_packed(kx, ky, phit));
-    zstore(f4 + N + idx, s * (ax + zi(ay)));
-    zstore(f4 + 2 * N + idx, s * grad_packed(kx, ky, ax));
-    zstore(f4 + 3 * N + idx, s * grad_packed(kx, ky, ay));
+    out[0] = s * grad_packed(m.kx, m.ky, phit);
+    out[1] = s * (ax + zi(ay));
+    out[2] = s * grad_packed(m.kx, m.ky, ax);
+    out[3] = s * grad_packed(m.kx, m.ky, ay);
 }
 
-// Block-wide sum of D_NSLOTS accumulators, then one atomicAdd per slot.
+// Block-wide sum of D_NSLOTS accumulators, then one atomicAdd per slot (256 threads).
 __device__ void reduce_diag(double* acc, double* diag) {
     __shared__ double red[kModeThreads / 32][D_NSLOTS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -95,124 +104,118 @@ __device__ void reduce_diag(double* acc, double* diag) {
     }
 }
 
-__device__ __forceinline__ void diag_fields(double* acc, const ModeCommon& mc, double kx,
-                                            double ky, zd ex, zd ey, zd ax, zd ay) {
+__device__ __forceinline__ void diag_fields(double* acc, double kx, double ky, zd ex, zd ey,
+                                            zd ax, zd ay) {
     acc[D_WE] += znorm2(ex) + znorm2(ey);
     zd bz = zi(kx * ay) - zi(ky * ax);
     acc[D_WB] += znorm2(bz);
     acc[D_DIVA] += znorm2(div2(kx, ky, ax, ay));
 }
 
-template <typename C>
-__global__ void __launch_bounds__(kModeThreads)
-k_mode_bdf(ModeCommon mc, BdfParams bp, const C* __restrict__ z, C* __restrict__ f4,
-           C* __restrict__ epk, double* __restrict__ diag) {
-    const int nmodes = mc.nx * mc.ny;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[D_NSLOTS];
-#pragma unroll
-    for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
-    if (idx < nmodes) {
-        ModeIn m = mode_in(mc, z, idx);
-        const int k = bp.k;
-        zd rho_new = -bp.bdt * m.divj;
-        for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * zload((const double2*)bp.rho[d - 1] + idx);
-        rho_new = (1.0 / bp.a[0]) * rho_new;
-        const double inv = 1.0 / (bp.C[0] + bp.g * m.K);
-        zd sphi = (bp.g / mc.eps0) * rho_new;
-        zd sax = (bp.g * mc.mu0) * m.jx;
-        zd say = (bp.g * mc.mu0) * m.jy;
-        for (int d = 1; d <= 2 * k; ++d) {
-            sphi = sphi - bp.C[d] * zload((const double2*)bp.phi[d - 1] + idx);
-            sax = sax - bp.C[d] * zload((const double2*)bp.ax[d - 1] + idx);
-            say = say - bp.C[d] * zload((const double2*)bp.ay[d - 1] + idx);
-        }
-        zd phi_new = inv * sphi, ax_new = inv * sax, ay_new = inv * say;
-        if (mc.diag) {
-            // section 3.2: gauge eps_1, continuity eps_2, and Gauss with
-            // E^{n+1} = -grad phi^{n+1} - (1/(beta dt)) sum_j a_j A^{n+1-j}
-            zd dphi = bp.a[0] * phi_new, dax = bp.a[0] * ax_new, day = bp.a[0] * ay_new;
-            zd drho = bp.a[0] * rho_new;
-            for (int d = 1; d <= k; ++d) {
-                dphi = dphi + bp.a[d] * zload((const double2*)bp.phi[d - 1] + idx);
-                dax = dax + bp.a[d] * zload((const double2*)bp.ax[d - 1] + idx);
-                day = day + bp.a[d] * zload((const double2*)bp.ay[d - 1] + idx);
-                drho = drho + bp.a[d] * zload((const double2*)bp.rho[d - 1] + idx);
-            }
-            const double ibdt = 1.0 / bp.bdt;
-            zd diva = div2(m.kx, m.ky, ax_new, ay_new);
-            zd gauge = (ibdt / (mc.c * mc.c)) * dphi + diva;
-            zd cont = ibdt * drho + m.divj;
-            zd ex = -zi(m.kx * phi_new) - ibdt * dax;
-            zd ey = -zi(m.ky * phi_new) - ibdt * day;
-            zd rs = (1.0 / mc.eps0) * rho_new;
-            zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
-            acc[D_GAUGE] += znorm2(gauge);
-            acc[D_CONT] += znorm2(cont);
-            acc[D_GAUSS] += znorm2(gauss);
-            acc[D_RHO] += znorm2(rs);
-            diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
-            zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
-        }
-        zstore((double2*)bp.rho_new + idx, rho_new);
-        zstore((double2*)bp.phi_new + idx, phi_new);
-        zstore((double2*)bp.ax_new + idx, ax_new);
-        zstore((double2*)bp.ay_new + idx, ay_new);
-        store_outputs(mc, f4, idx, m.kx, m.ky, phi_new, ax_new, ay_new);
-    }
-    if (mc.diag) reduce_diag(acc, diag);
+__device__ __forceinline__ zd hload(const void* p, int idx) {
+    return zload(reinterpret_cast<const double2*>(p) + idx);
+}
+__device__ __forceinline__ void hstore(void* p, int idx, zd v) {
+    zstore(reinterpret_cast<double2*>(p) + idx, v);
 }
 
+// ---------------------------------------------------------------- BDF-k ----
+
 template <typename C>
-__global__ void __launch_bounds__(kModeThreads)
-k_mode_cdf2(ModeCommon mc, CdfParams cp, const C* __restrict__ z, C* __restrict__ f4,
-            C* __restrict__ epk, double* __restrict__ diag) {
-    const int nmodes = mc.nx * mc.ny;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[D_NSLOTS];
-#pragma unroll
-    for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
-    if (idx < nmodes) {
-        ModeIn m = mode_in(mc, z, idx);
-        const double dt = mc.dt;
-        const double th = 0.5 * mc.c * mc.c * dt * dt;
-        const double inv = 1.0 / (1.0 + th * m.K);
-        zd phi = zload((const double2*)cp.phi + idx), phi_prev = zload((const double2*)cp.phi_prev + idx);
-        zd rho = zload((const double2*)cp.rho + idx), rho_prev = zload((const double2*)cp.rho_prev + idx);
-        zd ax = zload((const double2*)cp.ax + idx), ax_prev = zload((const double2*)cp.ax_prev + idx);
-        zd ay = zload((const double2*)cp.ay + idx), ay_prev = zload((const double2*)cp.ay_prev + idx);
-        zd jx_prev = zload((const double2*)cp.jx_prev + idx), jy_prev = zload((const double2*)cp.jy_prev + idx);
-        zd rho_new = rho - dt * m.divj;                                    // rho^{n+3/2}
-        zd phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
-        zd ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
-        zd ay_new = inv * (2.0 * ay + (th * mc.mu0) * (m.jy + jy_prev)) - ay_prev;
-        if (mc.diag) {
-            // section 3.1: eps_1^{n+1}, eps_2^{n+1} and Gauss at t^{n+1/2}
-            zd diva = div2(m.kx, m.ky, ax_new, ay_new);
-            zd gauge = (1.0 / (mc.c * mc.c * dt)) * (phi_new - phi) + diva;
-            zd cont = (1.0 / dt) * (rho_new - rho) + m.divj;
-            zd pavg = 0.5 * (phi_new + phi_prev);
-            zd ex = -zi(m.kx * pavg) - (1.0 / dt) * (ax_new - ax);
-            zd ey = -zi(m.ky * pavg) - (1.0 / dt) * (ay_new - ay);
-            zd rs = (0.5 / mc.eps0) * (rho_new + rho_prev);
-            zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
-            acc[D_GAUGE] += znorm2(gauge);
-            acc[D_CONT] += znorm2(cont);
-            acc[D_GAUSS] += znorm2(gauss);
-            acc[D_RHO] += znorm2((1.0 / mc.eps0) * rho_new);
-            diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
-            zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
-        }
-        zstore((double2*)cp.phi_prev + idx, phi_new);
-        zstore((double2*)cp.rho_prev + idx, rho_new);
-        zstore((double2*)cp.ax_prev + idx, ax_new);
-        zstore((double2*)cp.ay_prev + idx, ay_new);
-        zstore((double2*)cp.jx_prev + idx, m.jx);
-        zstore((double2*)cp.jy_prev + idx, m.jy);
-        store_outputs(mc, f4, idx, m.kx, m.ky, 0.5 * (phi_new + phi), ax_new, ay_new);
+__device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParams& bp,
+                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+    const int idx = m.idx, k = bp.k;
+    zd rho_new = -bp.bdt * m.divj;
+    for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * hload(bp.rho[d - 1], idx);
+    rho_new = (1.0 / bp.a[0]) * rho_new;
+    const double inv = 1.0 / (bp.C[0] + bp.g * m.K);
+    zd sphi = (bp.g / mc.eps0) * rho_new;
+    zd sax = (bp.g * mc.mu0) * m.jx;
+    zd say = (bp.g * mc.mu0) * m.jy;
+    for (int d = 1; d <= 2 * k; ++d) {
+        sphi = sphi - bp.C[d] * hload(bp.phi[d - 1], idx);
+        sax = sax - bp.C[d] * hload(bp.ax[d - 1], idx);
+        say = say - bp.C[d] * hload(bp.ay[d - 1], idx);
     }
-    if (mc.diag) reduce_diag(acc, diag);
+    const zd phi_new = inv * sphi, ax_new = inv * sax, ay_new = inv * say;
+    if (mc.diag) {
+        // section 3.2: gauge eps_1, continuity eps_2, and Gauss with
+        // E^{n+1} = -grad phi^{n+1} - (1/(beta dt)) sum_j a_j A^{n+1-j}
+        zd dphi = bp.a[0] * phi_new, dax = bp.a[0] * ax_new, day = bp.a[0] * ay_new;
+        zd drho = bp.a[0] * rho_new;
+        for (int d = 1; d <= k; ++d) {
+            dphi = dphi + bp.a[d] * hload(bp.phi[d - 1], idx);
+            dax = dax + bp.a[d] * hload(bp.ax[d - 1], idx);
+            day = day + bp.a[d] * hload(bp.ay[d - 1], idx);
+            drho = drho + bp.a[d] * hload(bp.rho[d - 1], idx);
+        }
+        const double ibdt = 1.0 / bp.bdt;
+        const zd diva = div2(m.kx, m.ky, ax_new, ay_new);
+        const zd gauge = (ibdt / (mc.c * mc.c)) * dphi + diva;
+        const zd cont = ibdt * drho + m.divj;
+        const zd ex = -zi(m.kx * phi_new) - ibdt * dax;
+        const zd ey = -zi(m.ky * phi_new) - ibdt * day;
+        const zd rs = (1.0 / mc.eps0) * rho_new;
+        const zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
+        acc[D_GAUGE] += znorm2(gauge);
+        acc[D_CONT] += znorm2(cont);
+        acc[D_GAUSS] += znorm2(gauss);
+        acc[D_RHO] += znorm2(rs);
+        diag_fields(acc, m.kx, m.ky, ex, ey, ax_new, ay_new);
+        zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
+    }
+    hstore(bp.rho_new, idx, rho_new);
+    hstore(bp.phi_new, idx, phi_new);
+    hstore(bp.ax_new, idx, ax_new);
+    hstore(bp.ay_new, idx, ay_new);
+    packed_outputs(mc, m, phi_new, ax_new, ay_new, out);
 }
+
+// ---------------------------------------------------------------- CDF-2 ----
+
+template <typename C>
+__device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParams& cp,
+                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+    const int idx = m.idx;
+    const double dt = mc.dt;
+    const double th = 0.5 * mc.c * mc.c * dt * dt;
+    const double inv = 1.0 / (1.0 + th * m.K);
+    const zd phi = hload(cp.phi, idx), phi_prev = hload(cp.phi_prev, idx);
+    const zd rho = hload(cp.rho, idx), rho_prev = hload(cp.rho_prev, idx);
+    const zd ax = hload(cp.ax, idx), ax_prev = hload(cp.ax_prev, idx);
+    const zd ay = hload(cp.ay, idx), ay_prev = hload(cp.ay_prev, idx);
+    const zd jx_prev = hload(cp.jx_prev, idx), jy_prev = hload(cp.jy_prev, idx);
+    const zd rho_new = rho - dt * m.divj;  // rho^{n+3/2}
+    const zd phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
+    const zd ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
+    const zd ay_new = inv * (2.0 * ay + (th * mc.mu0) * (m.jy + jy_prev)) - ay_prev;
+    if (mc.diag) {
+        // section 3.1: eps_1^{n+1}, eps_2^{n+1} and Gauss at t^{n+1/2}
+        const zd diva = div2(m.kx, m.ky, ax_new, ay_new);
+        const zd gauge = (1.0 / (mc.c * mc.c * dt)) * (phi_new - phi) + diva;
+        const zd cont = (1.0 / dt) * (rho_new - rho) + m.divj;
+        const zd pavg = 0.5 * (phi_new + phi_prev);
+        const zd ex = -zi(m.kx * pavg) - (1.0 / dt) * (ax_new - ax);
+        const zd ey = -zi(m.ky * pavg) - (1.0 / dt) * (ay_new - ay);
+        const zd rs = (0.5 / mc.eps0) * (rho_new + rho_prev);
+        const zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
+        acc[D_GAUGE] += znorm2(gauge);
+        acc[D_CONT] += znorm2(cont);
+        acc[D_GAUSS] += znorm2(gauss);
+        acc[D_RHO] += znorm2((1.0 / mc.eps0) * rho_new);
+        diag_fields(acc, m.kx, m.ky, ex, ey, ax_new, ay_new);
+        zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
+    }
+    hstore(cp.phi_prev, idx, phi_new);
+    hstore(cp.rho_prev, idx, rho_new);
+    hstore(cp.ax_prev, idx, ax_new);
+    hstore(cp.ay_prev, idx, ay_new);
+    hstore(cp.jx_prev, idx, m.jx);
+    hstore(cp.jy_prev, idx, m.jy);
+    packed_outputs(mc, m, 0.5 * (phi_new + phi), ax_new, ay_new, out);
+}
+
+// ---------------------------------------------------------------- DIRK-s ---
 
 // One s-stage DIRK step of d/dt (v, u) = (c^2 (S - K u), v) for one mode (section 3.3.1).
 __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double c, double h,
@@ -227,10 +230,10 @@ __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double
             ub = ub + (h * dp.a[i * kMaxDirk + j]) * ku[j];
             vb = vb + (h * dp.a[i * kMaxDirk + j]) * kv[j];
         }
-        zd src = (1.0 - dp.c[i]) * sn + dp.c[i] * snew;
+        const zd src = (1.0 - dp.c[i]) * sn + dp.c[i] * snew;
         const double gam = h * dp.a[i * kMaxDirk + i];
         const double d = 1.0 / (1.0 + (gam * c) * (gam * c) * K);
-        zd force = c2 * (src - K * ub);
+        const zd force = c2 * (src - K * ub);
         ku[i] = d * (vb + gam * force);
         kv[i] = d * (force - (gam * c2 * K) * vb);
     }
@@ -241,61 +244,124 @@ __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double
 }
 
 template <typename C>
+__device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkParams& dp,
+                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+    const int idx = m.idx;
+    const double h = mc.dt;
+    const zd phi = hload(dp.phi, idx), vphi = hload(dp.vphi, idx);
+    const zd ax = hload(dp.ax, idx), vax = hload(dp.vax, idx);
+    const zd ay = hload(dp.ay, idx), vay = hload(dp.vay, idx);
+    const zd rho = hload(dp.rho, idx);
+    const zd jxn = hload(dp.jx, idx), jyn = hload(dp.jy, idx);
+    const zd divjn = div2(m.kx, m.ky, jxn, jyn);
+    zd rho_new = rho;
+    for (int i = 0; i < dp.s; ++i)
+        rho_new = rho_new - (h * dp.b[i]) * ((1.0 - dp.c[i]) * divjn + dp.c[i] * m.divj);
+    zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
+    const double ie = 1.0 / mc.eps0;
+    dirk_mode(dp, m.K, mc.c, h, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
+    dirk_mode(dp, m.K, mc.c, h, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
+    dirk_mode(dp, m.K, mc.c, h, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
+    if (mc.diag) {
+        // section 3.3.2: eps_1, eps_2 and eps_3; Gauss with E = -grad phi - v_A (reported only)
+        const double c2h = mc.c * mc.c * h;
+        const zd diva_n = div2(m.kx, m.ky, ax, ay), diva = div2(m.kx, m.ky, ax_new, ay_new);
+        const zd divva_n = div2(m.kx, m.ky, vax, vay), divva = div2(m.kx, m.ky, vax_new, vay_new);
+        const zd gauge = -(phi_new - phi) - c2h * (dp.r0 * diva_n + dp.r1 * diva);
+        const zd gauge_dt = -(vphi_new - vphi) - c2h * (dp.r0 * divva_n + dp.r1 * divva);
+        const zd cont = -(rho_new - rho) - h * (dp.r0 * divjn + dp.r1 * m.divj);
+        const zd ex = -zi(m.kx * phi_new) - vax_new;
+        const zd ey = -zi(m.ky * phi_new) - vay_new;
+        const zd rs = ie * rho_new;
+        const zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
+        acc[D_GAUGE] += znorm2(gauge);
+        acc[D_GAUGE_DT] += znorm2(gauge_dt);
+        acc[D_CONT] += znorm2(cont);
+        acc[D_GAUSS] += znorm2(gauss);
+        acc[D_RHO] += znorm2(rs);
+        diag_fields(acc, m.kx, m.ky, ex, ey, ax_new, ay_new);
+        zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
+    }
+    hstore(dp.phi, idx, phi_new);
+    hstore(dp.vphi, idx, vphi_new);
+    hstore(dp.ax, idx, ax_new);
+    hstore(dp.vax, idx, vax_new);
+    hstore(dp.ay, idx, ay_new);
+    hstore(dp.vay, idx, vay_new);
+    hstore(dp.rho, idx, rho_new);
+    hstore(dp.jx, idx, m.jx);
+    hstore(dp.jy, idx, m.jy);
+    packed_outputs(mc, m, phi_new, ax_new, ay_new, out);
+}
+
+// ------------------------------------------------------------- drivers -----
+
+// One thread per mode over the transformed current spectrum z.
+template <typename C, typename Params>
 __global__ void __launch_bounds__(kModeThreads)
-k_mode_dirk(ModeCommon mc, DirkParams dp, const C* __restrict__ z, C* __restrict__ f4,
-            C* __restrict__ epk, double* __restrict__ diag) {
+k_mode(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
+       C* __restrict__ epk, double* __restrict__ diag) {
     const int nmodes = mc.nx * mc.ny;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[D_NSLOTS];
 #pragma unroll
     for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
     if (idx < nmodes) {
-        ModeIn m = mode_in(mc, z, idx);
-        const double h = mc.dt;
-        zd phi = zload((const double2*)dp.phi + idx), vphi = zload((const double2*)dp.vphi + idx);
-        zd ax = zload((const double2*)dp.ax + idx), vax = zload((const double2*)dp.vax + idx);
-        zd ay = zload((const double2*)dp.ay + idx), vay = zload((const double2*)dp.vay + idx);
-        zd rho = zload((const double2*)dp.rho + idx);
-        zd jxn = zload((const double2*)dp.jx + idx), jyn = zload((const double2*)dp.jy + idx);
-        zd divjn = div2(m.kx, m.ky, jxn, jyn);
-        zd rho_new = rho;
-        for (int i = 0; i < dp.s; ++i)
-            rho_new = rho_new - (h * dp.b[i]) * ((1.0 - dp.c[i]) * divjn + dp.c[i] * m.divj);
-        zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
-        const double ie = 1.0 / mc.eps0;
-        dirk_mode(dp, m.K, mc.c, h, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
-        dirk_mode(dp, m.K, mc.c, h, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
-        dirk_mode(dp, m.K, mc.c, h, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
-        if (mc.diag) {
-            // section 3.3.2: eps_1, eps_2 and eps_3; Gauss with E = -grad phi - v_A (reported only)
-            const double c2h = mc.c * mc.c * h;
-            zd diva_n = div2(m.kx, m.ky, ax, ay), diva = div2(m.kx, m.ky, ax_new, ay_new);
-            zd divva_n = div2(m.kx, m.ky, vax, vay), divva = div2(m.kx, m.ky, vax_new, vay_new);
-            zd gauge = -(phi_new - phi) - c2h * (dp.r0 * diva_n + dp.r1 * diva);
-            zd gauge_dt = -(vphi_new - vphi) - c2h * (dp.r0 * divva_n + dp.r1 * divva);
-            zd cont = -(rho_new - rho) - h * (dp.r0 * divjn + dp.r1 * m.divj);
-            zd ex = -zi(m.kx * phi_new) - vax_new;
-            zd ey = -zi(m.ky * phi_new) - vay_new;
-            zd rs = ie * rho_new;
-            zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
-            acc[D_GAUGE] += znorm2(gauge);
-            acc[D_GAUGE_DT] += znorm2(gauge_dt);
-            acc[D_CONT] += znorm2(cont);
-            acc[D_GAUSS] += znorm2(gauss);
-            acc[D_RHO] += znorm2(rs);
-            diag_fields(acc, mc, m.kx, m.ky, ex, ey, ax_new, ay_new);
-            zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
-        }
-        zstore((double2*)dp.phi + idx, phi_new);
-        zstore((double2*)dp.vphi + idx, vphi_new);
-        zstore((double2*)dp.ax + idx, ax_new);
-        zstore((double2*)dp.vax + idx, vax_new);
-        zstore((double2*)dp.ay + idx, ay_new);
-        zstore((double2*)dp.vay + idx, vay_new);
-        zstore((double2*)dp.rho + idx, rho_new);
-        zstore((double2*)dp.jx + idx, m.jx);
-        zstore((double2*)dp.jy + idx, m.jy);
-        store_outputs(mc, f4, idx, m.kx, m.ky, phi_new, ax_new, ay_new);
+        const ModeIn m = mode_from_global(mc, z, idx);
+        zd out[4];
+        mode_update(mc, prm, m, acc, epk, out);
+        const size_t N = (size_t)nmodes;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) zstore(f4 + f * N + idx, out[f]);
+    }
+    if (mc.diag) reduce_diag(acc, diag);
+}
+
+// Fused column pass.  CTA b owns the column pair (j, ny - j), j = b (j = 0 and j = ny/2
+// are their own partners): the partner -k of every mode of one column is in the other.
+// It loads the pair from the row-transformed current, transforms along x, updates every
+// mode of both columns, and transforms the four packed outputs of both columns back
+// along x, all in shared memory; the caller finishes with the inverse transform along y.
+template <typename C, typename Params>
+__global__ void __launch_bounds__(kModeThreads)
+k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
+                C* __restrict__ epk, double* __restrict__ diag, FftDesc fd,
+                const C* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = mc.nx, ny = mc.ny;
+    const int j = blockIdx.x;
+    const int jp = (j == 0) ? 0 : ny - j;
+    const int ncols = (jp == j) ? 1 : 2;
+    C* bufA = reinterpret_cast<C*>(smem_raw);  // 8 lines of nx
+    C* bufB = bufA + 8 * nx;                   // 8 lines of nx
+    for (int t = threadIdx.x; t < ncols * nx; t += blockDim.x) {
+        const int c = t / nx, i = t - c * nx;
+        bufA[t] = z[(size_t)i * ny + (c ? jp : j)];
+    }
+    __syncthreads();
+    C* zc = run_passes(bufA, bufB, fd, ncols, tw, -1);  // forward along x
+    C* out = (zc == bufA) ? bufB : bufA;               // the other buffer
+    double acc[D_NSLOTS];
+#pragma unroll
+    for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
+    for (int t = threadIdx.x; t < ncols * nx; t += blockDim.x) {
+        const int c = t / nx, i = t - c * nx;
+        const int cp = (ncols == 1) ? 0 : 1 - c;
+        const int ip = (i == 0) ? 0 : nx - i;
+        const ModeIn m = make_mode(mc, i, c ? jp : j, zload(zc + c * nx + i),
+                                   zload(zc + cp * nx + ip));
+        zd o[4];
+        mode_update(mc, prm, m, acc, epk, o);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) zstore(out + (f * ncols + c) * nx + i, o[f]);
+    }
+    __syncthreads();
+    C* res = run_passes(out, zc, fd, 4 * ncols, tw, +1);  // inverse along x
+    const size_t N = (size_t)nx * ny;
+    for (int t = threadIdx.x; t < 4 * ncols * nx; t += blockDim.x) {
+        const int l = t / nx, i = t - l * nx;
+        const int f = l / ncols, c = l - f * ncols;
+        f4[f * N + (size_t)i * ny + (c ? jp : j)] = res[t];
     }
     if (mc.diag) reduce_diag(acc, diag);
 }
@@ -308,12 +374,12 @@ k_mode_init(ModeCommon mc, const C* __restrict__ zq, double2* __restrict__ rho_o
             double2* __restrict__ phi_out, C* __restrict__ epk) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= mc.nx * mc.ny) return;
-    ModeIn m = mode_in(mc, zq, idx);
-    zd rho = (m.K > 0.0) ? m.jx : zd{0.0, 0.0};
-    zd phi = (m.K > 0.0) ? (1.0 / (mc.eps0 * m.K)) * rho : zd{0.0, 0.0};
+    const ModeIn m = mode_from_global(mc, zq, idx);
+    const zd rho = (m.K > 0.0) ? m.jx : zd{0.0, 0.0};
+    const zd phi = (m.K > 0.0) ? (1.0 / (mc.eps0 * m.K)) * rho : zd{0.0, 0.0};
     zstore(rho_out + idx, rho);
     zstore(phi_out + idx, phi);
-    zd ex = -zi(m.kx * phi), ey = -zi(m.ky * phi);
+    const zd ex = -zi(m.kx * phi), ey = -zi(m.ky * phi);
     zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
 }
 
@@ -324,12 +390,12 @@ k_mode_pack2(ModeCommon mc, const double2* __restrict__ a, const double2* __rest
              C* __restrict__ out) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= mc.nx * mc.ny) return;
-    zd va = a ? zload(a + idx) : zd{0, 0};
-    zd vb = b ? zload(b + idx) : zd{0, 0};
+    const zd va = a ? zload(a + idx) : zd{0, 0};
+    const zd vb = b ? zload(b + idx) : zd{0, 0};
     zd r;
     if (op == 1) {
-        int i = idx / mc.ny, j = idx - i * mc.ny;
-        double kx = wavenumber(i, mc.nx, mc.kx_scale), ky = wavenumber(j, mc.ny, mc.ky_scale);
+        const int i = idx / mc.ny, j = idx - i * mc.ny;
+        const double kx = wavenumber(i, mc.nx, mc.kx_scale), ky = wavenumber(j, mc.ny, mc.ky_scale);
         r = zi(kx * vb) - zi(ky * va);
     } else {
         r = va + zi(vb);
@@ -341,41 +407,72 @@ inline int mode_blocks(const ModeCommon& mc) {
     return (mc.nx * mc.ny + kModeThreads - 1) / kModeThreads;
 }
 
+template <typename C, typename Params>
+cudaError_t launch_mode_generic(const ModeCommon& mc, const Params& prm, const void* z, void* f4,
+                                void* e, double* diag, cudaStream_t s) {
+    k_mode<C, Params><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, prm, (const C*)z, (C*)f4,
+                                                               (C*)e, diag);
+    return cudaGetLastError();
+}
+
+template <typename C, typename Params>
+cudaError_t launch_columns_generic(const ModeCommon& mc, const Params& prm, const void* z,
+                                   void* f4, void* e, double* diag, const FftDesc& fd,
+                                   const void* tw, cudaStream_t s) {
+    const size_t smem = field_columns_smem(mc.nx, sizeof(C));
+    if (smem > kFieldColumnsSmemMax) return cudaErrorInvalidValue;
+    auto kern = k_field_columns<C, Params>;
+    if (smem > 48 * 1024) {
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem);
+        if (e2 != cudaSuccess) return e2;
+    }
+    kern<<<mc.ny / 2 + 1, kModeThreads, smem, s>>>(mc, prm, (const C*)z, (C*)f4, (C*)e, diag, fd,
+                                                   (const C*)tw);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_mode_bdf(const ModeCommon& mc, const BdfParams& bp, const void* z, void* f4,
                             void* e, double* diag, cudaStream_t s) {
-    using C = cplx_t<T>;
-    k_mode_bdf<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, bp, (const C*)z, (C*)f4, (C*)e, diag);
-    return cudaGetLastError();
+    return launch_mode_generic<cplx_t<T>>(mc, bp, z, f4, e, diag, s);
 }
 template <typename T>
 cudaError_t launch_mode_cdf2(const ModeCommon& mc, const CdfParams& cp, const void* z, void* f4,
                              void* e, double* diag, cudaStream_t s) {
-    using C = cplx_t<T>;
-    k_mode_cdf2<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, cp, (const C*)z, (C*)f4, (C*)e, diag);
-    return cudaGetLastError();
+    return launch_mode_generic<cplx_t<T>>(mc, cp, z, f4, e, diag, s);
 }
 template <typename T>
 cudaError_t launch_mode_dirk(const ModeCommon& mc, const DirkParams& dp, const void* z, void* f4,
                              void* e, double* diag, cudaStream_t s) {
+    return launch_mode_generic<cplx_t<T>>(mc, dp, z, f4, e, diag, s);
+}
+template <typename T>
+cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams& bp,
+                                 const CdfParams& cp, const DirkParams& dp, const void* z,
+                                 void* f4, void* e, double* diag, const FftDesc& fd,
+                                 const void* tw, cudaStream_t s) {
     using C = cplx_t<T>;
-    k_mode_dirk<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, dp, (const C*)z, (C*)f4, (C*)e, diag);
-    return cudaGetLastError();
+    if (kind == K_BDF) return launch_columns_generic<C>(mc, bp, z, f4, e, diag, fd, tw, s);
+    if (kind == K_CDF2) return launch_columns_generic<C>(mc, cp, z, f4, e, diag, fd, tw, s);
+    return launch_columns_generic<C>(mc, dp, z, f4, e, diag, fd, tw, s);
 }
 template <typename T>
 cudaError_t launch_mode_init(const ModeCommon& mc, const void* zq, void* rho, void* phi, void* e,
                              cudaStream_t s) {
     using C = cplx_t<T>;
-    k_mode_init<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const C*)zq, (double2*)rho, (double2*)phi, (C*)e);
+    k_mode_init<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const C*)zq, (double2*)rho,
+                                                            (double2*)phi, (C*)e);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,
                               void* out, cudaStream_t s) {
     using C = cplx_t<T>;
-    k_mode_pack2<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const double2*)a, (const double2*)b, op, (C*)out);
+    k_mode_pack2<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, (const double2*)a,
+                                                             (const double2*)b, op, (C*)out);
     return cudaGetLastError();
 }
 
@@ -386,6 +483,10 @@ cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b
                                              void*, void*, double*, cudaStream_t);                \
     template cudaError_t launch_mode_dirk<T>(const ModeCommon&, const DirkParams&, const void*,   \
                                              void*, void*, double*, cudaStream_t);                \
+    template cudaError_t launch_field_columns<T>(const ModeCommon&, int, const BdfParams&,        \
+                                                 const CdfParams&, const DirkParams&, const void*, \
+                                                 void*, void*, double*, const FftDesc&,           \
+                                                 const void*, cudaStream_t);                      \
     template cudaError_t launch_mode_init<T>(const ModeCommon&, const void*, void*, void*, void*, \
                                              cudaStream_t);                                       \
     template cudaError_t launch_mode_pack2<T>(const ModeCommon&, const void*, const void*, int,  \

@@ -30,6 +30,23 @@ inline int blocks_for(int64_t n) {
     return (int)b;
 }
 
+// The eight gather fields of one node ([node][4] complex, 32 B in FP32, 64 B in FP64) with
+// 16-byte loads.
+__device__ __forceinline__ void load_node(const float2* node, float* g) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(node));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(node) + 1);
+    g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
+    g[4] = b.x; g[5] = b.y; g[6] = b.z; g[7] = b.w;
+}
+__device__ __forceinline__ void load_node(const double2* node, double* g) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double2 v = __ldg(node + k);
+        g[2 * k] = v.x;
+        g[2 * k + 1] = v.y;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ bool in_domain(T xi, int n) {
     return xi >= (T)0 && xi <= (T)n;
@@ -51,20 +68,44 @@ struct AccF64 {
     }
 };
 
+// Round-to-nearest-even integer of a float with |x| < 2^22, without a conversion
+// instruction: adding 1.5 * 2^23 leaves the rounded integer in the low mantissa bits.
+__device__ __forceinline__ int round_small(float x) {
+    return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
 struct AccFix {
     longlong2* J;
     float scale;
-    __device__ __forceinline__ static unsigned long long q(float v, float s) {
-        return (unsigned long long)__float2ll_rn(v * s);
+    // round(v * scale), the contribution in units of the quantum 1/scale (set-up only:
+    // the float-to-int64 conversion runs on the FP64 pipe)
+    __device__ __forceinline__ static long long q(float v, float s) {
+        return __float2ll_rn(__fmul_rn(v, s));
+    }
+    // The same integer round(v * scale) as hi * 2^19 + lo with FP32 and integer operations
+    // only, for |v * scale| < 2^38: t = v * scale, hi = floor(t / 2^19) (exact),
+    // lo = round(t - hi 2^19) with t - hi 2^19 in [0, 2^19] exact.  hi 2^19 is an even
+    // integer, so rounding t - hi 2^19 to nearest even gives round(t) - hi 2^19.
+    __device__ __forceinline__ static void split(float v, float s, int& hi, int& lo) {
+        const float t = __fmul_rn(v, s);
+        const float hf = floorf(__fmul_rn(t, 1.0f / 524288.0f));
+        hi = round_small(hf);
+        lo = round_small(__fmaf_rn(-hf, 524288.0f, t));
+    }
+    __device__ __forceinline__ static unsigned long long join(int hi, int lo) {
+        return (unsigned long long)((long long)hi * 524288ll + (long long)lo);
     }
     template <typename T>
     __device__ __forceinline__ void add(size_t node, T a, T b) const {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), q((float)a, scale));
-        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].y), q((float)b, scale));
+        int ha, la, hb, lb;
+        split((float)a, scale, ha, la);
+        split((float)b, scale, hb, lb);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), join(ha, la));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].y), join(hb, lb));
     }
     template <typename T>
     __device__ __forceinline__ void add1(size_t node, T a) const {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), q((float)a, scale));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), (unsigned long long)q((float)a, scale));
     }
 };
 
@@ -76,11 +117,11 @@ k_move_deposit(ParticleGeom g, T* __restrict__ x, T* __restrict__ y, const T* __
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const T vxi = vx[p], vyi = vy[p];
-        T xp = wrap_pos(x[p] + vxi * dt, lx);
-        T yp = wrap_pos(y[p] + vyi * dt, ly);
+        T xp = move_pos(x[p], vxi, dt, lx);
+        T yp = move_pos(y[p], vyi, dt, ly);
         x[p] = xp;
         y[p] = yp;
-        const T xi = xp * idx_, yj = yp * idy;
+        const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
         if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
@@ -91,12 +132,12 @@ k_move_deposit(ParticleGeom g, T* __restrict__ x, T* __restrict__ y, const T* __
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const int gi = wrap_idx(ix + a, g.nx);
-            const T tx = vxi * wx[a], ty = vyi * wx[a];
+            const T tx = rmul(vxi, wx[a]), ty = rmul(vyi, wx[a]);
             const size_t row = (size_t)gi * g.ny;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                acc.add(row + gj, tx * wy[b], ty * wy[b]);
+                acc.add(row + gj, rmul(tx, wy[b]), rmul(ty, wy[b]));
             }
         }
     }
@@ -109,7 +150,7 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
     const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const T xi = x[p] * idx_, yj = y[p] * idy;
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
         if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
@@ -123,10 +164,120 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                acc.add1((size_t)gi * g.ny + gj, wx[a] * wy[b]);
+                acc.add1((size_t)gi * g.ny + gj, rmul(wx[a], wy[b]));
             }
         }
     }
+}
+
+
+// Move + deposit over particles sorted by tile (see sort.cu), FP32 form.  CTA b owns
+// particles [b*chunk, (b+1)*chunk); for each run of particles of one tile it accumulates
+// the fixed-point contributions into a shared-memory copy of that tile's node region (the
+// tile plus a halo) and adds the region to the global grid once.
+//
+// Shared atomics are native for 32-bit integers, so each contribution q is split exactly
+// as q = hi * 2^19 + lo with lo in [0, 2^19] and |hi| <= 2^(k-19) <= 2^19 (the quantum is
+// 2^-k c with k <= 38, see pic_api.cu; AccFix::split), and hi and lo are summed apart.
+// A node receives at most one contribution per particle and a CTA at most kDepositChunk
+// particles, so both 32-bit sums stay within 2^30 + 2^11.  The flush recombines them.
+// A node outside the region (a particle that drifted further than the halo since the
+// last sort) goes straight to the global grid.  Integer sums make the result independent
+// of the order of the particles.
+constexpr int kDepositChunk = 2048;
+constexpr int kLoBits = 19;
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_move_deposit_tiled(ParticleGeom g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
+                     const T* __restrict__ vx, const T* __restrict__ vy, int64_t n,
+                     const int* __restrict__ keys, const int* __restrict__ off, AccFix acc,
+                     unsigned int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // four int arrays of R words (lo_x, lo_y, hi_x, hi_y): a node's word k sits in bank
+    // k mod 32, so lanes hitting different nodes rarely share a bank
+    const int R = tg.rx * tg.ry;
+    int* lo_x = reinterpret_cast<int*>(smem_raw);
+    int* lo_y = lo_x + R;
+    int* hi_x = lo_y + R;
+    int* hi_y = hi_x + R;
+    const int64_t c0 = (int64_t)blockIdx.x * kDepositChunk;
+    if (c0 >= n) return;
+    const int64_t c1 = c0 + kDepositChunk < n ? c0 + kDepositChunk : n;
+    const T dt = (T)g.dt, lx = (T)g.lx, ly = (T)g.ly, idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
+    unsigned bad = 0;
+    int64_t p0 = c0;
+    while (p0 < c1) {
+        const int key = keys[p0];
+        const int64_t tend = (int64_t)off[key + 1];
+        const int64_t seg_end = tend < c1 ? tend : c1;
+        const int tx = key / tg.nty, ty = key - tx * tg.nty;
+        // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
+        // [0, 2n), so one correction wraps each exactly (whatever the halo)
+        int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
+        if (bi < 0) bi += g.nx;
+        if (bj < 0) bj += g.ny;
+        for (int k = threadIdx.x; k < 4 * R; k += blockDim.x) lo_x[k] = 0;
+        __syncthreads();
+        for (int64_t p = p0 + threadIdx.x; p < seg_end; p += blockDim.x) {
+            const T vxi = vx[p], vyi = vy[p];
+            T xp = move_pos(x[p], vxi, dt, lx);
+            T yp = move_pos(y[p], vyi, dt, ly);
+            x[p] = xp;
+            y[p] = yp;
+            const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
+            if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+                bad |= ERR_NONFINITE;
+                continue;
+            }
+            T wx[P + 1], wy[P + 1];
+            const int ix = Shape<P, T>::weights(xi, wx);
+            const int iy = Shape<P, T>::weights(yj, wy);
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+                const int gi = wrap_idx(ix + a, g.nx);
+                int ri = gi - bi;
+                if (ri < 0) ri += g.nx;
+                const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const int gj = wrap_idx(iy + b, g.ny);
+                    int rj = gj - bj;
+                    if (rj < 0) rj += g.ny;
+                    const T cx = rmul(tx_, wy[b]), cy = rmul(ty_, wy[b]);
+                    if (ri < tg.rx && rj < tg.ry) {
+                        int hx, lx2, hy, ly2;
+                        AccFix::split((float)cx, acc.scale, hx, lx2);
+                        AccFix::split((float)cy, acc.scale, hy, ly2);
+                        const int k = ri * tg.ry + rj;
+                        atomicAdd(lo_x + k, lx2);
+                        atomicAdd(lo_y + k, ly2);
+                        atomicAdd(hi_x + k, hx);
+                        atomicAdd(hi_y + k, hy);
+                    } else {
+                        acc.add((size_t)gi * g.ny + gj, cx, cy);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < R; k += blockDim.x) {
+            const int lx_ = lo_x[k], ly_ = lo_y[k], hx = hi_x[k], hy = hi_y[k];
+            if (!(lx_ | ly_ | hx | hy)) continue;
+            const long long sx = (long long)hx * (1ll << kLoBits) + (long long)lx_;
+            const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
+            const int ri = k / tg.ry, rj = k - ri * tg.ry;
+            int gi = bi + ri, gj = bj + rj;
+            if (gi >= g.nx) gi -= g.nx;
+            if (gj >= g.ny) gj -= g.ny;
+            const size_t node = (size_t)gi * g.ny + gj;
+            if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
+            if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
+        }
+        __syncthreads();
+        p0 = seg_end;
+    }
+    if (bad) atomicOr(err, bad);
 }
 
 // Fixed-point (Jx, Jy) sums to complex storage values, times `unscale`.
@@ -164,7 +315,7 @@ k_gather_push(ParticleGeom g, PushParams pp, const T* __restrict__ x, const T* _
     unsigned bad = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const T xi = x[p] * idx_, yj = y[p] * idy;
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
         if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
             bad |= ERR_NONFINITE;
             continue;
@@ -182,15 +333,16 @@ k_gather_push(ParticleGeom g, PushParams pp, const T* __restrict__ x, const T* _
                 const int gj = wrap_idx(iy + b, g.ny);
                 const T w = wx[a] * wy[b];
                 const C* node = row + (size_t)gj * 4;
-                const C g0 = node[0], g1 = node[1], g2 = node[2], g3 = node[3];
-                f0 += w * g0.x;  // dphi/dx
-                f1 += w * g0.y;  // dphi/dy
-                f2 += w * g1.x;  // Ax
-                f3 += w * g1.y;  // Ay
-                f4 += w * g2.x;  // dAx/dx
-                f5 += w * g2.y;  // dAx/dy
-                f6 += w * g3.x;  // dAy/dx
-                f7 += w * g3.y;  // dAy/dy
+                T g[8];
+                load_node(node, g);  // dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy
+                f0 += w * g[0];
+                f1 += w * g[1];
+                f2 += w * g[2];
+                f3 += w * g[3];
+                f4 += w * g[4];
+                f5 += w * g[5];
+                f6 += w * g[6];
+                f7 += w * g[7];
             }
         }
         const T vxn = vx[p], vyn = vy[p];
@@ -229,7 +381,7 @@ k_init_particles(ParticleGeom g, PushParams pp, T* __restrict__ x, T* __restrict
     const double c2 = pp.c * pp.c;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const T xi = x[p] * idx_, yj = y[p] * idy;
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
         const double vxn = (double)vx[p], vyn = (double)vy[p];
         const double v2 = vxn * vxn + vyn * vyn;
         if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !(v2 < c2)) {
@@ -352,6 +504,38 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
     return cudaGetLastError();
 }
 
+
+template <typename T>
+cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
+                                      T* y, const T* vx, const T* vy, int64_t n, const int* keys,
+                                      const int* off, void* j, bool fix, float scale,
+                                      unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (!fix) return cudaErrorInvalidValue;  // the tiled pass is the fixed-point form's
+    const int blocks = (int)((n + kDepositChunk - 1) / kDepositChunk);
+    const size_t smem = (size_t)tg.rx * tg.ry * 4 * sizeof(int);
+    if (smem > 96 * 1024) return cudaErrorInvalidValue;
+    AccFix acc{(longlong2*)j, scale};
+    cudaError_t e = cudaSuccess;
+#define GPIC_TILED(PP)                                                                             \
+    {                                                                                              \
+        auto kern = k_move_deposit_tiled<T, PP>;                                                   \
+        if (smem > 48 * 1024)                                                                      \
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess)                                                                      \
+            kern<<<blocks, kThreads, smem, s>>>(g, tg, x, y, vx, vy, n, keys, off, acc, err);    \
+    }
+    switch (p) {
+        case 2: GPIC_TILED(2) break;
+        case 3: GPIC_TILED(3) break;
+        case 4: GPIC_TILED(4) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPIC_TILED
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,
                                cudaStream_t s) {
@@ -444,7 +628,11 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                       const T*, int64_t, longlong2*, float,       \
                                                       unsigned int*, cudaStream_t);               \
     template cudaError_t launch_fix_to_cplx<T>(const longlong2*, double, void*, int64_t,          \
-                                               cudaStream_t);
+                                               cudaStream_t);                                     \
+    template cudaError_t launch_move_deposit_tiled<T>(int, const ParticleGeom&, const TileGeom&,  \
+                                                      T*, T*, const T*, const T*, int64_t,        \
+                                                      const int*, const int*, void*, bool, float, \
+                                                      unsigned int*, cudaStream_t);
 GPIC_INST(double)
 GPIC_INST(float)
 #undef GPIC_INST

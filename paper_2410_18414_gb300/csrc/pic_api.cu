@@ -34,6 +34,13 @@ struct pic_handle {
     void* v[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
     double* stage = nullptr;  // FP64 staging for conversions (n values)
+    // tile sort (sort_interval > 0): second set of particle arrays, original indices, keys
+    bool sorting = false;
+    TileGeom tg{};
+    void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t *id = nullptr, *id_alt = nullptr;
+    int *keys = nullptr, *keys_sorted = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr;
+    int launches_now = 0, launches_last = 0;
     // grid buffers
     double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
     // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
@@ -229,6 +236,19 @@ pic_status alloc_state(pic_handle* h) {
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->v[b][k], pn));
     CK(dalloc(h, (void**)&h->stage, (size_t)std::max<int64_t>(h->n, 1) * sizeof(double)));
+    if (h->sorting) {
+        const size_t ni = (size_t)std::max<int64_t>(h->n, 1) * sizeof(int);
+        for (int a = 0; a < 8; ++a) CK(dalloc(h, &h->alt[a], pn));
+        CK(dalloc(h, (void**)&h->id, ni));
+        CK(dalloc(h, (void**)&h->id_alt, ni));
+        CK(dalloc(h, (void**)&h->keys, ni));
+        CK(dalloc(h, (void**)&h->keys_sorted, ni));
+        const size_t nt = (size_t)h->tg.ntx * h->tg.nty + 1;
+        CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
+        CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
+        CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
+        CK(launch_iota(h->id, h->n, h->s));
+    }
     CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
     CK(dalloc(h, &h->Z, h->ng * cs));
     CK(dalloc(h, &h->F4, 4 * h->ng * cs));
@@ -384,6 +404,26 @@ bool diag_due(const pic_handle* h) {
     return h->diag_every > 0 && ((h->step + 1) % h->diag_every) == 0;
 }
 
+pic_status sort_particles(pic_handle* h) {
+    void** cur[8] = {&h->x, &h->y, &h->px, &h->py, &h->v[0][0], &h->v[0][1], &h->v[1][0], &h->v[1][1]};
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        SortArrays<T> src, dst;
+        for (int a = 0; a < 8; ++a) {
+            src.a[a] = (T*)*cur[a];
+            dst.a[a] = (T*)h->alt[a];
+        }
+        src.id = h->id;
+        dst.id = h->id_alt;
+        return launch_tile_sort<T>(h->tg, src, dst, h->n, h->keys, h->keys_sorted, h->hist, h->off,
+                                   h->cursor, h->s);
+    }));
+    for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
+    std::swap(h->id, h->id_alt);
+    h->launches_now += 3;
+    return PIC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -420,17 +460,46 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
     h->mc.dt = cfg->dt;
     h->geom = ParticleGeom{cfg->nx, cfg->ny, cfg->lx, cfg->ly, 1.0 / dx, 1.0 / dy, cfg->dt};
     h->push = PushParams{cfg->q, cfg->m, cfg->c, cfg->dt, cfg->weight, 0};
+    h->sorting = cfg->sort_interval > 0;
+    if (h->sorting) {
+        // Tiles of t x t cells holding about 4096 particles at the mean density.  Between
+        // two sorts a particle moves at most c dt per step, so a CTA's shared-memory region
+        // is its tile plus a halo of that drift and the stencil reach (capped so the region
+        // stays within 2048 nodes); nodes beyond it fall back to global atomics.
+        TileGeom& tg = h->tg;
+        tg.nx = cfg->nx;
+        tg.ny = cfg->ny;
+        const double ppc = (double)std::max<int64_t>(h->n, 1) / ((double)cfg->nx * cfg->ny);
+        tg.t = 4;
+        while (tg.t < 32 && (double)(2 * tg.t) * (2 * tg.t) * ppc <= 8192.0 &&
+               2 * tg.t <= std::min(cfg->nx, cfg->ny))
+            tg.t *= 2;
+        tg.ntx = (cfg->nx + tg.t - 1) / tg.t;
+        tg.nty = (cfg->ny + tg.t - 1) / tg.t;
+        const double drift = cfg->c * cfg->dt * cfg->sort_interval / std::fmin(dx, dy);
+        tg.halo = (int)std::ceil(drift) + cfg->spline_order / 2 + 2;
+        while (tg.halo > 1 && (tg.t + 2 * tg.halo) * (tg.t + 2 * tg.halo) > 2048) --tg.halo;
+        tg.rx = std::min(tg.t + 2 * tg.halo, cfg->nx);
+        tg.ry = std::min(tg.t + 2 * tg.halo, cfg->ny);
+        tg.inv_dx = 1.0 / dx;
+        tg.inv_dy = 1.0 / dy;
+    }
     if (h->fp32) {
-        // Fixed-point scale 2^k: every contribution is at most |v| W <= c (current) or
-        // W <= 1 (charge), so with k = 62 - ceil(log2 n) no node total can reach 2^62
-        // whatever the particle distribution.
+        // Current quantum c 2^-k with k = min(38, 62 - ceil(log2 n)): a contribution
+        // |v| W_x W_y is below c, i.e. below 2^k quanta, so no int64 node total can reach
+        // 2^62 whatever the distribution, and k <= 38 lets the tiled deposit split each
+        // contribution into two parts that fit 32-bit shared atomics.  At k = 38 the
+        // quantum (3.6e-12 c) is far below the FP32 rounding of a contribution.
+        int kj = 38;
+        if (h->n > 1) kj = std::min(38, 62 - (int)std::ceil(std::log2((double)h->n)));
+        h->fix_scale_j = (float)(std::ldexp(1.0, kj) / cfg->c);
+        h->fix_unscale_j = 1.0 / (double)h->fix_scale_j;
+        // Charge at t = 0 (only the untiled pass): W_x W_y <= 1 with 2^k quanta,
+        // k = 62 - ceil(log2 n), so no node total can reach 2^62.
         int k = 46;
         if (h->n > 1) k = std::min(46, 62 - (int)std::ceil(std::log2((double)h->n)));
-        const double two_k = std::ldexp(1.0, k);
-        h->fix_scale_j = (float)(two_k / cfg->c);
-        h->fix_unscale_j = 1.0 / (double)h->fix_scale_j;
-        h->fix_scale_q = (float)two_k;
-        h->fix_unscale_q = 1.0 / two_k;
+        h->fix_scale_q = (float)std::ldexp(1.0, k);
+        h->fix_unscale_q = std::ldexp(1.0, -k);
     }
     st = alloc_state(h);
     if (st == PIC_OK) st = setup(h, init);
@@ -448,9 +517,20 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
 pic_status pic_deposit(pic_handle* h) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_deposit: the previous step is not finished");
+    h->launches_now = 0;
+    if (h->sorting && h->step % h->cfg.sort_interval == 0) {
+        pic_status st = sort_particles(h);
+        if (st != PIC_OK) return st;
+    }
     CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    h->launches_now += 1;
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
+        if (h->sorting && h->fp32)
+            return launch_move_deposit_tiled<T>(h->p, h->geom, h->tg, (T*)h->x, (T*)h->y,
+                                                (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
+                                                h->n, h->keys_sorted, h->off, h->J, h->fp32,
+                                                h->fix_scale_j, h->err, h->s);
         if (h->fp32)
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
                                               (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
@@ -469,15 +549,25 @@ pic_status pic_field_solve(pic_handle* h) {
     h->diag_now = diag_due(h);
     h->mc.diag = h->diag_now ? 1 : 0;
     if (h->diag_now) CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
+    const bool fused = field_columns_smem(h->nx, 2 * h->rsz) <= kFieldColumnsSmemMax;
+
+    // forward transform along y (the FP32 form converts the fixed-point sums on load)
     if (h->fp32) {
-        CK(launch_fix_to_cplx<float>((const longlong2*)h->J, h->fix_unscale_j, h->tmp, h->ng, h->s));
-        CK(forward_fft(h, h->tmp, h->Z));
+        CK(launch_fft_y_from_fix<float>((const longlong2*)h->J, h->fix_unscale_j, h->Z, h->nx,
+                                        h->ny, h->fy, h->twy, h->s));
     } else {
-        CK(forward_fft(h, h->J, h->Z));
+        CK(launch_fft_y<double>(h->J, h->Z, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s));
     }
+    if (!fused) CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        return launch_fft_x<T>(h->Z, h->Z, h->nx, h->ny, 1, h->fx, h->twx, -1, h->s);
+    }));
+
+    // per-mode update with the stepper's history levels
     const int st = h->cfg.stepper;
+    BdfParams bp = h->bdf;
+    int nslot = 0, nr = 0;
     if (st == PIC_STEPPER_BDF) {
-        BdfParams bp = h->bdf;
         const int k = bp.k;
         for (int d = 1; d <= 2 * k; ++d) {
             const int slot = ((h->head - (d - 1)) % h->L + h->L) % h->L;
@@ -486,35 +576,45 @@ pic_status pic_field_solve(pic_handle* h) {
             bp.ay[d - 1] = h->ay_l[slot];
         }
         for (int d = 1; d <= k; ++d) bp.rho[d - 1] = h->rho_l[((h->head_r - (d - 1)) % h->Lr + h->Lr) % h->Lr];
-        const int nslot = (h->head + 1) % h->L, nr = (h->head_r + 1) % h->Lr;
+        nslot = (h->head + 1) % h->L;
+        nr = (h->head_r + 1) % h->Lr;
         bp.phi_new = h->phi_l[nslot];
         bp.ax_new = h->ax_l[nslot];
         bp.ay_new = h->ay_l[nslot];
         bp.rho_new = h->rho_l[nr];
-        CK(by_prec(h, [&](auto t) {
-            using T = decltype(t);
-            return launch_mode_bdf<T>(h->mc, bp, h->Z, h->F4, h->E, h->diag, h->s);
-        }));
+    }
+    const int kind = st == PIC_STEPPER_BDF ? K_BDF : (st == PIC_STEPPER_CDF2 ? K_CDF2 : K_DIRK);
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        if (fused)
+            return launch_field_columns<T>(h->mc, kind, bp, h->cdf, h->dirk, h->Z, h->F4, h->E,
+                                           h->diag, h->fx, h->twx, h->s);
+        if (kind == K_BDF) return launch_mode_bdf<T>(h->mc, bp, h->Z, h->F4, h->E, h->diag, h->s);
+        if (kind == K_CDF2) return launch_mode_cdf2<T>(h->mc, h->cdf, h->Z, h->F4, h->E, h->diag, h->s);
+        return launch_mode_dirk<T>(h->mc, h->dirk, h->Z, h->F4, h->E, h->diag, h->s);
+    }));
+    if (st == PIC_STEPPER_BDF) {
         h->head = nslot;
         h->head_r = nr;
     } else if (st == PIC_STEPPER_CDF2) {
-        CK(by_prec(h, [&](auto t) {
-            using T = decltype(t);
-            return launch_mode_cdf2<T>(h->mc, h->cdf, h->Z, h->F4, h->E, h->diag, h->s);
-        }));
         std::swap(h->cdf.phi, h->cdf.phi_prev);
         std::swap(h->cdf.rho, h->cdf.rho_prev);
         std::swap(h->cdf.ax, h->cdf.ax_prev);
         std::swap(h->cdf.ay, h->cdf.ay_prev);
         std::swap(h->cdf.jx, h->cdf.jx_prev);
         std::swap(h->cdf.jy, h->cdf.jy_prev);
-    } else {
-        CK(by_prec(h, [&](auto t) {
-            using T = decltype(t);
-            return launch_mode_dirk<T>(h->mc, h->dirk, h->Z, h->F4, h->E, h->diag, h->s);
-        }));
     }
-    CK(inverse_fft(h, h->F4, h->G, 4));
+
+    // inverse transforms: along x (unless fused above), then along y into the [node][4]
+    // gather layout
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t r = cudaSuccess;
+        if (!fused) r = launch_fft_x<T>(h->F4, h->F4, h->nx, h->ny, 4, h->fx, h->twx, +1, h->s);
+        if (r != cudaSuccess) return r;
+        return launch_fft_y<T>(h->F4, h->G, h->nx, h->ny, 4, h->fy, h->twy, +1, 1, h->s);
+    }));
+    h->launches_now += fused ? 3 : 5;
     h->phase = 2;
     return PIC_OK;
 }
@@ -533,6 +633,8 @@ pic_status pic_gather_push(pic_handle* h) {
                                      h->n, h->G, h->diag, h->err, h->s);
     }));
     h->vcur = vo;
+    h->launches_now += 1;
+    h->launches_last = h->launches_now;
     h->step += 1;
     h->stepped = true;
     h->e_valid = h->diag_now;
@@ -648,6 +750,15 @@ pic_status pic_read_particles(pic_handle* h, double* x, double* y, double* px, d
     const size_t nb = (size_t)h->n * sizeof(double);
     for (int i = 0; i < 8; ++i) {
         if (!dst[i] || h->n == 0) continue;
+        if (h->sorting) {  // restore the order given to pic_init
+            CK(by_prec(h, [&](auto t) {
+                using T = decltype(t);
+                return launch_scatter_by_id<T>((const T*)src[i], h->id, h->stage, h->n, h->s);
+            }));
+            CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            continue;
+        }
         if (h->fp32) {
             CK(launch_convert<float, double>((const float*)src[i], h->stage, h->n, h->s));
             CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
@@ -669,9 +780,15 @@ int64_t pic_step_count(const pic_handle* h) { return h ? h->step : -1; }
 
 int32_t pic_kernels_per_step(const pic_handle* h) {
     if (!h) return 0;
-    // move_deposit, 2 forward FFT passes, per-mode update, 2 inverse FFT passes,
-    // gather_push; the FP32 form adds one conversion kernel.
-    return 7 + (h->fp32 ? 1 : 0);
+    // Kernels the most recent complete step launched: move_deposit, the row transform,
+    // the fused column pass (or column transforms and the per-mode update on grids too
+    // large for it), the inverse row transform, gather_push; a sort step adds its 3
+    // kernels.  Before any step: the count of a step without a sort.
+    if (!h->stepped) {
+        const bool fused = field_columns_smem(h->nx, 2 * h->rsz) <= kFieldColumnsSmemMax;
+        return fused ? 5 : 7;
+    }
+    return h->launches_last;
 }
 
 const char* pic_last_error(const pic_handle* h) {

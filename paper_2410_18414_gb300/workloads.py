@@ -48,7 +48,7 @@ class Workload:
 
     @property
     def weight(self):
-        return self.lx * self.ly / self.n
+        return self.lx * self.ly / max(self.n, 1)
 
 
 def _proper_to_velocity(ux, uy):

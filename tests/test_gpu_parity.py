@@ -231,3 +231,46 @@ def test_device_pointers_accepted(device):
     sim.field("jx", jx)
     assert np.array_equal(jx.cpu().numpy(), sim.field("jx"))
     sim.close()
+
+
+SORT_CASES = [
+    # name, workload, nsteps, sort interval, stepper kwargs
+    ("cloud32_sort1_bdf1", lambda: workloads.drifting_cloud(n=16384, nx=32, ny=32), 8, 1,
+     dict(stepper="bdf", bdf_order=1)),
+    ("weibel96x64_sort4_bdf2_p3", lambda: workloads.weibel(96, 64, 4, 0.5, 0.01, 27, 3, n=24571),
+     9, 4, dict(stepper="bdf", bdf_order=2)),
+    ("weibel16_sort3_dirk2_p4", lambda: workloads.weibel(16, 16, 8, 0.6, 0.02, 28, 4, n=2047), 7, 3,
+     dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG)),
+    # sort interval far beyond the halo: particles leave their tile region (global fallback)
+    ("weibel8x12_sort40_cdf2", lambda: workloads.weibel(8, 12, 6, 0.9, 0.05, 29, 2, n=577), 45,
+     40, dict(stepper="cdf2")),
+    # 0.36 cells per step for 100 steps overruns the 24-cell halo: global fallback path
+    ("weibel128_sort100_beyond_halo", lambda: workloads.weibel(128, 128, 1, 0.9, 0.05, 30, 2,
+                                                              n=2003), 105, 100,
+     dict(stepper="bdf", bdf_order=1)),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps,sort,kw", SORT_CASES, ids=[c[0] for c in SORT_CASES])
+def test_parity_with_tile_sort(device, name, make, nsteps, sort, kw):
+    wl = make()
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                          sort_interval=sort, **kw)
+    sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device)
+    sim.step(nsteps)
+    ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, w=wl.weight, **kw)
+    st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, nsteps)
+    compare(sim, st, wl, fields=("jx", "jy", "rho", "phi", "ax", "ay", "dphidx", "daydy"))
+    sim.close()
+
+
+def test_tile_sort_full_size_weibel_128(device):
+    wl = workloads.weibel_128(stepper="bdf", bdf_order=2)
+    cfg = pic.make_config(128, 128, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf", bdf_order=2,
+                          weight=wl.weight, sort_interval=8)
+    sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device)
+    sim.step(2)
+    st = opic.run(opic.Config(nx=128, ny=128, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=3, stepper="bdf",
+                              bdf_order=2, w=wl.weight), wl.x, wl.y, wl.vx, wl.vy, 2)
+    compare(sim, st, wl, fields=("jx", "jy", "phi", "ax", "dphidx"))
+    sim.close()
