@@ -31,6 +31,12 @@ struct ModeCommon {
     double inv_n;               // 1 / (nx ny): inverse-FFT normalisation folded in
     double eps0, mu0, c, dt;
     int diag;                   // accumulate diagnostics this step
+    // precomputed FP64 tables (pic_init): wavenumbers per axis and the inverse implicit-
+    // solve denominator per mode (BDF: 1/(C_0 + g K); CDF: 1/(1 + th K); DIRK stage i:
+    // invd[i*nx*ny + mode] = 1/(1 + (h a_ii c)^2 K))
+    const double* kxt;
+    const double* kyt;
+    const double* invd;
 };
 
 struct BdfParams {
@@ -103,10 +109,10 @@ template <typename T>
 cudaError_t launch_mode_dirk(const ModeCommon& mc, const DirkParams& dp, const void* z, void* f4,
                              void* e_packed, double* diag, cudaStream_t s);
 // Fused column pass of the field solve (forward transform along x, per-mode update,
-// inverse transforms along x of the four outputs): one CTA per column pair, 16 lines of
-// nx complex values in shared memory.  `kind` is a StepperKind.
+// inverse transforms along x of the four outputs): one CTA per column, 8 lines of nx
+// complex values in shared memory.  `kind` is a StepperKind.
 inline size_t field_columns_smem(int nx, size_t complex_bytes) {
-    return 16 * (size_t)nx * complex_bytes;
+    return 8 * (size_t)nx * complex_bytes;
 }
 constexpr size_t kFieldColumnsSmemMax = 200 * 1024;
 template <typename T>
@@ -114,6 +120,10 @@ cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams
                                  const CdfParams& cp, const DirkParams& dp, const void* z,
                                  void* f4, void* e, double* diag, const FftDesc& fd,
                                  const void* tw, cudaStream_t s);
+// Fill the wavenumber and inverse-denominator tables of mc (kind: StepperKind).
+cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& bp,
+                               const DirkParams& dp, double* kxt, double* kyt, double* invd,
+                               cudaStream_t s);
 // Pack two spectra a + i b (scaled by inv_n) for an inverse transform to two real fields.
 template <typename T>
 cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,
@@ -181,6 +191,10 @@ cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, i
 struct TileGeom {
     int nx, ny, t, ntx, nty, halo, rx, ry;
     double inv_dx, inv_dy;
+    int half;  // 1 for even spline degree: the stencil base cell is floor(x/dx + 1/2)
+    // sort key of a particle: tile-major, then the stencil base cell inside the tile,
+    // key = tile * t * t + (bx mod t) * t + (by mod t); nkeys = ntx * nty * t * t
+    __host__ __device__ int nkeys() const { return ntx * nty * t * t; }
 };
 
 // Particle arrays moved by the sort: x, y, Px, Py, v[0].x, v[0].y, v[1].x, v[1].y, and the

@@ -43,8 +43,8 @@ struct ModeIn {
 __device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, zd za, zd zb) {
     ModeIn m;
     m.idx = i * mc.ny + j;
-    m.kx = wavenumber(i, mc.nx, mc.kx_scale);
-    m.ky = wavenumber(j, mc.ny, mc.ky_scale);
+    m.kx = mc.kxt[i];
+    m.ky = mc.kyt[j];
     m.K = m.kx * m.kx + m.ky * m.ky;
     const zd b = zconj(zb);
     const double hs = 0.5 * mc.jscale;
@@ -128,7 +128,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParam
     zd rho_new = -bp.bdt * m.divj;
     for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * hload(bp.rho[d - 1], idx);
     rho_new = (1.0 / bp.a[0]) * rho_new;
-    const double inv = 1.0 / (bp.C[0] + bp.g * m.K);
+    const double inv = mc.invd[idx];  // 1/(C_0 + g K)
     zd sphi = (bp.g / mc.eps0) * rho_new;
     zd sax = (bp.g * mc.mu0) * m.jx;
     zd say = (bp.g * mc.mu0) * m.jy;
@@ -179,7 +179,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParam
     const int idx = m.idx;
     const double dt = mc.dt;
     const double th = 0.5 * mc.c * mc.c * dt * dt;
-    const double inv = 1.0 / (1.0 + th * m.K);
+    const double inv = mc.invd[idx];  // 1/(1 + th K)
     const zd phi = hload(cp.phi, idx), phi_prev = hload(cp.phi_prev, idx);
     const zd rho = hload(cp.rho, idx), rho_prev = hload(cp.rho_prev, idx);
     const zd ax = hload(cp.ax, idx), ax_prev = hload(cp.ax_prev, idx);
@@ -218,8 +218,10 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParam
 // ---------------------------------------------------------------- DIRK-s ---
 
 // One s-stage DIRK step of d/dt (v, u) = (c^2 (S - K u), v) for one mode (section 3.3.1).
+// dinv[i * stride] = 1/(1 + (h a_ii c)^2 K) for stage i.
 __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double c, double h,
-                                          zd u, zd v, zd sn, zd snew, zd& uo, zd& vo) {
+                                          const double* dinv, size_t stride, zd u, zd v, zd sn,
+                                          zd snew, zd& uo, zd& vo) {
     zd ku[kMaxDirk], kv[kMaxDirk];
     const double c2 = c * c;
     uo = u;
@@ -232,7 +234,7 @@ __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double
         }
         const zd src = (1.0 - dp.c[i]) * sn + dp.c[i] * snew;
         const double gam = h * dp.a[i * kMaxDirk + i];
-        const double d = 1.0 / (1.0 + (gam * c) * (gam * c) * K);
+        const double d = dinv[i * stride];
         const zd force = c2 * (src - K * ub);
         ku[i] = d * (vb + gam * force);
         kv[i] = d * (force - (gam * c2 * K) * vb);
@@ -259,9 +261,11 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkPara
         rho_new = rho_new - (h * dp.b[i]) * ((1.0 - dp.c[i]) * divjn + dp.c[i] * m.divj);
     zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
     const double ie = 1.0 / mc.eps0;
-    dirk_mode(dp, m.K, mc.c, h, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
-    dirk_mode(dp, m.K, mc.c, h, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
-    dirk_mode(dp, m.K, mc.c, h, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
+    const double* dinv = mc.invd + idx;
+    const size_t stride = (size_t)mc.nx * mc.ny;
+    dirk_mode(dp, m.K, mc.c, h, dinv, stride, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
+    dirk_mode(dp, m.K, mc.c, h, dinv, stride, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
+    dirk_mode(dp, m.K, mc.c, h, dinv, stride, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
     if (mc.diag) {
         // section 3.3.2: eps_1, eps_2 and eps_3; Gauss with E = -grad phi - v_A (reported only)
         const double c2h = mc.c * mc.c * h;
@@ -317,11 +321,11 @@ k_mode(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
     if (mc.diag) reduce_diag(acc, diag);
 }
 
-// Fused column pass.  CTA b owns the column pair (j, ny - j), j = b (j = 0 and j = ny/2
-// are their own partners): the partner -k of every mode of one column is in the other.
-// It loads the pair from the row-transformed current, transforms along x, updates every
-// mode of both columns, and transforms the four packed outputs of both columns back
-// along x, all in shared memory; the caller finishes with the inverse transform along y.
+// Fused column pass.  CTA j owns column j (fixed y-index, all x-indices).  The partner
+// -k of a mode of column j lies in column ny - j (mod ny), so the CTA loads both columns
+// from the row-transformed current and transforms both along x, updates the modes of
+// its own column, and transforms that column's four packed outputs back along x, all
+// in shared memory; the caller finishes with the inverse transform along y.
 template <typename C, typename Params>
 __global__ void __launch_bounds__(kModeThreads)
 k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
@@ -331,9 +335,9 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     const int nx = mc.nx, ny = mc.ny;
     const int j = blockIdx.x;
     const int jp = (j == 0) ? 0 : ny - j;
-    const int ncols = (jp == j) ? 1 : 2;
-    C* bufA = reinterpret_cast<C*>(smem_raw);  // 8 lines of nx
-    C* bufB = bufA + 8 * nx;                   // 8 lines of nx
+    const int ncols = (jp == j) ? 1 : 2;  // column j, then its partner column
+    C* bufA = reinterpret_cast<C*>(smem_raw);  // 4 lines of nx
+    C* bufB = bufA + 4 * nx;                   // 4 lines of nx
     for (int t = threadIdx.x; t < ncols * nx; t += blockDim.x) {
         const int c = t / nx, i = t - c * nx;
         bufA[t] = z[(size_t)i * ny + (c ? jp : j)];
@@ -341,29 +345,50 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     __syncthreads();
     C* zc = run_passes(bufA, bufB, fd, ncols, tw, -1);  // forward along x
     C* out = (zc == bufA) ? bufB : bufA;               // the other buffer
+    const C* zp = zc + (ncols - 1) * nx;               // partner column
     double acc[D_NSLOTS];
 #pragma unroll
     for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
-    for (int t = threadIdx.x; t < ncols * nx; t += blockDim.x) {
-        const int c = t / nx, i = t - c * nx;
-        const int cp = (ncols == 1) ? 0 : 1 - c;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = (i == 0) ? 0 : nx - i;
-        const ModeIn m = make_mode(mc, i, c ? jp : j, zload(zc + c * nx + i),
-                                   zload(zc + cp * nx + ip));
+        const ModeIn m = make_mode(mc, i, j, zload(zc + i), zload(zp + ip));
         zd o[4];
         mode_update(mc, prm, m, acc, epk, o);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) zstore(out + (f * ncols + c) * nx + i, o[f]);
+        for (int f = 0; f < 4; ++f) zstore(out + f * nx + i, o[f]);
     }
     __syncthreads();
-    C* res = run_passes(out, zc, fd, 4 * ncols, tw, +1);  // inverse along x
+    C* res = run_passes(out, zc, fd, 4, tw, +1);  // inverse along x
     const size_t N = (size_t)nx * ny;
-    for (int t = threadIdx.x; t < 4 * ncols * nx; t += blockDim.x) {
-        const int l = t / nx, i = t - l * nx;
-        const int f = l / ncols, c = l - f * ncols;
-        f4[f * N + (size_t)i * ny + (c ? jp : j)] = res[t];
+    for (int t = threadIdx.x; t < 4 * nx; t += blockDim.x) {
+        const int f = t / nx, i = t - f * nx;
+        f4[f * N + (size_t)i * ny + j] = res[t];
     }
     if (mc.diag) reduce_diag(acc, diag);
+}
+
+__global__ void k_mode_tables(ModeCommon mc, int kind, BdfParams bp, DirkParams dp,
+                              double* __restrict__ kxt, double* __restrict__ kyt,
+                              double* __restrict__ invd) {
+    const int nmodes = mc.nx * mc.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < mc.nx) kxt[idx] = wavenumber(idx, mc.nx, mc.kx_scale);
+    if (idx < mc.ny) kyt[idx] = wavenumber(idx, mc.ny, mc.ky_scale);
+    if (idx >= nmodes) return;
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const double kx = wavenumber(i, mc.nx, mc.kx_scale), ky = wavenumber(j, mc.ny, mc.ky_scale);
+    const double K = kx * kx + ky * ky;
+    if (kind == K_BDF) {
+        invd[idx] = 1.0 / (bp.C[0] + bp.g * K);
+    } else if (kind == K_CDF2) {
+        const double th = 0.5 * mc.c * mc.c * mc.dt * mc.dt;
+        invd[idx] = 1.0 / (1.0 + th * K);
+    } else {
+        for (int st = 0; st < dp.s; ++st) {
+            const double gc = mc.dt * dp.a[st * kMaxDirk + st] * mc.c;
+            invd[(size_t)st * nmodes + idx] = 1.0 / (1.0 + gc * gc * K);
+        }
+    }
 }
 
 // t = 0: rho^0 (deposited charge, K = 0 modes removed), phi^0 from Poisson, and the
@@ -427,8 +452,8 @@ cudaError_t launch_columns_generic(const ModeCommon& mc, const Params& prm, cons
                                               (int)smem);
         if (e2 != cudaSuccess) return e2;
     }
-    kern<<<mc.ny / 2 + 1, kModeThreads, smem, s>>>(mc, prm, (const C*)z, (C*)f4, (C*)e, diag, fd,
-                                                   (const C*)tw);
+    kern<<<mc.ny, kModeThreads, smem, s>>>(mc, prm, (const C*)z, (C*)f4, (C*)e, diag, fd,
+                                           (const C*)tw);
     return cudaGetLastError();
 }
 
@@ -459,6 +484,15 @@ cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams
     if (kind == K_CDF2) return launch_columns_generic<C>(mc, cp, z, f4, e, diag, fd, tw, s);
     return launch_columns_generic<C>(mc, dp, z, f4, e, diag, fd, tw, s);
 }
+cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& bp,
+                               const DirkParams& dp, double* kxt, double* kyt, double* invd,
+                               cudaStream_t s) {
+    const int n = mc.nx * mc.ny > mc.nx ? mc.nx * mc.ny : mc.nx;
+    k_mode_tables<<<(n + kModeThreads - 1) / kModeThreads, kModeThreads, 0, s>>>(
+        mc, kind, bp, dp, kxt, kyt, invd);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mode_init(const ModeCommon& mc, const void* zq, void* rho, void* phi, void* e,
                              cudaStream_t s) {

@@ -22,6 +22,30 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Geometry and push constants in the storage precision, converted once on the host so
+// the per-thread set-up of the FP32 kernels issues no FP64 conversions (GB300 has little
+// FP64 throughput).
+template <typename T>
+struct GeomT {
+    int nx, ny;
+    T lx, ly, inv_dx, inv_dy, dt;
+};
+template <typename T>
+GeomT<T> typed(const ParticleGeom& g) {
+    return GeomT<T>{g.nx, g.ny, (T)g.lx, (T)g.ly, (T)g.inv_dx, (T)g.inv_dy, (T)g.dt};
+}
+template <typename T>
+struct PushT {
+    T q, qdt, c2, mc2;
+    double c, m, weight;  // FP64 kinetic-energy diagnostic
+    int diag;
+};
+template <typename T>
+PushT<T> typed(const PushParams& pp) {
+    return PushT<T>{(T)pp.q, (T)(pp.q * pp.dt), (T)(pp.c * pp.c), (T)(pp.m * pp.c * pp.c),
+                    pp.c, pp.m, pp.weight, pp.diag};
+}
+
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     const int64_t cap = 152 * 16;
@@ -111,9 +135,9 @@ struct AccFix {
 
 template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
-k_move_deposit(ParticleGeom g, T* __restrict__ x, T* __restrict__ y, const T* __restrict__ vx,
+k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __restrict__ vx,
                const T* __restrict__ vy, int64_t n, Acc acc, unsigned int* __restrict__ err) {
-    const T dt = (T)g.dt, lx = (T)g.lx, ly = (T)g.ly, idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
+    const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const T vxi = vx[p], vyi = vy[p];
@@ -187,9 +211,18 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 constexpr int kDepositChunk = 2048;
 constexpr int kLoBits = 19;
 
+__device__ __forceinline__ int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
-k_move_deposit_tiled(ParticleGeom g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
+k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
                      const T* __restrict__ vx, const T* __restrict__ vy, int64_t n,
                      const int* __restrict__ keys, const int* __restrict__ off, AccFix acc,
                      unsigned int* __restrict__ err) {
@@ -204,25 +237,46 @@ k_move_deposit_tiled(ParticleGeom g, TileGeom tg, T* __restrict__ x, T* __restri
     const int64_t c0 = (int64_t)blockIdx.x * kDepositChunk;
     if (c0 >= n) return;
     const int64_t c1 = c0 + kDepositChunk < n ? c0 + kDepositChunk : n;
-    const T dt = (T)g.dt, lx = (T)g.lx, ly = (T)g.ly, idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
+    const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
+    const int tt = tg.t * tg.t;
+    __shared__ int64_t stride_sh;
     unsigned bad = 0;
     int64_t p0 = c0;
     while (p0 < c1) {
-        const int key = keys[p0];
-        const int64_t tend = (int64_t)off[key + 1];
+        const int tile = keys[p0] / tt;
+        const int64_t tend = (int64_t)off[(tile + 1) * tt];
         const int64_t seg_end = tend < c1 ? tend : c1;
-        const int tx = key / tg.nty, ty = key - tx * tg.nty;
+        const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
         // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
         // [0, 2n), so one correction wraps each exactly (whatever the halo)
         int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
         if (bi < 0) bi += g.nx;
         if (bj < 0) bj += g.ny;
+        // Walk the segment in a stride permutation pos = j s mod L (gcd(s, L) = 1,
+        // s ~ L/32): the particles are stored by cell, so consecutive positions share
+        // nodes, while the 32 lanes of a warp then sit in ~32 different cells and their
+        // shared atomics rarely hit the same word.
+        const int64_t L = seg_end - p0;
+        if (threadIdx.x == 0) {
+            int64_t st = L / 32;
+            st |= 1;
+            while (gcd64(st, L) != 1) st += 2;
+            stride_sh = st;
+        }
         for (int k = threadIdx.x; k < 4 * R; k += blockDim.x) lo_x[k] = 0;
         __syncthreads();
-        for (int64_t p = p0 + threadIdx.x; p < seg_end; p += blockDim.x) {
+        const int64_t st = stride_sh;
+        const int64_t step = (int64_t)((unsigned long long)blockDim.x * (unsigned long long)st %
+                                       (unsigned long long)L);
+        int64_t pos = (int64_t)((unsigned long long)threadIdx.x * (unsigned long long)st %
+                                (unsigned long long)L);
+        for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
+            const int64_t p = p0 + pos;
+            pos += step;
+            if (pos >= L) pos -= L;
             const T vxi = vx[p], vyi = vy[p];
-            T xp = move_pos(x[p], vxi, dt, lx);
-            T yp = move_pos(y[p], vyi, dt, ly);
+            const T xp = move_pos(x[p], vxi, dt, lx);
+            const T yp = move_pos(y[p], vyi, dt, ly);
             x[p] = xp;
             y[p] = yp;
             const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
@@ -302,15 +356,14 @@ __global__ void k_extract_fix(const longlong2* __restrict__ J, int comp, double 
 
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
-k_gather_push(ParticleGeom g, PushParams pp, const T* __restrict__ x, const T* __restrict__ y,
+k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restrict__ y,
               T* __restrict__ px, T* __restrict__ py, const T* __restrict__ vx,
               const T* __restrict__ vy, T* __restrict__ vxo, T* __restrict__ vyo, int64_t n,
               const cplx_t<T>* __restrict__ F, double* __restrict__ diag,
               unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
-    const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
-    const T q = (T)pp.q, qdt = (T)(pp.q * pp.dt), c2 = (T)(pp.c * pp.c);
-    const T mc2 = (T)(pp.m * pp.c * pp.c);
+    const T idx_ = g.inv_dx, idy = g.inv_dy;
+    const T q = pp.q, qdt = pp.qdt, c2 = pp.c2, mc2 = pp.mc2;
     double kin = 0.0;
     unsigned bad = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
@@ -474,7 +527,7 @@ cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const 
                                 const T* vy, int64_t n, double2* j, unsigned int* err,
                                 cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_move_deposit, AccF64, g, x, y, vx, vy, n, AccF64{j}, err)
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccF64, typed<T>(g), x, y, vx, vy, n, AccF64{j}, err)
     return cudaGetLastError();
 }
 
@@ -491,7 +544,8 @@ cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, co
                                     const T* vy, int64_t n, longlong2* j, float scale,
                                     unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, g, x, y, vx, vy, n, (AccFix{j, scale}), err)
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, typed<T>(g), x, y, vx, vy, n, (AccFix{j, scale}),
+                     err)
     return cudaGetLastError();
 }
 
@@ -523,7 +577,8 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
         if (smem > 48 * 1024)                                                                      \
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e == cudaSuccess)                                                                      \
-            kern<<<blocks, kThreads, smem, s>>>(g, tg, x, y, vx, vy, n, keys, off, acc, err);    \
+            kern<<<blocks, kThreads, smem, s>>>(typed<T>(g), tg, x, y, vx, vy, n, keys, off, acc, \
+                                                err);                                           \
     }
     switch (p) {
         case 2: GPIC_TILED(2) break;
@@ -555,7 +610,7 @@ cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& p
                                T* vyo, int64_t n, const void* f, double* diag, unsigned int* err,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_P(p, k_gather_push, g, pp, x, y, px, py, vx, vy, vxo, vyo, n,
+    GPIC_DISPATCH_P(p, k_gather_push, typed<T>(g), typed<T>(pp), x, y, px, py, vx, vy, vxo, vyo, n,
                     (const cplx_t<T>*)f, diag, err)
     return cudaGetLastError();
 }

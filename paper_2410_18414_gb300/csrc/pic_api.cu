@@ -243,7 +243,7 @@ pic_status alloc_state(pic_handle* h) {
         CK(dalloc(h, (void**)&h->id_alt, ni));
         CK(dalloc(h, (void**)&h->keys, ni));
         CK(dalloc(h, (void**)&h->keys_sorted, ni));
-        const size_t nt = (size_t)h->tg.ntx * h->tg.nty + 1;
+        const size_t nt = (size_t)h->tg.nkeys() + 1;
         CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
@@ -259,6 +259,16 @@ pic_status alloc_state(pic_handle* h) {
     CK(dalloc(h, &h->twx, (size_t)c.nx * cs));
     CK(dalloc(h, &h->twy, (size_t)c.ny * cs));
     CK(dalloc(h, (void**)&h->diag, D_NSLOTS * sizeof(double)));
+    {
+        const int stages = c.stepper == PIC_STEPPER_DIRK ? c.dirk_stages : 1;
+        double *kxt = nullptr, *kyt = nullptr, *invd = nullptr;
+        CK(dalloc(h, (void**)&kxt, (size_t)c.nx * sizeof(double)));
+        CK(dalloc(h, (void**)&kyt, (size_t)c.ny * sizeof(double)));
+        CK(dalloc(h, (void**)&invd, (size_t)stages * h->ng * sizeof(double)));
+        h->mc.kxt = kxt;
+        h->mc.kyt = kyt;
+        h->mc.invd = invd;
+    }
     CK(dalloc(h, (void**)&h->err, sizeof(unsigned int)));
     CK(cudaMemsetAsync(h->err, 0, sizeof(unsigned int), h->s));
     CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
@@ -325,6 +335,11 @@ pic_status alloc_state(pic_handle* h) {
         }
         h->dirk.r0 = r0;
         h->dirk.r1 = r1;
+    }
+    {
+        const int kind = c.stepper == PIC_STEPPER_BDF ? K_BDF : (c.stepper == PIC_STEPPER_CDF2 ? K_CDF2 : K_DIRK);
+        CK(launch_mode_tables(h->mc, kind, h->bdf, h->dirk, const_cast<double*>(h->mc.kxt),
+                              const_cast<double*>(h->mc.kyt), const_cast<double*>(h->mc.invd), h->s));
     }
     return PIC_OK;
 }
@@ -483,6 +498,7 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         tg.ry = std::min(tg.t + 2 * tg.halo, cfg->ny);
         tg.inv_dx = 1.0 / dx;
         tg.inv_dy = 1.0 / dy;
+        tg.half = (cfg->spline_order % 2 == 0) ? 1 : 0;
     }
     if (h->fp32) {
         // Current quantum c 2^-k with k = min(38, 62 - ceil(log2 n)): a contribution

@@ -1,7 +1,8 @@
-// Counting sort of the particles by tile (every sort_interval steps).
+// Counting sort of the particles by tile and cell (every sort_interval steps).
 //
-// The domain is cut into tiles of T x T cells; a particle's key is the tile of its
-// current cell.  Three kernels: a histogram of keys (shared-memory privatised), one
+// The domain is cut into tiles of T x T cells; a particle's key is its stencil base
+// cell, numbered tile by tile, so the particles of one tile are contiguous and, inside
+// it, those of one cell are.  Three kernels: a histogram of keys (shared-memory privatised), one
 // single-CTA exclusive scan giving each tile's first slot, and a scatter that moves all
 // particle arrays (and the particle's original index) to the slots of its tile.  The
 // scatter order inside a tile is not fixed; nothing depends on it: the FP32 form sums the
@@ -39,13 +40,20 @@ __device__ __forceinline__ int warp_aggregated_claim(int* counter_base, int key)
     return key >= 0 ? start + rank : -1;
 }
 
+// Stencil base cell of a position (floor(x/dx) for odd spline degree, floor(x/dx + 1/2)
+// for even degree: particles with equal base cells share all their stencil nodes),
+// wrapped into the grid, then the tile-major key of that cell.
 template <typename T>
 __device__ __forceinline__ int tile_key(T x, T y, const TileGeom& tg) {
-    int ix = (int)floor(rmul(x, (T)tg.inv_dx));  // in the storage precision: FP32 keys
-    int iy = (int)floor(rmul(y, (T)tg.inv_dy));  // stay off the FP64 pipe
-    ix = ix < 0 ? 0 : (ix >= tg.nx ? tg.nx - 1 : ix);
-    iy = iy < 0 ? 0 : (iy >= tg.ny ? tg.ny - 1 : iy);
-    return (ix / tg.t) * tg.nty + iy / tg.t;
+    const T h = tg.half ? (T)0.5 : (T)0;
+    int bx = (int)floor(radd(rmul(x, (T)tg.inv_dx), h));  // in the storage precision: FP32
+    int by = (int)floor(radd(rmul(y, (T)tg.inv_dy), h));  // keys stay off the FP64 pipe
+    bx = bx < 0 ? 0 : (bx >= tg.nx ? bx - tg.nx : bx);
+    by = by < 0 ? 0 : (by >= tg.ny ? by - tg.ny : by);
+    bx = bx >= tg.nx ? tg.nx - 1 : bx;
+    by = by >= tg.ny ? tg.ny - 1 : by;
+    const int tx = bx / tg.t, ty = by / tg.t;
+    return ((tx * tg.nty + ty) * tg.t + (bx - tx * tg.t)) * tg.t + (by - ty * tg.t);
 }
 
 template <typename T>
@@ -53,7 +61,7 @@ __global__ void __launch_bounds__(kThreads)
 k_tile_hist(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             int* __restrict__ keys, int* __restrict__ hist) {
     extern __shared__ int sh[];
-    const int ntiles = tg.ntx * tg.nty;
+    const int ntiles = tg.nkeys();
     const bool priv = ntiles <= kSmemHistMax;
     if (priv) {
         for (int i = threadIdx.x; i < ntiles; i += blockDim.x) sh[i] = 0;
@@ -170,7 +178,7 @@ template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int* keys, int* keys_out, int* hist, int* off, int* cursor,
                              cudaStream_t s) {
-    const int ntiles = tg.ntx * tg.nty;
+    const int ntiles = tg.nkeys();  // number of sort keys (cells, tile-major)
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ntiles, s);
     if (e != cudaSuccess || n == 0) {
         if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, sizeof(int) * (ntiles + 1), s);
