@@ -190,6 +190,7 @@ cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, i
 // before its tile's first node (wrapping periodically).
 struct TileGeom {
     int nx, ny, t, ntx, nty, halo, rx, ry;
+    int pitch;  // shared-memory row pitch of the region (>= ry, = t mod 32)
     double inv_dx, inv_dy;
     int half;  // 1 for even spline degree: the stencil base cell is floor(x/dx + 1/2)
     // sort key of a particle: tile-major, then the stencil base cell inside the tile,
@@ -205,9 +206,10 @@ struct SortArrays {
     int32_t* id;
 };
 
+int sort_scan_chunks(int nkeys);  // chunk totals the scan keeps (size of its bsum array)
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
-                             int* keys, int* keys_out, int* hist, int* off, int* cursor,
+                             int* keys, int* hist, int* off, int* cursor, int* bsum,
                              cudaStream_t s);
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 
@@ -216,9 +218,9 @@ cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 // fixed-point accumulation (J is longlong2) with `scale`, else FP64 (J is double2).
 template <typename T>
 cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const T* vx, const T* vy, int64_t n, const int* keys,
-                                      const int* off, void* j, bool fix, float scale,
-                                      unsigned int* err, cudaStream_t s);
+                                      T* y, const T* vx, const T* vy, int64_t n, const int* off,
+                                      void* j, bool fix, float scale, unsigned int* err,
+                                      cudaStream_t s);
 
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };

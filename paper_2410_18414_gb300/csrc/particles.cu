@@ -92,29 +92,30 @@ struct AccF64 {
     }
 };
 
-// Round-to-nearest-even integer of a float with |x| < 2^22, without a conversion
-// instruction: adding 1.5 * 2^23 leaves the rounded integer in the low mantissa bits.
-__device__ __forceinline__ int round_small(float x) {
-    return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
-}
-
 struct AccFix {
     longlong2* J;
-    float scale;
-    // round(v * scale), the contribution in units of the quantum 1/scale (set-up only:
-    // the float-to-int64 conversion runs on the FP64 pipe)
+    float scale;     // 1 / quantum, a power of two
+    float s_hi;      // scale 2^-19
+    float neg_step;  // -2^19 / scale
+    static AccFix make(void* j, float scale) {
+        return AccFix{(longlong2*)j, scale, scale * (1.0f / 524288.0f), -524288.0f / scale};
+    }
+    // round(v * scale), the contribution in units of the quantum (set-up only: the
+    // float-to-int64 conversion runs on the FP64 pipe)
     __device__ __forceinline__ static long long q(float v, float s) {
         return __float2ll_rn(__fmul_rn(v, s));
     }
-    // The same integer round(v * scale) as hi * 2^19 + lo with FP32 and integer operations
-    // only, for |v * scale| < 2^38: t = v * scale, hi = floor(t / 2^19) (exact),
-    // lo = round(t - hi 2^19) with t - hi 2^19 in [0, 2^19] exact.  hi 2^19 is an even
-    // integer, so rounding t - hi 2^19 to nearest even gives round(t) - hi 2^19.
-    __device__ __forceinline__ static void split(float v, float s, int& hi, int& lo) {
-        const float t = __fmul_rn(v, s);
-        const float hf = floorf(__fmul_rn(t, 1.0f / 524288.0f));
-        hi = round_small(hf);
-        lo = round_small(__fmaf_rn(-hf, 524288.0f, t));
+    // The same integer round(v * scale) as hi * 2^19 + lo with |hi| <= 2^19 and
+    // |lo| <= 2^18, by FP32 and integer operations only, for |v * scale| <= 2^38:
+    //   hi = rne(v scale 2^-19)   -- fma with 1.5 * 2^23 leaves it in the low mantissa bits
+    //   d  = v - hi 2^19 / scale  -- exact (a power-of-two scale, |d scale| <= 2^18)
+    //   lo = rne(d scale)         -- the same trick, d scale is exact
+    // hi 2^19 is even, so rne(v scale - hi 2^19) = rne(v scale) - hi 2^19.
+    __device__ __forceinline__ void split(float v, int& hi, int& lo) const {
+        const float m1 = __fmaf_rn(v, s_hi, 12582912.0f);
+        hi = __float_as_int(m1) - 0x4B400000;
+        const float d = __fmaf_rn(__fsub_rn(m1, 12582912.0f), neg_step, v);
+        lo = __float_as_int(__fmaf_rn(d, scale, 12582912.0f)) - 0x4B400000;
     }
     __device__ __forceinline__ static unsigned long long join(int hi, int lo) {
         return (unsigned long long)((long long)hi * 524288ll + (long long)lo);
@@ -122,8 +123,8 @@ struct AccFix {
     template <typename T>
     __device__ __forceinline__ void add(size_t node, T a, T b) const {
         int ha, la, hb, lb;
-        split((float)a, scale, ha, la);
-        split((float)b, scale, hb, lb);
+        split((float)a, ha, la);
+        split((float)b, hb, lb);
         atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), join(ha, la));
         atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].y), join(hb, lb));
     }
@@ -195,85 +196,77 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 }
 
 
-// Move + deposit over particles sorted by tile (see sort.cu), FP32 form.  CTA b owns
-// particles [b*chunk, (b+1)*chunk); for each run of particles of one tile it accumulates
-// the fixed-point contributions into a shared-memory copy of that tile's node region (the
-// tile plus a halo) and adds the region to the global grid once.
+// Move + deposit over particles sorted by tile and cell (see sort.cu), FP32 form.
 //
-// Shared atomics are native for 32-bit integers, so each contribution q is split exactly
-// as q = hi * 2^19 + lo with lo in [0, 2^19] and |hi| <= 2^(k-19) <= 2^19 (the quantum is
-// 2^-k c with k <= 38, see pic_api.cu; AccFix::split), and hi and lo are summed apart.
-// A node receives at most one contribution per particle and a CTA at most kDepositChunk
-// particles, so both 32-bit sums stay within 2^30 + 2^11.  The flush recombines them.
-// A node outside the region (a particle that drifted further than the halo since the
-// last sort) goes straight to the global grid.  Integer sums make the result independent
-// of the order of the particles.
-constexpr int kDepositChunk = 2048;
+// CTA (tile, split) deposits the particles of one tile into a shared-memory copy of the
+// tile's node region (the tile plus a halo, rows of `pitch` words) and adds the region
+// to the global grid.  Traversal: thread tid serves local cell c = tid mod t^2 and phase
+// f = tid div t^2 and takes, one per round, the particles f, f + F, f + 2F, ... of the
+// CTA's share of that cell (F = threads per cell).  The 32 lanes of a warp thus work on 32
+// consecutive local cells -- a block of 32/t x t cells -- and the row pitch is = t
+// (mod 32), so for each stencil offset their nodes fall in 32 different banks while the
+// particles sit in their sorted cells.
+//
+// Shared atomics are native for 32-bit integers, so each contribution is split exactly
+// into hi * 2^19 + lo (AccFix::split) and the parts are summed apart.  The region is
+// flushed to the global grid every kFlushRounds rounds: a round adds at most one
+// contribution per thread to a node, so between flushes a 32-bit sum holds at most
+// kFlushRounds * 256 = 2^11 terms of magnitude <= 2^19 (< 2^31).  A particle whose
+// stencil leaves the region (it drifted further than the halo) adds the nodes outside
+// straight to the global grid.  Integer sums make the result independent of the order
+// of the particles.
+constexpr int kFlushRounds = 8;
 constexpr int kLoBits = 19;
-
-__device__ __forceinline__ int64_t gcd64(int64_t a, int64_t b) {
-    while (b) {
-        const int64_t t = a % b;
-        a = b;
-        b = t;
-    }
-    return a;
-}
+constexpr int kRegionCap = 2560;  // largest region (rx * pitch words), 40 KB for four arrays
 
 template <typename T, int P>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
 k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
-                     const T* __restrict__ vx, const T* __restrict__ vy, int64_t n,
-                     const int* __restrict__ keys, const int* __restrict__ off, AccFix acc,
+                     const T* __restrict__ vx, const T* __restrict__ vy,
+                     const int* __restrict__ off, int nsplit, AccFix acc,
                      unsigned int* __restrict__ err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // four int arrays of R words (lo_x, lo_y, hi_x, hi_y): a node's word k sits in bank
-    // k mod 32, so lanes hitting different nodes rarely share a bank
-    const int R = tg.rx * tg.ry;
-    int* lo_x = reinterpret_cast<int*>(smem_raw);
-    int* lo_y = lo_x + R;
-    int* hi_x = lo_y + R;
-    int* hi_y = hi_x + R;
-    const int64_t c0 = (int64_t)blockIdx.x * kDepositChunk;
-    if (c0 >= n) return;
-    const int64_t c1 = c0 + kDepositChunk < n ? c0 + kDepositChunk : n;
-    const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
+    // four arrays of R = rx * pitch words: lo_x, lo_y, hi_x, hi_y (sized to the region,
+    // so that the rest of the L1 caches the scattered particle loads)
+    extern __shared__ int sacc[];
+    __shared__ int max_rounds;
+    const int pitch = tg.pitch;
+    const int R = tg.rx * pitch;
     const int tt = tg.t * tg.t;
-    __shared__ int64_t stride_sh;
+    const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+    const int cell = threadIdx.x % tt;
+    const int phases = blockDim.x / tt;   // threads per cell in this CTA
+    const int phase = threadIdx.x / tt;
+    const int key = tile * tt + cell;
+    const int o0 = off[key], count = off[key + 1] - o0;
+    // split s takes the contiguous share [s count / nsplit, (s+1) count / nsplit) of the
+    // cell, so the particles of one 32-byte sector are read by one CTA
+    const int lo_ = (int)((int64_t)count * split / nsplit);
+    const int hi_ = (int)((int64_t)count * (split + 1) / nsplit);
+    const int64_t cbeg = (int64_t)o0 + lo_ + phase;
+    const int streams = phases;
+    const int len = hi_ - lo_;
+    const int mine = len > phase ? (len - phase + phases - 1) / phases : 0;
+    if (threadIdx.x == 0) max_rounds = 0;
+    for (int k = threadIdx.x; k < R; k += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sacc[q * R + k] = 0;
+    }
+    __syncthreads();
+    atomicMax(&max_rounds, mine);
+    __syncthreads();
+    const int rounds = max_rounds;
+    if (rounds == 0) return;  // empty tile (uniform for the CTA)
+    const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
+    // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
+    // [0, 2n), so one correction wraps each exactly (whatever the halo)
+    int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
+    if (bi < 0) bi += g.nx;
+    if (bj < 0) bj += g.ny;
+    const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
     unsigned bad = 0;
-    int64_t p0 = c0;
-    while (p0 < c1) {
-        const int tile = keys[p0] / tt;
-        const int64_t tend = (int64_t)off[(tile + 1) * tt];
-        const int64_t seg_end = tend < c1 ? tend : c1;
-        const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
-        // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
-        // [0, 2n), so one correction wraps each exactly (whatever the halo)
-        int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
-        if (bi < 0) bi += g.nx;
-        if (bj < 0) bj += g.ny;
-        // Walk the segment in a stride permutation pos = j s mod L (gcd(s, L) = 1,
-        // s ~ L/32): the particles are stored by cell, so consecutive positions share
-        // nodes, while the 32 lanes of a warp then sit in ~32 different cells and their
-        // shared atomics rarely hit the same word.
-        const int64_t L = seg_end - p0;
-        if (threadIdx.x == 0) {
-            int64_t st = L / 32;
-            st |= 1;
-            while (gcd64(st, L) != 1) st += 2;
-            stride_sh = st;
-        }
-        for (int k = threadIdx.x; k < 4 * R; k += blockDim.x) lo_x[k] = 0;
-        __syncthreads();
-        const int64_t st = stride_sh;
-        const int64_t step = (int64_t)((unsigned long long)blockDim.x * (unsigned long long)st %
-                                       (unsigned long long)L);
-        int64_t pos = (int64_t)((unsigned long long)threadIdx.x * (unsigned long long)st %
-                                (unsigned long long)L);
-        for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
-            const int64_t p = p0 + pos;
-            pos += step;
-            if (pos >= L) pos -= L;
+    for (int r = 0; r < rounds; ++r) {
+        if (r < mine) {
+            const int64_t p = cbeg + (int64_t)r * streams;
             const T vxi = vx[p], vyi = vy[p];
             const T xp = move_pos(x[p], vxi, dt, lx);
             const T yp = move_pos(y[p], vyi, dt, ly);
@@ -282,54 +275,80 @@ k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__
             const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
             if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
                 bad |= ERR_NONFINITE;
-                continue;
-            }
-            T wx[P + 1], wy[P + 1];
-            const int ix = Shape<P, T>::weights(xi, wx);
-            const int iy = Shape<P, T>::weights(yj, wy);
+            } else {
+                T wx[P + 1], wy[P + 1];
+                const int ix = wrap_idx(Shape<P, T>::weights(xi, wx), g.nx);
+                const int iy = wrap_idx(Shape<P, T>::weights(yj, wy), g.ny);
+                int ri0 = ix - bi, rj0 = iy - bj;
+                if (ri0 < 0) ri0 += g.nx;
+                if (rj0 < 0) rj0 += g.ny;
+                if (ri0 + P < tg.rx && rj0 + P < tg.ry) {
+                    // whole stencil in the region: rows ri0.., columns rj0.. (no wrap)
+                    int* row = sacc + ri0 * pitch + rj0;
 #pragma unroll
-            for (int a = 0; a <= P; ++a) {
-                const int gi = wrap_idx(ix + a, g.nx);
-                int ri = gi - bi;
-                if (ri < 0) ri += g.nx;
-                const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
+                    for (int a = 0; a <= P; ++a) {
+                        const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
 #pragma unroll
-                for (int b = 0; b <= P; ++b) {
-                    const int gj = wrap_idx(iy + b, g.ny);
-                    int rj = gj - bj;
-                    if (rj < 0) rj += g.ny;
-                    const T cx = rmul(tx_, wy[b]), cy = rmul(ty_, wy[b]);
-                    if (ri < tg.rx && rj < tg.ry) {
-                        int hx, lx2, hy, ly2;
-                        AccFix::split((float)cx, acc.scale, hx, lx2);
-                        AccFix::split((float)cy, acc.scale, hy, ly2);
-                        const int k = ri * tg.ry + rj;
-                        atomicAdd(lo_x + k, lx2);
-                        atomicAdd(lo_y + k, ly2);
-                        atomicAdd(hi_x + k, hx);
-                        atomicAdd(hi_y + k, hy);
-                    } else {
-                        acc.add((size_t)gi * g.ny + gj, cx, cy);
+                        for (int b = 0; b <= P; ++b) {
+                            int hx, lx2, hy, ly2;
+                            acc.split((float)rmul(tx_, wy[b]), hx, lx2);
+                            acc.split((float)rmul(ty_, wy[b]), hy, ly2);
+                            atomicAdd(row + b, lx2);
+                            atomicAdd(row + R + b, ly2);
+                            atomicAdd(row + 2 * R + b, hx);
+                            atomicAdd(row + 3 * R + b, hy);
+                        }
+                        row += pitch;
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a <= P; ++a) {
+                        const int gi = wrap_idx(ix + a, g.nx);
+                        int ri = gi - bi;
+                        if (ri < 0) ri += g.nx;
+                        const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
+#pragma unroll
+                        for (int b = 0; b <= P; ++b) {
+                            const int gj = wrap_idx(iy + b, g.ny);
+                            int rj = gj - bj;
+                            if (rj < 0) rj += g.ny;
+                            const T cx = rmul(tx_, wy[b]), cy = rmul(ty_, wy[b]);
+                            if (ri < tg.rx && rj < tg.ry) {
+                                int hx, lx2, hy, ly2;
+                                acc.split((float)cx, hx, lx2);
+                                acc.split((float)cy, hy, ly2);
+                                int* c = sacc + ri * pitch + rj;
+                                atomicAdd(c, lx2);
+                                atomicAdd(c + R, ly2);
+                                atomicAdd(c + 2 * R, hx);
+                                atomicAdd(c + 3 * R, hy);
+                            } else {
+                                acc.add((size_t)gi * g.ny + gj, cx, cy);
+                            }
+                        }
                     }
                 }
             }
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < R; k += blockDim.x) {
-            const int lx_ = lo_x[k], ly_ = lo_y[k], hx = hi_x[k], hy = hi_y[k];
-            if (!(lx_ | ly_ | hx | hy)) continue;
-            const long long sx = (long long)hx * (1ll << kLoBits) + (long long)lx_;
-            const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
-            const int ri = k / tg.ry, rj = k - ri * tg.ry;
-            int gi = bi + ri, gj = bj + rj;
-            if (gi >= g.nx) gi -= g.nx;
-            if (gj >= g.ny) gj -= g.ny;
-            const size_t node = (size_t)gi * g.ny + gj;
-            if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
-            if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
+        if ((r + 1) % kFlushRounds == 0 || r == rounds - 1) {  // uniform in the CTA
+            __syncthreads();
+            for (int k = threadIdx.x; k < R; k += blockDim.x) {
+                const int lx_ = sacc[k], ly_ = sacc[R + k];
+                const int hx = sacc[2 * R + k], hy = sacc[3 * R + k];
+                if (!(lx_ | ly_ | hx | hy)) continue;
+                sacc[k] = sacc[R + k] = sacc[2 * R + k] = sacc[3 * R + k] = 0;
+                const int ri = k / pitch, rj = k - ri * pitch;
+                int gi = bi + ri, gj = bj + rj;
+                if (gi >= g.nx) gi -= g.nx;
+                if (gj >= g.ny) gj -= g.ny;
+                const size_t node = (size_t)gi * g.ny + gj;
+                const long long sx = (long long)hx * (1ll << kLoBits) + (long long)lx_;
+                const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
+                if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
+                if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        p0 = seg_end;
     }
     if (bad) atomicOr(err, bad);
 }
@@ -544,7 +563,7 @@ cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, co
                                     const T* vy, int64_t n, longlong2* j, float scale,
                                     unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, typed<T>(g), x, y, vx, vy, n, (AccFix{j, scale}),
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, typed<T>(g), x, y, vx, vy, n, (AccFix::make(j, scale)),
                      err)
     return cudaGetLastError();
 }
@@ -554,32 +573,33 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
                                       int64_t n, longlong2* j, float scale, unsigned int* err,
                                       cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix{j, scale}), err)
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix::make(j, scale)), err)
     return cudaGetLastError();
 }
 
 
 template <typename T>
 cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const T* vx, const T* vy, int64_t n, const int* keys,
-                                      const int* off, void* j, bool fix, float scale,
-                                      unsigned int* err, cudaStream_t s) {
+                                      T* y, const T* vx, const T* vy, int64_t n, const int* off,
+                                      void* j, bool fix, float scale, unsigned int* err,
+                                      cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     if (!fix) return cudaErrorInvalidValue;  // the tiled pass is the fixed-point form's
-    const int blocks = (int)((n + kDepositChunk - 1) / kDepositChunk);
-    const size_t smem = (size_t)tg.rx * tg.ry * 4 * sizeof(int);
-    if (smem > 96 * 1024) return cudaErrorInvalidValue;
-    AccFix acc{(longlong2*)j, scale};
-    cudaError_t e = cudaSuccess;
-#define GPIC_TILED(PP)                                                                             \
-    {                                                                                              \
-        auto kern = k_move_deposit_tiled<T, PP>;                                                   \
-        if (smem > 48 * 1024)                                                                      \
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e == cudaSuccess)                                                                      \
-            kern<<<blocks, kThreads, smem, s>>>(typed<T>(g), tg, x, y, vx, vy, n, keys, off, acc, \
-                                                err);                                           \
-    }
+    if (tg.t * tg.t > kThreads || kThreads % (tg.t * tg.t) != 0) return cudaErrorInvalidValue;
+    // splits per tile: about 1366 particles (5 or 6 rounds of 256) per CTA at the mean
+    // density, so that a grid of 64-per-cell tiles holds about five CTAs per SM (timed
+    // fastest of 512..2048 on a 128 x 128 grid with 2^20 particles)
+    const int ntiles = tg.ntx * tg.nty;
+    int nsplit = (int)((n + (int64_t)ntiles * 1366 - 1) / ((int64_t)ntiles * 1366));
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 64) nsplit = 64;
+    const int blocks = ntiles * nsplit;
+    if (tg.rx * tg.pitch > kRegionCap || tg.ry > tg.pitch) return cudaErrorInvalidValue;
+    const AccFix acc = AccFix::make(j, scale);
+    const size_t smem = (size_t)4 * tg.rx * tg.pitch * sizeof(int);
+#define GPIC_TILED(PP)                                                                          \
+    k_move_deposit_tiled<T, PP><<<blocks, kThreads, smem, s>>>(typed<T>(g), tg, x, y, vx, vy, off, \
+                                                              nsplit, acc, err);
     switch (p) {
         case 2: GPIC_TILED(2) break;
         case 3: GPIC_TILED(3) break;
@@ -587,7 +607,6 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
         default: return cudaErrorInvalidValue;
     }
 #undef GPIC_TILED
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -686,7 +705,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                cudaStream_t);                                     \
     template cudaError_t launch_move_deposit_tiled<T>(int, const ParticleGeom&, const TileGeom&,  \
                                                       T*, T*, const T*, const T*, int64_t,        \
-                                                      const int*, const int*, void*, bool, float, \
+                                                      const int*, void*, bool, float,             \
                                                       unsigned int*, cudaStream_t);
 GPIC_INST(double)
 GPIC_INST(float)

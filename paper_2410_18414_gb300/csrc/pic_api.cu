@@ -39,7 +39,7 @@ struct pic_handle {
     TileGeom tg{};
     void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t *id = nullptr, *id_alt = nullptr;
-    int *keys = nullptr, *keys_sorted = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr;
+    int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
     int launches_now = 0, launches_last = 0;
     // grid buffers
     double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
@@ -127,6 +127,8 @@ pic_status validate(const pic_config* c, const pic_particles_in* in) {
         !std::isfinite(c->weight) || c->weight < 0)
         return fail(h, PIC_ERR_INVALID_ARG,
                     "lx, ly, c, eps0, dt, m must be finite and > 0; q finite; weight >= 0");
+    if (c->precision == PIC_FP32_FIX64 && (c->c < 0x1p-60 || c->c > 0x1p60))
+        return fail(h, PIC_ERR_INVALID_ARG, "the FP32 form needs 2^-60 <= c <= 2^60");
     if (c->c * c->dt >= std::fmin(c->lx, c->ly))
         return fail(h, PIC_ERR_INVALID_ARG, "c*dt must be below the domain size");
     if (c->stepper == PIC_STEPPER_BDF) {
@@ -242,11 +244,11 @@ pic_status alloc_state(pic_handle* h) {
         CK(dalloc(h, (void**)&h->id, ni));
         CK(dalloc(h, (void**)&h->id_alt, ni));
         CK(dalloc(h, (void**)&h->keys, ni));
-        CK(dalloc(h, (void**)&h->keys_sorted, ni));
         const size_t nt = (size_t)h->tg.nkeys() + 1;
         CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
+        CK(dalloc(h, (void**)&h->bsum, sort_scan_chunks(h->tg.nkeys()) * sizeof(int)));
         CK(launch_iota(h->id, h->n, h->s));
     }
     CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
@@ -430,12 +432,12 @@ pic_status sort_particles(pic_handle* h) {
         }
         src.id = h->id;
         dst.id = h->id_alt;
-        return launch_tile_sort<T>(h->tg, src, dst, h->n, h->keys, h->keys_sorted, h->hist, h->off,
-                                   h->cursor, h->s);
+        return launch_tile_sort<T>(h->tg, src, dst, h->n, h->keys, h->hist, h->off, h->cursor,
+                                   h->bsum, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
-    h->launches_now += 3;
+    h->launches_now += 4;
     return PIC_OK;
 }
 
@@ -486,29 +488,35 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         tg.ny = cfg->ny;
         const double ppc = (double)std::max<int64_t>(h->n, 1) / ((double)cfg->nx * cfg->ny);
         tg.t = 4;
-        while (tg.t < 32 && (double)(2 * tg.t) * (2 * tg.t) * ppc <= 8192.0 &&
+        while (tg.t < 16 && (double)(2 * tg.t) * (2 * tg.t) * ppc <= 8192.0 &&
                2 * tg.t <= std::min(cfg->nx, cfg->ny))
             tg.t *= 2;
         tg.ntx = (cfg->nx + tg.t - 1) / tg.t;
         tg.nty = (cfg->ny + tg.t - 1) / tg.t;
         const double drift = cfg->c * cfg->dt * cfg->sort_interval / std::fmin(dx, dy);
         tg.halo = (int)std::ceil(drift) + cfg->spline_order / 2 + 2;
-        while (tg.halo > 1 && (tg.t + 2 * tg.halo) * (tg.t + 2 * tg.halo) > 2048) --tg.halo;
+        while (tg.halo > 1 && (tg.t + 2 * tg.halo) * (tg.t + 2 * tg.halo + 31) > 2560) --tg.halo;
         tg.rx = std::min(tg.t + 2 * tg.halo, cfg->nx);
         tg.ry = std::min(tg.t + 2 * tg.halo, cfg->ny);
+        // row pitch = t (mod 32): the 32/t x t cells a warp serves map their nodes to
+        // 32 different shared-memory banks
+        tg.pitch = tg.ry + ((tg.t - tg.ry % 32) % 32 + 32) % 32;
         tg.inv_dx = 1.0 / dx;
         tg.inv_dy = 1.0 / dy;
         tg.half = (cfg->spline_order % 2 == 0) ? 1 : 0;
     }
     if (h->fp32) {
-        // Current quantum c 2^-k with k = min(38, 62 - ceil(log2 n)): a contribution
-        // |v| W_x W_y is below c, i.e. below 2^k quanta, so no int64 node total can reach
-        // 2^62 whatever the distribution, and k <= 38 lets the tiled deposit split each
-        // contribution into two parts that fit 32-bit shared atomics.  At k = 38 the
-        // quantum (3.6e-12 c) is far below the FP32 rounding of a contribution.
+        // Current quantum: the power of two 2^(kc - k) >= c 2^-k, with c <= 2^kc and
+        // k = min(38, 62 - ceil(log2 n)).  A contribution |v| W_x W_y is below c, i.e.
+        // below 2^k quanta, so no int64 node total can reach 2^62 whatever the
+        // distribution, and k <= 38 lets the deposit split each contribution exactly into
+        // two parts that fit 32-bit shared atomics (the power of two makes the split's
+        // scalings exact).  At k = 38 the quantum (3.6e-12 c for c = 1) is far below the
+        // FP32 rounding of a contribution.
         int kj = 38;
         if (h->n > 1) kj = std::min(38, 62 - (int)std::ceil(std::log2((double)h->n)));
-        h->fix_scale_j = (float)(std::ldexp(1.0, kj) / cfg->c);
+        const int kc = (int)std::ceil(std::log2(cfg->c));
+        h->fix_scale_j = (float)std::ldexp(1.0, kj - kc);
         h->fix_unscale_j = 1.0 / (double)h->fix_scale_j;
         // Charge at t = 0 (only the untiled pass): W_x W_y <= 1 with 2^k quanta,
         // k = 62 - ceil(log2 n), so no node total can reach 2^62.
@@ -545,7 +553,7 @@ pic_status pic_deposit(pic_handle* h) {
         if (h->sorting && h->fp32)
             return launch_move_deposit_tiled<T>(h->p, h->geom, h->tg, (T*)h->x, (T*)h->y,
                                                 (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
-                                                h->n, h->keys_sorted, h->off, h->J, h->fp32,
+                                                h->n, h->off, h->J, h->fp32,
                                                 h->fix_scale_j, h->err, h->s);
         if (h->fp32)
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,

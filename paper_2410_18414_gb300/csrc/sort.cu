@@ -2,12 +2,12 @@
 //
 // The domain is cut into tiles of T x T cells; a particle's key is its stencil base
 // cell, numbered tile by tile, so the particles of one tile are contiguous and, inside
-// it, those of one cell are.  Three kernels: a histogram of keys (shared-memory privatised), one
-// single-CTA exclusive scan giving each tile's first slot, and a scatter that moves all
-// particle arrays (and the particle's original index) to the slots of its tile.  The
-// scatter order inside a tile is not fixed; nothing depends on it: the FP32 form sums the
-// current in int64, the push is per particle, and read-back restores the caller's order
-// through the index array.  Sorting keeps the particles of one CTA inside one tile, so
+// it, those of one cell are.  Four kernels: the keys with their histogram, a two-pass
+// exclusive scan giving each key's first slot, and a scatter that moves all particle
+// arrays (and the particle's original index) to the slots of its key.  The order inside
+// a cell is not fixed; nothing depends on it: the FP32 form sums the current in integers,
+// the push is per particle, and read-back restores the caller's order through the index
+// array.  Sorting keeps the particles of one CTA inside one tile, so
 // the deposit can accumulate in shared memory and the gather reuses cached field tiles.
 #include "common.cuh"
 #include "gpic_internal.h"
@@ -18,26 +18,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kSmemHistMax = 12 * 1024;  // tiles held in a shared-memory histogram
+constexpr int kScanChunk = 4 * kScanThreads;  // keys per CTA of the scan
+constexpr int kScatterPer = 4;                // particles per thread in the scatter
 
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     if (b > 152 * 8) b = 152 * 8;
     return (int)(b < 1 ? 1 : b);
-}
-
-// Lanes of the calling warp holding the same key: one of them adds the group's count
-// to *counter; every lane returns its slot (old value + rank inside the group).  All 32
-// lanes must call it (invalid lanes pass key = -1 and get -1 back).
-__device__ __forceinline__ int warp_aggregated_claim(int* counter_base, int key) {
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    int start = 0;
-    if (lane == leader && key >= 0) start = atomicAdd(counter_base + key, __popc(peers));
-    start = __shfl_sync(0xffffffffu, start, leader);
-    return key >= 0 ? start + rank : -1;
 }
 
 // Stencil base cell of a position (floor(x/dx) for odd spline degree, floor(x/dx + 1/2)
@@ -56,17 +43,12 @@ __device__ __forceinline__ int tile_key(T x, T y, const TileGeom& tg) {
     return ((tx * tg.nty + ty) * tg.t + (bx - tx * tg.t)) * tg.t + (by - ty * tg.t);
 }
 
+// Keys and their histogram.  Particles arrive in the order of the previous sort, so the
+// lanes of a warp mostly share a key: one lane adds the group's count (no return value).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_tile_hist(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+k_sort_keys(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             int* __restrict__ keys, int* __restrict__ hist) {
-    extern __shared__ int sh[];
-    const int ntiles = tg.nkeys();
-    const bool priv = ntiles <= kSmemHistMax;
-    if (priv) {
-        for (int i = threadIdx.x; i < ntiles; i += blockDim.x) sh[i] = 0;
-        __syncthreads();
-    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += stride) {  // warp-uniform
         const int64_t p = b + threadIdx.x;
@@ -75,93 +57,113 @@ k_tile_hist(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64
             k = tile_key(x[p], y[p], tg);
             keys[p] = k;
         }
-        warp_aggregated_claim(priv ? sh : hist, k);
-    }
-    if (priv) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < ntiles; i += blockDim.x)
-            if (sh[i]) atomicAdd(&hist[i], sh[i]);
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        if (k >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + k, __popc(peers));
     }
 }
 
-// Exclusive scan of hist[0..ntiles) into off[0..ntiles] (off[ntiles] = n); cursor = off.
-__global__ void __launch_bounds__(kScanThreads)
-k_tile_scan(const int* __restrict__ hist, int ntiles, int* __restrict__ off,
-            int* __restrict__ cursor) {
-    __shared__ int part[kScanThreads];
-    const int per = (ntiles + kScanThreads - 1) / kScanThreads;
-    const int b = threadIdx.x * per;
-    int s = 0;
-    for (int i = 0; i < per && b + i < ntiles; ++i) s += hist[b + i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {  // Hillis-Steele inclusive scan
-        int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int run = part[threadIdx.x] - s;  // exclusive prefix of this thread's block
-    for (int i = 0; i < per && b + i < ntiles; ++i) {
-        off[b + i] = run;
-        cursor[b + i] = run;
-        run += hist[b + i];
-    }
-    if (threadIdx.x == kScanThreads - 1) off[ntiles] = part[kScanThreads - 1];
-}
-
-// Scatter with per-CTA slot reservation: CTA b counts its chunk's particles per tile in
-// shared memory, reserves each tile's slots with one global atomic, then hands out slots
-// from the reservation with shared-memory atomics.  (One global atomic per particle on a
-// few dozen tile cursors serialises badly.)
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_tile_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ keys, int64_t n,
-               int ntiles, int chunk, int* __restrict__ cursor, int* __restrict__ keys_out) {
-    extern __shared__ int base[];
-    const int64_t c0 = (int64_t)blockIdx.x * chunk;
-    if (c0 >= n) return;
-    const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) base[t] = 0;
-    __syncthreads();
-    for (int64_t b = c0; b < c1; b += blockDim.x) {  // warp-uniform trip count
-        const int64_t p = b + threadIdx.x;
-        warp_aggregated_claim(base, p < c1 ? keys[p] : -1);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const int c = base[t];
-        base[t] = c ? atomicAdd(&cursor[t], c) : 0;
-    }
-    __syncthreads();
-    for (int64_t b = c0; b < c1; b += blockDim.x) {
-        const int64_t p = b + threadIdx.x;
-        const int k = p < c1 ? keys[p] : -1;
-        const int q = warp_aggregated_claim(base, k);
-        if (k >= 0) {
+// Exclusive scan of the thread sums of a CTA (blockDim.x = kScanThreads); returns the
+// thread's exclusive prefix and sets *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
 #pragma unroll
-            for (int a = 0; a < 8; ++a) dst.a[a][q] = src.a[a][p];
-            dst.id[q] = src.id[p];
-            keys_out[q] = k;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_sums[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
         }
+        warp_sums[lane] = wi - w;  // exclusive prefix of the warp totals
+        if (lane == 31) warp_sums[32] = wi;
     }
+    __syncthreads();
+    *total = warp_sums[32];
+    return warp_sums[warp] + inc - v;
 }
 
-// Fallback for more tiles than fit a shared-memory table: one global atomic per particle.
+// Scan, pass 1: CTA b scans keys [b C, (b+1) C) locally (C = kScanChunk) into off and
+// stores the chunk total in bsum[b].
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_local(const int* __restrict__ hist, int nkeys, int* __restrict__ off,
+             int* __restrict__ bsum) {
+    __shared__ int warp_sums[33];
+    const int i0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+    int v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = i0 + j < nkeys ? hist[i0 + j] : 0;
+    int total;
+    int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], warp_sums, &total);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (i0 + j < nkeys) off[i0 + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// Scan, pass 2: adds the totals of the earlier chunks; cursor = off; off[nkeys] = n.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_add(int nkeys, int nchunks, const int* __restrict__ bsum, int* __restrict__ off,
+           int* __restrict__ cursor) {
+    __shared__ int warp_sums[33];
+    int s = 0;
+    for (int c = threadIdx.x; c < blockIdx.x; c += blockDim.x) s += bsum[c];
+    int total;
+    block_exclusive_scan(s, warp_sums, &total);  // total = sum of bsum[0 .. blockIdx.x)
+    const int base = total;
+    const int i0 = blockIdx.x * kScanChunk;
+    for (int i = i0 + threadIdx.x; i < i0 + kScanChunk && i < nkeys; i += blockDim.x) {
+        const int o = off[i] + base;
+        off[i] = o;
+        cursor[i] = o;
+    }
+    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) off[nkeys] = base + bsum[nchunks - 1];
+}
+
+// Scatter: every particle claims a slot of its key (warp-aggregated atomics on the key
+// cursors).  A thread handles kScatterPer particles and issues all their claims before
+// it waits for any, then moves the particle arrays and the original index.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_tile_scatter_global(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ keys,
-                      int64_t n, int* __restrict__ cursor, int* __restrict__ keys_out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += stride) {
-        const int64_t p = b + threadIdx.x;
-        const int k = p < n ? keys[p] : -1;
-        const int q = warp_aggregated_claim(cursor, k);
-        if (k >= 0) {
+k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ keys, int64_t n,
+               int* __restrict__ cursor) {
+    const int lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * kScatterPer + threadIdx.x;
+    int k[kScatterPer], slot[kScatterPer], leader[kScatterPer];
+    unsigned peers[kScatterPer];
+#pragma unroll
+    for (int i = 0; i < kScatterPer; ++i) {
+        const int64_t p = base + (int64_t)i * blockDim.x;
+        k[i] = p < n ? keys[p] : -1;
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterPer; ++i) {
+        peers[i] = __match_any_sync(0xffffffffu, k[i]);
+        leader[i] = __ffs(peers[i]) - 1;
+        slot[i] = 0;
+        if (lane == leader[i] && k[i] >= 0) slot[i] = atomicAdd(cursor + k[i], __popc(peers[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterPer; ++i)
+        slot[i] = __shfl_sync(0xffffffffu, slot[i], leader[i]) +
+                  __popc(peers[i] & ((1u << lane) - 1u));
+#pragma unroll
+    for (int i = 0; i < kScatterPer; ++i) {
+        const int64_t p = base + (int64_t)i * blockDim.x;
+        if (k[i] >= 0) {
+            const int q = slot[i];
 #pragma unroll
             for (int a = 0; a < 8; ++a) dst.a[a][q] = src.a[a][p];
             dst.id[q] = src.id[p];
-            keys_out[q] = k;
         }
     }
 }
@@ -174,37 +176,25 @@ __global__ void k_iota(int32_t* __restrict__ id, int64_t n) {
 
 }  // namespace
 
+int sort_scan_chunks(int nkeys) { return (nkeys + kScanChunk - 1) / kScanChunk; }
+
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
-                             int* keys, int* keys_out, int* hist, int* off, int* cursor,
+                             int* keys, int* hist, int* off, int* cursor, int* bsum,
                              cudaStream_t s) {
-    const int ntiles = tg.nkeys();  // number of sort keys (cells, tile-major)
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * ntiles, s);
+    const int nkeys = tg.nkeys();  // number of sort keys (cells, tile-major)
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * nkeys, s);
     if (e != cudaSuccess || n == 0) {
-        if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, sizeof(int) * (ntiles + 1), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
         return e;
     }
-    const size_t sh = ntiles <= kSmemHistMax ? sizeof(int) * ntiles : 0;
-    if (sh > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_tile_hist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e != cudaSuccess) return e;
-    }
-    k_tile_hist<T><<<blocks_for(n), kThreads, sh, s>>>(tg, src.a[0], src.a[1], n, keys, hist);
-    k_tile_scan<<<1, kScanThreads, 0, s>>>(hist, ntiles, off, cursor);
-    if (ntiles <= kSmemHistMax) {
-        const int chunk = 1024;
-        const int blocks = (int)((n + chunk - 1) / chunk);
-        if (sh > 48 * 1024) {
-            e = cudaFuncSetAttribute(k_tile_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sh);
-            if (e != cudaSuccess) return e;
-        }
-        k_tile_scatter<T><<<blocks, kThreads, sh, s>>>(src, dst, keys, n, ntiles, chunk, cursor,
-                                                       keys_out);
-    } else {
-        k_tile_scatter_global<T><<<blocks_for(n), kThreads, 0, s>>>(src, dst, keys, n, cursor,
-                                                                    keys_out);
-    }
+    k_sort_keys<T><<<blocks_for(n), kThreads, 0, s>>>(tg, src.a[0], src.a[1], n, keys, hist);
+    const int nchunks = sort_scan_chunks(nkeys);
+    k_scan_local<<<nchunks, kScanThreads, 0, s>>>(hist, nkeys, off, bsum);
+    k_scan_add<<<nchunks, kScanThreads, 0, s>>>(nkeys, nchunks, bsum, off, cursor);
+    const int64_t per_cta = (int64_t)kThreads * kScatterPer;
+    k_sort_scatter<T><<<(unsigned)((n + per_cta - 1) / per_cta), kThreads, 0, s>>>(src, dst, keys,
+                                                                                   n, cursor);
     return cudaGetLastError();
 }
 
