@@ -105,7 +105,16 @@ def bytes_move_deposit(rsz):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
 # captures (profiles/), keyed by (kernel, form); None when the kernel changed since.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --set full, 3 launches of k_move_deposit_tiled<float,3> on the 128x128 Weibel
+    # workload: dram__bytes_read 17.15 MB + dram__bytes_write 0.27 MB (the x, y writes
+    # stay in L2 until after the kernel)
+    ("move_deposit", "fp32"): 17.42e6,
+}
+
+# Conflict-free 32-bit shared-memory atomicAdd throughput of the whole GPU, in warp
+# instructions per ns (1.873 per SM per ns measured on GB300, x 152 SMs).
+SMEM_ATOMIC_RATE = 1.873 * 152
 
 
 def peaks():
@@ -252,31 +261,47 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm --
 
-def time_steps(sim, steps, warmup, stream, flush, count=None):
+def time_steps(sim, steps, warmup, stream, flush, count=None, detail=False):
+    """Per-step device times (CUDA events on the simulation's stream), L2 flushed between
+    steps outside the events.  detail=False brackets each whole step with one event pair
+    (the headline); detail=True also records the phase boundaries and the library's
+    per-kernel event pairs, which add about a dozen event records to every step."""
     import torch
     for _ in range(warmup):
         sim.step(1)
         flush.zero_()
     torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    if detail:
+        sim.set_kernel_timing(steps + 1)   # the library's per-kernel event pairs, made up front
+    nev = 4 if detail else 2
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)]
     for k in range(steps):
         e = ev[k]
         e[0].record(stream)
-        sim.deposit()
-        e[1].record(stream)
-        sim.field_solve()
-        e[2].record(stream)
-        sim.gather_push()
-        e[3].record(stream)
+        if detail:
+            sim.deposit()
+            e[1].record(stream)
+            sim.field_solve()
+            e[2].record(stream)
+            sim.gather_push()
+        else:
+            sim.step(1)
+        e[-1].record(stream)
         if count is not None:
             count[0] += sim.kernels_per_step
         flush.zero_()       # cold L2 for the next step (outside the events)
     torch.cuda.synchronize()
-    dep = [e[0].elapsed_time(e[1]) for e in ev]
-    fld = [e[1].elapsed_time(e[2]) for e in ev]
-    psh = [e[2].elapsed_time(e[3]) for e in ev]
-    tot = [e[0].elapsed_time(e[3]) for e in ev]
-    return {"deposit_ms": dep, "field_ms": fld, "push_ms": psh, "step_ms": tot}
+    out = {"step_ms": [e[0].elapsed_time(e[-1]) for e in ev]}
+    if detail:
+        kt = {}
+        for name in ("sort", "deposit", "field_solve", "gather_push"):
+            ms, nl = sim.kernel_time(name)
+            kt[name] = {"launches": nl, "ms_per_launch": ms / nl if nl else None, "ms_total": ms}
+        sim.set_kernel_timing(0)
+        out.update(deposit_ms=[e[0].elapsed_time(e[1]) for e in ev],
+                   field_ms=[e[1].elapsed_time(e[2]) for e in ev],
+                   push_ms=[e[2].elapsed_time(e[3]) for e in ev], kernels=kt)
+    return out
 
 
 def main():
@@ -326,8 +351,13 @@ def main():
         total_ms = float(tt.item())
     n_all = wl.n * world
     value = n_all * a.steps / (total_ms * 1e-3)
+    # phase and per-kernel breakdown: an instrumented run of the same simulation right
+    # after the timed region (its extra event records would slow the headline steps)
+    nd = min(a.steps, 500)
+    t = time_steps(sim, nd, 3, stream, flush, detail=True)
 
-    # roofline of the dominant kernel (per-launch averages from the events above)
+    # roofline of the dominant kernel: per-launch averages of the library's own event
+    # pairs around each kernel (same stream, timed region only)
     pk = peaks()
     fp32 = a.precision == "fp32"
     rsz = 4 if fp32 else 8
@@ -335,10 +365,13 @@ def main():
     dep_ms = statistics.mean(t["deposit_ms"])
     psh_ms = statistics.mean(t["push_ms"])
     fld_ms = statistics.mean(t["field_ms"])
+    kt = t["kernels"]
     kern = {
-        "gather_push": {"ms": psh_ms, "flops": flops_gather_push(p) * wl.n,
+        "gather_push": {"ms": kt["gather_push"]["ms_per_launch"],
+                        "flops": flops_gather_push(p) * wl.n,
                         "bytes": bytes_gather_push(rsz) * wl.n},
-        "move_deposit": {"ms": dep_ms, "flops": flops_move_deposit(p) * wl.n,
+        "move_deposit": {"ms": kt["deposit"]["ms_per_launch"],
+                         "flops": flops_move_deposit(p) * wl.n,
                          "bytes": bytes_move_deposit(rsz) * wl.n},
     }
     for k in kern.values():
@@ -353,6 +386,15 @@ def main():
         roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["gbs"],
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dom["gbs"] / pk["hbm_gbs"],
                     "traffic": TRAFFIC.get((dom_name, a.precision)), "peak_source": pk["hbm_src"]}
+        if dom_name == "move_deposit":
+            # what actually bounds it: 32-bit shared-memory atomics, (p+1)^2 nodes x 2
+            # components x 2 halves per particle, at the measured conflict-free rate
+            atoms = 4 * (p + 1) ** 2 * wl.n / 32
+            floor_ms = atoms / (SMEM_ATOMIC_RATE * 1e6)
+            roofline["smem_atomics"] = {
+                "warp_atomics_per_launch": atoms, "peak_warp_atomics_per_ns": SMEM_ATOMIC_RATE,
+                "floor_ms": floor_ms, "frac": floor_ms / dom["ms"],
+                "peak_source": "measured: conflict-free 32-bit shared atomicAdd, 152 SMs"}
     else:
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
                     "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
@@ -370,13 +412,15 @@ def main():
     so = pic.Simulation(make_config(wl, a.stepper, other, other_sort), wl.x, wl.y, wl.vx,
                         wl.vy, stream=sp)
     to = time_steps(so, max(20, a.steps // 4), 5, stream, flush)
+    tod = time_steps(so, 50, 2, stream, flush, detail=True)
     so.close()
     other_ms = statistics.mean(to["step_ms"])
     other_form = {"form": other, "ms_per_step": other_ms, "sort_interval": other_sort,
                   "value": wl.n * world / (other_ms * 1e-3),
-                  "phase_ms": {"deposit": statistics.mean(to["deposit_ms"]),
-                               "field_solve": statistics.mean(to["field_ms"]),
-                               "gather_push": statistics.mean(to["push_ms"])}}
+                  "phase_ms": {"deposit": statistics.mean(tod["deposit_ms"]),
+                               "field_solve": statistics.mean(tod["field_ms"]),
+                               "gather_push": statistics.mean(tod["push_ms"])},
+                  "kernel_ms": {k: v["ms_per_launch"] for k, v in tod["kernels"].items()}}
 
     # other steppers of the same workload (shorter runs)
     by_stepper = {a.stepper: total_ms / a.steps}
@@ -435,6 +479,8 @@ def main():
             "kernels": {k: {kk: round(vv, 6) if isinstance(vv, float) else vv
                             for kk, vv in v.items()} for k, v in kern.items()},
             "phase_ms": {"deposit": dep_ms, "field_solve": fld_ms, "gather_push": psh_ms},
+            "kernel_ms": {k: v["ms_per_launch"] for k, v in kt.items()},
+            "kernel_launches": {k: v["launches"] for k, v in kt.items()},
             "by_stepper_ms_per_step": by_stepper,
             "other_form": other_form,
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),

@@ -82,7 +82,7 @@ typedef enum {
 } pic_field;
 
 typedef struct {
-    int32_t nx, ny;          /* grid nodes per direction, each 8..4096, of the form 2^a 3^b */
+    int32_t nx, ny;          /* grid nodes per direction: even, 8..1024, of the form 2^a 3^b */
     int32_t spline_order;    /* B-spline degree p of the particle shape: 2, 3 or 4          */
     int32_t stepper;         /* pic_stepper                                                 */
     int32_t bdf_order;       /* k for PIC_STEPPER_BDF (1..6)                                */
@@ -175,6 +175,32 @@ int64_t pic_step_count(const pic_handle *h);
 
 /* Number of CUDA kernels one step launches (for launch accounting). */
 int32_t pic_kernels_per_step(const pic_handle *h);
+
+/* Kernel timing, a measurement aid.  The library brackets each launch group below with
+ * a pair of CUDA events on the handle's stream and sums their elapsed times:
+ *   PIC_KT_SORT     the particle sort (keys, scan, scatter) of a sorting step
+ *   PIC_KT_DEPOSIT  the move + current deposit kernel (not the clearing of J)
+ *   PIC_KT_FIELD    all kernels of pic_field_solve
+ *   PIC_KT_GATHER   the gather + push kernel */
+typedef enum {
+    PIC_KT_SORT = 0,
+    PIC_KT_DEPOSIT = 1,
+    PIC_KT_FIELD = 2,
+    PIC_KT_GATHER = 3,
+    PIC_KT_COUNT = 4
+} pic_kernel_timer;
+
+/* max_launches > 0 starts timing: resets every timer and creates max_launches event
+ * pairs per timer up front (launches beyond that are not timed; a timer counts only
+ * the launches it timed).  max_launches = 0 stops timing and keeps the sums.  Events are
+ * created only here, never inside a step.  PIC_ERR_INVALID_ARG for max_launches < 0 or
+ * above 2^20; PIC_ERR_CUDA if event creation fails. */
+pic_status pic_set_kernel_timing(pic_handle *h, int32_t max_launches);
+
+/* Sum of the timed durations (milliseconds) and the number of timed launches of timer
+ * `which` since timing was last started.  Synchronizes the handle's stream.
+ * PIC_ERR_INVALID_ARG for an unknown timer or NULL outputs. */
+pic_status pic_kernel_time(pic_handle *h, int32_t which, double *total_ms, int64_t *launches);
 
 /* One-line description of the last failure on this handle (or of the last failed
  * pic_init when h is NULL).  Valid until the next call on the handle. */

@@ -96,6 +96,11 @@ __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rsqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double rsqrt_rn(double a) { return __dsqrt_rn(a); }
+
 // x + v dt, wrapped (the IAEM position update)
 template <typename T> __device__ __forceinline__ T move_pos(T x, T v, T dt, T l) {
     return wrap_pos(rfma(v, dt, x), l);

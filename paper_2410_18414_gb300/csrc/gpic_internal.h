@@ -222,6 +222,13 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
                                       void* j, bool fix, float scale, unsigned int* err,
                                       cudaStream_t s);
 
+// Gather + push of particles sorted by launch_tile_sort (FP32 form), fields staged per tile.
+cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
+                                    const TileGeom& tg, const float* x, const float* y, float* px,
+                                    float* py, const float* vx, const float* vy, float* vx_old,
+                                    float* vy_old, int64_t n, const int* off, const void* fields4,
+                                    double* diag, unsigned int* err, cudaStream_t s);
+
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };
 

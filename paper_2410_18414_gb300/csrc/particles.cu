@@ -71,6 +71,16 @@ __device__ __forceinline__ void load_node(const double2* node, double* g) {
     }
 }
 
+// Asks the L2 to fetch the 16-byte-aligned part of [p, p + bytes) (a bulk prefetch: one
+// instruction, no registers, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t lo = (a + 15) & ~(uintptr_t)15, hi = (a + bytes) & ~(uintptr_t)15;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo))
+                     : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ bool in_domain(T xi, int n) {
     return xi >= (T)0 && xi <= (T)n;
@@ -237,6 +247,11 @@ k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__
     const int phases = blockDim.x / tt;   // threads per cell in this CTA
     const int phase = threadIdx.x / tt;
     const int key = tile * tt + cell;
+    if (threadIdx.x < 4) {  // the tile's particles come to L2 while the region is cleared
+        const T* arr[4] = {x, y, vx, vy};
+        const int64_t a0 = off[tile * tt], a1 = off[(tile + 1) * tt];
+        prefetch_l2(arr[threadIdx.x] + a0, (size_t)(a1 - a0) * sizeof(T));
+    }
     const int o0 = off[key], count = off[key + 1] - o0;
     // split s takes the contiguous share [s count / nsplit, (s+1) count / nsplit) of the
     // cell, so the particles of one 32-byte sector are read by one CTA
@@ -373,6 +388,57 @@ __global__ void k_extract_fix(const longlong2* __restrict__ J, int comp, double 
     }
 }
 
+// Gather of the eight fields at one particle: f += W_x[a] W_y[b] g(node), nodes in the
+// order a = 0..P, b = 0..P (the same order and roundings in every gather kernel).
+template <typename T>
+__device__ __forceinline__ void gather_node(T w, const T* g, T* f) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = rfma(w, g[k], f[k]);
+}
+
+// IAEM push of particle p from its gathered fields (section 3.3):
+//   P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*),  v* = 2 v^n - v^{n-1}
+//   u = P^{n+1} - q A,  v^{n+1} = c^2 u / sqrt(c^2 |u|^2 + (m c^2)^2)
+// f = (dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy).  v^{n+1} overwrites
+// v^{n-1}.  Written with explicit roundings, so every kernel gives the same bits.
+template <typename T>
+__device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t p,
+                                         T* __restrict__ px, T* __restrict__ py,
+                                         const T* __restrict__ vx, const T* __restrict__ vy,
+                                         T* __restrict__ vxo, T* __restrict__ vyo, unsigned& bad,
+                                         double& kin) {
+    const T vsx = rfma((T)2, vx[p], -vxo[p]);
+    const T vsy = rfma((T)2, vy[p], -vyo[p]);
+    const T fx = rfma(f[6], vsy, rfma(f[4], vsx, -f[0]));
+    const T fy = rfma(f[7], vsy, rfma(f[5], vsx, -f[1]));
+    const T Px = rfma(pp.qdt, fx, px[p]);
+    const T Py = rfma(pp.qdt, fy, py[p]);
+    const T ux = rfma(-pp.q, f[2], Px), uy = rfma(-pp.q, f[3], Py);
+    const T den = rsqrt_rn(rfma(pp.c2, rfma(ux, ux, rmul(uy, uy)), rmul(pp.mc2, pp.mc2)));
+    const T rc = rdiv(pp.c2, den);
+    const T vxn1 = rmul(rc, ux), vyn1 = rmul(rc, uy);
+    px[p] = Px;
+    py[p] = Py;
+    vxo[p] = vxn1;
+    vyo[p] = vyn1;
+    if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
+    if (pp.diag) {  // m c^2 (gamma - 1) per unit weight, in FP64 for either storage type
+        const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
+        kin += sqrt(c2d * (uxd * uxd + uyd * uyd) + mc2d * mc2d) - mc2d;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void push_finish(const PushT<T>& pp, unsigned bad, double kin,
+                                            double* __restrict__ diag,
+                                            unsigned int* __restrict__ err) {
+    if (bad) atomicOr(err, bad);
+    if (pp.diag) {
+        for (int o = 16; o > 0; o >>= 1) kin += __shfl_down_sync(0xffffffffu, kin, o);
+        if ((threadIdx.x & 31) == 0 && kin != 0.0) atomicAdd(diag + D_KIN, kin * pp.weight);
+    }
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
 k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restrict__ y,
@@ -382,7 +448,6 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
               unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
     const T idx_ = g.inv_dx, idy = g.inv_dy;
-    const T q = pp.q, qdt = pp.qdt, c2 = pp.c2, mc2 = pp.mc2;
     double kin = 0.0;
     unsigned bad = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
@@ -395,7 +460,7 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
         T wx[P + 1], wy[P + 1];
         const int ix = Shape<P, T>::weights(xi, wx);
         const int iy = Shape<P, T>::weights(yj, wy);
-        T f0 = 0, f1 = 0, f2 = 0, f3 = 0, f4 = 0, f5 = 0, f6 = 0, f7 = 0;
+        T f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const int gi = wrap_idx(ix + a, g.nx);
@@ -403,43 +468,102 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                const T w = wx[a] * wy[b];
-                const C* node = row + (size_t)gj * 4;
-                T g[8];
-                load_node(node, g);  // dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy
-                f0 += w * g[0];
-                f1 += w * g[1];
-                f2 += w * g[2];
-                f3 += w * g[3];
-                f4 += w * g[4];
-                f5 += w * g[5];
-                f6 += w * g[6];
-                f7 += w * g[7];
+                T gv[8];
+                load_node(row + (size_t)gj * 4, gv);
+                gather_node(rmul(wx[a], wy[b]), gv, f);
             }
         }
-        const T vxn = vx[p], vyn = vy[p];
-        const T vsx = (T)2 * vxn - vxo[p];
-        const T vsy = (T)2 * vyn - vyo[p];
-        const T Px = px[p] + qdt * (-f0 + f4 * vsx + f6 * vsy);
-        const T Py = py[p] + qdt * (-f1 + f5 * vsx + f7 * vsy);
-        const T ux = Px - q * f2, uy = Py - q * f3;
-        const T den = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
-        const T vxn1 = c2 * ux / den, vyn1 = c2 * uy / den;
-        px[p] = Px;
-        py[p] = Py;
-        vxo[p] = vxn1;
-        vyo[p] = vyn1;
-        if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
-        if (pp.diag) {  // m c^2 (gamma - 1) per unit weight, in FP64 for either storage type
-            const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
-            kin += sqrt(c2d * (uxd * uxd + uyd * uyd) + mc2d * mc2d) - mc2d;
+        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin);
+    }
+    push_finish(pp, bad, kin, diag, err);
+}
+
+// Gather + push over particles sorted by tile and cell (see sort.cu), FP32 form.
+//
+// CTA (tile, split) copies the gather fields of the tile's node region (the tile plus a
+// halo: rx x ry nodes, 32 B each) into shared memory, then pushes a contiguous share of
+// the tile's particles.  Consecutive particles mostly sit in one cell, so the lanes of a
+// warp read the same node: shared-memory broadcasts.  A particle whose stencil leaves the
+// region (it drifted further than the halo) reads the global fields.  Node order and
+// roundings are those of k_gather_push, so the two give the same bits.
+template <int P>
+__global__ void __launch_bounds__(kThreads, 4)
+k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __restrict__ x,
+                    const float* __restrict__ y, float* __restrict__ px,
+                    float* __restrict__ py, const float* __restrict__ vx,
+                    const float* __restrict__ vy, float* __restrict__ vxo,
+                    float* __restrict__ vyo, const int* __restrict__ off, int nsplit,
+                    const float2* __restrict__ F, double* __restrict__ diag,
+                    unsigned int* __restrict__ err) {
+    extern __shared__ float4 sf[];  // [rx][ry] nodes, two float4 each
+    const int tt = tg.t * tg.t;
+    const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+    const int64_t t0 = off[tile * tt], cnt = (int64_t)off[(tile + 1) * tt] - t0;
+    const int64_t p0 = t0 + cnt * split / nsplit, p1 = t0 + cnt * (split + 1) / nsplit;
+    if (p0 == p1) return;  // uniform for the CTA
+    if (threadIdx.x < 8) {  // the CTA's particles come to L2 while it stages the fields
+        const float* arr[8] = {x, y, px, py, vx, vy, vxo, vyo};
+        prefetch_l2(arr[threadIdx.x] + p0, (size_t)(p1 - p0) * sizeof(float));
+    }
+    const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
+    int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
+    if (bi < 0) bi += g.nx;
+    if (bj < 0) bj += g.ny;
+    const int rx = tg.rx, ry = tg.ry;
+    const float4* F4 = reinterpret_cast<const float4*>(F);
+    for (int k = threadIdx.x; k < 2 * rx * ry; k += blockDim.x) {
+        const int node = k >> 1;
+        const int ri = node / ry, rj = node - ri * ry;
+        int gi = bi + ri, gj = bj + rj;
+        if (gi >= g.nx) gi -= g.nx;
+        if (gj >= g.ny) gj -= g.ny;
+        sf[k] = __ldg(F4 + ((size_t)gi * g.ny + gj) * 2 + (k & 1));
+    }
+    __syncthreads();
+    const float idx_ = g.inv_dx, idy = g.inv_dy;
+    double kin = 0.0;
+    unsigned bad = 0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const float xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+            bad |= ERR_NONFINITE;
+            continue;
         }
+        float wx[P + 1], wy[P + 1];
+        const int ix = wrap_idx(Shape<P, float>::weights(xi, wx), g.nx);
+        const int iy = wrap_idx(Shape<P, float>::weights(yj, wy), g.ny);
+        int ri0 = ix - bi, rj0 = iy - bj;
+        if (ri0 < 0) ri0 += g.nx;
+        if (rj0 < 0) rj0 += g.ny;
+        float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (ri0 + P < rx && rj0 + P < ry) {
+            const float4* row = sf + 2 * (ri0 * ry + rj0);
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const float4 u = row[2 * b], v = row[2 * b + 1];
+                    const float gv[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+                    gather_node(rmul(wx[a], wy[b]), gv, f);
+                }
+                row += 2 * ry;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a <= P; ++a) {
+                const int gi = wrap_idx(ix + a, g.nx);
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const int gj = wrap_idx(iy + b, g.ny);
+                    float gv[8];
+                    load_node(F + ((size_t)gi * g.ny + gj) * 4, gv);
+                    gather_node(rmul(wx[a], wy[b]), gv, f);
+                }
+            }
+        }
+        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin);
     }
-    if (bad) atomicOr(err, bad);
-    if (pp.diag) {
-        for (int o = 16; o > 0; o >>= 1) kin += __shfl_down_sync(0xffffffffu, kin, o);
-        if ((threadIdx.x & 31) == 0 && kin != 0.0) atomicAdd(diag + D_KIN, kin * pp.weight);
-    }
+    push_finish(pp, bad, kin, diag, err);
 }
 
 template <typename T, int P>
@@ -631,6 +755,43 @@ cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& p
     if (n == 0) return cudaSuccess;
     GPIC_DISPATCH_P(p, k_gather_push, typed<T>(g), typed<T>(pp), x, y, px, py, vx, vy, vxo, vyo, n,
                     (const cplx_t<T>*)f, diag, err)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
+                                    const TileGeom& tg, const float* x, const float* y, float* px,
+                                    float* py, const float* vx, const float* vy, float* vxo,
+                                    float* vyo, int64_t n, const int* off, const void* f,
+                                    double* diag, unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    // splits per tile: about 2048 particles per CTA at the mean density (so that a grid of
+    // 64-per-cell tiles is a single wave of four CTAs per SM)
+    const int ntiles = tg.ntx * tg.nty;
+    int nsplit = (int)((n + (int64_t)ntiles * 2048 - 1) / ((int64_t)ntiles * 2048));
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 64) nsplit = 64;
+    const int blocks = ntiles * nsplit;
+    const size_t smem = (size_t)tg.rx * tg.ry * 2 * sizeof(float4);
+    if (smem > 100 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+#define GPIC_GTILED(PP)                                                                        \
+    {                                                                                          \
+        static const cudaError_t attr = cudaFuncSetAttribute(                                  \
+            k_gather_push_tiled<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
+        e = attr;                                                                              \
+        if (e == cudaSuccess)                                                                  \
+            k_gather_push_tiled<PP><<<blocks, kThreads, smem, s>>>(                            \
+                typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo, vyo, off,    \
+                nsplit, (const float2*)f, diag, err);                                          \
+    }
+    switch (p) {
+        case 2: GPIC_GTILED(2) break;
+        case 3: GPIC_GTILED(3) break;
+        case 4: GPIC_GTILED(4) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPIC_GTILED
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

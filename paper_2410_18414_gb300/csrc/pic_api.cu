@@ -21,6 +21,14 @@ thread_local std::string g_init_error;
 
 struct pic_handle {
     pic_config cfg{};
+    // kernel timing (pic_set_kernel_timing): per timer, event pairs created up front
+    struct KTimer {
+        std::vector<cudaEvent_t> ev;  // start, stop, start, stop, ...
+        int64_t used = 0;             // pairs recorded since timing started
+    };
+    KTimer kt[PIC_KT_COUNT];
+    bool ktiming = false;
+    int64_t kt_cap = 0;  // pairs each timer may record since timing started
     cudaStream_t s = nullptr;
     int device = 0;
     int64_t n = 0;
@@ -171,7 +179,40 @@ cudaError_t dalloc(pic_handle* h, void** p, size_t bytes) {
     return e;
 }
 
+void free_timers(pic_handle* h) {
+    for (auto& t : h->kt) {
+        for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+        t.ev.clear();
+        t.used = 0;
+    }
+}
+
+// Brackets one launch group with the next event pair of a timer (when timing is on and
+// a pair is left); the stop event is recorded when the scope ends, early returns included.
+class TimedScope {
+  public:
+    TimedScope(pic_handle* h, int which) {
+        if (!h->ktiming) return;
+        auto& t = h->kt[which];
+        if (t.used >= h->kt_cap || 2 * (t.used + 1) > (int64_t)t.ev.size()) return;
+        stop_ = t.ev[2 * t.used + 1];
+        s_ = h->s;
+        cudaEventRecord(t.ev[2 * t.used], s_);
+        ++t.used;
+    }
+    ~TimedScope() {
+        if (stop_) cudaEventRecord(stop_, s_);
+    }
+    TimedScope(const TimedScope&) = delete;
+    TimedScope& operator=(const TimedScope&) = delete;
+
+  private:
+    cudaEvent_t stop_ = nullptr;
+    cudaStream_t s_ = nullptr;
+};
+
 void free_all(pic_handle* h) {
+    free_timers(h);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
 }
@@ -543,11 +584,13 @@ pic_status pic_deposit(pic_handle* h) {
     if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_deposit: the previous step is not finished");
     h->launches_now = 0;
     if (h->sorting && h->step % h->cfg.sort_interval == 0) {
+        TimedScope ts(h, PIC_KT_SORT);
         pic_status st = sort_particles(h);
         if (st != PIC_OK) return st;
     }
     CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
     h->launches_now += 1;
+    TimedScope ts(h, PIC_KT_DEPOSIT);
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
         if (h->sorting && h->fp32)
@@ -574,6 +617,7 @@ pic_status pic_field_solve(pic_handle* h) {
     h->mc.diag = h->diag_now ? 1 : 0;
     if (h->diag_now) CK(cudaMemsetAsync(h->diag, 0, D_NSLOTS * sizeof(double), h->s));
     const bool fused = field_columns_smem(h->nx, 2 * h->rsz) <= kFieldColumnsSmemMax;
+    TimedScope ts(h, PIC_KT_FIELD);
 
     // forward transform along y (the FP32 form converts the fixed-point sums on load)
     if (h->fp32) {
@@ -649,13 +693,23 @@ pic_status pic_gather_push(pic_handle* h) {
     PushParams pp = h->push;
     pp.diag = h->diag_now ? 1 : 0;
     const int vo = 1 - h->vcur;
-    CK(by_prec(h, [&](auto t) {
-        using T = decltype(t);
-        return launch_gather_push<T>(h->p, h->geom, pp, (const T*)h->x, (const T*)h->y,
-                                     (T*)h->px, (T*)h->py, (const T*)h->v[h->vcur][0],
-                                     (const T*)h->v[h->vcur][1], (T*)h->v[vo][0], (T*)h->v[vo][1],
-                                     h->n, h->G, h->diag, h->err, h->s);
-    }));
+    if (h->sorting && h->fp32) {
+        TimedScope ts(h, PIC_KT_GATHER);
+        CK(launch_gather_push_tiled(h->p, h->geom, pp, h->tg, (const float*)h->x,
+                                    (const float*)h->y, (float*)h->px, (float*)h->py,
+                                    (const float*)h->v[h->vcur][0], (const float*)h->v[h->vcur][1],
+                                    (float*)h->v[vo][0], (float*)h->v[vo][1], h->n, h->off, h->G,
+                                    h->diag, h->err, h->s));
+    } else {
+        TimedScope ts(h, PIC_KT_GATHER);
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_gather_push<T>(h->p, h->geom, pp, (const T*)h->x, (const T*)h->y,
+                                         (T*)h->px, (T*)h->py, (const T*)h->v[h->vcur][0],
+                                         (const T*)h->v[h->vcur][1], (T*)h->v[vo][0],
+                                         (T*)h->v[vo][1], h->n, h->G, h->diag, h->err, h->s);
+        }));
+    }
     h->vcur = vo;
     h->launches_now += 1;
     h->launches_last = h->launches_now;
@@ -817,6 +871,49 @@ int32_t pic_kernels_per_step(const pic_handle* h) {
 
 const char* pic_last_error(const pic_handle* h) {
     return h ? h->errmsg.c_str() : g_init_error.c_str();
+}
+
+pic_status pic_set_kernel_timing(pic_handle* h, int32_t max_launches) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (max_launches < 0 || max_launches > (1 << 20))
+        return fail(h, PIC_ERR_INVALID_ARG, "max_launches must be in 0..2^20");
+    if (max_launches == 0) {
+        h->ktiming = false;
+        return PIC_OK;
+    }
+    CK(cudaStreamSynchronize(h->s));  // no recorded pair is still pending
+    for (auto& t : h->kt) {
+        t.used = 0;
+        while ((int64_t)t.ev.size() < 2 * (int64_t)max_launches) {
+            cudaEvent_t e;
+            const cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) {
+                h->ktiming = false;
+                return fail(h, PIC_ERR_CUDA, "kernel timing: %s", cudaGetErrorString(r));
+            }
+            t.ev.push_back(e);
+        }
+    }
+    h->kt_cap = max_launches;
+    h->ktiming = true;
+    return PIC_OK;
+}
+
+pic_status pic_kernel_time(pic_handle* h, int32_t which, double* total_ms, int64_t* launches) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (which < 0 || which >= PIC_KT_COUNT || !total_ms || !launches)
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown timer or NULL output");
+    CK(cudaStreamSynchronize(h->s));
+    const auto& t = h->kt[which];
+    double sum = 0.0;
+    for (int64_t i = 0; i < t.used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]));
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = t.used;
+    return PIC_OK;
 }
 
 void pic_destroy(pic_handle* h) {

@@ -30,6 +30,7 @@ FP64, FP32_FIX64 = 0, 1
 FIELDS = {"jx": 0, "jy": 1, "rho": 2, "phi": 3, "ax": 4, "ay": 5, "bz": 6, "ex": 7, "ey": 8,
           "dphidx": 9, "dphidy": 10, "gax": 11, "gay": 12, "daxdx": 13, "daxdy": 14,
           "daydx": 15, "daydy": 16}
+KERNEL_TIMERS = {"sort": 0, "deposit": 1, "field_solve": 2, "gather_push": 3}
 
 
 class PicError(RuntimeError):
@@ -96,6 +97,8 @@ def load_library(path=LIB_PATH):
         "pic_sync": ([vp], i32),
         "pic_step_count": ([vp], i64),
         "pic_kernels_per_step": ([vp], i32),
+        "pic_set_kernel_timing": ([vp, i32], i32),
+        "pic_kernel_time": ([vp, i32, dp, ctypes.POINTER(i64)], i32),
         "pic_last_error": ([vp], ctypes.c_char_p),
         "pic_destroy": ([vp], None),
     }
@@ -211,6 +214,18 @@ class Simulation:
     @property
     def kernels_per_step(self):
         return int(self.lib.pic_kernels_per_step(self.h))
+
+    def set_kernel_timing(self, max_launches):
+        """Start (max_launches > 0) or stop (0) the library's per-kernel event timers."""
+        self._check(self.lib.pic_set_kernel_timing(self.h, max_launches))
+
+    def kernel_time(self, which):
+        """(total milliseconds, timed launches) of timer `which` (see KERNEL_TIMERS)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.pic_kernel_time(self.h, KERNEL_TIMERS[which], ctypes.byref(ms),
+                                             ctypes.byref(n)))
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -106,4 +106,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pic_step(None, 1) == 1
     assert lib.pic_sync(None) == 1
     assert lib.pic_step_count(None) == -1
+    assert lib.pic_set_kernel_timing(None, 8) == 1
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    assert lib.pic_kernel_time(None, 0, ctypes.byref(ms), ctypes.byref(n)) == 1
     lib.pic_destroy(None)

@@ -187,3 +187,28 @@ def test_fp32_tile_sort_is_bitwise_identical_to_unsorted(device, make, sort, nst
     assert sorted_.kernels_per_step >= 5
     plain.close()
     sorted_.close()
+
+
+def test_kernel_timers_count_the_launches_they_bracket(device):
+    # sort every 4 steps: a sort at steps 0, 4, 8 of 10; every step one deposit, one
+    # field solve and one gather; launches beyond the reserved pairs go untimed
+    wl = workloads.weibel(32, 32, 8, 0.5, 0.01, 96, 3)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                          precision=pic.FP32_FIX64, sort_interval=4, stepper="bdf", bdf_order=2)
+    with pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device) as sim:
+        sim.set_kernel_timing(16)
+        sim.step(10)
+        got = {k: sim.kernel_time(k) for k in pic.KERNEL_TIMERS}
+        assert {k: v[1] for k, v in got.items()} == {
+            "sort": 3, "deposit": 10, "field_solve": 10, "gather_push": 10}
+        assert all(v[0] > 0 for v in got.values()), got
+        sim.set_kernel_timing(4)  # restart with fewer pairs than launches
+        sim.step(6)
+        assert sim.kernel_time("deposit")[1] == 4
+        sim.set_kernel_timing(0)
+        sim.step(1)
+        assert sim.kernel_time("deposit")[1] == 4
+        with pytest.raises(pic.PicError):
+            sim.set_kernel_timing(-1)
+        with pytest.raises(KeyError):
+            sim.kernel_time("fft")
