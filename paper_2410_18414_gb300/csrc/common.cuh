@@ -59,6 +59,21 @@ template <typename C> __device__ __forceinline__ void zstore(C* p, zd v) {
     *p = w;
 }
 
+// ------------------------------------------------------------ launch chain ---
+//
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic stream-serialization attribute (launch_pdl) may start while the kernel
+// before it in the stream is still running.  griddep_wait() blocks until that kernel
+// has completed and its writes are visible; griddep_launch() allows the next kernel to
+// start launching.  Every kernel of the step calls griddep_launch() only after its own
+// griddep_wait(), so when a kernel starts, all kernels but its immediate predecessor
+// have completed: before its wait it may read what those earlier kernels wrote, and it
+// writes nothing.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------ grid --------
 
 // Spectral wavenumber of index m on an n-point periodic grid of length L:

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "fft_device.cuh"
 #include "gpic_internal.h"
+#include "launch.cuh"
 
 namespace gpic {
 
@@ -35,6 +36,8 @@ k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, i
     C* b1 = b0 + lines * ny;
     const int i0 = blockIdx.x * rows;
     const size_t plane = (size_t)nx * ny;
+    griddep_wait();  // the input is the previous kernel's output
+    griddep_launch();
     for (int e = threadIdx.x; e < lines * ny; e += blockDim.x) {
         int l = e / ny, jj = e - l * ny;
         int b = l / rows, r = l - b * rows;
@@ -120,9 +123,8 @@ static cudaError_t fft_y_impl(const void* in, void* out, int nx, int ny, int nb,
     size_t smem = (size_t)rows * nb * per_line;
     cudaError_t e = set_smem(k_fft_y<T>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_y<T><<<nx / rows, kThreads, smem, s>>>((const C*)in, (C*)out, nx, ny, nb, rows, d,
-                                                 (const C*)tw, sign, interleave, fix_in, unscale);
-    return cudaGetLastError();
+    return launch_pdl(k_fft_y<T>, dim3(nx / rows), dim3(kThreads), smem, s, (const C*)in, (C*)out,
+                      nx, ny, nb, rows, d, (const C*)tw, sign, interleave, fix_in, unscale);
 }
 
 template <typename T>

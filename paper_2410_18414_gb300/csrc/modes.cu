@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "fft_device.cuh"
 #include "gpic_internal.h"
+#include "launch.cuh"
 
 namespace gpic {
 
@@ -326,6 +327,35 @@ k_mode(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
 // from the row-transformed current and transforms both along x, updates the modes of
 // its own column, and transforms that column's four packed outputs back along x, all
 // in shared memory; the caller finishes with the inverse transform along y.
+// L2 prefetch of the history entries of column j's modes (a hint: the L2 is coherent,
+// so it is safe while the previous kernel runs; the histories were written two or more
+// kernels back).
+__device__ __forceinline__ void prefetch_l2(const void* base, int idx) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const double2*>(base) + idx));
+}
+__device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const BdfParams& bp, int j) {
+    for (int i = threadIdx.x; i < mc.nx; i += blockDim.x) {
+        const int idx = i * mc.ny + j;
+        for (int d = 0; d < 2 * bp.k; ++d) {
+            prefetch_l2(bp.phi[d], idx);
+            prefetch_l2(bp.ax[d], idx);
+            prefetch_l2(bp.ay[d], idx);
+        }
+        for (int d = 0; d < bp.k; ++d) prefetch_l2(bp.rho[d], idx);
+    }
+}
+__device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const CdfParams& cp, int j) {
+    const void* const arr[10] = {cp.phi, cp.phi_prev, cp.rho, cp.rho_prev, cp.ax,
+                                 cp.ax_prev, cp.ay, cp.ay_prev, cp.jx_prev, cp.jy_prev};
+    for (int i = threadIdx.x; i < mc.nx; i += blockDim.x)
+        for (int a = 0; a < 10; ++a) prefetch_l2(arr[a], i * mc.ny + j);
+}
+__device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const DirkParams& dp, int j) {
+    const void* const arr[9] = {dp.phi, dp.vphi, dp.ax, dp.vax, dp.ay, dp.vay, dp.rho, dp.jx, dp.jy};
+    for (int i = threadIdx.x; i < mc.nx; i += blockDim.x)
+        for (int a = 0; a < 9; ++a) prefetch_l2(arr[a], i * mc.ny + j);
+}
+
 template <typename C, typename Params>
 __global__ void __launch_bounds__(kModeThreads)
 k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
@@ -338,6 +368,9 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     const int ncols = (jp == j) ? 1 : 2;  // column j, then its partner column
     C* bufA = reinterpret_cast<C*>(smem_raw);  // 4 lines of nx
     C* bufB = bufA + 4 * nx;                   // 4 lines of nx
+    prefetch_history(mc, prm, j);              // written two or more kernels back
+    griddep_wait();                            // z is the previous kernel's output
+    griddep_launch();
     for (int t = threadIdx.x; t < ncols * nx; t += blockDim.x) {
         const int c = t / nx, i = t - c * nx;
         bufA[t] = z[(size_t)i * ny + (c ? jp : j)];
@@ -452,9 +485,8 @@ cudaError_t launch_columns_generic(const ModeCommon& mc, const Params& prm, cons
                                               (int)smem);
         if (e2 != cudaSuccess) return e2;
     }
-    kern<<<mc.ny, kModeThreads, smem, s>>>(mc, prm, (const C*)z, (C*)f4, (C*)e, diag, fd,
-                                           (const C*)tw);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(mc.ny), dim3(kModeThreads), smem, s, mc, prm, (const C*)z,
+                      (C*)f4, (C*)e, diag, fd, (const C*)tw);
 }
 
 }  // namespace

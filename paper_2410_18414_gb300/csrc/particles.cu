@@ -15,6 +15,7 @@
 // particle is skipped and the non-finite bit of the device error word is set.
 #include "common.cuh"
 #include "gpic_internal.h"
+#include "launch.cuh"
 
 namespace gpic {
 
@@ -271,6 +272,8 @@ k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__
     __syncthreads();
     const int rounds = max_rounds;
     if (rounds == 0) return;  // empty tile (uniform for the CTA)
+    griddep_wait();  // particles and J come from the previous operations of the stream
+    griddep_launch();
     const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
     // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
     // [0, 2n), so one correction wraps each exactly (whatever the halo)
@@ -511,6 +514,8 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
     if (bj < 0) bj += g.ny;
     const int rx = tg.rx, ry = tg.ry;
     const float4* F4 = reinterpret_cast<const float4*>(F);
+    griddep_wait();  // the fields are the previous kernel's output
+    griddep_launch();
     for (int k = threadIdx.x; k < 2 * rx * ry; k += blockDim.x) {
         const int node = k >> 1;
         const int ri = node / ry, rj = node - ri * ry;
@@ -721,9 +726,10 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
     if (tg.rx * tg.pitch > kRegionCap || tg.ry > tg.pitch) return cudaErrorInvalidValue;
     const AccFix acc = AccFix::make(j, scale);
     const size_t smem = (size_t)4 * tg.rx * tg.pitch * sizeof(int);
-#define GPIC_TILED(PP)                                                                          \
-    k_move_deposit_tiled<T, PP><<<blocks, kThreads, smem, s>>>(typed<T>(g), tg, x, y, vx, vy, off, \
-                                                              nsplit, acc, err);
+#define GPIC_TILED(PP)                                                                     \
+    e = launch_pdl(k_move_deposit_tiled<T, PP>, dim3(blocks), dim3(kThreads), smem, s,        \
+                   typed<T>(g), tg, x, y, vx, vy, off, nsplit, acc, err);
+    cudaError_t e = cudaSuccess;
     switch (p) {
         case 2: GPIC_TILED(2) break;
         case 3: GPIC_TILED(3) break;
@@ -731,7 +737,7 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
         default: return cudaErrorInvalidValue;
     }
 #undef GPIC_TILED
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>
@@ -780,9 +786,9 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
             k_gather_push_tiled<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
         e = attr;                                                                              \
         if (e == cudaSuccess)                                                                  \
-            k_gather_push_tiled<PP><<<blocks, kThreads, smem, s>>>(                            \
-                typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo, vyo, off,    \
-                nsplit, (const float2*)f, diag, err);                                          \
+            e = launch_pdl(k_gather_push_tiled<PP>, dim3(blocks), dim3(kThreads), smem, s,     \
+                           typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo,   \
+                           vyo, off, nsplit, (const float2*)f, diag, err);                     \
     }
     switch (p) {
         case 2: GPIC_GTILED(2) break;
@@ -791,8 +797,7 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
         default: return cudaErrorInvalidValue;
     }
 #undef GPIC_GTILED
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>

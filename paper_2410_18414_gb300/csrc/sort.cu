@@ -11,6 +11,7 @@
 // the deposit can accumulate in shared memory and the gather reuses cached field tiles.
 #include "common.cuh"
 #include "gpic_internal.h"
+#include "launch.cuh"
 
 namespace gpic {
 
@@ -49,6 +50,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_sort_keys(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             int* __restrict__ keys, int* __restrict__ hist) {
+    griddep_wait();
+    griddep_launch();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += stride) {  // warp-uniform
         const int64_t p = b + threadIdx.x;
@@ -97,6 +100,8 @@ k_scan_local(const int* __restrict__ hist, int nkeys, int* __restrict__ off,
              int* __restrict__ bsum) {
     __shared__ int warp_sums[33];
     const int i0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+    griddep_wait();
+    griddep_launch();
     int v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = i0 + j < nkeys ? hist[i0 + j] : 0;
@@ -115,6 +120,8 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan_add(int nkeys, int nchunks, const int* __restrict__ bsum, int* __restrict__ off,
            int* __restrict__ cursor) {
     __shared__ int warp_sums[33];
+    griddep_wait();
+    griddep_launch();
     int s = 0;
     for (int c = threadIdx.x; c < blockIdx.x; c += blockDim.x) s += bsum[c];
     int total;
@@ -138,6 +145,8 @@ k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ key
                int* __restrict__ cursor) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * kScatterPer + threadIdx.x;
+    griddep_wait();
+    griddep_launch();
     int k[kScatterPer], slot[kScatterPer], leader[kScatterPer];
     unsigned peers[kScatterPer];
 #pragma unroll
@@ -188,14 +197,20 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
         if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
         return e;
     }
-    k_sort_keys<T><<<blocks_for(n), kThreads, 0, s>>>(tg, src.a[0], src.a[1], n, keys, hist);
+    e = launch_pdl(k_sort_keys<T>, dim3(blocks_for(n)), dim3(kThreads), 0, s, tg,
+                   (const T*)src.a[0], (const T*)src.a[1], n, keys, hist);
     const int nchunks = sort_scan_chunks(nkeys);
-    k_scan_local<<<nchunks, kScanThreads, 0, s>>>(hist, nkeys, off, bsum);
-    k_scan_add<<<nchunks, kScanThreads, 0, s>>>(nkeys, nchunks, bsum, off, cursor);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_scan_local, dim3(nchunks), dim3(kScanThreads), 0, s, (const int*)hist,
+                       nkeys, off, bsum);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_scan_add, dim3(nchunks), dim3(kScanThreads), 0, s, nkeys, nchunks,
+                       (const int*)bsum, off, cursor);
     const int64_t per_cta = (int64_t)kThreads * kScatterPer;
-    k_sort_scatter<T><<<(unsigned)((n + per_cta - 1) / per_cta), kThreads, 0, s>>>(src, dst, keys,
-                                                                                   n, cursor);
-    return cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_pdl(k_sort_scatter<T>, dim3((unsigned)((n + per_cta - 1) / per_cta)),
+                       dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor);
+    return e;
 }
 
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {
