@@ -28,7 +28,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, int ny, int nb,
         int rows, FftDesc d, const cplx_t<T>* __restrict__ tw, int sign, int interleave,
-        const longlong2* __restrict__ fix_in, double unscale) {
+        const longlong2* __restrict__ fix_in, double unscale, longlong2* __restrict__ clear) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* b0 = reinterpret_cast<C*>(smem_raw);
@@ -44,6 +44,7 @@ k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, i
         const size_t src = b * plane + (size_t)(i0 + r) * ny + jj;
         if (fix_in) {  // fixed-point current sums, converted on load
             const longlong2 v = fix_in[src];
+            if (clear) clear[src] = longlong2{0, 0};  // the other buffer, for the next deposit
             b0[e] = mk<C>((double)v.x * unscale, (double)v.y * unscale);
         } else {
             b0[e] = in[src];
@@ -112,7 +113,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename T>
 static cudaError_t fft_y_impl(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
                               const void* tw, int sign, int interleave, const longlong2* fix_in,
-                              double unscale, cudaStream_t s) {
+                              double unscale, longlong2* clear, cudaStream_t s) {
     using C = cplx_t<T>;
     const size_t per_line = 2 * (size_t)ny * sizeof(C);
     // few lines per CTA: these transforms are latency-bound, so favour CTAs (one row of
@@ -124,19 +125,20 @@ static cudaError_t fft_y_impl(const void* in, void* out, int nx, int ny, int nb,
     cudaError_t e = set_smem(k_fft_y<T>, smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fft_y<T>, dim3(nx / rows), dim3(kThreads), smem, s, (const C*)in, (C*)out,
-                      nx, ny, nb, rows, d, (const C*)tw, sign, interleave, fix_in, unscale);
+                      nx, ny, nb, rows, d, (const C*)tw, sign, interleave, fix_in, unscale, clear);
 }
 
 template <typename T>
 cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
                          const void* tw, int sign, int interleave, cudaStream_t s) {
-    return fft_y_impl<T>(in, out, nx, ny, nb, d, tw, sign, interleave, nullptr, 0.0, s);
+    return fft_y_impl<T>(in, out, nx, ny, nb, d, tw, sign, interleave, nullptr, 0.0, nullptr, s);
 }
 
 template <typename T>
 cudaError_t launch_fft_y_from_fix(const longlong2* j, double unscale, void* out, int nx, int ny,
-                                  const FftDesc& d, const void* tw, cudaStream_t s) {
-    return fft_y_impl<T>(nullptr, out, nx, ny, 1, d, tw, -1, 0, j, unscale, s);
+                                  const FftDesc& d, const void* tw, longlong2* clear,
+                                  cudaStream_t s) {
+    return fft_y_impl<T>(nullptr, out, nx, ny, 1, d, tw, -1, 0, j, unscale, clear, s);
 }
 
 template <typename T>
@@ -172,9 +174,11 @@ template cudaError_t launch_fft_x<double>(const void*, void*, int, int, int, con
 template cudaError_t launch_fft_x<float>(const void*, void*, int, int, int, const FftDesc&,
                                          const void*, int, cudaStream_t);
 template cudaError_t launch_fft_y_from_fix<double>(const longlong2*, double, void*, int, int,
-                                                   const FftDesc&, const void*, cudaStream_t);
+                                                   const FftDesc&, const void*, longlong2*,
+                                                   cudaStream_t);
 template cudaError_t launch_fft_y_from_fix<float>(const longlong2*, double, void*, int, int,
-                                                  const FftDesc&, const void*, cudaStream_t);
+                                                  const FftDesc&, const void*, longlong2*,
+                                                  cudaStream_t);
 template cudaError_t launch_twiddles<double>(void*, int, cudaStream_t);
 template cudaError_t launch_twiddles<float>(void*, int, cudaStream_t);
 

@@ -83,10 +83,12 @@ enum StepperKind { K_BDF = 0, K_CDF2 = 1, K_DIRK = 2 };
 template <typename T>
 cudaError_t launch_fft_y(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,
                          const void* twiddle, int sign, int out_interleave, cudaStream_t s);
-// Forward transform along y of the fixed-point current (converted on load).
+// Forward transform along y of the fixed-point current (converted on load); zeroes
+// `clear` (same shape, may be NULL) on the way, the buffer the next deposit sums into.
 template <typename T>
 cudaError_t launch_fft_y_from_fix(const longlong2* j, double unscale, void* out, int nx, int ny,
-                                  const FftDesc& d, const void* tw, cudaStream_t s);
+                                  const FftDesc& d, const void* tw, longlong2* clear,
+                                  cudaStream_t s);
 // Along x (stride ny).
 template <typename T>
 cudaError_t launch_fft_x(const void* in, void* out, int nx, int ny, int nb, const FftDesc& d,

@@ -51,6 +51,7 @@ struct pic_handle {
     int launches_now = 0, launches_last = 0;
     // grid buffers
     double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
+    double2* Jalt = nullptr; // FP32 form: the other int64 buffer, zeroed by the row transform
     // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
     float fix_scale_j = 0.f, fix_scale_q = 0.f;
     double fix_unscale_j = 0.0, fix_unscale_q = 0.0;
@@ -287,12 +288,17 @@ pic_status alloc_state(pic_handle* h) {
         CK(dalloc(h, (void**)&h->keys, ni));
         const size_t nt = (size_t)h->tg.nkeys() + 1;
         CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
+        CK(cudaMemsetAsync(h->hist, 0, nt * sizeof(int), h->s));  // kept zero by the sort's scan
         CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->bsum, sort_scan_chunks(h->tg.nkeys()) * sizeof(int)));
         CK(launch_iota(h->id, h->n, h->s));
     }
     CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
+    if (h->fp32) {
+        CK(dalloc(h, (void**)&h->Jalt, h->ng * sizeof(double2)));
+        CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));
+    }
     CK(dalloc(h, &h->Z, h->ng * cs));
     CK(dalloc(h, &h->F4, 4 * h->ng * cs));
     CK(dalloc(h, &h->G, 4 * h->ng * cs));
@@ -588,7 +594,13 @@ pic_status pic_deposit(pic_handle* h) {
         pic_status st = sort_particles(h);
         if (st != PIC_OK) return st;
     }
-    CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    if (h->fp32) {
+        // the buffer the previous field solve zeroed (a memset here would break the chain
+        // of dependent launches); J^n stays readable until then
+        std::swap(h->J, h->Jalt);
+    } else {
+        CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    }
     h->launches_now += 1;
     TimedScope ts(h, PIC_KT_DEPOSIT);
     CK(by_prec(h, [&](auto t) {
@@ -622,7 +634,7 @@ pic_status pic_field_solve(pic_handle* h) {
     // forward transform along y (the FP32 form converts the fixed-point sums on load)
     if (h->fp32) {
         CK(launch_fft_y_from_fix<float>((const longlong2*)h->J, h->fix_unscale_j, h->Z, h->nx,
-                                        h->ny, h->fy, h->twy, h->s));
+                                        h->ny, h->fy, h->twy, (longlong2*)h->Jalt, h->s));
     } else {
         CK(launch_fft_y<double>(h->J, h->Z, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s));
     }

@@ -94,17 +94,22 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* 
 }
 
 // Scan, pass 1: CTA b scans keys [b C, (b+1) C) locally (C = kScanChunk) into off and
-// stores the chunk total in bsum[b].
+// stores the chunk total in bsum[b].  It leaves the histogram zeroed for the next sort.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_local(const int* __restrict__ hist, int nkeys, int* __restrict__ off,
-             int* __restrict__ bsum) {
+k_scan_local(int* __restrict__ hist, int nkeys, int* __restrict__ off, int* __restrict__ bsum) {
     __shared__ int warp_sums[33];
     const int i0 = blockIdx.x * kScanChunk + 4 * threadIdx.x;
     griddep_wait();
     griddep_launch();
     int v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = i0 + j < nkeys ? hist[i0 + j] : 0;
+    for (int j = 0; j < 4; ++j) {
+        v[j] = 0;
+        if (i0 + j < nkeys) {
+            v[j] = hist[i0 + j];
+            hist[i0 + j] = 0;
+        }
+    }
     int total;
     int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], warp_sums, &total);
 #pragma unroll
@@ -191,18 +196,15 @@ template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int* keys, int* hist, int* off, int* cursor, int* bsum,
                              cudaStream_t s) {
+    // hist is all zero on entry: zeroed once at allocation, then by every scan
     const int nkeys = tg.nkeys();  // number of sort keys (cells, tile-major)
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * nkeys, s);
-    if (e != cudaSuccess || n == 0) {
-        if (e == cudaSuccess) e = cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
-        return e;
-    }
-    e = launch_pdl(k_sort_keys<T>, dim3(blocks_for(n)), dim3(kThreads), 0, s, tg,
+    if (n == 0) return cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
+    cudaError_t e = launch_pdl(k_sort_keys<T>, dim3(blocks_for(n)), dim3(kThreads), 0, s, tg,
                    (const T*)src.a[0], (const T*)src.a[1], n, keys, hist);
     const int nchunks = sort_scan_chunks(nkeys);
     if (e == cudaSuccess)
-        e = launch_pdl(k_scan_local, dim3(nchunks), dim3(kScanThreads), 0, s, (const int*)hist,
-                       nkeys, off, bsum);
+        e = launch_pdl(k_scan_local, dim3(nchunks), dim3(kScanThreads), 0, s, hist, nkeys, off,
+                       bsum);
     if (e == cudaSuccess)
         e = launch_pdl(k_scan_add, dim3(nchunks), dim3(kScanThreads), 0, s, nkeys, nchunks,
                        (const int*)bsum, off, cursor);
