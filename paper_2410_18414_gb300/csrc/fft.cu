@@ -34,6 +34,8 @@ k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, i
     C* b0 = reinterpret_cast<C*>(smem_raw);
     const int lines = nb * rows;
     C* b1 = b0 + lines * ny;
+    C* tws = b1 + lines * ny;  // twiddles, staged before the wait (they are constant)
+    stage_twiddles(tw, tws, ny);
     const int i0 = blockIdx.x * rows;
     const size_t plane = (size_t)nx * ny;
     griddep_wait();  // the input is the previous kernel's output
@@ -51,7 +53,7 @@ k_fft_y(const cplx_t<T>* __restrict__ in, cplx_t<T>* __restrict__ out, int nx, i
         }
     }
     __syncthreads();
-    C* res = run_passes(b0, b1, d, lines, tw, sign);
+    C* res = run_passes(b0, b1, d, lines, (const C*)tws, sign);
     if (interleave) {
         for (int e = threadIdx.x; e < lines * ny; e += blockDim.x) {
             int b = e % nb, t = e / nb;
@@ -116,12 +118,13 @@ static cudaError_t fft_y_impl(const void* in, void* out, int nx, int ny, int nb,
                               double unscale, longlong2* clear, cudaStream_t s) {
     using C = cplx_t<T>;
     const size_t per_line = 2 * (size_t)ny * sizeof(C);
+    const size_t tw_bytes = (size_t)ny * sizeof(C);
     // few lines per CTA: these transforms are latency-bound, so favour CTAs (one row of
     // all nb arrays each, or two rows when there is a single array)
     int rows = nb == 1 && nx % 2 == 0 ? 2 : 1;
-    if ((size_t)rows * nb * per_line > 200 * 1024) rows = 1;
-    if ((size_t)rows * nb * per_line > 200 * 1024) return cudaErrorInvalidValue;
-    size_t smem = (size_t)rows * nb * per_line;
+    if ((size_t)rows * nb * per_line + tw_bytes > 200 * 1024) rows = 1;
+    if ((size_t)rows * nb * per_line + tw_bytes > 200 * 1024) return cudaErrorInvalidValue;
+    size_t smem = (size_t)rows * nb * per_line + tw_bytes;
     cudaError_t e = set_smem(k_fft_y<T>, smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fft_y<T>, dim3(nx / rows), dim3(kThreads), smem, s, (const C*)in, (C*)out,

@@ -14,8 +14,13 @@
 
 namespace gpic {
 
-template <typename C>
-__device__ __forceinline__ void small_dft(C* a, int R, int sign) {
+// x / d for x < 2^16 by one multiply-high with m = ceil(2^32 / d) (m = 0: d = 1).
+__device__ __forceinline__ int fdiv(int x, unsigned m) {
+    return m ? (int)__umulhi((unsigned)x, m) : x;
+}
+
+template <int R, typename C>
+__device__ __forceinline__ void small_dft_r(C* a, int sign) {
     if (R == 2) {
         C t = a[0];
         a[0] = cadd(t, a[1]);
@@ -46,52 +51,60 @@ __device__ __forceinline__ void small_dft(C* a, int R, int sign) {
     }
 }
 
-template <typename C>
+// One radix-R pass of pass index f over `lines` lines.
+template <int R, typename C>
 __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst,
-                                              int n, int R, int Ns, int lines,
+                                              const FftDesc& d, int f, int lines,
                                               const C* __restrict__ tw, int sign) {
-    const int nr = n / R;
-    const int twstep = n / (Ns * R);
+    const int n = d.n, Ns = d.ns[f], nr = d.nr[f], twstep = d.twstep[f];
+    const unsigned m_nr = d.m_nr[f], m_ns = d.m_ns[f];
     for (int idx = threadIdx.x; idx < lines * nr; idx += blockDim.x) {
-        int line = idx / nr;
-        int j = idx - line * nr;
-        int k = j % Ns;
+        const int line = fdiv(idx, m_nr);
+        const int j = idx - line * nr;
+        const int q = fdiv(j, m_ns);
+        const int k = j - q * Ns;
         const C* s = src + line * n;
-        C a[4];
+        C a[R];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < R) a[r] = s[j + r * nr];
+        for (int r = 0; r < R; ++r) a[r] = s[j + r * nr];
+        if (k != 0) {
 #pragma unroll
-        for (int r = 1; r < 4; ++r) {
-            if (r < R && k != 0) {
-                C w = __ldg(tw + r * k * twstep);
+            for (int r = 1; r < R; ++r) {
+                C w = tw[r * k * twstep];
                 if (sign > 0) w.y = -w.y;
                 a[r] = cmul(a[r], w);
             }
         }
-        small_dft(a, R, sign);
-        int base = (j / Ns) * Ns * R + k;
-        C* d = dst + line * n;
+        small_dft_r<R>(a, sign);
+        C* o = dst + line * n + q * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < R) d[base + r * Ns] = a[r];
+        for (int r = 0; r < R; ++r) o[r * Ns] = a[r];
     }
 }
 
-// Runs all passes; returns the buffer that holds the result.
+// Copies the n twiddles to shared memory (all threads of the CTA; the caller syncs).
+// They are constant, so a kernel may do this before waiting on its predecessor.
+template <typename C>
+__device__ __forceinline__ void stage_twiddles(const C* __restrict__ tw, C* __restrict__ dst, int n) {
+    for (int m = threadIdx.x; m < n; m += blockDim.x) dst[m] = __ldg(tw + m);
+}
+
+// Runs all passes (tw may point to global or shared memory); returns the buffer that
+// holds the result.
 template <typename C>
 __device__ __forceinline__ C* run_passes(C* b0, C* b1, const FftDesc& d, int lines, const C* tw, int sign) {
     C* src = b0;
     C* dst = b1;
-    int Ns = 1;
     for (int f = 0; f < d.nf; ++f) {
-        int R = d.radix[f];
-        stockham_pass(src, dst, d.n, R, Ns, lines, tw, sign);
+        switch (d.radix[f]) {
+            case 4: stockham_pass<4>(src, dst, d, f, lines, tw, sign); break;
+            case 2: stockham_pass<2>(src, dst, d, f, lines, tw, sign); break;
+            default: stockham_pass<3>(src, dst, d, f, lines, tw, sign); break;
+        }
         __syncthreads();
         C* t = src;
         src = dst;
         dst = t;
-        Ns *= R;
     }
     return src;
 }

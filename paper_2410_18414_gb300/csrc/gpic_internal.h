@@ -12,10 +12,18 @@ constexpr int kMaxBdf = 6;
 constexpr int kMaxDirk = 4;
 
 // 1-D transform description: length n = prod(radix[0..nf-1]), radices in {2,3,4}.
+// Per pass f, precomputed on the host: Ns (product of the earlier radices), nr = n / R,
+// the twiddle stride n / (Ns R), and multipliers ceil(2^32 / d) that divide indices
+// below 2^16 exactly by d = nr or Ns with one multiply-high (0 when d = 1).
 struct FftDesc {
     int n;
     int nf;
     int radix[kMaxRadices];
+    int ns[kMaxRadices];
+    int nr[kMaxRadices];
+    int twstep[kMaxRadices];
+    unsigned m_nr[kMaxRadices];
+    unsigned m_ns[kMaxRadices];
 };
 
 // Diagnostic accumulators (device, FP64): sums of |.|^2 over modes and particles.
@@ -114,7 +122,7 @@ cudaError_t launch_mode_dirk(const ModeCommon& mc, const DirkParams& dp, const v
 // inverse transforms along x of the four outputs): one CTA per column, 8 lines of nx
 // complex values in shared memory.  `kind` is a StepperKind.
 inline size_t field_columns_smem(int nx, size_t complex_bytes) {
-    return 8 * (size_t)nx * complex_bytes;
+    return 9 * (size_t)nx * complex_bytes;  // two buffers of 4 lines, the twiddles
 }
 constexpr size_t kFieldColumnsSmemMax = 200 * 1024;
 template <typename T>

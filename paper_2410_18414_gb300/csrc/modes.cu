@@ -34,6 +34,17 @@ namespace {
 
 constexpr int kModeThreads = 256;
 
+// Explicitly rounded complex operations for the values a step stores or outputs: the
+// per-mode update is compiled in more than one context (one or two threads per mode,
+// with or without diagnostics), and explicit roundings keep the compiler from fusing
+// products differently in each, so every context gives the same bits.
+__device__ __forceinline__ zd zscale(double s, zd a) {
+    return zd{__dmul_rn(s, a.re), __dmul_rn(s, a.im)};
+}
+__device__ __forceinline__ zd zfms(zd a, double c, zd b) {  // a - c b
+    return zd{__fma_rn(-c, b.re, a.re), __fma_rn(-c, b.im, a.im)};
+}
+
 struct ModeIn {
     int idx;  // i * ny + j
     double kx, ky, K;
@@ -49,10 +60,11 @@ __device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, 
     m.K = m.kx * m.kx + m.ky * m.ky;
     const zd b = zconj(zb);
     const double hs = 0.5 * mc.jscale;
-    m.jx = hs * (za + b);
-    const zd d = za - b;  // = 2i Jy / jscale
-    m.jy = zd{hs * d.im, -hs * d.re};
-    m.divj = zi(m.kx * m.jx + m.ky * m.jy);
+    m.jx = zscale(hs, zd{__dadd_rn(za.re, b.re), __dadd_rn(za.im, b.im)});
+    const zd d = zd{__dsub_rn(za.re, b.re), __dsub_rn(za.im, b.im)};  // = 2i Jy / jscale
+    m.jy = zd{__dmul_rn(hs, d.im), __dmul_rn(-hs, d.re)};
+    m.divj = zi(zd{__fma_rn(m.ky, m.jy.re, __dmul_rn(m.kx, m.jx.re)),
+                   __fma_rn(m.ky, m.jy.im, __dmul_rn(m.kx, m.jx.im))});
     return m;
 }
 
@@ -74,17 +86,21 @@ __device__ __forceinline__ zd div2(double kx, double ky, zd ax, zd ay) {
 
 // (i kx - ky) u : the packed gradient (du/dx) + i (du/dy).
 __device__ __forceinline__ zd grad_packed(double kx, double ky, zd u) {
-    return zi(kx * u) - ky * u;
+    return zd{__fma_rn(-ky, u.re, __dmul_rn(-kx, u.im)), __fma_rn(-ky, u.im, __dmul_rn(kx, u.re))};
+}
+// s (ax + i ay)
+__device__ __forceinline__ zd packed_a(double s, zd ax, zd ay) {
+    return zd{__dmul_rn(s, __dsub_rn(ax.re, ay.im)), __dmul_rn(s, __dadd_rn(ax.im, ay.re))};
 }
 
 // The four packed output spectra of one mode, with the inverse-FFT factor 1/(nx ny).
 __device__ __forceinline__ void packed_outputs(const ModeCommon& mc, const ModeIn& m, zd phit,
                                                zd ax, zd ay, zd* out) {
     const double s = mc.inv_n;
-    out[0] = s * grad_packed(m.kx, m.ky, phit);
-    out[1] = s * (ax + zi(ay));
-    out[2] = s * grad_packed(m.kx, m.ky, ax);
-    out[3] = s * grad_packed(m.kx, m.ky, ay);
+    out[0] = zscale(s, grad_packed(m.kx, m.ky, phit));
+    out[1] = packed_a(s, ax, ay);
+    out[2] = zscale(s, grad_packed(m.kx, m.ky, ax));
+    out[3] = zscale(s, grad_packed(m.kx, m.ky, ay));
 }
 
 // Block-wide sum of D_NSLOTS accumulators, then one atomicAdd per slot (256 threads).
@@ -122,23 +138,39 @@ __device__ __forceinline__ void hstore(void* p, int idx, zd v) {
 
 // ---------------------------------------------------------------- BDF-k ----
 
+// The BDF-k recurrences of one mode: continuity and the phi wave update; the A wave
+// updates.
+__device__ __forceinline__ void bdf_rho_phi(const ModeCommon& mc, const BdfParams& bp,
+                                            const ModeIn& m, zd& rho_new, zd& phi_new) {
+    const int idx = m.idx, k = bp.k;
+    rho_new = zscale(-bp.bdt, m.divj);
+    for (int d = 1; d <= k; ++d) rho_new = zfms(rho_new, bp.a[d], hload(bp.rho[d - 1], idx));
+    rho_new = zscale(1.0 / bp.a[0], rho_new);
+    zd sphi = zscale(bp.g / mc.eps0, rho_new);
+    for (int d = 1; d <= 2 * k; ++d) sphi = zfms(sphi, bp.C[d], hload(bp.phi[d - 1], idx));
+    phi_new = zscale(mc.invd[idx], sphi);  // 1/(C_0 + g K)
+}
+__device__ __forceinline__ void bdf_a(const ModeCommon& mc, const BdfParams& bp, const ModeIn& m,
+                                      zd& ax_new, zd& ay_new) {
+    const int idx = m.idx, k = bp.k;
+    zd sax = zscale(bp.g * mc.mu0, m.jx);
+    zd say = zscale(bp.g * mc.mu0, m.jy);
+    for (int d = 1; d <= 2 * k; ++d) {
+        sax = zfms(sax, bp.C[d], hload(bp.ax[d - 1], idx));
+        say = zfms(say, bp.C[d], hload(bp.ay[d - 1], idx));
+    }
+    const double inv = mc.invd[idx];
+    ax_new = zscale(inv, sax);
+    ay_new = zscale(inv, say);
+}
+
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParams& bp,
                                             const ModeIn& m, double* acc, C* epk, zd* out) {
     const int idx = m.idx, k = bp.k;
-    zd rho_new = -bp.bdt * m.divj;
-    for (int d = 1; d <= k; ++d) rho_new = rho_new - bp.a[d] * hload(bp.rho[d - 1], idx);
-    rho_new = (1.0 / bp.a[0]) * rho_new;
-    const double inv = mc.invd[idx];  // 1/(C_0 + g K)
-    zd sphi = (bp.g / mc.eps0) * rho_new;
-    zd sax = (bp.g * mc.mu0) * m.jx;
-    zd say = (bp.g * mc.mu0) * m.jy;
-    for (int d = 1; d <= 2 * k; ++d) {
-        sphi = sphi - bp.C[d] * hload(bp.phi[d - 1], idx);
-        sax = sax - bp.C[d] * hload(bp.ax[d - 1], idx);
-        say = say - bp.C[d] * hload(bp.ay[d - 1], idx);
-    }
-    const zd phi_new = inv * sphi, ax_new = inv * sax, ay_new = inv * say;
+    zd rho_new, phi_new, ax_new, ay_new;
+    bdf_rho_phi(mc, bp, m, rho_new, phi_new);
+    bdf_a(mc, bp, m, ax_new, ay_new);
     if (mc.diag) {
         // section 3.2: gauge eps_1, continuity eps_2, and Gauss with
         // E^{n+1} = -grad phi^{n+1} - (1/(beta dt)) sum_j a_j A^{n+1-j}
@@ -368,6 +400,8 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     const int ncols = (jp == j) ? 1 : 2;  // column j, then its partner column
     C* bufA = reinterpret_cast<C*>(smem_raw);  // 4 lines of nx
     C* bufB = bufA + 4 * nx;                   // 4 lines of nx
+    C* tws = bufB + 4 * nx;                    // twiddles (constant: staged before the wait)
+    stage_twiddles(tw, tws, nx);
     prefetch_history(mc, prm, j);              // written two or more kernels back
     griddep_wait();                            // z is the previous kernel's output
     griddep_launch();
@@ -376,7 +410,7 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
         bufA[t] = z[(size_t)i * ny + (c ? jp : j)];
     }
     __syncthreads();
-    C* zc = run_passes(bufA, bufB, fd, ncols, tw, -1);  // forward along x
+    C* zc = run_passes(bufA, bufB, fd, ncols, (const C*)tws, -1);  // forward along x
     C* out = (zc == bufA) ? bufB : bufA;               // the other buffer
     const C* zp = zc + (ncols - 1) * nx;               // partner column
     double acc[D_NSLOTS];
@@ -391,7 +425,7 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
         for (int f = 0; f < 4; ++f) zstore(out + f * nx + i, o[f]);
     }
     __syncthreads();
-    C* res = run_passes(out, zc, fd, 4, tw, +1);  // inverse along x
+    C* res = run_passes(out, zc, fd, 4, (const C*)tws, +1);  // inverse along x
     const size_t N = (size_t)nx * ny;
     for (int t = threadIdx.x; t < 4 * nx; t += blockDim.x) {
         const int f = t / nx, i = t - f * nx;

@@ -114,7 +114,21 @@ bool factor_23(int n, FftDesc& d) {
     while (m % 4 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 4; m /= 4; }
     while (m % 2 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 2; m /= 2; }
     while (m % 3 == 0 && d.nf < kMaxRadices) { d.radix[d.nf++] = 3; m /= 3; }
-    return m == 1;
+    if (m != 1) return false;
+    auto magic = [](int div) -> unsigned {  // ceil(2^32 / div); 0 marks div = 1
+        return div == 1 ? 0u : (unsigned)(((1ull << 32) + div - 1) / div);
+    };
+    int Ns = 1;
+    for (int f = 0; f < d.nf; ++f) {
+        const int R = d.radix[f];
+        d.ns[f] = Ns;
+        d.nr[f] = n / R;
+        d.twstep[f] = n / (Ns * R);
+        d.m_nr[f] = magic(n / R);
+        d.m_ns[f] = magic(Ns);
+        Ns *= R;
+    }
+    return true;
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }

@@ -212,3 +212,37 @@ def test_kernel_timers_count_the_launches_they_bracket(device):
             sim.set_kernel_timing(-1)
         with pytest.raises(KeyError):
             sim.kernel_time("fft")
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_FIX64], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("stepper,kw", [("bdf", dict(bdf_order=2)), ("bdf", dict(bdf_order=3)),
+                                        ("cdf2", {})], ids=["bdf2", "bdf3", "cdf2"])
+def test_diagnostics_do_not_change_the_trajectory(device, precision, stepper, kw):
+    # diagnosed steps take a different (one thread per mode) path through the per-mode
+    # update; the arithmetic must be the same.  The FP32 form sums the current in
+    # integers, so its trajectories are bitwise equal; the FP64 path sums it with FP64
+    # atomics in no fixed order, so two of its runs agree to roundoff only.
+    wl = workloads.weibel(48, 32, 8, 0.5, 0.01, 97, 3)
+    sims = []
+    for diag in (0, 3):
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                              precision=precision, stepper=stepper, **kw)
+        sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device)
+        if diag:
+            sim.set_diagnostics(diag)
+        sim.step(7)
+        sims.append(sim)
+    a, b = sims[0].particles(), sims[1].particles()
+    fields = [(sims[0].field(f), sims[1].field(f)) for f in ("phi", "ax", "ay", "rho", "daxdy")]
+    if precision == pic.FP32_FIX64:
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+        for u, v in fields:
+            assert np.array_equal(u, v)
+    else:
+        for k in a:
+            assert rel(a[k], b[k]) < 1e-13, k
+        for u, v in fields:
+            assert rel(u, v) < 1e-12
+    for s in sims:
+        s.close()
