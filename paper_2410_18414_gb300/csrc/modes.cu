@@ -68,6 +68,30 @@ __device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, 
     return m;
 }
 
+__device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, double2 za,
+                                            double2 zb) {
+    return make_mode(mc, i, j, zd{za.x, za.y}, zd{zb.x, zb.y});
+}
+// FP32 form: Jx, Jy unpacked in FP32 (the transforms are FP32) and converted exactly;
+// div J is then formed in FP64 from those same values, so the continuity and gauge
+// identities of the FP64 recurrences hold to FP64 roundoff.
+__device__ __forceinline__ ModeIn make_mode(const ModeCommon& mc, int i, int j, float2 za,
+                                            float2 zb) {
+    ModeIn m;
+    m.idx = i * mc.ny + j;
+    m.kx = mc.kxt[i];
+    m.ky = mc.kyt[j];
+    m.K = m.kx * m.kx + m.ky * m.ky;
+    const float hs = (float)(0.5 * mc.jscale);
+    const float2 b = make_float2(zb.x, -zb.y);
+    m.jx = zd{__fmul_rn(hs, __fadd_rn(za.x, b.x)), __fmul_rn(hs, __fadd_rn(za.y, b.y))};
+    const float dre = __fsub_rn(za.x, b.x), dim = __fsub_rn(za.y, b.y);  // 2i Jy / jscale
+    m.jy = zd{__fmul_rn(hs, dim), __fmul_rn(-hs, dre)};
+    m.divj = zi(zd{__fma_rn(m.ky, m.jy.re, __dmul_rn(m.kx, m.jx.re)),
+                   __fma_rn(m.ky, m.jy.im, __dmul_rn(m.kx, m.jx.im))});
+    return m;
+}
+
 template <typename C>
 __device__ __forceinline__ ModeIn mode_from_global(const ModeCommon& mc, const C* z, int idx) {
     const int i = idx / mc.ny, j = idx - i * mc.ny;
@@ -77,7 +101,7 @@ __device__ __forceinline__ ModeIn mode_from_global(const ModeCommon& mc, const C
         ModeIn m = make_mode(mc, i, j, zd{0, 0}, zd{0, 0});
         return m;
     }
-    return make_mode(mc, i, j, zload(z + idx), zload(z + (ip * mc.ny + jp)));
+    return make_mode(mc, i, j, z[idx], z[ip * mc.ny + jp]);
 }
 
 __device__ __forceinline__ zd div2(double kx, double ky, zd ax, zd ay) {
@@ -93,14 +117,31 @@ __device__ __forceinline__ zd packed_a(double s, zd ax, zd ay) {
     return zd{__dmul_rn(s, __dsub_rn(ax.re, ay.im)), __dmul_rn(s, __dadd_rn(ax.im, ay.re))};
 }
 
-// The four packed output spectra of one mode, with the inverse-FFT factor 1/(nx ny).
+// The four packed output spectra of one mode, with the inverse-FFT factor 1/(nx ny):
+// (i kx - ky) phi, ax + i ay, (i kx - ky) ax, (i kx - ky) ay.  FP64 for the FP64 form;
+// FP32 from the FP64 fields for the FP32 form, whose transforms and gather are FP32.
 __device__ __forceinline__ void packed_outputs(const ModeCommon& mc, const ModeIn& m, zd phit,
-                                               zd ax, zd ay, zd* out) {
+                                               zd ax, zd ay, double2* out) {
     const double s = mc.inv_n;
-    out[0] = zscale(s, grad_packed(m.kx, m.ky, phit));
-    out[1] = packed_a(s, ax, ay);
-    out[2] = zscale(s, grad_packed(m.kx, m.ky, ax));
-    out[3] = zscale(s, grad_packed(m.kx, m.ky, ay));
+    const zd o[4] = {zscale(s, grad_packed(m.kx, m.ky, phit)), packed_a(s, ax, ay),
+                     zscale(s, grad_packed(m.kx, m.ky, ax)), zscale(s, grad_packed(m.kx, m.ky, ay))};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[f] = make_double2(o[f].re, o[f].im);
+}
+__device__ __forceinline__ float2 grad_packed_f(float s, float kx, float ky, float2 u) {
+    return make_float2(__fmul_rn(s, __fmaf_rn(-ky, u.x, __fmul_rn(-kx, u.y))),
+                       __fmul_rn(s, __fmaf_rn(-ky, u.y, __fmul_rn(kx, u.x))));
+}
+__device__ __forceinline__ void packed_outputs(const ModeCommon& mc, const ModeIn& m, zd phit,
+                                               zd ax, zd ay, float2* out) {
+    const float s = (float)mc.inv_n, kx = (float)m.kx, ky = (float)m.ky;
+    const float2 p = make_float2((float)phit.re, (float)phit.im);
+    const float2 a = make_float2((float)ax.re, (float)ax.im);
+    const float2 b = make_float2((float)ay.re, (float)ay.im);
+    out[0] = grad_packed_f(s, kx, ky, p);
+    out[1] = make_float2(__fmul_rn(s, __fsub_rn(a.x, b.y)), __fmul_rn(s, __fadd_rn(a.y, b.x)));
+    out[2] = grad_packed_f(s, kx, ky, a);
+    out[3] = grad_packed_f(s, kx, ky, b);
 }
 
 // Block-wide sum of D_NSLOTS accumulators, then one atomicAdd per slot (256 threads).
@@ -166,7 +207,7 @@ __device__ __forceinline__ void bdf_a(const ModeCommon& mc, const BdfParams& bp,
 
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParams& bp,
-                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+                                            const ModeIn& m, double* acc, C* epk, C* out) {
     const int idx = m.idx, k = bp.k;
     zd rho_new, phi_new, ax_new, ay_new;
     bdf_rho_phi(mc, bp, m, rho_new, phi_new);
@@ -208,7 +249,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParam
 
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParams& cp,
-                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+                                            const ModeIn& m, double* acc, C* epk, C* out) {
     const int idx = m.idx;
     const double dt = mc.dt;
     const double th = 0.5 * mc.c * mc.c * dt * dt;
@@ -280,7 +321,7 @@ __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double
 
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkParams& dp,
-                                            const ModeIn& m, double* acc, C* epk, zd* out) {
+                                            const ModeIn& m, double* acc, C* epk, C* out) {
     const int idx = m.idx;
     const double h = mc.dt;
     const zd phi = hload(dp.phi, idx), vphi = hload(dp.vphi, idx);
@@ -345,11 +386,11 @@ k_mode(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restrict__ f4,
     for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
     if (idx < nmodes) {
         const ModeIn m = mode_from_global(mc, z, idx);
-        zd out[4];
+        C out[4];
         mode_update(mc, prm, m, acc, epk, out);
         const size_t N = (size_t)nmodes;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) zstore(f4 + f * N + idx, out[f]);
+        for (int f = 0; f < 4; ++f) f4[f * N + idx] = out[f];
     }
     if (mc.diag) reduce_diag(acc, diag);
 }
@@ -418,11 +459,11 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = (i == 0) ? 0 : nx - i;
-        const ModeIn m = make_mode(mc, i, j, zload(zc + i), zload(zp + ip));
-        zd o[4];
+        const ModeIn m = make_mode(mc, i, j, zc[i], zp[ip]);
+        C o[4];
         mode_update(mc, prm, m, acc, epk, o);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) zstore(out + f * nx + i, o[f]);
+        for (int f = 0; f < 4; ++f) out[f * nx + i] = o[f];
     }
     __syncthreads();
     C* res = run_passes(out, zc, fd, 4, (const C*)tws, +1);  // inverse along x
