@@ -202,6 +202,7 @@ struct TileGeom {
     int nx, ny, t, ntx, nty, halo, rx, ry;
     int pitch;  // shared-memory row pitch of the region (>= ry, = t mod 32)
     double inv_dx, inv_dy;
+    double dt, lx, ly;  // the sort keys a particle by its position after this step's move
     int half;  // 1 for even spline degree: the stencil base cell is floor(x/dx + 1/2)
     // sort key of a particle: tile-major, then the stencil base cell inside the tile,
     // key = tile * t * t + (bx mod t) * t + (by mod t); nkeys = ntx * nty * t * t
@@ -217,9 +218,10 @@ struct SortArrays {
 };
 
 int sort_scan_chunks(int nkeys);  // chunk totals the scan keeps (size of its bsum array)
+// vidx: index in src.a of the x velocity this step's move uses (y velocity: vidx + 1).
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
-                             int* keys, int* hist, int* off, int* cursor, int* bsum,
+                             int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
                              cudaStream_t s);
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 

@@ -493,8 +493,9 @@ pic_status sort_particles(pic_handle* h) {
         }
         src.id = h->id;
         dst.id = h->id_alt;
-        return launch_tile_sort<T>(h->tg, src, dst, h->n, h->keys, h->hist, h->off, h->cursor,
-                                   h->bsum, h->s);
+        // cur[4 + 2 vcur] is v^n_x, the velocity of this step's move
+        return launch_tile_sort<T>(h->tg, src, dst, h->n, 4 + 2 * h->vcur, h->keys, h->hist,
+                                   h->off, h->cursor, h->bsum, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
@@ -564,6 +565,9 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         tg.pitch = tg.ry + ((tg.t - tg.ry % 32) % 32 + 32) % 32;
         tg.inv_dx = 1.0 / dx;
         tg.inv_dy = 1.0 / dy;
+        tg.dt = cfg->dt;
+        tg.lx = cfg->lx;
+        tg.ly = cfg->ly;
         tg.half = (cfg->spline_order % 2 == 0) ? 1 : 0;
     }
     if (h->fp32) {

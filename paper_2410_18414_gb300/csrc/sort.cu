@@ -48,16 +48,20 @@ __device__ __forceinline__ int tile_key(T x, T y, const TileGeom& tg) {
 // lanes of a warp mostly share a key: one lane adds the group's count (no return value).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_sort_keys(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+k_sort_keys(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y,
+            const T* __restrict__ vx, const T* __restrict__ vy, int64_t n,
             int* __restrict__ keys, int* __restrict__ hist) {
     griddep_wait();
     griddep_launch();
+    const T dt = (T)tg.dt, lx = (T)tg.lx, ly = (T)tg.ly;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += stride) {  // warp-uniform
         const int64_t p = b + threadIdx.x;
         int k = -1;
         if (p < n) {
-            k = tile_key(x[p], y[p], tg);
+            // the cell the particle will deposit from after this step's move, so that the
+            // step right after a sort sees no drift from the sorted cells
+            k = tile_key(move_pos(x[p], vx[p], dt, lx), move_pos(y[p], vy[p], dt, ly), tg);
             keys[p] = k;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, k);
@@ -194,13 +198,15 @@ int sort_scan_chunks(int nkeys) { return (nkeys + kScanChunk - 1) / kScanChunk; 
 
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
-                             int* keys, int* hist, int* off, int* cursor, int* bsum,
+                             int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
                              cudaStream_t s) {
+    if (vidx < 0 || vidx + 1 >= 8) return cudaErrorInvalidValue;
     // hist is all zero on entry: zeroed once at allocation, then by every scan
     const int nkeys = tg.nkeys();  // number of sort keys (cells, tile-major)
     if (n == 0) return cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
     cudaError_t e = launch_pdl(k_sort_keys<T>, dim3(blocks_for(n)), dim3(kThreads), 0, s, tg,
-                   (const T*)src.a[0], (const T*)src.a[1], n, keys, hist);
+                   (const T*)src.a[0], (const T*)src.a[1], (const T*)src.a[vidx],
+                   (const T*)src.a[vidx + 1], n, keys, hist);
     const int nchunks = sort_scan_chunks(nkeys);
     if (e == cudaSuccess)
         e = launch_pdl(k_scan_local, dim3(nchunks), dim3(kScanThreads), 0, s, hist, nkeys, off,
@@ -222,9 +228,10 @@ cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {
 }
 
 template cudaError_t launch_tile_sort<float>(const TileGeom&, SortArrays<float>, SortArrays<float>,
-                                             int64_t, int*, int*, int*, int*, int*, cudaStream_t);
+                                             int64_t, int, int*, int*, int*, int*, int*,
+                                             cudaStream_t);
 template cudaError_t launch_tile_sort<double>(const TileGeom&, SortArrays<double>,
-                                              SortArrays<double>, int64_t, int*, int*, int*, int*,
-                                              int*, cudaStream_t);
+                                              SortArrays<double>, int64_t, int, int*, int*, int*,
+                                              int*, int*, cudaStream_t);
 
 }  // namespace gpic
