@@ -218,19 +218,23 @@ struct SortArrays {
 };
 
 int sort_scan_chunks(int nkeys);  // chunk totals the scan keeps (size of its bsum array)
-// vidx: index in src.a of the x velocity this step's move uses (y velocity: vidx + 1).
+// vidx: index in src.a of the x velocity this step's move uses (4 or 6; y velocity:
+// vidx + 1).  p4 (may be NULL): receives (x, y, vx, vy) of each particle in the new
+// order, the packed input of the tiled deposit.
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
-                             cudaStream_t s);
+                             float4* p4, cudaStream_t s);
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 
 // Move + deposit over tile-sorted particles: CTA b takes particles [b*chunk, (b+1)*chunk)
 // and accumulates each tile segment in shared memory.  `fix` selects the int64
 // fixed-point accumulation (J is longlong2) with `scale`, else FP64 (J is double2).
 template <typename T>
+// p4: (x, y, vx, vy) of each particle in the sorted order (written by the last sort or
+// tiled gather); the moved positions go to x, y.
 cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const T* vx, const T* vy, int64_t n, const int* off,
+                                      T* y, const float4* p4, int64_t n, const int* off,
                                       void* j, bool fix, float scale, unsigned int* err,
                                       cudaStream_t s);
 
@@ -238,8 +242,9 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
                                     const TileGeom& tg, const float* x, const float* y, float* px,
                                     float* py, const float* vx, const float* vy, float* vx_old,
-                                    float* vy_old, int64_t n, const int* off, const void* fields4,
-                                    double* diag, unsigned int* err, cudaStream_t s);
+                                    float* vy_old, float4* p4, int64_t n, const int* off,
+                                    const void* fields4, double* diag, unsigned int* err,
+                                    cudaStream_t s);
 
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };

@@ -233,9 +233,8 @@ constexpr int kRegionCap = 2560;  // largest region (rx * pitch words), 40 KB fo
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads, 5)
 k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
-                     const T* __restrict__ vx, const T* __restrict__ vy,
-                     const int* __restrict__ off, int nsplit, AccFix acc,
-                     unsigned int* __restrict__ err) {
+                     const float4* __restrict__ p4, const int* __restrict__ off, int nsplit,
+                     AccFix acc, unsigned int* __restrict__ err) {
     // four arrays of R = rx * pitch words: lo_x, lo_y, hi_x, hi_y (sized to the region,
     // so that the rest of the L1 caches the scattered particle loads)
     extern __shared__ int sacc[];
@@ -248,10 +247,9 @@ k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__
     const int phases = blockDim.x / tt;   // threads per cell in this CTA
     const int phase = threadIdx.x / tt;
     const int key = tile * tt + cell;
-    if (threadIdx.x < 4) {  // the tile's particles come to L2 while the region is cleared
-        const T* arr[4] = {x, y, vx, vy};
+    if (threadIdx.x == 0) {  // the tile's particles come to L2 while the region is cleared
         const int64_t a0 = off[tile * tt], a1 = off[(tile + 1) * tt];
-        prefetch_l2(arr[threadIdx.x] + a0, (size_t)(a1 - a0) * sizeof(T));
+        prefetch_l2(p4 + a0, (size_t)(a1 - a0) * sizeof(float4));
     }
     const int o0 = off[key], count = off[key + 1] - o0;
     // split s takes the contiguous share [s count / nsplit, (s+1) count / nsplit) of the
@@ -285,9 +283,10 @@ k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__
     for (int r = 0; r < rounds; ++r) {
         if (r < mine) {
             const int64_t p = cbeg + (int64_t)r * streams;
-            const T vxi = vx[p], vyi = vy[p];
-            const T xp = move_pos(x[p], vxi, dt, lx);
-            const T yp = move_pos(y[p], vyi, dt, ly);
+            const float4 q4 = p4[p];  // one 16-byte load: x, y, vx, vy
+            const T vxi = (T)q4.z, vyi = (T)q4.w;
+            const T xp = move_pos((T)q4.x, vxi, dt, lx);
+            const T yp = move_pos((T)q4.y, vyi, dt, ly);
             x[p] = xp;
             y[p] = yp;
             const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
@@ -409,7 +408,7 @@ __device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t
                                          T* __restrict__ px, T* __restrict__ py,
                                          const T* __restrict__ vx, const T* __restrict__ vy,
                                          T* __restrict__ vxo, T* __restrict__ vyo, unsigned& bad,
-                                         double& kin) {
+                                         double& kin, T& vx_new, T& vy_new) {
     const T vsx = rfma((T)2, vx[p], -vxo[p]);
     const T vsy = rfma((T)2, vy[p], -vyo[p]);
     const T fx = rfma(f[6], vsy, rfma(f[4], vsx, -f[0]));
@@ -424,6 +423,8 @@ __device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t
     py[p] = Py;
     vxo[p] = vxn1;
     vyo[p] = vyn1;
+    vx_new = vxn1;
+    vy_new = vyn1;
     if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
     if (pp.diag) {  // m c^2 (gamma - 1) per unit weight, in FP64 for either storage type
         const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
@@ -476,7 +477,8 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
                 gather_node(rmul(wx[a], wy[b]), gv, f);
             }
         }
-        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin);
+        T vxn1, vyn1;
+        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
     }
     push_finish(pp, bad, kin, diag, err);
 }
@@ -495,9 +497,9 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
                     const float* __restrict__ y, float* __restrict__ px,
                     float* __restrict__ py, const float* __restrict__ vx,
                     const float* __restrict__ vy, float* __restrict__ vxo,
-                    float* __restrict__ vyo, const int* __restrict__ off, int nsplit,
-                    const float2* __restrict__ F, double* __restrict__ diag,
-                    unsigned int* __restrict__ err) {
+                    float* __restrict__ vyo, float4* __restrict__ p4,
+                    const int* __restrict__ off, int nsplit, const float2* __restrict__ F,
+                    double* __restrict__ diag, unsigned int* __restrict__ err) {
     extern __shared__ float4 sf[];  // [rx][ry] nodes, two float4 each
     const int tt = tg.t * tg.t;
     const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
@@ -529,7 +531,8 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
     double kin = 0.0;
     unsigned bad = 0;
     for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const float xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
+        const float xp = x[p], yp = y[p];
+        const float xi = rmul(xp, idx_), yj = rmul(yp, idy);
         if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
             bad |= ERR_NONFINITE;
             continue;
@@ -566,7 +569,9 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
                 }
             }
         }
-        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin);
+        float vxn1, vyn1;
+        push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
+        p4[p] = make_float4(xp, yp, vxn1, vyn1);  // the next deposit's packed input
     }
     push_finish(pp, bad, kin, diag, err);
 }
@@ -709,7 +714,7 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
 
 template <typename T>
 cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const T* vx, const T* vy, int64_t n, const int* off,
+                                      T* y, const float4* p4, int64_t n, const int* off,
                                       void* j, bool fix, float scale, unsigned int* err,
                                       cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -728,7 +733,7 @@ cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGe
     const size_t smem = (size_t)4 * tg.rx * tg.pitch * sizeof(int);
 #define GPIC_TILED(PP)                                                                     \
     e = launch_pdl(k_move_deposit_tiled<T, PP>, dim3(blocks), dim3(kThreads), smem, s,        \
-                   typed<T>(g), tg, x, y, vx, vy, off, nsplit, acc, err);
+                   typed<T>(g), tg, x, y, p4, off, nsplit, acc, err);
     cudaError_t e = cudaSuccess;
     switch (p) {
         case 2: GPIC_TILED(2) break;
@@ -767,8 +772,9 @@ cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& p
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
                                     const TileGeom& tg, const float* x, const float* y, float* px,
                                     float* py, const float* vx, const float* vy, float* vxo,
-                                    float* vyo, int64_t n, const int* off, const void* f,
-                                    double* diag, unsigned int* err, cudaStream_t s) {
+                                    float* vyo, float4* p4, int64_t n, const int* off,
+                                    const void* f, double* diag, unsigned int* err,
+                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     // splits per tile: about 2048 particles per CTA at the mean density (so that a grid of
     // 64-per-cell tiles is a single wave of four CTAs per SM)
@@ -788,7 +794,7 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
         if (e == cudaSuccess)                                                                  \
             e = launch_pdl(k_gather_push_tiled<PP>, dim3(blocks), dim3(kThreads), smem, s,     \
                            typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo,   \
-                           vyo, off, nsplit, (const float2*)f, diag, err);                     \
+                           vyo, p4, off, nsplit, (const float2*)f, diag, err);                 \
     }
     switch (p) {
         case 2: GPIC_GTILED(2) break;
@@ -870,7 +876,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
     template cudaError_t launch_fix_to_cplx<T>(const longlong2*, double, void*, int64_t,          \
                                                cudaStream_t);                                     \
     template cudaError_t launch_move_deposit_tiled<T>(int, const ParticleGeom&, const TileGeom&,  \
-                                                      T*, T*, const T*, const T*, int64_t,        \
+                                                      T*, T*, const float4*, int64_t,             \
                                                       const int*, void*, bool, float,             \
                                                       unsigned int*, cudaStream_t);
 GPIC_INST(double)

@@ -48,6 +48,9 @@ struct pic_handle {
     void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t *id = nullptr, *id_alt = nullptr;
     int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
+    // FP32 sorted path: (x, y, vx, vy) of each particle, the tiled deposit's input; written
+    // by every sort and every tiled gather, and a tiled deposit follows one of them
+    float4* p4 = nullptr;
     int launches_now = 0, launches_last = 0;
     // grid buffers
     double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
@@ -303,6 +306,7 @@ pic_status alloc_state(pic_handle* h) {
         const size_t nt = (size_t)h->tg.nkeys() + 1;
         CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
         CK(cudaMemsetAsync(h->hist, 0, nt * sizeof(int), h->s));  // kept zero by the sort's scan
+        if (h->fp32) CK(dalloc(h, (void**)&h->p4, (size_t)std::max<int64_t>(h->n, 1) * sizeof(float4)));
         CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->bsum, sort_scan_chunks(h->tg.nkeys()) * sizeof(int)));
@@ -495,7 +499,7 @@ pic_status sort_particles(pic_handle* h) {
         dst.id = h->id_alt;
         // cur[4 + 2 vcur] is v^n_x, the velocity of this step's move
         return launch_tile_sort<T>(h->tg, src, dst, h->n, 4 + 2 * h->vcur, h->keys, h->hist,
-                                   h->off, h->cursor, h->bsum, h->s);
+                                   h->off, h->cursor, h->bsum, h->fp32 ? h->p4 : nullptr, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
@@ -625,8 +629,7 @@ pic_status pic_deposit(pic_handle* h) {
         using T = decltype(t);
         if (h->sorting && h->fp32)
             return launch_move_deposit_tiled<T>(h->p, h->geom, h->tg, (T*)h->x, (T*)h->y,
-                                                (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
-                                                h->n, h->off, h->J, h->fp32,
+                                                h->p4, h->n, h->off, h->J, h->fp32,
                                                 h->fix_scale_j, h->err, h->s);
         if (h->fp32)
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
@@ -728,7 +731,8 @@ pic_status pic_gather_push(pic_handle* h) {
         CK(launch_gather_push_tiled(h->p, h->geom, pp, h->tg, (const float*)h->x,
                                     (const float*)h->y, (float*)h->px, (float*)h->py,
                                     (const float*)h->v[h->vcur][0], (const float*)h->v[h->vcur][1],
-                                    (float*)h->v[vo][0], (float*)h->v[vo][1], h->n, h->off, h->G,
+                                    (float*)h->v[vo][0], (float*)h->v[vo][1], h->p4, h->n,
+                                    h->off, h->G,
                                     h->diag, h->err, h->s));
     } else {
         TimedScope ts(h, PIC_KT_GATHER);

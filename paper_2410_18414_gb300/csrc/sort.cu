@@ -151,7 +151,7 @@ k_scan_add(int nkeys, int nchunks, const int* __restrict__ bsum, int* __restrict
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ keys, int64_t n,
-               int* __restrict__ cursor) {
+               int* __restrict__ cursor, float4* __restrict__ p4, int vidx) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * kScatterPer + threadIdx.x;
     griddep_wait();
@@ -179,9 +179,16 @@ k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ key
         const int64_t p = base + (int64_t)i * blockDim.x;
         if (k[i] >= 0) {
             const int q = slot[i];
+            T v[8];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) dst.a[a][q] = src.a[a][p];
+            for (int a = 0; a < 8; ++a) {
+                v[a] = src.a[a][p];
+                dst.a[a][q] = v[a];
+            }
             dst.id[q] = src.id[p];
+            if (p4)  // the deposit's packed input: position and the velocity of its move
+                p4[q] = make_float4((float)v[0], (float)v[1], (float)(vidx == 4 ? v[4] : v[6]),
+                                    (float)(vidx == 4 ? v[5] : v[7]));
         }
     }
 }
@@ -199,8 +206,8 @@ int sort_scan_chunks(int nkeys) { return (nkeys + kScanChunk - 1) / kScanChunk; 
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
-                             cudaStream_t s) {
-    if (vidx < 0 || vidx + 1 >= 8) return cudaErrorInvalidValue;
+                             float4* p4, cudaStream_t s) {
+    if (vidx != 4 && vidx != 6) return cudaErrorInvalidValue;
     // hist is all zero on entry: zeroed once at allocation, then by every scan
     const int nkeys = tg.nkeys();  // number of sort keys (cells, tile-major)
     if (n == 0) return cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
@@ -217,7 +224,7 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
     const int64_t per_cta = (int64_t)kThreads * kScatterPer;
     if (e == cudaSuccess)
         e = launch_pdl(k_sort_scatter<T>, dim3((unsigned)((n + per_cta - 1) / per_cta)),
-                       dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor);
+                       dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor, p4, vidx);
     return e;
 }
 
@@ -229,9 +236,9 @@ cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {
 
 template cudaError_t launch_tile_sort<float>(const TileGeom&, SortArrays<float>, SortArrays<float>,
                                              int64_t, int, int*, int*, int*, int*, int*,
-                                             cudaStream_t);
+                                             float4*, cudaStream_t);
 template cudaError_t launch_tile_sort<double>(const TileGeom&, SortArrays<double>,
                                               SortArrays<double>, int64_t, int, int*, int*, int*,
-                                              int*, int*, cudaStream_t);
+                                              int*, int*, float4*, cudaStream_t);
 
 }  // namespace gpic
