@@ -106,10 +106,10 @@ def bytes_move_deposit(rsz):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
 # captures (profiles/), keyed by (kernel, form); None when the kernel changed since.
 TRAFFIC = {
-    # ncu --set full, 3 launches of k_move_deposit_tiled<float,3> on the 128x128 Weibel
-    # workload: dram__bytes_read 17.15 MB + dram__bytes_write 0.27 MB (the x, y writes
-    # stay in L2 until after the kernel)
-    ("move_deposit", "fp32"): 17.42e6,
+    # ncu --set full, 2 launches of k_move_deposit_tiled<float,3> on the 128x128 Weibel
+    # workload: dram__bytes_read 18.28 MB + dram__bytes_write 1.15 MB (mean; most of the
+    # x, y writes are still in L2 when the kernel ends)
+    ("move_deposit", "fp32"): 19.43e6,
 }
 
 # Conflict-free 32-bit shared-memory atomicAdd throughput of the whole GPU, in warp
