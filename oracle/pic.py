@@ -304,8 +304,13 @@ def taylor_back_velocity(cfg, vx, vy, ex, ey):
     return vx - coef * (ex - vx * vdote / c2), vy - coef * (ey - vy * vdote / c2)
 
 
-def initial_state(cfg, x0, y0, vx0, vy0):
-    """t = 0 state for Algorithm 1 (readings listed in the module docstring)."""
+def initial_state(cfg, x0, y0, vx0, vy0, sample=None):
+    """t = 0 state for Algorithm 1 (readings listed in the module docstring).
+
+    sample: optional particle indices.  The grid quantities always come from every
+    particle; with a sample, the particle arrays of the state (and the Taylor start) are
+    those of the sampled particles only, each equal to its value without sampling.
+    """
     x0 = wrap(np.asarray(x0, dtype=np.float64), cfg.lx)
     y0 = wrap(np.asarray(y0, dtype=np.float64), cfg.ly)
     vx0 = np.asarray(vx0, dtype=np.float64).copy()
@@ -319,6 +324,8 @@ def initial_state(cfg, x0, y0, vx0, vy0):
     phi_hat = np.where(K > 0.0, rho_hat / (cfg.eps0 * np.where(K > 0.0, K, 1.0)), 0.0)
     ex = spectral.idft2(-1j * kx * phi_hat).real
     ey = spectral.idft2(-1j * ky * phi_hat).real
+    if sample is not None:
+        x0, y0, vx0, vy0 = x0[sample], y0[sample], vx0[sample], vy0[sample]
     exp_ = gather(cfg, x0, y0, ex)
     eyp = gather(cfg, x0, y0, ey)
     vx_old, vy_old = taylor_back_velocity(cfg, vx0, vy0, exp_, eyp)
@@ -368,6 +375,31 @@ def run(cfg, x0, y0, vx0, vy0, nsteps):
     st = initial_state(cfg, x0, y0, vx0, vy0)
     for _ in range(nsteps):
         step(cfg, st)
+    return st
+
+
+def first_step_sampled(cfg, x0, y0, vx0, vy0, sample):
+    """The first step of run(..., 1) for problems too large to push every particle on
+    the CPU: the move, the deposit and the field solve use every particle, as in step();
+    the gather and the push are done for the particles `sample` only.  The returned
+    state holds those particles (in the order of `sample`) and the full grid quantities;
+    every value equals the corresponding value of run(..., 1).
+    """
+    st = initial_state(cfg, x0, y0, vx0, vy0, sample=sample)
+    x0 = wrap(np.asarray(x0, dtype=np.float64), cfg.lx)
+    y0 = wrap(np.asarray(y0, dtype=np.float64), cfg.ly)
+    vx0 = np.asarray(vx0, dtype=np.float64)
+    vy0 = np.asarray(vy0, dtype=np.float64)
+    x1 = wrap(x0 + vx0 * cfg.dt, cfg.lx)
+    y1 = wrap(y0 + vy0 * cfg.dt, cfg.ly)
+    qp = cfg.w * cfg.q
+    jx = deposit(cfg, x1, y1, qp * vx0)
+    jy = deposit(cfg, x1, y1, qp * vy0)
+    fields = field_solve(cfg, st, jx, jy)
+    st.x, st.y = x1[sample], y1[sample]
+    g = {name: gather(cfg, st.x, st.y, fields[name]) for name in FIELD_NAMES}
+    iaem_push(cfg, st, g)
+    st.n += 1
     return st
 
 

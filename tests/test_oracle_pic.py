@@ -326,3 +326,23 @@ def test_energies_are_finite_and_bounded():
     cfg, st, _ = _run_cloud("cdf2", 1, None, nsteps=10)
     e = pic.energies(cfg, st)
     assert all(np.isfinite(v) and v >= 0 for v in e.values())
+
+
+@pytest.mark.parametrize("stepper,extra", [("bdf", dict(bdf_order=2)),
+                                           ("dirk", dict(dirk=steppers.DIRK3_MIDPOINT))],
+                         ids=["bdf2", "dirk3"])
+def test_first_step_sampled_equals_full_first_step(stepper, extra):
+    # the sampled first step (used on problems too large to push every particle on the
+    # CPU) must reproduce run(..., 1) exactly: full grids, sampled particles
+    wl = workloads.weibel(24, 16, 8, 0.6, 0.02, 71, 4, n=3072)
+    cfg = pic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p,
+                     stepper=stepper, w=wl.weight, **extra)
+    full = pic.run(cfg, wl.x, wl.y, wl.vx, wl.vy, 1)
+    idx = np.random.default_rng(3).choice(wl.n, 300, replace=False)
+    part = pic.first_step_sampled(cfg, wl.x, wl.y, wl.vx, wl.vy, idx)
+    for k in ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old"):
+        assert np.array_equal(getattr(part, k), getattr(full, k)[idx]), k
+    for name, g in full.grids.items():
+        if name in ("ex0", "ey0"):  # the t = 0 gathers, per particle
+            continue
+        assert np.array_equal(part.grids[name], g), name
