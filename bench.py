@@ -39,21 +39,37 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default="bdf2")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="weibel128",
+                    help="weibel128: the headline configuration; weibel512: the large one")
+    ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default=None,
+                    help="default: the workload's own (bdf2 for weibel128, dirk3 for weibel512)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="form timed for the headline value; the other form is timed beside it")
     ap.add_argument("--sort-interval", type=int, default=8,
                     help="re-sort particles by tile every this many steps (0 = never)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-steppers", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.stepper is None:
+        a.stepper = WORKLOADS[a.workload]["stepper"]
+    return a
 
 
 # ----------------------------------------------------------------- workload --
 
-def make_workload(seed):
+# Workloads: the 128x128 Weibel (2^20 particles, cubic, BDF-2: the headline) and the
+# 512x512 one (26,214,400 particles, quartic, 3-stage DIRK).  seed: the seed of rank 0.
+WORKLOADS = {
+    "weibel128": dict(n=128, ppc=64, v_drift=0.5, u_th=0.01, p=3, seed=2, stepper="bdf2"),
+    "weibel512": dict(n=512, ppc=100, v_drift=0.6, u_th=0.02, p=4, seed=3, stepper="dirk3"),
+}
+
+
+def make_workload(name, rank=0):
     from paper_2410_18414_gb300 import workloads
-    return workloads.weibel(128, 128, 64, 0.5, 0.01, seed, 3, "bdf", 2, 2000)
+    w = WORKLOADS[name]
+    return workloads.weibel(w["n"], w["n"], w["ppc"], w["v_drift"], w["u_th"], w["seed"] + rank,
+                            w["p"], "bdf", 2, 2000)
 
 
 def dirk_tableau(name):
@@ -74,10 +90,12 @@ def make_config(wl, stepper_name, precision="fp64", sort_interval=0):
                            sort_interval=sort_interval)
 
 
-def workload_desc(wl, stepper_name):
-    return {"workload": f"weibel_{wl.nx}x{wl.ny}_ppc64_cubic_{stepper_name}",
+def workload_desc(name, wl, stepper_name):
+    w = WORKLOADS[name]
+    shape = {2: "quadratic", 3: "cubic", 4: "quartic"}[wl.p]
+    return {"workload": f"weibel_{wl.nx}x{wl.ny}_ppc{w['ppc']}_{shape}_{stepper_name}",
             "nx": wl.nx, "ny": wl.ny, "particles_per_gpu": wl.n, "spline_order": wl.p,
-            "stepper": stepper_name, "dt": wl.dt, "v_drift": 0.5, "u_th": 0.01}
+            "stepper": stepper_name, "dt": wl.dt, "v_drift": w["v_drift"], "u_th": w["u_th"]}
 
 
 # --------------------------------------------------- algorithmic op counts --
@@ -193,10 +211,10 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle import pic as opic
 from paper_2410_18414_gb300 import workloads
-wl = workloads.weibel(128, 128, 64, 0.5, 0.01, {seed}, 3, "bdf", 2, 2000)
+wl = workloads.weibel({nx}, {nx}, {ppc}, {v_drift}, {u_th}, {seed}, {p}, "bdf", 2, 2000)
 n = {n}
 x, y, vx, vy = wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n]
-cfg = opic.Config(nx=128, ny=128, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=3, stepper={stepper!r},
+cfg = opic.Config(nx={nx}, ny={nx}, lx=wl.lx, ly=wl.ly, dt=wl.dt, p={p}, stepper={stepper!r},
                   bdf_order={k}, dirk={dirk!r}, w=wl.lx * wl.ly / n)
 st = opic.initial_state(cfg, x, y, vx, vy)
 for _ in range({warmup}):
@@ -210,11 +228,13 @@ print(json.dumps({{"times": times}}))
 """
 
 
-def run_oracle(stepper_name, n, steps, warmup, seed=2):
+def run_oracle(workload, stepper_name, n, steps, warmup):
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
-    code = ORACLE_SNIPPET.format(root=ROOT, seed=seed, n=n, stepper=stepper, k=k, dirk=dirk,
-                                 warmup=warmup, steps=steps)
+    w = WORKLOADS[workload]
+    code = ORACLE_SNIPPET.format(root=ROOT, seed=w["seed"], n=n, stepper=stepper, k=k, dirk=dirk,
+                                 warmup=warmup, steps=steps, nx=w["n"], ppc=w["ppc"],
+                                 v_drift=w["v_drift"], u_th=w["u_th"], p=w["p"])
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -225,15 +245,17 @@ def run_oracle(stepper_name, n, steps, warmup, seed=2):
     return times
 
 
-def cpu_baseline(stepper_name):
+def cpu_baseline(workload, stepper_name):
     n = 262144
     steps = 4
-    times = run_oracle(stepper_name, n, steps, 1)
+    times = run_oracle(workload, stepper_name, n, steps, 1)
     v = n * len(times) / sum(times)
+    w = WORKLOADS[workload]
+    total = w["n"] * w["n"] * w["ppc"]
     return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 oracle, single thread, 128x128 grid with the first {n} of the "
-                      f"1,048,576 particles (weight rescaled), {steps} timed steps after 1 warm-up, "
-                      f"{sum(times):.1f} s"}
+            "sample": f"numpy FP64 oracle, single thread, {w['n']}x{w['n']} grid with the first "
+                      f"{n} of the {total:,} particles (weight rescaled), {steps} timed steps "
+                      f"after 1 warm-up, {sum(times):.1f} s"}
 
 
 def run_reference(a):
@@ -242,10 +264,10 @@ def run_reference(a):
     if rank != 0:
         return
     n = 131072
-    times = run_oracle(a.stepper, n, a.steps, a.warmup)
+    times = run_oracle(a.workload, a.stepper, n, a.steps, a.warmup)
     total = sum(times)
     value = n * len(times) / total
-    wl_desc = workload_desc(make_workload(2), a.stepper)
+    wl_desc = workload_desc(a.workload, make_workload(a.workload), a.stepper)
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
@@ -326,7 +348,7 @@ def main():
     sp = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    wl = make_workload(2 + rank)
+    wl = make_workload(a.workload, rank)
     cfg = make_config(wl, a.stepper, a.precision, a.sort_interval)
     sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
 
@@ -459,7 +481,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(a.stepper)
+            cpu = cpu_baseline(a.workload, a.stepper)
         except Exception as exc:  # the line still prints; the failure is stated
             cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {exc}"[:300]}
@@ -470,7 +492,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
             "data": "synthetic",
-            "config": dict(workload_desc(wl, a.stepper),
+            "config": dict(workload_desc(a.workload, wl, a.stepper),
                            form="fp32_fix64" if fp32 else "fp64",
                            l2="flushed between timed steps (256 MiB device write)",
                            sort_interval=a.sort_interval,
