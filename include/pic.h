@@ -148,6 +148,49 @@ pic_status pic_gather_push(pic_handle *h);
 /* nsteps complete steps (deposit, field solve, gather/push each). */
 pic_status pic_step(pic_handle *h, int32_t nsteps);
 
+/* ---- Ensembles: many independent runs in one CUDA-graph launch ----------------------
+ *
+ * Independent simulations (each its own pic_handle, of any grid size, particle count
+ * and form) advance together: pic_ensemble_create captures P steps of every run into
+ * one CUDA graph, each run on its own stream so that the runs overlap on the GPU, and
+ * pic_ensemble_step replays that graph.  P is the common period of the runs' per-step
+ * buffer rotations (history rings, velocity and current buffers, sort buffers: the
+ * least common multiple of 2, the BDF ring lengths and twice each sort interval), so
+ * every replay finds every buffer where the captured launches expect it.  The results
+ * are those of pic_step on each run, bit for bit (the FP32 form; the FP64 path sums the
+ * current with FP64 atomics in no fixed order, so its runs agree to roundoff).
+ *
+ * Not a step of the paper: a batching of its step (no counterpart there). */
+typedef struct pic_ensemble pic_ensemble; /* opaque, owned by the library */
+
+/* Capture P steps of runs[0..count) into one graph launched on `stream` (a cudaStream_t;
+ * not NULL, the legacy default stream cannot be captured).  Every run must be between
+ * steps, with diagnostics and kernel timing off, and should have a stream of its own
+ * (runs that share a stream are serialised).  Runs nothing on the GPU: the captured
+ * steps execute only in pic_ensemble_step.  The runs' host-side state is unchanged on
+ * return (on failure as well).  The ensemble keeps the run pointers: destroy it before
+ * its runs.  Errors: PIC_ERR_INVALID_ARG (NULL or repeated runs, count < 1 or > 4096,
+ * NULL stream), PIC_ERR_STATE (a run mid-step, with diagnostics or timing on),
+ * PIC_ERR_CUDA (capture or instantiation failed); the text is in pic_last_error(NULL). */
+pic_status pic_ensemble_create(pic_handle *const *runs, int32_t count, void *stream,
+                               pic_ensemble **out);
+
+/* Advance every run by nsteps, a multiple of the period (pic_ensemble_period), as
+ * nsteps / P graph launches on the ensemble's stream.  The launches wait for work
+ * already enqueued on the runs' streams, and later work on a run's stream waits for
+ * them, so pic_step, pic_read_particles, pic_get_field... on a run see the result.  A
+ * run advanced on its own (pic_step) by a number of steps that is not a multiple of P
+ * no longer matches the graph: PIC_ERR_STATE.  Errors: PIC_ERR_INVALID_ARG (NULL,
+ * nsteps < 0 or not a multiple of P), PIC_ERR_CUDA; text in pic_last_error(NULL).
+ * Device-side errors latch in each run and are reported by pic_sync on that run. */
+pic_status pic_ensemble_step(pic_ensemble *e, int32_t nsteps);
+
+/* Steps captured in the graph (the period P), 0 for NULL. */
+int32_t pic_ensemble_period(const pic_ensemble *e);
+
+/* Release the graph and the ensemble's events (not the runs).  NULL is allowed. */
+void pic_ensemble_destroy(pic_ensemble *e);
+
 /* Compute diagnostics every `every` steps (0 = never, the default).  They cost one
  * extra reduction over modes and particles per diagnosed step. */
 pic_status pic_set_diagnostics(pic_handle *h, int32_t every);

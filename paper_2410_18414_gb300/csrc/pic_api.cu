@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -768,6 +769,173 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
         if (st != PIC_OK) return st;
     }
     return PIC_OK;
+}
+
+// ------------------------------------------------------------ ensembles ----
+
+}  // extern "C"
+
+struct pic_ensemble {
+    std::vector<pic_handle*> runs;
+    std::vector<int64_t> step0;  // each run's step count when the graph was captured
+    cudaStream_t s = nullptr;
+    int period = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev = nullptr;    // fork / join marks on the ensemble's stream
+    std::vector<cudaEvent_t> ev_run;
+};
+
+namespace {
+
+int64_t lcm64(int64_t a, int64_t b) { return a / std::gcd(a, b) * b; }
+
+// Steps after which every per-step rotation of the run's buffers is back where it was:
+// velocity buffers (2), BDF rings (L, Lr), CDF-2 level swaps (2), the FP32 current
+// buffers (2), the sort's particle sets (two sorts, 2 S).
+int64_t step_period(const pic_handle* h) {
+    int64_t p = 2;
+    if (h->cfg.stepper == PIC_STEPPER_BDF) p = lcm64(lcm64(p, h->L), h->Lr);
+    if (h->sorting) p = lcm64(p, 2 * (int64_t)h->cfg.sort_interval);
+    return p;
+}
+
+void ensemble_release(pic_ensemble* e) {
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->ev) cudaEventDestroy(e->ev);
+    for (cudaEvent_t v : e->ev_run) cudaEventDestroy(v);
+    delete e;
+}
+
+pic_status efail(pic_ensemble* e, pic_status st, const char* msg, cudaError_t ce = cudaSuccess) {
+    if (e) ensemble_release(e);
+    if (ce != cudaSuccess) return fail(nullptr, st, "%s: %s", msg, cudaGetErrorString(ce));
+    return fail(nullptr, st, "%s", msg);
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_ensemble_create(pic_handle* const* runs, int32_t count, void* stream,
+                               pic_ensemble** out) {
+    if (!runs || !out || count < 1 || count > 4096)
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "runs, out must not be NULL; 1 <= count <= 4096");
+    if (!stream)
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "the ensemble needs a stream other than NULL");
+    *out = nullptr;
+    int64_t period = 1;
+    for (int32_t i = 0; i < count; ++i) {
+        const pic_handle* h = runs[i];
+        if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "run %d is NULL", i);
+        for (int32_t k = 0; k < i; ++k)
+            if (runs[k] == h) return fail(nullptr, PIC_ERR_INVALID_ARG, "run %d repeats run %d", i, k);
+        if (!h->s) return fail(nullptr, PIC_ERR_INVALID_ARG, "run %d uses the NULL stream", i);
+        if (h->phase != 0) return fail(nullptr, PIC_ERR_STATE, "run %d is in the middle of a step", i);
+        if (h->diag_every > 0 || h->ktiming)
+            return fail(nullptr, PIC_ERR_STATE, "run %d has diagnostics or kernel timing on", i);
+        period = lcm64(period, step_period(h));
+        if (period > (1 << 16)) return fail(nullptr, PIC_ERR_INVALID_ARG, "common period too long");
+    }
+    pic_ensemble* e = new pic_ensemble;
+    e->runs.assign(runs, runs + count);
+    e->s = (cudaStream_t)stream;
+    e->period = (int)period;
+    cudaError_t ce = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
+    for (int32_t i = 0; i < count && ce == cudaSuccess; ++i) {
+        cudaEvent_t v = nullptr;
+        ce = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+        if (ce == cudaSuccess) e->ev_run.push_back(v);
+    }
+    if (ce != cudaSuccess) return efail(e, PIC_ERR_CUDA, "event creation failed", ce);
+    // nothing of the runs may be pending outside the capture
+    for (pic_handle* h : e->runs)
+        if ((ce = cudaStreamSynchronize(h->s)) != cudaSuccess)
+            return efail(e, PIC_ERR_CUDA, "synchronising a run failed", ce);
+    if ((ce = cudaStreamSynchronize(e->s)) != cudaSuccess)
+        return efail(e, PIC_ERR_CUDA, "synchronising the ensemble stream failed", ce);
+    // Capturing runs the step functions on the host: their buffer rotations advance by
+    // the period and so end where they started; the step counts are put back.
+    std::vector<pic_handle> saved;
+    saved.reserve(count);
+    for (pic_handle* h : e->runs) {
+        saved.push_back(*h);
+        e->step0.push_back(h->step);
+    }
+    auto restore = [&] {
+        for (int32_t i = 0; i < count; ++i) *e->runs[i] = saved[i];
+    };
+    ce = cudaStreamBeginCapture(e->s, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) return efail(e, PIC_ERR_CUDA, "cudaStreamBeginCapture failed", ce);
+    pic_status st = PIC_OK;
+    int32_t failed = 0;
+    cudaError_t cap = cudaEventRecord(e->ev, e->s);
+    for (int32_t i = 0; i < count && cap == cudaSuccess && st == PIC_OK; ++i) {
+        pic_handle* h = e->runs[i];
+        failed = i;
+        cap = cudaStreamWaitEvent(h->s, e->ev, 0);  // the run's stream joins the capture
+        if (cap == cudaSuccess) st = pic_step(h, e->period);
+        if (cap == cudaSuccess && st == PIC_OK) cap = cudaEventRecord(e->ev_run[i], h->s);
+        if (cap == cudaSuccess && st == PIC_OK) cap = cudaStreamWaitEvent(e->s, e->ev_run[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(e->s, &g);
+    e->graph = g;
+    std::string why = st != PIC_OK ? "capturing the steps of run " + std::to_string(failed) +
+                                         " failed: " + e->runs[failed]->errmsg
+                                   : "";
+    restore();
+    if (st != PIC_OK) return efail(e, st, why.c_str());
+    if (cap != cudaSuccess) return efail(e, PIC_ERR_CUDA, "capture failed", cap);
+    if (ce != cudaSuccess || !g) return efail(e, PIC_ERR_CUDA, "cudaStreamEndCapture failed", ce);
+    ce = cudaGraphInstantiate(&e->exec, e->graph, 0);
+    if (ce != cudaSuccess) return efail(e, PIC_ERR_CUDA, "cudaGraphInstantiate failed", ce);
+    *out = e;
+    return PIC_OK;
+}
+
+pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps) {
+    if (!e) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL ensemble");
+    if (nsteps < 0 || nsteps % e->period != 0)
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "nsteps must be a non-negative multiple of %d",
+                    e->period);
+    const size_t n = e->runs.size();
+    for (size_t i = 0; i < n; ++i) {
+        const pic_handle* h = e->runs[i];
+        if (h->phase != 0 || h->diag_every > 0 || h->ktiming ||
+            (h->step - e->step0[i]) % e->period != 0)
+            return fail(nullptr, PIC_ERR_STATE,
+                        "run %d no longer matches the captured graph (mid-step, diagnostics or "
+                        "timing on, or advanced alone by a number of steps that is not a "
+                        "multiple of %d)", (int)i, e->period);
+    }
+    if (nsteps == 0) return PIC_OK;
+    cudaError_t ce = cudaSuccess;
+    for (size_t i = 0; i < n && ce == cudaSuccess; ++i) {  // after the runs' pending work
+        ce = cudaEventRecord(e->ev_run[i], e->runs[i]->s);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->s, e->ev_run[i], 0);
+    }
+    for (int32_t k = 0; k < nsteps / e->period && ce == cudaSuccess; ++k)
+        ce = cudaGraphLaunch(e->exec, e->s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e->ev, e->s);
+    for (size_t i = 0; i < n && ce == cudaSuccess; ++i)  // later work on a run comes after
+        ce = cudaStreamWaitEvent(e->runs[i]->s, e->ev, 0);
+    if (ce != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "ensemble launch failed: %s",
+                                       cudaGetErrorString(ce));
+    for (pic_handle* h : e->runs) {
+        h->step += nsteps;
+        h->stepped = true;
+    }
+    return PIC_OK;
+}
+
+int32_t pic_ensemble_period(const pic_ensemble* e) { return e ? e->period : 0; }
+
+void pic_ensemble_destroy(pic_ensemble* e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->s);
+    ensemble_release(e);
 }
 
 pic_status pic_set_diagnostics(pic_handle* h, int32_t every) {

@@ -99,6 +99,10 @@ def load_library(path=LIB_PATH):
         "pic_kernels_per_step": ([vp], i32),
         "pic_set_kernel_timing": ([vp, i32], i32),
         "pic_kernel_time": ([vp, i32, dp, ctypes.POINTER(i64)], i32),
+        "pic_ensemble_create": ([ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)], i32),
+        "pic_ensemble_step": ([vp, i32], i32),
+        "pic_ensemble_period": ([vp], i32),
+        "pic_ensemble_destroy": ([vp], None),
         "pic_last_error": ([vp], ctypes.c_char_p),
         "pic_destroy": ([vp], None),
     }
@@ -243,3 +247,47 @@ class Simulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Ensemble:
+    """Independent runs advanced together by one CUDA-graph launch per period
+    (pic_ensemble_*).  `sims`: Simulation objects, each best on a stream of its own;
+    `stream`: the stream the graph is launched on (a CUDA stream handle, not 0)."""
+
+    def __init__(self, sims, stream):
+        self.lib = load_library()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h for s in self.sims])
+        e = ctypes.c_void_p()
+        st = self.lib.pic_ensemble_create(arr, len(self.sims), ctypes.c_void_p(stream),
+                                          ctypes.byref(e))
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(None).decode())
+        self.e = e
+
+    @property
+    def period(self):
+        return int(self.lib.pic_ensemble_period(self.e))
+
+    def step(self, nsteps):
+        st = self.lib.pic_ensemble_step(self.e, nsteps)
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "e", None):
+            self.lib.pic_ensemble_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

@@ -107,6 +107,14 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pic_sync(None) == 1
     assert lib.pic_step_count(None) == -1
     assert lib.pic_set_kernel_timing(None, 8) == 1
+    out = ctypes.c_void_p()
+    assert lib.pic_ensemble_create(None, 1, ctypes.c_void_p(1), ctypes.byref(out)) == 1
+    runs = (ctypes.c_void_p * 1)(None)
+    assert lib.pic_ensemble_create(runs, 1, ctypes.c_void_p(1), ctypes.byref(out)) == 1
+    assert b"NULL" in lib.pic_last_error(None)
+    assert lib.pic_ensemble_step(None, 0) == 1
+    assert lib.pic_ensemble_period(None) == 0
+    lib.pic_ensemble_destroy(None)
     ms, n = ctypes.c_double(), ctypes.c_int64()
     assert lib.pic_kernel_time(None, 0, ctypes.byref(ms), ctypes.byref(n)) == 1
     lib.pic_destroy(None)

@@ -1,0 +1,144 @@
+"""GPU checks of ensembles (pic_ensemble_*): independent runs captured into one CUDA
+graph and advanced by replaying it must give the results of pic_step on each run --
+bit for bit in the FP32 form, whose current is an integer sum; to roundoff in the FP64
+path, whose FP64 current atomics have no fixed order."""
+import numpy as np
+import pytest
+
+from oracle import steppers as osteps
+from paper_2410_18414_gb300 import pic, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+# (workload, precision, sort interval, stepper kwargs)
+RUNS = [
+    (lambda: workloads.weibel(32, 32, 16, 0.4, 0.01, 1001, 3), pic.FP32_FIX64, 8,
+     dict(stepper="bdf", bdf_order=2)),
+    (lambda: workloads.weibel(48, 32, 24, 0.6, 0.01, 1002, 3), pic.FP32_FIX64, 4,
+     dict(stepper="bdf", bdf_order=2)),
+    (lambda: workloads.weibel(64, 64, 16, 0.3, 0.01, 1003, 3), pic.FP32_FIX64, 0,
+     dict(stepper="cdf2")),
+    (lambda: workloads.weibel(24, 24, 8, 0.5, 0.02, 1004, 4), pic.FP64, 0,
+     dict(stepper="bdf", bdf_order=3)),
+    (lambda: workloads.weibel(32, 48, 8, 0.5, 0.02, 1005, 2), pic.FP32_FIX64, 2,
+     dict(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT)),
+]
+
+
+def make(torch, spec, stream=None):
+    make_wl, prec, sort, kw = spec
+    wl = make_wl()
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                          precision=prec, sort_interval=sort, **kw)
+    s = stream if stream is not None else torch.cuda.Stream()
+    return pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=s.cuda_stream), s
+
+
+def assert_same(a, b, prec):
+    pa, pb = a.particles(), b.particles()
+    for k in pa:
+        if prec == pic.FP32_FIX64:
+            assert np.array_equal(pa[k], pb[k]), k
+        else:
+            assert rel(pa[k], pb[k]) < 1e-13, k
+    for f in ("jx", "phi", "ay", "daxdy"):
+        u, v = a.field(f), b.field(f)
+        if prec == pic.FP32_FIX64:
+            assert np.array_equal(u, v), f
+        else:
+            assert rel(u, v) < 1e-12, f
+
+
+def test_ensemble_matches_runs_stepped_alone(torch_mod):
+    torch = torch_mod
+    runs = [make(torch, spec) for spec in RUNS]
+    solo = [make(torch, spec) for spec in RUNS]
+    master = torch.cuda.Stream()
+    with pic.Ensemble([r for r, _ in runs], master.cuda_stream) as ens:
+        P = ens.period
+        # lcm(2, BDF-2 rings 4 and 2, BDF-3 rings 6 and 3, twice the sort intervals 16, 8, 4)
+        assert P == 48
+        ens.step(2 * P)
+        for (r, _), (s, _) in zip(runs, solo):
+            s.step(2 * P)
+            assert r.step_count == s.step_count == 2 * P
+        for (r, _), (s, _), spec in zip(runs, solo, RUNS):
+            assert_same(r, s, spec[1])
+        # a run may go on alone afterwards; then the graph no longer matches it
+        runs[0][0].step(3)
+        solo[0][0].step(3)
+        assert_same(runs[0][0], solo[0][0], RUNS[0][1])
+        with pytest.raises(pic.PicError, match="no longer matches"):
+            ens.step(P)
+        runs[0][0].step(P - 3)  # back in phase: the graph applies again
+        solo[0][0].step(P - 3)
+        ens.step(P)
+        for (r, _), (s, _) in zip(runs[1:], solo[1:]):
+            s.step(P)
+        for (r, _), (s, _), spec in zip(runs, solo, RUNS):
+            if r is runs[0][0]:
+                s.step(P)
+            assert_same(r, s, spec[1])
+    for r, _ in runs + solo:
+        r.close()
+
+
+def test_ensemble_capture_runs_nothing_and_leaves_runs_unchanged(torch_mod):
+    torch = torch_mod
+    runs = [make(torch, spec) for spec in RUNS[:2]]
+    solo = [make(torch, spec) for spec in RUNS[:2]]
+    ens = pic.Ensemble([r for r, _ in runs], torch.cuda.Stream().cuda_stream)
+    assert ens.period == 16
+    ens.close()  # captured, never launched
+    for (r, _), (s, _), spec in zip(runs, solo, RUNS):
+        assert r.step_count == 0
+        r.step(5)
+        s.step(5)
+        assert_same(r, s, spec[1])
+    for r, _ in runs + solo:
+        r.close()
+
+
+def test_ensemble_rejects_misuse(torch_mod):
+    torch = torch_mod
+    r0, _ = make(torch, RUNS[0])
+    r1, _ = make(torch, RUNS[1])
+    master = torch.cuda.Stream().cuda_stream
+    with pytest.raises(pic.PicError, match="repeats"):
+        pic.Ensemble([r0, r0], master)
+    with pytest.raises(pic.PicError, match="stream"):
+        pic.Ensemble([r0], 0)
+    r1.set_diagnostics(2)
+    with pytest.raises(pic.PicError, match="diagnostics"):
+        pic.Ensemble([r0, r1], master)
+    r1.set_diagnostics(0)
+    r1.deposit()
+    with pytest.raises(pic.PicError, match="middle of a step"):
+        pic.Ensemble([r0, r1], master)
+    r1.field_solve()
+    r1.gather_push()
+    with pic.Ensemble([r0, r1], master) as ens:
+        with pytest.raises(pic.PicError, match="multiple"):
+            ens.step(ens.period + 1)
+        ens.step(0)
+    r0.close()
+    r1.close()
