@@ -39,8 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="weibel128",
-                    help="weibel128: the headline configuration; weibel512: the large one")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["ensemble256"], default="weibel128",
+                    help="weibel128: the headline configuration; weibel512: the large one; "
+                         "ensemble256: 256 independent runs in one graph launch per period")
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default=None,
                     help="default: the workload's own (bdf2 for weibel128, dirk3 for weibel512)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
@@ -51,7 +52,7 @@ def parse():
     ap.add_argument("--no-extra-steppers", action="store_true")
     a = ap.parse_args()
     if a.stepper is None:
-        a.stepper = WORKLOADS[a.workload]["stepper"]
+        a.stepper = WORKLOADS[a.workload]["stepper"] if a.workload in WORKLOADS else "bdf2"
     return a
 
 
@@ -212,7 +213,7 @@ sys.path.insert(0, {root!r})
 from oracle import pic as opic
 from paper_2410_18414_gb300 import workloads
 wl = workloads.weibel({nx}, {nx}, {ppc}, {v_drift}, {u_th}, {seed}, {p}, "bdf", 2, 2000)
-n = {n}
+n = min({n}, len(wl.x))
 x, y, vx, vy = wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n]
 cfg = opic.Config(nx={nx}, ny={nx}, lx=wl.lx, ly=wl.ly, dt=wl.dt, p={p}, stepper={stepper!r},
                   bdf_order={k}, dirk={dirk!r}, w=wl.lx * wl.ly / n)
@@ -224,14 +225,24 @@ for _ in range({steps}):
     t0 = time.perf_counter()
     opic.step(cfg, st)
     times.append(time.perf_counter() - t0)
-print(json.dumps({{"times": times}}))
+print(json.dumps({{"times": times, "n": n}}))
 """
+
+
+def workload_params(workload):
+    """WORKLOADS entry, or for the ensemble the parameters of its first run."""
+    if workload in WORKLOADS:
+        return WORKLOADS[workload]
+    from paper_2410_18414_gb300 import workloads
+    sp = workloads.ensemble_specs(count=1)[0]
+    return dict(n=sp["n"], ppc=sp["ppc"], v_drift=sp["v_drift"], u_th=0.01, p=3,
+                seed=sp["seed"], stepper="bdf2")
 
 
 def run_oracle(workload, stepper_name, n, steps, warmup):
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
-    w = WORKLOADS[workload]
+    w = workload_params(workload)
     code = ORACLE_SNIPPET.format(root=ROOT, seed=w["seed"], n=n, stepper=stepper, k=k, dirk=dirk,
                                  warmup=warmup, steps=steps, nx=w["n"], ppc=w["ppc"],
                                  v_drift=w["v_drift"], u_th=w["u_th"], p=w["p"])
@@ -241,8 +252,10 @@ def run_oracle(workload, stepper_name, n, steps, warmup):
                        timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
-    times = json.loads(r.stdout.strip().splitlines()[-1])["times"]
-    return times
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    if out["n"] != n:
+        raise RuntimeError(f"the workload holds only {out['n']} particles, fewer than {n}")
+    return out["times"]
 
 
 def cpu_baseline(workload, stepper_name):
@@ -263,11 +276,17 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n = 131072
+    wp = workload_params(a.workload)
+    n = min(131072, wp["n"] * wp["n"] * wp["ppc"])
     times = run_oracle(a.workload, a.stepper, n, a.steps, a.warmup)
     total = sum(times)
     value = n * len(times) / total
-    wl_desc = workload_desc(a.workload, make_workload(a.workload), a.stepper)
+    if a.workload in WORKLOADS:
+        wl_desc = workload_desc(a.workload, make_workload(a.workload), a.stepper)
+    else:
+        wp = workload_params(a.workload)
+        wl_desc = {"workload": "ensemble_256_weibel_cubic_bdf2",
+                   "oracle_sample": f"first run: {wp['n']}x{wp['n']}, {wp['ppc']} per cell"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
@@ -326,10 +345,127 @@ def time_steps(sim, steps, warmup, stream, flush, count=None, detail=False):
     return out
 
 
+def run_ensemble(a):
+    """256 independent Weibel runs (grid sizes, densities and drifts drawn per run; FP32
+    form, BDF-2, cubic), sort intervals from the autotuner, advanced together by one
+    CUDA-graph launch per period (pic_ensemble_step); the same runs stepped on their own
+    streams without the graph are timed beside it."""
+    import torch
+    from paper_2410_18414_gb300 import autotune, pic, workloads
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    pic.load_library()
+    specs = workloads.ensemble_specs(seed0=1000 + 256 * rank)
+    t0 = time.perf_counter()
+    sorts = [autotune.tune_sort_interval(sp["n"], sp["ppc"]) for sp in specs]
+    tune_s = time.perf_counter() - t0
+
+    def build():
+        sims, streams = [], []
+        for sp, si in zip(specs, sorts):
+            wl = workloads.ensemble_run(sp)
+            cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf",
+                                  bdf_order=2, weight=wl.weight, precision=pic.FP32_FIX64,
+                                  sort_interval=si)
+            st = torch.cuda.Stream()
+            sims.append(pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=st.cuda_stream))
+            streams.append(st)
+        return sims, streams
+
+    def join(master, streams):
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            master.wait_event(ev)
+
+    sims, streams = build()
+    n_total = sum(s.n for s in sims)
+    master = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    ens = pic.Ensemble(sims, master.cuda_stream)
+    capture_s = time.perf_counter() - t0
+    P = ens.period
+    steps = a.steps
+    full, rest = (steps // P) * P, steps % P
+    warm = max(1, -(-a.warmup // P)) * P       # whole periods keep the runs in phase
+    ens.step(warm)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(master)
+    ens.step(full)
+    for s in sims:      # the steps left over after whole periods, on the runs' own streams
+        if rest:
+            s.step(rest)
+    join(master, streams)
+    e1.record(master)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ens.close()
+    for s in sims:
+        s.sync()  # reports any latched device error
+        s.close()
+    # the same runs without the graph: every run's steps enqueued on its own stream
+    sims, streams = build()
+    for s in sims:
+        s.step(warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(master)
+    for st in streams:         # start after the event above
+        st.wait_event(f0)
+    for s in sims:
+        s.step(steps)
+    join(master, streams)
+    f1.record(master)
+    f1.synchronize()
+    ms_plain = f0.elapsed_time(f1)
+    for s in sims:
+        s.close()
+    if rank != 0:
+        return
+    value = n_total * world * steps / (ms * 1e-3)
+    hist = {}
+    for si in sorts:
+        hist[str(si)] = hist.get(str(si), 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble_256_weibel_cubic_bdf2", "runs": len(specs),
+                   "particles_total": n_total, "grid_sizes": sorted({sp["n"] for sp in specs}),
+                   "ppc_range": [min(sp["ppc"] for sp in specs), max(sp["ppc"] for sp in specs)],
+                   "sort_intervals": hist, "period": P, "graph_steps": full,
+                   "steps_outside_graph": rest, "form": "fp32_fix64",
+                   "l2": "no flush: the ensemble's particle state (about 7 GB) is far larger "
+                         "than L2", "parallelism": "single"},
+        "roofline": {"kernel": "whole step, all runs", "bound": "hbm",
+                     "achieved": 72.0 * n_total * steps / (ms * 1e-3) / 1e9,
+                     "peak": peaks()["hbm_gbs"], "unit": "GB/s",
+                     "frac": 72.0 * n_total * steps / (ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
+                     "traffic": None, "peak_source": peaks()["hbm_src"],
+                     "note": "72 B algorithmic per particle-step (deposit 24 + gather 48)"},
+        "no_graph": {"ms_per_step": ms_plain / steps,
+                     "value": n_total * world * steps / (ms_plain * 1e-3),
+                     "how": "each run's steps enqueued on its own stream, no graph"},
+        "autotune_s": tune_s, "capture_s": capture_s,
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload == "ensemble256":
+        run_ensemble(a)
         return
     import numpy as np
     import torch

@@ -106,3 +106,24 @@ def weibel_512(stepper="dirk", seed=3):
 def weibel_adjoint_128(seed=5):
     """128x128 Weibel, 16 per cell (262,144), v_d = 0.5c, BDF-2, cubic, 200 steps."""
     return weibel(128, 128, 16, 0.5, 0.01, seed, 3, "bdf", 2, 200)
+
+
+def ensemble_specs(count=256, seed0=1000):
+    """Parameters of the batched-ensemble runs: run r draws, from PCG64(seed0 + r), a grid
+    of N x N with N uniform in {32, 48, 64, 96, 128}, an integer number of particles per
+    cell uniform in 16..64 and a drift uniform in (0.3, 0.7) c; u_th = 0.01 c, cubic
+    shapes, BDF-2, dt = 0.4 dx, 300 steps."""
+    specs = []
+    for r in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed0 + r))
+        n_axis = int(rng.choice([32, 48, 64, 96, 128]))
+        ppc = int(rng.integers(16, 65))
+        v_drift = float(rng.uniform(0.3, 0.7))
+        specs.append({"n": n_axis, "ppc": ppc, "v_drift": v_drift, "seed": seed0 + r})
+    return specs
+
+
+def ensemble_run(spec):
+    """The particles of one ensemble run (seeded with the run's own seed)."""
+    return weibel(spec["n"], spec["n"], spec["ppc"], spec["v_drift"], 0.01, spec["seed"], 3,
+                  "bdf", 2, 300)

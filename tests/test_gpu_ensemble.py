@@ -142,3 +142,12 @@ def test_ensemble_rejects_misuse(torch_mod):
         ens.step(0)
     r0.close()
     r1.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches(torch_mod):
+    from paper_2410_18414_gb300 import autotune
+    s = autotune.tune_sort_interval(32, 20)
+    assert s in autotune.CANDIDATES
+    assert autotune.density_class(20) == 16 and autotune.density_class(50) == 64
+    assert autotune._cache[(32, 16, 3, pic.FP32_FIX64)] == s
+    assert autotune.tune_sort_interval(32, 18) == s  # same key: from the cache
