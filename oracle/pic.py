@@ -52,6 +52,7 @@ class Config:
     stepper: str = "bdf"            # "bdf" | "cdf2" | "dirk"
     bdf_order: int = 1
     dirk: dict = None               # {"A": [[..]], "b": [..], "c": [..]}
+    cdf_form: str = "implicit"      # CDF-2 only: "implicit" | "semi" | "explicit" (section 3.1)
     c: float = 1.0
     eps0: float = 1.0
     q: float = -1.0
@@ -220,12 +221,19 @@ def field_solve(cfg, st, jx, jy):
 
     elif cfg.stepper == "cdf2":
         rho_new = steppers.cdf2_continuity(h["rho"], divj, dt)              # rho^{n+3/2}
-        phi_new = steppers.cdf2_wave_update(h["phi"], h["phi_prev"], rho_new / eps0,
-                                            h["rho_prev"] / eps0, K, c, dt)  # phi^{n+3/2}
-        ax_new = steppers.cdf2_wave_update(h["ax"], h["ax_prev"], mu0 * jx_hat,
-                                           mu0 * h["jx_prev"], K, c, dt)     # A^{n+1}
-        ay_new = steppers.cdf2_wave_update(h["ay"], h["ay_prev"], mu0 * jy_hat,
-                                           mu0 * h["jy_prev"], K, c, dt)
+        if cfg.cdf_form == "implicit":
+            phi_new = steppers.cdf2_wave_update(h["phi"], h["phi_prev"], rho_new / eps0,
+                                                h["rho_prev"] / eps0, K, c, dt)  # phi^{n+3/2}
+            ax_new = steppers.cdf2_wave_update(h["ax"], h["ax_prev"], mu0 * jx_hat,
+                                               mu0 * h["jx_prev"], K, c, dt)     # A^{n+1}
+            ay_new = steppers.cdf2_wave_update(h["ay"], h["ay_prev"], mu0 * jy_hat,
+                                               mu0 * h["jy_prev"], K, c, dt)
+        else:  # sources at the middle level: rho^{n+1/2} and J^n
+            upd = {"semi": steppers.cdf2_semi_implicit_update,
+                   "explicit": steppers.cdf2_explicit_update}[cfg.cdf_form]
+            phi_new = upd(h["phi"], h["phi_prev"], h["rho"] / eps0, K, c, dt)
+            ax_new = upd(h["ax"], h["ax_prev"], mu0 * h["jx"], K, c, dt)
+            ay_new = upd(h["ay"], h["ay_prev"], mu0 * h["jy"], K, c, dt)
         div_a = spectral.div_hat(ax_new, ay_new, kx, ky)
         # section 3.1: eps_1, eps_2 and Gauss at t^{n+1/2} for the implicit scheme
         res["gauge"] = (phi_new - h["phi"]) / (c * c * dt) + div_a

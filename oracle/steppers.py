@@ -101,6 +101,27 @@ def cdf2_wave_update(u_now, u_prev, s_new, s_old, K, c, dt):
     return (2.0 * u_now + inv_alpha2 * (s_new + s_old)) / (1.0 + inv_alpha2 * K) - u_prev
 
 
+def cdf2_semi_implicit_update(u_now, u_prev, s_now, K, c, dt):
+    """Semi-implicit CDF-2 update of one mode (section 3.1, the second form): the
+    Laplacian averaged over levels n+1 and n-1, the source at level n,
+
+        (u^{n+1} - 2u^n + u^{n-1}) / (c^2 dt^2) + K (u^{n+1} + u^{n-1}) / 2 = S^n,
+
+    so u^{n+1} = (2 u^n + c^2 dt^2 S^n) / (1 + alpha^-2 K) - u^{n-1}, alpha^-2 = c^2 dt^2 / 2.
+    """
+    inv_alpha2 = 0.5 * c * c * dt * dt
+    return (2.0 * u_now + c * c * dt * dt * s_now) / (1.0 + inv_alpha2 * K) - u_prev
+
+
+def cdf2_explicit_update(u_now, u_prev, s_now, K, c, dt):
+    """Explicit CDF-2 update of one mode (section 3.1, the third form): the Laplacian and
+    the source at level n,
+
+        (u^{n+1} - 2u^n + u^{n-1}) / (c^2 dt^2) + K u^n = S^n.
+    """
+    return 2.0 * u_now - u_prev + c * c * dt * dt * (s_now - K * u_now)
+
+
 # ---------------------------------------------------------------- DIRK -------
 
 # The tableau printed in section 5 for the Qin-Zhang method, exactly as printed.

@@ -271,3 +271,52 @@ def test_continuity_updates():
     r0, r1 = steppers.dirk_interp_weights(tab["b"], tab["c"])
     assert (r0, r1) == (0.5, 0.5)
     np.testing.assert_allclose(new, rho[0] - dt * (0.5 * divj_n + 0.5 * divj), atol=1e-14)
+
+
+# ------------------------------------------- CDF-2 semi-implicit / explicit ----
+
+def _transfer(update, K, c, dt):
+    """2x2 transfer matrix of a source-free two-level update u^{n+1} = f(u^n, u^{n-1})."""
+    M = np.zeros((2, 2))
+    for col in range(2):
+        u = [np.zeros(1), np.zeros(1)]
+        u[col][0] = 1.0
+        M[0, col] = update(u[0], u[1], 0.0, K, c, dt)[0]
+    M[1, 0] = 1.0
+    return M
+
+
+@pytest.mark.parametrize("K", [0.3, 4.0, 150.0, 3.0e4])
+def test_cdf2_semi_implicit_roots_of_printed_equation(K):
+    # section 3.1, second form: (u+ - 2u + u-)/(c^2 dt^2) + K (u+ + u-)/2 = S^n; with S = 0
+    # the roots of (1/(c dt)^2 + K/2) z^2 - 2/(c dt)^2 z + (1/(c dt)^2 + K/2) are the
+    # eigenvalues of the update, on the unit circle for every K
+    c, dt = 1.0, 0.05
+    h = 1.0 / (c * c * dt * dt)
+    expect = np.roots([h + 0.5 * K, -2.0 * h, h + 0.5 * K])
+    ev = np.linalg.eigvals(_transfer(steppers.cdf2_semi_implicit_update, K, c, dt))
+    np.testing.assert_allclose(np.sort_complex(ev), np.sort_complex(expect), atol=1e-12)
+    np.testing.assert_allclose(np.abs(ev), 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("K", [0.3, 4.0, 150.0, 1500.0, 1700.0])
+def test_cdf2_explicit_roots_and_stability_limit(K):
+    # section 3.1, third form: (u+ - 2u + u-)/(c^2 dt^2) + K u = S^n; roots of
+    # z^2 - (2 - (c dt)^2 K) z + 1: unit modulus while (c dt)^2 K <= 4, growth beyond
+    c, dt = 1.0, 0.05
+    expect = np.roots([1.0, -(2.0 - c * c * dt * dt * K), 1.0])
+    ev = np.linalg.eigvals(_transfer(steppers.cdf2_explicit_update, K, c, dt))
+    np.testing.assert_allclose(np.sort_complex(ev), np.sort_complex(expect), atol=1e-12)
+    if c * c * dt * dt * K <= 4.0:
+        np.testing.assert_allclose(np.abs(ev), 1.0, atol=1e-9)
+    else:
+        assert np.max(np.abs(ev)) > 1.0 + 1e-3
+
+
+@pytest.mark.parametrize("K", [0.5, 20.0])
+def test_cdf2_variants_static_equilibrium(K):
+    # u = S/K (the Poisson solution) is a fixed point of both forms
+    c, dt, S = 0.7, 0.03, 2.5 + 1.5j
+    u_eq = np.array([S / K])
+    for upd in (steppers.cdf2_semi_implicit_update, steppers.cdf2_explicit_update):
+        np.testing.assert_allclose(upd(u_eq, u_eq, S, K, c, dt), u_eq, rtol=1e-13)
