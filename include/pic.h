@@ -59,7 +59,13 @@ typedef enum {
 typedef enum {
     PIC_STEPPER_BDF = 0,  /* BDF-k, k = bdf_order in 1..6 (section 3.2)               */
     PIC_STEPPER_CDF2 = 1, /* implicit centred CDF-2, phi at half levels (section 3.1) */
-    PIC_STEPPER_DIRK = 2  /* s-stage DIRK with the tableau in pic_config (section 3.3) */
+    PIC_STEPPER_DIRK = 2, /* s-stage DIRK with the tableau in pic_config (section 3.3) */
+    PIC_STEPPER_CDF2_SEMI = 3,    /* semi-implicit CDF-2 (section 3.1, second form): the
+                                     Laplacian averaged over levels n+1 and n-1, sources
+                                     rho^{n+1/2} and J^n */
+    PIC_STEPPER_CDF2_EXPLICIT = 4 /* explicit CDF-2 (section 3.1, third form): Laplacian and
+                                     sources at level n; stable while (c dt)^2 |k|^2 <= 4 for
+                                     every resolved mode */
 } pic_stepper;
 
 typedef enum {

@@ -70,6 +70,7 @@ struct CdfParams {
     // A^n, A^{n-1} (new A^{n+1} overwrites *_prev); J^n, J^{n-1} (new J overwrites j_prev)
     void *phi, *phi_prev, *rho, *rho_prev, *ax, *ax_prev, *ay, *ay_prev;
     void *jx, *jx_prev, *jy, *jy_prev;
+    int form;  // 0 implicit, 1 semi-implicit, 2 explicit (section 3.1)
 };
 
 struct DirkParams {

@@ -260,9 +260,25 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParam
     const zd ay = hload(cp.ay, idx), ay_prev = hload(cp.ay_prev, idx);
     const zd jx_prev = hload(cp.jx_prev, idx), jy_prev = hload(cp.jy_prev, idx);
     const zd rho_new = rho - dt * m.divj;  // rho^{n+3/2}
-    const zd phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
-    const zd ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
-    const zd ay_new = inv * (2.0 * ay + (th * mc.mu0) * (m.jy + jy_prev)) - ay_prev;
+    zd phi_new, ax_new, ay_new;
+    if (cp.form == 0) {  // implicit: sources averaged over the new and the oldest level
+        phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
+        ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
+        ay_new = inv * (2.0 * ay + (th * mc.mu0) * (m.jy + jy_prev)) - ay_prev;
+    } else {  // sources at the middle level: rho^{n+1/2} and J^n
+        const double h2 = mc.c * mc.c * dt * dt;
+        const zd jx_n = hload(cp.jx, idx), jy_n = hload(cp.jy, idx);
+        const zd sphi = (1.0 / mc.eps0) * rho, sax = mc.mu0 * jx_n, say = mc.mu0 * jy_n;
+        if (cp.form == 1) {  // semi-implicit: Laplacian averaged over levels n+1, n-1
+            phi_new = inv * (2.0 * phi + h2 * sphi) - phi_prev;
+            ax_new = inv * (2.0 * ax + h2 * sax) - ax_prev;
+            ay_new = inv * (2.0 * ay + h2 * say) - ay_prev;
+        } else {  // explicit: Laplacian at level n
+            phi_new = 2.0 * phi - phi_prev + h2 * (sphi - m.K * phi);
+            ax_new = 2.0 * ax - ax_prev + h2 * (sax - m.K * ax);
+            ay_new = 2.0 * ay - ay_prev + h2 * (say - m.K * ay);
+        }
+    }
     if (mc.diag) {
         // section 3.1: eps_1^{n+1}, eps_2^{n+1} and Gauss at t^{n+1/2}
         const zd diva = div2(m.kx, m.ky, ax_new, ay_new);

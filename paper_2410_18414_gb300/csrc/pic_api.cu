@@ -177,7 +177,8 @@ pic_status validate(const pic_config* c, const pic_particles_in* in) {
                     return fail(h, PIC_ERR_INVALID_ARG, "DIRK diagonal must be >= 0");
             }
         }
-    } else if (c->stepper != PIC_STEPPER_CDF2) {
+    } else if (c->stepper != PIC_STEPPER_CDF2 && c->stepper != PIC_STEPPER_CDF2_SEMI &&
+               c->stepper != PIC_STEPPER_CDF2_EXPLICIT) {
         return fail(h, PIC_ERR_INVALID_ARG, "unknown stepper %d", c->stepper);
     }
     if (c->precision != PIC_FP64 && c->precision != PIC_FP32_FIX64)
@@ -520,6 +521,12 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
     if (st != PIC_OK) return st;
     pic_handle* h = new pic_handle();
     h->cfg = *cfg;
+    // the CDF-2 forms share its buffers and kernels; the form goes with the parameters
+    int cdf_form = 0;
+    if (cfg->stepper == PIC_STEPPER_CDF2_SEMI) cdf_form = 1;
+    if (cfg->stepper == PIC_STEPPER_CDF2_EXPLICIT) cdf_form = 2;
+    if (cdf_form) h->cfg.stepper = PIC_STEPPER_CDF2;
+    h->cdf.form = cdf_form;
     h->s = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
     h->nx = cfg->nx;

@@ -23,7 +23,9 @@ STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_INVALID_ARG", 2: "PIC_ERR_UNSUPPORTED",
                 7: "PIC_ERR_STATE"}
 # pic_stepper
 STEPPER_BDF, STEPPER_CDF2, STEPPER_DIRK = 0, 1, 2
-STEPPERS = {"bdf": STEPPER_BDF, "cdf2": STEPPER_CDF2, "dirk": STEPPER_DIRK}
+STEPPER_CDF2_SEMI, STEPPER_CDF2_EXPLICIT = 3, 4
+STEPPERS = {"bdf": STEPPER_BDF, "cdf2": STEPPER_CDF2, "dirk": STEPPER_DIRK,
+            "cdf2_semi": STEPPER_CDF2_SEMI, "cdf2_explicit": STEPPER_CDF2_EXPLICIT}
 # pic_precision
 FP64, FP32_FIX64 = 0, 1
 # pic_field

@@ -44,6 +44,11 @@ def wrapped_rel(a, b, length):
     return float(np.linalg.norm(d) / np.linalg.norm(b))
 
 
+# the CDF-2 forms of section 3.1: library stepper name -> (oracle stepper, oracle cdf_form)
+CDF_FORMS = {"cdf2": ("cdf2", "implicit"), "cdf2_semi": ("cdf2", "semi"),
+             "cdf2_explicit": ("cdf2", "explicit")}
+
+
 def run_both(wl, device, nsteps, stepper="bdf", bdf_order=1, dirk=None, p=None, diag=0):
     p = wl.p if p is None else p
     cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=p, stepper=stepper,
@@ -52,8 +57,9 @@ def run_both(wl, device, nsteps, stepper="bdf", bdf_order=1, dirk=None, p=None, 
     if diag:
         sim.set_diagnostics(diag)
     sim.step(nsteps)
-    ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=p, stepper=stepper,
-                       bdf_order=bdf_order, dirk=dirk, w=wl.weight)
+    ostepper, form = CDF_FORMS.get(stepper, (stepper, "implicit"))
+    ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=p, stepper=ostepper,
+                       bdf_order=bdf_order, dirk=dirk, w=wl.weight, cdf_form=form)
     st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, nsteps)
     return sim, st, ocfg
 
@@ -86,6 +92,12 @@ CASES = [
      dict(stepper="bdf", bdf_order=3)),
     ("cloud96x64_cdf2_p2", lambda: workloads.drifting_cloud(n=7777, nx=96, ny=64, seed=26), 6,
      dict(stepper="cdf2")),
+    ("weibel32x24_cdf2semi_p3", lambda: workloads.weibel(32, 24, 8, 0.5, 0.01, 27, 3, n=6001), 10,
+     dict(stepper="cdf2_semi")),
+    ("weibel24x32_cdf2explicit_p2", lambda: workloads.weibel(24, 32, 8, 0.5, 0.01, 28, 2, n=5999),
+     10, dict(stepper="cdf2_explicit")),
+    ("weibel16_dirk2printed_p3", lambda: workloads.weibel(16, 16, 8, 0.5, 0.01, 29, 3, n=2047), 10,
+     dict(stepper="dirk", dirk=osteps.DIRK2_AS_PRINTED)),
 ]
 
 
@@ -120,7 +132,7 @@ def test_parity_step_phases_match_pic_step(device):
 
 
 @pytest.mark.parametrize("stepper,kw", [("bdf", dict(bdf_order=1)), ("bdf", dict(bdf_order=2)),
-                                        ("cdf2", {}),
+                                        ("cdf2", {}), ("cdf2_semi", {}),
                                         ("dirk", dict(dirk=osteps.DIRK2_QIN_ZHANG))])
 def test_diagnostics_invariants_and_energies(device, stepper, kw):
     wl = workloads.drifting_cloud(n=6000, nx=32, ny=32, seed=41)
@@ -133,6 +145,9 @@ def test_diagnostics_invariants_and_energies(device, stepper, kw):
     if stepper == "dirk":
         assert d["gauge_dt_rms"] <= 1e-11 * d["rho_rms"], d
         assert d["gauss_rms"] > 1e-9 * d["rho_rms"]        # not a theorem for DIRK
+    elif stepper == "cdf2_semi":
+        # Gauss as the implicit form defines it is not a theorem for the semi-implicit form
+        assert d["gauss_rms"] > 1e-9 * d["rho_rms"]
     else:
         assert d["gauss_rms"] <= 1e-11 * d["rho_rms"], d
     e = opic.energies(ocfg, st)
