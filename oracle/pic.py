@@ -53,6 +53,7 @@ class Config:
     bdf_order: int = 1
     dirk: dict = None               # {"A": [[..]], "b": [..], "c": [..]}
     cdf_form: str = "implicit"      # CDF-2 only: "implicit" | "semi" | "explicit" (section 3.1)
+    charge: str = "continuity"      # "continuity" | "deposit" (the naive update of section 5)
     c: float = 1.0
     eps0: float = 1.0
     q: float = -1.0
@@ -173,13 +174,26 @@ def _grid_fields(cfg, phi_hat, ax_hat, ay_hat):
     return {name: spectral.idft2(s).real for name, s in spectra.items()}
 
 
-def field_solve(cfg, st, jx, jy):
+def deposited_charge_hat(cfg, x, y):
+    """Spectrum of the charge deposited at the given positions, its K = 0 modes removed
+    as at t = 0 (reading R15): rho^{n+1} of the naive update that section 5 compares
+    against (both rho and J mapped to the mesh with the particle shape)."""
+    kx, ky, K = _k(cfg)
+    rho_hat = spectral.dft2(deposit(cfg, x, y, np.full(len(x), cfg.w * cfg.q)))
+    rho_hat[K == 0.0] = 0.0
+    return rho_hat
+
+
+def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
     """Continuity + implicit wave solve + spectral gradients for the new J (Algorithm 1).
 
     Updates st.hist, records residual spectra in st.res (before the history shift,
     so every level a residual needs is still there) and returns the eight mesh
-    fields the particles gather.
+    fields the particles gather.  With cfg.charge == "deposit" (BDF-k and DIRK only),
+    rho^{n+1} is rho_dep_hat, the deposited charge, instead of the continuity update.
     """
+    if cfg.charge == "deposit" and (rho_dep_hat is None or cfg.stepper == "cdf2"):
+        raise ValueError("the deposited-charge update needs rho_dep_hat and a BDF or DIRK stepper")
     kx, ky, K = _k(cfg)
     c, dt, eps0, mu0 = cfg.c, cfg.dt, cfg.eps0, cfg.mu0
     h = st.hist
@@ -193,6 +207,8 @@ def field_solve(cfg, st, jx, jy):
         C = steppers.bdf_second_derivative_coefficients(a)
         bdt = float(beta) * dt
         rho_new = steppers.bdf_continuity(h["rho"], divj, dt, a, beta)
+        if cfg.charge == "deposit":
+            rho_new = rho_dep_hat
         phi_new = steppers.bdf_wave_update(h["phi"], rho_new / eps0, K, c, dt, beta, C)
         ax_new = steppers.bdf_wave_update(h["ax"], mu0 * jx_hat, K, c, dt, beta, C)
         ay_new = steppers.bdf_wave_update(h["ay"], mu0 * jy_hat, K, c, dt, beta, C)
@@ -257,6 +273,8 @@ def field_solve(cfg, st, jx, jy):
         A, b, cv = cfg.dirk["A"], cfg.dirk["b"], cfg.dirk["c"]
         divj_n = spectral.div_hat(h["jx"], h["jy"], kx, ky)
         rho_new = steppers.dirk_continuity(h["rho"], divj_n, divj, dt, b, cv)
+        if cfg.charge == "deposit":
+            rho_new = rho_dep_hat
         phi_new, vphi_new = steppers.dirk_wave_update(
             h["phi"], h["vphi"], h["rho"] / eps0, rho_new / eps0, K, c, dt, A, b, cv)
         ax_new, vax_new = steppers.dirk_wave_update(
@@ -372,7 +390,8 @@ def step(cfg, st):
     qp = cfg.w * cfg.q
     jx = deposit(cfg, st.x, st.y, qp * st.vx)
     jy = deposit(cfg, st.x, st.y, qp * st.vy)
-    fields = field_solve(cfg, st, jx, jy)
+    rho_dep = deposited_charge_hat(cfg, st.x, st.y) if cfg.charge == "deposit" else None
+    fields = field_solve(cfg, st, jx, jy, rho_dep)
     g = {name: gather(cfg, st.x, st.y, fields[name]) for name in FIELD_NAMES}
     iaem_push(cfg, st, g)
     st.n += 1
@@ -403,7 +422,8 @@ def first_step_sampled(cfg, x0, y0, vx0, vy0, sample):
     qp = cfg.w * cfg.q
     jx = deposit(cfg, x1, y1, qp * vx0)
     jy = deposit(cfg, x1, y1, qp * vy0)
-    fields = field_solve(cfg, st, jx, jy)
+    rho_dep = deposited_charge_hat(cfg, x1, y1) if cfg.charge == "deposit" else None
+    fields = field_solve(cfg, st, jx, jy, rho_dep)
     st.x, st.y = x1[sample], y1[sample]
     g = {name: gather(cfg, st.x, st.y, fields[name]) for name in FIELD_NAMES}
     iaem_push(cfg, st, g)

@@ -371,3 +371,32 @@ def test_first_step_sampled_equals_full_first_step(stepper, extra):
         if name in ("ex0", "ey0"):  # the t = 0 gathers, per particle
             continue
         assert np.array_equal(part.grids[name], g), name
+
+
+@pytest.mark.parametrize("stepper,k,tab", [("bdf", 2, None), ("dirk", 1, steppers.DIRK2_QIN_ZHANG)])
+def test_naive_deposited_charge_breaks_continuity_and_gauge(stepper, k, tab):
+    # section 5: the naive update maps rho to the mesh like J instead of using the
+    # continuity equation; continuity then fails, and the gauge residual is no longer at
+    # roundoff, while the conserving update keeps both (tested above)
+    wl = workloads.drifting_cloud(n=4000, nx=16, ny=16, seed=4)
+    cfg = pic.Config(nx=16, ny=16, lx=1.0, ly=1.0, dt=wl.dt, p=2, stepper=stepper,
+                     bdf_order=k, dirk=tab, w=wl.weight, charge="deposit")
+    st = pic.initial_state(cfg, wl.x, wl.y, wl.vx, wl.vy)
+    for _ in range(10):
+        pic.step(cfg, st)
+    rho_scale = np.max(np.abs(spectral.dft2(st.grids["rho"])))
+    gauge_scale = rho_scale / cfg.dt if stepper != "dirk" else rho_scale * cfg.dt
+    assert np.max(np.abs(st.res["continuity"])) > 1e-6 * rho_scale / cfg.dt
+    assert np.max(np.abs(st.res["gauge"])) > 1e-6 * gauge_scale
+    # rho of the last step is the charge deposited at the particles' positions
+    np.testing.assert_allclose(spectral.dft2(st.grids["rho"]),
+                               pic.deposited_charge_hat(cfg, st.x, st.y), atol=1e-12 * rho_scale)
+
+
+def test_naive_charge_needs_a_bdf_or_dirk_stepper():
+    wl = workloads.drifting_cloud(n=100, nx=16, ny=16, seed=4)
+    cfg = pic.Config(nx=16, ny=16, lx=1.0, ly=1.0, dt=wl.dt, stepper="cdf2", w=wl.weight,
+                     charge="deposit")
+    st = pic.initial_state(cfg, wl.x, wl.y, wl.vx, wl.vy)
+    with pytest.raises(ValueError):
+        pic.step(cfg, st)
