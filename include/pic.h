@@ -103,8 +103,19 @@ typedef struct {
     double dirk_a[16];       /* s x s Butcher matrix, row-major (lower triangular)          */
     double dirk_b[4];        /* Butcher weights                                             */
     double dirk_c[4];        /* Butcher nodes                                               */
-    int32_t reserved[8];     /* must be zero                                                */
+    int32_t charge;          /* pic_charge: where rho^{n+1} comes from (0: continuity)      */
+    int32_t reserved[7];     /* must be zero                                                */
 } pic_config;
+
+/* Source of the charge rho^{n+1} of each step. */
+typedef enum {
+    PIC_CHARGE_CONTINUITY = 0, /* the method: the stepper's continuity update from J^{n+1} */
+    PIC_CHARGE_DEPOSIT = 1     /* the naive update section 5 compares against: rho mapped to
+                                  the mesh from x^{n+1} with the particle shape, like J.
+                                  Continuity and the gauge then hold only approximately.
+                                  BDF-k and DIRK only (PIC_ERR_UNSUPPORTED for CDF-2, whose
+                                  charge lives at half levels) */
+} pic_charge;
 
 /* Initial particle state: positions x^0 (wrapped into the domain by pic_init) and
  * velocities v^0 (|v^0| < c).  Arrays of n FP64 values, host or device. */

@@ -45,6 +45,9 @@ struct ModeCommon {
     const double* kxt;
     const double* kyt;
     const double* invd;
+    // naive update (PIC_CHARGE_DEPOSIT): spectrum of the charge deposited at x^{n+1}
+    // (raw shape-weight sums, storage type of the form); NULL: continuity
+    const void* zq;
 };
 
 struct BdfParams {

@@ -179,14 +179,24 @@ __device__ __forceinline__ void hstore(void* p, int idx, zd v) {
 
 // ---------------------------------------------------------------- BDF-k ----
 
+// rho^{n+1} of the naive update: the deposited charge's spectrum in density units, its
+// K = 0 modes removed as at t = 0 (reading R15).
+template <typename C>
+__device__ __forceinline__ zd deposited_rho(const ModeCommon& mc, const ModeIn& m) {
+    if (m.K == 0.0) return zd{0.0, 0.0};
+    return zscale(mc.jscale, zload(reinterpret_cast<const C*>(mc.zq) + m.idx));
+}
+
 // The BDF-k recurrences of one mode: continuity and the phi wave update; the A wave
 // updates.
 __device__ __forceinline__ void bdf_rho_phi(const ModeCommon& mc, const BdfParams& bp,
-                                            const ModeIn& m, zd& rho_new, zd& phi_new) {
+                                            const ModeIn& m, zd& rho_new, zd& phi_new,
+                                            const zd* rho_dep = nullptr) {
     const int idx = m.idx, k = bp.k;
     rho_new = zscale(-bp.bdt, m.divj);
     for (int d = 1; d <= k; ++d) rho_new = zfms(rho_new, bp.a[d], hload(bp.rho[d - 1], idx));
     rho_new = zscale(1.0 / bp.a[0], rho_new);
+    if (rho_dep) rho_new = *rho_dep;  // the naive update: the deposited charge
     zd sphi = zscale(bp.g / mc.eps0, rho_new);
     for (int d = 1; d <= 2 * k; ++d) sphi = zfms(sphi, bp.C[d], hload(bp.phi[d - 1], idx));
     phi_new = zscale(mc.invd[idx], sphi);  // 1/(C_0 + g K)
@@ -210,7 +220,9 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParam
                                             const ModeIn& m, double* acc, C* epk, C* out) {
     const int idx = m.idx, k = bp.k;
     zd rho_new, phi_new, ax_new, ay_new;
-    bdf_rho_phi(mc, bp, m, rho_new, phi_new);
+    zd rho_dep;
+    if (mc.zq) rho_dep = deposited_rho<C>(mc, m);
+    bdf_rho_phi(mc, bp, m, rho_new, phi_new, mc.zq ? &rho_dep : nullptr);
     bdf_a(mc, bp, m, ax_new, ay_new);
     if (mc.diag) {
         // section 3.2: gauge eps_1, continuity eps_2, and Gauss with
@@ -349,6 +361,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkPara
     zd rho_new = rho;
     for (int i = 0; i < dp.s; ++i)
         rho_new = rho_new - (h * dp.b[i]) * ((1.0 - dp.c[i]) * divjn + dp.c[i] * m.divj);
+    if (mc.zq) rho_new = deposited_rho<C>(mc, m);  // the naive update
     zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
     const double ie = 1.0 / mc.eps0;
     const double* dinv = mc.invd + idx;

@@ -64,6 +64,10 @@ struct pic_handle {
     void* G = nullptr;       // [node][4] complex: the eight real gather fields
     void* E = nullptr;       // packed E spectrum of the last diagnosed step
     void* tmp = nullptr;     // complex scratch (ng)
+    // naive update (PIC_CHARGE_DEPOSIT): the deposited charge (FP64 pairs, or int64 sums
+    // in the FP32 form) and its spectrum
+    void* rhoq = nullptr;
+    void* ZQ = nullptr;
     double* tmpd = nullptr;  // real scratch (ng)
     void *twx = nullptr, *twy = nullptr;
     FftDesc fx{}, fy{};
@@ -140,8 +144,15 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 pic_status validate(const pic_config* c, const pic_particles_in* in) {
     pic_handle* h = nullptr;
     if (!c || !in) return fail(h, PIC_ERR_INVALID_ARG, "cfg and init must not be NULL");
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (c->reserved[i] != 0) return fail(h, PIC_ERR_INVALID_ARG, "reserved fields must be 0");
+    if (c->charge != PIC_CHARGE_CONTINUITY && c->charge != PIC_CHARGE_DEPOSIT)
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown charge source %d", c->charge);
+    if (c->charge == PIC_CHARGE_DEPOSIT &&
+        (c->stepper == PIC_STEPPER_CDF2 || c->stepper == PIC_STEPPER_CDF2_SEMI ||
+         c->stepper == PIC_STEPPER_CDF2_EXPLICIT))
+        return fail(h, PIC_ERR_UNSUPPORTED,
+                    "a deposited charge needs integer time levels: BDF-k or DIRK, not CDF-2");
     FftDesc d;
     for (int n : {c->nx, c->ny})
         if (n < 8 || n > 1024 || (n & 1) || !factor_23(n, d))
@@ -320,6 +331,11 @@ pic_status alloc_state(pic_handle* h) {
         CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));
     }
     CK(dalloc(h, &h->Z, h->ng * cs));
+    if (h->cfg.charge == PIC_CHARGE_DEPOSIT) {
+        CK(dalloc(h, &h->rhoq, h->ng * sizeof(double2)));
+        CK(dalloc(h, &h->ZQ, h->ng * cs));
+        h->mc.zq = h->ZQ;
+    }
     CK(dalloc(h, &h->F4, 4 * h->ng * cs));
     CK(dalloc(h, &h->G, 4 * h->ng * cs));
     CK(dalloc(h, &h->E, h->ng * cs));
@@ -671,6 +687,28 @@ pic_status pic_field_solve(pic_handle* h) {
         using T = decltype(t);
         return launch_fft_x<T>(h->Z, h->Z, h->nx, h->ny, 1, h->fx, h->twx, -1, h->s);
     }));
+
+    // the naive update takes rho^{n+1} from the charge deposited at x^{n+1}, transformed
+    // like the t = 0 charge
+    if (h->cfg.charge == PIC_CHARGE_DEPOSIT) {
+        CK(cudaMemsetAsync(h->rhoq, 0, h->ng * sizeof(double2), h->s));
+        CK(by_prec(h, [&](auto t) -> cudaError_t {
+            using T = decltype(t);
+            cudaError_t r;
+            if (h->fp32) {
+                r = launch_deposit_charge_fix<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y,
+                                                 h->n, (longlong2*)h->rhoq, h->fix_scale_q,
+                                                 h->err, h->s);
+                if (r == cudaSuccess)
+                    r = launch_fix_to_cplx<T>((const longlong2*)h->rhoq, h->fix_unscale_q, h->tmp,
+                                              h->ng, h->s);
+                return r == cudaSuccess ? forward_fft(h, h->tmp, h->ZQ) : r;
+            }
+            r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, h->n,
+                                         (double2*)h->rhoq, h->err, h->s);
+            return r == cudaSuccess ? forward_fft(h, h->rhoq, h->ZQ) : r;
+        }));
+    }
 
     // per-mode update with the stepper's history levels
     const int st = h->cfg.stepper;

@@ -52,7 +52,8 @@ class PicConfig(ctypes.Structure):
         ("q", ctypes.c_double), ("m", ctypes.c_double), ("weight", ctypes.c_double),
         ("dirk_a", ctypes.c_double * 16), ("dirk_b", ctypes.c_double * 4),
         ("dirk_c", ctypes.c_double * 4),
-        ("reserved", ctypes.c_int32 * 8),
+        ("charge", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -133,8 +134,12 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+CHARGE_CONTINUITY, CHARGE_DEPOSIT = 0, 1
+
+
 def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, c=1.0, eps0=1.0,
-                q=-1.0, m=1.0, weight=1.0, precision=FP64, sort_interval=0):
+                q=-1.0, m=1.0, weight=1.0, precision=FP64, sort_interval=0,
+                charge=CHARGE_CONTINUITY):
     cfg = PicConfig()
     cfg.nx, cfg.ny, cfg.lx, cfg.ly, cfg.dt = nx, ny, lx, ly, dt
     cfg.spline_order = p
@@ -143,6 +148,7 @@ def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, 
     cfg.c, cfg.eps0, cfg.q, cfg.m, cfg.weight = c, eps0, q, m, weight
     cfg.precision = precision
     cfg.sort_interval = sort_interval
+    cfg.charge = charge
     if dirk is not None:
         s = len(dirk["b"])
         cfg.dirk_stages = s

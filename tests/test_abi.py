@@ -55,9 +55,10 @@ def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
-        "int main(){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_config),"
+        "int main(){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_config),"
         " offsetof(pic_config, lx), offsetof(pic_config, dirk_a), offsetof(pic_config, reserved),"
-        " sizeof(pic_diagnostics), sizeof(pic_particles_in), offsetof(pic_diagnostics, step));"
+        " sizeof(pic_diagnostics), sizeof(pic_particles_in), offsetof(pic_diagnostics, step),"
+        " offsetof(pic_config, charge));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -65,7 +66,8 @@ def test_struct_layout_matches_header(tmp_path):
                                              check=True).stdout.split()]
     py_vals = [ctypes.sizeof(pic.PicConfig), pic.PicConfig.lx.offset, pic.PicConfig.dirk_a.offset,
                pic.PicConfig.reserved.offset, ctypes.sizeof(pic.PicDiagnostics),
-               ctypes.sizeof(pic.PicParticlesIn), pic.PicDiagnostics.step.offset]
+               ctypes.sizeof(pic.PicParticlesIn), pic.PicDiagnostics.step.offset,
+               pic.PicConfig.charge.offset]
     assert c_vals == py_vals
 
 
@@ -82,10 +84,17 @@ def _bad(lib, **kw):
     dict(nx=7), dict(nx=10), dict(ny=2048), dict(nx=14), dict(p=5), dict(p=1), dict(dt=-1.0),
     dict(dt=2.0), dict(bdf_order=7), dict(bdf_order=0), dict(stepper=9), dict(lx=float("nan")),
     dict(stepper="dirk"),  # zero stages
+    dict(charge=2),
 ])
 def test_invalid_config_is_rejected_without_a_device(lib, kw):
     err = _bad(lib, **kw)
     assert err.status == 1, err
+
+
+@pytest.mark.parametrize("stepper", ["cdf2", "cdf2_semi", "cdf2_explicit"])
+def test_deposited_charge_with_cdf2_is_unsupported(lib, stepper):
+    # CDF-2 keeps its charge at half levels; a deposit at x^{n+1} has no place there
+    assert _bad(lib, stepper=stepper, charge=pic.CHARGE_DEPOSIT).status == 2
 
 
 def test_upper_triangular_dirk_rejected(lib):

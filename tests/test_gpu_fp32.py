@@ -71,6 +71,8 @@ CASES = [
      dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG)),
     ("weibel48x32_dirk3_p4", lambda: workloads.weibel(48, 32, 3, 0.6, 0.02, 24, 4, n=4099),
      dict(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT)),
+    ("weibel24x16_bdf2_naive_p3", lambda: workloads.weibel(24, 16, 8, 0.5, 0.01, 33, 3, n=3001),
+     dict(stepper="bdf", bdf_order=2, charge="deposit")),
 ]
 
 
@@ -78,7 +80,11 @@ CASES = [
 def test_fp32_form_against_oracle(device, name, make, kw):
     wl = make()
     nsteps = 10
-    sim = fp32_sim(wl, device, diag=1, **kw)
+    naive = kw.get("charge") == "deposit"
+    gkw = {k: v for k, v in kw.items() if k != "charge"}
+    if naive:
+        gkw["charge"] = pic.CHARGE_DEPOSIT
+    sim = fp32_sim(wl, device, diag=1, **gkw)
     sim.step(nsteps)
     got = sim.particles()
     ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, w=wl.weight, **kw)
@@ -90,8 +96,12 @@ def test_fp32_form_against_oracle(device, name, make, kw):
              ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "dphidx", "daxdx", "daydy")}
     bad.update({k: v for k, v in ferrs.items() if not v <= F_TOL})
     assert not bad, bad
-    # the theorems of section 3 hold to FP64 roundoff in the FP32 form too
+    # the theorems of section 3 hold to FP64 roundoff in the FP32 form too (not for the
+    # naive update, which gives them up)
     d = sim.residuals()
+    if naive:
+        sim.close()
+        return
     assert d["gauge_rms"] <= 1e-11 * d["div_a_rms"], d
     assert d["continuity_rms"] <= 1e-11 * d["rho_rms"] / wl.dt, d
     if kw["stepper"] != "dirk":

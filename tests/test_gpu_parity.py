@@ -49,17 +49,19 @@ CDF_FORMS = {"cdf2": ("cdf2", "implicit"), "cdf2_semi": ("cdf2", "semi"),
              "cdf2_explicit": ("cdf2", "explicit")}
 
 
-def run_both(wl, device, nsteps, stepper="bdf", bdf_order=1, dirk=None, p=None, diag=0):
+def run_both(wl, device, nsteps, stepper="bdf", bdf_order=1, dirk=None, p=None, diag=0,
+             charge=pic.CHARGE_CONTINUITY):
     p = wl.p if p is None else p
     cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=p, stepper=stepper,
-                          bdf_order=bdf_order, dirk=dirk, weight=wl.weight)
+                          bdf_order=bdf_order, dirk=dirk, weight=wl.weight, charge=charge)
     sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device)
     if diag:
         sim.set_diagnostics(diag)
     sim.step(nsteps)
     ostepper, form = CDF_FORMS.get(stepper, (stepper, "implicit"))
     ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=p, stepper=ostepper,
-                       bdf_order=bdf_order, dirk=dirk, w=wl.weight, cdf_form=form)
+                       bdf_order=bdf_order, dirk=dirk, w=wl.weight, cdf_form=form,
+                       charge="deposit" if charge == pic.CHARGE_DEPOSIT else "continuity")
     st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, nsteps)
     return sim, st, ocfg
 
@@ -98,6 +100,11 @@ CASES = [
      10, dict(stepper="cdf2_explicit")),
     ("weibel16_dirk2printed_p3", lambda: workloads.weibel(16, 16, 8, 0.5, 0.01, 29, 3, n=2047), 10,
      dict(stepper="dirk", dirk=osteps.DIRK2_AS_PRINTED)),
+    # the naive update of section 5: rho^{n+1} deposited instead of from continuity
+    ("weibel24x16_bdf2_naive_p2", lambda: workloads.weibel(24, 16, 8, 0.5, 0.01, 30, 2, n=3001), 10,
+     dict(stepper="bdf", bdf_order=2, charge=pic.CHARGE_DEPOSIT)),
+    ("weibel16_dirk2_naive_p3", lambda: workloads.weibel(16, 16, 8, 0.5, 0.01, 31, 3, n=2047), 10,
+     dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG, charge=pic.CHARGE_DEPOSIT)),
 ]
 
 
@@ -289,3 +296,22 @@ def test_tile_sort_full_size_weibel_128(device):
                               bdf_order=2, w=wl.weight), wl.x, wl.y, wl.vx, wl.vy, 2)
     compare(sim, st, wl, fields=("jx", "jy", "phi", "ax", "dphidx"))
     sim.close()
+
+
+def test_naive_charge_breaks_the_gauge_as_section_5_reports(device):
+    # with the deposited charge, the gauge and continuity residuals leave roundoff; with
+    # the conserving update they stay there (same workload, same steps)
+    wl = workloads.weibel(32, 32, 8, 0.5, 0.01, 32, 2, n=8191)
+    out = {}
+    for charge in (pic.CHARGE_CONTINUITY, pic.CHARGE_DEPOSIT):
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf",
+                              bdf_order=2, weight=wl.weight, charge=charge)
+        with pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device) as sim:
+            sim.set_diagnostics(1)
+            sim.step(20)
+            out[charge] = sim.residuals()
+    good, naive = out[pic.CHARGE_CONTINUITY], out[pic.CHARGE_DEPOSIT]
+    assert good["gauge_rms"] <= 1e-11 * good["div_a_rms"]
+    assert naive["gauge_rms"] > 1e-6 * naive["div_a_rms"], naive
+    assert naive["continuity_rms"] > 1e-6 * naive["rho_rms"] / wl.dt, naive
+
