@@ -22,6 +22,8 @@ Modules:
   steppers  -- BDF-k, CDF-2 and s-stage DIRK per-mode wave updates (section 3)
   pic       -- deposit, gather, IAEM push, initial state, Algorithm 1 step,
                residuals and energies (sections 2, 3, 4)
+  adjoint   -- discrete adjoint of the BDF-k step: gradients of the final magnetic
+               energy (or final momenta) with respect to v^0 and P^0
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 against something the paper or plain mathematics fixes.
