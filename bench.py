@@ -39,9 +39,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["ensemble256"], default="weibel128",
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["ensemble256", "adjoint128"],
+                    default="weibel128",
                     help="weibel128: the headline configuration; weibel512: the large one; "
-                         "ensemble256: 256 independent runs in one graph launch per period")
+                         "ensemble256: 256 independent runs in one graph launch per period; "
+                         "adjoint128: gradient of the final magnetic energy (FP64 adjoint)")
+    ap.add_argument("--repeats", type=int, default=3,
+                    help="adjoint128: timed gradient evaluations per checkpoint interval")
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default=None,
                     help="default: the workload's own (bdf2 for weibel128, dirk3 for weibel512)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
@@ -459,6 +463,93 @@ def run_ensemble(a):
     print(json.dumps(line))
 
 
+def run_adjoint(a):
+    """Gradient of the magnetic energy W_B = 1/2 sum B_z^2 dx dy after 200 steps of the
+    128x128 Weibel run with 16 particles per cell (262,144), FP64, BDF-2, cubic, with
+    respect to every initial velocity and momentum, by the library's adjoint.  Timed per
+    whole run with CUDA events (L2 flushed between runs): the plain forward run
+    (pic_step), the recording forward run and the reverse sweep, with checkpoints every
+    20 steps (the backward pass recomputes 9 of the 10 segments) and with every step kept
+    in HBM (3.4 GB, nothing recomputed).  value = (recording forward + reverse sweep) /
+    plain forward at K = 20."""
+    import torch
+    from paper_2410_18414_gb300 import pic, workloads
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    pic.load_library()
+    wl = workloads.weibel_adjoint_128(seed=5 + rank)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf", bdf_order=2,
+                          weight=wl.weight)
+    N = min(wl.nsteps, a.steps)   # --steps shortens the run (profiling); default: all 200
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    area = (wl.lx / wl.nx) * (wl.ly / wl.ny)
+    x = torch.tensor(wl.x, device="cuda")
+    y = torch.tensor(wl.y, device="cuda")
+    vx = torch.tensor(wl.vx, device="cuda")
+    vy = torch.tensor(wl.vy, device="cuda")
+    bz = torch.empty((wl.nx, wl.ny), dtype=torch.float64, device="cuda")
+    out = {k: torch.empty(wl.n, dtype=torch.float64, device="cuda") for k in ("vx", "vy", "px", "py")}
+
+    def once(K):
+        sim = pic.Simulation(cfg, x, y, vx, vy, stream=sid)
+        adj = pic.Adjoint(sim, N, K) if K else None
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        if adj is None:
+            sim.step(N)
+        else:
+            adj.forward()
+        ev[1].record(stream)
+        if adj is not None:
+            sim.field("bz", out=bz)
+            adj.backward(bz_bar=(bz * area).contiguous(), out=out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if adj is not None:
+            adj.close()
+        sim.close()
+        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+
+    for K in (0, min(20, N), N):      # warm-up: one of each
+        once(K)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    reps = max(1, a.repeats)
+    fwd = [once(0)[0] for _ in range(reps)]
+    k20 = [once(min(20, N)) for _ in range(reps)]
+    kall = [once(N) for _ in range(reps)]
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    med = statistics.median
+    f = med(fwd)
+    r20 = (med([t[0] for t in k20]) + med([t[1] for t in k20])) / f
+    rall = (med([t[0] for t in kall]) + med([t[1] for t in kall])) / f
+    line = {
+        "metric": "adjoint/forward time", "value": r20, "unit": "ratio", "n_gpus": world,
+        "steps": N, "warmup": 1, "repeats": reps, "ms_per_step": med([t[1] for t in k20]) / N,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "particles": wl.n,
+                   "steps_per_run": N, "objective": "W_B at the last step",
+                   "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": "fp64",
+                   "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
+        "forward_ms": f,
+        "checkpoint_20": {"record_forward_ms": med([t[0] for t in k20]),
+                          "backward_ms": med([t[1] for t in k20]), "ratio": r20},
+        "keep_all_steps": {"record_forward_ms": med([t[0] for t in kall]),
+                           "backward_ms": med([t[1] for t in kall]), "ratio": rall,
+                           "hbm_bytes": int(N * (64 * wl.n + 64 * wl.nx * wl.ny))},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -466,6 +557,9 @@ def main():
         return
     if a.workload == "ensemble256":
         run_ensemble(a)
+        return
+    if a.workload == "adjoint128":
+        run_adjoint(a)
         return
     import numpy as np
     import torch

@@ -269,6 +269,65 @@ const char *pic_last_error(const pic_handle *h);
 /* Release every device allocation of the handle.  NULL is allowed. */
 void pic_destroy(pic_handle *h);
 
+/* ---------------------------------------------------------------- adjoint ----
+ * Discrete adjoint of the FP64 BDF-k step: the exact gradient of an objective of the
+ * final state,
+ *     J = sum_ij bz_bar(i, j) B_z(i, j) + sum_p (px_bar_p Px_p + py_bar_p Py_p),
+ * B_z = dAy/dx - dAx/dy of the last level and P the last momenta, with respect to the
+ * initial velocities v^0 given to pic_init (and, with P^0 = gamma m v^0 taken as the
+ * independent variable, with respect to P^0).  For the magnetic energy
+ * W_B = 1/2 sum B_z^2 dx dy (section 5) pass bz_bar = B_z dx dy.  The gradient is the
+ * transpose of the Jacobian of the forward map that pic_step computes (Algorithm 1 of
+ * section 4.2 with the BDF-k update of section 3.2 and the charge from continuity),
+ * applied step by step in reverse:
+ *   - the transpose of the current deposit is a gather of the current's adjoint with
+ *     the shape weights and their derivatives;
+ *   - the transpose of the field gather is a deposit of the eight field adjoints;
+ *   - per Fourier mode, the BDF-k recurrences run backwards with their real
+ *     multipliers, and i k maps to -i k;
+ *   - the IAEM push and the t = 0 set-up (P^0 = gamma m v^0 and the Taylor start
+ *     v^{-1}) are transposed per particle.
+ * The paper states the forward method only; the adjoint is a derived capability.
+ *
+ * Memory: the state (particles and field histories) is checkpointed every
+ * `checkpoint_every` steps (K).  The backward pass recomputes each segment of K steps
+ * from its checkpoint, keeping that segment's per-step particle state and gather fields
+ * (8 n + 64 nx ny bytes per step), then runs it backwards.  The last segment is kept by
+ * the forward pass itself, so with K = nsteps nothing is recomputed.  Device memory
+ * used: about (nsteps/K + 1) * 64 n + K * (64 n + 64 nx ny) bytes plus the adjoint state. */
+typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
+
+/* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init
+ * (step 0, no step started), FP64, PIC_STEPPER_BDF, PIC_CHARGE_CONTINUITY and without
+ * sorting (sort_interval 0), else PIC_ERR_UNSUPPORTED (or PIC_ERR_STATE for a handle
+ * that has stepped).  checkpoint_every is clamped to 1..nsteps.  Allocates all the
+ * adjoint's device memory here (PIC_ERR_CUDA if that fails).  The adjoint keeps h:
+ * destroy it before h.  PIC_ERR_INVALID_ARG for NULL pointers or nsteps < 1. */
+pic_status pic_adjoint_create(pic_handle *h, int32_t nsteps, int32_t checkpoint_every,
+                              pic_adjoint **out);
+
+/* Run the nsteps forward steps on h (as pic_step), keeping the checkpoints.  Once only;
+ * PIC_ERR_STATE on a second call. */
+pic_status pic_adjoint_forward(pic_adjoint *a);
+
+/* Gradient of J (defined above) after pic_adjoint_forward.  Inputs (device memory, FP64,
+ * any may be NULL for a zero term): bz_bar nx*ny (grid layout), px_bar, py_bar n each
+ * (the order of pic_init).  Outputs (device memory, FP64, n each, any may be NULL):
+ * dJ/dvx^0, dJ/dvy^0, and dJ/dPx^0, dJ/dPy^0 with P^0 independent.  May be called again
+ * with other seeds.  h is left with the state of the end of the forward run (particles,
+ * histories, J and gather fields of the last step).  Enqueued on h's stream;
+ * synchronizes at the end and reports latched device errors.  PIC_ERR_STATE before
+ * pic_adjoint_forward. */
+pic_status pic_adjoint_backward(pic_adjoint *a, const double *bz_bar, const double *px_bar,
+                                const double *py_bar, double *dvx0, double *dvy0,
+                                double *dpx0, double *dpy0);
+
+/* Steps between checkpoints after clamping (0 for NULL). */
+int32_t pic_adjoint_checkpoint_every(const pic_adjoint *a);
+
+/* Release the adjoint's device memory (not the handle).  NULL is allowed. */
+void pic_adjoint_destroy(pic_adjoint *a);
+
 /* Allocation-free move + deposit pass (the first two lines of one step, as pic_deposit
  * does them) for callers that cannot let a library allocate device memory: hosts whose
  * GPU memory is owned by their own pool allocator (a hidden cudaMalloc would fail or

@@ -1,0 +1,472 @@
+// Discrete adjoint of the FP64 BDF-k step: the transpose of the Jacobian of one step of
+// Algorithm 1 (section 4.2) with the BDF-k field solve of section 3.2, applied in
+// reverse, for the gradient of an objective of the final state with respect to the
+// initial velocities.
+//
+// Adjoint of a quantity z is written zb; the pairing is the plain sum over particles and
+// grid nodes, and Re sum conj(zb) dz for a spectrum.  Reverse of step n -> n+1:
+//
+//   push + gather (k_adj_push_gather), per particle at x^{n+1}:
+//     u = P^{n+1} - q A_p, v^{n+1} = c^2 u / D, D = sqrt(c^2 |u|^2 + (m c^2)^2)
+//     ub = (c^2/D) (vb - c^2 u (u . vb)/D^2);  Pb += ub;  A_p b = -q ub
+//     P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*):  (grad phi)b = -q dt Pb,
+//       (d_l A_m)b = q dt Pb_l v*_m,  v*b_m = q dt sum_l Pb_l d_l A_m
+//     v* = 2 v^n - v^{n-1}:  v^n b += 2 v*b,  v^{n-1} b = -v*b
+//     the gather's transpose deposits the eight field adjoints with the same weights,
+//     and x^{n+1} b gets sum_f gb_f grad(sum_node F_f W)
+//   field solve (k_adj_modes_bdf), per mode, after forward transforms of the deposited
+//     field adjoints: conj(i k) = -i k for the spectral gradients, then the BDF-k
+//     recurrences run backwards with their real multipliers, ending in the adjoint of
+//     the current spectrum, inverse-transformed to the mesh
+//   deposit + move (k_adj_deposit_move), per particle:
+//     J = q_p v^n W(x^{n+1}) / (dx dy):  v^n b += gather(Jb),
+//       x^{n+1} b += v^n . grad gather(Jb)   (q_p/(dx dy) folded into Jb)
+//     x^{n+1} = x^n + dt v^n:  x^n b = x^{n+1} b,  v^n b += dt x^{n+1} b
+//   t = 0 (k_adj_init): P^0 = gamma m v^0 and the Taylor start v^{-1}(v^0, E^0).
+//
+// Everything is FP64, one thread per particle or per mode.  Shape weights come from
+// Shape<P, double> (the forward's), their derivatives from the closed forms below.
+#include <algorithm>
+
+#include "common.cuh"
+#include "gpic_internal.h"
+
+namespace gpic {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    const int64_t cap = 152 * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// d w[a] / d xi for the weights of Shape<P, double>, from the same offset d.
+template <int P> struct DShape;
+template <> struct DShape<2> {
+    // w = ((1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2)
+    static __device__ __forceinline__ void dweights(double xi, double* dw) {
+        const double d = xi - floor(xi + 0.5);
+        dw[0] = d - 0.5;
+        dw[1] = -2.0 * d;
+        dw[2] = d + 0.5;
+    }
+};
+template <> struct DShape<3> {
+    // w = (e^3/6, 2/3 - d^2 + d^3/2, 2/3 - e^2 + e^3/2, d^3/6), e = 1 - d
+    static __device__ __forceinline__ void dweights(double xi, double* dw) {
+        const double d = xi - floor(xi), e = 1.0 - d;
+        dw[0] = -0.5 * e * e;
+        dw[1] = d * (1.5 * d - 2.0);
+        dw[2] = e * (2.0 - 1.5 * e);
+        dw[3] = 0.5 * d * d;
+    }
+};
+template <> struct DShape<4> {
+    // derivative of (55 + 20 t - 120 t^2 + 80 t^3 - 16 t^4)/96
+    static __device__ __forceinline__ double dmid(double t) {
+        return (20.0 + t * (-240.0 + t * (240.0 - 64.0 * t))) * (1.0 / 96.0);
+    }
+    // w = ((1-2d)^4/384, mid(1+d), (115 - 120 d^2 + 48 d^4)/192, mid(1-d), (1+2d)^4/384)
+    static __device__ __forceinline__ void dweights(double xi, double* dw) {
+        const double d = xi - floor(xi + 0.5);
+        const double a = 1.0 - 2.0 * d, b = 1.0 + 2.0 * d;
+        dw[0] = -a * a * a * (1.0 / 48.0);
+        dw[1] = dmid(1.0 + d);
+        dw[2] = d * (d * d - 1.25);
+        dw[3] = -dmid(1.0 - d);
+        dw[4] = b * b * b * (1.0 / 48.0);
+    }
+};
+
+__device__ __forceinline__ bool inside(double xi, int n) { return xi >= 0.0 && xi <= (double)n; }
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
+                  const double* __restrict__ y1, const double* __restrict__ px1,
+                  const double* __restrict__ py1, const double* __restrict__ vx,
+                  const double* __restrict__ vy, const double* __restrict__ vxo,
+                  const double* __restrict__ vyo, const double2* __restrict__ F, AdjParticles ab,
+                  double2* __restrict__ Fb, int64_t n, unsigned int* __restrict__ err) {
+    const size_t ng = (size_t)g.nx * g.ny;
+    const double q = pp.q, qdt = pp.q * pp.dt, c2 = pp.c * pp.c, mc2 = pp.m * pp.c * pp.c;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = rmul(x1[p], g.inv_dx), yj = rmul(y1[p], g.inv_dy);
+        if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
+            atomicOr(err, (unsigned)ERR_NONFINITE);
+            continue;
+        }
+        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, double>::weights(xi, wx);
+        const int iy = Shape<P, double>::weights(yj, wy);
+        DShape<P>::dweights(xi, dwx);
+        DShape<P>::dweights(yj, dwy);
+        // gathered fields (dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy)
+        double f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const double2* node = F + (row + wrap_idx(iy + b, g.ny)) * 4;
+                const double w = wx[a] * wy[b];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double2 v = __ldg(node + k);
+                    f[2 * k] += w * v.x;
+                    f[2 * k + 1] += w * v.y;
+                }
+            }
+        }
+        // velocity: v = c^2 u / D
+        const double ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
+        const double D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
+        const double vbx = ab.vx[p], vby = ab.vy[p];
+        const double cd = c2 / D, udv = (ux * vbx + uy * vby) * c2 / (D * D);
+        const double ubx = cd * (vbx - ux * udv), uby = cd * (vby - uy * udv);
+        const double pbx = ab.px[p] + ubx, pby = ab.py[p] + uby;
+        // momentum: P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*)
+        const double vsx = 2.0 * vx[p] - vxo[p], vsy = 2.0 * vy[p] - vyo[p];
+        double gb[8];
+        gb[0] = -qdt * pbx;
+        gb[1] = -qdt * pby;
+        gb[2] = -q * ubx;
+        gb[3] = -q * uby;
+        gb[4] = qdt * pbx * vsx;
+        gb[5] = qdt * pby * vsx;
+        gb[6] = qdt * pbx * vsy;
+        gb[7] = qdt * pby * vsy;
+        const double vsbx = qdt * (pbx * f[4] + pby * f[5]);
+        const double vsby = qdt * (pbx * f[6] + pby * f[7]);
+        // second pass over the stencil: the position gradient and the deposit of gb
+        double xg = 0.0, yg = 0.0;
+#pragma unroll 1
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const size_t nd = row + wrap_idx(iy + b, g.ny);
+                const double2* node = F + nd * 4;
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double2 v = __ldg(node + k);
+                    s += gb[2 * k] * v.x + gb[2 * k + 1] * v.y;
+                }
+                xg += s * (dwx[a] * wy[b]);
+                yg += s * (wx[a] * dwy[b]);
+                const double w = wx[a] * wy[b];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    atomicAdd(&Fb[k * ng + nd].x, w * gb[2 * k]);
+                    atomicAdd(&Fb[k * ng + nd].y, w * gb[2 * k + 1]);
+                }
+            }
+        }
+        ab.x[p] += g.inv_dx * xg;
+        ab.y[p] += g.inv_dy * yg;
+        ab.px[p] = pbx;
+        ab.py[p] = pby;
+        ab.vx[p] = ab.vxo[p] + 2.0 * vsbx;
+        ab.vy[p] = ab.vyo[p] + 2.0 * vsby;
+        ab.vxo[p] = -vsbx;
+        ab.vyo[p] = -vsby;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+k_adj_deposit_move(ParticleGeom g, const double* __restrict__ x1, const double* __restrict__ y1,
+                   const double* __restrict__ vx, const double* __restrict__ vy,
+                   const double2* __restrict__ Jb, AdjParticles ab, int64_t n,
+                   unsigned int* __restrict__ err) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = rmul(x1[p], g.inv_dx), yj = rmul(y1[p], g.inv_dy);
+        if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
+            atomicOr(err, (unsigned)ERR_NONFINITE);
+            continue;
+        }
+        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, double>::weights(xi, wx);
+        const int iy = Shape<P, double>::weights(yj, wy);
+        DShape<P>::dweights(xi, dwx);
+        DShape<P>::dweights(yj, dwy);
+        double sx = 0, sy = 0, dxx = 0, dxy = 0, dyx = 0, dyy = 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const double2 j = __ldg(Jb + row + wrap_idx(iy + b, g.ny));
+                const double w = wx[a] * wy[b], ddx = dwx[a] * wy[b], ddy = wx[a] * dwy[b];
+                sx += w * j.x;
+                sy += w * j.y;
+                dxx += ddx * j.x;  // d/dxi of the gathered Jx adjoint
+                dxy += ddx * j.y;  // d/dxi of the gathered Jy adjoint
+                dyx += ddy * j.x;
+                dyy += ddy * j.y;
+            }
+        }
+        const double vxp = vx[p], vyp = vy[p];
+        const double xb = ab.x[p] + g.inv_dx * (vxp * dxx + vyp * dxy);
+        const double yb = ab.y[p] + g.inv_dy * (vxp * dyx + vyp * dyy);
+        ab.x[p] = xb;
+        ab.y[p] = yb;
+        ab.vx[p] = ab.vx[p] + sx + g.dt * xb;
+        ab.vy[p] = ab.vy[p] + sy + g.dt * yb;
+    }
+}
+
+constexpr int kModeThreads = 256;
+
+__device__ __forceinline__ zd zl(const double2* p) { return zd{p->x, p->y}; }
+__device__ __forceinline__ void zs(double2* p, zd v) { *p = make_double2(v.re, v.im); }
+
+__global__ void __launch_bounds__(kModeThreads)
+k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
+                double2* __restrict__ Js) {
+    const int ng = mc.nx * mc.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ng) return;
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const int ip = (i == 0) ? 0 : mc.nx - i;
+    const int jp = (j == 0) ? 0 : mc.ny - j;
+    const int idm = ip * mc.ny + jp;
+    const double kx = mc.kxt[i], ky = mc.kyt[j];
+    // the eight field adjoints' spectra / (nx ny), from the packed pairs (f_2k + i f_2k+1)
+    zd a[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const zd za = zl(Zb + (size_t)k * ng + idx);
+        const zd zb = zconj(zl(Zb + (size_t)k * ng + idm));
+        const double h = 0.5 * mc.inv_n;
+        a[2 * k] = h * (za + zb);
+        const zd d = za - zb;  // 2i F(f_2k+1)
+        a[2 * k + 1] = zd{h * d.im, -h * d.re};
+    }
+    // gradient fields i k_l u: adjoint multiplier -i k_l
+    const zd phis = zl(ap.phi[0] + idx) - zi(kx * a[0]) - zi(ky * a[1]);
+    const zd axs = zl(ap.ax[0] + idx) + a[2] - zi(kx * a[4]) - zi(ky * a[5]);
+    const zd ays = zl(ap.ay[0] + idx) + a[3] - zi(kx * a[6]) - zi(ky * a[7]);
+    // u^{n+1} = (g S - sum_d C_d u^{n+1-d}) / (C_0 + g K)
+    const double inv = mc.invd[idx];
+    const int L = 2 * ap.k;
+    for (int d = 1; d < L; ++d) {
+        const double c = ap.C[d] * inv;
+        zs(ap.phi[d] + idx, zl(ap.phi[d] + idx) - c * phis);
+        zs(ap.ax[d] + idx, zl(ap.ax[d] + idx) - c * axs);
+        zs(ap.ay[d] + idx, zl(ap.ay[d] + idx) - c * ays);
+    }
+    const double cl = ap.C[L] * inv;
+    zs(ap.phi[0] + idx, -(cl * phis));
+    zs(ap.ax[0] + idx, -(cl * axs));
+    zs(ap.ay[0] + idx, -(cl * ays));
+    // rho^{n+1} = -sum_j a_j rho^{n+1-j} - beta dt i k . J   (a_0 = 1); phi's source rho/eps0
+    const zd rhos = zl(ap.rho[0] + idx) + (ap.g * inv / mc.eps0) * phis;
+    for (int d = 1; d < ap.k; ++d) zs(ap.rho[d] + idx, zl(ap.rho[d] + idx) - ap.a[d] * rhos);
+    zs(ap.rho[0] + idx, -(ap.a[ap.k] * rhos));
+    // current: -beta dt i k_l (continuity) and g mu0 / (C_0 + g K) (A's source)
+    const double ga = ap.g * mc.mu0 * inv;
+    const zd jx = zi(ap.bdt * kx * rhos) + ga * axs;
+    const zd jy = zi(ap.bdt * ky * rhos) + ga * ays;
+    // packed (Jx + i Jy), times q_p/(dx dy): the adjoint of the raw deposit sums after
+    // the unnormalised inverse transform
+    zs(Js + idx, mc.jscale * (jx + zi(jy)));
+}
+
+// Final-level seed of an objective sum bzb B_z: B_z = IDFT(i kx Ay - i ky Ax), so
+// Ay b += -i kx DFT(bzb)/N and Ax b += i ky DFT(bzb)/N.
+__global__ void __launch_bounds__(kModeThreads)
+k_adj_seed(ModeCommon mc, const double2* __restrict__ zs_, double2* __restrict__ ax,
+           double2* __restrict__ ay) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= mc.nx * mc.ny) return;
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const double kx = mc.kxt[i], ky = mc.kyt[j];
+    const zd z = mc.inv_n * zl(zs_ + idx);
+    zs(ay + idx, zl(ay + idx) - zi(kx * z));
+    zs(ax + idx, zl(ax + idx) + zi(ky * z));
+}
+
+// (Ex + i Ey)/(nx ny) of E = -grad phi, for an inverse transform to the mesh E^0.
+__global__ void __launch_bounds__(kModeThreads)
+k_adj_e0(ModeCommon mc, const double2* __restrict__ phi, double2* __restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= mc.nx * mc.ny) return;
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const double kx = mc.kxt[i], ky = mc.kyt[j];
+    const zd ph = zl(phi + idx);
+    const zd ex = -zi(kx * ph), ey = -zi(ky * ph);
+    zs(out + idx, mc.inv_n * (ex + zi(ey)));
+}
+
+// dst[k n + i] = src.p[k][i] (pack) or dst.p[k][i] = src[k n + i] (unpack), k = blockIdx.y.
+__global__ void k_pack8(Ptr8 src, double* __restrict__ dst, int64_t n) {
+    const double* s = src.p[blockIdx.y];
+    double* d = dst + (size_t)blockIdx.y * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+__global__ void k_unpack8(const double* __restrict__ src, Ptr8 dst, int64_t n) {
+    const double* s = src + (size_t)blockIdx.y * n;
+    double* d = const_cast<double*>(dst.p[blockIdx.y]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+__global__ void k_real_to_cplx(const double* __restrict__ src, double2* __restrict__ dst,
+                               int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = make_double2(src[p], 0.0);
+}
+
+// t = 0: P^0 = gamma m v^0 and v^{-1} = v^0 - kappa (E - v (v . E)/c^2), kappa =
+// dt q/(gamma m), E = E^0 gathered at x^0.  Gradient with respect to v^0 (gv) and, with
+// P^0 as the independent variable, with respect to P^0 (gp = (dv/dP)^T gv).
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+k_adj_init(ParticleGeom g, PushParams pp, const double* __restrict__ x0,
+           const double* __restrict__ y0, const double* __restrict__ vx0,
+           const double* __restrict__ vy0, const double2* __restrict__ E, AdjParticles ab,
+           double* __restrict__ gvx, double* __restrict__ gvy, double* __restrict__ gpx,
+           double* __restrict__ gpy, int64_t n, unsigned int* __restrict__ err) {
+    const double c2 = pp.c * pp.c, m = pp.m;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x0[p] * g.inv_dx, yj = y0[p] * g.inv_dy;
+        if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
+            atomicOr(err, (unsigned)ERR_NONFINITE);
+            continue;
+        }
+        double wx[P + 1], wy[P + 1];
+        const int ix = Shape<P, double>::weights(xi, wx);
+        const int iy = Shape<P, double>::weights(yj, wy);
+        double ex = 0, ey = 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const double2 e = E[row + wrap_idx(iy + b, g.ny)];
+                const double w = wx[a] * wy[b];
+                ex += w * e.x;
+                ey += w * e.y;
+            }
+        }
+        const double vx = vx0[p], vy = vy0[p];
+        const double gam = 1.0 / sqrt(1.0 - (vx * vx + vy * vy) / c2);
+        // dP/dv = gamma m (I + gamma^2 v v^T / c^2)
+        const double pbx = ab.px[p], pby = ab.py[p];
+        const double pvb = vx * pbx + vy * pby;
+        double gx = ab.vx[p] + gam * m * (pbx + gam * gam * vx * pvb / c2);
+        double gy = ab.vy[p] + gam * m * (pby + gam * gam * vy * pvb / c2);
+        // v^{-1}: transpose of I + kappa gamma^2 T v^T / c^2 + kappa (v E^T + (v.E) I)/c^2
+        const double wxb = ab.vxo[p], wyb = ab.vyo[p];
+        const double kap = pp.dt * pp.q / (gam * m);
+        const double vde = vx * ex + vy * ey;
+        const double tx = ex - vx * vde / c2, ty = ey - vy * vde / c2;
+        const double tw = tx * wxb + ty * wyb, vw = vx * wxb + vy * wyb;
+        gx += wxb + kap * gam * gam * vx * tw / c2 + (kap / c2) * (ex * vw + vde * wxb);
+        gy += wyb + kap * gam * gam * vy * tw / c2 + (kap / c2) * (ey * vw + vde * wyb);
+        if (gvx) gvx[p] = gx;
+        if (gvy) gvy[p] = gy;
+        // dv/dP = (I - v v^T / c^2) / (gamma m)
+        const double vg = vx * gx + vy * gy;
+        if (gpx) gpx[p] = (gx - vx * vg / c2) / (gam * m);
+        if (gpy) gpy[p] = (gy - vy * vg / c2) / (gam * m);
+    }
+}
+
+inline int mode_blocks(const ModeCommon& mc) {
+    return (mc.nx * mc.ny + kModeThreads - 1) / kModeThreads;
+}
+
+}  // namespace
+
+#define GPIC_ADJ_DISPATCH(p, KERNEL, ...)                                                  \
+    switch (p) {                                                                         \
+        case 2: KERNEL<2><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
+        case 3: KERNEL<3><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
+        case 4: KERNEL<4><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
+        default: return cudaErrorInvalidValue;                                          \
+    }
+
+cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
+                                   const double* x1, const double* y1, const double* px1,
+                                   const double* py1, const double* vx, const double* vy,
+                                   const double* vxo, const double* vyo, const double2* F,
+                                   AdjParticles ab, double2* Fb, int64_t n, unsigned int* err,
+                                   cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, F, ab, Fb,
+                      n, err)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
+                                    const double* y1, const double* vx, const double* vy,
+                                    const double2* Jb, AdjParticles ab, int64_t n,
+                                    unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    GPIC_ADJ_DISPATCH(p, k_adj_deposit_move, g, x1, y1, vx, vy, Jb, ab, n, err)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const double* x0,
+                            const double* y0, const double* vx0, const double* vy0,
+                            const double2* E, AdjParticles ab, double* gvx, double* gvy,
+                            double* gpx, double* gpy, int64_t n, unsigned int* err,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    GPIC_ADJ_DISPATCH(p, k_adj_init, g, pp, x0, y0, vx0, vy0, E, ab, gvx, gvy, gpx, gpy, n, err)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
+                                 double2* Js, cudaStream_t s) {
+    k_adj_modes_bdf<<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, ap, Zb, Js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seed(const ModeCommon& mc, const double2* zs_, double2* ax, double2* ay,
+                            cudaStream_t s) {
+    k_adj_seed<<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, zs_, ax, ay);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_e0(const ModeCommon& mc, const double2* phi, double2* out, cudaStream_t s) {
+    k_adj_e0<<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, phi, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack8(Ptr8 src, double* dst, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int bx = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
+    k_pack8<<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack8(const double* src, Ptr8 dst, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int bx = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
+    k_unpack8<<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_real_to_cplx<<<blocks_for(n), kThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace gpic

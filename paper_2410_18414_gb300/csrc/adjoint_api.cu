@@ -1,0 +1,338 @@
+// Host side of the adjoint API (include/pic.h): checkpoints of the forward run, the
+// segment-by-segment recomputation and the reverse sweep of the FP64 BDF-k step.
+//
+// Storage (all FP64, device):
+//   state     the eight particle arrays of one time level, in the order x, y, Px, Py,
+//             v^n (x, y), v^{n-1} (x, y): 8 n values
+//   ck[c]     checkpoint c: the state at step c K, the BDF ring contents in slot order
+//             and the ring heads; ck[nseg] is the end of the run, with the last step's
+//             J and gather fields, so the handle can be put back after the sweep
+//   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1), and
+//             recg[j] the gather fields that step used (the level c0 + j + 1)
+//   adjoint   particle adjoints (8 n), the history adjoints (3 L + k spectra, slot of
+//             time level t = t mod L), field-adjoint planes and transform scratch
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gpic_internal.h"
+#include "handle.h"
+#include "pic.h"
+
+using namespace gpic;
+
+struct pic_adjoint {
+    pic_handle* h = nullptr;
+    int32_t nsteps = 0, K = 0, nseg = 0;
+    int L = 0, Lr = 0;
+    size_t n = 0, ng = 0;
+    struct Ck {
+        double* state = nullptr;
+        double2* hist = nullptr;  // (3 L + Lr) spectra, slot order
+        int head = 0, head_r = 0;
+        int64_t step = 0;
+    };
+    std::vector<Ck> ck;
+    double2* final_j = nullptr;  // J of the last step
+    double2* final_g = nullptr;  // gather fields of the last step
+    double* rec = nullptr;       // K states
+    double2* recg = nullptr;     // K x 4 ng
+    int seg_held = -1;           // segment whose records rec/recg hold
+    double* ab = nullptr;        // particle adjoints, 8 n
+    double2* hb = nullptr;       // history adjoints, (3 L + Lr) ng
+    double2* fb = nullptr;       // field-adjoint planes, 4 ng
+    double2* zb = nullptr;       // their transforms, 4 ng
+    double2* js = nullptr;       // adjoint current spectrum, ng
+    double2* jg = nullptr;       // adjoint current on the mesh, ng
+    double2* e0 = nullptr;       // E^0 on the mesh, ng (Ex, Ey)
+    double2* tmp = nullptr;      // ng
+    bool forward_done = false;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+cudaError_t aalloc(pic_adjoint* a, void** p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) a->allocs.push_back(*p);
+    return e;
+}
+
+void release(pic_adjoint* a) {
+    for (void* p : a->allocs) cudaFree(p);
+    a->allocs.clear();
+}
+
+// The handle's particle arrays in state order (v^n first).
+void handle_arrays(pic_handle* h, void* arr[8]) {
+    arr[0] = h->x;
+    arr[1] = h->y;
+    arr[2] = h->px;
+    arr[3] = h->py;
+    arr[4] = h->v[h->vcur][0];
+    arr[5] = h->v[h->vcur][1];
+    arr[6] = h->v[1 - h->vcur][0];
+    arr[7] = h->v[1 - h->vcur][1];
+}
+
+std::vector<void*> ring_slots(pic_handle* h) {
+    std::vector<void*> s;
+    for (void* p : h->phi_l) s.push_back(p);
+    for (void* p : h->ax_l) s.push_back(p);
+    for (void* p : h->ay_l) s.push_back(p);
+    for (void* p : h->rho_l) s.push_back(p);
+    return s;
+}
+
+Ptr8 handle_ptrs(pic_handle* h) {
+    void* arr[8];
+    handle_arrays(h, arr);
+    Ptr8 p;
+    for (int k = 0; k < 8; ++k) p.p[k] = (const double*)arr[k];
+    return p;
+}
+
+pic_status save_state(pic_adjoint* a, double* dst) {
+    pic_handle* h = a->h;
+    CK(launch_pack8(handle_ptrs(h), dst, (int64_t)a->n, h->s));
+    return PIC_OK;
+}
+
+pic_status save_checkpoint(pic_adjoint* a, pic_adjoint::Ck& c) {
+    pic_handle* h = a->h;
+    pic_status st = save_state(a, c.state);
+    if (st != PIC_OK) return st;
+    const std::vector<void*> slots = ring_slots(h);
+    for (size_t i = 0; i < slots.size(); ++i)
+        CK(cudaMemcpyAsync(c.hist + i * a->ng, slots[i], a->ng * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, h->s));
+    c.head = h->head;
+    c.head_r = h->head_r;
+    c.step = h->step;
+    return PIC_OK;
+}
+
+pic_status restore_checkpoint(pic_adjoint* a, const pic_adjoint::Ck& c) {
+    pic_handle* h = a->h;
+    h->vcur = 0;
+    CK(launch_unpack8(c.state, handle_ptrs(h), (int64_t)a->n, h->s));
+    const std::vector<void*> slots = ring_slots(h);
+    for (size_t i = 0; i < slots.size(); ++i)
+        CK(cudaMemcpyAsync(slots[i], c.hist + i * a->ng, a->ng * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, h->s));
+    h->head = c.head;
+    h->head_r = c.head_r;
+    h->step = c.step;
+    h->phase = 0;
+    return PIC_OK;
+}
+
+// One forward step of h, keeping the new state and the step's gather fields in rec[j].
+pic_status step_and_record(pic_adjoint* a, int j) {
+    pic_handle* h = a->h;
+    pic_status st = pic_step(h, 1);
+    if (st != PIC_OK) return st;
+    st = save_state(a, a->rec + (size_t)j * 8 * a->n);
+    if (st != PIC_OK) return st;
+    CK(cudaMemcpyAsync(a->recg + (size_t)j * 4 * a->ng, h->G, 4 * a->ng * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, h->s));
+    return PIC_OK;
+}
+
+int seg_begin(const pic_adjoint* a, int c) { return c * a->K; }
+int seg_end(const pic_adjoint* a, int c) { return std::min(a->nsteps, (c + 1) * a->K); }
+
+AdjParticles adjoint_arrays(pic_adjoint* a) {
+    double* b = a->ab;
+    const size_t n = a->n;
+    return AdjParticles{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n};
+}
+
+double2* hist_slot(pic_adjoint* a, int field, int64_t t) {
+    // field 0..2: phi, Ax, Ay (L slots each); 3: rho (Lr slots)
+    if (field == 3) {
+        const int s = (int)(((t % a->Lr) + a->Lr) % a->Lr);
+        return a->hb + (size_t)(3 * a->L + s) * a->ng;
+    }
+    const int s = (int)(((t % a->L) + a->L) % a->L);
+    return a->hb + (size_t)(field * a->L + s) * a->ng;
+}
+
+// Reverse of step n (from level n+1 to level n): s0 = state n, s1 = state n+1, g = the
+// gather fields of the step.
+pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const double* s1,
+                         const double2* g) {
+    pic_handle* h = a->h;
+    const size_t np = a->n, ng = a->ng;
+    AdjParticles ab = adjoint_arrays(a);
+    CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
+    CK(launch_adj_push_gather(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np, s1 + 3 * np,
+                              s0 + 4 * np, s0 + 5 * np, s0 + 6 * np, s0 + 7 * np, g, ab, a->fb,
+                              (int64_t)np, h->err, h->s));
+    CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, h->twy, -1, 0, h->s));
+    CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
+    AdjModeParams ap{};
+    ap.k = h->bdf.k;
+    for (int i = 0; i <= ap.k; ++i) ap.a[i] = h->bdf.a[i];
+    for (int d = 0; d <= 2 * ap.k; ++d) ap.C[d] = h->bdf.C[d];
+    ap.g = h->bdf.g;
+    ap.bdt = h->bdf.bdt;
+    for (int d = 0; d < a->L; ++d) {
+        ap.phi[d] = hist_slot(a, 0, n + 1 - d);
+        ap.ax[d] = hist_slot(a, 1, n + 1 - d);
+        ap.ay[d] = hist_slot(a, 2, n + 1 - d);
+    }
+    for (int d = 0; d < a->Lr; ++d) ap.rho[d] = hist_slot(a, 3, n + 1 - d);
+    CK(launch_adj_modes_bdf(h->mc, ap, a->zb, a->js, h->s));
+    CK(inverse_fft(h, a->js, a->jg, 1));
+    CK(launch_adj_deposit_move(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np, a->jg, ab,
+                               (int64_t)np, h->err, h->s));
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_every,
+                              pic_adjoint** out) {
+    if (!out) return fail(h, PIC_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (nsteps < 1) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 1");
+    if (h->fp32 || h->cfg.stepper != PIC_STEPPER_BDF || h->cfg.charge != PIC_CHARGE_CONTINUITY ||
+        h->sorting)
+        return fail(h, PIC_ERR_UNSUPPORTED,
+                    "the adjoint needs the FP64 path, the BDF-k stepper, the continuity charge "
+                    "and no sorting");
+    if (h->step != 0 || h->phase != 0)
+        return fail(h, PIC_ERR_STATE, "the adjoint needs a handle fresh from pic_init");
+    pic_adjoint* a = new pic_adjoint();
+    a->h = h;
+    a->nsteps = nsteps;
+    a->K = std::max(1, std::min(checkpoint_every, nsteps));
+    a->nseg = (nsteps + a->K - 1) / a->K;
+    a->L = h->L;
+    a->Lr = h->Lr;
+    a->n = (size_t)h->n;
+    a->ng = h->ng;
+    const size_t sb = 8 * std::max<size_t>(a->n, 1) * sizeof(double);
+    const size_t hbytes = (size_t)(3 * a->L + a->Lr) * a->ng * sizeof(double2);
+    const size_t gb = a->ng * sizeof(double2);
+    cudaError_t e = cudaSuccess;
+    a->ck.resize(a->nseg + 1);
+    for (auto& c : a->ck) {
+        if (e == cudaSuccess) e = aalloc(a, (void**)&c.state, sb);
+        if (e == cudaSuccess) e = aalloc(a, (void**)&c.hist, hbytes);
+    }
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_j, gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_g, 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->rec, (size_t)a->K * sb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recg, (size_t)a->K * 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->ab, sb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->hb, hbytes);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->fb, 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->zb, 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->js, gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->jg, gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->e0, gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->tmp, gb);
+    // E^0 = -grad phi^0 on the mesh (every phi level holds phi^0 at step 0)
+    if (e == cudaSuccess) e = launch_adj_e0(h->mc, (const double2*)h->phi_l[h->head], a->tmp, h->s);
+    if (e == cudaSuccess) e = inverse_fft(h, a->tmp, a->e0, 1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) {
+        release(a);
+        delete a;
+        return fail(h, PIC_ERR_CUDA, "pic_adjoint_create: %s", cudaGetErrorString(e));
+    }
+    *out = a;
+    return PIC_OK;
+}
+
+pic_status pic_adjoint_forward(pic_adjoint* a) {
+    if (!a) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL adjoint");
+    pic_handle* h = a->h;
+    if (a->forward_done) return fail(h, PIC_ERR_STATE, "pic_adjoint_forward runs once");
+    if (h->step != 0 || h->phase != 0)
+        return fail(h, PIC_ERR_STATE, "the handle has stepped since pic_adjoint_create");
+    a->forward_done = true;
+    for (int c = 0; c < a->nseg; ++c) {
+        pic_status st = save_checkpoint(a, a->ck[c]);
+        if (st != PIC_OK) return st;
+        const bool last = c == a->nseg - 1;
+        for (int s = seg_begin(a, c); s < seg_end(a, c); ++s) {
+            st = last ? step_and_record(a, s - seg_begin(a, c)) : pic_step(h, 1);
+            if (st != PIC_OK) return st;
+        }
+    }
+    a->seg_held = a->nseg - 1;
+    pic_status st = save_checkpoint(a, a->ck[a->nseg]);
+    if (st != PIC_OK) return st;
+    CK(cudaMemcpyAsync(a->final_j, h->J, a->ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(a->final_g, h->G, 4 * a->ng * sizeof(double2), cudaMemcpyDeviceToDevice,
+                       h->s));
+    return PIC_OK;
+}
+
+pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const double* px_bar,
+                                const double* py_bar, double* dvx0, double* dvy0, double* dpx0,
+                                double* dpy0) {
+    if (!a) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL adjoint");
+    pic_handle* h = a->h;
+    if (!a->forward_done) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward needs pic_adjoint_forward");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward inside a step");
+    const size_t np = a->n, ng = a->ng;
+    const size_t hbytes = (size_t)(3 * a->L + a->Lr) * ng * sizeof(double2);
+    CK(cudaMemsetAsync(a->ab, 0, 8 * std::max<size_t>(np, 1) * sizeof(double), h->s));
+    CK(cudaMemsetAsync(a->hb, 0, hbytes, h->s));
+    if (px_bar && np) CK(cudaMemcpyAsync(a->ab + 2 * np, px_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
+    if (py_bar && np) CK(cudaMemcpyAsync(a->ab + 3 * np, py_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
+    if (bz_bar) {
+        CK(launch_real_to_cplx(bz_bar, a->tmp, (int64_t)ng, h->s));
+        CK(forward_fft(h, a->tmp, a->js));
+        CK(launch_adj_seed(h->mc, a->js, hist_slot(a, 1, a->nsteps), hist_slot(a, 2, a->nsteps), h->s));
+    }
+    for (int c = a->nseg - 1; c >= 0; --c) {
+        const int c0 = seg_begin(a, c), c1 = seg_end(a, c);
+        if (a->seg_held != c) {
+            pic_status st = restore_checkpoint(a, a->ck[c]);
+            if (st != PIC_OK) return st;
+            for (int s = c0; s < c1; ++s) {
+                st = step_and_record(a, s - c0);
+                if (st != PIC_OK) return st;
+            }
+            a->seg_held = c;
+        }
+        for (int s = c1 - 1; s >= c0; --s) {
+            const int j = s - c0;
+            const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
+            const double* s1 = a->rec + (size_t)j * 8 * np;
+            pic_status st = backward_step(a, s, s0, s1, a->recg + (size_t)j * 4 * ng);
+            if (st != PIC_OK) return st;
+        }
+    }
+    const double* x0 = a->ck[0].state;
+    CK(launch_adj_init(h->p, h->geom, h->push, x0, x0 + np, x0 + 4 * np, x0 + 5 * np, a->e0,
+                       adjoint_arrays(a), dvx0, dvy0, dpx0, dpy0, (int64_t)np, h->err, h->s));
+    // put the handle back at the end of the forward run
+    pic_status st = restore_checkpoint(a, a->ck[a->nseg]);
+    if (st != PIC_OK) return st;
+    CK(cudaMemcpyAsync(h->J, a->final_j, ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->G, a->final_g, 4 * ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    return check_device_error(h);
+}
+
+int32_t pic_adjoint_checkpoint_every(const pic_adjoint* a) { return a ? a->K : 0; }
+
+void pic_adjoint_destroy(pic_adjoint* a) {
+    if (!a) return;
+    if (a->h) cudaStreamSynchronize(a->h->s);
+    release(a);
+    delete a;
+}
+
+}  // extern "C"

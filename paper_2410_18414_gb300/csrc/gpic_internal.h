@@ -250,6 +250,63 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
                                     const void* fields4, double* diag, unsigned int* err,
                                     cudaStream_t s);
 
+// ---------------------------------------------------------------- adjoint (FP64)
+//
+// Adjoints of the eight particle arrays of one state: x, y, Px, Py, v^n (vx, vy) and
+// v^{n-1} (vxo, vyo).
+struct AdjParticles {
+    double *x, *y, *px, *py, *vx, *vy, *vxo, *vyo;
+};
+// Reverse BDF-k field step: the history adjoints, slot of level d (time n+1-d) for
+// d = 0..2k-1 (rho: d = 0..k-1); level 0 is read first and rewritten with the new
+// oldest level, which shares its slot.
+struct AdjModeParams {
+    int k;
+    double a[kMaxBdf + 1];
+    double C[2 * kMaxBdf + 1];
+    double g, bdt;
+    double2* phi[2 * kMaxBdf];
+    double2* ax[2 * kMaxBdf];
+    double2* ay[2 * kMaxBdf];
+    double2* rho[kMaxBdf];
+};
+// Reverse push + gather of one step: reads x^{n+1}, P^{n+1} (state n+1), v^n, v^{n-1}
+// (state n) and the step's gather fields F ([node][4]); updates the particle adjoints
+// and adds the eight field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
+cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
+                                   const double* x1, const double* y1, const double* px1,
+                                   const double* py1, const double* vx, const double* vy,
+                                   const double* vxo, const double* vyo, const double2* F,
+                                   AdjParticles ab, double2* Fb, int64_t n, unsigned int* err,
+                                   cudaStream_t s);
+// Reverse BDF-k field solve per mode: Zb = forward transforms of the four Fb planes;
+// writes the packed adjoint current spectrum Js (unnormalised inverse transform -> mesh).
+cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
+                                 double2* Js, cudaStream_t s);
+// Reverse deposit + move: gathers the mesh current adjoint Jb ([node] (jx, jy)) at x^{n+1}.
+cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
+                                    const double* y1, const double* vx, const double* vy,
+                                    const double2* Jb, AdjParticles ab, int64_t n,
+                                    unsigned int* err, cudaStream_t s);
+// Objective seed sum bzb B_z at the final level, from zs = DFT(bzb).
+cudaError_t launch_adj_seed(const ModeCommon& mc, const double2* zs, double2* ax, double2* ay,
+                            cudaStream_t s);
+// (Ex + i Ey)/(nx ny) of E = -grad phi (for the mesh E^0 by an inverse transform).
+cudaError_t launch_adj_e0(const ModeCommon& mc, const double2* phi, double2* out, cudaStream_t s);
+// t = 0 reverse: gradients with respect to v^0 and P^0 (any output may be NULL).
+cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const double* x0,
+                            const double* y0, const double* vx0, const double* vy0,
+                            const double2* E, AdjParticles ab, double* gvx, double* gvy,
+                            double* gpx, double* gpy, int64_t n, unsigned int* err,
+                            cudaStream_t s);
+cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cudaStream_t s);
+// Eight FP64 arrays of n values <-> one contiguous block of 8 n (array k at k n).
+struct Ptr8 {
+    const double* p[8];
+};
+cudaError_t launch_pack8(Ptr8 src, double* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_unpack8(const double* src, Ptr8 dst, int64_t n, cudaStream_t s);
+
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };
 

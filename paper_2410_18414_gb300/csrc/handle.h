@@ -1,0 +1,116 @@
+// The simulation handle behind the opaque pic_handle of include/pic.h and the host
+// helpers the library's API translation units share.  Internal: not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "gpic_internal.h"
+#include "pic.h"
+
+struct pic_handle {
+    pic_config cfg{};
+    // kernel timing (pic_set_kernel_timing): per timer, event pairs created up front
+    struct KTimer {
+        std::vector<cudaEvent_t> ev;  // start, stop, start, stop, ...
+        int64_t used = 0;             // pairs recorded since timing started
+    };
+    KTimer kt[PIC_KT_COUNT];
+    bool ktiming = false;
+    int64_t kt_cap = 0;  // pairs each timer may record since timing started
+    cudaStream_t s = nullptr;
+    int device = 0;
+    int64_t n = 0;
+    bool fp32 = false;
+    size_t rsz = 8;
+    int p = 2;
+    int nx = 0, ny = 0;
+    size_t ng = 0;
+    // particle state (FP64 or FP32 by precision); v[buffer][component]
+    void *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr;
+    void* v[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
+    double* stage = nullptr;  // FP64 staging for conversions (n values)
+    // tile sort (sort_interval > 0): second set of particle arrays, original indices, keys
+    bool sorting = false;
+    gpic::TileGeom tg{};
+    void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t *id = nullptr, *id_alt = nullptr;
+    int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
+    // FP32 sorted path: (x, y, vx, vy) of each particle, the tiled deposit's input; written
+    // by every sort and every tiled gather, and a tiled deposit follows one of them
+    float4* p4 = nullptr;
+    int launches_now = 0, launches_last = 0;
+    // grid buffers
+    double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
+    double2* Jalt = nullptr; // FP32 form: the other int64 buffer, zeroed by the row transform
+    // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
+    float fix_scale_j = 0.f, fix_scale_q = 0.f;
+    double fix_unscale_j = 0.0, fix_unscale_q = 0.0;
+    void* Z = nullptr;       // spectrum of J (complex)
+    void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
+    void* G = nullptr;       // [node][4] complex: the eight real gather fields
+    void* E = nullptr;       // packed E spectrum of the last diagnosed step
+    void* tmp = nullptr;     // complex scratch (ng)
+    // naive update (PIC_CHARGE_DEPOSIT): the deposited charge (FP64 pairs, or int64 sums
+    // in the FP32 form) and its spectrum
+    void* rhoq = nullptr;
+    void* ZQ = nullptr;
+    double* tmpd = nullptr;  // real scratch (ng)
+    void *twx = nullptr, *twy = nullptr;
+    gpic::FftDesc fx{}, fy{};
+    // time histories (BDF rings; CDF pairs; DIRK state)
+    std::vector<void*> phi_l, ax_l, ay_l, rho_l;
+    int L = 0, Lr = 0, head = 0, head_r = 0;
+    gpic::BdfParams bdf{};
+    gpic::CdfParams cdf{};
+    gpic::DirkParams dirk{};
+    // diagnostics and errors
+    double* diag = nullptr;
+    unsigned int* err = nullptr;
+    int diag_every = 0;
+    bool diag_now = false, diag_valid = false, e_valid = false;
+    int64_t diag_step = -1;
+    int64_t step = 0;
+    int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
+    bool stepped = false;
+    std::vector<void*> allocs;
+    gpic::ModeCommon mc{};
+    gpic::ParticleGeom geom{};
+    gpic::PushParams push{};
+    std::string errmsg;
+};
+
+namespace gpic {
+
+// Records the formatted message on h (or as the last pic_init error when h is NULL) and
+// returns st.
+pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...);
+
+// Run f with a value of the storage type (double or float).
+template <typename F>
+cudaError_t by_prec(pic_handle* h, F&& f) {
+    if (h->fp32) return f(float{});
+    return f(double{});
+}
+
+// Forward 2-D transform of one complex array (along y, then along x in place).
+cudaError_t forward_fft(pic_handle* h, const void* in, void* out);
+// Inverse transform of nb packed spectra in `buf` (in place along x), then along y into
+// `out` (interleaved by array when nb > 1).
+cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb);
+// Waits for the stream and maps the device error word to a status.
+pic_status check_device_error(pic_handle* h);
+
+}  // namespace gpic
+
+// Returns PIC_ERR_CUDA from the enclosing function (with the call's text as the message
+// on h) when a CUDA runtime call fails.
+#define CK(...)                                                                           \
+    do {                                                                                  \
+        cudaError_t e_ = (__VA_ARGS__);                                                        \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, PIC_ERR_CUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+    } while (0)

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "gpic_internal.h"
+#include "handle.h"
 #include "pic.h"
 
 using namespace gpic;
@@ -20,80 +21,8 @@ namespace {
 thread_local std::string g_init_error;
 }
 
-struct pic_handle {
-    pic_config cfg{};
-    // kernel timing (pic_set_kernel_timing): per timer, event pairs created up front
-    struct KTimer {
-        std::vector<cudaEvent_t> ev;  // start, stop, start, stop, ...
-        int64_t used = 0;             // pairs recorded since timing started
-    };
-    KTimer kt[PIC_KT_COUNT];
-    bool ktiming = false;
-    int64_t kt_cap = 0;  // pairs each timer may record since timing started
-    cudaStream_t s = nullptr;
-    int device = 0;
-    int64_t n = 0;
-    bool fp32 = false;
-    size_t rsz = 8;
-    int p = 2;
-    int nx = 0, ny = 0;
-    size_t ng = 0;
-    // particle state (FP64 or FP32 by precision); v[buffer][component]
-    void *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr;
-    void* v[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
-    double* stage = nullptr;  // FP64 staging for conversions (n values)
-    // tile sort (sort_interval > 0): second set of particle arrays, original indices, keys
-    bool sorting = false;
-    TileGeom tg{};
-    void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    int32_t *id = nullptr, *id_alt = nullptr;
-    int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
-    // FP32 sorted path: (x, y, vx, vy) of each particle, the tiled deposit's input; written
-    // by every sort and every tiled gather, and a tiled deposit follows one of them
-    float4* p4 = nullptr;
-    int launches_now = 0, launches_last = 0;
-    // grid buffers
-    double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
-    double2* Jalt = nullptr; // FP32 form: the other int64 buffer, zeroed by the row transform
-    // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
-    float fix_scale_j = 0.f, fix_scale_q = 0.f;
-    double fix_unscale_j = 0.0, fix_unscale_q = 0.0;
-    void* Z = nullptr;       // spectrum of J (complex)
-    void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
-    void* G = nullptr;       // [node][4] complex: the eight real gather fields
-    void* E = nullptr;       // packed E spectrum of the last diagnosed step
-    void* tmp = nullptr;     // complex scratch (ng)
-    // naive update (PIC_CHARGE_DEPOSIT): the deposited charge (FP64 pairs, or int64 sums
-    // in the FP32 form) and its spectrum
-    void* rhoq = nullptr;
-    void* ZQ = nullptr;
-    double* tmpd = nullptr;  // real scratch (ng)
-    void *twx = nullptr, *twy = nullptr;
-    FftDesc fx{}, fy{};
-    // time histories (BDF rings; CDF pairs; DIRK state)
-    std::vector<void*> phi_l, ax_l, ay_l, rho_l;
-    int L = 0, Lr = 0, head = 0, head_r = 0;
-    BdfParams bdf{};
-    CdfParams cdf{};
-    DirkParams dirk{};
-    // diagnostics and errors
-    double* diag = nullptr;
-    unsigned int* err = nullptr;
-    int diag_every = 0;
-    bool diag_now = false, diag_valid = false, e_valid = false;
-    int64_t diag_step = -1;
-    int64_t step = 0;
-    int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
-    bool stepped = false;
-    std::vector<void*> allocs;
-    ModeCommon mc{};
-    ParticleGeom geom{};
-    PushParams push{};
-    std::string errmsg;
-};
 
-namespace {
+namespace gpic {
 
 pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
     char buf[512];
@@ -108,12 +37,41 @@ pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
     return st;
 }
 
-#define CK(...)                                                                           \
-    do {                                                                                  \
-        cudaError_t e_ = (__VA_ARGS__);                                                        \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(h, PIC_ERR_CUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
-    } while (0)
+
+cudaError_t forward_fft(pic_handle* h, const void* in, void* out) {
+    return by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t e = launch_fft_y<T>(in, out, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s);
+        if (e != cudaSuccess) return e;
+        return launch_fft_x<T>(out, out, h->nx, h->ny, 1, h->fx, h->twx, -1, h->s);
+    });
+}
+
+// Inverse transform of nb packed spectra in `buf` (in place along x), then along y
+// into `out` (interleaved by array when nb > 1).
+cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb) {
+    return by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        cudaError_t e = launch_fft_x<T>(buf, buf, h->nx, h->ny, nb, h->fx, h->twx, +1, h->s);
+        if (e != cudaSuccess) return e;
+        return launch_fft_y<T>(buf, out, h->nx, h->ny, nb, h->fy, h->twy, +1, nb > 1, h->s);
+    });
+}
+
+pic_status check_device_error(pic_handle* h) {
+    unsigned int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (e & ERR_OVERFLOW) return fail(h, PIC_ERR_OVERFLOW, "fixed-point current overflow");
+    if (e & ERR_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_NONFINITE)
+        return fail(h, PIC_ERR_NONFINITE, "non-finite or out-of-domain particle data");
+    return PIC_OK;
+}
+
+}  // namespace gpic
+
+namespace {
 
 bool factor_23(int n, FftDesc& d) {
     d.n = n;
@@ -248,33 +206,6 @@ void free_all(pic_handle* h) {
     h->allocs.clear();
 }
 
-// Run f with a value of the storage type (double or float).
-template <typename F>
-cudaError_t by_prec(pic_handle* h, F&& f) {
-    if (h->fp32) return f(float{});
-    return f(double{});
-}
-
-cudaError_t forward_fft(pic_handle* h, const void* in, void* out) {
-    return by_prec(h, [&](auto t) {
-        using T = decltype(t);
-        cudaError_t e = launch_fft_y<T>(in, out, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s);
-        if (e != cudaSuccess) return e;
-        return launch_fft_x<T>(out, out, h->nx, h->ny, 1, h->fx, h->twx, -1, h->s);
-    });
-}
-
-// Inverse transform of nb packed spectra in `buf` (in place along x), then along y
-// into `out` (interleaved by array when nb > 1).
-cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb) {
-    return by_prec(h, [&](auto t) {
-        using T = decltype(t);
-        cudaError_t e = launch_fft_x<T>(buf, buf, h->nx, h->ny, nb, h->fx, h->twx, +1, h->s);
-        if (e != cudaSuccess) return e;
-        return launch_fft_y<T>(buf, out, h->nx, h->ny, nb, h->fy, h->twy, +1, nb > 1, h->s);
-    });
-}
-
 // Newest spectral level: 0 phi, 1 Ax, 2 Ay, 3 rho.
 void* newest(pic_handle* h, int which) {
     switch (h->cfg.stepper) {
@@ -288,16 +219,6 @@ void* newest(pic_handle* h, int which) {
     }
 }
 
-pic_status check_device_error(pic_handle* h) {
-    unsigned int e = 0;
-    CK(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    if (e & ERR_OVERFLOW) return fail(h, PIC_ERR_OVERFLOW, "fixed-point current overflow");
-    if (e & ERR_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a bounded device wait gave up");
-    if (e & ERR_NONFINITE)
-        return fail(h, PIC_ERR_NONFINITE, "non-finite or out-of-domain particle data");
-    return PIC_OK;
-}
 
 pic_status alloc_state(pic_handle* h) {
     const pic_config& c = h->cfg;

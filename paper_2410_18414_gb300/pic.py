@@ -106,6 +106,11 @@ def load_library(path=LIB_PATH):
         "pic_ensemble_step": ([vp, i32], i32),
         "pic_ensemble_period": ([vp], i32),
         "pic_ensemble_destroy": ([vp], None),
+        "pic_adjoint_create": ([vp, i32, i32, ctypes.POINTER(vp)], i32),
+        "pic_adjoint_forward": ([vp], i32),
+        "pic_adjoint_backward": ([vp] + [vp] * 7, i32),
+        "pic_adjoint_checkpoint_every": ([vp], i32),
+        "pic_adjoint_destroy": ([vp], None),
         "pic_last_error": ([vp], ctypes.c_char_p),
         "pic_destroy": ([vp], None),
     }
@@ -299,3 +304,67 @@ class Ensemble:
     def __exit__(self, *exc):
         self.close()
 
+
+
+class Adjoint:
+    """Discrete adjoint of the next `nsteps` steps of a fresh FP64 BDF-k Simulation
+    (pic_adjoint_*): run forward() once, then backward(...) for the gradient of
+    J = sum bz_bar B_z + sum (px_bar Px + py_bar Py) of the final state with respect to
+    v^0 and, with P^0 = gamma m v^0 independent, to P^0.  Seeds and results are CUDA
+    float64 tensors (the library reads and writes device memory)."""
+
+    def __init__(self, sim, nsteps, checkpoint_every=None):
+        self.lib = load_library()
+        self.sim = sim
+        self.nsteps = int(nsteps)
+        a = ctypes.c_void_p()
+        k = self.nsteps if checkpoint_every is None else int(checkpoint_every)
+        st = self.lib.pic_adjoint_create(sim.h, self.nsteps, k, ctypes.byref(a))
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(sim.h).decode())
+        self.a = a
+
+    @property
+    def checkpoint_every(self):
+        return int(self.lib.pic_adjoint_checkpoint_every(self.a))
+
+    def _check(self, st):
+        if st != PIC_OK:
+            raise PicError(st, self.lib.pic_last_error(self.sim.h).decode())
+
+    def forward(self):
+        self._check(self.lib.pic_adjoint_forward(self.a))
+
+    def backward(self, bz_bar=None, px_bar=None, py_bar=None, out=None):
+        """Dict of CUDA tensors "vx", "vy" (dJ/dv^0) and "px", "py" (dJ/dP^0)."""
+        import torch
+        n = self.sim.n
+        if out is None:
+            out = {k: torch.empty(n, dtype=torch.float64, device="cuda")
+                   for k in ("vx", "vy", "px", "py")}
+        for t in (bz_bar, px_bar, py_bar, *out.values()):
+            if t is not None and not (hasattr(t, "is_cuda") and t.is_cuda):
+                raise TypeError("adjoint seeds and outputs must be CUDA float64 tensors")
+        vp = ctypes.c_void_p
+        args = [vp(_ptr(t)) if t is not None else None
+                for t in (bz_bar, px_bar, py_bar, out.get("vx"), out.get("vy"),
+                          out.get("px"), out.get("py"))]
+        self._check(self.lib.pic_adjoint_backward(self.a, *args))
+        return out
+
+    def close(self):
+        if getattr(self, "a", None):
+            self.lib.pic_adjoint_destroy(self.a)
+            self.a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -126,4 +126,11 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.pic_ensemble_destroy(None)
     ms, n = ctypes.c_double(), ctypes.c_int64()
     assert lib.pic_kernel_time(None, 0, ctypes.byref(ms), ctypes.byref(n)) == 1
+    adj = ctypes.c_void_p()
+    assert lib.pic_adjoint_create(None, 10, 5, ctypes.byref(adj)) == 1
+    assert not adj.value
+    assert lib.pic_adjoint_forward(None) == 1
+    assert lib.pic_adjoint_backward(None, None, None, None, None, None, None, None) == 1
+    assert lib.pic_adjoint_checkpoint_every(None) == 0
+    lib.pic_adjoint_destroy(None)
     lib.pic_destroy(None)

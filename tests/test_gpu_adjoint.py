@@ -1,0 +1,237 @@
+"""GPU checks of the discrete adjoint (pic_adjoint_*) of the FP64 BDF-k run.
+
+- Against the oracle's adjoint (oracle.adjoint, pinned on CPU by finite differences
+  and transpose identities): small grids, several spline orders and BDF orders, both
+  seeds (the magnetic energy W_B and a final-momentum objective), checkpoint intervals
+  that leave a ragged last segment.  Measured on GB300: <= 2e-14 relative; bound 1e-11.
+- Checkpoint-interval invariance: K = 1, 3, N give the same gradient (to the FP64
+  atomic-order roundoff of the forward's current deposit).
+- The 128 x 128 Weibel configuration (262,144 particles, v_d = 0.5c, BDF-2, cubic, 200
+  steps): the gradient of W_B against central finite differences of the forward run with
+  h = 1e-6 along v_d (through u_d = gamma_d v_d) and along 4 random directions in v^0;
+  bound 1e-6 relative (measured <= 1.5e-7).  Along 32 random single components of P^0
+  the forward's own roundoff limits the finite difference: W_B carries FP64 roundoff
+  amplified by 200 steps of the unstable dynamics (identical runs differ by 1e-14 to
+  2.6e-13 relative, since the current sums FP64 atomics in no fixed order; a perturbed
+  input reshuffles the roundoff the same way), while one particle's derivative is only
+  ~1e-10 against W_B = 5.8e-7.  The finite difference then carries an error of about
+  sigma W_B / h; values up to sigma = 1.1e-12 were seen.  There h = 1e-4 and the bound is
+  1e-6 |g| + sigma W_B / h with sigma = 4e-12 (about 1e-4 of a typical component).
+- The handle is left at the end of the forward run; torch.autograd returns the same
+  gradient as the library call.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle import pic as opic
+from paper_2410_18414_gb300 import pic, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def device():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _case(p, k, nx, ny, n, seed):
+    rng = np.random.default_rng(seed)
+    lx, ly = 1.0, 0.8
+    x = rng.uniform(0, lx, n)
+    y = rng.uniform(0, ly, n)
+    sgn = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    vx = 0.05 * rng.standard_normal(n)
+    vy = sgn * 0.3 + 0.05 * rng.standard_normal(n)
+    dt = 0.4 * lx / nx
+    w = lx * ly / n
+    cfg = pic.make_config(nx, ny, lx, ly, dt, p=p, stepper="bdf", bdf_order=k, weight=w)
+    ocfg = opic.Config(nx=nx, ny=ny, lx=lx, ly=ly, dt=dt, p=p, stepper="bdf", bdf_order=k, w=w)
+    return cfg, ocfg, x, y, vx, vy
+
+
+def _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, pb=None):
+    import torch
+    area = cfg.lx / cfg.nx * cfg.ly / cfg.ny
+    with pic.Simulation(cfg, x, y, vx, vy, stream=device) as sim:
+        with pic.Adjoint(sim, nsteps, K) as adj:
+            adj.forward()
+            bz = torch.empty((cfg.nx, cfg.ny), dtype=torch.float64, device="cuda")
+            sim.field("bz", out=bz)
+            wb = 0.5 * area * float((bz * bz).sum())
+            if pb is None:
+                g = adj.backward(bz_bar=(bz * area).contiguous())
+            else:
+                g = adj.backward(px_bar=torch.tensor(pb[0], device="cuda"),
+                                 py_bar=torch.tensor(pb[1], device="cuda"))
+            return wb, {key: v.cpu().numpy() for key, v in g.items()}
+
+
+CASES = [(2, 1, 24, 16, 3000, 13, 5), (3, 2, 32, 32, 4096, 13, 5), (4, 3, 16, 24, 2000, 9, 4)]
+
+
+@pytest.mark.parametrize("p,k,nx,ny,n,nsteps,K", CASES, ids=["p2-bdf1", "p3-bdf2", "p4-bdf3"])
+def test_adjoint_matches_oracle(device, p, k, nx, ny, n, nsteps, K):
+    cfg, ocfg, x, y, vx, vy = _case(p, k, nx, ny, n, seed=p)
+    tape = oadj.record(ocfg, x, y, vx, vy, nsteps)
+    expect = oadj.gradient(tape)
+    wb, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K)
+    assert abs(wb / oadj.magnetic_energy(ocfg, tape.final) - 1.0) <= 1e-12
+    errs = {"vx": rel(got["vx"], expect["v0"][0]), "vy": rel(got["vy"], expect["v0"][1]),
+            "px": rel(got["px"], expect["p0"][0]), "py": rel(got["py"], expect["p0"][1])}
+    assert max(errs.values()) <= 1e-11, errs
+    # final-momentum objective
+    rng = np.random.default_rng(20 + p)
+    pb = (rng.standard_normal(n), rng.standard_normal(n))
+    expect = oadj.gradient(tape, px_bar=pb[0], py_bar=pb[1])
+    _, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, pb=pb)
+    errs = {"vx": rel(got["vx"], expect["v0"][0]), "vy": rel(got["vy"], expect["v0"][1]),
+            "px": rel(got["px"], expect["p0"][0]), "py": rel(got["py"], expect["p0"][1])}
+    assert max(errs.values()) <= 1e-11, errs
+
+
+def test_checkpoint_interval_invariance(device):
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=3)
+    ref = _gpu_gradient(device, cfg, x, y, vx, vy, 13, 5)[1]
+    for K in (1, 3, 13, 100):
+        got = _gpu_gradient(device, cfg, x, y, vx, vy, 13, K)[1]
+        for key in ref:
+            assert rel(got[key], ref[key]) <= 1e-12, (K, key)
+
+
+def test_handle_left_at_end_of_forward_run(device):
+    import torch
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=4)
+    with pic.Simulation(cfg, x, y, vx, vy, stream=device) as sim:
+        with pic.Adjoint(sim, 10, 3) as adj:
+            adj.forward()
+            before = sim.particles()
+            fields = {f: sim.field(f) for f in ("bz", "jx", "phi", "ay", "dphidx")}
+            bz = torch.tensor(fields["bz"], device="cuda")
+            adj.backward(bz_bar=bz)
+            after = sim.particles()
+            assert sim.step_count == 10
+            for key in before:
+                assert np.array_equal(before[key], after[key]), key
+            for f, v in fields.items():
+                assert np.array_equal(sim.field(f), v), f
+            sim.step(2)  # the handle steps on from there
+
+
+def test_adjoint_rejects_unsupported_handles(device):
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 512, seed=5)
+    for kw in (dict(precision=pic.FP32_FIX64), dict(stepper="cdf2"), dict(sort_interval=4),
+               dict(charge=pic.CHARGE_DEPOSIT)):
+        args = dict(p=3, stepper="bdf", bdf_order=2, weight=cfg.weight)
+        args.update(kw)
+        c = pic.make_config(cfg.nx, cfg.ny, cfg.lx, cfg.ly, cfg.dt, **args)
+        with pic.Simulation(c, x, y, vx, vy, stream=device) as sim:
+            with pytest.raises(pic.PicError) as e:
+                pic.Adjoint(sim, 5)
+            assert e.value.status == 2
+    with pic.Simulation(cfg, x, y, vx, vy, stream=device) as sim:
+        sim.step(1)
+        with pytest.raises(pic.PicError) as e:
+            pic.Adjoint(sim, 5)
+        assert e.value.status == 7
+
+
+def test_autograd_matches_library(device):
+    import torch
+    from paper_2410_18414_gb300 import autograd
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=6)
+    vx0 = torch.tensor(vx, device="cuda", requires_grad=True)
+    vy0 = torch.tensor(vy, device="cuda", requires_grad=True)
+    wb = autograd.magnetic_energy(cfg, x, y, vx0, vy0, 12, checkpoint_every=5)
+    (2.5 * wb).backward()
+    _, ref = _gpu_gradient(device, cfg, x, y, vx, vy, 12, 12)
+    assert rel(vx0.grad.cpu().numpy(), 2.5 * ref["vx"]) <= 1e-12
+    assert rel(vy0.grad.cpu().numpy(), 2.5 * ref["vy"]) <= 1e-12
+
+
+# ------------------------------------------------------------ 128 x 128 Weibel --
+
+@pytest.fixture(scope="module")
+def c5(device):
+    wl = workloads.weibel_adjoint_128()
+    assert (wl.nx, wl.ny, wl.n, wl.p, wl.nsteps) == (128, 128, 262144, 3, 200)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf",
+                          bdf_order=2, weight=wl.weight)
+    wb, g = _gpu_gradient(device, cfg, wl.x, wl.y, wl.vx, wl.vy, wl.nsteps, 20)
+    return wl, cfg, wb, g
+
+
+def _wb(device, wl, cfg, vx, vy):
+    with pic.Simulation(cfg, wl.x, wl.y, vx, vy, stream=device) as sim:
+        sim.step(wl.nsteps)
+        bz = sim.field("bz")
+    return 0.5 * (wl.lx / wl.nx) * (wl.ly / wl.ny) * float(np.sum(bz * bz))
+
+
+def _v_of_vd(wl, vd):
+    # the workload's draws (weibel(): x, y, then u_x, then the u_y spread), with the drift
+    rng = np.random.Generator(np.random.PCG64(5))
+    rng.uniform(0.0, wl.lx, wl.n)
+    rng.uniform(0.0, wl.ly, wl.n)
+    ux = 0.01 * rng.standard_normal(wl.n)
+    uy = np.where(np.arange(wl.n) % 2 == 0, 1.0, -1.0) * (vd / np.sqrt(1 - vd * vd)) \
+        + 0.01 * rng.standard_normal(wl.n)
+    gam = np.sqrt(1.0 + ux * ux + uy * uy)
+    return ux / gam, uy / gam
+
+
+def test_c5_drift_gradient_matches_finite_differences(device, c5):
+    wl, cfg, wb, g = c5
+    vx, vy = _v_of_vd(wl, 0.5)
+    assert np.array_equal(vx, wl.vx) and np.array_equal(vy, wl.vy)
+    # P^0_y = m u_y, u_y = +-u_d + spread, du_d/dv_d = gamma_d^3 (m = 1)
+    sgn = np.where(np.arange(wl.n) % 2 == 0, 1.0, -1.0)
+    adj = (1.0 / np.sqrt(0.75)) ** 3 * float(np.sum(sgn * g["py"]))
+    h = 1e-6
+    fd = (_wb(device, wl, cfg, *_v_of_vd(wl, 0.5 + h))
+          - _wb(device, wl, cfg, *_v_of_vd(wl, 0.5 - h))) / (2 * h)
+    assert abs(fd - adj) <= 1e-6 * abs(adj), (fd, adj)
+
+
+def test_c5_direction_gradients_match_finite_differences(device, c5):
+    wl, cfg, wb, g = c5
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal((2, wl.n))
+        ad = float(np.dot(g["vx"], d[0]) + np.dot(g["vy"], d[1]))
+        fd = (_wb(device, wl, cfg, wl.vx + h * d[0], wl.vy + h * d[1])
+              - _wb(device, wl, cfg, wl.vx - h * d[0], wl.vy - h * d[1])) / (2 * h)
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_c5_momentum_components_match_finite_differences(device, c5):
+    wl, cfg, wb, g = c5
+    gam = 1.0 / np.sqrt(1.0 - (wl.vx ** 2 + wl.vy ** 2))
+    px0, py0 = gam * wl.vx, gam * wl.vy
+    rng = np.random.default_rng(12)
+    h, sigma = 1e-4, 4e-12
+    for i in rng.choice(wl.n, 32, replace=False):
+        comp = int(rng.integers(2))
+        vals = []
+        for s in (1.0, -1.0):
+            p = [px0.copy(), py0.copy()]
+            p[comp][i] += s * h
+            den = np.sqrt(p[0] ** 2 + p[1] ** 2 + 1.0)
+            vals.append(_wb(device, wl, cfg, p[0] / den, p[1] / den))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        ad = g["px" if comp == 0 else "py"][i]
+        assert abs(fd - ad) <= 1e-6 * abs(ad) + sigma * wb / h, (i, comp, fd, ad)
