@@ -470,7 +470,7 @@ def run_adjoint(a):
     whole run with CUDA events (L2 flushed between runs): the plain forward run
     (pic_step), the recording forward run and the reverse sweep, with checkpoints every
     20 steps (the backward pass recomputes 9 of the 10 segments) and with every step kept
-    in HBM (3.4 GB, nothing recomputed).  value = (recording forward + reverse sweep) /
+    in HBM (6.9 GB, nothing recomputed).  value = (recording forward + reverse sweep) /
     plain forward at K = 20."""
     import torch
     from paper_2410_18414_gb300 import pic, workloads
@@ -544,7 +544,7 @@ def run_adjoint(a):
                           "backward_ms": med([t[1] for t in k20]), "ratio": r20},
         "keep_all_steps": {"record_forward_ms": med([t[0] for t in kall]),
                            "backward_ms": med([t[1] for t in kall]), "ratio": rall,
-                           "hbm_bytes": int(N * (64 * wl.n + 64 * wl.nx * wl.ny))},
+                           "hbm_bytes": int(N * (128 * wl.n + 64 * wl.nx * wl.ny))},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -291,10 +291,11 @@ void pic_destroy(pic_handle *h);
  *
  * Memory: the state (particles and field histories) is checkpointed every
  * `checkpoint_every` steps (K).  The backward pass recomputes each segment of K steps
- * from its checkpoint, keeping that segment's per-step particle state and gather fields
- * (8 n + 64 nx ny bytes per step), then runs it backwards.  The last segment is kept by
- * the forward pass itself, so with K = nsteps nothing is recomputed.  Device memory
- * used: about (nsteps/K + 1) * 64 n + K * (64 n + 64 nx ny) bytes plus the adjoint state. */
+ * from its checkpoint, keeping that segment's per-step particle state, the eight values
+ * each step's push gathered per particle and the step's gather fields (128 n + 64 nx ny
+ * bytes per step), then runs it backwards.  The last segment is kept by the forward pass
+ * itself, so with K = nsteps nothing is recomputed.  Device memory used: about
+ * (nsteps/K + 1) * 64 n + K * (128 n + 64 nx ny) bytes plus the adjoint state. */
 typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init

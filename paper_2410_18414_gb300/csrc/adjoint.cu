@@ -6,7 +6,8 @@
 // Adjoint of a quantity z is written zb; the pairing is the plain sum over particles and
 // grid nodes, and Re sum conj(zb) dz for a spectrum.  Reverse of step n -> n+1:
 //
-//   push + gather (k_adj_push_gather), per particle at x^{n+1}:
+//   push + gather (k_adj_push_gather), per particle at x^{n+1}, from the fields the
+//   forward push gathered (kept by the recording step):
 //     u = P^{n+1} - q A_p, v^{n+1} = c^2 u / D, D = sqrt(c^2 |u|^2 + (m c^2)^2)
 //     ub = (c^2/D) (vb - c^2 u (u . vb)/D^2);  Pb += ub;  A_p b = -q ub
 //     P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*):  (grad phi)b = -q dt Pb,
@@ -29,6 +30,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fft_device.cuh"
 #include "gpic_internal.h"
 
 namespace gpic {
@@ -86,13 +88,14 @@ template <> struct DShape<4> {
 __device__ __forceinline__ bool inside(double xi, int n) { return xi >= 0.0 && xi <= (double)n; }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
                   const double* __restrict__ y1, const double* __restrict__ px1,
                   const double* __restrict__ py1, const double* __restrict__ vx,
                   const double* __restrict__ vy, const double* __restrict__ vxo,
-                  const double* __restrict__ vyo, const double2* __restrict__ F, AdjParticles ab,
-                  double2* __restrict__ Fb, int64_t n, unsigned int* __restrict__ err) {
+                  const double* __restrict__ vyo, const double* __restrict__ gf,
+                  const double2* __restrict__ F, AdjParticles ab, double2* __restrict__ Fb,
+                  int64_t n, unsigned int* __restrict__ err) {
     const size_t ng = (size_t)g.nx * g.ny;
     const double q = pp.q, qdt = pp.q * pp.dt, c2 = pp.c * pp.c, mc2 = pp.m * pp.c * pp.c;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
@@ -102,33 +105,17 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
-        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
-        const int ix = Shape<P, double>::weights(xi, wx);
-        const int iy = Shape<P, double>::weights(yj, wy);
-        DShape<P>::dweights(xi, dwx);
-        DShape<P>::dweights(yj, dwy);
-        // gathered fields (dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy)
-        double f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 1
-        for (int a = 0; a <= P; ++a) {
-            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+        // the fields the forward push gathered at x^{n+1} (dphi/dx, dphi/dy, Ax, Ay,
+        // dAx/dx, dAx/dy, dAy/dx, dAy/dy)
+        double f[8];
 #pragma unroll
-            for (int b = 0; b <= P; ++b) {
-                const double2* node = F + (row + wrap_idx(iy + b, g.ny)) * 4;
-                const double w = wx[a] * wy[b];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const double2 v = __ldg(node + k);
-                    f[2 * k] += w * v.x;
-                    f[2 * k + 1] += w * v.y;
-                }
-            }
-        }
+        for (int k = 0; k < 8; ++k) f[k] = gf[(size_t)k * n + p];
         // velocity: v = c^2 u / D
         const double ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
         const double D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
+        const double id = 1.0 / D;
         const double vbx = ab.vx[p], vby = ab.vy[p];
-        const double cd = c2 / D, udv = (ux * vbx + uy * vby) * c2 / (D * D);
+        const double cd = c2 * id, udv = (ux * vbx + uy * vby) * cd * id;
         const double ubx = cd * (vbx - ux * udv), uby = cd * (vby - uy * udv);
         const double pbx = ab.px[p] + ubx, pby = ab.py[p] + uby;
         // momentum: P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*)
@@ -144,30 +131,40 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
         gb[7] = qdt * pby * vsy;
         const double vsbx = qdt * (pbx * f[4] + pby * f[5]);
         const double vsby = qdt * (pbx * f[6] + pby * f[7]);
-        // second pass over the stencil: the position gradient and the deposit of gb
+        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, double>::weights(xi, wx);
+        const int iy = Shape<P, double>::weights(yj, wy);
+        DShape<P>::dweights(xi, dwx);
+        DShape<P>::dweights(yj, dwy);
+        // one pass over the stencil: s = sum_f gb_f F_f at each node gives the position
+        // gradient (separable: along y in the row, then across rows), and gb is deposited
         double xg = 0.0, yg = 0.0;
 #pragma unroll 1
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+            const double wxa = wx[a];
+            double sx = 0.0, sy = 0.0;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const size_t nd = row + wrap_idx(iy + b, g.ny);
                 const double2* node = F + nd * 4;
-                double s = 0.0;
+                double sn = 0.0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const double2 v = __ldg(node + k);
-                    s += gb[2 * k] * v.x + gb[2 * k + 1] * v.y;
+                    sn += gb[2 * k] * v.x + gb[2 * k + 1] * v.y;
                 }
-                xg += s * (dwx[a] * wy[b]);
-                yg += s * (wx[a] * dwy[b]);
-                const double w = wx[a] * wy[b];
+                sx += wy[b] * sn;
+                sy += dwy[b] * sn;
+                const double w = wxa * wy[b];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     atomicAdd(&Fb[k * ng + nd].x, w * gb[2 * k]);
                     atomicAdd(&Fb[k * ng + nd].y, w * gb[2 * k + 1]);
                 }
             }
+            xg += dwx[a] * sx;
+            yg += wxa * sy;
         }
         ab.x[p] += g.inv_dx * xg;
         ab.y[p] += g.inv_dy * yg;
@@ -198,21 +195,26 @@ k_adj_deposit_move(ParticleGeom g, const double* __restrict__ x1, const double* 
         const int iy = Shape<P, double>::weights(yj, wy);
         DShape<P>::dweights(xi, dwx);
         DShape<P>::dweights(yj, dwy);
+        // separable sums: row a first along y with wy and dwy, then across rows
         double sx = 0, sy = 0, dxx = 0, dxy = 0, dyx = 0, dyy = 0;
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+            double rx = 0, ry = 0, rdx = 0, rdy = 0;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const double2 j = __ldg(Jb + row + wrap_idx(iy + b, g.ny));
-                const double w = wx[a] * wy[b], ddx = dwx[a] * wy[b], ddy = wx[a] * dwy[b];
-                sx += w * j.x;
-                sy += w * j.y;
-                dxx += ddx * j.x;  // d/dxi of the gathered Jx adjoint
-                dxy += ddx * j.y;  // d/dxi of the gathered Jy adjoint
-                dyx += ddy * j.x;
-                dyy += ddy * j.y;
+                rx += wy[b] * j.x;
+                ry += wy[b] * j.y;
+                rdx += dwy[b] * j.x;
+                rdy += dwy[b] * j.y;
             }
+            sx += wx[a] * rx;
+            sy += wx[a] * ry;
+            dxx += dwx[a] * rx;  // d/dxi of the gathered Jx adjoint
+            dxy += dwx[a] * ry;  // d/dxi of the gathered Jy adjoint
+            dyx += wx[a] * rdx;
+            dyy += wx[a] * rdy;
         }
         const double vxp = vx[p], vyp = vy[p];
         const double xb = ab.x[p] + g.inv_dx * (vxp * dxx + vyp * dxy);
@@ -229,26 +231,19 @@ constexpr int kModeThreads = 256;
 __device__ __forceinline__ zd zl(const double2* p) { return zd{p->x, p->y}; }
 __device__ __forceinline__ void zs(double2* p, zd v) { *p = make_double2(v.re, v.im); }
 
-__global__ void __launch_bounds__(kModeThreads)
-k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
-                double2* __restrict__ Js) {
-    const int ng = mc.nx * mc.ny;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= ng) return;
-    const int i = idx / mc.ny, j = idx - i * mc.ny;
-    const int ip = (i == 0) ? 0 : mc.nx - i;
-    const int jp = (j == 0) ? 0 : mc.ny - j;
-    const int idm = ip * mc.ny + jp;
-    const double kx = mc.kxt[i], ky = mc.kyt[j];
+// Reverse BDF-k field step of mode (i, j), idx = i ny + j.  za[k] = F(f_2k + i f_2k+1)(k),
+// zb[k] = the same at -k, for the four packed field-adjoint planes.  Updates the history
+// adjoints of the mode and returns the packed adjoint current (Jx + i Jy) q_p/(dx dy).
+__device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const AdjModeParams& ap, int idx,
+                                       double kx, double ky, const zd* za, const zd* zb) {
     // the eight field adjoints' spectra / (nx ny), from the packed pairs (f_2k + i f_2k+1)
     zd a[8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const zd za = zl(Zb + (size_t)k * ng + idx);
-        const zd zb = zconj(zl(Zb + (size_t)k * ng + idm));
+        const zd c = zconj(zb[k]);
         const double h = 0.5 * mc.inv_n;
-        a[2 * k] = h * (za + zb);
-        const zd d = za - zb;  // 2i F(f_2k+1)
+        a[2 * k] = h * (za[k] + c);
+        const zd d = za[k] - c;  // 2i F(f_2k+1)
         a[2 * k + 1] = zd{h * d.im, -h * d.re};
     }
     // gradient fields i k_l u: adjoint multiplier -i k_l
@@ -278,7 +273,69 @@ k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
     const zd jy = zi(ap.bdt * ky * rhos) + ga * ays;
     // packed (Jx + i Jy), times q_p/(dx dy): the adjoint of the raw deposit sums after
     // the unnormalised inverse transform
-    zs(Js + idx, mc.jscale * (jx + zi(jy)));
+    return mc.jscale * (jx + zi(jy));
+}
+
+// One thread per mode over the transformed planes Zb (four planes of nx ny).
+__global__ void __launch_bounds__(kModeThreads)
+k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
+                double2* __restrict__ Js) {
+    const int ng = mc.nx * mc.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ng) return;
+    const int i = idx / mc.ny, j = idx - i * mc.ny;
+    const int ip = (i == 0) ? 0 : mc.nx - i;
+    const int jp = (j == 0) ? 0 : mc.ny - j;
+    const int idm = ip * mc.ny + jp;
+    zd za[4], zb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        za[k] = zl(Zb + (size_t)k * ng + idx);
+        zb[k] = zl(Zb + (size_t)k * ng + idm);
+    }
+    zs(Js + idx, adj_mode(mc, ap, idx, mc.kxt[i], mc.kyt[j], za, zb));
+}
+
+// Fused column pass of the reverse field step.  CTA j loads columns j and ny - j (mod ny)
+// of the four row-transformed planes, transforms them along x in shared memory, updates
+// the modes of column j and transforms column j of the adjoint current back along x;
+// the caller finishes with the inverse transform along y.
+__global__ void __launch_bounds__(kModeThreads)
+k_adj_columns(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
+              double2* __restrict__ Js, FftDesc fd, const double2* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = mc.nx, ny = mc.ny;
+    const size_t ng = (size_t)nx * ny;
+    const int j = blockIdx.x;
+    const int jp = (j == 0) ? 0 : ny - j;
+    const int ncols = (jp == j) ? 1 : 2;
+    double2* bufA = reinterpret_cast<double2*>(smem_raw);  // 8 lines of nx: line c*4 + k
+    double2* bufB = bufA + 8 * nx;
+    double2* tws = bufB + 8 * nx;
+    stage_twiddles(tw, tws, nx);
+    for (int t = threadIdx.x; t < 4 * ncols * nx; t += blockDim.x) {
+        const int l = t / nx, i = t - l * nx;
+        const int c = l >> 2, k = l & 3;
+        bufA[t] = Zb[k * ng + (size_t)i * ny + (c ? jp : j)];
+    }
+    __syncthreads();
+    double2* zc = run_passes(bufA, bufB, fd, 4 * ncols, (const double2*)tws, -1);
+    double2* out = (zc == bufA) ? bufB : bufA;
+    const double2* zp = zc + (size_t)(ncols - 1) * 4 * nx;
+    const double ky = mc.kyt[j];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int ip = (i == 0) ? 0 : nx - i;
+        zd za[4], zb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            za[k] = zl(zc + k * nx + i);
+            zb[k] = zl(zp + k * nx + ip);
+        }
+        zs(out + i, adj_mode(mc, ap, i * ny + j, mc.kxt[i], ky, za, zb));
+    }
+    __syncthreads();
+    double2* res = run_passes(out, zc, fd, 1, (const double2*)tws, +1);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) Js[(size_t)i * ny + j] = res[i];
 }
 
 // Final-level seed of an objective sum bzb B_z: B_z = IDFT(i kx Ay - i ky Ax), so
@@ -404,12 +461,12 @@ inline int mode_blocks(const ModeCommon& mc) {
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
                                    const double* x1, const double* y1, const double* px1,
                                    const double* py1, const double* vx, const double* vy,
-                                   const double* vxo, const double* vyo, const double2* F,
-                                   AdjParticles ab, double2* Fb, int64_t n, unsigned int* err,
-                                   cudaStream_t s) {
+                                   const double* vxo, const double* vyo, const double* gf,
+                                   const double2* F, AdjParticles ab, double2* Fb, int64_t n,
+                                   unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, F, ab, Fb,
-                      n, err)
+    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gf, F, ab,
+                      Fb, n, err)
     return cudaGetLastError();
 }
 
@@ -435,6 +492,18 @@ cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, 
 cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
                                  double2* Js, cudaStream_t s) {
     k_adj_modes_bdf<<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, ap, Zb, Js);
+    return cudaGetLastError();
+}
+
+size_t adj_columns_smem(int nx) { return 17 * (size_t)nx * sizeof(double2); }
+
+cudaError_t launch_adj_columns(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
+                               double2* Js, const FftDesc& fd, const double2* tw, cudaStream_t s) {
+    const size_t sm = adj_columns_smem(mc.nx);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_columns, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_adj_columns<<<mc.ny, kModeThreads, sm, s>>>(mc, ap, Zb, Js, fd, tw);
     return cudaGetLastError();
 }
 

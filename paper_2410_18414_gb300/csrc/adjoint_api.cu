@@ -7,8 +7,9 @@
 //   ck[c]     checkpoint c: the state at step c K, the BDF ring contents in slot order
 //             and the ring heads; ck[nseg] is the end of the run, with the last step's
 //             J and gather fields, so the handle can be put back after the sweep
-//   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1), and
-//             recg[j] the gather fields that step used (the level c0 + j + 1)
+//   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1),
+//             recg[j] the gather fields that step used (the level c0 + j + 1) and recf[j]
+//             the eight values its push gathered per particle (8 n)
 //   adjoint   particle adjoints (8 n), the history adjoints (3 L + k spectra, slot of
 //             time level t = t mod L), field-adjoint planes and transform scratch
 #include <cuda_runtime.h>
@@ -39,6 +40,7 @@ struct pic_adjoint {
     double2* final_g = nullptr;  // gather fields of the last step
     double* rec = nullptr;       // K states
     double2* recg = nullptr;     // K x 4 ng
+    double* recf = nullptr;      // K x 8 n: the fields each step's push gathered
     int seg_held = -1;           // segment whose records rec/recg hold
     double* ab = nullptr;        // particle adjoints, 8 n
     double2* hb = nullptr;       // history adjoints, (3 L + Lr) ng
@@ -130,10 +132,13 @@ pic_status restore_checkpoint(pic_adjoint* a, const pic_adjoint::Ck& c) {
     return PIC_OK;
 }
 
-// One forward step of h, keeping the new state and the step's gather fields in rec[j].
+// One forward step of h, keeping the new state, the step's gather fields and the values
+// its push gathered in record j.
 pic_status step_and_record(pic_adjoint* a, int j) {
     pic_handle* h = a->h;
+    h->gather_out = a->recf + (size_t)j * 8 * a->n;
     pic_status st = pic_step(h, 1);
+    h->gather_out = nullptr;
     if (st != PIC_OK) return st;
     st = save_state(a, a->rec + (size_t)j * 8 * a->n);
     if (st != PIC_OK) return st;
@@ -164,16 +169,17 @@ double2* hist_slot(pic_adjoint* a, int field, int64_t t) {
 // Reverse of step n (from level n+1 to level n): s0 = state n, s1 = state n+1, g = the
 // gather fields of the step.
 pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const double* s1,
-                         const double2* g) {
+                         const double* gf, const double2* g) {
     pic_handle* h = a->h;
     const size_t np = a->n, ng = a->ng;
     AdjParticles ab = adjoint_arrays(a);
     CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
     CK(launch_adj_push_gather(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np, s1 + 3 * np,
-                              s0 + 4 * np, s0 + 5 * np, s0 + 6 * np, s0 + 7 * np, g, ab, a->fb,
+                              s0 + 4 * np, s0 + 5 * np, s0 + 6 * np, s0 + 7 * np, gf, g, ab, a->fb,
                               (int64_t)np, h->err, h->s));
     CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, h->twy, -1, 0, h->s));
-    CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
+    const bool fused = adj_columns_smem(h->nx) <= kFieldColumnsSmemMax;
+    if (!fused) CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
     AdjModeParams ap{};
     ap.k = h->bdf.k;
     for (int i = 0; i <= ap.k; ++i) ap.a[i] = h->bdf.a[i];
@@ -186,8 +192,13 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const doub
         ap.ay[d] = hist_slot(a, 2, n + 1 - d);
     }
     for (int d = 0; d < a->Lr; ++d) ap.rho[d] = hist_slot(a, 3, n + 1 - d);
-    CK(launch_adj_modes_bdf(h->mc, ap, a->zb, a->js, h->s));
-    CK(inverse_fft(h, a->js, a->jg, 1));
+    if (fused) {
+        CK(launch_adj_columns(h->mc, ap, a->zb, a->js, h->fx, (const double2*)h->twx, h->s));
+        CK(launch_fft_y<double>(a->js, a->jg, h->nx, h->ny, 1, h->fy, h->twy, +1, 0, h->s));
+    } else {
+        CK(launch_adj_modes_bdf(h->mc, ap, a->zb, a->js, h->s));
+        CK(inverse_fft(h, a->js, a->jg, 1));
+    }
     CK(launch_adj_deposit_move(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np, a->jg, ab,
                                (int64_t)np, h->err, h->s));
     return PIC_OK;
@@ -232,6 +243,7 @@ pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_g, 4 * gb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->rec, (size_t)a->K * sb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->recg, (size_t)a->K * 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recf, (size_t)a->K * sb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->ab, sb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->hb, hbytes);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->fb, 4 * gb);
@@ -311,7 +323,8 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
             const int j = s - c0;
             const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
             const double* s1 = a->rec + (size_t)j * 8 * np;
-            pic_status st = backward_step(a, s, s0, s1, a->recg + (size_t)j * 4 * ng);
+            pic_status st = backward_step(a, s, s0, s1, a->recf + (size_t)j * 8 * np,
+                                          a->recg + (size_t)j * 4 * ng);
             if (st != PIC_OK) return st;
         }
     }

@@ -182,11 +182,12 @@ struct PushParams {
     int diag;
 };
 
+// gout (FP64, may be NULL): receives the eight gathered fields, field k at gout[k n + p].
 template <typename T>
 cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vx_old,
-                               T* vy_old, int64_t n, const void* fields4, double* diag,
-                               unsigned int* err, cudaStream_t s);
+                               T* vy_old, int64_t n, const void* fields4, double* gout,
+                               double* diag, unsigned int* err, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_particles(int p, const ParticleGeom& g, const PushParams& pp, T* x, T* y,
                                   T* px, T* py, const T* vx, const T* vy, T* vx_old, T* vy_old,
@@ -271,18 +272,24 @@ struct AdjModeParams {
     double2* rho[kMaxBdf];
 };
 // Reverse push + gather of one step: reads x^{n+1}, P^{n+1} (state n+1), v^n, v^{n-1}
-// (state n) and the step's gather fields F ([node][4]); updates the particle adjoints
-// and adds the eight field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
+// (state n), the eight fields the forward push gathered (gf, field k at k n) and the
+// step's gather fields F ([node][4]); updates the particle adjoints and adds the eight
+// field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
                                    const double* x1, const double* y1, const double* px1,
                                    const double* py1, const double* vx, const double* vy,
-                                   const double* vxo, const double* vyo, const double2* F,
-                                   AdjParticles ab, double2* Fb, int64_t n, unsigned int* err,
-                                   cudaStream_t s);
+                                   const double* vxo, const double* vyo, const double* gf,
+                                   const double2* F, AdjParticles ab, double2* Fb, int64_t n,
+                                   unsigned int* err, cudaStream_t s);
 // Reverse BDF-k field solve per mode: Zb = forward transforms of the four Fb planes;
 // writes the packed adjoint current spectrum Js (unnormalised inverse transform -> mesh).
 cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
                                  double2* Js, cudaStream_t s);
+// Fused column pass of the same (Zb transformed along y only; Js transformed back along x
+// only), when adj_columns_smem(nx) fits kFieldColumnsSmemMax.
+size_t adj_columns_smem(int nx);
+cudaError_t launch_adj_columns(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
+                               double2* Js, const FftDesc& fd, const double2* tw, cudaStream_t s);
 // Reverse deposit + move: gathers the mesh current adjoint Jb ([node] (jx, jy)) at x^{n+1}.
 cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
                                     const double* y1, const double* vx, const double* vy,

@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(kThreads)
 k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restrict__ y,
               T* __restrict__ px, T* __restrict__ py, const T* __restrict__ vx,
               const T* __restrict__ vy, T* __restrict__ vxo, T* __restrict__ vyo, int64_t n,
-              const cplx_t<T>* __restrict__ F, double* __restrict__ diag,
-              unsigned int* __restrict__ err) {
+              const cplx_t<T>* __restrict__ F, double* __restrict__ gout,
+              double* __restrict__ diag, unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
     const T idx_ = g.inv_dx, idy = g.inv_dy;
     double kin = 0.0;
@@ -476,6 +476,10 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
                 load_node(row + (size_t)gj * 4, gv);
                 gather_node(rmul(wx[a], wy[b]), gv, f);
             }
+        }
+        if (gout) {  // the gathered fields, kept for the adjoint (SoA, field k at k n)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) gout[(size_t)k * n + p] = (double)f[k];
         }
         T vxn1, vyn1;
         push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
@@ -761,11 +765,11 @@ cudaError_t launch_extract_fix(const longlong2* j, int comp, double scale, doubl
 template <typename T>
 cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vxo,
-                               T* vyo, int64_t n, const void* f, double* diag, unsigned int* err,
-                               cudaStream_t s) {
+                               T* vyo, int64_t n, const void* f, double* gout, double* diag,
+                               unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     GPIC_DISPATCH_P(p, k_gather_push, typed<T>(g), typed<T>(pp), x, y, px, py, vx, vy, vxo, vyo, n,
-                    (const cplx_t<T>*)f, diag, err)
+                    (const cplx_t<T>*)f, gout, diag, err)
     return cudaGetLastError();
 }
 
@@ -856,7 +860,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                   cudaStream_t);                                \
     template cudaError_t launch_gather_push<T>(int, const ParticleGeom&, const PushParams&,     \
                                                const T*, const T*, T*, T*, const T*, const T*,  \
-                                               T*, T*, int64_t, const void*, double*,           \
+                                               T*, T*, int64_t, const void*, double*, double*,  \
                                                unsigned int*, cudaStream_t);                    \
     template cudaError_t launch_init_particles<T>(int, const ParticleGeom&, const PushParams&,  \
                                                   T*, T*, T*, T*, const T*, const T*, T*, T*,   \

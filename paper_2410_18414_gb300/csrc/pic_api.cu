@@ -708,7 +708,8 @@ pic_status pic_gather_push(pic_handle* h) {
             return launch_gather_push<T>(h->p, h->geom, pp, (const T*)h->x, (const T*)h->y,
                                          (T*)h->px, (T*)h->py, (const T*)h->v[h->vcur][0],
                                          (const T*)h->v[h->vcur][1], (T*)h->v[vo][0],
-                                         (T*)h->v[vo][1], h->n, h->G, h->diag, h->err, h->s);
+                                         (T*)h->v[vo][1], h->n, h->G, h->gather_out, h->diag,
+                                         h->err, h->s);
         }));
     }
     h->vcur = vo;
