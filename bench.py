@@ -517,6 +517,23 @@ def run_adjoint(a):
 
     for K in (0, min(20, N), N):      # warm-up: one of each
         once(K)
+    # one instrumented reverse sweep (every step kept): the library's per-kernel event
+    # pairs around the three reverse launch groups of every step
+    sim = pic.Simulation(cfg, x, y, vx, vy, stream=sid)
+    adj = pic.Adjoint(sim, N, N)
+    adj.forward()
+    sim.field("bz", out=bz)
+    flush.zero_()
+    torch.cuda.synchronize()
+    sim.set_kernel_timing(N + 1)
+    adj.backward(bz_bar=(bz * area).contiguous(), out=out)
+    kt = {}
+    for name in ("adj_push", "adj_field", "adj_deposit"):
+        ms, nl = sim.kernel_time(name)
+        kt[name] = {"launches": nl, "ms_per_launch": ms / nl if nl else None}
+    sim.set_kernel_timing(0)
+    adj.close()
+    sim.close()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     reps = max(1, a.repeats)
@@ -545,9 +562,36 @@ def run_adjoint(a):
         "keep_all_steps": {"record_forward_ms": med([t[0] for t in kall]),
                            "backward_ms": med([t[1] for t in kall]), "ratio": rall,
                            "hbm_bytes": int(N * (128 * wl.n + 64 * wl.nx * wl.ny))},
+        "kernels": kt,
+        "roofline": adjoint_roofline(wl.p, wl.n, kt["adj_push"]["ms_per_launch"]),
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
+
+
+def flops_adj_push(p):
+    """FP64 flops per particle of k_adj_push_gather: weights and their derivatives on both
+    axes, the reverse push (48), per stencil node the field dot product, the separable
+    position-gradient sums, the weight product and the eight deposit operands (29), per
+    row the two cross-row sums (4), and the final updates (10).  600 for cubic shapes."""
+    w = {2: 10, 3: 19, 4: 39}[p]
+    dw = {2: 5, 3: 12, 4: 25}[p]
+    return 2 * (w + dw) + 48 + 29 * (p + 1) ** 2 + 4 * (p + 1) + 10
+
+
+def adjoint_roofline(p, n, ms):
+    """k_adj_push_gather against the FP64 pipe (nominal 1.25 TFLOP/s; the kernel's DRAM
+    traffic, 49.6 MB per launch by ncu at this size, is about 3% of the HBM roof)."""
+    if not ms:
+        return None
+    pk = peaks()
+    achieved = flops_adj_push(p) * n / (ms * 1e-3) / 1e12
+    return {"kernel": "k_adj_push_gather", "bound": "alu", "achieved": achieved,
+            "peak": pk["fp64_gflops"] / 1e3, "unit": "TFLOP/s",
+            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": 49.6e6,
+            "peak_source": pk["fp64_src"],
+            "note": f"{flops_adj_push(p)} FP64 flops per particle (cubic: 600); traffic = "
+                    "dram read + write of one launch from ncu on this workload"}
 
 
 def main():

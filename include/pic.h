@@ -241,13 +241,20 @@ int32_t pic_kernels_per_step(const pic_handle *h);
  *   PIC_KT_SORT     the particle sort (keys, scan, scatter) of a sorting step
  *   PIC_KT_DEPOSIT  the move + current deposit kernel (not the clearing of J)
  *   PIC_KT_FIELD    all kernels of pic_field_solve
- *   PIC_KT_GATHER   the gather + push kernel */
+ *   PIC_KT_GATHER   the gather + push kernel
+ * and, in pic_adjoint_backward (one launch group per reversed step):
+ *   PIC_KT_ADJ_PUSH     the reverse push + gather kernel (with its field-adjoint deposit)
+ *   PIC_KT_ADJ_FIELD    the reverse field solve (transforms and per-mode update)
+ *   PIC_KT_ADJ_DEPOSIT  the reverse deposit + move kernel */
 typedef enum {
     PIC_KT_SORT = 0,
     PIC_KT_DEPOSIT = 1,
     PIC_KT_FIELD = 2,
     PIC_KT_GATHER = 3,
-    PIC_KT_COUNT = 4
+    PIC_KT_ADJ_PUSH = 4,
+    PIC_KT_ADJ_FIELD = 5,
+    PIC_KT_ADJ_DEPOSIT = 6,
+    PIC_KT_COUNT = 7
 } pic_kernel_timer;
 
 /* max_launches > 0 starts timing: resets every timer and creates max_launches event

@@ -174,9 +174,12 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const doub
     const size_t np = a->n, ng = a->ng;
     AdjParticles ab = adjoint_arrays(a);
     CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
+    TimedScope tp(h, PIC_KT_ADJ_PUSH);
     CK(launch_adj_push_gather(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np, s1 + 3 * np,
                               s0 + 4 * np, s0 + 5 * np, s0 + 6 * np, s0 + 7 * np, gf, g, ab, a->fb,
                               (int64_t)np, h->err, h->s));
+    tp.end();
+    TimedScope tf(h, PIC_KT_ADJ_FIELD);
     CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, h->twy, -1, 0, h->s));
     const bool fused = adj_columns_smem(h->nx) <= kFieldColumnsSmemMax;
     if (!fused) CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
@@ -199,6 +202,8 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const doub
         CK(launch_adj_modes_bdf(h->mc, ap, a->zb, a->js, h->s));
         CK(inverse_fft(h, a->js, a->jg, 1));
     }
+    tf.end();
+    TimedScope td(h, PIC_KT_ADJ_DEPOSIT);
     CK(launch_adj_deposit_move(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np, a->jg, ab,
                                (int64_t)np, h->err, h->s));
     return PIC_OK;

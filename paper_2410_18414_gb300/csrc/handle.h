@@ -106,6 +106,34 @@ cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb);
 // Waits for the stream and maps the device error word to a status.
 pic_status check_device_error(pic_handle* h);
 
+// Brackets one launch group with the next event pair of a timer (when timing is on and
+// a pair is left); the stop event is recorded by end() or when the scope ends, early
+// returns included.
+class TimedScope {
+  public:
+    TimedScope(pic_handle* h, int which) {
+        if (!h->ktiming) return;
+        auto& t = h->kt[which];
+        if (t.used >= h->kt_cap || 2 * (t.used + 1) > (int64_t)t.ev.size()) return;
+        stop_ = t.ev[2 * t.used + 1];
+        s_ = h->s;
+        cudaEventRecord(t.ev[2 * t.used], s_);
+        ++t.used;
+    }
+    ~TimedScope() { end(); }
+    // Records the stop event now (once).
+    void end() {
+        if (stop_) cudaEventRecord(stop_, s_);
+        stop_ = nullptr;
+    }
+    TimedScope(const TimedScope&) = delete;
+    TimedScope& operator=(const TimedScope&) = delete;
+
+  private:
+    cudaEvent_t stop_ = nullptr;
+    cudaStream_t s_ = nullptr;
+};
+
 }  // namespace gpic
 
 // Returns PIC_ERR_CUDA from the enclosing function (with the call's text as the message

@@ -176,29 +176,6 @@ void free_timers(pic_handle* h) {
     }
 }
 
-// Brackets one launch group with the next event pair of a timer (when timing is on and
-// a pair is left); the stop event is recorded when the scope ends, early returns included.
-class TimedScope {
-  public:
-    TimedScope(pic_handle* h, int which) {
-        if (!h->ktiming) return;
-        auto& t = h->kt[which];
-        if (t.used >= h->kt_cap || 2 * (t.used + 1) > (int64_t)t.ev.size()) return;
-        stop_ = t.ev[2 * t.used + 1];
-        s_ = h->s;
-        cudaEventRecord(t.ev[2 * t.used], s_);
-        ++t.used;
-    }
-    ~TimedScope() {
-        if (stop_) cudaEventRecord(stop_, s_);
-    }
-    TimedScope(const TimedScope&) = delete;
-    TimedScope& operator=(const TimedScope&) = delete;
-
-  private:
-    cudaEvent_t stop_ = nullptr;
-    cudaStream_t s_ = nullptr;
-};
 
 void free_all(pic_handle* h) {
     free_timers(h);

@@ -32,7 +32,8 @@ FP64, FP32_FIX64 = 0, 1
 FIELDS = {"jx": 0, "jy": 1, "rho": 2, "phi": 3, "ax": 4, "ay": 5, "bz": 6, "ex": 7, "ey": 8,
           "dphidx": 9, "dphidy": 10, "gax": 11, "gay": 12, "daxdx": 13, "daxdy": 14,
           "daydx": 15, "daydy": 16}
-KERNEL_TIMERS = {"sort": 0, "deposit": 1, "field_solve": 2, "gather_push": 3}
+KERNEL_TIMERS = {"sort": 0, "deposit": 1, "field_solve": 2, "gather_push": 3,
+                 "adj_push": 4, "adj_field": 5, "adj_deposit": 6}
 
 
 class PicError(RuntimeError):
