@@ -21,7 +21,8 @@ Modules:
   spectral  -- naive 2-D DFT, wavenumbers, spectral gradient / divergence
   steppers  -- BDF-k, CDF-2 and s-stage DIRK per-mode wave updates (section 3)
   pic       -- deposit, gather, IAEM push, initial state, Algorithm 1 step,
-               residuals and energies (sections 2, 3, 4)
+               residuals and energies (sections 2, 3, 4); 2D-2V or 2D-3V, one
+               species or a species table
   adjoint   -- discrete adjoint of the BDF-k step: gradients of the final magnetic
                energy (or final momenta) with respect to v^0 and P^0
 

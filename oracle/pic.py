@@ -32,6 +32,7 @@ Readings of points the paper leaves open (each also listed in the design notes):
     other signs); CDF particles use phi~ = (phi^{n+3/2} + phi^{n+1/2})/2.
   * Positions wrap into [0, L) after the move; node indices wrap modulo N.
 """
+import dataclasses
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -39,6 +40,8 @@ import numpy as np
 from . import bspline, spectral, steppers
 
 FIELD_NAMES = ("dphidx", "dphidy", "ax", "ay", "daxdx", "daxdy", "daydx", "daydy")
+# 2D-3V adds the z potential and its in-plane gradient (d/dz = 0 on the plane)
+FIELD_NAMES_Z = ("az", "dazdx", "dazdy")
 
 
 @dataclass
@@ -59,6 +62,19 @@ class Config:
     q: float = -1.0
     m: float = 1.0
     w: float = 1.0                  # macro-particle weight
+    vdim: int = 2                   # velocity components: 2 (2D-2V) or 3 (2D-3V)
+    species: tuple = None           # ((q, m, w), ...) per species, or None: one species
+
+    def particle_constants(self, sp=None):
+        """(q_p = w q, q, m) of each particle.  Section 2.2 writes the equations of motion
+        and the densities with the charge q_i and mass m_i of each particle, and section
+        2.1 sums the densities over species; with a species table the values come per
+        particle from its species index sp, else they are the single species' scalars."""
+        if self.species is None:
+            return self.w * self.q, self.q, self.m
+        tab = np.asarray(self.species, dtype=np.float64)
+        sp = np.asarray(sp)
+        return tab[sp, 2] * tab[sp, 0], tab[sp, 0], tab[sp, 1]
 
     @property
     def mu0(self):
@@ -87,6 +103,10 @@ class State:
     n: int = 0
     grids: dict = field(default_factory=dict)   # last step's grid quantities
     res: dict = field(default_factory=dict)     # last step's residual spectra
+    pz: np.ndarray = None                       # 2D-3V: z momentum and velocities
+    vz: np.ndarray = None
+    vz_old: np.ndarray = None
+    sp: np.ndarray = None                       # species index of each particle
 
 
 # ------------------------------------------------------- particle <-> mesh ----
@@ -146,6 +166,8 @@ def iaem_push(cfg, st, g):
     g holds the eight gathered quantities of FIELD_NAMES; (grad A . v*)_l is
     sum_m (d_l A_m) v*_m.  v^{n+1} overwrites v^n and v^n becomes v^{n-1}.
     """
+    if cfg.vdim == 3 or cfg.species is not None:
+        return iaem_push_general(cfg, st, g)
     dt, q = cfg.dt, cfg.q
     vsx = 2.0 * st.vx - st.vx_old
     vsy = 2.0 * st.vy - st.vy_old
@@ -157,6 +179,38 @@ def iaem_push(cfg, st, g):
 
 
 # ------------------------------------------------------------ field solve ----
+
+def iaem_push_general(cfg, st, g):
+    """The IAEM update of section 4.1 with per-particle charges and masses (section 2.2)
+    and, in 2D-3V, three momentum components: (grad A . v*)_l = sum_{m=x,y,z} d_l A_m v*_m
+    for l = x, y, and d/dz = 0 leaves P_z unchanged; u = P - q A has three components and
+    v = c^2 u / sqrt(c^2 |u|^2 + (m c^2)^2)."""
+    _, q, m = cfg.particle_constants(st.sp)
+    dt, c2 = cfg.dt, cfg.c * cfg.c
+    three = cfg.vdim == 3
+    vsx = 2.0 * st.vx - st.vx_old
+    vsy = 2.0 * st.vy - st.vy_old
+    fx = -g["dphidx"] + g["daxdx"] * vsx + g["daydx"] * vsy
+    fy = -g["dphidy"] + g["daxdy"] * vsx + g["daydy"] * vsy
+    if three:
+        vsz = 2.0 * st.vz - st.vz_old
+        fx = fx + g["dazdx"] * vsz
+        fy = fy + g["dazdy"] * vsz
+    st.px = st.px + q * dt * fx
+    st.py = st.py + q * dt * fy
+    ux = st.px - q * g["ax"]
+    uy = st.py - q * g["ay"]
+    u2 = ux * ux + uy * uy
+    if three:
+        uz = st.pz - q * g["az"]
+        u2 = u2 + uz * uz
+    den = np.sqrt(c2 * u2 + (m * c2) ** 2)
+    st.vx_old, st.vy_old = st.vx, st.vy
+    st.vx, st.vy = c2 * ux / den, c2 * uy / den
+    if three:
+        st.vz_old = st.vz
+        st.vz = c2 * uz / den
+
 
 def _k(cfg):
     return spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
@@ -174,23 +228,35 @@ def _grid_fields(cfg, phi_hat, ax_hat, ay_hat):
     return {name: spectral.idft2(s).real for name, s in spectra.items()}
 
 
-def deposited_charge_hat(cfg, x, y):
+def _grid_fields_z(cfg, az_hat):
+    """A_z and its in-plane gradient on the mesh (2D-3V)."""
+    kx, ky, _ = _k(cfg)
+    spectra = {"az": az_hat, "dazdx": 1j * kx * az_hat, "dazdy": 1j * ky * az_hat}
+    return {name: spectral.idft2(s).real for name, s in spectra.items()}
+
+
+def deposited_charge_hat(cfg, x, y, sp=None):
     """Spectrum of the charge deposited at the given positions, its K = 0 modes removed
     as at t = 0 (reading R15): rho^{n+1} of the naive update that section 5 compares
     against (both rho and J mapped to the mesh with the particle shape)."""
     kx, ky, K = _k(cfg)
-    rho_hat = spectral.dft2(deposit(cfg, x, y, np.full(len(x), cfg.w * cfg.q)))
+    qp = cfg.particle_constants(sp)[0] * np.ones(len(x))
+    rho_hat = spectral.dft2(deposit(cfg, x, y, qp))
     rho_hat[K == 0.0] = 0.0
     return rho_hat
 
 
-def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
+def field_solve(cfg, st, jx, jy, rho_dep_hat=None, jz=None):
     """Continuity + implicit wave solve + spectral gradients for the new J (Algorithm 1).
 
     Updates st.hist, records residual spectra in st.res (before the history shift,
     so every level a residual needs is still there) and returns the eight mesh
     fields the particles gather.  With cfg.charge == "deposit" (BDF-k and DIRK only),
     rho^{n+1} is rho_dep_hat, the deposited charge, instead of the continuity update.
+    In 2D-3V (jz given) A_z follows the same stepper with the source mu0 J_z and the
+    three A_z fields are returned too; A_z is in neither the continuity equation nor the
+    gauge (d/dz = 0), and E_z = -dA_z/dt is the stepper's discrete derivative (BDF: the
+    BDF difference, CDF-2: the centred difference at n+1/2, DIRK: -v_Az).
     """
     if cfg.charge == "deposit" and (rho_dep_hat is None or cfg.stepper == "cdf2"):
         raise ValueError("the deposited-charge update needs rho_dep_hat and a BDF or DIRK stepper")
@@ -228,6 +294,12 @@ def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
         ey_hat = -1j * ky * phi_new - day / bdt
         res["gauss"] = spectral.div_hat(ex_hat, ey_hat, kx, ky) - rho_new / eps0
         res["ex"], res["ey"] = ex_hat, ey_hat
+        if jz is not None:
+            jz_hat = spectral.dft2(jz)
+            az_new = steppers.bdf_wave_update(h["az"], mu0 * jz_hat, K, c, dt, beta, C)
+            azs = [az_new] + h["az"]
+            res["ez"] = -sum(float(a[j]) * azs[j] for j in range(len(a))) / bdt
+            h["az"] = azs[:-1]
         h["phi"] = phis[:-1]
         h["ax"] = axs[:-1]
         h["ay"] = ays[:-1]
@@ -261,6 +333,16 @@ def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
                         - 0.5 * (rho_new + h["rho_prev"]) / eps0)
         res["ex"], res["ey"] = ex_hat, ey_hat
         phi_part = 0.5 * (phi_new + h["phi"])                               # phi~ at t^{n+1}
+        if jz is not None:
+            jz_hat = spectral.dft2(jz)
+            if cfg.cdf_form == "implicit":
+                az_new = steppers.cdf2_wave_update(h["az"], h["az_prev"], mu0 * jz_hat,
+                                                   mu0 * h["jz_prev"], K, c, dt)
+            else:
+                az_new = upd(h["az"], h["az_prev"], mu0 * h["jz"], K, c, dt)
+            res["ez"] = -(az_new - h["az"]) / dt
+            h["az_prev"], h["az"] = h["az"], az_new
+            h["jz_prev"], h["jz"] = h["jz"], jz_hat
         h["phi_prev"], h["phi"] = h["phi"], phi_new
         h["rho_prev"], h["rho"] = h["rho"], rho_new
         h["ax_prev"], h["ax"] = h["ax"], ax_new
@@ -294,6 +376,12 @@ def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
         ey_hat = -1j * ky * phi_new - vay_new
         res["gauss"] = spectral.div_hat(ex_hat, ey_hat, kx, ky) - rho_new / eps0
         res["ex"], res["ey"] = ex_hat, ey_hat
+        if jz is not None:
+            jz_hat = spectral.dft2(jz)
+            az_new, vaz_new = steppers.dirk_wave_update(
+                h["az"], h["vaz"], mu0 * h["jz"], mu0 * jz_hat, K, c, dt, A, b, cv)
+            res["ez"] = -vaz_new
+            h.update(az=az_new, vaz=vaz_new, jz=jz_hat)
         h.update(phi=phi_new, vphi=vphi_new, ax=ax_new, vax=vax_new, ay=ay_new,
                  vay=vay_new, rho=rho_new, jx=jx_hat, jy=jy_hat)
         phi_part = phi_new
@@ -311,6 +399,13 @@ def field_solve(cfg, st, jx, jy, rho_dep_hat=None):
         "ey": spectral.idft2(res["ey"]).real,
     }
     fields = _grid_fields(cfg, phi_part, ax_new, ay_new)
+    if jz is not None:
+        az_new = h["az"][0] if cfg.stepper == "bdf" else h["az"]
+        st.grids.update(jz=jz, az=spectral.idft2(az_new).real,
+                        bx=spectral.idft2(1j * ky * az_new).real,
+                        by=spectral.idft2(-1j * kx * az_new).real,
+                        ez=spectral.idft2(res["ez"]).real)
+        fields.update(_grid_fields_z(cfg, az_new))
     st.grids.update(fields)
     return fields
 
@@ -330,13 +425,28 @@ def taylor_back_velocity(cfg, vx, vy, ex, ey):
     return vx - coef * (ex - vx * vdote / c2), vy - coef * (ey - vy * vdote / c2)
 
 
-def initial_state(cfg, x0, y0, vx0, vy0, sample=None):
+def taylor_back_velocity3(cfg, vx, vy, vz, ex, ey, q, m):
+    """The Taylor start of taylor_back_velocity with three velocity components and the
+    particles' own charges and masses (E_z = 0 at t = 0: A^0 = 0 and dA_z/dt = 0)."""
+    c2 = cfg.c * cfg.c
+    gamma = 1.0 / np.sqrt(1.0 - (vx * vx + vy * vy + vz * vz) / c2)
+    vdote = vx * ex + vy * ey
+    coef = cfg.dt * q / (gamma * m)
+    return (vx - coef * (ex - vx * vdote / c2), vy - coef * (ey - vy * vdote / c2),
+            vz + coef * vz * vdote / c2)
+
+
+def initial_state(cfg, x0, y0, vx0, vy0, sample=None, vz0=None, species=None):
     """t = 0 state for Algorithm 1 (readings listed in the module docstring).
 
     sample: optional particle indices.  The grid quantities always come from every
     particle; with a sample, the particle arrays of the state (and the Taylor start) are
     those of the sampled particles only, each equal to its value without sampling.
+    vz0: the z velocities (2D-3V); species: each particle's index into cfg.species.
     """
+    general = cfg.vdim == 3 or cfg.species is not None
+    if general:
+        return _initial_state_general(cfg, x0, y0, vx0, vy0, vz0, species, sample)
     x0 = wrap(np.asarray(x0, dtype=np.float64), cfg.lx)
     y0 = wrap(np.asarray(y0, dtype=np.float64), cfg.ly)
     vx0 = np.asarray(vx0, dtype=np.float64).copy()
@@ -383,23 +493,86 @@ def initial_state(cfg, x0, y0, vx0, vy0, sample=None):
     return st
 
 
+def _initial_state_general(cfg, x0, y0, vx0, vy0, vz0, species, sample):
+    """initial_state with per-particle charges and masses and/or three velocity components:
+    rho^0 deposits each particle's q_p, P^0 = gamma m v^0 with the particle's mass and the
+    three-component gamma, and every A_z level (and its current history) starts at 0."""
+    n = len(x0)
+    if cfg.species is not None and species is None:
+        raise ValueError("a species table needs each particle's species index")
+    sp = None if species is None else np.asarray(species).copy()
+    vz0 = (np.zeros(n) if vz0 is None else np.asarray(vz0, dtype=np.float64).copy())
+    st = initial_state(dataclasses.replace(cfg, vdim=2, species=None), x0, y0, vx0, vy0)
+    # rho^0 from every particle's own charge (the single-species set-up above used w q)
+    x0 = wrap(np.asarray(x0, dtype=np.float64), cfg.lx)
+    y0 = wrap(np.asarray(y0, dtype=np.float64), cfg.ly)
+    kx, ky, K = _k(cfg)
+    qp, q, m = cfg.particle_constants(sp)
+    rho_hat = spectral.dft2(deposit(cfg, x0, y0, qp * np.ones(n)))
+    rho_hat[K == 0.0] = 0.0
+    phi_hat = np.where(K > 0.0, rho_hat / (cfg.eps0 * np.where(K > 0.0, K, 1.0)), 0.0)
+    ex = spectral.idft2(-1j * kx * phi_hat).real
+    ey = spectral.idft2(-1j * ky * phi_hat).real
+    vx0 = np.asarray(vx0, dtype=np.float64).copy()
+    vy0 = np.asarray(vy0, dtype=np.float64).copy()
+    if sample is not None:
+        x0, y0, vx0, vy0, vz0 = x0[sample], y0[sample], vx0[sample], vy0[sample], vz0[sample]
+        if sp is not None:
+            sp = sp[sample]
+        q = q if np.isscalar(q) else q[sample]
+        m = m if np.isscalar(m) else m[sample]
+    exp_ = gather(cfg, x0, y0, ex)
+    eyp = gather(cfg, x0, y0, ey)
+    vxo, vyo, vzo = taylor_back_velocity3(cfg, vx0, vy0, vz0, exp_, eyp, q, m)
+    c2 = cfg.c * cfg.c
+    gamma = 1.0 / np.sqrt(1.0 - (vx0 * vx0 + vy0 * vy0 + vz0 * vz0) / c2)
+    st.x, st.y = x0, y0
+    st.px, st.py = gamma * m * vx0, gamma * m * vy0
+    st.vx, st.vy, st.vx_old, st.vy_old = vx0, vy0, vxo, vyo
+    st.sp = sp
+    if cfg.vdim == 3:
+        st.pz, st.vz, st.vz_old = gamma * m * vz0, vz0, vzo
+    zero = np.zeros_like(rho_hat)
+    h = st.hist
+    for key in list(h):
+        if key.startswith("phi"):
+            h[key] = ([phi_hat.copy() for _ in h[key]] if isinstance(h[key], list)
+                      else phi_hat.copy())
+        elif key.startswith("rho"):
+            h[key] = ([rho_hat.copy() for _ in h[key]] if isinstance(h[key], list)
+                      else rho_hat.copy())
+    if cfg.vdim == 3:
+        if cfg.stepper == "bdf":
+            h["az"] = [zero.copy() for _ in range(2 * cfg.bdf_order)]
+        elif cfg.stepper == "cdf2":
+            h.update(az=zero.copy(), az_prev=zero.copy(), jz=zero.copy(), jz_prev=zero.copy())
+        else:
+            h.update(az=zero.copy(), vaz=zero.copy(), jz=zero.copy())
+    st.grids = {"rho": spectral.idft2(rho_hat).real, "phi": spectral.idft2(phi_hat).real,
+                "ex0": exp_, "ey0": eyp}
+    return st
+
+
 def step(cfg, st):
     """Advance one time step of Algorithm 1 (section 4.2)."""
     st.x = wrap(st.x + st.vx * cfg.dt, cfg.lx)
     st.y = wrap(st.y + st.vy * cfg.dt, cfg.ly)
-    qp = cfg.w * cfg.q
+    qp = cfg.particle_constants(st.sp)[0]
     jx = deposit(cfg, st.x, st.y, qp * st.vx)
     jy = deposit(cfg, st.x, st.y, qp * st.vy)
-    rho_dep = deposited_charge_hat(cfg, st.x, st.y) if cfg.charge == "deposit" else None
-    fields = field_solve(cfg, st, jx, jy, rho_dep)
-    g = {name: gather(cfg, st.x, st.y, fields[name]) for name in FIELD_NAMES}
+    jz = deposit(cfg, st.x, st.y, qp * st.vz) if cfg.vdim == 3 else None
+    rho_dep = (deposited_charge_hat(cfg, st.x, st.y, st.sp) if cfg.charge == "deposit"
+               else None)
+    fields = field_solve(cfg, st, jx, jy, rho_dep, jz=jz)
+    names = FIELD_NAMES + (FIELD_NAMES_Z if cfg.vdim == 3 else ())
+    g = {name: gather(cfg, st.x, st.y, fields[name]) for name in names}
     iaem_push(cfg, st, g)
     st.n += 1
     return st
 
 
-def run(cfg, x0, y0, vx0, vy0, nsteps):
-    st = initial_state(cfg, x0, y0, vx0, vy0)
+def run(cfg, x0, y0, vx0, vy0, nsteps, vz0=None, species=None):
+    st = initial_state(cfg, x0, y0, vx0, vy0, vz0=vz0, species=species)
     for _ in range(nsteps):
         step(cfg, st)
     return st
@@ -452,9 +625,20 @@ def energies(cfg, st):
     """
     area = cfg.dx * cfg.dy
     bz = st.grids["bz"]
-    wb = float(np.sum(bz * bz) * area / (2.0 * cfg.mu0))
-    we = float(0.5 * cfg.eps0 * np.sum(st.grids["ex"] ** 2 + st.grids["ey"] ** 2) * area)
+    b2 = bz * bz
+    e2 = st.grids["ex"] ** 2 + st.grids["ey"] ** 2
     v2 = st.vx * st.vx + st.vy * st.vy
+    if cfg.vdim == 3:   # B_x = dA_z/dy, B_y = -dA_z/dx, E_z = -dA_z/dt
+        b2 = b2 + st.grids["bx"] ** 2 + st.grids["by"] ** 2
+        e2 = e2 + st.grids["ez"] ** 2
+        v2 = v2 + st.vz * st.vz
+    wb = float(np.sum(b2) * area / (2.0 * cfg.mu0))
+    we = float(0.5 * cfg.eps0 * np.sum(e2) * area)
     gamma = 1.0 / np.sqrt(1.0 - v2 / (cfg.c * cfg.c))
-    ke = float(np.sum(cfg.w * cfg.m * cfg.c * cfg.c * (gamma - 1.0)))
+    if cfg.species is None:
+        wm = cfg.w * cfg.m
+    else:
+        tab = np.asarray(cfg.species, dtype=np.float64)
+        wm = tab[st.sp, 2] * tab[st.sp, 1]
+    ke = float(np.sum(wm * cfg.c * cfg.c * (gamma - 1.0)))
     return {"wb": wb, "we": we, "ke": ke}
