@@ -84,7 +84,12 @@ typedef enum {
     PIC_FIELD_DPHIDX = 9, PIC_FIELD_DPHIDY = 10,  /* the eight fields the particles      */
     PIC_FIELD_GAX = 11, PIC_FIELD_GAY = 12,       /* gather: grad phi~, A, grad A        */
     PIC_FIELD_DAXDX = 13, PIC_FIELD_DAXDY = 14,
-    PIC_FIELD_DAYDX = 15, PIC_FIELD_DAYDY = 16
+    PIC_FIELD_DAYDX = 15, PIC_FIELD_DAYDY = 16,
+    /* 2D-3V only (vdim = 3), PIC_ERR_STATE otherwise: */
+    PIC_FIELD_JZ = 17,                        /* J_z^{n+1}                                 */
+    PIC_FIELD_AZ = 18,                        /* A_z^{n+1}                                 */
+    PIC_FIELD_BX = 19, PIC_FIELD_BY = 20,    /* dAz/dy, -dAz/dx at n+1                    */
+    PIC_FIELD_DAZDX = 21, PIC_FIELD_DAZDY = 22  /* the in-plane gradient the particles gather */
 } pic_field;
 
 typedef struct {
@@ -104,7 +109,17 @@ typedef struct {
     double dirk_b[4];        /* Butcher weights                                             */
     double dirk_c[4];        /* Butcher nodes                                               */
     int32_t charge;          /* pic_charge: where rho^{n+1} comes from (0: continuity)      */
-    int32_t reserved[7];     /* must be zero                                                */
+    int32_t vdim;            /* velocity components: 0 or 2 = 2D-2V; 3 = 2D-3V (adds P_z,
+                                v_z, J_z and A_z; d/dz = 0, so P_z is constant and A_z
+                                obeys its own wave equation with source mu0 J_z)           */
+    int32_t nspecies;        /* 0: one species (q, m, weight above); 1..4: each particle
+                                carries a species index into species_q/m/w (section 2.1
+                                sums the densities over species; section 2.2 writes the
+                                equations with each particle's own charge and mass)        */
+    int32_t reserved[5];     /* must be zero                                                */
+    double species_q[4];     /* charge, mass and macro-particle weight of each species     */
+    double species_m[4];
+    double species_w[4];
 } pic_config;
 
 /* Source of the charge rho^{n+1} of each step. */
@@ -118,10 +133,14 @@ typedef enum {
 } pic_charge;
 
 /* Initial particle state: positions x^0 (wrapped into the domain by pic_init) and
- * velocities v^0 (|v^0| < c).  Arrays of n FP64 values, host or device. */
+ * velocities v^0 (|v^0| < c).  Arrays of n FP64 values, host or device.  vz (2D-3V) and
+ * species (nspecies > 0: int32 indices in 0..nspecies-1; an index out of range is
+ * reported as PIC_ERR_NONFINITE) are required when the config uses them, else ignored. */
 typedef struct {
     const double *x, *y, *vx, *vy;
     int64_t n;
+    const double *vz;
+    const int32_t *species;
 } pic_particles_in;
 
 /* Diagnostics of the last step that ran with diagnostics enabled (all FP64).
@@ -133,9 +152,9 @@ typedef struct {
     double gauge_dt_rms;   /* DIRK only: residual of the time-differentiated gauge (eps_2)  */
     double rho_rms;        /* RMS of rho/eps0 (scale for gauss_rms)                         */
     double div_a_rms;      /* RMS of div A^{n+1} (scale for gauge_rms)                      */
-    double w_e;            /* eps0/2 sum |E|^2 dx dy                                        */
-    double w_b;            /* 1/(2 mu0) sum B_z^2 dx dy                                     */
-    double kinetic;        /* sum_p weight m c^2 (gamma_p - 1)                              */
+    double w_e;            /* eps0/2 sum |E|^2 dx dy (2D-3V: with E_z = -dA_z/dt)          */
+    double w_b;            /* 1/(2 mu0) sum |B|^2 dx dy (2D-2V: B_z only)                   */
+    double kinetic;        /* sum_p weight m c^2 (gamma_p - 1), per species                 */
     int64_t step;          /* step index n+1 these values belong to                         */
 } pic_diagnostics;
 
@@ -144,7 +163,9 @@ typedef struct {
  * charge with its K = 0 modes removed (neutralising background), phi^0 from
  * Poisson's equation, A^0 = 0, P^0 = gamma m v^0, v^{-1} by a first-order Taylor
  * step back in E^0 = -grad phi^0, and every history level at its t = 0 value.
- * On success *out receives the handle.  The stream must outlive the handle. */
+ * On success *out receives the handle.  The stream must outlive the handle.
+ * 2D-3V and species tables run on the unsorted kernels: with sort_interval > 0 they are
+ * PIC_ERR_UNSUPPORTED. */
 pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,
                     pic_handle **out);
 
@@ -227,6 +248,13 @@ pic_status pic_get_field(pic_handle *h, int32_t which, double *dst);
 pic_status pic_read_particles(pic_handle *h, double *x, double *y, double *px, double *py,
                               double *vx, double *vy, double *vx_old, double *vy_old);
 
+/* 2D-3V and species state, as pic_read_particles: pz: P_z (constant), vz, vz_old: v_z^n and
+ * v_z^{n-1}; species: each particle's species index (int32).  Any pointer may be NULL.
+ * PIC_ERR_STATE when the handle has no such state (vdim 2 for the first three, no species
+ * table for the last). */
+pic_status pic_read_particles_z(pic_handle *h, double *pz, double *vz, double *vz_old,
+                                int32_t *species);
+
 /* Wait for all work enqueued by this handle; report latched device errors. */
 pic_status pic_sync(pic_handle *h);
 
@@ -307,8 +335,8 @@ typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init
  * (step 0, no step started), FP64, PIC_STEPPER_BDF, PIC_CHARGE_CONTINUITY and without
- * sorting (sort_interval 0), else PIC_ERR_UNSUPPORTED (or PIC_ERR_STATE for a handle
- * that has stepped).  checkpoint_every is clamped to 1..nsteps.  Allocates all the
+ * sorting (sort_interval 0), 2D-2V with one species, else PIC_ERR_UNSUPPORTED (or
+ * PIC_ERR_STATE for a handle that has stepped).  checkpoint_every is clamped to 1..nsteps.  Allocates all the
  * adjoint's device memory here (PIC_ERR_CUDA if that fails).  The adjoint keeps h:
  * destroy it before h.  PIC_ERR_INVALID_ARG for NULL pointers or nsteps < 1. */
 pic_status pic_adjoint_create(pic_handle *h, int32_t nsteps, int32_t checkpoint_every,

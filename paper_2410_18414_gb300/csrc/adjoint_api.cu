@@ -220,10 +220,10 @@ pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 1) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 1");
     if (h->fp32 || h->cfg.stepper != PIC_STEPPER_BDF || h->cfg.charge != PIC_CHARGE_CONTINUITY ||
-        h->sorting)
+        h->sorting || h->vdim == 3 || h->spp.n > 0)
         return fail(h, PIC_ERR_UNSUPPORTED,
-                    "the adjoint needs the FP64 path, the BDF-k stepper, the continuity charge "
-                    "and no sorting");
+                    "the adjoint needs the FP64 path, the BDF-k stepper, the continuity charge, "
+                    "one species in 2D-2V and no sorting");
     if (h->step != 0 || h->phase != 0)
         return fail(h, PIC_ERR_STATE, "the adjoint needs a handle fresh from pic_init");
     pic_adjoint* a = new pic_adjoint();

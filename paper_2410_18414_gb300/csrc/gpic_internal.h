@@ -10,6 +10,18 @@ namespace gpic {
 constexpr int kMaxRadices = 16;
 constexpr int kMaxBdf = 6;
 constexpr int kMaxDirk = 4;
+constexpr int kMaxSpecies = 4;
+
+// Per-particle constants from a species table: section 2.2 writes the equations of motion
+// and the densities with each particle's own charge and mass, section 2.1 sums the
+// densities over species.  n = 0: one species (the kernels take the plain path and never
+// read the index array).  With a table the deposits multiply each contribution by q_s w_s
+// (the handle's current scale is then 1/(dx dy)).
+struct SpeciesParams {
+    int n;
+    double qw[kMaxSpecies];
+    double q[kMaxSpecies], m[kMaxSpecies], w[kMaxSpecies];
+};
 
 // 1-D transform description: length n = prod(radix[0..nf-1]), radices in {2,3,4}.
 // Per pass f, precomputed on the host: Ns (product of the earlier radices), nr = n / R,
@@ -134,6 +146,22 @@ cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams
                                  const CdfParams& cp, const DirkParams& dp, const void* z,
                                  void* f4, void* e, double* diag, const FftDesc& fd,
                                  const void* tw, cudaStream_t s);
+// 2D-3V: the A_z wave update of the stepper in use (the same recurrences as A_x with the
+// source mu0 J_z), from zz = FFT(J_z sums); writes the two packed outputs
+// f2 = [(i kx - ky) A_z, A_z] / (nx ny) for the inverse transforms, and adds |E_z|^2 and
+// |B_x|^2 + |B_y|^2 to the diagnostics when mc.diag.
+struct ZParams {
+    int kind, form;
+    void* az[2 * kMaxBdf];   // BDF: history newest first; az_new: the slot of the new level
+    void* az_new;
+    void *az_n, *az_prev;    // CDF: A_z^n, A_z^{n-1} (the new level overwrites az_prev);
+    void *jz_n, *jz_prev;    //      J_z^n, J_z^{n-1} (the new current overwrites jz_prev)
+    void* vaz;               // DIRK: dA_z/dt; az_n and jz_n hold A_z^n and J_z^n
+};
+template <typename T>
+cudaError_t launch_zfield(const ModeCommon& mc, const BdfParams& bp, const DirkParams& dp,
+                          const ZParams& zp, const void* zz, void* f2, double* diag,
+                          cudaStream_t s);
 // Fill the wavenumber and inverse-denominator tables of mc (kind: StepperKind).
 cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& bp,
                                const DirkParams& dp, double* kxt, double* kyt, double* invd,
@@ -149,22 +177,34 @@ struct ParticleGeom {
     double lx, ly, inv_dx, inv_dy, dt;
 };
 
+// sp/spp (optional): each particle's species index and the table; the contributions are
+// then multiplied by q_s w_s.
 template <typename T>
 cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
                                 const T* vy, int64_t n, double2* j, unsigned int* err,
-                                cudaStream_t s);
+                                cudaStream_t s, const int32_t* sp = nullptr,
+                                const SpeciesParams* spp = nullptr);
 template <typename T>
 cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
-                                  double2* j, unsigned int* err, cudaStream_t s);
+                                  double2* j, unsigned int* err, cudaStream_t s,
+                                  const int32_t* sp = nullptr, const SpeciesParams* spp = nullptr);
 // Fixed-point current (int64 per component, contribution = round(value * scale)).
 template <typename T>
 cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
                                     const T* vy, int64_t n, longlong2* j, float scale,
-                                    unsigned int* err, cudaStream_t s);
+                                    unsigned int* err, cudaStream_t s, const int32_t* sp = nullptr,
+                                    const SpeciesParams* spp = nullptr);
 template <typename T>
 cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, const T* y,
                                       int64_t n, longlong2* j, float scale, unsigned int* err,
-                                      cudaStream_t s);
+                                      cudaStream_t s, const int32_t* sp = nullptr,
+                                      const SpeciesParams* spp = nullptr);
+// 2D-3V: J_z of the moved particles (x^{n+1}, v_z^n) into the .x parts of jz (FP64 sums,
+// or int64 with `scale` when fix).
+template <typename T>
+cudaError_t launch_deposit_z(int p, const ParticleGeom& g, const T* x, const T* y, const T* vz,
+                             int64_t n, const int32_t* sp, const SpeciesParams& spp, void* jz,
+                             bool fix, float scale, unsigned int* err, cudaStream_t s);
 // out[k] = (J[k].x, J[k].y) * unscale in complex storage type T.
 template <typename T>
 cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,
@@ -188,6 +228,21 @@ cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& p
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vx_old,
                                T* vy_old, int64_t n, const void* fields4, double* gout,
                                double* diag, unsigned int* err, cudaStream_t s);
+// Gather + push with a species table and/or three velocity components (vz == NULL: 2D-2V):
+// fz holds the A_z fields as [node][2] complex ((dAz/dx, dAz/dy), (Az, 0)); P_z is constant.
+template <typename T>
+cudaError_t launch_gather_push3(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
+                                const T* y, T* px, T* py, const T* pz, const T* vx, const T* vy,
+                                const T* vz, T* vx_old, T* vy_old, T* vz_old, const int32_t* sp,
+                                const SpeciesParams& spp, int64_t n, const void* fields4,
+                                const void* fz, double* diag, unsigned int* err, cudaStream_t s);
+// t = 0 with a species table and/or three velocity components.
+template <typename T>
+cudaError_t launch_init_particles3(int p, const ParticleGeom& g, const PushParams& pp, T* x, T* y,
+                                   T* px, T* py, T* pz, const T* vx, const T* vy, const T* vz,
+                                   T* vx_old, T* vy_old, T* vz_old, const int32_t* sp,
+                                   const SpeciesParams& spp, int64_t n, const void* e2,
+                                   unsigned int* err, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_particles(int p, const ParticleGeom& g, const PushParams& pp, T* x, T* y,
                                   T* px, T* py, const T* vx, const T* vy, T* vx_old, T* vy_old,

@@ -63,6 +63,19 @@ struct pic_handle {
     double* tmpd = nullptr;  // real scratch (ng)
     void *twx = nullptr, *twy = nullptr;
     gpic::FftDesc fx{}, fy{};
+    // 2D-3V (vdim 3) and species tables
+    int vdim = 2;
+    gpic::SpeciesParams spp{};        // spp.n = 0: one species (q, m, weight of cfg)
+    int32_t* species = nullptr;       // each particle's species index (device)
+    void* pz = nullptr;               // P_z (constant: d/dz = 0)
+    void* vz[2] = {nullptr, nullptr}; // v_z, rotated with v
+    void* Jz = nullptr;               // J_z sums in the .x parts (double2, or longlong2)
+    void* Zz = nullptr;               // spectrum of J_z
+    void* F2 = nullptr;               // the two packed A_z output spectra
+    void* Gz = nullptr;               // [node][2] complex: (dAz/dx, dAz/dy), (Az, 0)
+    std::vector<void*> az_l;          // BDF: A_z ring (the slots and head of phi, Ax, Ay)
+    void *az = nullptr, *az_prev = nullptr, *jz = nullptr, *jz_prev = nullptr,
+         *vaz = nullptr;              // CDF-2: A_z^n, A_z^{n-1}, J_z^n, J_z^{n-1}; DIRK: az, vaz, jz
     // time histories (BDF rings; CDF pairs; DIRK state)
     std::vector<void*> phi_l, ax_l, ay_l, rho_l;
     int L = 0, Lr = 0, head = 0, head_r = 0;

@@ -504,6 +504,69 @@ k_field_columns(ModeCommon mc, Params prm, const C* __restrict__ z, C* __restric
     if (mc.diag) reduce_diag(acc, diag);
 }
 
+// 2D-3V: the A_z update of mode idx (one thread per mode over zz = FFT(J_z sums)).  With
+// d/dz = 0 the z component of the vector potential obeys its own wave equation with source
+// mu0 J_z, stepped with the same recurrences as A_x; it enters neither the continuity
+// equation nor the gauge.  E_z = -dA_z/dt is the stepper's discrete derivative (BDF: the
+// BDF difference; CDF-2: the centred difference at n+1/2; DIRK: -v_Az), B_x = i ky A_z,
+// B_y = -i kx A_z.
+template <typename C>
+__global__ void __launch_bounds__(kModeThreads)
+k_zmode(ModeCommon mc, BdfParams bp, DirkParams dp, ZParams zp, const C* __restrict__ zz,
+        C* __restrict__ f2, double* __restrict__ diag) {
+    const int nmodes = mc.nx * mc.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[D_NSLOTS];
+#pragma unroll
+    for (int s = 0; s < D_NSLOTS; ++s) acc[s] = 0.0;
+    if (idx < nmodes) {
+        const int i = idx / mc.ny, j = idx - i * mc.ny;
+        const double kx = mc.kxt[i], ky = mc.kyt[j], K = kx * kx + ky * ky;
+        const zd jz = zscale(mc.jscale, zload(zz + idx));
+        zd az_new, ez;
+        if (zp.kind == K_BDF) {
+            zd s = zscale(bp.g * mc.mu0, jz);
+            for (int d = 1; d <= 2 * bp.k; ++d) s = zfms(s, bp.C[d], hload(zp.az[d - 1], idx));
+            az_new = zscale(mc.invd[idx], s);
+            zd daz = bp.a[0] * az_new;
+            for (int d = 1; d <= bp.k; ++d) daz = daz + bp.a[d] * hload(zp.az[d - 1], idx);
+            ez = -(1.0 / bp.bdt) * daz;
+            hstore(zp.az_new, idx, az_new);
+        } else if (zp.kind == K_CDF2) {
+            const double dt = mc.dt, inv = mc.invd[idx];
+            const zd az = hload(zp.az_n, idx), azp = hload(zp.az_prev, idx);
+            if (zp.form == 0) {
+                const double th = 0.5 * mc.c * mc.c * dt * dt;
+                az_new = inv * (2.0 * az + (th * mc.mu0) * (jz + hload(zp.jz_prev, idx))) - azp;
+            } else {
+                const double h2 = mc.c * mc.c * dt * dt;
+                const zd s = mc.mu0 * hload(zp.jz_n, idx);
+                az_new = (zp.form == 1) ? inv * (2.0 * az + h2 * s) - azp
+                                        : 2.0 * az - azp + h2 * (s - K * az);
+            }
+            ez = -(1.0 / dt) * (az_new - az);
+            hstore(zp.az_prev, idx, az_new);
+            hstore(zp.jz_prev, idx, jz);
+        } else {
+            const zd az = hload(zp.az_n, idx), vaz = hload(zp.vaz, idx);
+            zd vaz_new;
+            dirk_mode(dp, K, mc.c, mc.dt, mc.invd + idx, (size_t)nmodes, az, vaz,
+                      mc.mu0 * hload(zp.jz_n, idx), mc.mu0 * jz, az_new, vaz_new);
+            ez = -vaz_new;
+            hstore(zp.az_n, idx, az_new);
+            hstore(zp.vaz, idx, vaz_new);
+            hstore(zp.jz_n, idx, jz);
+        }
+        if (mc.diag) {
+            acc[D_WE] += znorm2(ez);
+            acc[D_WB] += K * znorm2(az_new);
+        }
+        zstore(f2 + idx, zscale(mc.inv_n, grad_packed(kx, ky, az_new)));
+        zstore(f2 + (size_t)nmodes + idx, zscale(mc.inv_n, az_new));
+    }
+    if (mc.diag) reduce_diag(acc, diag);
+}
+
 __global__ void k_mode_tables(ModeCommon mc, int kind, BdfParams bp, DirkParams dp,
                               double* __restrict__ kxt, double* __restrict__ kyt,
                               double* __restrict__ invd) {
@@ -545,7 +608,8 @@ k_mode_init(ModeCommon mc, const C* __restrict__ zq, double2* __restrict__ rho_o
     zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
 }
 
-// out = inv_n * (A + i B) with (op 0) A = a, B = b, or (op 1) A = i kx b - i ky a, B = 0.
+// out = inv_n * (A + i B) with (op 0) A = a, B = b, (op 1) A = i kx b - i ky a, B = 0, or
+// (op 2) A = i ky a, B = -i kx a (B_x, B_y of A_z = a).
 template <typename C>
 __global__ void __launch_bounds__(kModeThreads)
 k_mode_pack2(ModeCommon mc, const double2* __restrict__ a, const double2* __restrict__ b, int op,
@@ -559,6 +623,10 @@ k_mode_pack2(ModeCommon mc, const double2* __restrict__ a, const double2* __rest
         const int i = idx / mc.ny, j = idx - i * mc.ny;
         const double kx = wavenumber(i, mc.nx, mc.kx_scale), ky = wavenumber(j, mc.ny, mc.ky_scale);
         r = zi(kx * vb) - zi(ky * va);
+    } else if (op == 2) {
+        const int i = idx / mc.ny, j = idx - i * mc.ny;
+        const double kx = wavenumber(i, mc.nx, mc.kx_scale), ky = wavenumber(j, mc.ny, mc.ky_scale);
+        r = zi(ky * va) + zi(zi(-kx * va));
     } else {
         r = va + zi(vb);
     }
@@ -630,6 +698,16 @@ cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& 
 }
 
 template <typename T>
+cudaError_t launch_zfield(const ModeCommon& mc, const BdfParams& bp, const DirkParams& dp,
+                          const ZParams& zp, const void* zz, void* f2, double* diag,
+                          cudaStream_t s) {
+    using C = cplx_t<T>;
+    k_zmode<C><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, bp, dp, zp, (const C*)zz, (C*)f2,
+                                                        diag);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_mode_init(const ModeCommon& mc, const void* zq, void* rho, void* phi, void* e,
                              cudaStream_t s) {
     using C = cplx_t<T>;
@@ -659,6 +737,9 @@ cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b
                                                  const void*, cudaStream_t);                      \
     template cudaError_t launch_mode_init<T>(const ModeCommon&, const void*, void*, void*, void*, \
                                              cudaStream_t);                                       \
+    template cudaError_t launch_zfield<T>(const ModeCommon&, const BdfParams&, const DirkParams&, \
+                                          const ZParams&, const void*, void*, double*,            \
+                                          cudaStream_t);                                          \
     template cudaError_t launch_mode_pack2<T>(const ModeCommon&, const void*, const void*, int,  \
                                               void*, cudaStream_t);
 GPIC_INST(double)

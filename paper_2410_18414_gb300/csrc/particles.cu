@@ -47,6 +47,33 @@ PushT<T> typed(const PushParams& pp) {
                     pp.c, pp.m, pp.weight, pp.diag};
 }
 
+// The deposit factors q_s w_s of a species table in the storage precision.
+template <typename T>
+struct SpeciesT {
+    int n;
+    T qw[kMaxSpecies];
+};
+template <typename T>
+SpeciesT<T> typed_species(const SpeciesParams* spp) {
+    SpeciesT<T> r{};
+    if (spp) {
+        r.n = spp->n;
+        for (int k = 0; k < kMaxSpecies; ++k) r.qw[k] = (T)spp->qw[k];
+    }
+    return r;
+}
+// q_s w_s of particle p (1 without a table); false for an index outside the table.
+template <typename T>
+__device__ __forceinline__ bool species_factor(const int32_t* __restrict__ sp,
+                                               const SpeciesT<T>& spt, int64_t p, T& f) {
+    f = (T)1;
+    if (!sp) return true;
+    const int s = sp[p];
+    if ((unsigned)s >= (unsigned)spt.n) return false;
+    f = spt.qw[s];
+    return true;
+}
+
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     const int64_t cap = 152 * 16;
@@ -148,19 +175,25 @@ struct AccFix {
 template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __restrict__ vx,
-               const T* __restrict__ vy, int64_t n, Acc acc, unsigned int* __restrict__ err) {
+               const T* __restrict__ vy, int64_t n, Acc acc, unsigned int* __restrict__ err,
+               const int32_t* __restrict__ sp, SpeciesT<T> spt) {
     const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const T vxi = vx[p], vyi = vy[p];
+        T vxi = vx[p], vyi = vy[p];
         T xp = move_pos(x[p], vxi, dt, lx);
         T yp = move_pos(y[p], vyi, dt, ly);
         x[p] = xp;
         y[p] = yp;
         const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
-        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+        T fq;
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !species_factor(sp, spt, p, fq)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
+        }
+        if (sp) {  // each contribution carries the particle's q_s w_s
+            vxi = rmul(vxi, fq);
+            vyi = rmul(vyi, fq);
         }
         T wx[P + 1], wy[P + 1];
         const int ix = Shape<P, T>::weights(xi, wx);
@@ -182,12 +215,14 @@ k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __rest
 template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                 Acc acc, unsigned int* __restrict__ err) {
+                 Acc acc, unsigned int* __restrict__ err, const int32_t* __restrict__ sp,
+                 SpeciesT<T> spt) {
     const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
-        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+        T fq;
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !species_factor(sp, spt, p, fq)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
@@ -200,7 +235,8 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const int gj = wrap_idx(iy + b, g.ny);
-                acc.add1((size_t)gi * g.ny + gj, rmul(wx[a], wy[b]));
+                const T wab = rmul(wx[a], wy[b]);
+                acc.add1((size_t)gi * g.ny + gj, sp ? rmul(wab, fq) : wab);
             }
         }
     }
@@ -651,6 +687,206 @@ __global__ void k_scatter_by_id(const T* __restrict__ s, const int32_t* __restri
     }
 }
 
+// ------------------------------------------------------------ 2D-3V, species ----
+//
+// Section 2.2 writes the particle equations with three-component P and A and each
+// particle's own charge and mass.  On the plane d/dz = 0: J_z is deposited like J_x, A_z
+// gathered with its in-plane gradient, (grad A . v*)_l gains d_l A_z v*_z for l = x, y,
+// P_z is constant, and u = P - q A has three components.
+
+// J_z of the moved particles (after the move of k_move_deposit): x^{n+1}, v_z^n.
+template <typename T, int P, typename Acc>
+__global__ void __launch_bounds__(kThreads)
+k_deposit_z(GeomT<T> g, const T* __restrict__ x, const T* __restrict__ y,
+            const T* __restrict__ vz, int64_t n, const int32_t* __restrict__ sp, SpeciesT<T> spt,
+            Acc acc, unsigned int* __restrict__ err) {
+    const T idx_ = g.inv_dx, idy = g.inv_dy;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
+        T fq;
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !species_factor(sp, spt, p, fq)) {
+            atomicOr(err, (unsigned)ERR_NONFINITE);
+            continue;
+        }
+        T wx[P + 1], wy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        const T vzi = sp ? rmul(vz[p], fq) : vz[p];
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+            const T tz = rmul(vzi, wx[a]);
+#pragma unroll
+            for (int b = 0; b <= P; ++b) acc.add1(row + wrap_idx(iy + b, g.ny), rmul(tz, wy[b]));
+        }
+    }
+}
+
+// Species constants of particle p in the storage precision (the table's, or the single
+// species' q, m, weight).
+template <typename T>
+struct PushConst {
+    T q, qdt, mc2;
+    double qd, m, w;
+};
+template <typename T>
+__device__ __forceinline__ bool push_const(const PushParams& pp, const int32_t* __restrict__ sp,
+                                           const SpeciesParams& spp, int64_t p, PushConst<T>& k) {
+    double q = pp.q, m = pp.m, w = pp.weight;
+    if (sp) {
+        const int s = sp[p];
+        if ((unsigned)s >= (unsigned)spp.n) return false;
+        q = spp.q[s];
+        m = spp.m[s];
+        w = spp.w[s];
+    }
+    k.q = (T)q;
+    k.qdt = (T)(q * pp.dt);
+    k.mc2 = (T)(m * pp.c * pp.c);
+    k.qd = q;
+    k.m = m;
+    k.w = w;
+    return true;
+}
+
+template <typename T, int P, bool Z3>
+__global__ void __launch_bounds__(kThreads)
+k_gather_push3(GeomT<T> g, PushParams pp, const T* __restrict__ x, const T* __restrict__ y,
+               T* __restrict__ px, T* __restrict__ py, const T* __restrict__ pz,
+               const T* __restrict__ vx, const T* __restrict__ vy, const T* __restrict__ vz,
+               T* __restrict__ vxo, T* __restrict__ vyo, T* __restrict__ vzo,
+               const int32_t* __restrict__ sp, SpeciesParams spp, int64_t n,
+               const cplx_t<T>* __restrict__ F, const cplx_t<T>* __restrict__ Fz,
+               double* __restrict__ diag, unsigned int* __restrict__ err) {
+    using C = cplx_t<T>;
+    const T idx_ = g.inv_dx, idy = g.inv_dy, c2 = (T)(pp.c * pp.c);
+    double kin = 0.0;
+    unsigned bad = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
+        PushConst<T> k;
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !push_const(pp, sp, spp, p, k)) {
+            bad |= ERR_NONFINITE;
+            continue;
+        }
+        T wx[P + 1], wy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        T f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        T fz[3] = {0, 0, 0};  // dAz/dx, dAz/dy, Az
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const size_t nd = row + wrap_idx(iy + b, g.ny);
+                T gv[8];
+                load_node(F + nd * 4, gv);
+                const T w = rmul(wx[a], wy[b]);
+                gather_node(w, gv, f);
+                if (Z3) {
+                    const C z0 = Fz[nd * 2], z1 = Fz[nd * 2 + 1];
+                    fz[0] = rfma(w, z0.x, fz[0]);
+                    fz[1] = rfma(w, z0.y, fz[1]);
+                    fz[2] = rfma(w, z1.x, fz[2]);
+                }
+            }
+        }
+        const T vsx = rfma((T)2, vx[p], -vxo[p]);
+        const T vsy = rfma((T)2, vy[p], -vyo[p]);
+        T fx = rfma(f[6], vsy, rfma(f[4], vsx, -f[0]));
+        T fy = rfma(f[7], vsy, rfma(f[5], vsx, -f[1]));
+        T vsz = (T)0;
+        if (Z3) {
+            vsz = rfma((T)2, vz[p], -vzo[p]);
+            fx = rfma(fz[0], vsz, fx);
+            fy = rfma(fz[1], vsz, fy);
+        }
+        const T Px = rfma(k.qdt, fx, px[p]);
+        const T Py = rfma(k.qdt, fy, py[p]);
+        const T ux = rfma(-k.q, f[2], Px), uy = rfma(-k.q, f[3], Py);
+        T u2 = rfma(ux, ux, rmul(uy, uy));
+        T uz = (T)0;
+        if (Z3) {
+            uz = rfma(-k.q, fz[2], pz[p]);
+            u2 = rfma(uz, uz, u2);
+        }
+        const T den = rsqrt_rn(rfma(c2, u2, rmul(k.mc2, k.mc2)));
+        const T rc = rdiv(c2, den);
+        const T vxn1 = rmul(rc, ux), vyn1 = rmul(rc, uy);
+        px[p] = Px;
+        py[p] = Py;
+        vxo[p] = vxn1;
+        vyo[p] = vyn1;
+        if (Z3) vzo[p] = rmul(rc, uz);
+        if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
+        if (pp.diag) {  // w m c^2 (gamma - 1) in FP64
+            const double c2d = pp.c * pp.c, mc2d = k.m * c2d;
+            const double ud2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+            kin += k.w * (sqrt(c2d * ud2 + mc2d * mc2d) - mc2d);
+        }
+    }
+    if (bad) atomicOr(err, bad);
+    if (pp.diag) {
+        for (int o = 16; o > 0; o >>= 1) kin += __shfl_down_sync(0xffffffffu, kin, o);
+        if ((threadIdx.x & 31) == 0 && kin != 0.0) atomicAdd(diag + D_KIN, kin);
+    }
+}
+
+// t = 0 with species and/or three velocity components: P^0 = gamma m_s v^0 and the Taylor
+// start v^{-1} = v^0 - kappa (E - v (v . E)/c^2), kappa = dt q_s/(gamma m_s), E = (Ex, Ey, 0).
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_init_particles3(ParticleGeom g, PushParams pp, T* __restrict__ x, T* __restrict__ y,
+                  T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
+                  const T* __restrict__ vx, const T* __restrict__ vy, const T* __restrict__ vz,
+                  T* __restrict__ vxo, T* __restrict__ vyo, T* __restrict__ vzo,
+                  const int32_t* __restrict__ sp, SpeciesParams spp, int64_t n,
+                  const cplx_t<T>* __restrict__ E, unsigned int* __restrict__ err) {
+    using C = cplx_t<T>;
+    const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
+    const double c2 = pp.c * pp.c;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const T xi = rmul(x[p], idx_), yj = rmul(y[p], idy);
+        const double vxn = (double)vx[p], vyn = (double)vy[p], vzn = vz ? (double)vz[p] : 0.0;
+        const double v2 = vxn * vxn + vyn * vyn + vzn * vzn;
+        PushConst<T> k;
+        if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny) || !(v2 < c2) ||
+            !push_const(pp, sp, spp, p, k)) {
+            atomicOr(err, (unsigned)ERR_NONFINITE);
+            continue;
+        }
+        T wx[P + 1], wy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        T ex = 0, ey = 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+            const int gi = wrap_idx(ix + a, g.nx);
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const C e = E[(size_t)gi * g.ny + wrap_idx(iy + b, g.ny)];
+                const T w = wx[a] * wy[b];
+                ex += w * e.x;
+                ey += w * e.y;
+            }
+        }
+        const double m = k.m, qs = k.qd;
+        const double gamma = 1.0 / sqrt(1.0 - v2 / c2);
+        px[p] = (T)(gamma * m * vxn);
+        py[p] = (T)(gamma * m * vyn);
+        if (vz) pz[p] = (T)(gamma * m * vzn);
+        const double coef = pp.dt * qs / (gamma * m);
+        const double vdote = vxn * (double)ex + vyn * (double)ey;
+        vxo[p] = (T)(vxn - coef * ((double)ex - vxn * vdote / c2));
+        vyo[p] = (T)(vyn - coef * ((double)ey - vyn * vdote / c2));
+        if (vz) vzo[p] = (T)(vzn + coef * vzn * vdote / c2);
+    }
+}
+
 template <typename T>
 __global__ void k_extract(const cplx_t<T>* __restrict__ src, int stride, int comp, double scale,
                           double* __restrict__ dst, int64_t n) {
@@ -682,36 +918,99 @@ __global__ void k_extract(const cplx_t<T>* __restrict__ src, int stride, int com
 template <typename T>
 cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
                                 const T* vy, int64_t n, double2* j, unsigned int* err,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int32_t* sp, const SpeciesParams* spp) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_move_deposit, AccF64, typed<T>(g), x, y, vx, vy, n, AccF64{j}, err)
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccF64, typed<T>(g), x, y, vx, vy, n, AccF64{j}, err,
+                     sp, typed_species<T>(spp))
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
-                                  double2* j, unsigned int* err, cudaStream_t s) {
+                                  double2* j, unsigned int* err, cudaStream_t s,
+                                  const int32_t* sp, const SpeciesParams* spp) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_deposit_charge, AccF64, g, x, y, n, AccF64{j}, err)
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccF64, g, x, y, n, AccF64{j}, err, sp,
+                     typed_species<T>(spp))
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_move_deposit_fix(int p, const ParticleGeom& g, T* x, T* y, const T* vx,
                                     const T* vy, int64_t n, longlong2* j, float scale,
-                                    unsigned int* err, cudaStream_t s) {
+                                    unsigned int* err, cudaStream_t s, const int32_t* sp,
+                                    const SpeciesParams* spp) {
     if (n == 0) return cudaSuccess;
     GPIC_DISPATCH_PA(p, k_move_deposit, AccFix, typed<T>(g), x, y, vx, vy, n, (AccFix::make(j, scale)),
-                     err)
+                     err, sp, typed_species<T>(spp))
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, const T* y,
                                       int64_t n, longlong2* j, float scale, unsigned int* err,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, const int32_t* sp, const SpeciesParams* spp) {
     if (n == 0) return cudaSuccess;
-    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix::make(j, scale)), err)
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix::make(j, scale)), err, sp,
+                     typed_species<T>(spp))
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_deposit_z(int p, const ParticleGeom& g, const T* x, const T* y, const T* vz,
+                             int64_t n, const int32_t* sp, const SpeciesParams& spp, void* jz,
+                             bool fix, float scale, unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int32_t* spi = spp.n > 0 ? sp : nullptr;
+    if (fix) {
+        GPIC_DISPATCH_PA(p, k_deposit_z, AccFix, typed<T>(g), x, y, vz, n, spi,
+                         typed_species<T>(&spp), (AccFix::make(jz, scale)), err)
+    } else {
+        GPIC_DISPATCH_PA(p, k_deposit_z, AccF64, typed<T>(g), x, y, vz, n, spi,
+                         typed_species<T>(&spp), AccF64{(double2*)jz}, err)
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_push3(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
+                                const T* y, T* px, T* py, const T* pz, const T* vx, const T* vy,
+                                const T* vz, T* vx_old, T* vy_old, T* vz_old, const int32_t* sp,
+                                const SpeciesParams& spp, int64_t n, const void* fields4,
+                                const void* fz, double* diag, unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    using C = cplx_t<T>;
+    const int32_t* spi = spp.n > 0 ? sp : nullptr;
+    const bool z3 = vz != nullptr;
+#define GPIC_GP3(PP)                                                                           \
+    if (z3)                                                                                    \
+        k_gather_push3<T, PP, true><<<blocks_for(n), kThreads, 0, s>>>(                        \
+            typed<T>(g), pp, x, y, px, py, pz, vx, vy, vz, vx_old, vy_old, vz_old, spi, spp, n, \
+            (const C*)fields4, (const C*)fz, diag, err);                                       \
+    else                                                                                       \
+        k_gather_push3<T, PP, false><<<blocks_for(n), kThreads, 0, s>>>(                       \
+            typed<T>(g), pp, x, y, px, py, pz, vx, vy, vz, vx_old, vy_old, vz_old, spi, spp, n, \
+            (const C*)fields4, (const C*)fz, diag, err);
+    switch (p) {
+        case 2: GPIC_GP3(2) break;
+        case 3: GPIC_GP3(3) break;
+        case 4: GPIC_GP3(4) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPIC_GP3
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init_particles3(int p, const ParticleGeom& g, const PushParams& pp, T* x, T* y,
+                                   T* px, T* py, T* pz, const T* vx, const T* vy, const T* vz,
+                                   T* vx_old, T* vy_old, T* vz_old, const int32_t* sp,
+                                   const SpeciesParams& spp, int64_t n, const void* e2,
+                                   unsigned int* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int32_t* spi = spp.n > 0 ? sp : nullptr;
+    GPIC_DISPATCH_P(p, k_init_particles3, g, pp, x, y, px, py, pz, vx, vy, vz, vx_old, vy_old,
+                    vz_old, spi, spp, n, (const cplx_t<T>*)e2, err)
     return cudaGetLastError();
 }
 
@@ -854,10 +1153,27 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
 #define GPIC_INST(T)                                                                            \
     template cudaError_t launch_move_deposit<T>(int, const ParticleGeom&, T*, T*, const T*,     \
                                                 const T*, int64_t, double2*, unsigned int*,     \
-                                                cudaStream_t);                                  \
+                                                cudaStream_t, const int32_t*,                   \
+                                                const SpeciesParams*);                          \
     template cudaError_t launch_deposit_charge<T>(int, const ParticleGeom&, const T*, const T*, \
                                                   int64_t, double2*, unsigned int*,             \
-                                                  cudaStream_t);                                \
+                                                  cudaStream_t, const int32_t*,                 \
+                                                  const SpeciesParams*);                        \
+    template cudaError_t launch_deposit_z<T>(int, const ParticleGeom&, const T*, const T*,      \
+                                             const T*, int64_t, const int32_t*,                 \
+                                             const SpeciesParams&, void*, bool, float,          \
+                                             unsigned int*, cudaStream_t);                      \
+    template cudaError_t launch_gather_push3<T>(int, const ParticleGeom&, const PushParams&,    \
+                                                const T*, const T*, T*, T*, const T*, const T*, \
+                                                const T*, const T*, T*, T*, T*, const int32_t*, \
+                                                const SpeciesParams&, int64_t, const void*,     \
+                                                const void*, double*, unsigned int*,            \
+                                                cudaStream_t);                                  \
+    template cudaError_t launch_init_particles3<T>(int, const ParticleGeom&, const PushParams&, \
+                                                   T*, T*, T*, T*, T*, const T*, const T*,      \
+                                                   const T*, T*, T*, T*, const int32_t*,        \
+                                                   const SpeciesParams&, int64_t, const void*,  \
+                                                   unsigned int*, cudaStream_t);                \
     template cudaError_t launch_gather_push<T>(int, const ParticleGeom&, const PushParams&,     \
                                                const T*, const T*, T*, T*, const T*, const T*,  \
                                                T*, T*, int64_t, const void*, double*, double*,  \
@@ -873,10 +1189,12 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
     template cudaError_t launch_wrap_positions<T>(T*, T*, int64_t, double, double, cudaStream_t); \
     template cudaError_t launch_move_deposit_fix<T>(int, const ParticleGeom&, T*, T*, const T*,   \
                                                     const T*, int64_t, longlong2*, float,         \
-                                                    unsigned int*, cudaStream_t);                 \
+                                                    unsigned int*, cudaStream_t, const int32_t*,  \
+                                                    const SpeciesParams*);                        \
     template cudaError_t launch_deposit_charge_fix<T>(int, const ParticleGeom&, const T*,         \
                                                       const T*, int64_t, longlong2*, float,       \
-                                                      unsigned int*, cudaStream_t);               \
+                                                      unsigned int*, cudaStream_t,                \
+                                                      const int32_t*, const SpeciesParams*);      \
     template cudaError_t launch_fix_to_cplx<T>(const longlong2*, double, void*, int64_t,          \
                                                cudaStream_t);                                     \
     template cudaError_t launch_move_deposit_tiled<T>(int, const ParticleGeom&, const TileGeom&,  \

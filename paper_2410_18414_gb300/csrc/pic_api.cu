@@ -102,8 +102,20 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 pic_status validate(const pic_config* c, const pic_particles_in* in) {
     pic_handle* h = nullptr;
     if (!c || !in) return fail(h, PIC_ERR_INVALID_ARG, "cfg and init must not be NULL");
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c->reserved[i] != 0) return fail(h, PIC_ERR_INVALID_ARG, "reserved fields must be 0");
+    if (c->vdim != 0 && c->vdim != 2 && c->vdim != 3)
+        return fail(h, PIC_ERR_INVALID_ARG, "vdim must be 0, 2 or 3");
+    if (c->nspecies < 0 || c->nspecies > kMaxSpecies)
+        return fail(h, PIC_ERR_INVALID_ARG, "nspecies must be 0..%d", kMaxSpecies);
+    for (int i = 0; i < c->nspecies; ++i)
+        if (!std::isfinite(c->species_q[i]) || !finite_pos(c->species_m[i]) ||
+            !std::isfinite(c->species_w[i]) || c->species_w[i] < 0)
+            return fail(h, PIC_ERR_INVALID_ARG,
+                        "species %d: q finite, m finite and > 0, weight finite and >= 0", i);
+    if ((c->vdim == 3 || c->nspecies > 0) && c->sort_interval > 0)
+        return fail(h, PIC_ERR_UNSUPPORTED,
+                    "2D-3V and species tables run on the unsorted kernels (sort_interval 0)");
     if (c->charge != PIC_CHARGE_CONTINUITY && c->charge != PIC_CHARGE_DEPOSIT)
         return fail(h, PIC_ERR_INVALID_ARG, "unknown charge source %d", c->charge);
     if (c->charge == PIC_CHARGE_DEPOSIT &&
@@ -157,6 +169,10 @@ pic_status validate(const pic_config* c, const pic_particles_in* in) {
         return fail(h, PIC_ERR_INVALID_ARG, "particle count must be 0..2^31-1");
     if (in->n > 0 && (!in->x || !in->y || !in->vx || !in->vy))
         return fail(h, PIC_ERR_INVALID_ARG, "particle arrays must not be NULL");
+    if (in->n > 0 && c->vdim == 3 && !in->vz)
+        return fail(h, PIC_ERR_INVALID_ARG, "vdim 3 needs the z velocities");
+    if (in->n > 0 && c->nspecies > 0 && !in->species)
+        return fail(h, PIC_ERR_INVALID_ARG, "a species table needs each particle's species");
     return PIC_OK;
 }
 
@@ -183,8 +199,9 @@ void free_all(pic_handle* h) {
     h->allocs.clear();
 }
 
-// Newest spectral level: 0 phi, 1 Ax, 2 Ay, 3 rho.
+// Newest spectral level: 0 phi, 1 Ax, 2 Ay, 3 rho, 4 Az (2D-3V).
 void* newest(pic_handle* h, int which) {
+    if (which == 4) return h->cfg.stepper == PIC_STEPPER_BDF ? h->az_l[h->head] : h->az;
     switch (h->cfg.stepper) {
         case PIC_STEPPER_BDF:
             if (which == 3) return h->rho_l[h->head_r];
@@ -223,6 +240,17 @@ pic_status alloc_state(pic_handle* h) {
         CK(dalloc(h, (void**)&h->bsum, sort_scan_chunks(h->tg.nkeys()) * sizeof(int)));
         CK(launch_iota(h->id, h->n, h->s));
     }
+    if (h->vdim == 3) {
+        CK(dalloc(h, &h->pz, pn));
+        CK(dalloc(h, &h->vz[0], pn));
+        CK(dalloc(h, &h->vz[1], pn));
+        CK(dalloc(h, &h->Jz, h->ng * sizeof(double2)));
+        CK(dalloc(h, &h->Zz, h->ng * cs));
+        CK(dalloc(h, &h->F2, 2 * h->ng * cs));
+        CK(dalloc(h, &h->Gz, 2 * h->ng * cs));
+    }
+    if (h->spp.n > 0)
+        CK(dalloc(h, (void**)&h->species, (size_t)std::max<int64_t>(h->n, 1) * sizeof(int32_t)));
     CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
     if (h->fp32) {
         CK(dalloc(h, (void**)&h->Jalt, h->ng * sizeof(double2)));
@@ -276,6 +304,10 @@ pic_status alloc_state(pic_handle* h) {
             CK(spec(&h->ay_l[i]));
         }
         for (int i = 0; i < h->Lr; ++i) CK(spec(&h->rho_l[i]));
+        if (h->vdim == 3) {
+            h->az_l.assign(h->L, nullptr);
+            for (int i = 0; i < h->L; ++i) CK(spec(&h->az_l[i]));
+        }
         // BDF-k with a_0 = 1 (section 3.2) from sum_{j=1..k} (1/j) nabla^j u = dt u'.
         double alpha[kMaxBdf + 1] = {0};
         for (int j = 1; j <= k; ++j) {
@@ -302,10 +334,14 @@ pic_status alloc_state(pic_handle* h) {
                           &h->cdf.ax,  &h->cdf.ax_prev,  &h->cdf.ay,  &h->cdf.ay_prev,
                           &h->cdf.jx,  &h->cdf.jx_prev,  &h->cdf.jy,  &h->cdf.jy_prev};
         for (void** sl : slots) CK(spec(sl));
+        if (h->vdim == 3)
+            for (void** sl : {&h->az, &h->az_prev, &h->jz, &h->jz_prev}) CK(spec(sl));
     } else {
         void** slots[] = {&h->dirk.phi, &h->dirk.vphi, &h->dirk.ax, &h->dirk.vax, &h->dirk.ay,
                           &h->dirk.vay, &h->dirk.rho,  &h->dirk.jx, &h->dirk.jy};
         for (void** sl : slots) CK(spec(sl));
+        if (h->vdim == 3)
+            for (void** sl : {&h->az, &h->vaz, &h->jz}) CK(spec(sl));
         const int s = c.dirk_stages;
         h->dirk.s = s;
         double r0 = 0, r1 = 0;
@@ -341,9 +377,14 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
 
     const int64_t n = h->n;
     const size_t nb64 = (size_t)n * sizeof(double);
-    const double* src[4] = {in->x, in->y, in->vx, in->vy};
-    void* dst[4] = {h->x, h->y, h->v[0][0], h->v[0][1]};
-    for (int i = 0; i < 4 && n > 0; ++i) {
+    const double* src[5] = {in->x, in->y, in->vx, in->vy, in->vz};
+    void* dst[5] = {h->x, h->y, h->v[0][0], h->v[0][1], h->vz[0]};
+    const int narr = h->vdim == 3 ? 5 : 4;
+    if (h->spp.n > 0 && n > 0)
+        CK(cudaMemcpyAsync(h->species, in->species, (size_t)n * sizeof(int32_t), cudaMemcpyDefault,
+                           h->s));
+    const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
+    for (int i = 0; i < narr && n > 0; ++i) {
         if (h->fp32) {
             CK(cudaMemcpyAsync(h->stage, src[i], nb64, cudaMemcpyDefault, h->s));
             CK(launch_convert<double, float>(h->stage, (float*)dst[i], n, h->s));
@@ -361,14 +402,15 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
         if (r != cudaSuccess) return r;
         if (h->fp32) {
             r = launch_deposit_charge_fix<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n,
-                                             (longlong2*)h->J, h->fix_scale_q, h->err, h->s);
+                                             (longlong2*)h->J, h->fix_scale_q, h->err, h->s, sp,
+                                             &h->spp);
             if (r != cudaSuccess) return r;
             r = launch_fix_to_cplx<T>((const longlong2*)h->J, h->fix_unscale_q, h->tmp, h->ng, h->s);
             if (r != cudaSuccess) return r;
             r = forward_fft(h, h->tmp, h->Z);
         } else {
             r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n, h->J,
-                                         h->err, h->s);
+                                         h->err, h->s, sp, &h->spp);
             if (r != cudaSuccess) return r;
             r = forward_fft(h, h->J, h->Z);
         }
@@ -377,6 +419,12 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
         if (r != cudaSuccess) return r;
         r = inverse_fft(h, h->F4, h->tmp, 1);  // grid (Ex, Ey) at t = 0
         if (r != cudaSuccess) return r;
+        if (h->vdim == 3 || h->spp.n > 0)
+            return launch_init_particles3<T>(h->p, h->geom, h->push, (T*)h->x, (T*)h->y,
+                                             (T*)h->px, (T*)h->py, (T*)h->pz, (const T*)h->v[0][0],
+                                             (const T*)h->v[0][1], (const T*)h->vz[0],
+                                             (T*)h->v[1][0], (T*)h->v[1][1], (T*)h->vz[1], sp,
+                                             h->spp, n, h->tmp, h->err, h->s);
         return launch_init_particles<T>(h->p, h->geom, h->push, (T*)h->x, (T*)h->y, (T*)h->px,
                                         (T*)h->py, (const T*)h->v[0][0], (const T*)h->v[0][1],
                                         (T*)h->v[1][0], (T*)h->v[1][1], n, h->tmp, h->err, h->s);
@@ -458,6 +506,22 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
     h->mc.kx_scale = 2.0 * M_PI / cfg->lx;
     h->mc.ky_scale = 2.0 * M_PI / cfg->ly;
     h->mc.jscale = cfg->weight * cfg->q / (dx * dy);
+    h->vdim = cfg->vdim == 3 ? 3 : 2;
+    double rmax = 1.0;  // bound on a deposit factor: 1, or max |q_s w_s| of a species table
+    if (cfg->nspecies > 0) {
+        // the deposits multiply each contribution by q_s w_s; the grid scale is 1/(dx dy)
+        h->spp.n = cfg->nspecies;
+        rmax = 0.0;
+        for (int i = 0; i < cfg->nspecies; ++i) {
+            h->spp.q[i] = cfg->species_q[i];
+            h->spp.m[i] = cfg->species_m[i];
+            h->spp.w[i] = cfg->species_w[i];
+            h->spp.qw[i] = cfg->species_q[i] * cfg->species_w[i];
+            rmax = std::max(rmax, std::fabs(h->spp.qw[i]));
+        }
+        if (!(rmax > 0.0)) rmax = 1.0;
+        h->mc.jscale = 1.0 / (dx * dy);
+    }
     h->mc.inv_n = 1.0 / (double)h->ng;
     h->mc.eps0 = cfg->eps0;
     h->mc.mu0 = 1.0 / (cfg->eps0 * cfg->c * cfg->c);
@@ -506,13 +570,15 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         // FP32 rounding of a contribution.
         int kj = 38;
         if (h->n > 1) kj = std::min(38, 62 - (int)std::ceil(std::log2((double)h->n)));
-        const int kc = (int)std::ceil(std::log2(cfg->c));
+        // (with a species table the bound is c max |q_s w_s|: the quantum scales with it)
+        const int kc = (int)std::ceil(std::log2(cfg->c)) + (int)std::ceil(std::log2(rmax));
         h->fix_scale_j = (float)std::ldexp(1.0, kj - kc);
         h->fix_unscale_j = 1.0 / (double)h->fix_scale_j;
-        // Charge at t = 0 (only the untiled pass): W_x W_y <= 1 with 2^k quanta,
-        // k = 62 - ceil(log2 n), so no node total can reach 2^62.
+        // Charge at t = 0 (only the untiled pass): W_x W_y <= 1 (times max |q_s w_s|) with
+        // 2^k quanta, k = 62 - ceil(log2 n), so no node total can reach 2^62.
         int k = 46;
         if (h->n > 1) k = std::min(46, 62 - (int)std::ceil(std::log2((double)h->n)));
+        k -= (int)std::ceil(std::log2(rmax));
         h->fix_scale_q = (float)std::ldexp(1.0, k);
         h->fix_unscale_q = std::ldexp(1.0, -k);
     }
@@ -553,14 +619,26 @@ pic_status pic_deposit(pic_handle* h) {
             return launch_move_deposit_tiled<T>(h->p, h->geom, h->tg, (T*)h->x, (T*)h->y,
                                                 h->p4, h->n, h->off, h->J, h->fp32,
                                                 h->fix_scale_j, h->err, h->s);
+        const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
         if (h->fp32)
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
                                               (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
-                                              h->n, (longlong2*)h->J, h->fix_scale_j, h->err, h->s);
+                                              h->n, (longlong2*)h->J, h->fix_scale_j, h->err, h->s,
+                                              sp, &h->spp);
         return launch_move_deposit<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
                                       (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1], h->n,
-                                      h->J, h->err, h->s);
+                                      h->J, h->err, h->s, sp, &h->spp);
     }));
+    if (h->vdim == 3) {  // J_z of the moved particles
+        CK(cudaMemsetAsync(h->Jz, 0, h->ng * sizeof(double2), h->s));
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_deposit_z<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y,
+                                       (const T*)h->vz[h->vcur], h->n, h->species, h->spp, h->Jz,
+                                       h->fp32, h->fix_scale_j, h->err, h->s);
+        }));
+        h->launches_now += 1;
+    }
     h->phase = 1;
     return PIC_OK;
 }
@@ -588,6 +666,7 @@ pic_status pic_field_solve(pic_handle* h) {
 
     // the naive update takes rho^{n+1} from the charge deposited at x^{n+1}, transformed
     // like the t = 0 charge
+    const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
     if (h->cfg.charge == PIC_CHARGE_DEPOSIT) {
         CK(cudaMemsetAsync(h->rhoq, 0, h->ng * sizeof(double2), h->s));
         CK(by_prec(h, [&](auto t) -> cudaError_t {
@@ -596,14 +675,14 @@ pic_status pic_field_solve(pic_handle* h) {
             if (h->fp32) {
                 r = launch_deposit_charge_fix<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y,
                                                  h->n, (longlong2*)h->rhoq, h->fix_scale_q,
-                                                 h->err, h->s);
+                                                 h->err, h->s, sp, &h->spp);
                 if (r == cudaSuccess)
                     r = launch_fix_to_cplx<T>((const longlong2*)h->rhoq, h->fix_unscale_q, h->tmp,
                                               h->ng, h->s);
                 return r == cudaSuccess ? forward_fft(h, h->tmp, h->ZQ) : r;
             }
             r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, h->n,
-                                         (double2*)h->rhoq, h->err, h->s);
+                                         (double2*)h->rhoq, h->err, h->s, sp, &h->spp);
             return r == cudaSuccess ? forward_fft(h, h->rhoq, h->ZQ) : r;
         }));
     }
@@ -611,6 +690,7 @@ pic_status pic_field_solve(pic_handle* h) {
     // per-mode update with the stepper's history levels
     const int st = h->cfg.stepper;
     BdfParams bp = h->bdf;
+    ZParams zp{};
     int nslot = 0, nr = 0;
     if (st == PIC_STEPPER_BDF) {
         const int k = bp.k;
@@ -619,6 +699,7 @@ pic_status pic_field_solve(pic_handle* h) {
             bp.phi[d - 1] = h->phi_l[slot];
             bp.ax[d - 1] = h->ax_l[slot];
             bp.ay[d - 1] = h->ay_l[slot];
+            if (h->vdim == 3) zp.az[d - 1] = h->az_l[slot];
         }
         for (int d = 1; d <= k; ++d) bp.rho[d - 1] = h->rho_l[((h->head_r - (d - 1)) % h->Lr + h->Lr) % h->Lr];
         nslot = (h->head + 1) % h->L;
@@ -627,8 +708,16 @@ pic_status pic_field_solve(pic_handle* h) {
         bp.ax_new = h->ax_l[nslot];
         bp.ay_new = h->ay_l[nslot];
         bp.rho_new = h->rho_l[nr];
+        if (h->vdim == 3) zp.az_new = h->az_l[nslot];
     }
     const int kind = st == PIC_STEPPER_BDF ? K_BDF : (st == PIC_STEPPER_CDF2 ? K_CDF2 : K_DIRK);
+    zp.kind = kind;
+    zp.form = h->cdf.form;
+    zp.az_n = h->az;
+    zp.az_prev = h->az_prev;
+    zp.jz_n = h->jz;
+    zp.jz_prev = h->jz_prev;
+    zp.vaz = h->vaz;
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
         if (fused)
@@ -660,6 +749,32 @@ pic_status pic_field_solve(pic_handle* h) {
         return launch_fft_y<T>(h->F4, h->G, h->nx, h->ny, 4, h->fy, h->twy, +1, 1, h->s);
     }));
     h->launches_now += fused ? 3 : 5;
+
+    // 2D-3V: A_z by the same stepper from J_z, and its gather fields (Gz)
+    if (h->vdim == 3) {
+        CK(by_prec(h, [&](auto t) -> cudaError_t {
+            using T = decltype(t);
+            cudaError_t r;
+            if (h->fp32) {
+                r = launch_fix_to_cplx<T>((const longlong2*)h->Jz, h->fix_unscale_j, h->tmp, h->ng,
+                                          h->s);
+                if (r == cudaSuccess) r = forward_fft(h, h->tmp, h->Zz);
+            } else {
+                r = forward_fft(h, h->Jz, h->Zz);  // J_z in the real parts
+            }
+            if (r != cudaSuccess) return r;
+            r = launch_zfield<T>(h->mc, bp, h->dirk, zp, h->Zz, h->F2, h->diag, h->s);
+            if (r != cudaSuccess) return r;
+            r = launch_fft_x<T>(h->F2, h->F2, h->nx, h->ny, 2, h->fx, h->twx, +1, h->s);
+            if (r != cudaSuccess) return r;
+            return launch_fft_y<T>(h->F2, h->Gz, h->nx, h->ny, 2, h->fy, h->twy, +1, 1, h->s);
+        }));
+        if (st == PIC_STEPPER_CDF2) {
+            std::swap(h->az, h->az_prev);
+            std::swap(h->jz, h->jz_prev);
+        }
+        h->launches_now += h->fp32 ? 6 : 5;
+    }
     h->phase = 2;
     return PIC_OK;
 }
@@ -678,6 +793,18 @@ pic_status pic_gather_push(pic_handle* h) {
                                     (float*)h->v[vo][0], (float*)h->v[vo][1], h->p4, h->n,
                                     h->off, h->G,
                                     h->diag, h->err, h->s));
+    } else if (h->vdim == 3 || h->spp.n > 0) {
+        TimedScope ts(h, PIC_KT_GATHER);
+        const bool z3 = h->vdim == 3;
+        CK(by_prec(h, [&](auto t) {
+            using T = decltype(t);
+            return launch_gather_push3<T>(
+                h->p, h->geom, pp, (const T*)h->x, (const T*)h->y, (T*)h->px, (T*)h->py,
+                (const T*)h->pz, (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
+                z3 ? (const T*)h->vz[h->vcur] : nullptr, (T*)h->v[vo][0], (T*)h->v[vo][1],
+                z3 ? (T*)h->vz[vo] : nullptr, h->species, h->spp, h->n, h->G, h->Gz, h->diag,
+                h->err, h->s);
+        }));
     } else {
         TimedScope ts(h, PIC_KT_GATHER);
         CK(by_prec(h, [&](auto t) {
@@ -915,8 +1042,10 @@ pic_status pic_residuals(pic_handle* h, pic_diagnostics* out) {
 
 pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
     if (!h || !dst) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
-    if (which < PIC_FIELD_JX || which > PIC_FIELD_DAYDY)
+    if (which < PIC_FIELD_JX || which > PIC_FIELD_DAZDY)
         return fail(h, PIC_ERR_INVALID_ARG, "unknown field %d", which);
+    if (which >= PIC_FIELD_JZ && h->vdim != 3)
+        return fail(h, PIC_ERR_STATE, "field %d needs 2D-3V (vdim 3)", which);
     if (!h->stepped && which != PIC_FIELD_RHO && which != PIC_FIELD_PHI)
         return fail(h, PIC_ERR_STATE, "field %d needs a completed step", which);
     if ((which == PIC_FIELD_EX || which == PIC_FIELD_EY) && !h->e_valid)
@@ -932,6 +1061,13 @@ pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
                     return launch_extract_fix((const longlong2*)h->J, which == PIC_FIELD_JY,
                                               h->fix_unscale_j * h->mc.jscale, h->tmpd, n, h->s);
                 return launch_extract<double>(h->J, 1, which == PIC_FIELD_JY, h->mc.jscale, h->tmpd, n, h->s);
+            case PIC_FIELD_JZ:
+                if (h->fp32)
+                    return launch_extract_fix((const longlong2*)h->Jz, 0,
+                                              h->fix_unscale_j * h->mc.jscale, h->tmpd, n, h->s);
+                return launch_extract<double>(h->Jz, 1, 0, h->mc.jscale, h->tmpd, n, h->s);
+            case PIC_FIELD_DAZDX: case PIC_FIELD_DAZDY:  // Gz: [node][2], (dAz/dx, dAz/dy) first
+                return launch_extract<T>(h->Gz, 2, which == PIC_FIELD_DAZDY, 1.0, h->tmpd, n, h->s);
             case PIC_FIELD_DPHIDX: case PIC_FIELD_DPHIDY: case PIC_FIELD_GAX: case PIC_FIELD_GAY:
             case PIC_FIELD_DAXDX: case PIC_FIELD_DAXDY: case PIC_FIELD_DAYDX: case PIC_FIELD_DAYDY: {
                 const int f = which - PIC_FIELD_DPHIDX;
@@ -950,6 +1086,11 @@ pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
             r = launch_mode_pack2<T>(h->mc, newest(h, 0), nullptr, 0, h->tmp, h->s);
         } else if (which == PIC_FIELD_BZ) {
             r = launch_mode_pack2<T>(h->mc, newest(h, 1), newest(h, 2), 1, h->tmp, h->s);
+        } else if (which == PIC_FIELD_AZ) {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 4), nullptr, 0, h->tmp, h->s);
+        } else if (which == PIC_FIELD_BX || which == PIC_FIELD_BY) {
+            r = launch_mode_pack2<T>(h->mc, newest(h, 4), nullptr, 2, h->tmp, h->s);
+            comp = which == PIC_FIELD_BY;
         } else {
             r = launch_mode_pack2<T>(h->mc, newest(h, 1), newest(h, 2), 0, h->tmp, h->s);
             comp = which == PIC_FIELD_AY;
@@ -994,6 +1135,32 @@ pic_status pic_read_particles(pic_handle* h, double* x, double* y, double* px, d
     return check_device_error(h);
 }
 
+pic_status pic_read_particles_z(pic_handle* h, double* pz, double* vz, double* vz_old,
+                                int32_t* species) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_read_particles_z inside a step");
+    if ((pz || vz || vz_old) && h->vdim != 3)
+        return fail(h, PIC_ERR_STATE, "no z components: the handle is 2D-2V");
+    if (species && h->spp.n == 0) return fail(h, PIC_ERR_STATE, "the handle has no species table");
+    const size_t nb = (size_t)h->n * sizeof(double);
+    const void* src[3] = {h->pz, h->vz[h->vcur], h->vz[1 - h->vcur]};
+    double* dst[3] = {pz, vz, vz_old};
+    for (int i = 0; i < 3 && h->n > 0; ++i) {
+        if (!dst[i]) continue;
+        if (h->fp32) {
+            CK(launch_convert<float, double>((const float*)src[i], h->stage, h->n, h->s));
+            CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
+            CK(cudaStreamSynchronize(h->s));  // the staging buffer is reused
+        } else {
+            CK(cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyDefault, h->s));
+        }
+    }
+    if (species && h->n > 0)
+        CK(cudaMemcpyAsync(species, h->species, (size_t)h->n * sizeof(int32_t), cudaMemcpyDefault,
+                           h->s));
+    return check_device_error(h);
+}
+
 pic_status pic_sync(pic_handle* h) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     CK(cudaStreamSynchronize(h->s));
@@ -1010,7 +1177,8 @@ int32_t pic_kernels_per_step(const pic_handle* h) {
     // kernels.  Before any step: the count of a step without a sort.
     if (!h->stepped) {
         const bool fused = field_columns_smem(h->nx, 2 * h->rsz) <= kFieldColumnsSmemMax;
-        return fused ? 5 : 7;
+        const int z = h->vdim == 3 ? (h->fp32 ? 7 : 6) : 0;  // J_z deposit and the A_z solve
+        return (fused ? 5 : 7) + z;
     }
     return h->launches_last;
 }

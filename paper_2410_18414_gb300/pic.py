@@ -31,7 +31,8 @@ FP64, FP32_FIX64 = 0, 1
 # pic_field
 FIELDS = {"jx": 0, "jy": 1, "rho": 2, "phi": 3, "ax": 4, "ay": 5, "bz": 6, "ex": 7, "ey": 8,
           "dphidx": 9, "dphidy": 10, "gax": 11, "gay": 12, "daxdx": 13, "daxdy": 14,
-          "daydx": 15, "daydy": 16}
+          "daydx": 15, "daydy": 16,
+          "jz": 17, "az": 18, "bx": 19, "by": 20, "dazdx": 21, "dazdy": 22}
 KERNEL_TIMERS = {"sort": 0, "deposit": 1, "field_solve": 2, "gather_push": 3,
                  "adj_push": 4, "adj_field": 5, "adj_deposit": 6}
 
@@ -54,13 +55,17 @@ class PicConfig(ctypes.Structure):
         ("dirk_a", ctypes.c_double * 16), ("dirk_b", ctypes.c_double * 4),
         ("dirk_c", ctypes.c_double * 4),
         ("charge", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("vdim", ctypes.c_int32), ("nspecies", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
+        ("species_q", ctypes.c_double * 4), ("species_m", ctypes.c_double * 4),
+        ("species_w", ctypes.c_double * 4),
     ]
 
 
 class PicParticlesIn(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("vx", ctypes.c_void_p),
-                ("vy", ctypes.c_void_p), ("n", ctypes.c_int64)]
+                ("vy", ctypes.c_void_p), ("n", ctypes.c_int64), ("vz", ctypes.c_void_p),
+                ("species", ctypes.c_void_p)]
 
 
 class PicDiagnostics(ctypes.Structure):
@@ -98,6 +103,7 @@ def load_library(path=LIB_PATH):
         "pic_residuals": ([vp, ctypes.POINTER(PicDiagnostics)], i32),
         "pic_get_field": ([vp, i32, vp], i32),
         "pic_read_particles": ([vp] + [vp] * 8, i32),
+        "pic_read_particles_z": ([vp] + [vp] * 4, i32),
         "pic_sync": ([vp], i32),
         "pic_step_count": ([vp], i64),
         "pic_kernels_per_step": ([vp], i32),
@@ -124,18 +130,18 @@ def load_library(path=LIB_PATH):
     return lib
 
 
-def _ptr(a):
-    """Raw address of a numpy array or torch tensor (contiguous float64)."""
+def _ptr(a, kind="float64"):
+    """Raw address of a numpy array or torch tensor (contiguous float64, or int32)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError("arrays must be contiguous float64")
+        if a.dtype != np.dtype(kind) or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"arrays must be contiguous {kind}")
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
         import torch
-        if a.dtype != torch.float64 or not a.is_contiguous():
-            raise TypeError("tensors must be contiguous float64")
+        if a.dtype != getattr(torch, kind) or not a.is_contiguous():
+            raise TypeError(f"tensors must be contiguous {kind}")
         return a.data_ptr()
     raise TypeError(f"unsupported array type {type(a)}")
 
@@ -145,7 +151,9 @@ CHARGE_CONTINUITY, CHARGE_DEPOSIT = 0, 1
 
 def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, c=1.0, eps0=1.0,
                 q=-1.0, m=1.0, weight=1.0, precision=FP64, sort_interval=0,
-                charge=CHARGE_CONTINUITY):
+                charge=CHARGE_CONTINUITY, vdim=2, species=None):
+    """species: optional ((q, m, w), ...) per species (at most 4); particles then carry a
+    species index (Simulation(..., species=...))."""
     cfg = PicConfig()
     cfg.nx, cfg.ny, cfg.lx, cfg.ly, cfg.dt = nx, ny, lx, ly, dt
     cfg.spline_order = p
@@ -155,6 +163,11 @@ def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, 
     cfg.precision = precision
     cfg.sort_interval = sort_interval
     cfg.charge = charge
+    cfg.vdim = vdim
+    if species is not None:
+        cfg.nspecies = len(species)
+        for i, (qs, ms, ws) in enumerate(species):
+            cfg.species_q[i], cfg.species_m[i], cfg.species_w[i] = qs, ms, ws
     if dirk is not None:
         s = len(dirk["b"])
         cfg.dirk_stages = s
@@ -169,12 +182,15 @@ def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, 
 class Simulation:
     """One simulation handle of libgpic (owns its device memory until close())."""
 
-    def __init__(self, cfg, x, y, vx, vy, stream=None):
+    def __init__(self, cfg, x, y, vx, vy, stream=None, vz=None, species=None):
+        """vz: z velocities (2D-3V, cfg.vdim = 3); species: int32 species indices (a config
+        with a species table)."""
         self.lib = load_library()
         self.cfg = cfg
         self.n = len(x)
-        self._keep = (x, y, vx, vy)
-        init = PicParticlesIn(_ptr(x), _ptr(y), _ptr(vx), _ptr(vy), self.n)
+        self._keep = (x, y, vx, vy, vz, species)
+        init = PicParticlesIn(_ptr(x), _ptr(y), _ptr(vx), _ptr(vy), self.n, _ptr(vz),
+                              _ptr(species, "int32"))
         handle = ctypes.c_void_p()
         st = self.lib.pic_init(ctypes.byref(cfg), ctypes.byref(init),
                                ctypes.c_void_p(stream or 0), ctypes.byref(handle))
@@ -214,12 +230,27 @@ class Simulation:
         return out
 
     def particles(self, out=None):
-        """Dict of the eight particle arrays (x, y, px, py, vx, vy, vx_old, vy_old), FP64."""
+        """Dict of the eight particle arrays (x, y, px, py, vx, vy, vx_old, vy_old), FP64;
+        in 2D-3V also pz, vz, vz_old, and with a species table the species indices."""
         names = ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old")
         if out is None:
             out = {k: np.empty(self.n, dtype=np.float64) for k in names}
         ptrs = [ctypes.c_void_p(_ptr(out[k])) if out.get(k) is not None else None for k in names]
         self._check(self.lib.pic_read_particles(self.h, *ptrs))
+        three = self.cfg.vdim == 3
+        table = self.cfg.nspecies > 0
+        if three or table:
+            z = {}
+            if three:
+                z = {k: out.get(k, np.empty(self.n, dtype=np.float64))
+                     for k in ("pz", "vz", "vz_old")}
+            if table:
+                z["species"] = out.get("species", np.empty(self.n, dtype=np.int32))
+            ptrs = [ctypes.c_void_p(_ptr(z[k])) if k in z else None
+                    for k in ("pz", "vz", "vz_old")]
+            ptrs.append(ctypes.c_void_p(_ptr(z["species"], "int32")) if table else None)
+            self._check(self.lib.pic_read_particles_z(self.h, *ptrs))
+            out.update(z)
         return out
 
     def sync(self):

@@ -134,3 +134,46 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pic_adjoint_checkpoint_every(None) == 0
     lib.pic_adjoint_destroy(None)
     lib.pic_destroy(None)
+
+
+def test_3v_and_species_configs_are_validated_without_a_device(lib):
+    x = np.zeros(4)
+    sp = np.zeros(4, dtype=np.int32)
+
+    def status(cfg, **kw):
+        with pytest.raises(pic.PicError) as e:
+            pic.Simulation(cfg, x, x, x, x, **kw)
+        return e.value.status
+
+    base = dict(nx=16, ny=16, lx=1.0, ly=1.0, dt=0.01, p=2, stepper="bdf", bdf_order=2)
+    assert status(pic.make_config(**base, vdim=4)) == 1
+    assert status(pic.make_config(**base, vdim=3)) == 1                  # no z velocities
+    assert status(pic.make_config(**base, species=((-1.0, 1.0, 1.0),))) == 1   # no indices
+    assert status(pic.make_config(**base, species=((-1.0, 0.0, 1.0),)), species=sp) == 1
+    assert status(pic.make_config(**base, species=((-1.0, 1.0, -1.0),)), species=sp) == 1
+    cfg = pic.make_config(**base)
+    cfg.nspecies = 5
+    assert status(cfg) == 1
+    assert status(pic.make_config(**base, vdim=3, sort_interval=4), vz=x) == 2
+    assert status(pic.make_config(**base, species=((-1.0, 1.0, 1.0),), sort_interval=4),
+                  species=sp) == 2
+
+
+def test_new_struct_fields_match_header(tmp_path):
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout2.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
+        "int main(){printf(\"%zu %zu %zu %zu %zu %zu\\n\", offsetof(pic_config, vdim),"
+        " offsetof(pic_config, nspecies), offsetof(pic_config, species_q),"
+        " offsetof(pic_config, species_w), offsetof(pic_particles_in, vz),"
+        " offsetof(pic_particles_in, species));return 0;}\n")
+    exe = tmp_path / "layout2"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    c_vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                             check=True).stdout.split()]
+    assert c_vals == [pic.PicConfig.vdim.offset, pic.PicConfig.nspecies.offset,
+                      pic.PicConfig.species_q.offset, pic.PicConfig.species_w.offset,
+                      pic.PicParticlesIn.vz.offset, pic.PicParticlesIn.species.offset]

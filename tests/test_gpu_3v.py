@@ -1,0 +1,169 @@
+"""GPU checks of the 2D-3V path (vdim 3: P_z, v_z, J_z, A_z) and of species tables.
+
+- FP64 against the oracle (oracle.pic with vdim = 3 and a species table, pinned in
+  tests/test_oracle_3v.py) after 10 steps: electrons and ions of mass 4, random species
+  and z velocities, BDF-2, CDF-2 and DIRK-2 (Qin-Zhang), and 2D-2V with the table.
+  Every particle array and grid field, relative L2, bound 1e-12 (the FP64 parity bound).
+- The FP32 form (unsorted) against the FP64 path after 5 steps (48 x 48, 20,000
+  particles): measured on GB300 <= 8.6e-8 on particle arrays and <= 2.9e-6 on fields
+  (J_x, J_y, J_z 2.9e-6; rho 1.6e-6; A_z and its gradient 1.7e-6); bounds 1e-6 and 3e-5.
+- P_z is never updated (d/dz = 0): bit for bit its t = 0 value.  Gauge and continuity
+  residuals stay at roundoff.  The diagnostics' W_B, W_E (with B_x, B_y and E_z) and the
+  per-species kinetic energy equal the oracle's energies.
+- Sorting with 2D-3V or a species table is PIC_ERR_UNSUPPORTED.
+"""
+import numpy as np
+import pytest
+
+from oracle import pic as opic
+from oracle import steppers as osteps
+from paper_2410_18414_gb300 import pic
+
+pytestmark = pytest.mark.gpu
+
+SPECIES = ((-1.0, 1.0, 1.0), (1.0, 4.0, 1.0))   # weights scaled per case below
+PARTICLE_KEYS = ("px", "py", "vx", "vy", "vx_old", "vy_old")
+Z_KEYS = ("pz", "vz", "vz_old")
+FIELDS = ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "dphidx", "dphidy", "daxdx", "daydy")
+Z_FIELDS = ("jz", "az", "bx", "by", "dazdx", "dazdy")
+
+
+@pytest.fixture(scope="module")
+def device():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def wrapped_rel(a, b, length):
+    d = np.mod(a - b + 0.5 * length, length) - 0.5 * length
+    return float(np.linalg.norm(d) / np.linalg.norm(b))
+
+
+def _case(n=3000, seed=1, nx=32, ny=24):
+    rng = np.random.default_rng(seed)
+    lx, ly = 1.0, 0.75
+    x = rng.uniform(0, lx, n)
+    y = rng.uniform(0, ly, n)
+    vx = 0.1 * rng.standard_normal(n)
+    vy = 0.1 * rng.standard_normal(n)
+    vz = 0.2 * rng.standard_normal(n)
+    sp = rng.integers(0, 2, n).astype(np.int32)
+    w = lx * ly / n
+    species = tuple((q, m, 2 * w) for q, m, _ in SPECIES)
+    return dict(nx=nx, ny=ny, lx=lx, ly=ly, dt=0.4 * lx / nx, x=x, y=y, vx=vx, vy=vy, vz=vz,
+                sp=sp, species=species)
+
+
+STEPPERS = [("bdf", dict(bdf_order=2), {}), ("cdf2", {}, {}),
+            ("dirk", dict(dirk=osteps.DIRK2_QIN_ZHANG), dict(dirk=osteps.DIRK2_QIN_ZHANG))]
+
+
+def _gpu(device, c, stepper, kw, vdim=3, precision=pic.FP64, p=3, sort=0):
+    cfg = pic.make_config(c["nx"], c["ny"], c["lx"], c["ly"], c["dt"], p=p, stepper=stepper,
+                          precision=precision, vdim=vdim, species=c["species"],
+                          sort_interval=sort, **kw)
+    return pic.Simulation(cfg, c["x"], c["y"], c["vx"], c["vy"], stream=device,
+                          vz=c["vz"] if vdim == 3 else None, species=c["sp"])
+
+
+def _oracle(c, stepper, okw, vdim=3, p=3, nsteps=10):
+    ocfg = opic.Config(nx=c["nx"], ny=c["ny"], lx=c["lx"], ly=c["ly"], dt=c["dt"], p=p,
+                       stepper=stepper, vdim=vdim, species=c["species"], **okw)
+    return ocfg, opic.run(ocfg, c["x"], c["y"], c["vx"], c["vy"], nsteps,
+                          vz0=c["vz"] if vdim == 3 else None, species=c["sp"])
+
+
+@pytest.mark.parametrize("stepper,kw,okw", STEPPERS, ids=["bdf2", "cdf2", "dirk2"])
+def test_3v_species_fp64_matches_oracle(device, stepper, kw, okw):
+    c = _case()
+    okw = dict(okw, bdf_order=kw.get("bdf_order", 1))
+    _, st = _oracle(c, stepper, okw)
+    with _gpu(device, c, stepper, kw) as sim:
+        sim.step(10)
+        got = sim.particles()
+        fields = {f: sim.field(f) for f in FIELDS + Z_FIELDS}
+    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"])}
+    for k in PARTICLE_KEYS + Z_KEYS:
+        errs[k] = rel(got[k], getattr(st, k))
+    for f in FIELDS + Z_FIELDS:
+        errs[f] = rel(fields[f], st.grids[f])
+    assert np.array_equal(got["species"], c["sp"])
+    bad = {k: v for k, v in errs.items() if not v <= 1e-12}
+    assert not bad, bad
+
+
+def test_2v_species_fp64_matches_oracle(device):
+    c = _case(seed=2)
+    _, st = _oracle(c, "bdf", dict(bdf_order=2), vdim=2, p=2)
+    with _gpu(device, c, "bdf", dict(bdf_order=2), vdim=2, p=2) as sim:
+        sim.step(10)
+        got = sim.particles()
+        fields = {f: sim.field(f) for f in FIELDS}
+        with pytest.raises(pic.PicError) as e:
+            sim.field("az")
+        assert e.value.status == 7
+    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"])}
+    for k in PARTICLE_KEYS:
+        errs[k] = rel(got[k], getattr(st, k))
+    for f in FIELDS:
+        errs[f] = rel(fields[f], st.grids[f])
+    bad = {k: v for k, v in errs.items() if not v <= 1e-12}
+    assert not bad, bad
+
+
+def test_3v_fp32_form_against_fp64(device):
+    c = _case(n=20000, seed=3, nx=48, ny=48)
+    out = {}
+    for prec in (pic.FP64, pic.FP32_FIX64):
+        with _gpu(device, c, "bdf", dict(bdf_order=2), precision=prec) as sim:
+            sim.step(5)
+            out[prec] = (sim.particles(), {f: sim.field(f) for f in FIELDS + Z_FIELDS})
+    (a64, f64), (a32, f32) = out[pic.FP64], out[pic.FP32_FIX64]
+    errs = {"x": wrapped_rel(a32["x"], a64["x"], c["lx"])}
+    for k in PARTICLE_KEYS + Z_KEYS:
+        errs[k] = rel(a32[k], a64[k])
+    bad = {k: v for k, v in errs.items() if not v <= 1e-6}
+    for f in FIELDS + Z_FIELDS:
+        errs[f] = rel(f32[f], f64[f])
+        if not errs[f] <= 3e-5:
+            bad[f] = errs[f]
+    print("FP32 form vs FP64, 2D-3V with species:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("stepper,kw,okw", STEPPERS, ids=["bdf2", "cdf2", "dirk2"])
+def test_3v_pz_constant_residuals_and_energies(device, stepper, kw, okw):
+    c = _case(seed=4)
+    okw = dict(okw, bdf_order=kw.get("bdf_order", 1))
+    ocfg, st = _oracle(c, stepper, okw, nsteps=6)
+    with _gpu(device, c, stepper, kw) as sim:
+        pz0 = sim.particles()["pz"].copy()
+        sim.set_diagnostics(1)
+        sim.step(6)
+        d = sim.residuals()
+        assert np.array_equal(sim.particles()["pz"], pz0)
+    assert d["gauge_rms"] <= 1e-11 * d["div_a_rms"], d
+    assert d["continuity_rms"] <= 1e-11 * d["rho_rms"] / c["dt"], d
+    e = opic.energies(ocfg, st)
+    for k, ko in (("w_b", "wb"), ("w_e", "we"), ("kinetic", "ke")):
+        assert abs(d[k] / e[ko] - 1.0) <= 1e-11, (k, d[k], e[ko])
+
+
+def test_3v_and_species_need_the_unsorted_kernels(device):
+    c = _case(n=256, seed=5)
+    for vdim in (3, 2):
+        with pytest.raises(pic.PicError) as e:
+            _gpu(device, c, "bdf", dict(bdf_order=2), vdim=vdim, sort=4)
+        assert e.value.status == 2
