@@ -54,6 +54,8 @@ def parse():
                     help="re-sort particles by tile every this many steps (0 = never)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-steppers", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint timing that the default line carries")
     a = ap.parse_args()
     if a.stepper is None:
         a.stepper = WORKLOADS[a.workload]["stepper"] if a.workload in WORKLOADS else "bdf2"
@@ -264,7 +266,7 @@ def run_oracle(workload, stepper_name, n, steps, warmup):
 
 def cpu_baseline(workload, stepper_name):
     n = 262144
-    steps = 4
+    steps = 12
     times = run_oracle(workload, stepper_name, n, steps, 1)
     v = n * len(times) / sum(times)
     w = WORKLOADS[workload]
@@ -463,25 +465,22 @@ def run_ensemble(a):
     print(json.dumps(line))
 
 
-def run_adjoint(a):
-    """Gradient of the magnetic energy W_B = 1/2 sum B_z^2 dx dy after 200 steps of the
-    128x128 Weibel run with 16 particles per cell (262,144), FP64, BDF-2, cubic, with
-    respect to every initial velocity and momentum, by the library's adjoint.  Timed per
-    whole run with CUDA events (L2 flushed between runs): the plain forward run
-    (pic_step), the recording forward run and the reverse sweep, with checkpoints every
+def adjoint_timings(steps, reps, rank=0):
+    """Gradient of the magnetic energy W_B = 1/2 sum B_z^2 dx dy after `steps` (at most 200)
+    steps of the 128x128 Weibel run with 16 particles per cell (262,144), FP64, BDF-2,
+    cubic, with respect to every initial velocity and momentum, by the library's adjoint.
+    Timed per whole run with CUDA events (L2 flushed before each run): the plain forward
+    run (pic_step), the recording forward run and the reverse sweep, with checkpoints every
     20 steps (the backward pass recomputes 9 of the 10 segments) and with every step kept
-    in HBM (6.9 GB, nothing recomputed).  value = (recording forward + reverse sweep) /
-    plain forward at K = 20."""
+    in HBM (6.9 GB, nothing recomputed); one more sweep runs under the library's adjoint
+    kernel timers."""
     import torch
     from paper_2410_18414_gb300 import pic, workloads
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     pic.load_library()
     wl = workloads.weibel_adjoint_128(seed=5 + rank)
     cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf", bdf_order=2,
                           weight=wl.weight)
-    N = min(wl.nsteps, a.steps)   # --steps shortens the run (profiling); default: all 200
+    N = min(wl.nsteps, steps)
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -515,7 +514,8 @@ def run_adjoint(a):
         sim.close()
         return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
 
-    for K in (0, min(20, N), N):      # warm-up: one of each
+    k20 = min(20, N)
+    for K in (0, k20, N):      # warm-up: one of each
         once(K)
     # one instrumented reverse sweep (every step kept): the library's per-kernel event
     # pairs around the three reverse launch groups of every step
@@ -534,36 +534,51 @@ def run_adjoint(a):
     sim.set_kernel_timing(0)
     adj.close()
     sim.close()
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start()
-    reps = max(1, a.repeats)
-    fwd = [once(0)[0] for _ in range(reps)]
-    k20 = [once(min(20, N)) for _ in range(reps)]
-    kall = [once(N) for _ in range(reps)]
-    clk = clocks.stop()
-    if rank != 0:
-        return
     med = statistics.median
-    f = med(fwd)
-    r20 = (med([t[0] for t in k20]) + med([t[1] for t in k20])) / f
-    rall = (med([t[0] for t in kall]) + med([t[1] for t in kall])) / f
-    line = {
-        "metric": "adjoint/forward time", "value": r20, "unit": "ratio", "n_gpus": world,
-        "steps": N, "warmup": 1, "repeats": reps, "ms_per_step": med([t[1] for t in k20]) / N,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "particles": wl.n,
-                   "steps_per_run": N, "objective": "W_B at the last step",
-                   "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": "fp64",
-                   "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
-        "forward_ms": f,
-        "checkpoint_20": {"record_forward_ms": med([t[0] for t in k20]),
-                          "backward_ms": med([t[1] for t in k20]), "ratio": r20},
-        "keep_all_steps": {"record_forward_ms": med([t[0] for t in kall]),
-                           "backward_ms": med([t[1] for t in kall]), "ratio": rall,
+    fwd = med([once(0)[0] for _ in range(reps)])
+    t20 = [once(k20) for _ in range(reps)]
+    tall = [once(N) for _ in range(reps)]
+    r20 = (med([t[0] for t in t20]) + med([t[1] for t in t20])) / fwd
+    rall = (med([t[0] for t in tall]) + med([t[1] for t in tall])) / fwd
+    return {
+        "workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "particles": wl.n,
+        "steps_per_run": N, "form": "fp64", "objective": "W_B at the last step",
+        "forward_ms": fwd,
+        "checkpoint_20": {"record_forward_ms": med([t[0] for t in t20]),
+                          "backward_ms": med([t[1] for t in t20]), "ratio": r20},
+        "keep_all_steps": {"record_forward_ms": med([t[0] for t in tall]),
+                           "backward_ms": med([t[1] for t in tall]), "ratio": rall,
                            "hbm_bytes": int(N * (128 * wl.n + 64 * wl.nx * wl.ny))},
         "kernels": kt,
         "roofline": adjoint_roofline(wl.p, wl.n, kt["adj_push"]["ms_per_launch"]),
+    }
+
+
+def run_adjoint(a):
+    """`--workload adjoint128`: the adjoint timings as their own line.  value = (recording
+    forward + reverse sweep) / plain forward with checkpoints every 20 steps."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    t = adjoint_timings(a.steps, max(1, a.repeats), rank)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    line = {
+        "metric": "adjoint/forward time", "value": t["checkpoint_20"]["ratio"], "unit": "ratio",
+        "n_gpus": world, "steps": t["steps_per_run"], "warmup": 1, "repeats": max(1, a.repeats),
+        "ms_per_step": t["checkpoint_20"]["backward_ms"] / t["steps_per_run"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": t["workload"], "particles": t["particles"],
+                   "steps_per_run": t["steps_per_run"], "objective": t["objective"],
+                   "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": "fp64",
+                   "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
+        "forward_ms": t["forward_ms"], "checkpoint_20": t["checkpoint_20"],
+        "keep_all_steps": t["keep_all_steps"], "kernels": t["kernels"], "roofline": t["roofline"],
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -752,6 +767,12 @@ def main():
         dist.all_reduce(ee, op=dist.ReduceOp.MAX)
         e2e["value"] = n_all * a.steps / float(ee.item())
 
+    # the adjoint (the metric's "adjoint/forward time"): the gradient of W_B on the
+    # 262,144-particle Weibel workload, FP64, one timed run per checkpoint setting
+    adjoint = None
+    if not a.no_adjoint:
+        adjoint = adjoint_timings(200, 1, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
@@ -780,6 +801,7 @@ def main():
             "by_stepper_ms_per_step": by_stepper,
             "other_form": other_form,
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches[0],
