@@ -733,6 +733,19 @@ def main():
                                "gather_push": statistics.mean(tod["push_ms"])},
                   "kernel_ms": {k: v["ms_per_launch"] for k, v in tod["kernels"].items()}}
 
+    # the same form with the residual and energy diagnostics (a10) on every step
+    sd = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+    sd.set_diagnostics(1)
+    td = time_steps(sd, max(20, a.steps // 4), 5, stream, flush)
+    diag_res = sd.residuals()
+    sd.close()
+    diag_ms = statistics.mean(td["step_ms"])
+    with_diagnostics = {"ms_per_step": diag_ms, "value": wl.n * world / (diag_ms * 1e-3),
+                        "every": 1, "steps": len(td["step_ms"]),
+                        "last_residuals": {k: diag_res[k] for k in
+                                           ("gauge_rms", "gauss_rms", "continuity_rms",
+                                            "div_a_rms", "rho_rms", "w_b", "w_e", "kinetic")}}
+
     # other steppers of the same workload (shorter runs)
     by_stepper = {a.stepper: total_ms / a.steps}
     if not a.no_extra_steppers:
@@ -801,6 +814,7 @@ def main():
             "by_stepper_ms_per_step": by_stepper,
             "other_form": other_form,
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
+            "with_diagnostics": with_diagnostics,
             "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -103,6 +103,21 @@ def weibel_512(stepper="dirk", seed=3):
     return weibel(512, 512, 100, 0.6, 0.02, seed, 4, stepper, 2, 500)
 
 
+def weibel_seeded(nx=128, ny=128, ppc=64, v_drift=0.5, u_th=0.01, seed=2, p=3, eps=1e-3,
+                  stepper="bdf", bdf_order=2, nsteps=2000, length=WEIBEL_L):
+    """The Weibel set-up with its lowest filamentation mode seeded: the two beams are
+    displaced in antiphase along x, x -> x + s (eps / k) cos(k x) for the beam moving along
+    s y (s = +-1), k = 2 pi / L, which modulates the beam densities by s eps sin(k x) to first
+    order: a current J_y ~ sin(k x) (the growing mode's B_z ~ cos(k x)) with the charge
+    density unchanged."""
+    wl = weibel(nx, ny, ppc, v_drift, u_th, seed, p, stepper, bdf_order, nsteps, length=length)
+    k = 2.0 * np.pi / length
+    s = np.where(np.arange(wl.n) % 2 == 0, 1.0, -1.0)
+    wl.x = np.mod(wl.x + s * (eps / k) * np.cos(k * wl.x), length)
+    wl.name = "weibel_seeded"
+    return wl
+
+
 def weibel_adjoint_128(seed=5):
     """128x128 Weibel, 16 per cell (262,144), v_d = 0.5c, BDF-2, cubic, 200 steps."""
     return weibel(128, 128, 16, 0.5, 0.01, seed, 3, "bdf", 2, 200)
