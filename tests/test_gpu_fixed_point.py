@@ -1,0 +1,61 @@
+"""The FP32 form's first move and fixed-point current, bit for bit against the CPU model
+oracle.fixed_point (pinned in tests/test_oracle_fixed_point.py): float32 positions after
+the move and every node of J_x, J_y (the int64 sums, read back through the library's
+scaling), for p = 2, 3, 4, unsorted (global int64 atomics) and sorted (the tiled pass:
+split 32-bit shared sums flushed into int64), on a 48 x 32 grid with a ragged particle
+count and particles that cross the periodic edges during the move."""
+import numpy as np
+import pytest
+
+from oracle import fixed_point as fx
+from paper_2410_18414_gb300 import pic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def device():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+@pytest.mark.parametrize("sort", [0, 1], ids=["unsorted", "sorted"])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_first_move_and_current_bit_exact(device, p, sort):
+    nx, ny, lx, ly = 48, 32, 1.0, 0.75
+    n = 20011
+    rng = np.random.default_rng(100 + p)
+    x = rng.uniform(0, lx, n)
+    y = rng.uniform(0, ly, n)
+    vx = rng.uniform(-0.4, 0.4, n)   # |v| < 0.73 c with the edge offsets below
+    vy = rng.uniform(-0.4, 0.4, n)
+    # a few hundred particles just inside the edges, moving across them
+    e = 300
+    x[:e] = lx - rng.uniform(0, 2e-3, e)
+    vx[:e] = np.abs(vx[:e]) + 0.2
+    y[e:2 * e] = rng.uniform(0, 2e-3, e)
+    vy[e:2 * e] = -np.abs(vy[e:2 * e]) - 0.2
+    dt = 0.4 * lx / nx
+    w, q = lx * ly / n, -1.0
+    cfg = pic.make_config(nx, ny, lx, ly, dt, p=p, stepper="bdf", bdf_order=2, weight=w, q=q,
+                          precision=pic.FP32_FIX64, sort_interval=sort)
+    with pic.Simulation(cfg, x, y, vx, vy, stream=device) as sim:
+        sim.step(1)
+        got = sim.particles()
+        jx, jy = sim.field("jx"), sim.field("jy")
+    scale = fx.current_scale(1.0, n)
+    x1, y1, ix, iy = fx.move_deposit(x, y, vx, vy, dt, lx, ly, nx, ny, p, scale)
+    assert np.array_equal(got["x"], x1.astype(np.float64))
+    assert np.array_equal(got["y"], y1.astype(np.float64))
+    dx, dy = lx / nx, ly / ny
+    out = (1.0 / scale) * (w * q / (dx * dy))    # the library's read-back factor
+    assert np.array_equal(jx, out * ix.astype(np.float64)), np.max(np.abs(jx - out * ix))
+    assert np.array_equal(jy, out * iy.astype(np.float64)), np.max(np.abs(jy - out * iy))
