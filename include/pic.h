@@ -255,6 +255,20 @@ pic_status pic_read_particles(pic_handle *h, double *x, double *y, double *px, d
 pic_status pic_read_particles_z(pic_handle *h, double *pz, double *vz, double *vz_old,
                                 int32_t *species);
 
+/* Checkpoint and resume.  pic_save_state writes the handle's state between two steps into
+ * host memory dst as one byte string: a header of the configuration and the rotation state
+ * (step count, which velocity buffer holds v^n, the BDF ring heads) followed by every device
+ * buffer a later step reads (particles, the sort's order and tile offsets, the field
+ * histories, the last step's J and gather fields).  With dst NULL it only stores the size
+ * needed in *size; with *size too small it returns PIC_ERR_INVALID_ARG and the size needed.
+ * Synchronizes.  pic_load_state restores such a string into a handle created with the same
+ * configuration and particle count (PIC_ERR_INVALID_ARG otherwise): the handle then steps
+ * exactly as the saved one would have (bit for bit in the FP32 form).  Diagnostics of the
+ * last step are not part of the state.  A handle that belongs to an ensemble or an adjoint
+ * must not be loaded into.  Both: PIC_ERR_STATE inside a step. */
+pic_status pic_save_state(pic_handle *h, void *dst, size_t *size);
+pic_status pic_load_state(pic_handle *h, const void *src, size_t size);
+
 /* Wait for all work enqueued by this handle; report latched device errors. */
 pic_status pic_sync(pic_handle *h);
 

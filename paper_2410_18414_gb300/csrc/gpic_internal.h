@@ -286,6 +286,9 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
                              int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
                              float4* p4, cudaStream_t s);
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
+// p4[p] = (x, y, vx, vy) of particle p (the packed input of the tiled deposit).
+cudaError_t launch_pack_p4(const float* x, const float* y, const float* vx, const float* vy,
+                           float4* p4, int64_t n, cudaStream_t s);
 
 // Move + deposit over tile-sorted particles: CTA b takes particles [b*chunk, (b+1)*chunk)
 // and accumulates each tile segment in shared memory.  `fix` selects the int64

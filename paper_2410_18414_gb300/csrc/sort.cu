@@ -193,6 +193,14 @@ k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ key
     }
 }
 
+__global__ void k_pack_p4(const float* __restrict__ x, const float* __restrict__ y,
+                          const float* __restrict__ vx, const float* __restrict__ vy,
+                          float4* __restrict__ p4, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        p4[p] = make_float4(x[p], y[p], vx[p], vy[p]);
+}
+
 __global__ void k_iota(int32_t* __restrict__ id, int64_t n) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -226,6 +234,13 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
         e = launch_pdl(k_sort_scatter<T>, dim3((unsigned)((n + per_cta - 1) / per_cta)),
                        dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor, p4, vidx);
     return e;
+}
+
+cudaError_t launch_pack_p4(const float* x, const float* y, const float* vx, const float* vy,
+                           float4* p4, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_pack_p4<<<blocks_for(n), kThreads, 0, s>>>(x, y, vx, vy, p4, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {

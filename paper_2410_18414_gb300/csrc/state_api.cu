@@ -1,0 +1,186 @@
+// Host side of pic_save_state / pic_load_state (include/pic.h): the handle's state between
+// two steps as one host byte string -- a header of the configuration and the rotation
+// state, then every device buffer a later step reads, in a fixed order.
+//
+// Buffers are taken by role, never by address: the CDF-2 levels by their current meaning
+// (phi^{n+1/2}, phi^{n-1/2}, ...), the BDF rings slot by slot with the head, the velocity
+// buffers by index with vcur.  Loading writes the same roles of the target handle, so the
+// target steps on exactly as the source would have.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "gpic_internal.h"
+#include "handle.h"
+#include "pic.h"
+
+using namespace gpic;
+
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, p, stepper, cdf_form, bdf_order, dirk_stages, precision;
+    int32_t sort_interval, vdim, nspecies, charge;
+    int64_t n, step;
+    int32_t vcur, head, head_r, stepped;
+    uint64_t payload;
+};
+constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '1'};
+
+struct Seg {
+    void* p;
+    size_t bytes;
+};
+
+std::vector<Seg> segments(pic_handle* h) {
+    std::vector<Seg> s;
+    const size_t pn = (size_t)h->n * h->rsz, cs = 2 * h->rsz, ng = h->ng;
+    const size_t sb = ng * sizeof(double2);  // spectral histories are FP64 in both forms
+    auto add = [&](void* p, size_t b) {
+        if (p && b) s.push_back({p, b});
+    };
+    for (void* p : {h->x, h->y, h->px, h->py, h->v[0][0], h->v[0][1], h->v[1][0], h->v[1][1]})
+        add(p, pn);
+    if (h->vdim == 3)
+        for (void* p : {h->pz, h->vz[0], h->vz[1]}) add(p, pn);
+    if (h->spp.n > 0) add(h->species, (size_t)h->n * sizeof(int32_t));
+    if (h->sorting) {
+        add(h->id, (size_t)h->n * sizeof(int32_t));
+        add(h->off, ((size_t)h->tg.nkeys() + 1) * sizeof(int));
+    }
+    add(h->J, sb);  // last step's current (double2, or longlong2 sums)
+    add(h->G, 4 * ng * cs);
+    if (h->vdim == 3) {
+        add(h->Jz, sb);
+        add(h->Gz, 2 * ng * cs);
+    }
+    switch (h->cfg.stepper) {
+        case PIC_STEPPER_BDF:
+            for (auto* l : {&h->phi_l, &h->ax_l, &h->ay_l, &h->rho_l, &h->az_l})
+                for (void* p : *l) add(p, sb);
+            break;
+        case PIC_STEPPER_CDF2:
+            for (void* p : {h->cdf.phi, h->cdf.phi_prev, h->cdf.rho, h->cdf.rho_prev, h->cdf.ax,
+                            h->cdf.ax_prev, h->cdf.ay, h->cdf.ay_prev, h->cdf.jx, h->cdf.jx_prev,
+                            h->cdf.jy, h->cdf.jy_prev, h->az, h->az_prev, h->jz, h->jz_prev})
+                add(p, sb);
+            break;
+        default:
+            for (void* p : {h->dirk.phi, h->dirk.vphi, h->dirk.ax, h->dirk.vax, h->dirk.ay,
+                            h->dirk.vay, h->dirk.rho, h->dirk.jx, h->dirk.jy, h->az, h->vaz, h->jz})
+                add(p, sb);
+    }
+    return s;
+}
+
+StateHeader header_of(pic_handle* h, uint64_t payload) {
+    StateHeader hd{};
+    std::memcpy(hd.magic, kMagic, 8);
+    const pic_config& c = h->cfg;
+    hd.nx = c.nx;
+    hd.ny = c.ny;
+    hd.p = c.spline_order;
+    hd.stepper = c.stepper;
+    hd.cdf_form = h->cdf.form;
+    hd.bdf_order = c.bdf_order;
+    hd.dirk_stages = c.dirk_stages;
+    hd.precision = c.precision;
+    hd.sort_interval = c.sort_interval;
+    hd.vdim = h->vdim;
+    hd.nspecies = h->spp.n;
+    hd.charge = c.charge;
+    hd.n = h->n;
+    hd.step = h->step;
+    hd.vcur = h->vcur;
+    hd.head = h->head;
+    hd.head_r = h->head_r;
+    hd.stepped = h->stepped ? 1 : 0;
+    hd.payload = payload;
+    return hd;
+}
+
+uint64_t payload_bytes(const std::vector<Seg>& segs) {
+    uint64_t b = 0;
+    for (const Seg& g : segs) b += g.bytes;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_save_state(pic_handle* h, void* dst, size_t* size) {
+    if (!h || !size) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_save_state inside a step");
+    const std::vector<Seg> segs = segments(h);
+    const uint64_t payload = payload_bytes(segs);
+    const size_t need = sizeof(StateHeader) + payload;
+    if (!dst) {
+        *size = need;
+        return PIC_OK;
+    }
+    if (*size < need) {
+        *size = need;
+        return fail(h, PIC_ERR_INVALID_ARG, "state buffer too small: %zu bytes needed", need);
+    }
+    const StateHeader hd = header_of(h, payload);
+    std::memcpy(dst, &hd, sizeof hd);
+    char* out = static_cast<char*>(dst) + sizeof hd;
+    for (const Seg& g : segs) {
+        CK(cudaMemcpyAsync(out, g.p, g.bytes, cudaMemcpyDefault, h->s));
+        out += g.bytes;
+    }
+    *size = need;
+    return check_device_error(h);  // synchronizes: dst is complete on return
+}
+
+pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
+    if (!h || !src) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_load_state inside a step");
+    if (size < sizeof(StateHeader)) return fail(h, PIC_ERR_INVALID_ARG, "not a saved state");
+    StateHeader hd;
+    std::memcpy(&hd, src, sizeof hd);
+    if (std::memcmp(hd.magic, kMagic, 8) != 0)
+        return fail(h, PIC_ERR_INVALID_ARG, "not a saved state of this library");
+    const std::vector<Seg> segs = segments(h);
+    const uint64_t payload = payload_bytes(segs);
+    const StateHeader mine = header_of(h, payload);
+    const bool same = hd.nx == mine.nx && hd.ny == mine.ny && hd.p == mine.p &&
+                      hd.stepper == mine.stepper && hd.cdf_form == mine.cdf_form &&
+                      hd.bdf_order == mine.bdf_order && hd.dirk_stages == mine.dirk_stages &&
+                      hd.precision == mine.precision && hd.sort_interval == mine.sort_interval &&
+                      hd.vdim == mine.vdim && hd.nspecies == mine.nspecies &&
+                      hd.charge == mine.charge && hd.n == mine.n && hd.payload == payload;
+    if (!same)
+        return fail(h, PIC_ERR_INVALID_ARG,
+                    "the saved state belongs to another configuration or particle count");
+    if (size < sizeof hd + payload) return fail(h, PIC_ERR_INVALID_ARG, "truncated state");
+    if (hd.vcur < 0 || hd.vcur > 1 || (h->L && (hd.head < 0 || hd.head >= h->L)) ||
+        (h->Lr && (hd.head_r < 0 || hd.head_r >= h->Lr)))
+        return fail(h, PIC_ERR_INVALID_ARG, "corrupt saved state");
+    const char* in = static_cast<const char*>(src) + sizeof hd;
+    for (const Seg& g : segs) {
+        CK(cudaMemcpyAsync(g.p, in, g.bytes, cudaMemcpyDefault, h->s));
+        in += g.bytes;
+    }
+    h->step = hd.step;
+    h->vcur = hd.vcur;
+    h->head = hd.head;
+    h->head_r = hd.head_r;
+    h->stepped = hd.stepped != 0;
+    h->diag_valid = h->e_valid = false;
+    if (h->fp32) {
+        // the buffer the next deposit sums into starts at zero (the row transform keeps it so)
+        CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));
+        if (h->sorting)
+            CK(launch_pack_p4((const float*)h->x, (const float*)h->y,
+                              (const float*)h->v[h->vcur][0], (const float*)h->v[h->vcur][1], h->p4,
+                              h->n, h->s));
+    }
+    CK(cudaStreamSynchronize(h->s));  // src may be released on return
+    return check_device_error(h);
+}
+
+}  // extern "C"

@@ -104,6 +104,8 @@ def load_library(path=LIB_PATH):
         "pic_get_field": ([vp, i32, vp], i32),
         "pic_read_particles": ([vp] + [vp] * 8, i32),
         "pic_read_particles_z": ([vp] + [vp] * 4, i32),
+        "pic_save_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pic_load_state": ([vp, vp, ctypes.c_size_t], i32),
         "pic_sync": ([vp], i32),
         "pic_step_count": ([vp], i64),
         "pic_kernels_per_step": ([vp], i32),
@@ -252,6 +254,19 @@ class Simulation:
             self._check(self.lib.pic_read_particles_z(self.h, *ptrs))
             out.update(z)
         return out
+
+    def save_state(self):
+        """The handle's state as bytes (pic_save_state)."""
+        size = ctypes.c_size_t(0)
+        self._check(self.lib.pic_save_state(self.h, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(self.lib.pic_save_state(self.h, buf, ctypes.byref(size)))
+        return buf.raw[:size.value]
+
+    def load_state(self, state):
+        """Restore bytes from save_state of a handle with the same configuration."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        self._check(self.lib.pic_load_state(self.h, buf, len(state)))
 
     def sync(self):
         self._check(self.lib.pic_sync(self.h))

@@ -133,6 +133,9 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pic_adjoint_backward(None, None, None, None, None, None, None, None) == 1
     assert lib.pic_adjoint_checkpoint_every(None) == 0
     lib.pic_adjoint_destroy(None)
+    size = ctypes.c_size_t(0)
+    assert lib.pic_save_state(None, None, ctypes.byref(size)) == 1
+    assert lib.pic_load_state(None, None, 0) == 1
     lib.pic_destroy(None)
 
 

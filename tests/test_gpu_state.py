@@ -1,0 +1,105 @@
+"""Checkpoint and resume (pic_save_state / pic_load_state): a handle loaded with the state
+of another steps on exactly as the other does -- bit for bit in the FP32 form, whose
+current sums are order-independent integers; to FP64 roundoff in the FP64 path, whose
+atomics sum in no fixed order.  Saved mid sort interval (the sort's order and tile
+offsets), after an odd number of CDF-2 steps (its swapped levels), with BDF rings whose
+head has moved, and in 2D-3V with species.  Loading into another configuration or from a
+truncated string is refused."""
+import numpy as np
+import pytest
+
+from oracle import steppers as osteps
+from paper_2410_18414_gb300 import pic, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def device():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(pic.LIB_PATH):
+        from paper_2410_18414_gb300 import build
+        build.build()
+    pic.load_library()
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+FIELDS = ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "dphidx", "daydy")
+
+CASES = [
+    ("fp32-bdf2-sorted", dict(stepper="bdf", bdf_order=2, precision=pic.FP32_FIX64,
+                              sort_interval=4), 2, 7),
+    ("fp32-cdf2", dict(stepper="cdf2", precision=pic.FP32_FIX64), 2, 7),
+    ("fp32-dirk2", dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG, precision=pic.FP32_FIX64),
+     2, 5),
+    ("fp32-bdf3-3v-species", dict(stepper="bdf", bdf_order=3, precision=pic.FP32_FIX64, vdim=3,
+                                  species=((-1.0, 1.0, 1.0 / 8192), (1.0, 4.0, 1.0 / 8192))),
+     3, 5),
+    ("fp64-cdf2", dict(stepper="cdf2"), 3, 5),
+]
+
+
+def _make(device, kw, seed):
+    wl = workloads.weibel(32, 32, 8, 0.5, 0.01, seed, 3, nsteps=20)
+    kw = dict(kw)
+    kw.setdefault("weight", wl.weight)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=3, **kw)
+    extra = {}
+    if kw.get("vdim") == 3:
+        extra["vz"] = np.random.default_rng(seed).uniform(-0.3, 0.3, wl.n)
+    if kw.get("species"):
+        extra["species"] = (np.arange(wl.n) % 2).astype(np.int32)
+    return pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device, **extra)
+
+
+def _snapshot(sim, three):
+    out = dict(sim.particles())
+    out.update({f: sim.field(f) for f in FIELDS + (("az", "jz") if three else ())})
+    return out
+
+
+@pytest.mark.parametrize("name,kw,before,after", CASES, ids=[c[0] for c in CASES])
+def test_resume_steps_on_like_the_source(device, name, kw, before, after):
+    three = kw.get("vdim") == 3
+    a = _make(device, kw, seed=1)
+    a.step(before * 2 + 1)
+    state = a.save_state()
+    a.step(after)
+    ref = _snapshot(a, three)
+    a.close()
+    b = _make(device, kw, seed=2)      # other particles: everything comes from the state
+    b.load_state(state)
+    assert b.step_count == before * 2 + 1
+    b.step(after)
+    got = _snapshot(b, three)
+    b.close()
+    exact = kw.get("precision") == pic.FP32_FIX64
+    for k, v in ref.items():
+        if exact:
+            assert np.array_equal(got[k], v), k
+        else:
+            err = np.linalg.norm(got[k] - v) / max(np.linalg.norm(v), 1e-300)
+            assert err <= 1e-12, (k, err)
+
+
+def test_load_refuses_other_configurations(device):
+    a = _make(device, dict(stepper="bdf", bdf_order=2), seed=1)
+    a.step(2)
+    state = a.save_state()
+    b = _make(device, dict(stepper="bdf", bdf_order=3), seed=1)
+    with pytest.raises(pic.PicError) as e:
+        b.load_state(state)
+    assert e.value.status == 1
+    with pytest.raises(pic.PicError) as e:
+        a.load_state(state[:len(state) // 2])
+    assert e.value.status == 1
+    with pytest.raises(pic.PicError) as e:
+        a.load_state(b"x" * 200)
+    assert e.value.status == 1
+    a.load_state(state)              # its own state: accepted
+    a.close()
+    b.close()
