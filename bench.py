@@ -277,10 +277,62 @@ def cpu_baseline(workload, stepper_name):
                       f"after 1 warm-up, {sum(times):.1f} s"}
 
 
+ADJOINT_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import adjoint as oadj, pic as opic
+from paper_2410_18414_gb300 import workloads
+wl = workloads.weibel_adjoint_128()
+n, steps = {n}, {steps}
+w = wl.lx * wl.ly / n
+cfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, stepper="bdf",
+                  bdf_order=2, w=w)
+args = (cfg, wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n], steps)
+t0 = time.perf_counter(); opic.run(*args); t1 = time.perf_counter()
+tape = oadj.record(*args); oadj.gradient(tape); t2 = time.perf_counter()
+print(json.dumps({{"forward_s": t1 - t0, "gradient_s": t2 - t1}}))
+"""
+
+
+def run_reference_adjoint(a):
+    """The reference arm of `--workload adjoint128`: the oracle's own forward run and its
+    recorded run plus reverse sweep (oracle.adjoint), on a bounded sample of the workload
+    (128 x 128 grid, the first 8192 of its 262,144 particles with the weight rescaled, 10
+    steps), as the same ratio."""
+    n, steps = 8192, min(10, max(1, a.steps))
+    code = ADJOINT_ORACLE_SNIPPET.format(root=ROOT, n=n, steps=steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle adjoint run failed: " + r.stderr[-2000:])
+    t = json.loads(r.stdout.strip().splitlines()[-1])
+    ratio = t["gradient_s"] / t["forward_s"]
+    sample = (f"numpy FP64 oracle, single thread: 128x128 grid, the first {n} of the 262,144 "
+              f"particles (weight rescaled), {steps} steps; forward {t['forward_s']:.1f} s, "
+              f"recorded run + reverse sweep {t['gradient_s']:.1f} s")
+    line = {"metric": "adjoint/forward time", "value": ratio, "unit": "ratio",
+            "impl": "reference", "n_gpus": a.gpus, "steps": steps, "warmup": 0,
+            "ms_per_step": 1e3 * t["gradient_s"] / steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "form": "fp64",
+                       "sample_particles": n, "parallelism": "replicas"},
+            "cpu_baseline": {"value": ratio, "unit": "ratio", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": ratio, "unit": "ratio", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(a):
     """The reference arm: the CPU oracle on the host cores, bounded samples of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if a.workload == "adjoint128":
+        run_reference_adjoint(a)
         return
     wp = workload_params(a.workload)
     n = min(131072, wp["n"] * wp["n"] * wp["ppc"])
