@@ -523,9 +523,10 @@ def adjoint_timings(steps, reps, rank=0):
     cubic, with respect to every initial velocity and momentum, by the library's adjoint.
     Timed per whole run with CUDA events (L2 flushed before each run): the plain forward
     run (pic_step), the recording forward run and the reverse sweep, with checkpoints every
-    20 steps (the backward pass recomputes 9 of the 10 segments) and with every step kept
-    in HBM (6.9 GB, nothing recomputed); one more sweep runs under the library's adjoint
-    kernel timers."""
+    20 steps -- replaying the particle states of each segment from the recorded gathered
+    fields (the default), or recomputing each segment's full steps (least memory) -- and
+    with one segment of 200 steps; one more sweep runs under the library's adjoint kernel
+    timers."""
     import torch
     from paper_2410_18414_gb300 import pic, workloads
     pic.load_library()
@@ -544,9 +545,9 @@ def adjoint_timings(steps, reps, rank=0):
     bz = torch.empty((wl.nx, wl.ny), dtype=torch.float64, device="cuda")
     out = {k: torch.empty(wl.n, dtype=torch.float64, device="cuda") for k in ("vx", "vy", "px", "py")}
 
-    def once(K):
+    def once(K, mode="replay"):
         sim = pic.Simulation(cfg, x, y, vx, vy, stream=sid)
-        adj = pic.Adjoint(sim, N, K) if K else None
+        adj = pic.Adjoint(sim, N, K, mode=mode) if K else None
         flush.zero_()
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -567,8 +568,8 @@ def adjoint_timings(steps, reps, rank=0):
         return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
 
     k20 = min(20, N)
-    for K in (0, k20, N):      # warm-up: one of each
-        once(K)
+    for K, mode in ((0, "replay"), (k20, "replay"), (k20, "recompute"), (N, "replay")):
+        once(K, mode)          # warm-up: one of each
     # one instrumented reverse sweep (every step kept): the library's per-kernel event
     # pairs around the three reverse launch groups of every step
     sim = pic.Simulation(cfg, x, y, vx, vy, stream=sid)
@@ -589,18 +590,28 @@ def adjoint_timings(steps, reps, rank=0):
     med = statistics.median
     fwd = med([once(0)[0] for _ in range(reps)])
     t20 = [once(k20) for _ in range(reps)]
+    t20r = [once(k20, "recompute") for _ in range(reps)]
     tall = [once(N) for _ in range(reps)]
     r20 = (med([t[0] for t in t20]) + med([t[1] for t in t20])) / fwd
+    r20r = (med([t[0] for t in t20r]) + med([t[1] for t in t20r])) / fwd
     rall = (med([t[0] for t in tall]) + med([t[1] for t in tall])) / fwd
+    seg = (N + k20 - 1) // k20
     return {
         "workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "particles": wl.n,
         "steps_per_run": N, "form": "fp64", "objective": "W_B at the last step",
         "forward_ms": fwd,
-        "checkpoint_20": {"record_forward_ms": med([t[0] for t in t20]),
-                          "backward_ms": med([t[1] for t in t20]), "ratio": r20},
-        "keep_all_steps": {"record_forward_ms": med([t[0] for t in tall]),
+        "checkpoint_20": {"mode": "replay", "record_forward_ms": med([t[0] for t in t20]),
+                          "backward_ms": med([t[1] for t in t20]), "ratio": r20,
+                          "record_bytes": int(N * (80 * wl.n + 64 * wl.nx * wl.ny)
+                                              + (seg + 1 + k20) * 64 * wl.n)},
+        "checkpoint_20_recompute": {"mode": "recompute",
+                                    "record_forward_ms": med([t[0] for t in t20r]),
+                                    "backward_ms": med([t[1] for t in t20r]), "ratio": r20r,
+                                    "record_bytes": int((seg + 1) * 64 * wl.n + k20 * (
+                                        144 * wl.n + 64 * wl.nx * wl.ny))},
+        "keep_all_steps": {"mode": "replay", "record_forward_ms": med([t[0] for t in tall]),
                            "backward_ms": med([t[1] for t in tall]), "ratio": rall,
-                           "hbm_bytes": int(N * (128 * wl.n + 64 * wl.nx * wl.ny))},
+                           "record_bytes": int(N * (144 * wl.n + 64 * wl.nx * wl.ny))},
         "kernels": kt,
         "roofline": adjoint_roofline(wl.p, wl.n, kt["adj_push"]["ms_per_launch"]),
     }
@@ -630,6 +641,7 @@ def run_adjoint(a):
                    "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": "fp64",
                    "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
         "forward_ms": t["forward_ms"], "checkpoint_20": t["checkpoint_20"],
+        "checkpoint_20_recompute": t["checkpoint_20_recompute"],
         "keep_all_steps": t["keep_all_steps"], "kernels": t["kernels"], "roofline": t["roofline"],
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }

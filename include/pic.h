@@ -339,13 +339,25 @@ void pic_destroy(pic_handle *h);
  * The paper states the forward method only; the adjoint is a derived capability.
  *
  * Memory: the state (particles and field histories) is checkpointed every
- * `checkpoint_every` steps (K).  The backward pass recomputes each segment of K steps
- * from its checkpoint, keeping that segment's per-step particle state, the eight values
- * each step's push gathered per particle and the step's gather fields (128 n + 64 nx ny
- * bytes per step), then runs it backwards.  The last segment is kept by the forward pass
- * itself, so with K = nsteps nothing is recomputed.  Device memory used: about
- * (nsteps/K + 1) * 64 n + K * (128 n + 64 nx ny) bytes plus the adjoint state. */
+ * `checkpoint_every` steps (K).  The backward pass rebuilds each segment of K steps from
+ * its checkpoint -- the particle states (64 n bytes per step of the segment) and each
+ * step's record (see pic_adjoint_mode) -- then runs it backwards.  PIC_ADJ_REPLAY (the
+ * default) keeps every step's record from the forward pass and replays only the particle
+ * move, costing about (nsteps/K + 1 + K) * 64 n + nsteps * (80 n + 64 nx ny) bytes;
+ * PIC_ADJ_RECOMPUTE re-runs the segment's full steps, costing about (nsteps/K + 1) * 64 n
+ * + K * (144 n + 64 nx ny) bytes.  Both hold the adjoint state besides. */
 typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
+
+/* What the forward pass keeps between checkpoints. */
+typedef enum {
+    PIC_ADJ_REPLAY = 0,    /* every step's record: its gather fields, and per particle
+                              P^{n+1}, v^{n+1} and the A, grad A its push gathered (80 n +
+                              64 nx ny bytes per step); the backward pass replays the particle
+                              states of a segment from its checkpoint with the move alone and
+                              the recorded P, v (bit for bit the forward's states) */
+    PIC_ADJ_RECOMPUTE = 1  /* nothing: the backward pass re-runs every segment's full forward
+                              steps from its checkpoint (least memory) */
+} pic_adjoint_mode;
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init
  * (step 0, no step started), FP64, PIC_STEPPER_BDF, PIC_CHARGE_CONTINUITY and without
@@ -355,6 +367,11 @@ typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
  * destroy it before h.  PIC_ERR_INVALID_ARG for NULL pointers or nsteps < 1. */
 pic_status pic_adjoint_create(pic_handle *h, int32_t nsteps, int32_t checkpoint_every,
                               pic_adjoint **out);
+
+/* As pic_adjoint_create (which uses PIC_ADJ_REPLAY) with the record mode given:
+ * PIC_ERR_INVALID_ARG for an unknown mode. */
+pic_status pic_adjoint_create_ex(pic_handle *h, int32_t nsteps, int32_t checkpoint_every,
+                                 int32_t mode, pic_adjoint **out);
 
 /* Run the nsteps forward steps on h (as pic_step), keeping the checkpoints.  Once only;
  * PIC_ERR_STATE on a second call. */

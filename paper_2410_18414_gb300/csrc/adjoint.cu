@@ -107,9 +107,10 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
         }
         // the fields the forward push gathered at x^{n+1} (dphi/dx, dphi/dy, Ax, Ay,
         // dAx/dx, dAx/dy, dAy/dx, dAy/dy)
-        double f[8];
+        double f[8];  // f[0], f[1] (grad phi) are not needed here
+        f[0] = f[1] = 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) f[k] = gf[(size_t)k * n + p];
+        for (int k = 2; k < 8; ++k) f[k] = gf[(size_t)(k + 2) * n + p];
         // velocity: v = c^2 u / D
         const double ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
         const double D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);

@@ -7,9 +7,10 @@
 //   ck[c]     checkpoint c: the state at step c K, the BDF ring contents in slot order
 //             and the ring heads; ck[nseg] is the end of the run, with the last step's
 //             J and gather fields, so the handle can be put back after the sweep
-//   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1),
-//             recg[j] the gather fields that step used (the level c0 + j + 1) and recf[j]
-//             the eight values its push gathered per particle (8 n)
+//   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1)
+//   records   per step (every step in the replay mode, the segment's in the recompute
+//             mode): the gather fields the step used (recg) and recf: P^{n+1}, v^{n+1} and
+//             the gathered A and grad A of each particle (10 n)
 //   adjoint   particle adjoints (8 n), the history adjoints (3 L + k spectra, slot of
 //             time level t = t mod L), field-adjoint planes and transform scratch
 #include <cuda_runtime.h>
@@ -40,8 +41,9 @@ struct pic_adjoint {
     double2* final_g = nullptr;  // gather fields of the last step
     double* rec = nullptr;       // K states
     double2* recg = nullptr;     // K x 4 ng
-    double* recf = nullptr;      // K x 8 n: the fields each step's push gathered
-    int seg_held = -1;           // segment whose records rec/recg hold
+    double* recf = nullptr;      // per step 10 n: P^{n+1}, v^{n+1} and the gathered A, grad A
+    int seg_held = -1;           // segment whose states rec holds
+    int mode = 0;                // PIC_ADJ_REPLAY or PIC_ADJ_RECOMPUTE
     double* ab = nullptr;        // particle adjoints, 8 n
     double2* hb = nullptr;       // history adjoints, (3 L + Lr) ng
     double2* fb = nullptr;       // field-adjoint planes, 4 ng
@@ -132,23 +134,34 @@ pic_status restore_checkpoint(pic_adjoint* a, const pic_adjoint::Ck& c) {
     return PIC_OK;
 }
 
-// One forward step of h, keeping the new state, the step's gather fields and the values
-// its push gathered in record j.
-pic_status step_and_record(pic_adjoint* a, int j) {
-    pic_handle* h = a->h;
-    h->gather_out = a->recf + (size_t)j * 8 * a->n;
-    pic_status st = pic_step(h, 1);
-    h->gather_out = nullptr;
-    if (st != PIC_OK) return st;
-    st = save_state(a, a->rec + (size_t)j * 8 * a->n);
-    if (st != PIC_OK) return st;
-    CK(cudaMemcpyAsync(a->recg + (size_t)j * 4 * a->ng, h->G, 4 * a->ng * sizeof(double2),
-                       cudaMemcpyDeviceToDevice, h->s));
-    return PIC_OK;
-}
+constexpr size_t kRec = 10;  // arrays of n in one step's record
 
 int seg_begin(const pic_adjoint* a, int c) { return c * a->K; }
 int seg_end(const pic_adjoint* a, int c) { return std::min(a->nsteps, (c + 1) * a->K); }
+
+// Record slot of step s: every step has its own in the replay mode; in the recompute mode
+// the slots are reused by each segment.
+size_t rec_slot(const pic_adjoint* a, int s) {
+    return a->mode == PIC_ADJ_REPLAY ? (size_t)s : (size_t)(s % a->K);
+}
+
+// One forward step of h (step s of the run), keeping the step's gather fields and the
+// values its push gathered, and (state_j >= 0) the new state in segment slot state_j.
+pic_status step_and_record(pic_adjoint* a, int s, int state_j) {
+    pic_handle* h = a->h;
+    const size_t r = rec_slot(a, s);
+    h->gather_out = a->recf + r * kRec * a->n;
+    pic_status st = pic_step(h, 1);
+    h->gather_out = nullptr;
+    if (st != PIC_OK) return st;
+    if (state_j >= 0) {
+        st = save_state(a, a->rec + (size_t)state_j * 8 * a->n);
+        if (st != PIC_OK) return st;
+    }
+    CK(cudaMemcpyAsync(a->recg + r * 4 * a->ng, h->G, 4 * a->ng * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, h->s));
+    return PIC_OK;
+}
 
 AdjParticles adjoint_arrays(pic_adjoint* a) {
     double* b = a->ab;
@@ -215,7 +228,14 @@ extern "C" {
 
 pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_every,
                               pic_adjoint** out) {
+    return pic_adjoint_create_ex(h, nsteps, checkpoint_every, PIC_ADJ_REPLAY, out);
+}
+
+pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoint_every,
+                                 int32_t mode, pic_adjoint** out) {
     if (!out) return fail(h, PIC_ERR_INVALID_ARG, "out must not be NULL");
+    if (mode != PIC_ADJ_REPLAY && mode != PIC_ADJ_RECOMPUTE)
+        return fail(h, PIC_ERR_INVALID_ARG, "unknown adjoint record mode %d", mode);
     *out = nullptr;
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 1) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 1");
@@ -231,6 +251,8 @@ pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_
     a->nsteps = nsteps;
     a->K = std::max(1, std::min(checkpoint_every, nsteps));
     a->nseg = (nsteps + a->K - 1) / a->K;
+    a->mode = mode;
+    const size_t nrec = mode == PIC_ADJ_REPLAY ? (size_t)nsteps : (size_t)a->K;
     a->L = h->L;
     a->Lr = h->Lr;
     a->n = (size_t)h->n;
@@ -247,8 +269,9 @@ pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_j, gb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_g, 4 * gb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->rec, (size_t)a->K * sb);
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recg, (size_t)a->K * 4 * gb);
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recf, (size_t)a->K * sb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recg, nrec * 4 * gb);
+    if (e == cudaSuccess)
+        e = aalloc(a, (void**)&a->recf, nrec * kRec * std::max<size_t>(a->n, 1) * sizeof(double));
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->ab, sb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->hb, hbytes);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->fb, 4 * gb);
@@ -277,16 +300,22 @@ pic_status pic_adjoint_forward(pic_adjoint* a) {
     if (h->step != 0 || h->phase != 0)
         return fail(h, PIC_ERR_STATE, "the handle has stepped since pic_adjoint_create");
     a->forward_done = true;
+    const bool replay = a->mode == PIC_ADJ_REPLAY;
     for (int c = 0; c < a->nseg; ++c) {
         pic_status st = save_checkpoint(a, a->ck[c]);
         if (st != PIC_OK) return st;
         const bool last = c == a->nseg - 1;
         for (int s = seg_begin(a, c); s < seg_end(a, c); ++s) {
-            st = last ? step_and_record(a, s - seg_begin(a, c)) : pic_step(h, 1);
+            // replay: every step's records, no states; recompute: the last segment's
+            // records and states, which the backward pass then need not recompute
+            if (replay)
+                st = step_and_record(a, s, -1);
+            else
+                st = last ? step_and_record(a, s, s - seg_begin(a, c)) : pic_step(h, 1);
             if (st != PIC_OK) return st;
         }
     }
-    a->seg_held = a->nseg - 1;
+    a->seg_held = replay ? -1 : a->nseg - 1;
     pic_status st = save_checkpoint(a, a->ck[a->nseg]);
     if (st != PIC_OK) return st;
     CK(cudaMemcpyAsync(a->final_j, h->J, a->ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
@@ -316,11 +345,21 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
     for (int c = a->nseg - 1; c >= 0; --c) {
         const int c0 = seg_begin(a, c), c1 = seg_end(a, c);
         if (a->seg_held != c) {
-            pic_status st = restore_checkpoint(a, a->ck[c]);
-            if (st != PIC_OK) return st;
-            for (int s = c0; s < c1; ++s) {
-                st = step_and_record(a, s - c0);
+            if (a->mode == PIC_ADJ_REPLAY) {
+                // the segment's particle states from its checkpoint and the recorded fields
+                for (int s = c0; s < c1; ++s) {
+                    const int j = s - c0;
+                    const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
+                    CK(launch_replay_step(h->geom, s0, a->rec + (size_t)j * 8 * np,
+                                          a->recf + rec_slot(a, s) * kRec * np, (int64_t)np, h->s));
+                }
+            } else {
+                pic_status st = restore_checkpoint(a, a->ck[c]);
                 if (st != PIC_OK) return st;
+                for (int s = c0; s < c1; ++s) {
+                    st = step_and_record(a, s, s - c0);
+                    if (st != PIC_OK) return st;
+                }
             }
             a->seg_held = c;
         }
@@ -328,8 +367,8 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
             const int j = s - c0;
             const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
             const double* s1 = a->rec + (size_t)j * 8 * np;
-            pic_status st = backward_step(a, s, s0, s1, a->recf + (size_t)j * 8 * np,
-                                          a->recg + (size_t)j * 4 * ng);
+            pic_status st = backward_step(a, s, s0, s1, a->recf + rec_slot(a, s) * kRec * np,
+                                          a->recg + rec_slot(a, s) * 4 * ng);
             if (st != PIC_OK) return st;
         }
     }

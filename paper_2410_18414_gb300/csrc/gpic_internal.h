@@ -222,7 +222,8 @@ struct PushParams {
     int diag;
 };
 
-// gout (FP64, may be NULL): receives the eight gathered fields, field k at gout[k n + p].
+// gout (FP64, may be NULL): the adjoint's record of the step, ten arrays of n: P^{n+1}
+// (x, y), v^{n+1} (x, y), then the gathered Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy.
 template <typename T>
 cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vx_old,
@@ -330,8 +331,8 @@ struct AdjModeParams {
     double2* rho[kMaxBdf];
 };
 // Reverse push + gather of one step: reads x^{n+1}, P^{n+1} (state n+1), v^n, v^{n-1}
-// (state n), the eight fields the forward push gathered (gf, field k at k n) and the
-// step's gather fields F ([node][4]); updates the particle adjoints and adds the eight
+// (state n), the step's record (gf: the gathered A and grad A at 4 n .. 10 n, see
+// launch_gather_push) and the step's gather fields F ([node][4]); updates the particle adjoints and adds the eight
 // field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
                                    const double* x1, const double* y1, const double* px1,
@@ -365,6 +366,10 @@ cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, 
                             double* gpx, double* gpy, int64_t n, unsigned int* err,
                             cudaStream_t s);
 cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cudaStream_t s);
+// Replay of one FP64 step's particle update from its record: state s0 -> state s1 (eight
+// arrays of n each), bit for bit the step's own.
+cudaError_t launch_replay_step(const ParticleGeom& g, const double* s0, double* s1,
+                               const double* rec, int64_t n, cudaStream_t s);
 // Eight FP64 arrays of n values <-> one contiguous block of 8 n (array k at k n).
 struct Ptr8 {
     const double* p[8];

@@ -513,12 +513,16 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
                 gather_node(rmul(wx[a], wy[b]), gv, f);
             }
         }
-        if (gout) {  // the gathered fields, kept for the adjoint (SoA, field k at k n)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) gout[(size_t)k * n + p] = (double)f[k];
-        }
         T vxn1, vyn1;
         push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
+        if (gout) {  // the adjoint's record of this step (ten arrays of n, see launcher)
+            gout[p] = (double)px[p];
+            gout[(size_t)n + p] = (double)py[p];
+            gout[2 * (size_t)n + p] = (double)vxn1;
+            gout[3 * (size_t)n + p] = (double)vyn1;
+#pragma unroll
+            for (int k = 2; k < 8; ++k) gout[(size_t)(k + 2) * n + p] = (double)f[k];
+        }
     }
     push_finish(pp, bad, kin, diag, err);
 }
@@ -684,6 +688,28 @@ __global__ void k_scatter_by_id(const T* __restrict__ s, const int32_t* __restri
          p += (int64_t)gridDim.x * blockDim.x) {
         int32_t k = id[p];
         if (k >= 0 && k < n) d[k] = (double)s[p];
+    }
+}
+
+// Replay of one FP64 step's particle update from the adjoint's record of that step:
+// state n -> state n+1 with the move of k_move_deposit (the same operations, so the same
+// bits) and the recorded P^{n+1}, v^{n+1}.  States are eight arrays of n in the order x, y,
+// Px, Py, v^n (x, y), v^{n-1} (x, y); rec is the step's record (P^{n+1}, v^{n+1} first).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_replay_step(GeomT<T> g, const T* __restrict__ s0, T* __restrict__ s1,
+              const double* __restrict__ rec, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const T vxi = s0[4 * n + p], vyi = s0[5 * n + p];
+        s1[p] = move_pos(s0[p], vxi, g.dt, g.lx);
+        s1[n + p] = move_pos(s0[n + p], vyi, g.dt, g.ly);
+        s1[2 * n + p] = (T)rec[p];
+        s1[3 * n + p] = (T)rec[n + p];
+        s1[4 * n + p] = (T)rec[2 * n + p];
+        s1[5 * n + p] = (T)rec[3 * n + p];
+        s1[6 * n + p] = vxi;
+        s1[7 * n + p] = vyi;
     }
 }
 
@@ -953,6 +979,13 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
     if (n == 0) return cudaSuccess;
     GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix, g, x, y, n, (AccFix::make(j, scale)), err, sp,
                      typed_species<T>(spp))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replay_step(const ParticleGeom& g, const double* s0, double* s1,
+                               const double* rec, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_replay_step<double><<<blocks_for(n), kThreads, 0, s>>>(typed<double>(g), s0, s1, rec, n);
     return cudaGetLastError();
 }
 

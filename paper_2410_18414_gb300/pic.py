@@ -116,6 +116,7 @@ def load_library(path=LIB_PATH):
         "pic_ensemble_period": ([vp], i32),
         "pic_ensemble_destroy": ([vp], None),
         "pic_adjoint_create": ([vp, i32, i32, ctypes.POINTER(vp)], i32),
+        "pic_adjoint_create_ex": ([vp, i32, i32, i32, ctypes.POINTER(vp)], i32),
         "pic_adjoint_forward": ([vp], i32),
         "pic_adjoint_backward": ([vp] + [vp] * 7, i32),
         "pic_adjoint_checkpoint_every": ([vp], i32),
@@ -360,13 +361,19 @@ class Adjoint:
     v^0 and, with P^0 = gamma m v^0 independent, to P^0.  Seeds and results are CUDA
     float64 tensors (the library reads and writes device memory)."""
 
-    def __init__(self, sim, nsteps, checkpoint_every=None):
+    MODES = {"replay": 0, "recompute": 1}
+
+    def __init__(self, sim, nsteps, checkpoint_every=None, mode="replay"):
+        """mode "replay": the forward pass keeps every step's gathered fields and the backward
+        pass replays particle states between checkpoints; "recompute": it re-runs each
+        segment's full steps (least memory)."""
         self.lib = load_library()
         self.sim = sim
         self.nsteps = int(nsteps)
         a = ctypes.c_void_p()
         k = self.nsteps if checkpoint_every is None else int(checkpoint_every)
-        st = self.lib.pic_adjoint_create(sim.h, self.nsteps, k, ctypes.byref(a))
+        st = self.lib.pic_adjoint_create_ex(sim.h, self.nsteps, k, self.MODES[mode],
+                                            ctypes.byref(a))
         if st != PIC_OK:
             raise PicError(st, self.lib.pic_last_error(sim.h).decode())
         self.a = a
