@@ -660,14 +660,14 @@ def flops_adj_push(p):
 
 def adjoint_roofline(p, n, ms):
     """k_adj_push_gather against the FP64 pipe (nominal 1.25 TFLOP/s; the kernel's DRAM
-    traffic, 49.6 MB per launch by ncu at this size, is about 3% of the HBM roof)."""
+    traffic, 50.0 MB per launch by ncu at this size, is about 3% of the HBM roof)."""
     if not ms:
         return None
     pk = peaks()
     achieved = flops_adj_push(p) * n / (ms * 1e-3) / 1e12
     return {"kernel": "k_adj_push_gather", "bound": "alu", "achieved": achieved,
             "peak": pk["fp64_gflops"] / 1e3, "unit": "TFLOP/s",
-            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": 49.6e6,
+            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": 50.0e6,
             "peak_source": pk["fp64_src"],
             "note": f"{flops_adj_push(p)} FP64 flops per particle (cubic: 600); traffic = "
                     "dram read + write of one launch from ncu on this workload"}
