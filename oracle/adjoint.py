@@ -1,10 +1,10 @@
-"""Discrete adjoint of the BDF-k PIC step (oracle; test infrastructure only).
+"""Discrete adjoint of the PIC step (oracle; test infrastructure only).
 
 The paper defines the forward method only; the gradient of an objective of the final
 state with respect to the initial velocities is the transpose of the Jacobian of the
 forward map, applied step by step in reverse.  The forward map is oracle.pic.step
-(Algorithm 1, section 4.2) with the BDF-k stepper of section 3.2 and the charge from
-the continuity equation.  The objective is
+(Algorithm 1, section 4.2) with the charge from the continuity equation and any of the
+steppers of section 3: BDF-k (3.2), the three CDF-2 forms (3.1) or s-stage DIRK (3.3).  The objective is
 
     W_B = 1/2 sum_ij B_z(i, j)^2 dx dy       (magnetic energy, section 5)
 
@@ -24,8 +24,10 @@ for a spectrum z the pairing Re sum conj(z_bar) dz):
               v* = 2 v^n - v^{n-1}: v^n_bar += 2 v*_bar, v^{n-1}_bar = -v*_bar
   7. gather:  field_bar(node) += g_bar W(node)  (a deposit); x_bar += g_bar grad_x(gather)
   6. fields:  F = IDFT(M u_hat)  ->  u_hat_bar += conj(M) DFT(F_bar)/N   (conj(i k) = -i k)
-  5. BDF-k:   u^{n+1} = (g S - sum_d C_d u^{n+1-d})/(C_0 + g K): real per-mode multipliers
-              rho^{n+1} = -sum_j a_j rho^{n+1-j} - beta dt i k . J_hat
+  5. stepper: BDF-k u^{n+1} = (g S - sum_d C_d u^{n+1-d})/(C_0 + g K),
+              rho^{n+1} = -sum_j a_j rho^{n+1-j} - beta dt i k . J_hat; CDF-2 and DIRK
+              likewise linear with real per-mode coefficients (DIRK's from the
+              stage recurrence, taken as the Jacobian of the forward stage loop)
   4. J_hat = DFT(J)  ->  J_bar = Re(N IDFT(J_hat_bar))
   3. deposit: J = q_p v^n W(x^{n+1}) / (dx dy): v^n_bar += q_p/(dx dy) gather(J_bar);
               x^{n+1}_bar += q_p/(dx dy) v^n . grad_x gather(J_bar)
@@ -101,8 +103,8 @@ def _snapshot(st):
 
 def record(cfg, x0, y0, vx0, vy0, nsteps):
     """Run oracle.pic for nsteps, keeping every particle state and every step's fields."""
-    if cfg.stepper != "bdf" or cfg.charge != "continuity":
-        raise ValueError("the adjoint covers the BDF-k stepper with the continuity charge")
+    if cfg.charge != "continuity" or cfg.vdim != 2 or cfg.species is not None:
+        raise ValueError("the adjoint covers the continuity charge, 2D-2V, one species")
     st = opic.initial_state(cfg, x0, y0, vx0, vy0)
     e0 = (st.grids["ex0"].copy(), st.grids["ey0"].copy())
     states = [_snapshot(st)]
@@ -120,6 +122,132 @@ def magnetic_energy(cfg, st):
 
 
 # ---------------------------------------------------------------- adjoint pieces ----
+
+def _gathered_field_adjoints(cfg, fbar):
+    """Spectral adjoints of the potentials behind the eight gathered mesh fields: the
+    fields are IDFT(i kx u), IDFT(i ky u), IDFT(A) with u = phi~, Ax, Ay, so each gets
+    -i k_l DFT(field_bar)/N (conj(i k) = -i k) or DFT(field_bar)/N."""
+    kx, ky, _ = spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
+    N = cfg.nx * cfg.ny
+    fh = {name: spectral.dft2(fbar[name]) / N for name in opic.FIELD_NAMES}
+    phi = -1j * kx * fh["dphidx"] - 1j * ky * fh["dphidy"]
+    ax = fh["ax"] - 1j * kx * fh["daxdx"] - 1j * ky * fh["daxdy"]
+    ay = fh["ay"] - 1j * kx * fh["daydx"] - 1j * ky * fh["daydy"]
+    return phi, ax, ay
+
+
+def _mesh_current_adjoint(cfg, jx_hat_bar, jy_hat_bar):
+    """J_hat = DFT(J) -> J_bar = Re(N IDFT(J_hat_bar))."""
+    N = cfg.nx * cfg.ny
+    return N * spectral.idft2(jx_hat_bar).real, N * spectral.idft2(jy_hat_bar).real
+
+
+def field_adjoint_cdf2(cfg, hbar, fbar):
+    """Reverse of one CDF-2 field solve (section 3.1; cfg.cdf_form implicit, semi or
+    explicit).  hbar: adjoints of the history after the step, with the forward's keys
+    (phi, phi_prev, rho, rho_prev, ax, ax_prev, ay, ay_prev, jx, jx_prev, jy, jy_prev);
+    returns (the adjoints before the step, the mesh J adjoint).  The particles use
+    phi~ = (phi^{n+3/2} + phi^{n+1/2})/2 and A^{n+1}; the shift moves each new level to the
+    current slot and the current one to the previous slot."""
+    kx, ky, K = spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
+    c, dt, eps0, mu0 = cfg.c, cfg.dt, cfg.eps0, cfg.mu0
+    phi_c, ax_c, ay_c = _gathered_field_adjoints(cfg, fbar)
+    # adjoints of the new levels and of the levels the step read (after the shift)
+    phin = hbar["phi"] + 0.5 * phi_c
+    phih = hbar["phi_prev"] + 0.5 * phi_c
+    rhon, rhoh = hbar["rho"], hbar["rho_prev"]
+    an = {"x": hbar["ax"] + ax_c, "y": hbar["ay"] + ay_c}
+    ah = {"x": hbar["ax_prev"], "y": hbar["ay_prev"]}
+    jn = {"x": hbar["jx"], "y": hbar["jy"]}
+    jh = {"x": hbar["jx_prev"], "y": hbar["jy_prev"]}
+    zero = np.zeros_like(phin)
+    phip, rhop = zero.copy(), zero.copy()
+    ap = {"x": zero.copy(), "y": zero.copy()}
+    jp = {"x": zero.copy(), "y": zero.copy()}
+    th = 0.5 * c * c * dt * dt
+    inv = 1.0 / (1.0 + th * K)
+    h2 = c * c * dt * dt
+    if cfg.cdf_form == "implicit":
+        # u^{n+1} = inv (2 u^n + th (S^{n+1} + S^{n-1})) - u^{n-1}
+        phih = phih + 2.0 * inv * phin
+        rhon = rhon + (inv * th / eps0) * phin
+        rhop = rhop + (inv * th / eps0) * phin
+        phip = phip - phin
+        for d in ("x", "y"):
+            ah[d] = ah[d] + 2.0 * inv * an[d]
+            jn[d] = jn[d] + (inv * th * mu0) * an[d]
+            jp[d] = jp[d] + (inv * th * mu0) * an[d]
+            ap[d] = ap[d] - an[d]
+    elif cfg.cdf_form == "semi":
+        # u^{n+1} = inv (2 u^n + c^2 dt^2 S^n) - u^{n-1}, S^n = rho^{n+1/2}/eps0, mu0 J^n
+        phih = phih + 2.0 * inv * phin
+        rhoh = rhoh + (inv * h2 / eps0) * phin
+        phip = phip - phin
+        for d in ("x", "y"):
+            ah[d] = ah[d] + 2.0 * inv * an[d]
+            jh[d] = jh[d] + (inv * h2 * mu0) * an[d]
+            ap[d] = ap[d] - an[d]
+    elif cfg.cdf_form == "explicit":
+        # u^{n+1} = 2 u^n - u^{n-1} + c^2 dt^2 (S^n - K u^n)
+        phih = phih + (2.0 - h2 * K) * phin
+        rhoh = rhoh + (h2 / eps0) * phin
+        phip = phip - phin
+        for d in ("x", "y"):
+            ah[d] = ah[d] + (2.0 - h2 * K) * an[d]
+            jh[d] = jh[d] + (h2 * mu0) * an[d]
+            ap[d] = ap[d] - an[d]
+    else:
+        raise ValueError(cfg.cdf_form)
+    # rho^{n+3/2} = rho^{n+1/2} - dt (i kx Jx + i ky Jy)
+    rhoh = rhoh + rhon
+    jn["x"] = jn["x"] + 1j * dt * kx * rhon
+    jn["y"] = jn["y"] + 1j * dt * ky * rhon
+    out = {"phi": phih, "phi_prev": phip, "rho": rhoh, "rho_prev": rhop,
+           "ax": ah["x"], "ax_prev": ap["x"], "ay": ah["y"], "ay_prev": ap["y"],
+           "jx": jh["x"], "jx_prev": jp["x"], "jy": jh["y"], "jy_prev": jp["y"]}
+    return out, _mesh_current_adjoint(cfg, jn["x"], jn["y"])
+
+
+def dirk_matrix(cfg, K):
+    """The real per-mode matrix of one DIRK wave step (section 3.3.1):
+    (u^{n+1}, v^{n+1}) = M (u^n, v^n, S^n, S^{n+1}), M[r][i] evaluated by running the stage
+    recurrence steppers.dirk_wave_update on unit inputs (the map is linear in them)."""
+    A, b, cv = cfg.dirk["A"], cfg.dirk["b"], cfg.dirk["c"]
+    cols = []
+    for e in np.eye(4):
+        uo, vo = steppers.dirk_wave_update(e[0] + 0.0 * K, e[1] + 0.0 * K, e[2], e[3], K, cfg.c,
+                                           cfg.dt, A, b, cv)
+        cols.append((uo, vo))
+    return [[cols[i][r] for i in range(4)] for r in range(2)]
+
+
+def field_adjoint_dirk(cfg, hbar, fbar):
+    """Reverse of one s-stage DIRK field solve (section 3.3).  hbar: adjoints of the state
+    after the step (phi, vphi, ax, vax, ay, vay, rho, jx, jy -- jx, jy the stored J^{n+1});
+    returns (the adjoints before the step, the mesh J^{n+1} adjoint)."""
+    kx, ky, K = spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
+    dt, eps0, mu0 = cfg.dt, cfg.eps0, cfg.mu0
+    r0, r1 = steppers.dirk_interp_weights(cfg.dirk["b"], cfg.dirk["c"])
+    M = dirk_matrix(cfg, K)
+    phi_c, ax_c, ay_c = _gathered_field_adjoints(cfg, fbar)
+
+    def back(ub, vb):  # transpose of M applied to (u_bar^{n+1}, v_bar^{n+1})
+        return [M[0][i] * ub + M[1][i] * vb for i in range(4)]
+
+    p = back(hbar["phi"] + phi_c, hbar["vphi"])
+    ax = back(hbar["ax"] + ax_c, hbar["vax"])
+    ay = back(hbar["ay"] + ay_c, hbar["vay"])
+    # phi's sources rho^n/eps0, rho^{n+1}/eps0; A's mu0 J^n, mu0 J^{n+1}
+    rhon = hbar["rho"] + p[3] / eps0
+    rho = p[2] / eps0 + rhon                           # rho^{n+1} = rho^n - dt (...)
+    jx = mu0 * ax[2] + 1j * dt * r0 * kx * rhon        # J^n (the stored level)
+    jy = mu0 * ay[2] + 1j * dt * r0 * ky * rhon
+    jxn = hbar["jx"] + mu0 * ax[3] + 1j * dt * r1 * kx * rhon
+    jyn = hbar["jy"] + mu0 * ay[3] + 1j * dt * r1 * ky * rhon
+    out = {"phi": p[0], "vphi": p[1], "ax": ax[0], "vax": ax[1], "ay": ay[0], "vay": ay[1],
+           "rho": rho, "jx": jx, "jy": jy}
+    return out, _mesh_current_adjoint(cfg, jxn, jyn)
+
 
 def field_adjoint_bdf(cfg, hbar, fbar):
     """Reverse of one BDF-k field solve (continuity + wave update + gradient fields).
@@ -212,7 +340,9 @@ def adjoint_step(cfg, s0, s1, fields, abar, hbar):
         gx, gy = gather_grad(cfg, x1, y1, fields[name])
         xb = xb + gbar[name] * gx
         yb = yb + gbar[name] * gy
-    hbar, (jxb, jyb) = field_adjoint_bdf(cfg, hbar, fbar)
+    field_adjoint = {"bdf": field_adjoint_bdf, "cdf2": field_adjoint_cdf2,
+                     "dirk": field_adjoint_dirk}[cfg.stepper]
+    hbar, (jxb, jyb) = field_adjoint(cfg, hbar, fbar)
     # step 3: J = q_p v^n W(x^{n+1}) / (dx dy)
     s = cfg.w * cfg.q / (cfg.dx * cfg.dy)
     vx, vy = s0["vx"], s0["vy"]
@@ -274,15 +404,20 @@ def gradient(tape, bz_bar=None, px_bar=None, py_bar=None):
     if bz_bar is None and px_bar is None and py_bar is None:
         bz_bar = fin.grids["bz"] * (cfg.dx * cfg.dy)
     kx, ky, _ = spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
-    k = cfg.bdf_order
     zero = np.zeros((cfg.nx, cfg.ny), dtype=np.complex128)
-    hbar = {"phi": [zero.copy() for _ in range(2 * k)], "ax": [zero.copy() for _ in range(2 * k)],
-            "ay": [zero.copy() for _ in range(2 * k)], "rho": [zero.copy() for _ in range(k)]}
+    # adjoints of the history after the last step, with the forward's keys; the newest
+    # A (the level B_z is taken from) is ax[0] for BDF-k and ax for CDF-2 and DIRK
+    hbar = {key: ([zero.copy() for _ in val] if isinstance(val, list) else zero.copy())
+            for key, val in fin.hist.items()}
     if bz_bar is not None:
         # B_z = IDFT(i kx Ay - i ky Ax) of the newest level
         zb = spectral.dft2(np.asarray(bz_bar, dtype=np.float64)) / (cfg.nx * cfg.ny)
-        hbar["ay"][0] = hbar["ay"][0] - 1j * kx * zb
-        hbar["ax"][0] = hbar["ax"][0] + 1j * ky * zb
+        if cfg.stepper == "bdf":
+            hbar["ay"][0] = hbar["ay"][0] - 1j * kx * zb
+            hbar["ax"][0] = hbar["ax"][0] + 1j * ky * zb
+        else:
+            hbar["ay"] = hbar["ay"] - 1j * kx * zb
+            hbar["ax"] = hbar["ax"] + 1j * ky * zb
     abar = {key: np.zeros(n) for key in PARTICLE_KEYS}
     if px_bar is not None:
         abar["px"] = np.asarray(px_bar, dtype=np.float64).copy()

@@ -1,8 +1,8 @@
-"""Pins for oracle.adjoint, the discrete adjoint of the BDF-k step.
+"""Pins for oracle.adjoint, the discrete adjoint of the PIC step.
 
 The adjoint is the transpose of the Jacobian of the forward map oracle.pic.step
-(Algorithm 1 with the BDF-k stepper of section 3.2), so it is pinned by things fixed
-outside it:
+(Algorithm 1 with the BDF-k stepper of section 3.2, the CDF-2 forms of section 3.1 or
+s-stage DIRK of section 3.3), so it is pinned by things fixed outside it:
   * spline derivatives against the closed-form B-spline polynomials (differentiated by
     hand for p = 2, by central differences for p = 3, 4) and their zero sum;
   * exact transpose identities of the linear pieces (scatter vs gather; the whole field
@@ -19,6 +19,7 @@ import pytest
 from oracle import adjoint as oadj
 from oracle import pic as opic
 from oracle import spectral
+from oracle import steppers as osteps
 
 from test_oracle_bspline import closed_form
 
@@ -127,6 +128,86 @@ def test_field_adjoint_is_transpose_of_field_solve(k):
     assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
 
 
+def _random_hist(rng, cfg, like):
+    return {key: ([_hermitian(rng, cfg) for _ in val] if isinstance(val, list)
+                  else _hermitian(rng, cfg)) for key, val in like.items()}
+
+
+def _pair_hist(a, b):
+    return sum(sum(_pair(x, y) for x, y in zip(a[key], b[key])) if isinstance(a[key], list)
+               else _pair(a[key], b[key]) for key in a)
+
+
+OTHER_STEPPERS = [
+    ("cdf2-implicit", dict(stepper="cdf2", cdf_form="implicit")),
+    ("cdf2-semi", dict(stepper="cdf2", cdf_form="semi")),
+    ("cdf2-explicit", dict(stepper="cdf2", cdf_form="explicit")),
+    ("dirk2", dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG)),
+    ("dirk3", dict(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT)),
+]
+
+
+@pytest.mark.parametrize("name,kw", OTHER_STEPPERS, ids=[c[0] for c in OTHER_STEPPERS])
+def test_cdf2_and_dirk_field_adjoints_are_transposes(name, kw):
+    # the same dot-product identity for the CDF-2 and DIRK field solves, on a history of
+    # random spectra (every level independent, so a dropped or misrouted term shows)
+    cfg = _cfg(**kw)
+    rng = np.random.default_rng(abs(hash(name)) % 1000)
+    st = opic.initial_state(cfg, *_beams(8, seed=1))
+    st.hist = _random_hist(rng, cfg, st.hist)
+    h_in = {key: ([v.copy() for v in val] if isinstance(val, list) else val.copy())
+            for key, val in st.hist.items()}
+    jx = rng.standard_normal((cfg.nx, cfg.ny))
+    jy = rng.standard_normal((cfg.nx, cfg.ny))
+    fields = opic.field_solve(cfg, st, jx, jy)
+    hbar_out = _random_hist(rng, cfg, st.hist)
+    fbar = {name_: rng.standard_normal((cfg.nx, cfg.ny)) for name_ in opic.FIELD_NAMES}
+    adj = oadj.field_adjoint_cdf2 if cfg.stepper == "cdf2" else oadj.field_adjoint_dirk
+    hbar_in, (jxb, jyb) = adj(cfg, hbar_out, fbar)
+    assert set(hbar_in) == set(h_in)
+    lhs = _pair_hist(hbar_out, st.hist)
+    lhs += sum(float(np.sum(fbar[f] * fields[f])) for f in opic.FIELD_NAMES)
+    rhs = _pair_hist(hbar_in, h_in) + float(np.sum(jxb * jx) + np.sum(jyb * jy))
+    scale = abs(_pair_hist(hbar_out, st.hist)) + abs(_pair_hist(hbar_in, h_in))
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
+    # each block separately: only the current, only one history entry
+    for key in h_in:
+        zero_out = {k: ([np.zeros_like(v) for v in val] if isinstance(val, list)
+                        else np.zeros_like(val)) for k, val in hbar_out.items()}
+        zero_out[key] = hbar_out[key]
+        nof = {f: np.zeros((cfg.nx, cfg.ny)) for f in opic.FIELD_NAMES}
+        hb, (jxb1, jyb1) = adj(cfg, zero_out, nof)
+        st.hist = {k: ([v.copy() for v in val] if isinstance(val, list) else val.copy())
+                   for k, val in h_in.items()}
+        opic.field_solve(cfg, st, jx, jy)
+        l1 = _pair_hist(zero_out, st.hist)
+        r1 = _pair_hist(hb, h_in) + float(np.sum(jxb1 * jx) + np.sum(jyb1 * jy))
+        assert abs(l1 - r1) <= 1e-12 * (abs(l1) + abs(r1) + 1.0), (key, l1, r1)
+
+
+def test_dirk_matrix_reproduces_the_stage_loop():
+    # the unit-input matrix applied to random inputs equals the stage recurrence itself
+    cfg = _cfg(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT)
+    _, _, K = spectral.wavenumber_grid(cfg.nx, cfg.ny, cfg.lx, cfg.ly)
+    rng = np.random.default_rng(2)
+    u, v, s0, s1 = (_hermitian(rng, cfg) for _ in range(4))
+    M = oadj.dirk_matrix(cfg, K)
+    A, b, cv = cfg.dirk["A"], cfg.dirk["b"], cfg.dirk["c"]
+    uo, vo = osteps.dirk_wave_update(u, v, s0, s1, K, cfg.c, cfg.dt, A, b, cv)
+    for r, ref in ((0, uo), (1, vo)):
+        got = M[r][0] * u + M[r][1] * v + M[r][2] * s0 + M[r][3] * s1
+        np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.max(np.abs(ref)))
+    # K = 0, one stage of the implicit midpoint: k_v = c^2 (S0 + S1)/2, k_u = v + h k_v / 2,
+    # so u' = u + h v + (h c)^2 (S0 + S1)/4 and v' = v + h c^2 (S0 + S1)/2
+    mid = _cfg(stepper="dirk", dirk={"A": [[0.5]], "b": [1.0], "c": [0.5]}, c=2.0)
+    m0 = oadj.dirk_matrix(mid, np.zeros(1))
+    h, c2 = mid.dt, mid.c ** 2
+    np.testing.assert_allclose([m0[0][i][0] for i in range(4)],
+                               [1.0, h, h * h * c2 / 4, h * h * c2 / 4], rtol=1e-14)
+    np.testing.assert_allclose([m0[1][i][0] for i in range(4)],
+                               [0.0, 1.0, h * c2 / 2, h * c2 / 2], rtol=1e-14, atol=1e-16)
+
+
 # ------------------------------------------------------------------ whole run --
 
 def _fd(f, h):
@@ -158,6 +239,36 @@ def test_magnetic_energy_gradient_matches_finite_differences(p, k):
         fd = _fd(lambda e: oadj.objective(cfg, x0, y0, vx0 + e * d[0], vy0 + e * d[1], nsteps), h)
         ad = float(np.dot(gvx, d[0]) + np.dot(gvy, d[1]))
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+@pytest.mark.parametrize("name,kw", OTHER_STEPPERS, ids=[c[0] for c in OTHER_STEPPERS])
+def test_cdf2_and_dirk_gradients_match_finite_differences(name, kw):
+    cfg = _cfg(p=3, **kw)
+    n, nsteps = 160, 10
+    x0, y0, vx0, vy0 = _beams(n, seed=11)
+    tape = oadj.record(cfg, x0, y0, vx0, vy0, nsteps)
+    g = oadj.gradient(tape)
+    gvx, gvy = g["v0"]
+    rng = np.random.default_rng(12)
+    h = 1e-6
+    for i in rng.choice(n, 3, replace=False):
+        def f(e, i=i):
+            v = vy0.copy()
+            v[i] += e
+            return oadj.objective(cfg, x0, y0, vx0, v, nsteps)
+        fd = _fd(f, h)
+        assert abs(fd - gvy[i]) <= 1e-6 * abs(gvy[i]) + 1e-13, (i, fd, gvy[i])
+    d = rng.standard_normal((2, n))
+    fd = _fd(lambda e: oadj.objective(cfg, x0, y0, vx0 + e * d[0], vy0 + e * d[1], nsteps), h)
+    ad = float(np.dot(gvx, d[0]) + np.dot(gvy, d[1]))
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+    # the final momenta as the objective
+    ax, ay = rng.standard_normal(n), rng.standard_normal(n)
+    gm = oadj.gradient(tape, px_bar=ax, py_bar=ay)
+    fd = _fd(lambda e: oadj.objective(cfg, x0, y0, vx0 + e * d[0], vy0 + e * d[1], nsteps,
+                                      px_bar=ax, py_bar=ay), h)
+    ad = float(np.dot(gm["v0"][0], d[0]) + np.dot(gm["v0"][1], d[1]))
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
 
 
 def test_momentum_gradient_with_p0_as_variable():
