@@ -319,7 +319,7 @@ const char *pic_last_error(const pic_handle *h);
 void pic_destroy(pic_handle *h);
 
 /* ---------------------------------------------------------------- adjoint ----
- * Discrete adjoint of the FP64 BDF-k step: the exact gradient of an objective of the
+ * Discrete adjoint of the FP64 step: the exact gradient of an objective of the
  * final state,
  *     J = sum_ij bz_bar(i, j) B_z(i, j) + sum_p (px_bar_p Px_p + py_bar_p Py_p),
  * B_z = dAy/dx - dAx/dy of the last level and P the last momenta, with respect to the
@@ -327,13 +327,14 @@ void pic_destroy(pic_handle *h);
  * independent variable, with respect to P^0).  For the magnetic energy
  * W_B = 1/2 sum B_z^2 dx dy (section 5) pass bz_bar = B_z dx dy.  The gradient is the
  * transpose of the Jacobian of the forward map that pic_step computes (Algorithm 1 of
- * section 4.2 with the BDF-k update of section 3.2 and the charge from continuity),
+ * section 4.2 with any of the field updates -- BDF-k of section 3.2, the three CDF-2 forms of
+ * section 3.1, DIRK of section 3.3 -- and the charge from continuity),
  * applied step by step in reverse:
  *   - the transpose of the current deposit is a gather of the current's adjoint with
  *     the shape weights and their derivatives;
  *   - the transpose of the field gather is a deposit of the eight field adjoints;
- *   - per Fourier mode, the BDF-k recurrences run backwards with their real
- *     multipliers, and i k maps to -i k;
+ *   - per Fourier mode, the stepper's recurrences run backwards with their real
+ *     multipliers (DIRK's from its stage recurrence on unit inputs), and i k maps to -i k;
  *   - the IAEM push and the t = 0 set-up (P^0 = gamma m v^0 and the Taylor start
  *     v^{-1}) are transposed per particle.
  * The paper states the forward method only; the adjoint is a derived capability.
@@ -360,7 +361,7 @@ typedef enum {
 } pic_adjoint_mode;
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init
- * (step 0, no step started), FP64, PIC_STEPPER_BDF, PIC_CHARGE_CONTINUITY and without
+ * (step 0, no step started), FP64 (any stepper), PIC_CHARGE_CONTINUITY and without
  * sorting (sort_interval 0), 2D-2V with one species, else PIC_ERR_UNSUPPORTED (or
  * PIC_ERR_STATE for a handle that has stepped).  checkpoint_every is clamped to 1..nsteps.  Allocates all the
  * adjoint's device memory here (PIC_ERR_CUDA if that fails).  The adjoint keeps h:

@@ -1,4 +1,4 @@
-"""torch.autograd interface to the discrete adjoint of the FP64 BDF-k run.
+"""torch.autograd interface to the discrete adjoint of the FP64 run (any stepper).
 
 magnetic_energy(cfg, x0, y0, vx0, vy0, nsteps) returns the magnetic energy
 W_B = 1/2 sum B_z^2 dx dy of the last level (section 5) after `nsteps` steps of
@@ -40,7 +40,7 @@ class _MagneticEnergy(torch.autograd.Function):
 
 
 def magnetic_energy(cfg, x0, y0, vx0, vy0, nsteps, checkpoint_every=None, stream=None):
-    """W_B after nsteps (FP64, BDF-k, no sorting); differentiable in vx0, vy0 (CUDA
+    """W_B after nsteps (FP64, continuity charge, no sorting); differentiable in vx0, vy0 (CUDA
     float64 tensors).  x0, y0: CUDA float64 tensors or numpy arrays."""
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream

@@ -1,7 +1,7 @@
-// Discrete adjoint of the FP64 BDF-k step: the transpose of the Jacobian of one step of
-// Algorithm 1 (section 4.2) with the BDF-k field solve of section 3.2, applied in
-// reverse, for the gradient of an objective of the final state with respect to the
-// initial velocities.
+// Discrete adjoint of the FP64 step: the transpose of the Jacobian of one step of
+// Algorithm 1 (section 4.2) with the BDF-k (section 3.2), CDF-2 (section 3.1) or DIRK
+// (section 3.3) field solve, applied in reverse, for the gradient of an objective of the
+// final state with respect to the initial velocities.
 //
 // Adjoint of a quantity z is written zb; the pairing is the plain sum over particles and
 // grid nodes, and Re sum conj(zb) dz for a spectrum.  Reverse of step n -> n+1:
@@ -15,10 +15,11 @@
 //     v* = 2 v^n - v^{n-1}:  v^n b += 2 v*b,  v^{n-1} b = -v*b
 //     the gather's transpose deposits the eight field adjoints with the same weights,
 //     and x^{n+1} b gets sum_f gb_f grad(sum_node F_f W)
-//   field solve (k_adj_modes_bdf), per mode, after forward transforms of the deposited
-//     field adjoints: conj(i k) = -i k for the spectral gradients, then the BDF-k
-//     recurrences run backwards with their real multipliers, ending in the adjoint of
-//     the current spectrum, inverse-transformed to the mesh
+//   field solve (k_adj_modes / k_adj_columns), per mode, after forward transforms of the
+//     deposited field adjoints: conj(i k) = -i k for the spectral gradients, then the
+//     stepper's recurrences run backwards with their real per-mode multipliers (DIRK's
+//     2 x 4 stage matrix from the forward stage loop on unit inputs), ending in the
+//     adjoint of the current spectrum, inverse-transformed to the mesh
 //   deposit + move (k_adj_deposit_move), per particle:
 //     J = q_p v^n W(x^{n+1}) / (dx dy):  v^n b += gather(Jb),
 //       x^{n+1} b += v^n . grad gather(Jb)   (q_p/(dx dy) folded into Jb)
@@ -232,12 +233,13 @@ constexpr int kModeThreads = 256;
 __device__ __forceinline__ zd zl(const double2* p) { return zd{p->x, p->y}; }
 __device__ __forceinline__ void zs(double2* p, zd v) { *p = make_double2(v.re, v.im); }
 
-// Reverse BDF-k field step of mode (i, j), idx = i ny + j.  za[k] = F(f_2k + i f_2k+1)(k),
-// zb[k] = the same at -k, for the four packed field-adjoint planes.  Updates the history
-// adjoints of the mode and returns the packed adjoint current (Jx + i Jy) q_p/(dx dy).
-__device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const AdjModeParams& ap, int idx,
-                                       double kx, double ky, const zd* za, const zd* zb) {
-    // the eight field adjoints' spectra / (nx ny), from the packed pairs (f_2k + i f_2k+1)
+// The eight field adjoints' spectra / (nx ny) of mode (kx, ky), from the packed pairs
+// za[k] = F(f_2k + i f_2k+1)(k) and zb[k] = the same at -k, folded into the adjoints of
+// the three potentials they are taken from: gradient fields i k_l u get -i k_l, the A
+// fields themselves 1.  (The particles' phi is phi~ for CDF-2, the new level otherwise.)
+__device__ __forceinline__ void gathered_adjoints(const ModeCommon& mc, double kx, double ky,
+                                                  const zd* za, const zd* zb, zd& phi, zd& ax,
+                                                  zd& ay) {
     zd a[8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -247,10 +249,20 @@ __device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const AdjModeParams
         const zd d = za[k] - c;  // 2i F(f_2k+1)
         a[2 * k + 1] = zd{h * d.im, -h * d.re};
     }
-    // gradient fields i k_l u: adjoint multiplier -i k_l
-    const zd phis = zl(ap.phi[0] + idx) - zi(kx * a[0]) - zi(ky * a[1]);
-    const zd axs = zl(ap.ax[0] + idx) + a[2] - zi(kx * a[4]) - zi(ky * a[5]);
-    const zd ays = zl(ap.ay[0] + idx) + a[3] - zi(kx * a[6]) - zi(ky * a[7]);
+    phi = zi(-kx * a[0]) - zi(ky * a[1]);
+    ax = a[2] - zi(kx * a[4]) - zi(ky * a[5]);
+    ay = a[3] - zi(kx * a[6]) - zi(ky * a[7]);
+}
+
+// Reverse BDF-k field step of mode idx = i ny + j.  Updates the history adjoints of the
+// mode and returns the packed adjoint current (Jx + i Jy) q_p/(dx dy).
+__device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const AdjModeParams& ap, int idx,
+                                       double kx, double ky, const zd* za, const zd* zb) {
+    zd phis, axs, ays;
+    gathered_adjoints(mc, kx, ky, za, zb, phis, axs, ays);
+    phis = zl(ap.phi[0] + idx) + phis;
+    axs = zl(ap.ax[0] + idx) + axs;
+    ays = zl(ap.ay[0] + idx) + ays;
     // u^{n+1} = (g S - sum_d C_d u^{n+1-d}) / (C_0 + g K)
     const double inv = mc.invd[idx];
     const int L = 2 * ap.k;
@@ -277,10 +289,141 @@ __device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const AdjModeParams
     return mc.jscale * (jx + zi(jy));
 }
 
+// Reverse CDF-2 field step of mode idx (section 3.1; form 0 implicit, 1 semi-implicit,
+// 2 explicit).  cp holds the adjoints of the levels after the step by role (cur, prev);
+// the adjoints of the levels before it are written into the other buffer of each pair
+// (cur into prev, prev into cur), so the host swaps each pair after the launch, the
+// mirror of the forward's swap.  The particles' phi~ = (phi^{n+3/2} + phi^{n+1/2})/2.
+__device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const CdfParams& cp, int idx,
+                                       double kx, double ky, const zd* za, const zd* zb) {
+    auto L = [&](void* p) { return zl(reinterpret_cast<const double2*>(p) + idx); };
+    auto S = [&](void* p, zd v) { zs(reinterpret_cast<double2*>(p) + idx, v); };
+    zd phic, axc, ayc;
+    gathered_adjoints(mc, kx, ky, za, zb, phic, axc, ayc);
+    const zd phin = L(cp.phi) + 0.5 * phic;   // phi^{n+3/2}
+    zd phih = L(cp.phi_prev) + 0.5 * phic;    // phi^{n+1/2}
+    zd rhon = L(cp.rho), rhoh = L(cp.rho_prev);
+    const zd axn = L(cp.ax) + axc, ayn = L(cp.ay) + ayc;  // A^{n+1}
+    zd axh = L(cp.ax_prev), ayh = L(cp.ay_prev);          // A^n
+    zd jxn = L(cp.jx), jyn = L(cp.jy);                    // J^{n+1} (this step's)
+    zd jxh = L(cp.jx_prev), jyh = L(cp.jy_prev);          // J^n
+    zd rhop{0.0, 0.0}, jxp{0.0, 0.0}, jyp{0.0, 0.0};      // the oldest levels read
+    const double dt = mc.dt, h2 = mc.c * mc.c * dt * dt;
+    if (cp.form == 0) {
+        // u^{n+1} = inv (2 u^n + th (S^{n+1} + S^{n-1})) - u^{n-1}, th = c^2 dt^2 / 2
+        const double inv = mc.invd[idx], ts = inv * 0.5 * h2;
+        phih = phih + (2.0 * inv) * phin;
+        rhon = rhon + (ts / mc.eps0) * phin;
+        rhop = (ts / mc.eps0) * phin;
+        axh = axh + (2.0 * inv) * axn;
+        ayh = ayh + (2.0 * inv) * ayn;
+        jxn = jxn + (ts * mc.mu0) * axn;
+        jyn = jyn + (ts * mc.mu0) * ayn;
+        jxp = (ts * mc.mu0) * axn;
+        jyp = (ts * mc.mu0) * ayn;
+    } else {
+        // semi: u^{n+1} = inv (2 u^n + c^2 dt^2 S^n) - u^{n-1};
+        // explicit: u^{n+1} = (2 - c^2 dt^2 K) u^n - u^{n-1} + c^2 dt^2 S^n
+        const double K = kx * kx + ky * ky;
+        const double inv = cp.form == 1 ? mc.invd[idx] : 1.0;
+        const double mu = cp.form == 1 ? 2.0 * inv : 2.0 - h2 * K, ss = inv * h2;
+        phih = phih + mu * phin;
+        rhoh = rhoh + (ss / mc.eps0) * phin;
+        axh = axh + mu * axn;
+        ayh = ayh + mu * ayn;
+        jxh = jxh + (ss * mc.mu0) * axn;
+        jyh = jyh + (ss * mc.mu0) * ayn;
+    }
+    // rho^{n+3/2} = rho^{n+1/2} - dt i k . J^{n+1}
+    rhoh = rhoh + rhon;
+    jxn = jxn + zi(dt * kx * rhon);
+    jyn = jyn + zi(dt * ky * rhon);
+    S(cp.phi_prev, phih);
+    S(cp.phi, -phin);
+    S(cp.rho_prev, rhoh);
+    S(cp.rho, rhop);
+    S(cp.ax_prev, axh);
+    S(cp.ax, -axn);
+    S(cp.ay_prev, ayh);
+    S(cp.ay, -ayn);
+    S(cp.jx_prev, jxh);
+    S(cp.jx, jxp);
+    S(cp.jy_prev, jyh);
+    S(cp.jy, jyp);
+    return mc.jscale * (jxn + zi(jyn));
+}
+
+// The real 2 x 4 matrix of one DIRK wave step of a mode: (u', v') = M (u, v, S^n, S^{n+1}),
+// by running the forward stage recurrence (section 3.3.1, the same closed-form stage
+// solve as the forward) on the four unit inputs; the map is linear with real
+// coefficients, so this is its Jacobian exactly.
+__device__ __forceinline__ void dirk_matrix(const DirkParams& dp, double K, double c, double h,
+                                            const double* dinv, size_t stride, double M[2][4]) {
+    const double c2 = c * c;
+#pragma unroll 1
+    for (int col = 0; col < 4; ++col) {
+        const double u = col == 0, v = col == 1, sn = col == 2, snew = col == 3;
+        double ku[kMaxDirk], kv[kMaxDirk];
+        double uo = u, vo = v;
+        for (int i = 0; i < dp.s; ++i) {
+            double ub = u, vb = v;
+            for (int j = 0; j < i; ++j) {
+                ub += (h * dp.a[i * kMaxDirk + j]) * ku[j];
+                vb += (h * dp.a[i * kMaxDirk + j]) * kv[j];
+            }
+            const double src = (1.0 - dp.c[i]) * sn + dp.c[i] * snew;
+            const double gam = h * dp.a[i * kMaxDirk + i];
+            const double d = dinv[i * stride];
+            const double force = c2 * (src - K * ub);
+            ku[i] = d * (vb + gam * force);
+            kv[i] = d * (force - (gam * c2 * K) * vb);
+        }
+        for (int i = 0; i < dp.s; ++i) {
+            uo += (h * dp.b[i]) * ku[i];
+            vo += (h * dp.b[i]) * kv[i];
+        }
+        M[0][col] = uo;
+        M[1][col] = vo;
+    }
+}
+
+// Reverse DIRK field step of mode idx (section 3.3): dp's state pointers hold the
+// adjoints of the state after the step (phi, v_phi, A, v_A, rho, J^{n+1}), overwritten in
+// place with those of the state before it (J^n in the J slots).
+__device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const DirkParams& dp, int idx,
+                                       double kx, double ky, const zd* za, const zd* zb) {
+    auto L = [&](void* p) { return zl(reinterpret_cast<const double2*>(p) + idx); };
+    auto S = [&](void* p, zd v) { zs(reinterpret_cast<double2*>(p) + idx, v); };
+    zd phic, axc, ayc;
+    gathered_adjoints(mc, kx, ky, za, zb, phic, axc, ayc);
+    double M[2][4];
+    dirk_matrix(dp, kx * kx + ky * ky, mc.c, mc.dt, mc.invd + idx, (size_t)mc.nx * mc.ny, M);
+    const zd phiu = L(dp.phi) + phic, phiv = L(dp.vphi);
+    const zd axu = L(dp.ax) + axc, axv = L(dp.vax);
+    const zd ayu = L(dp.ay) + ayc, ayv = L(dp.vay);
+    // transpose: input i gets M[0][i] u_bar' + M[1][i] v_bar'
+    S(dp.phi, M[0][0] * phiu + M[1][0] * phiv);
+    S(dp.vphi, M[0][1] * phiu + M[1][1] * phiv);
+    S(dp.ax, M[0][0] * axu + M[1][0] * axv);
+    S(dp.vax, M[0][1] * axu + M[1][1] * axv);
+    S(dp.ay, M[0][0] * ayu + M[1][0] * ayv);
+    S(dp.vay, M[0][1] * ayu + M[1][1] * ayv);
+    // phi's sources rho^n/eps0 and rho^{n+1}/eps0; A's mu0 J^n and mu0 J^{n+1}
+    const zd rhon = L(dp.rho) + (M[0][3] / mc.eps0) * phiu + (M[1][3] / mc.eps0) * phiv;
+    // rho^{n+1} = rho^n - dt (r0 i k . J^n + r1 i k . J^{n+1})
+    S(dp.rho, rhon + (M[0][2] / mc.eps0) * phiu + (M[1][2] / mc.eps0) * phiv);
+    const double dt = mc.dt;
+    const zd jxn = L(dp.jx) + mc.mu0 * (M[0][3] * axu + M[1][3] * axv) + zi(dt * dp.r1 * kx * rhon);
+    const zd jyn = L(dp.jy) + mc.mu0 * (M[0][3] * ayu + M[1][3] * ayv) + zi(dt * dp.r1 * ky * rhon);
+    S(dp.jx, mc.mu0 * (M[0][2] * axu + M[1][2] * axv) + zi(dt * dp.r0 * kx * rhon));
+    S(dp.jy, mc.mu0 * (M[0][2] * ayu + M[1][2] * ayv) + zi(dt * dp.r0 * ky * rhon));
+    return mc.jscale * (jxn + zi(jyn));
+}
+
 // One thread per mode over the transformed planes Zb (four planes of nx ny).
+template <typename Params>
 __global__ void __launch_bounds__(kModeThreads)
-k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
-                double2* __restrict__ Js) {
+k_adj_modes(ModeCommon mc, Params ap, const double2* __restrict__ Zb, double2* __restrict__ Js) {
     const int ng = mc.nx * mc.ny;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ng) return;
@@ -301,8 +444,9 @@ k_adj_modes_bdf(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
 // of the four row-transformed planes, transforms them along x in shared memory, updates
 // the modes of column j and transforms column j of the adjoint current back along x;
 // the caller finishes with the inverse transform along y.
+template <typename Params>
 __global__ void __launch_bounds__(kModeThreads)
-k_adj_columns(ModeCommon mc, AdjModeParams ap, const double2* __restrict__ Zb,
+k_adj_columns(ModeCommon mc, Params ap, const double2* __restrict__ Zb,
               double2* __restrict__ Js, FftDesc fd, const double2* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = mc.nx, ny = mc.ny;
@@ -490,22 +634,41 @@ cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
-                                 double2* Js, cudaStream_t s) {
-    k_adj_modes_bdf<<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, ap, Zb, Js);
+template <typename Params>
+cudaError_t adj_modes(const ModeCommon& mc, const Params& ap, const double2* Zb, double2* Js,
+                      cudaStream_t s) {
+    k_adj_modes<Params><<<mode_blocks(mc), kModeThreads, 0, s>>>(mc, ap, Zb, Js);
     return cudaGetLastError();
+}
+
+cudaError_t launch_adj_modes(const ModeCommon& mc, int kind, const AdjModeParams& ap,
+                             const CdfParams& cp, const DirkParams& dp, const double2* Zb,
+                             double2* Js, cudaStream_t s) {
+    if (kind == K_CDF2) return adj_modes(mc, cp, Zb, Js, s);
+    if (kind == K_DIRK) return adj_modes(mc, dp, Zb, Js, s);
+    return adj_modes(mc, ap, Zb, Js, s);
 }
 
 size_t adj_columns_smem(int nx) { return 17 * (size_t)nx * sizeof(double2); }
 
-cudaError_t launch_adj_columns(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
-                               double2* Js, const FftDesc& fd, const double2* tw, cudaStream_t s) {
+template <typename Params>
+cudaError_t adj_columns(const ModeCommon& mc, const Params& ap, const double2* Zb, double2* Js,
+                        const FftDesc& fd, const double2* tw, cudaStream_t s) {
     const size_t sm = adj_columns_smem(mc.nx);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_columns, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_columns<Params>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_adj_columns<<<mc.ny, kModeThreads, sm, s>>>(mc, ap, Zb, Js, fd, tw);
+    k_adj_columns<Params><<<mc.ny, kModeThreads, sm, s>>>(mc, ap, Zb, Js, fd, tw);
     return cudaGetLastError();
+}
+
+cudaError_t launch_adj_columns(const ModeCommon& mc, int kind, const AdjModeParams& ap,
+                               const CdfParams& cp, const DirkParams& dp, const double2* Zb,
+                               double2* Js, const FftDesc& fd, const double2* tw,
+                               cudaStream_t s) {
+    if (kind == K_CDF2) return adj_columns(mc, cp, Zb, Js, fd, tw, s);
+    if (kind == K_DIRK) return adj_columns(mc, dp, Zb, Js, fd, tw, s);
+    return adj_columns(mc, ap, Zb, Js, fd, tw, s);
 }
 
 cudaError_t launch_adj_seed(const ModeCommon& mc, const double2* zs_, double2* ax, double2* ay,

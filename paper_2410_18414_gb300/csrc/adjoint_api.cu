@@ -1,18 +1,22 @@
 // Host side of the adjoint API (include/pic.h): checkpoints of the forward run, the
-// segment-by-segment recomputation and the reverse sweep of the FP64 BDF-k step.
+// segment-by-segment recomputation and the reverse sweep of the FP64 step (BDF-k, the
+// three CDF-2 forms or DIRK).
 //
 // Storage (all FP64, device):
 //   state     the eight particle arrays of one time level, in the order x, y, Px, Py,
 //             v^n (x, y), v^{n-1} (x, y): 8 n values
-//   ck[c]     checkpoint c: the state at step c K, the BDF ring contents in slot order
-//             and the ring heads; ck[nseg] is the end of the run, with the last step's
-//             J and gather fields, so the handle can be put back after the sweep
+//   ck[c]     checkpoint c: the state at step c K and the field history (BDF: the ring
+//             contents in slot order and the ring heads; CDF-2, DIRK: the levels by
+//             role); ck[nseg] is the end of the run, with the last step's J and gather
+//             fields, so the handle can be put back after the sweep
 //   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1)
 //   records   per step (every step in the replay mode, the segment's in the recompute
 //             mode): the gather fields the step used (recg) and recf: P^{n+1}, v^{n+1} and
 //             the gathered A and grad A of each particle (10 n)
-//   adjoint   particle adjoints (8 n), the history adjoints (3 L + k spectra, slot of
-//             time level t = t mod L), field-adjoint planes and transform scratch
+//   adjoint   particle adjoints (8 n), the history adjoints (BDF: 3 L + k spectra, slot
+//             of time level t = t mod L; CDF-2: 12 by role, each (cur, prev) pair swapped
+//             after every reverse step; DIRK: 9 by role, in place), field-adjoint planes
+//             and transform scratch
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,10 +33,12 @@ struct pic_adjoint {
     pic_handle* h = nullptr;
     int32_t nsteps = 0, K = 0, nseg = 0;
     int L = 0, Lr = 0;
+    int kind = K_BDF;  // StepperKind of the handle
+    int nh = 0;        // history spectra: 3 L + Lr (BDF), 12 (CDF-2), 9 (DIRK)
     size_t n = 0, ng = 0;
     struct Ck {
         double* state = nullptr;
-        double2* hist = nullptr;  // (3 L + Lr) spectra, slot order
+        double2* hist = nullptr;  // nh spectra, slot or role order
         int head = 0, head_r = 0;
         int64_t step = 0;
     };
@@ -45,7 +51,8 @@ struct pic_adjoint {
     int seg_held = -1;           // segment whose states rec holds
     int mode = 0;                // PIC_ADJ_REPLAY or PIC_ADJ_RECOMPUTE
     double* ab = nullptr;        // particle adjoints, 8 n
-    double2* hb = nullptr;       // history adjoints, (3 L + Lr) ng
+    double2* hb = nullptr;       // history adjoints, nh ng
+    double2* role[12] = {};      // CDF-2, DIRK: the history adjoint of each role
     double2* fb = nullptr;       // field-adjoint planes, 4 ng
     double2* zb = nullptr;       // their transforms, 4 ng
     double2* js = nullptr;       // adjoint current spectrum, ng
@@ -82,8 +89,19 @@ void handle_arrays(pic_handle* h, void* arr[8]) {
     arr[7] = h->v[1 - h->vcur][1];
 }
 
+// The field history of the handle: the BDF ring slots, or the CDF-2 and DIRK levels in
+// role order (the buffer now in each role: CDF-2 swaps pairs every step).
 std::vector<void*> ring_slots(pic_handle* h) {
     std::vector<void*> s;
+    if (h->cfg.stepper == PIC_STEPPER_CDF2) {
+        const CdfParams& c = h->cdf;
+        return {c.phi, c.phi_prev, c.rho, c.rho_prev, c.ax, c.ax_prev,
+                c.ay,  c.ay_prev,  c.jx,  c.jx_prev,  c.jy, c.jy_prev};
+    }
+    if (h->cfg.stepper == PIC_STEPPER_DIRK) {
+        const DirkParams& d = h->dirk;
+        return {d.phi, d.vphi, d.ax, d.vax, d.ay, d.vay, d.rho, d.jx, d.jy};
+    }
     for (void* p : h->phi_l) s.push_back(p);
     for (void* p : h->ax_l) s.push_back(p);
     for (void* p : h->ay_l) s.push_back(p);
@@ -197,24 +215,41 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const doub
     const bool fused = adj_columns_smem(h->nx) <= kFieldColumnsSmemMax;
     if (!fused) CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
     AdjModeParams ap{};
-    ap.k = h->bdf.k;
-    for (int i = 0; i <= ap.k; ++i) ap.a[i] = h->bdf.a[i];
-    for (int d = 0; d <= 2 * ap.k; ++d) ap.C[d] = h->bdf.C[d];
-    ap.g = h->bdf.g;
-    ap.bdt = h->bdf.bdt;
-    for (int d = 0; d < a->L; ++d) {
-        ap.phi[d] = hist_slot(a, 0, n + 1 - d);
-        ap.ax[d] = hist_slot(a, 1, n + 1 - d);
-        ap.ay[d] = hist_slot(a, 2, n + 1 - d);
+    CdfParams cp{};
+    DirkParams dp{};
+    if (a->kind == K_BDF) {
+        ap.k = h->bdf.k;
+        for (int i = 0; i <= ap.k; ++i) ap.a[i] = h->bdf.a[i];
+        for (int d = 0; d <= 2 * ap.k; ++d) ap.C[d] = h->bdf.C[d];
+        ap.g = h->bdf.g;
+        ap.bdt = h->bdf.bdt;
+        for (int d = 0; d < a->L; ++d) {
+            ap.phi[d] = hist_slot(a, 0, n + 1 - d);
+            ap.ax[d] = hist_slot(a, 1, n + 1 - d);
+            ap.ay[d] = hist_slot(a, 2, n + 1 - d);
+        }
+        for (int d = 0; d < a->Lr; ++d) ap.rho[d] = hist_slot(a, 3, n + 1 - d);
+    } else if (a->kind == K_CDF2) {
+        cp.form = h->cdf.form;
+        void** roles[12] = {&cp.phi, &cp.phi_prev, &cp.rho, &cp.rho_prev, &cp.ax, &cp.ax_prev,
+                            &cp.ay,  &cp.ay_prev,  &cp.jx,  &cp.jx_prev,  &cp.jy, &cp.jy_prev};
+        for (int r = 0; r < 12; ++r) *roles[r] = a->role[r];
+    } else {
+        dp = h->dirk;  // the stage table; the state pointers become the adjoints
+        void** roles[9] = {&dp.phi, &dp.vphi, &dp.ax, &dp.vax, &dp.ay, &dp.vay, &dp.rho, &dp.jx, &dp.jy};
+        for (int r = 0; r < 9; ++r) *roles[r] = a->role[r];
     }
-    for (int d = 0; d < a->Lr; ++d) ap.rho[d] = hist_slot(a, 3, n + 1 - d);
     if (fused) {
-        CK(launch_adj_columns(h->mc, ap, a->zb, a->js, h->fx, (const double2*)h->twx, h->s));
+        CK(launch_adj_columns(h->mc, a->kind, ap, cp, dp, a->zb, a->js, h->fx,
+                              (const double2*)h->twx, h->s));
         CK(launch_fft_y<double>(a->js, a->jg, h->nx, h->ny, 1, h->fy, h->twy, +1, 0, h->s));
     } else {
-        CK(launch_adj_modes_bdf(h->mc, ap, a->zb, a->js, h->s));
+        CK(launch_adj_modes(h->mc, a->kind, ap, cp, dp, a->zb, a->js, h->s));
         CK(inverse_fft(h, a->js, a->jg, 1));
     }
+    // CDF-2: the adjoints before the step were written into the other buffer of each pair
+    if (a->kind == K_CDF2)
+        for (int r = 0; r < 12; r += 2) std::swap(a->role[r], a->role[r + 1]);
     tf.end();
     TimedScope td(h, PIC_KT_ADJ_DEPOSIT);
     CK(launch_adj_deposit_move(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np, a->jg, ab,
@@ -239,11 +274,11 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     *out = nullptr;
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 1) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 1");
-    if (h->fp32 || h->cfg.stepper != PIC_STEPPER_BDF || h->cfg.charge != PIC_CHARGE_CONTINUITY ||
-        h->sorting || h->vdim == 3 || h->spp.n > 0)
+    if (h->fp32 || h->cfg.charge != PIC_CHARGE_CONTINUITY || h->sorting || h->vdim == 3 ||
+        h->spp.n > 0)
         return fail(h, PIC_ERR_UNSUPPORTED,
-                    "the adjoint needs the FP64 path, the BDF-k stepper, the continuity charge, "
-                    "one species in 2D-2V and no sorting");
+                    "the adjoint needs the FP64 path, the continuity charge, one species in "
+                    "2D-2V and no sorting");
     if (h->step != 0 || h->phase != 0)
         return fail(h, PIC_ERR_STATE, "the adjoint needs a handle fresh from pic_init");
     pic_adjoint* a = new pic_adjoint();
@@ -255,10 +290,13 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     const size_t nrec = mode == PIC_ADJ_REPLAY ? (size_t)nsteps : (size_t)a->K;
     a->L = h->L;
     a->Lr = h->Lr;
+    a->kind = h->cfg.stepper == PIC_STEPPER_BDF ? K_BDF
+              : h->cfg.stepper == PIC_STEPPER_CDF2 ? K_CDF2 : K_DIRK;
+    a->nh = a->kind == K_BDF ? 3 * a->L + a->Lr : a->kind == K_CDF2 ? 12 : 9;
     a->n = (size_t)h->n;
     a->ng = h->ng;
     const size_t sb = 8 * std::max<size_t>(a->n, 1) * sizeof(double);
-    const size_t hbytes = (size_t)(3 * a->L + a->Lr) * a->ng * sizeof(double2);
+    const size_t hbytes = (size_t)a->nh * a->ng * sizeof(double2);
     const size_t gb = a->ng * sizeof(double2);
     cudaError_t e = cudaSuccess;
     a->ck.resize(a->nseg + 1);
@@ -281,7 +319,8 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->e0, gb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->tmp, gb);
     // E^0 = -grad phi^0 on the mesh (every phi level holds phi^0 at step 0)
-    if (e == cudaSuccess) e = launch_adj_e0(h->mc, (const double2*)h->phi_l[h->head], a->tmp, h->s);
+    const void* phi0 = a->kind == K_BDF ? h->phi_l[h->head] : a->kind == K_CDF2 ? h->cdf.phi : h->dirk.phi;
+    if (e == cudaSuccess) e = launch_adj_e0(h->mc, (const double2*)phi0, a->tmp, h->s);
     if (e == cudaSuccess) e = inverse_fft(h, a->tmp, a->e0, 1);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) {
@@ -332,15 +371,23 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
     if (!a->forward_done) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward needs pic_adjoint_forward");
     if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward inside a step");
     const size_t np = a->n, ng = a->ng;
-    const size_t hbytes = (size_t)(3 * a->L + a->Lr) * ng * sizeof(double2);
+    const size_t hbytes = (size_t)a->nh * ng * sizeof(double2);
     CK(cudaMemsetAsync(a->ab, 0, 8 * std::max<size_t>(np, 1) * sizeof(double), h->s));
     CK(cudaMemsetAsync(a->hb, 0, hbytes, h->s));
+    if (a->kind != K_BDF)
+        for (int r = 0; r < a->nh; ++r) a->role[r] = a->hb + (size_t)r * ng;
     if (px_bar && np) CK(cudaMemcpyAsync(a->ab + 2 * np, px_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
     if (py_bar && np) CK(cudaMemcpyAsync(a->ab + 3 * np, py_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
     if (bz_bar) {
         CK(launch_real_to_cplx(bz_bar, a->tmp, (int64_t)ng, h->s));
         CK(forward_fft(h, a->tmp, a->js));
-        CK(launch_adj_seed(h->mc, a->js, hist_slot(a, 1, a->nsteps), hist_slot(a, 2, a->nsteps), h->s));
+        // the newest A: the BDF ring slot of the last level, else the A role (CDF-2: 4, 6;
+        // DIRK: 2, 4)
+        double2* sax = a->kind == K_BDF ? hist_slot(a, 1, a->nsteps)
+                       : a->role[a->kind == K_CDF2 ? 4 : 2];
+        double2* say = a->kind == K_BDF ? hist_slot(a, 2, a->nsteps)
+                       : a->role[a->kind == K_CDF2 ? 6 : 4];
+        CK(launch_adj_seed(h->mc, a->js, sax, say, h->s));
     }
     for (int c = a->nseg - 1; c >= 0; --c) {
         const int c0 = seg_begin(a, c), c1 = seg_end(a, c);

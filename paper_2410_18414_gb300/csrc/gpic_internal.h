@@ -340,15 +340,21 @@ cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParam
                                    const double* vxo, const double* vyo, const double* gf,
                                    const double2* F, AdjParticles ab, double2* Fb, int64_t n,
                                    unsigned int* err, cudaStream_t s);
-// Reverse BDF-k field solve per mode: Zb = forward transforms of the four Fb planes;
+// Reverse field solve per mode of the stepper `kind` (a StepperKind: ap, cp or dp used,
+// their pointers the history adjoints): Zb = forward transforms of the four Fb planes;
 // writes the packed adjoint current spectrum Js (unnormalised inverse transform -> mesh).
-cudaError_t launch_adj_modes_bdf(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
-                                 double2* Js, cudaStream_t s);
+// CDF-2 writes the adjoints before the step into the other buffer of each (cur, prev)
+// pair, for the caller to swap; BDF and DIRK update in place.
+cudaError_t launch_adj_modes(const ModeCommon& mc, int kind, const AdjModeParams& ap,
+                             const CdfParams& cp, const DirkParams& dp, const double2* Zb,
+                             double2* Js, cudaStream_t s);
 // Fused column pass of the same (Zb transformed along y only; Js transformed back along x
 // only), when adj_columns_smem(nx) fits kFieldColumnsSmemMax.
 size_t adj_columns_smem(int nx);
-cudaError_t launch_adj_columns(const ModeCommon& mc, const AdjModeParams& ap, const double2* Zb,
-                               double2* Js, const FftDesc& fd, const double2* tw, cudaStream_t s);
+cudaError_t launch_adj_columns(const ModeCommon& mc, int kind, const AdjModeParams& ap,
+                               const CdfParams& cp, const DirkParams& dp, const double2* Zb,
+                               double2* Js, const FftDesc& fd, const double2* tw,
+                               cudaStream_t s);
 // Reverse deposit + move: gathers the mesh current adjoint Jb ([node] (jx, jy)) at x^{n+1}.
 cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
                                     const double* y1, const double* vx, const double* vy,

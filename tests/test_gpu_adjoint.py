@@ -1,9 +1,12 @@
-"""GPU checks of the discrete adjoint (pic_adjoint_*) of the FP64 BDF-k run.
+"""GPU checks of the discrete adjoint (pic_adjoint_*) of the FP64 run.
 
 - Against the oracle's adjoint (oracle.adjoint, pinned on CPU by finite differences
   and transpose identities): small grids, several spline orders and BDF orders, both
   seeds (the magnetic energy W_B and a final-momentum objective), checkpoint intervals
   that leave a ragged last segment.  Measured on GB300: <= 2e-14 relative; bound 1e-11.
+  The same for the three CDF-2 forms and DIRK (Qin-Zhang 2-stage, implicit-midpoint
+  3-stage), in both record modes, with the fused column pass and the separate mode
+  kernel (a grid whose x extent is too large for the column pass's shared memory).
 - Checkpoint-interval invariance: K = 1, 3, N give the same gradient (to the FP64
   atomic-order roundoff of the forward's current deposit).
 - The 128 x 128 Weibel configuration (262,144 particles, v_d = 0.5c, BDF-2, cubic, 200
@@ -25,6 +28,7 @@ import pytest
 
 from oracle import adjoint as oadj
 from oracle import pic as opic
+from oracle import steppers as osteps
 from paper_2410_18414_gb300 import pic, workloads
 
 pytestmark = pytest.mark.gpu
@@ -48,7 +52,7 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-def _case(p, k, nx, ny, n, seed):
+def _case(p, k, nx, ny, n, seed, stepper="bdf", dirk=None, cdf_form="implicit"):
     rng = np.random.default_rng(seed)
     lx, ly = 1.0, 0.8
     x = rng.uniform(0, lx, n)
@@ -58,8 +62,11 @@ def _case(p, k, nx, ny, n, seed):
     vy = sgn * 0.3 + 0.05 * rng.standard_normal(n)
     dt = 0.4 * lx / nx
     w = lx * ly / n
-    cfg = pic.make_config(nx, ny, lx, ly, dt, p=p, stepper="bdf", bdf_order=k, weight=w)
-    ocfg = opic.Config(nx=nx, ny=ny, lx=lx, ly=ly, dt=dt, p=p, stepper="bdf", bdf_order=k, w=w)
+    name = stepper if cdf_form == "implicit" else f"cdf2_{cdf_form}"
+    cfg = pic.make_config(nx, ny, lx, ly, dt, p=p, stepper=name, bdf_order=k, dirk=dirk,
+                          weight=w)
+    ocfg = opic.Config(nx=nx, ny=ny, lx=lx, ly=ly, dt=dt, p=p, stepper=stepper, bdf_order=k,
+                       w=w, dirk=dirk, cdf_form=cdf_form)
     return cfg, ocfg, x, y, vx, vy
 
 
@@ -104,6 +111,40 @@ def test_adjoint_matches_oracle(device, p, k, nx, ny, n, nsteps, K):
     assert max(errs.values()) <= 1e-11, errs
 
 
+OTHER = [
+    ("cdf2-implicit", dict(stepper="cdf2"), 3, 32, 24, 3000, 9, 4, "replay"),
+    ("cdf2-semi", dict(stepper="cdf2", cdf_form="semi"), 2, 24, 16, 2000, 9, 4, "recompute"),
+    # explicit form: c dt |k|_max = 1.7 < 2, inside its stability limit
+    ("cdf2-explicit", dict(stepper="cdf2", cdf_form="explicit"), 4, 16, 12, 2000, 8, 3, "replay"),
+    ("dirk2", dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG), 3, 32, 32, 3000, 9, 4, "replay"),
+    ("dirk3", dict(stepper="dirk", dirk=osteps.DIRK3_MIDPOINT), 2, 24, 24, 2000, 8, 3,
+     "recompute"),
+    # nx = 1024 exceeds the column pass's shared memory (17 nx complex values): the
+    # separate mode kernel runs
+    ("cdf2-wide", dict(stepper="cdf2"), 2, 1024, 8, 3000, 4, 2, "replay"),
+    ("dirk2-wide", dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG), 2, 1024, 8, 3000, 4, 2,
+     "replay"),
+]
+
+
+@pytest.mark.parametrize("name,kw,p,nx,ny,n,nsteps,K,mode", OTHER, ids=[c[0] for c in OTHER])
+def test_cdf2_and_dirk_adjoint_match_oracle(device, name, kw, p, nx, ny, n, nsteps, K, mode):
+    cfg, ocfg, x, y, vx, vy = _case(p, 1, nx, ny, n, seed=len(name), **kw)
+    tape = oadj.record(ocfg, x, y, vx, vy, nsteps)
+    expect = oadj.gradient(tape)
+    wb, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, mode=mode)
+    assert abs(wb / oadj.magnetic_energy(ocfg, tape.final) - 1.0) <= 1e-12
+    errs = {"vx": rel(got["vx"], expect["v0"][0]), "vy": rel(got["vy"], expect["v0"][1]),
+            "px": rel(got["px"], expect["p0"][0]), "py": rel(got["py"], expect["p0"][1])}
+    assert max(errs.values()) <= 1e-11, errs
+    rng = np.random.default_rng(31)
+    pb = (rng.standard_normal(n), rng.standard_normal(n))
+    expect = oadj.gradient(tape, px_bar=pb[0], py_bar=pb[1])
+    _, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, pb=pb, mode=mode)
+    errs = {"vx": rel(got["vx"], expect["v0"][0]), "vy": rel(got["vy"], expect["v0"][1])}
+    assert max(errs.values()) <= 1e-11, errs
+
+
 @pytest.mark.parametrize("mode", ["replay", "recompute"])
 def test_checkpoint_interval_invariance(device, mode):
     # the replay mode rebuilds the particle states between checkpoints from the recorded
@@ -137,7 +178,7 @@ def test_handle_left_at_end_of_forward_run(device):
 
 def test_adjoint_rejects_unsupported_handles(device):
     cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 512, seed=5)
-    for kw in (dict(precision=pic.FP32_FIX64), dict(stepper="cdf2"), dict(sort_interval=4),
+    for kw in (dict(precision=pic.FP32_FIX64), dict(sort_interval=4),
                dict(charge=pic.CHARGE_DEPOSIT)):
         args = dict(p=3, stepper="bdf", bdf_order=2, weight=cfg.weight)
         args.update(kw)
