@@ -6,7 +6,8 @@ s-stage DIRK of section 3.3), so it is pinned by things fixed outside it:
   * spline derivatives against the closed-form B-spline polynomials (differentiated by
     hand for p = 2, by central differences for p = 3, 4) and their zero sum;
   * exact transpose identities of the linear pieces (scatter vs gather; the whole field
-    solve against oracle.pic.field_solve by the dot-product test);
+    solve against oracle.pic.field_solve by the dot-product test), which a dropped term,
+    a flipped sign of i k or exchanged DIRK source columns planted in the adjoint break;
   * gradients of the full run against central finite differences of oracle.pic.run,
     for W_B = 1/2 sum B_z^2 dx dy and for the final momenta, per component and along
     random directions, for both v^0 and P^0 as the independent variable;
@@ -183,6 +184,63 @@ def test_cdf2_and_dirk_field_adjoints_are_transposes(name, kw):
         l1 = _pair_hist(zero_out, st.hist)
         r1 = _pair_hist(hb, h_in) + float(np.sum(jxb1 * jx) + np.sum(jyb1 * jy))
         assert abs(l1 - r1) <= 1e-12 * (abs(l1) + abs(r1) + 1.0), (key, l1, r1)
+
+
+def _identity_gap(cfg, seed, adjoint=None):
+    """(lhs - rhs, scale) of the dot-product identity of one field solve and its adjoint
+    on random histories, currents and field adjoints."""
+    rng = np.random.default_rng(seed)
+    st = opic.initial_state(cfg, *_beams(8, seed=1))
+    st.hist = _random_hist(rng, cfg, st.hist)
+    h_in = {key: ([v.copy() for v in val] if isinstance(val, list) else val.copy())
+            for key, val in st.hist.items()}
+    jx = rng.standard_normal((cfg.nx, cfg.ny))
+    jy = rng.standard_normal((cfg.nx, cfg.ny))
+    fields = opic.field_solve(cfg, st, jx, jy)
+    hbar_out = _random_hist(rng, cfg, st.hist)
+    fbar = {f: rng.standard_normal((cfg.nx, cfg.ny)) for f in opic.FIELD_NAMES}
+    if adjoint is None:
+        adjoint = oadj.field_adjoint_cdf2 if cfg.stepper == "cdf2" else oadj.field_adjoint_dirk
+    hbar_in, (jxb, jyb) = adjoint(cfg, hbar_out, fbar)
+    lhs = _pair_hist(hbar_out, st.hist) + sum(float(np.sum(fbar[f] * fields[f]))
+                                              for f in opic.FIELD_NAMES)
+    rhs = _pair_hist(hbar_in, h_in) + float(np.sum(jxb * jx) + np.sum(jyb * jy))
+    return lhs - rhs, abs(lhs) + abs(rhs)
+
+
+def test_planted_adjoint_mistakes_break_the_identity(monkeypatch):
+    # the dot-product identity is the adjoints' pin: each plausible mistake, planted in a
+    # copy of the oracle's adjoint, must break it by far more than its 1e-12 tolerance
+    cfg = _cfg(stepper="cdf2", cdf_form="implicit")
+    gap, scale = _identity_gap(cfg, 5)
+    assert abs(gap) <= 1e-12 * scale
+
+    def dropped_term(c, hb, fb):  # the implicit form's rho^{n-1} source left out
+        out, j = oadj.field_adjoint_cdf2(c, hb, fb)
+        out["rho_prev"] = np.zeros_like(out["rho_prev"])
+        return out, j
+    gap, scale = _identity_gap(cfg, 5, dropped_term)
+    assert abs(gap) > 1e-6 * scale
+
+    def wrong_sign(c, hb, fb):  # conj(i k) taken as +i k (every k flipped in the adjoint)
+        with monkeypatch.context() as m:
+            kgrid = spectral.wavenumber_grid
+            m.setattr(spectral, "wavenumber_grid",
+                      lambda *a: (lambda kx, ky, K: (-kx, -ky, K))(*kgrid(*a)))
+            return oadj.field_adjoint_cdf2(c, hb, fb)
+    gap, scale = _identity_gap(cfg, 5, wrong_sign)
+    assert abs(gap) > 1e-6 * scale
+
+    # DIRK: the S^n and S^{n+1} columns of the stage matrix exchanged (an index mistake)
+    dcfg = _cfg(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG)
+    _, _, K = spectral.wavenumber_grid(dcfg.nx, dcfg.ny, dcfg.lx, dcfg.ly)
+    M = oadj.dirk_matrix(dcfg, K)
+    assert np.max(np.abs(M[0][2] - M[0][3])) > 1e-3 * np.max(np.abs(M[0][2]))
+    good = oadj.dirk_matrix
+    monkeypatch.setattr(oadj, "dirk_matrix",
+                        lambda c, k: [[r[0], r[1], r[3], r[2]] for r in good(c, k)])
+    gap, scale = _identity_gap(dcfg, 6)
+    assert abs(gap) > 1e-6 * scale
 
 
 def test_dirk_matrix_reproduces_the_stage_loop():
