@@ -286,8 +286,8 @@ from paper_2410_18414_gb300 import workloads
 wl = workloads.weibel_adjoint_128()
 n, steps = {n}, {steps}
 w = wl.lx * wl.ly / n
-cfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, stepper="bdf",
-                  bdf_order=2, w=w)
+cfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p, w=w,
+                  **json.loads({stepper_kw!r}))
 args = (cfg, wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n], steps)
 t0 = time.perf_counter(); opic.run(*args); t1 = time.perf_counter()
 tape = oadj.record(*args); oadj.gradient(tape); t2 = time.perf_counter()
@@ -301,7 +301,11 @@ def run_reference_adjoint(a):
     (128 x 128 grid, the first 8192 of its 262,144 particles with the weight rescaled, 10
     steps), as the same ratio."""
     n, steps = 8192, min(10, max(1, a.steps))
-    code = ADJOINT_ORACLE_SNIPPET.format(root=ROOT, n=n, steps=steps)
+    stepper, k = STEPPER_NAMES[a.stepper]
+    kw = dict(stepper=stepper, bdf_order=k)
+    if stepper == "dirk":
+        kw["dirk"] = dirk_tableau(a.stepper)
+    code = ADJOINT_ORACLE_SNIPPET.format(root=ROOT, n=n, steps=steps, stepper_kw=json.dumps(kw))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -317,7 +321,7 @@ def run_reference_adjoint(a):
             "impl": "reference", "n_gpus": a.gpus, "steps": steps, "warmup": 0,
             "ms_per_step": 1e3 * t["gradient_s"] / steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "form": "fp64",
+            "config": {"workload": f"weibel_adjoint_128x128_16ppc_cubic_{a.stepper}", "form": "fp64",
                        "sample_particles": n, "parallelism": "replicas"},
             "cpu_baseline": {"value": ratio, "unit": "ratio", "cores": 1, "kind": "oracle",
                              "sample": sample},
@@ -517,10 +521,10 @@ def run_ensemble(a):
     print(json.dumps(line))
 
 
-def adjoint_timings(steps, reps, rank=0):
+def adjoint_timings(steps, reps, rank=0, stepper="bdf2"):
     """Gradient of the magnetic energy W_B = 1/2 sum B_z^2 dx dy after `steps` (at most 200)
-    steps of the 128x128 Weibel run with 16 particles per cell (262,144), FP64, BDF-2,
-    cubic, with respect to every initial velocity and momentum, by the library's adjoint.
+    steps of the 128x128 Weibel run with 16 particles per cell (262,144), FP64, cubic,
+    under `stepper` (a STEPPER_NAMES key; BDF-2 by default), with respect to every initial velocity and momentum, by the library's adjoint.
     Timed per whole run with CUDA events (L2 flushed before each run): the plain forward
     run (pic_step), the recording forward run and the reverse sweep, with checkpoints every
     20 steps -- replaying the particle states of each segment from the recorded gathered
@@ -531,8 +535,7 @@ def adjoint_timings(steps, reps, rank=0):
     from paper_2410_18414_gb300 import pic, workloads
     pic.load_library()
     wl = workloads.weibel_adjoint_128(seed=5 + rank)
-    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf", bdf_order=2,
-                          weight=wl.weight)
+    cfg = make_config(wl, stepper)
     N = min(wl.nsteps, steps)
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
@@ -597,7 +600,7 @@ def adjoint_timings(steps, reps, rank=0):
     rall = (med([t[0] for t in tall]) + med([t[1] for t in tall])) / fwd
     seg = (N + k20 - 1) // k20
     return {
-        "workload": "weibel_adjoint_128x128_16ppc_cubic_bdf2", "particles": wl.n,
+        "workload": f"weibel_adjoint_128x128_16ppc_cubic_{stepper}", "particles": wl.n,
         "steps_per_run": N, "form": "fp64", "objective": "W_B at the last step",
         "forward_ms": fwd,
         "checkpoint_20": {"mode": "replay", "record_forward_ms": med([t[0] for t in t20]),
@@ -626,7 +629,7 @@ def run_adjoint(a):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    t = adjoint_timings(a.steps, max(1, a.repeats), rank)
+    t = adjoint_timings(a.steps, max(1, a.repeats), rank, a.stepper)
     clk = clocks.stop()
     if rank != 0:
         return
