@@ -72,6 +72,56 @@ WORKLOADS = {
 }
 
 
+class Ranks:
+    """The ranks of a torchrun launch (RANK, WORLD_SIZE, LOCAL_RANK): every rank runs an
+    independent replica, so the only collectives are the barriers around a timed region
+    and the max of its duration over ranks.  With one rank both are local no-ops.
+    backend/device: "nccl"/"cuda" on the GPU box, "gloo"/"cpu" for the CPU tests."""
+
+    def __init__(self, backend="nccl", device="cuda"):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def _sync(self):
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+
+    def barrier(self):
+        """Synchronize the device, wait for every rank, synchronize again."""
+        self._sync()
+        if self.dist:
+            self.dist.barrier()
+        self._sync()
+
+    def max(self, value):
+        """The largest of the ranks' values (a float)."""
+        if not self.dist:
+            return float(value)
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_per_rank, world, steps, max_ms):
+    """Units (particle-steps) per second of the whole job: every rank's units over the
+    slowest rank's time."""
+    return units_per_rank * world * steps / (max_ms * 1e-3)
+
+
 def make_workload(name, rank=0):
     from paper_2410_18414_gb300 import workloads
     w = WORKLOADS[name]
@@ -414,9 +464,9 @@ def run_ensemble(a):
     streams without the graph are timed beside it."""
     import torch
     from paper_2410_18414_gb300 import autotune, pic, workloads
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
+    rank, world = ranks.rank, ranks.world
     pic.load_library()
     specs = workloads.ensemble_specs(seed0=1000 + 256 * rank)
     t0 = time.perf_counter()
@@ -452,8 +502,8 @@ def run_ensemble(a):
     full, rest = (steps // P) * P, steps % P
     warm = max(1, -(-a.warmup // P)) * P       # whole periods keep the runs in phase
     ens.step(warm)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    ranks.barrier()
+    clocks = ClockSampler(ranks.local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(master)
@@ -465,7 +515,8 @@ def run_ensemble(a):
     e1.record(master)
     e1.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ranks.barrier()
+    ms = ranks.max(e0.elapsed_time(e1))
     ens.close()
     for s in sims:
         s.sync()  # reports any latched device error
@@ -474,8 +525,7 @@ def run_ensemble(a):
     sims, streams = build()
     for s in sims:
         s.step(warm)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    ranks.barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(master)
     for st in streams:         # start after the event above
@@ -485,12 +535,14 @@ def run_ensemble(a):
     join(master, streams)
     f1.record(master)
     f1.synchronize()
-    ms_plain = f0.elapsed_time(f1)
+    ranks.barrier()
+    ms_plain = ranks.max(f0.elapsed_time(f1))
     for s in sims:
         s.close()
+    ranks.close()
     if rank != 0:
         return
-    value = n_total * world * steps / (ms * 1e-3)
+    value = whole_job_rate(n_total, world, steps, ms)
     hist = {}
     for si in sorts:
         hist[str(si)] = hist.get(str(si), 0) + 1
@@ -512,7 +564,7 @@ def run_ensemble(a):
                      "traffic": None, "peak_source": peaks()["hbm_src"],
                      "note": "72 B algorithmic per particle-step (deposit 24 + gather 48)"},
         "no_graph": {"ms_per_step": ms_plain / steps,
-                     "value": n_total * world * steps / (ms_plain * 1e-3),
+                     "value": whole_job_rate(n_total, world, steps, ms_plain),
                      "how": "each run's steps enqueued on its own stream, no graph"},
         "autotune_s": tune_s, "capture_s": capture_s,
         "cpu_baseline": None, "e2e": None,
@@ -624,17 +676,22 @@ def run_adjoint(a):
     """`--workload adjoint128`: the adjoint timings as their own line.  value = (recording
     forward + reverse sweep) / plain forward with checkpoints every 20 steps."""
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
+    rank, world = ranks.rank, ranks.world
+    ranks.barrier()
+    clocks = ClockSampler(ranks.local)
     clocks.start()
     t = adjoint_timings(a.steps, max(1, a.repeats), rank, a.stepper)
     clk = clocks.stop()
+    ranks.barrier()
+    # every replica's own ratio; the line reports the slowest rank's
+    ratio = ranks.max(t["checkpoint_20"]["ratio"])
+    ranks.close()
     if rank != 0:
         return
     line = {
-        "metric": "adjoint/forward time", "value": t["checkpoint_20"]["ratio"], "unit": "ratio",
+        "metric": "adjoint/forward time", "value": ratio, "unit": "ratio",
         "n_gpus": world, "steps": t["steps_per_run"], "warmup": 1, "repeats": max(1, a.repeats),
         "ms_per_step": t["checkpoint_20"]["backward_ms"] / t["steps_per_run"],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -691,14 +748,10 @@ def main():
     import torch
     from paper_2410_18414_gb300 import pic
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks = Ranks()
+    rank, world = ranks.rank, ranks.world
     pic.load_library()
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
@@ -708,27 +761,17 @@ def main():
     cfg = make_config(wl, a.stepper, a.precision, a.sort_interval)
     sim = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    barrier()
+    ranks.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     launches = [0]
     t = time_steps(sim, a.steps, a.warmup, stream, flush, launches)
     clk = clocks.stop()
-    barrier()
+    ranks.barrier()
     sim.sync()
-    total_ms = sum(t["step_ms"])
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = ranks.max(sum(t["step_ms"]))
     n_all = wl.n * world
-    value = n_all * a.steps / (total_ms * 1e-3)
+    value = whole_job_rate(wl.n, world, a.steps, total_ms)
     # phase and per-kernel breakdown: an instrumented run of the same simulation right
     # after the timed region (its extra event records would slow the headline steps)
     nd = min(a.steps, 500)
@@ -829,23 +872,22 @@ def main():
     host = {k: torch.from_numpy(getattr(wl, k).copy()).pin_memory() for k in ("x", "y", "vx", "vy")}
     outs = {k: torch.empty(wl.n, dtype=torch.float64).pin_memory()
             for k in ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old")}
-    torch.cuda.synchronize()
+    ranks.barrier()
     t0 = time.perf_counter()
     s3 = pic.Simulation(cfg, host["x"], host["y"], host["vx"], host["vy"], stream=sp)
     s3.step(a.steps)
     s3.particles(outs)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    ranks.barrier()
     s3.close()
     e2e = {"value": n_all * a.steps / e2e_s if world == 1 else None, "unit": METRIC,
            "h2d_bytes_per_step": 4 * 8 * wl.n / a.steps,
            "d2h_bytes_per_step": 8 * 8 * wl.n / a.steps,
            "includes": "pic_init from pinned host arrays (incl. device allocation and t=0 solve), "
                        "K steps, read-back of all 8 particle arrays"}
-    if dist:
-        ee = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ee, op=dist.ReduceOp.MAX)
-        e2e["value"] = n_all * a.steps / float(ee.item())
+    if world > 1:
+        e2e["value"] = n_all * a.steps / ranks.max(e2e_s)
 
     # the adjoint (the metric's "adjoint/forward time"): the gradient of W_B on the
     # 262,144-particle Weibel workload, FP64, one timed run per checkpoint setting
@@ -890,8 +932,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     sim.close()
-    if dist:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
