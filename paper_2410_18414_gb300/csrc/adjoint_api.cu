@@ -333,6 +333,7 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
 }
 
 pic_status pic_adjoint_forward(pic_adjoint* a) {
+    NvtxRange r("adjoint_forward");
     if (!a) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL adjoint");
     pic_handle* h = a->h;
     if (a->forward_done) return fail(h, PIC_ERR_STATE, "pic_adjoint_forward runs once");
@@ -366,6 +367,7 @@ pic_status pic_adjoint_forward(pic_adjoint* a) {
 pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const double* px_bar,
                                 const double* py_bar, double* dvx0, double* dvy0, double* dpx0,
                                 double* dpy0) {
+    NvtxRange r("adjoint_backward");
     if (!a) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL adjoint");
     pic_handle* h = a->h;
     if (!a->forward_done) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward needs pic_adjoint_forward");

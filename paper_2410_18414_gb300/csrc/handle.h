@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -119,12 +120,32 @@ cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb);
 // Waits for the stream and maps the device error word to a status.
 pic_status check_device_error(pic_handle* h);
 
-// Brackets one launch group with the next event pair of a timer (when timing is on and
-// a pair is left); the stop event is recorded by end() or when the scope ends, early
-// returns included.
+// NVTX ranges of the library, in the domain "gpic" (host-side markers for timeline and
+// profiler tools: nsys, or ncu --nvtx --nvtx-include "gpic@deposit/"); a push without an
+// attached tool is a check of a function pointer.
+nvtxDomainHandle_t nvtx_domain();
+void nvtx_push(const char* name);
+inline void nvtx_pop() { nvtxDomainRangePop(nvtx_domain()); }
+// The range names of the kernel timers (PIC_KT_*): sort, deposit, field_solve,
+// gather_push, adj_push, adj_field, adj_deposit.
+const char* timer_name(int which);
+
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char* name) { nvtx_push(name); }
+    ~NvtxRange() { nvtx_pop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Brackets one launch group with an NVTX range named for the timer and, when timing is
+// on and a pair is left, with the timer's next event pair; the range ends and the stop
+// event is recorded by end() or when the scope ends, early returns included.
 class TimedScope {
   public:
     TimedScope(pic_handle* h, int which) {
+        nvtx_push(timer_name(which));
+        open_ = true;
         if (!h->ktiming) return;
         auto& t = h->kt[which];
         if (t.used >= h->kt_cap || 2 * (t.used + 1) > (int64_t)t.ev.size()) return;
@@ -134,10 +155,12 @@ class TimedScope {
         ++t.used;
     }
     ~TimedScope() { end(); }
-    // Records the stop event now (once).
+    // Records the stop event and ends the range now (once).
     void end() {
         if (stop_) cudaEventRecord(stop_, s_);
         stop_ = nullptr;
+        if (open_) nvtx_pop();
+        open_ = false;
     }
     TimedScope(const TimedScope&) = delete;
     TimedScope& operator=(const TimedScope&) = delete;
@@ -145,6 +168,7 @@ class TimedScope {
   private:
     cudaEvent_t stop_ = nullptr;
     cudaStream_t s_ = nullptr;
+    bool open_ = false;
 };
 
 }  // namespace gpic

@@ -24,6 +24,26 @@ thread_local std::string g_init_error;
 
 namespace gpic {
 
+nvtxDomainHandle_t nvtx_domain() {
+    static const nvtxDomainHandle_t d = nvtxDomainCreateA("gpic");
+    return d;
+}
+
+void nvtx_push(const char* name) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+}
+
+const char* timer_name(int which) {
+    static const char* const names[PIC_KT_COUNT] = {
+        "sort", "deposit", "field_solve", "gather_push", "adj_push", "adj_field", "adj_deposit"};
+    return which >= 0 && which < PIC_KT_COUNT ? names[which] : "?";
+}
+
 pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -834,6 +854,7 @@ pic_status pic_step(pic_handle* h, int32_t nsteps) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 0) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 0");
     for (int32_t i = 0; i < nsteps; ++i) {
+        NvtxRange r("step");
         pic_status st = pic_deposit(h);
         if (st == PIC_OK) st = pic_field_solve(h);
         if (st == PIC_OK) st = pic_gather_push(h);
