@@ -5,8 +5,9 @@ The FP32 form is a build-side design (the paper computes in FP64): positions and
 velocities are FP32, and each current contribution q_p v W_x W_y is deposited as an
 integer multiple of a power-of-two quantum and summed in int64, so the grid sums are
 exact and independent of the order of the particles.  This module restates that
-arithmetic -- the first two lines of Algorithm 1 (section 4.2: x^{n+1} = x^n + v^n dt,
-then J^{n+1} from x^{n+1} and v^n with the B-spline shape of section 4) -- in numpy
+arithmetic -- the position update and current deposit of Algorithm 1 (section 4.2:
+x^{n+1} = x^n + v^n dt, then J^{n+1} from x^{n+1} and v^n with the B-spline shape of
+section 4) -- in numpy
 float32 with exact integer sums, so that the GPU's current can be compared bit for bit:
 
   * every float32 operation is one IEEE-754 operation rounded to nearest even;
