@@ -7,8 +7,8 @@ integer multiple of a power-of-two quantum and summed in int64, so the grid sums
 exact and independent of the order of the particles.  This module restates that
 arithmetic -- the position update and current deposit of Algorithm 1 (section 4.2:
 x^{n+1} = x^n + v^n dt, then J^{n+1} from x^{n+1} and v^n with the B-spline shape of
-section 4) -- in numpy
-float32 with exact integer sums, so that the GPU's current can be compared bit for bit:
+section 4) -- in numpy float32 with exact integer sums, so that the GPU's current can be
+compared bit for bit:
 
   * every float32 operation is one IEEE-754 operation rounded to nearest even;
   * a fused multiply-add a b + c is rounded once: the product is exact in float64, the
