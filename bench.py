@@ -76,7 +76,7 @@ class Ranks:
     """The ranks of a torchrun launch (RANK, WORLD_SIZE, LOCAL_RANK): every rank runs an
     independent replica, so the only collectives are the barriers around a timed region
     and the max of its duration over ranks.  With one rank both are local no-ops.
-    backend/device: "nccl"/"cuda" on the GPU box, "gloo"/"cpu" for the CPU tests."""
+    backend/device: "nccl"/"cuda" on GPUs, "gloo"/"cpu" for the CPU tests."""
 
     def __init__(self, backend="nccl", device="cuda"):
         self.rank = int(os.environ.get("RANK", "0"))

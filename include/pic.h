@@ -47,7 +47,7 @@ typedef struct pic_handle pic_handle; /* opaque, owned by the library */
 typedef enum {
     PIC_OK = 0,
     PIC_ERR_INVALID_ARG = 1, /* a size, pointer or parameter outside its range     */
-    PIC_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement      */
+    PIC_ERR_UNSUPPORTED = 2, /* a valid request the library does not implement     */
     PIC_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed        */
     PIC_ERR_NONFINITE = 4,   /* a particle momentum or velocity became inf/NaN     */
     PIC_ERR_OVERFLOW = 5,    /* the int64 fixed-point current would overflow       */
