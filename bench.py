@@ -269,11 +269,34 @@ sys.path.insert(0, {root!r})
 from oracle import pic as opic
 from paper_2410_18414_gb300 import workloads
 wl = workloads.weibel({nx}, {nx}, {ppc}, {v_drift}, {u_th}, {seed}, {p}, "bdf", 2, 2000)
+
+
+def start(n):
+    cfg = opic.Config(nx={nx}, ny={nx}, lx=wl.lx, ly=wl.ly, dt=wl.dt, p={p},
+                      stepper={stepper!r}, bdf_order={k}, dirk={dirk!r}, w=wl.lx * wl.ly / n)
+    return cfg, opic.initial_state(cfg, wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n])
+
+
+def one_step_s(n):
+    cfg, st = start(n)
+    opic.step(cfg, st)
+    t0 = time.perf_counter()
+    opic.step(cfg, st)
+    return time.perf_counter() - t0
+
+
 n = min({n}, len(wl.x))
-x, y, vx, vy = wl.x[:n], wl.y[:n], wl.vx[:n], wl.vy[:n]
-cfg = opic.Config(nx={nx}, ny={nx}, lx=wl.lx, ly=wl.ly, dt=wl.dt, p={p}, stepper={stepper!r},
-                  bdf_order={k}, dirk={dirk!r}, w=wl.lx * wl.ly / n)
-st = opic.initial_state(cfg, x, y, vx, vy)
+budget = {budget_s}
+if budget > 0:
+    # a step costs a + b n (the grid's transforms plus the particles): size the sample so
+    # that warm-up and timed steps fit the budget
+    n0, n1 = 1024, min(16384, n)
+    t0, t1 = one_step_s(n0), one_step_s(n1)
+    b = max((t1 - t0) / (n1 - n0), 1e-9) if n1 > n0 else 1e-9
+    a = max(t0 - b * n0, 0.0)
+    per_step = budget / max(1, {warmup} + {steps})
+    n = int(min(n, max(n0, (per_step - a) / b)))
+cfg, st = start(n)
 for _ in range({warmup}):
     opic.step(cfg, st)
 times = []
@@ -295,13 +318,17 @@ def workload_params(workload):
                 seed=sp["seed"], stepper="bdf2")
 
 
-def run_oracle(workload, stepper_name, n, steps, warmup):
+def run_oracle(workload, stepper_name, n, steps, warmup, budget_s=0.0):
+    """Per-step times of the oracle on the first n particles of the workload (weight
+    rescaled), after `warmup` untimed steps.  budget_s > 0: n is lowered, from a two-size
+    probe of the step cost, so that all the steps take about budget_s.  Returns (times, n)."""
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
     w = workload_params(workload)
     code = ORACLE_SNIPPET.format(root=ROOT, seed=w["seed"], n=n, stepper=stepper, k=k, dirk=dirk,
                                  warmup=warmup, steps=steps, nx=w["n"], ppc=w["ppc"],
-                                 v_drift=w["v_drift"], u_th=w["u_th"], p=w["p"])
+                                 v_drift=w["v_drift"], u_th=w["u_th"], p=w["p"],
+                                 budget_s=float(budget_s))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
@@ -309,15 +336,15 @@ def run_oracle(workload, stepper_name, n, steps, warmup):
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     out = json.loads(r.stdout.strip().splitlines()[-1])
-    if out["n"] != n:
+    if budget_s <= 0 and out["n"] != n:
         raise RuntimeError(f"the workload holds only {out['n']} particles, fewer than {n}")
-    return out["times"]
+    return out["times"], out["n"]
 
 
 def cpu_baseline(workload, stepper_name):
     n = 262144
     steps = 12
-    times = run_oracle(workload, stepper_name, n, steps, 1)
+    times, _ = run_oracle(workload, stepper_name, n, steps, 1)
     v = n * len(times) / sum(times)
     w = WORKLOADS[workload]
     total = w["n"] * w["n"] * w["ppc"]
@@ -389,8 +416,10 @@ def run_reference(a):
         run_reference_adjoint(a)
         return
     wp = workload_params(a.workload)
+    # every one of the K + W steps runs, each on a sample sized so that they all take
+    # about two minutes of one host core
     n = min(131072, wp["n"] * wp["n"] * wp["ppc"])
-    times = run_oracle(a.workload, a.stepper, n, a.steps, a.warmup)
+    times, n = run_oracle(a.workload, a.stepper, n, a.steps, a.warmup, budget_s=120.0)
     total = sum(times)
     value = n * len(times) / total
     if a.workload in WORKLOADS:
@@ -405,8 +434,10 @@ def run_reference(a):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(wl_desc, form="fp64", sample_particles=n, parallelism="replicas"),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the numpy FP64 oracle on the 128x128 grid with "
-                                       f"the first {n} particles, single thread"},
+                             "sample": f"each step: the numpy FP64 oracle on the {wp['n']}x{wp['n']} "
+                                       f"grid with the first {n} particles (weight rescaled; the "
+                                       f"sample sized so that the {a.warmup} + {a.steps} steps take "
+                                       f"about 2 minutes), single thread"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
