@@ -388,7 +388,6 @@ pic_status alloc_state(pic_handle* h) {
 // fill every history level with its t = 0 value.
 pic_status setup(pic_handle* h, const pic_particles_in* in) {
     const pic_config& c = h->cfg;
-    const size_t cs = 2 * h->rsz;
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
         cudaError_t r = launch_twiddles<T>(h->twx, c.nx, h->s);
