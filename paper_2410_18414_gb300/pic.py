@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgpic.so")
+# the in-tree build; GPIC_LIB names another build of the same library (the host-sanitizer
+# build libgpic_asan.so, say)
+LIB_PATH = os.environ.get("GPIC_LIB") or os.path.join(_HERE, "libgpic.so")
 
 # pic_status
 PIC_OK = 0
@@ -81,11 +83,12 @@ EXPORTS = ("pic_init", "pic_deposit", "pic_field_solve", "pic_gather_push", "pic
 _lib = None
 
 
-def load_library(path=LIB_PATH):
-    """Load libgpic.so (once).  Raises if it has not been built."""
+def load_library(path=None):
+    """Load libgpic.so (once; path defaults to LIB_PATH).  Raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libgpic.so not found at {path}: build it with "
                            "`python -m paper_2410_18414_gb300.build` (needs nvcc)")
