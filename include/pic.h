@@ -169,17 +169,17 @@ typedef struct {
 pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,
                     pic_handle **out);
 
-/* Algorithm 1, first two lines: move every particle with v^n (wrapping into the
- * domain) and deposit J^{n+1} with the new positions and v^n.  Re-sorts the
- * particles first when sort_interval says so. */
+/* Algorithm 1, the position update and deposit: move every particle with v^n
+ * (wrapping into the domain) and deposit J^{n+1} with the new positions and v^n.
+ * Re-sorts the particles first when sort_interval says so. */
 pic_status pic_deposit(pic_handle *h);
 
-/* Algorithm 1, charge and field lines: FFT of J^{n+1}, rho^{n+1} from continuity,
+/* Algorithm 1, the charge and field steps: FFT of J^{n+1}, rho^{n+1} from continuity,
  * the implicit per-mode wave update of phi and A, and the eight spectral gradient
  * fields on the grid.  Needs a preceding pic_deposit of the same step. */
 pic_status pic_field_solve(pic_handle *h);
 
-/* Algorithm 1, particle lines: gather the eight fields at x^{n+1}, IAEM momentum
+/* Algorithm 1, the particle update: gather the eight fields at x^{n+1}, IAEM momentum
  * update with v*, new velocity; then shift the time histories (end of the step). */
 pic_status pic_gather_push(pic_handle *h);
 
@@ -396,10 +396,10 @@ int32_t pic_adjoint_checkpoint_every(const pic_adjoint *a);
 /* Release the adjoint's device memory (not the handle).  NULL is allowed. */
 void pic_adjoint_destroy(pic_adjoint *a);
 
-/* Allocation-free move + deposit pass (the first two lines of one step, as pic_deposit
- * does them) for callers that cannot let a library allocate device memory: hosts whose
- * GPU memory is owned by their own pool allocator (a hidden cudaMalloc would fail or
- * bypass the pool), and latency-bound loops that cannot afford the device-wide
+/* Allocation-free move + deposit pass (the position update and deposit of one step, as
+ * pic_deposit does them) for callers that cannot let a library allocate device memory:
+ * hosts whose GPU memory is owned by their own pool allocator (a hidden cudaMalloc would
+ * fail or bypass the pool), and latency-bound loops that cannot afford the device-wide
  * synchronisation cudaMalloc/cudaFree imply.  The paper has no counterpart; this is a
  * deployment convenience.
  *

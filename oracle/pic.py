@@ -152,7 +152,7 @@ def wrap(x, length):
 
 
 def velocity_from_momentum(cfg, px, py, ax, ay):
-    """v = c^2 (P - qA) / sqrt(c^2 |P - qA|^2 + (m c^2)^2) (section 2.2; IAEM last line)."""
+    """v = c^2 (P - qA) / sqrt(c^2 |P - qA|^2 + (m c^2)^2) (section 2.2; the velocity update of the IAEM scheme)."""
     ux = px - cfg.q * ax
     uy = py - cfg.q * ay
     c2 = cfg.c * cfg.c
