@@ -237,6 +237,17 @@ pic_status pic_set_diagnostics(pic_handle *h, int32_t every);
  * PIC_ERR_STATE if no step has been diagnosed yet. */
 pic_status pic_residuals(pic_handle *h, pic_diagnostics *out);
 
+/* The diagnostics of every diagnosed step since the previous call (or since
+ * pic_set_diagnostics), oldest first, into out[0..capacity) on the host; *count receives
+ * how many were written.  Each diagnosed step's accumulators are copied on the device into
+ * a ring of PIC_DIAG_HISTORY records as the step ends, so stepping needs no host
+ * synchronisation; when more steps were diagnosed than the ring or capacity holds, the
+ * oldest are dropped (the step fields tell).  Synchronizes.  PIC_ERR_INVALID_ARG for NULL
+ * pointers or capacity < 0. */
+#define PIC_DIAG_HISTORY 4096
+pic_status pic_diagnostics_history(pic_handle *h, pic_diagnostics *out, int32_t capacity,
+                                   int32_t *count);
+
 /* Copy one real nx*ny grid quantity of the last step into dst (FP64, host or
  * device).  PIC_ERR_STATE for EX/EY unless the last step was diagnosed, and for
  * every field before the first step except RHO and PHI. Synchronizes. */

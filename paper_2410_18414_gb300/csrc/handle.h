@@ -89,6 +89,11 @@ struct pic_handle {
     int diag_every = 0;
     bool diag_now = false, diag_valid = false, e_valid = false;
     int64_t diag_step = -1;
+    // per-step records (pic_diagnostics_history): a device ring of PIC_DIAG_HISTORY x
+    // D_NSLOTS accumulators, each slot's step on the host, the records not yet read
+    double* diag_ring = nullptr;
+    std::vector<int64_t> ring_step;
+    int64_t ring_written = 0, ring_read = 0;
     int64_t step = 0;
     int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
     bool stepped = false;

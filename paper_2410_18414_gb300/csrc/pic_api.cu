@@ -844,6 +844,13 @@ pic_status pic_gather_push(pic_handle* h) {
     if (h->diag_now) {
         h->diag_valid = true;
         h->diag_step = h->step;
+        if (h->diag_ring) {  // this step's record, stream-ordered after its reductions
+            const int64_t slot = h->ring_written % PIC_DIAG_HISTORY;
+            CK(cudaMemcpyAsync(h->diag_ring + slot * D_NSLOTS, h->diag,
+                               D_NSLOTS * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+            h->ring_step[slot] = h->step;
+            ++h->ring_written;
+        }
     }
     h->phase = 0;
     return PIC_OK;
@@ -1032,17 +1039,21 @@ void pic_ensemble_destroy(pic_ensemble* e) {
 pic_status pic_set_diagnostics(pic_handle* h, int32_t every) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (every < 0) return fail(h, PIC_ERR_INVALID_ARG, "every must be >= 0");
+    if (every > 0 && !h->diag_ring) {
+        void* p = nullptr;
+        CK(dalloc(h, &p, (size_t)PIC_DIAG_HISTORY * D_NSLOTS * sizeof(double)));
+        h->diag_ring = static_cast<double*>(p);
+        h->ring_step.assign(PIC_DIAG_HISTORY, -1);
+    }
     h->diag_every = every;
+    h->ring_read = h->ring_written;  // the history starts here
     return PIC_OK;
 }
 
-pic_status pic_residuals(pic_handle* h, pic_diagnostics* out) {
-    if (!h || !out) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
-    double acc[D_NSLOTS];
-    CK(cudaMemcpyAsync(acc, h->diag, sizeof acc, cudaMemcpyDeviceToHost, h->s));
-    pic_status st = check_device_error(h);
-    if (st != PIC_OK) return st;
-    if (!h->diag_valid) return fail(h, PIC_ERR_STATE, "no step has been diagnosed yet");
+namespace {
+
+// The diagnostics of one step from its raw accumulators (sums over modes and particles).
+void to_diagnostics(const pic_handle* h, const double* acc, int64_t step, pic_diagnostics* out) {
     const double N = (double)h->ng;
     const double area = (h->cfg.lx / h->nx) * (h->cfg.ly / h->ny);
     // Parseval: grid mean of |f|^2 = (1/N^2) sum_k |f_hat|^2
@@ -1056,7 +1067,52 @@ pic_status pic_residuals(pic_handle* h, pic_diagnostics* out) {
     out->w_e = 0.5 * h->cfg.eps0 * area * acc[D_WE] / N;
     out->w_b = 0.5 / h->mc.mu0 * area * acc[D_WB] / N;
     out->kinetic = acc[D_KIN];
-    out->step = h->diag_step;
+    out->step = step;
+}
+
+}  // namespace
+
+pic_status pic_residuals(pic_handle* h, pic_diagnostics* out) {
+    if (!h || !out) return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    double acc[D_NSLOTS];
+    CK(cudaMemcpyAsync(acc, h->diag, sizeof acc, cudaMemcpyDeviceToHost, h->s));
+    pic_status st = check_device_error(h);
+    if (st != PIC_OK) return st;
+    if (!h->diag_valid) return fail(h, PIC_ERR_STATE, "no step has been diagnosed yet");
+    to_diagnostics(h, acc, h->diag_step, out);
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics_history(pic_handle* h, pic_diagnostics* out, int32_t capacity,
+                                   int32_t* count) {
+    if (!h || !count || (capacity > 0 && !out))
+        return fail(h, PIC_ERR_INVALID_ARG, "NULL argument");
+    if (capacity < 0) return fail(h, PIC_ERR_INVALID_ARG, "capacity must be >= 0");
+    *count = 0;
+    pic_status st = check_device_error(h);  // also waits for the ring's copies
+    if (st != PIC_OK) return st;
+    // the unread records still in the ring, the newest `capacity` of them
+    int64_t first = std::max(h->ring_read, h->ring_written - (int64_t)PIC_DIAG_HISTORY);
+    first = std::max(first, h->ring_written - (int64_t)capacity);
+    const int64_t nrec = h->ring_written - first;
+    if (nrec > 0) {
+        std::vector<double> acc((size_t)nrec * D_NSLOTS);
+        for (int64_t r = first; r < h->ring_written; ) {  // at most two contiguous pieces
+            const int64_t slot = r % PIC_DIAG_HISTORY;
+            const int64_t len = std::min(h->ring_written - r, (int64_t)PIC_DIAG_HISTORY - slot);
+            CK(cudaMemcpyAsync(acc.data() + (size_t)(r - first) * D_NSLOTS,
+                               h->diag_ring + slot * D_NSLOTS,
+                               (size_t)len * D_NSLOTS * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->s));
+            r += len;
+        }
+        CK(cudaStreamSynchronize(h->s));
+        for (int64_t r = first; r < h->ring_written; ++r)
+            to_diagnostics(h, acc.data() + (size_t)(r - first) * D_NSLOTS,
+                           h->ring_step[r % PIC_DIAG_HISTORY], out + (r - first));
+    }
+    h->ring_read = h->ring_written;
+    *count = (int32_t)nrec;
     return PIC_OK;
 }
 

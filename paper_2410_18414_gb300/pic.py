@@ -70,6 +70,9 @@ class PicParticlesIn(ctypes.Structure):
                 ("species", ctypes.c_void_p)]
 
 
+DIAG_HISTORY = 4096  # PIC_DIAG_HISTORY: records the device ring holds
+
+
 class PicDiagnostics(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in
                 ("gauge_rms", "gauss_rms", "continuity_rms", "gauge_dt_rms", "rho_rms",
@@ -104,6 +107,8 @@ def load_library(path=None):
         "pic_step": ([vp, i32], i32),
         "pic_set_diagnostics": ([vp, i32], i32),
         "pic_residuals": ([vp, ctypes.POINTER(PicDiagnostics)], i32),
+        "pic_diagnostics_history": ([vp, ctypes.POINTER(PicDiagnostics), i32,
+                                     ctypes.POINTER(i32)], i32),
         "pic_get_field": ([vp, i32, vp], i32),
         "pic_read_particles": ([vp] + [vp] * 8, i32),
         "pic_read_particles_z": ([vp] + [vp] * 4, i32),
@@ -228,6 +233,15 @@ class Simulation:
         d = PicDiagnostics()
         self._check(self.lib.pic_residuals(self.h, ctypes.byref(d)))
         return {name: getattr(d, name) for name, _ in PicDiagnostics._fields_}
+
+    def diagnostics_history(self, capacity=DIAG_HISTORY):
+        """The diagnostics of every step diagnosed since the previous call (or since
+        set_diagnostics), oldest first, as a list of dicts like residuals()."""
+        buf = (PicDiagnostics * max(1, capacity))()
+        count = ctypes.c_int32(0)
+        self._check(self.lib.pic_diagnostics_history(self.h, buf, capacity, ctypes.byref(count)))
+        return [{name: getattr(buf[i], name) for name, _ in PicDiagnostics._fields_}
+                for i in range(count.value)]
 
     def field(self, name, out=None):
         if out is None:

@@ -136,6 +136,9 @@ def test_null_handle_calls_fail_cleanly(lib):
     size = ctypes.c_size_t(0)
     assert lib.pic_save_state(None, None, ctypes.byref(size)) == 1
     assert lib.pic_load_state(None, None, 0) == 1
+    count = ctypes.c_int32(7)
+    assert lib.pic_diagnostics_history(None, None, 0, ctypes.byref(count)) == 1
+    assert lib.pic_diagnostics_history(None, None, 0, None) == 1
     lib.pic_destroy(None)
 
 

@@ -257,3 +257,38 @@ def test_diagnostics_do_not_change_the_trajectory(device, precision, stepper, kw
             assert rel(u, v) < 1e-12
     for s in sims:
         s.close()
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_FIX64], ids=["fp64", "fp32"])
+def test_diagnostics_history_records_every_diagnosed_step(device, precision):
+    # the device ring keeps each diagnosed step's accumulators: read back later, every
+    # record equals what pic_residuals returned right after that step
+    wl = workloads.weibel(32, 32, 8, 0.5, 0.01, 98, 3)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                          precision=precision, stepper="bdf", bdf_order=2,
+                          sort_interval=4 if precision == pic.FP32_FIX64 else 0)
+    with pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device) as sim:
+        sim.step(3)
+        sim.set_diagnostics(2)
+        assert sim.diagnostics_history() == []
+        direct = []
+        for _ in range(5):
+            sim.step(2)
+            direct.append(sim.residuals())
+        hist = sim.diagnostics_history()
+        # a step is diagnosed when its new index is a multiple of `every`
+        assert [h["step"] for h in hist] == [4, 6, 8, 10, 12]
+        assert hist == direct
+        assert sim.diagnostics_history() == []          # read once
+        sim.step(6)
+        last = sim.diagnostics_history(capacity=2)      # the newest two of three
+        assert [h["step"] for h in last] == [16, 18]
+        # a wrapped ring: more diagnosed steps than it holds keep the newest
+        sim.set_diagnostics(1)
+        sim.step(pic.DIAG_HISTORY + 3)
+        wrapped = sim.diagnostics_history()
+        assert len(wrapped) == pic.DIAG_HISTORY
+        assert wrapped[-1]["step"] == sim.step_count
+        assert [h["step"] for h in wrapped] == list(range(sim.step_count - pic.DIAG_HISTORY + 1,
+                                                          sim.step_count + 1))
+        assert wrapped[-1] == sim.residuals()
