@@ -23,8 +23,10 @@ Modules:
   pic       -- deposit, gather, IAEM push, initial state, Algorithm 1 step,
                residuals and energies (sections 2, 3, 4); 2D-2V or 2D-3V, one
                species or a species table
-  adjoint   -- discrete adjoint of the BDF-k step: gradients of the final magnetic
-               energy (or final momenta) with respect to v^0 and P^0
+  adjoint   -- discrete adjoint of the step (BDF-k, the three CDF-2 forms, DIRK):
+               gradients of the final magnetic energy (or final momenta) with respect
+               to v^0 and P^0
+  fixed_point -- bit-exact model of the FP32 form's move and fixed-point deposit
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``
 against something the paper or plain mathematics fixes.
