@@ -230,7 +230,10 @@ int32_t pic_ensemble_period(const pic_ensemble *e);
 void pic_ensemble_destroy(pic_ensemble *e);
 
 /* Compute diagnostics every `every` steps (0 = never, the default).  They cost one
- * extra reduction over modes and particles per diagnosed step. */
+ * extra reduction over modes and particles per diagnosed step, and a device copy of its
+ * accumulators into the history ring (pic_diagnostics_history), which the first call
+ * with every > 0 allocates (PIC_ERR_CUDA if that fails).  Each call starts a new history:
+ * records not yet read are dropped. */
 pic_status pic_set_diagnostics(pic_handle *h, int32_t every);
 
 /* Copy the diagnostics of the last diagnosed step to *out (synchronizes).
