@@ -276,10 +276,14 @@ pic_status pic_read_particles_z(pic_handle *h, double *pz, double *vz, double *v
  * histories, the last step's J and gather fields).  With dst NULL it only stores the size
  * needed in *size; with *size too small it returns PIC_ERR_INVALID_ARG and the size needed.
  * Synchronizes.  pic_load_state restores such a string into a handle created with the same
- * configuration and particle count (PIC_ERR_INVALID_ARG otherwise): the handle then steps
- * exactly as the saved one would have (bit for bit in the FP32 form).  Diagnostics of the
- * last step are not part of the state.  A handle that belongs to an ensemble or an adjoint
- * must not be loaded into.  Both: PIC_ERR_STATE inside a step. */
+ * configuration and particle count (PIC_ERR_INVALID_ARG otherwise; the layout fields and
+ * every FP64 parameter a step uses -- lx, ly, c, eps0, dt, q, m, weight, the DIRK tableau
+ * and the species table -- are compared bit for bit): the handle then steps exactly as
+ * the saved one would have (bit for bit in the FP32 form).  Diagnostics of the last step
+ * are not part of the state, and the per-step diagnostics log restarts at the load
+ * (pic_diagnostics_history returns no record of a step before it).  A handle that belongs
+ * to an ensemble or an adjoint must not be loaded into.  Both: PIC_ERR_STATE inside a
+ * step. */
 pic_status pic_save_state(pic_handle *h, void *dst, size_t *size);
 pic_status pic_load_state(pic_handle *h, const void *src, size_t size);
 
@@ -425,14 +429,20 @@ void pic_adjoint_destroy(pic_adjoint *a);
  *           current density, weight*q*sum_p v_p W W / (dx dy).
  *
  * The only scratch is a fixed 4 MiB array inside the library, resident on every device
- * that loads it until the process exits.  The first call on a device looks up that
- * array's device address (a one-time set-up, so make that first call before any stream
- * capture).  Every call shares the array and clears what it uses; calls that overlap on
- * the GPU (other threads or streams) race on it.  The call enqueues on cuda_stream and
- * returns once the pass has finished.  Returns PIC_ERR_INVALID_ARG for a grid above the
- * limit or a bad argument, PIC_ERR_UNSUPPORTED for FP32, PIC_ERR_NONFINITE if a position
- * was outside the domain or not finite (that particle is skipped), PIC_ERR_CUDA on a
- * runtime failure.  No call allocates or frees device memory. */
+ * that loads it until the process exits.  The calls themselves never call cudaMalloc or
+ * cudaFree, but the 4 MiB is committed when the CUDA module holding the array is loaded
+ * on a device: under CUDA's default lazy module loading that is the first call on that
+ * device (which also looks up the array's device address once), outside any pool the
+ * caller manages.  A caller whose pool takes the whole GPU should therefore make one call
+ * (or load the library with CUDA_MODULE_LOADING=EAGER) before its pool claims the device;
+ * otherwise that first call can fail with PIC_ERR_CUDA.  Every call shares the array and
+ * clears what it uses; calls that overlap on the GPU (other threads or streams) race on
+ * it.  The call enqueues on cuda_stream, reads the device error flag back and
+ * synchronizes that stream, so it returns once the pass has finished and cannot be
+ * captured into a CUDA graph.  Returns PIC_ERR_INVALID_ARG for a grid above the limit or
+ * a bad argument, PIC_ERR_UNSUPPORTED for FP32, PIC_ERR_NONFINITE if a position was
+ * outside the domain or not finite (that particle is skipped), PIC_ERR_CUDA on a runtime
+ * failure. */
 pic_status pic_move_deposit_noalloc(const pic_config *cfg, int64_t n, double *x, double *y,
                                     const double *vx, const double *vy, double *jx, double *jy,
                                     void *cuda_stream);

@@ -8,6 +8,7 @@
 // target steps on exactly as the source would have.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -19,6 +20,9 @@ using namespace gpic;
 
 namespace {
 
+// The configuration a state was saved under: the integer layout fields and every FP64
+// parameter a later step uses (box, constants, time step, particle constants, the DIRK
+// tableau and the species table).  A load compares them bit for bit.
 struct StateHeader {
     char magic[8];
     int32_t nx, ny, p, stepper, cdf_form, bdf_order, dirk_stages, precision;
@@ -26,8 +30,11 @@ struct StateHeader {
     int64_t n, step;
     int32_t vcur, head, head_r, stepped;
     uint64_t payload;
+    double lx, ly, c, eps0, dt, q, m, weight;
+    double dirk_a[16], dirk_b[4], dirk_c[4];
+    double species_q[4], species_m[4], species_w[4];
 };
-constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '1'};
+constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '2'};
 
 struct Seg {
     void* p;
@@ -98,7 +105,39 @@ StateHeader header_of(pic_handle* h, uint64_t payload) {
     hd.head_r = h->head_r;
     hd.stepped = h->stepped ? 1 : 0;
     hd.payload = payload;
+    hd.lx = c.lx;
+    hd.ly = c.ly;
+    hd.c = c.c;
+    hd.eps0 = c.eps0;
+    hd.dt = c.dt;
+    hd.q = c.q;
+    hd.m = c.m;
+    hd.weight = c.weight;
+    // only the entries the configuration uses (the rest of a caller's struct may hold
+    // anything); unused entries stay zero
+    if (c.stepper == PIC_STEPPER_DIRK) {
+        const int st = c.dirk_stages;
+        for (int i = 0; i < st; ++i) {
+            for (int j = 0; j < st; ++j) hd.dirk_a[i * st + j] = c.dirk_a[i * st + j];
+            hd.dirk_b[i] = c.dirk_b[i];
+            hd.dirk_c[i] = c.dirk_c[i];
+        }
+    }
+    for (int k = 0; k < h->spp.n; ++k) {
+        hd.species_q[k] = c.species_q[k];
+        hd.species_m[k] = c.species_m[k];
+        hd.species_w[k] = c.species_w[k];
+    }
     return hd;
+}
+
+// Bitwise equality of the FP64 parameters of two headers (a state saved under another
+// dt, box, constant, tableau or species table belongs to another configuration).
+bool same_parameters(const StateHeader& a, const StateHeader& b) {
+    const size_t first = offsetof(StateHeader, lx);
+    const size_t last = offsetof(StateHeader, species_w) + sizeof(a.species_w);
+    return std::memcmp(reinterpret_cast<const char*>(&a) + first,
+                       reinterpret_cast<const char*>(&b) + first, last - first) == 0;
 }
 
 uint64_t payload_bytes(const std::vector<Seg>& segs) {
@@ -152,7 +191,8 @@ pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
                       hd.bdf_order == mine.bdf_order && hd.dirk_stages == mine.dirk_stages &&
                       hd.precision == mine.precision && hd.sort_interval == mine.sort_interval &&
                       hd.vdim == mine.vdim && hd.nspecies == mine.nspecies &&
-                      hd.charge == mine.charge && hd.n == mine.n && hd.payload == payload;
+                      hd.charge == mine.charge && hd.n == mine.n && hd.payload == payload &&
+                      same_parameters(hd, mine);
     if (!same)
         return fail(h, PIC_ERR_INVALID_ARG,
                     "the saved state belongs to another configuration or particle count");
@@ -171,6 +211,8 @@ pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
     h->head_r = hd.head_r;
     h->stepped = hd.stepped != 0;
     h->diag_valid = h->e_valid = false;
+    // the diagnostics log restarts: records of steps before the load are not returned
+    h->ring_read = h->ring_written;
     if (h->fp32) {
         // the buffer the next deposit sums into starts at zero (the row transform keeps it so)
         CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));

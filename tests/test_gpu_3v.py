@@ -19,6 +19,8 @@ from oracle import pic as opic
 from oracle import steppers as osteps
 from paper_2410_18414_gb300 import pic
 
+from test_gpu_parity import maxrel, wrapped_maxrel
+
 pytestmark = pytest.mark.gpu
 
 SPECIES = ((-1.0, 1.0, 1.0), (1.0, 4.0, 1.0))   # weights scaled per case below
@@ -94,11 +96,15 @@ def test_3v_species_fp64_matches_oracle(device, stepper, kw, okw):
         sim.step(10)
         got = sim.particles()
         fields = {f: sim.field(f) for f in FIELDS + Z_FIELDS}
-    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"])}
+    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"]),
+            "x max": wrapped_maxrel(got["x"], st.x, c["lx"]),
+            "y max": wrapped_maxrel(got["y"], st.y, c["ly"])}
     for k in PARTICLE_KEYS + Z_KEYS:
         errs[k] = rel(got[k], getattr(st, k))
+        errs[k + " max"] = maxrel(got[k], getattr(st, k))
     for f in FIELDS + Z_FIELDS:
         errs[f] = rel(fields[f], st.grids[f])
+        errs[f + " max"] = maxrel(fields[f], st.grids[f])
     assert np.array_equal(got["species"], c["sp"])
     bad = {k: v for k, v in errs.items() if not v <= 1e-12}
     assert not bad, bad
@@ -114,11 +120,15 @@ def test_2v_species_fp64_matches_oracle(device):
         with pytest.raises(pic.PicError) as e:
             sim.field("az")
         assert e.value.status == 7
-    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"])}
+    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"]),
+            "x max": wrapped_maxrel(got["x"], st.x, c["lx"]),
+            "y max": wrapped_maxrel(got["y"], st.y, c["ly"])}
     for k in PARTICLE_KEYS:
         errs[k] = rel(got[k], getattr(st, k))
+        errs[k + " max"] = maxrel(got[k], getattr(st, k))
     for f in FIELDS:
         errs[f] = rel(fields[f], st.grids[f])
+        errs[f + " max"] = maxrel(fields[f], st.grids[f])
     bad = {k: v for k, v in errs.items() if not v <= 1e-12}
     assert not bad, bad
 

@@ -103,3 +103,54 @@ def test_load_refuses_other_configurations(device):
     a.load_state(state)              # its own state: accepted
     a.close()
     b.close()
+
+
+def _make_cfg(device, seed, dt_scale=1.0, species=None, **kw):
+    wl = workloads.weibel(32, 32, 8, 0.5, 0.01, seed, 3, nsteps=20)
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt * dt_scale, p=3, stepper="bdf",
+                          bdf_order=2, weight=wl.weight, species=species, **kw)
+    extra = {}
+    if species:
+        extra["species"] = (np.arange(wl.n) % len(species)).astype(np.int32)
+    return pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device, **extra)
+
+
+def test_load_refuses_other_fp64_parameters(device):
+    # Same layout (grid, order, stepper, particle count) but another dt, or one species
+    # mass changed: the state belongs to another configuration.
+    a = _make_cfg(device, 1)
+    a.step(2)
+    state = a.save_state()
+    b = _make_cfg(device, 1, dt_scale=1.0 + 2.0 ** -40)
+    with pytest.raises(pic.PicError) as e:
+        b.load_state(state)
+    assert e.value.status == 1
+    b.close()
+    tab = ((-1.0, 1.0, 1.0 / 8192), (1.0, 4.0, 1.0 / 8192))
+    c = _make_cfg(device, 1, species=tab)
+    c.step(1)
+    sstate = c.save_state()
+    d = _make_cfg(device, 1, species=((-1.0, 1.0, 1.0 / 8192), (1.0, 4.5, 1.0 / 8192)))
+    with pytest.raises(pic.PicError) as e:
+        d.load_state(sstate)
+    assert e.value.status == 1
+    e2 = _make_cfg(device, 2, species=tab)   # the same table: accepted
+    e2.load_state(sstate)
+    assert e2.step_count == 1
+    for s in (a, c, d, e2):
+        s.close()
+
+
+def test_diagnostics_log_restarts_at_a_load(device):
+    # Records logged before a load are not returned after it, so step numbers never repeat
+    # or go backwards.
+    a = _make_cfg(device, 1)
+    a.set_diagnostics(1)
+    a.step(3)
+    state = a.save_state()            # saved at step 3
+    a.step(4)                         # steps 4..7 logged, not read
+    a.load_state(state)               # back to step 3
+    a.step(2)                         # steps 4, 5
+    steps = [r["step"] for r in a.diagnostics_history()]
+    assert steps == [4, 5], steps
+    a.close()
