@@ -302,6 +302,10 @@ int32_t pic_kernels_per_step(const pic_handle *h);
  *   PIC_KT_DEPOSIT  the move + current deposit kernel (not the clearing of J)
  *   PIC_KT_FIELD    all kernels of pic_field_solve
  *   PIC_KT_GATHER   the gather + push kernel
+ *   PIC_KT_GATHER_DEPOSIT  the fused kernel of the sorted FP32 form inside pic_step: the
+ *                   gather + push of one step with the move + deposit of the next (a step
+ *                   that ends with it has no PIC_KT_GATHER launch, the next no
+ *                   PIC_KT_DEPOSIT launch)
  * and, in pic_adjoint_backward (one launch group per reversed step):
  *   PIC_KT_ADJ_PUSH     the reverse push + gather kernel (with its field-adjoint deposit)
  *   PIC_KT_ADJ_FIELD    the reverse field solve (transforms and per-mode update)
@@ -314,7 +318,8 @@ typedef enum {
     PIC_KT_ADJ_PUSH = 4,
     PIC_KT_ADJ_FIELD = 5,
     PIC_KT_ADJ_DEPOSIT = 6,
-    PIC_KT_COUNT = 7
+    PIC_KT_GATHER_DEPOSIT = 7,
+    PIC_KT_COUNT = 8
 } pic_kernel_timer;
 
 /* max_launches > 0 starts timing: resets every timer and creates max_launches event

@@ -17,7 +17,10 @@ compared bit for bit:
   * the shape weights are the closed-form piecewise polynomials of the centred cardinal
     B-splines (degrees 2, 3, 4), written in the operation order this form fixes (the
     oracle's FP64 path uses the Cox-de Boor recursion instead);
-  * a contribution c is summed as rint(c * 2^s) (half to even), exact for |c 2^s| < 2^53.
+  * a contribution of node (a, b) is t_a W_y,b with t_a = v W_x,a rounded to float32; it is
+    summed as rint(t_a W_y,b 2^s) of the exact product (half to even), i.e. rounded once to
+    the quantum: the float64 product of two float32 values is exact, and so is its scaling
+    by the power of two 2^s.
 """
 import numpy as np
 
@@ -108,12 +111,20 @@ def current_scale(c, n, rmax=1.0):
     return float(2.0 ** (k - int(np.ceil(np.log2(c))) - int(np.ceil(np.log2(rmax)))))
 
 
+def contribution(t, w, scale):
+    """rint(t w scale) of the exact product of the float32 values t and w (int64)."""
+    t = np.asarray(t, dtype=np.float32).astype(np.float64)
+    w = np.asarray(w, dtype=np.float32).astype(np.float64)
+    return np.rint(t * w * np.float64(scale)).astype(np.int64)
+
+
 def move_deposit(x, y, vx, vy, dt, lx, ly, nx, ny, p, scale):
     """One move + fixed-point deposit from FP64 inputs rounded to float32.
 
     Returns (x1, y1, jx, jy): the moved float32 positions and the int64 node sums of
-    rint(v W_x W_y * scale) for each current component, shape (nx, ny).  The positions are
-    first rounded to float32 and wrapped, as at t = 0."""
+    rint((v W_x) W_y * scale) for each current component (v W_x rounded to float32, the
+    product with W_y exact), shape (nx, ny).  The positions are first rounded to float32 and
+    wrapped, as at t = 0."""
     x = wrap32(np.asarray(x, dtype=np.float64).astype(np.float32), lx)
     y = wrap32(np.asarray(y, dtype=np.float64).astype(np.float32), ly)
     vx = np.asarray(vx, dtype=np.float64).astype(np.float32)
@@ -127,15 +138,12 @@ def move_deposit(x, y, vx, vy, dt, lx, ly, nx, ny, p, scale):
     j0, wy = weights32(yj, p)
     jx = np.zeros(nx * ny, dtype=np.int64)
     jy = np.zeros(nx * ny, dtype=np.int64)
-    s = np.float64(scale)
     for a in range(p + 1):
         ii = np.mod(i0 + a, nx)
         tx = (vx * wx[:, a]).astype(np.float32)
         ty = (vy * wx[:, a]).astype(np.float32)
         for b in range(p + 1):
             node = ii * ny + np.mod(j0 + b, ny)
-            cx = (tx * wy[:, b]).astype(np.float32)
-            cy = (ty * wy[:, b]).astype(np.float32)
-            np.add.at(jx, node, np.rint(cx.astype(np.float64) * s).astype(np.int64))
-            np.add.at(jy, node, np.rint(cy.astype(np.float64) * s).astype(np.int64))
+            np.add.at(jx, node, contribution(tx, wy[:, b], scale))
+            np.add.at(jy, node, contribution(ty, wy[:, b], scale))
     return x1, y1, jx.reshape(nx, ny), jy.reshape(nx, ny)

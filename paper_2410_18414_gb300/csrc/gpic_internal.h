@@ -279,34 +279,34 @@ struct SortArrays {
 };
 
 int sort_scan_chunks(int nkeys);  // chunk totals the scan keeps (size of its bsum array)
-// vidx: index in src.a of the x velocity this step's move uses (4 or 6; y velocity:
-// vidx + 1).  p4 (may be NULL): receives (x, y, vx, vy) of each particle in the new
-// order, the packed input of the tiled deposit.
+// vidx: index in src.a of the x velocity the keys' move uses (4 or 6; y velocity: vidx + 1),
+// or -1: keys at the current positions (particles that have moved already).
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
-                             float4* p4, cudaStream_t s);
+                             cudaStream_t s);
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
-// p4[p] = (x, y, vx, vy) of particle p (the packed input of the tiled deposit).
-cudaError_t launch_pack_p4(const float* x, const float* y, const float* vx, const float* vy,
-                           float4* p4, int64_t n, cudaStream_t s);
 
-// Move + deposit over tile-sorted particles: CTA b takes particles [b*chunk, (b+1)*chunk)
-// and accumulates each tile segment in shared memory.  `fix` selects the int64
-// fixed-point accumulation (J is longlong2) with `scale`, else FP64 (J is double2).
-template <typename T>
-// p4: (x, y, vx, vy) of each particle in the sorted order (written by the last sort or
-// tiled gather); the moved positions go to x, y.
-cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const float4* p4, int64_t n, const int* off,
-                                      void* j, bool fix, float scale, unsigned int* err,
-                                      cudaStream_t s);
+// Binned move + deposit of the FP32 form over tile-sorted particles (x, y, v^n = vx, vy)
+// into the int64 current j: each CTA bins its particles by deposit cell in shared memory
+// and sums each cell's contributions in registers before its shared atomics.  fused: the
+// gather + push of the step before runs first on each particle (fields4 = that step's gather
+// fields, P and v^{n+1} -> px, py, vxo, vyo; the move and deposit then use v^{n+1}), as
+// launch_gather_push_tiled does it.  per_cta: particles per CTA at the mean density.
+// deposit_binned_fits: whether the tile's regions fit the pass's shared memory.
+bool deposit_binned_fits(const TileGeom& tg, int p, bool fused);
+cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
+                                  const TileGeom& tg, float* x, float* y, float* px, float* py,
+                                  const float* vx, const float* vy, float* vxo, float* vyo,
+                                  int64_t n, const int* off, const void* fields4, void* j,
+                                  float scale, double* diag, unsigned int* err, cudaStream_t s,
+                                  bool fused, int per_cta);
 
 // Gather + push of particles sorted by launch_tile_sort (FP32 form), fields staged per tile.
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
                                     const TileGeom& tg, const float* x, const float* y, float* px,
                                     float* py, const float* vx, const float* vy, float* vx_old,
-                                    float* vy_old, float4* p4, int64_t n, const int* off,
+                                    float* vy_old, int64_t n, const int* off,
                                     const void* fields4, double* diag, unsigned int* err,
                                     cudaStream_t s);
 

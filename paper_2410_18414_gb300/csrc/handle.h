@@ -40,9 +40,6 @@ struct pic_handle {
     void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t *id = nullptr, *id_alt = nullptr;
     int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
-    // FP32 sorted path: (x, y, vx, vy) of each particle, the tiled deposit's input; written
-    // by every sort and every tiled gather, and a tiled deposit follows one of them
-    float4* p4 = nullptr;
     int launches_now = 0, launches_last = 0;
     // grid buffers
     double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
@@ -96,6 +93,7 @@ struct pic_handle {
     int64_t ring_written = 0, ring_read = 0;
     int64_t step = 0;
     int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
+    bool fused_deposit = false;  // phase 1 reached by the fused gather + deposit of pic_step
     bool stepped = false;
     std::vector<void*> allocs;
     gpic::ModeCommon mc{};
@@ -132,7 +130,7 @@ nvtxDomainHandle_t nvtx_domain();
 void nvtx_push(const char* name);
 inline void nvtx_pop() { nvtxDomainRangePop(nvtx_domain()); }
 // The range names of the kernel timers (PIC_KT_*): sort, deposit, field_solve,
-// gather_push, adj_push, adj_field, adj_deposit.
+// gather_push, adj_push, adj_field, adj_deposit, gather_deposit.
 const char* timer_name(int which);
 
 class NvtxRange {

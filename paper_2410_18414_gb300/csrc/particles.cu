@@ -119,10 +119,15 @@ __device__ __forceinline__ bool in_domain(T xi, int n) {
 // atomics, so the grid total does not depend on the order of the additions.
 struct AccF64 {
     double2* J;
+    // (tx wy, ty wy) to node: the two current components of one stencil node
     template <typename T>
-    __device__ __forceinline__ void add(size_t node, T a, T b) const {
-        atomicAdd(&J[node].x, (double)a);
-        atomicAdd(&J[node].y, (double)b);
+    __device__ __forceinline__ void add2(size_t node, T tx, T ty, T wy) const {
+        atomicAdd(&J[node].x, (double)rmul(tx, wy));
+        atomicAdd(&J[node].y, (double)rmul(ty, wy));
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1f(size_t node, T t, T w) const {
+        atomicAdd(&J[node].x, (double)rmul(t, w));
     }
     template <typename T>
     __device__ __forceinline__ void add1(size_t node, T a) const {
@@ -134,37 +139,53 @@ struct AccFix {
     longlong2* J;
     float scale;     // 1 / quantum, a power of two
     float s_hi;      // scale 2^-19
-    float neg_step;  // -2^19 / scale
     static AccFix make(void* j, float scale) {
-        return AccFix{(longlong2*)j, scale, scale * (1.0f / 524288.0f), -524288.0f / scale};
+        return AccFix{(longlong2*)j, scale, scale * (1.0f / 524288.0f)};
     }
-    // round(v * scale), the contribution in units of the quantum (set-up only: the
-    // float-to-int64 conversion runs on the FP64 pipe)
+    // round(v * scale), the contribution in units of the quantum (the deposited charge of
+    // the naive update only: the float-to-int64 conversion runs on the FP64 pipe)
     __device__ __forceinline__ static long long q(float v, float s) {
         return __float2ll_rn(__fmul_rn(v, s));
     }
-    // The same integer round(v * scale) as hi * 2^19 + lo with |hi| <= 2^19 and
-    // |lo| <= 2^18, by FP32 and integer operations only, for |v * scale| <= 2^38:
-    //   hi = rne(v scale 2^-19)   -- fma with 1.5 * 2^23 leaves it in the low mantissa bits
-    //   d  = v - hi 2^19 / scale  -- exact (a power-of-two scale, |d scale| <= 2^18)
-    //   lo = rne(d scale)         -- the same trick, d scale is exact
-    // hi 2^19 is even, so rne(v scale - hi 2^19) = rne(v scale) - hi 2^19.
-    __device__ __forceinline__ void split(float v, int& hi, int& lo) const {
-        const float m1 = __fmaf_rn(v, s_hi, 12582912.0f);
+    // The contribution of a current component to one node is t w (t = v W_x rounded to
+    // FP32, w = W_y): its exact product, rounded once to the quantum, rne(t w scale), split
+    // as hi 2^19 + lo with three FMAs, for |t w scale| <= 2^38.  wh = w scale 2^-19 and
+    // ws = w scale are exact (power-of-two scalings, see scaled()).  With M = 1.5 2^23:
+    //   m1 = rne(t wh + M)             = M + hi,   hi = rne(t w scale 2^-19), |hi| <= 2^19
+    //   mt = m1 (-2^19) + M (2^19 + 1) = M - hi 2^19   (exact: a multiple of 2^19 below 2^39)
+    //   l  = rne(t ws + mt)            = M + lo,   lo = rne(t w scale - hi 2^19), |lo| <= 2^18
+    // (every FMA rounds the exact a b + c once; results in [2^23, 2^24) round to integers).
+    // hi 2^19 is even, so hi 2^19 + lo = rne(t w scale).
+    __device__ __forceinline__ static void split2(float t, float wh, float ws, int& hi, int& lo) {
+        const float m1 = __fmaf_rn(t, wh, 12582912.0f);
+        const float mt = __fmaf_rn(m1, -524288.0f, 6597082349568.0f);
         hi = __float_as_int(m1) - 0x4B400000;
-        const float d = __fmaf_rn(__fsub_rn(m1, 12582912.0f), neg_step, v);
-        lo = __float_as_int(__fmaf_rn(d, scale, 12582912.0f)) - 0x4B400000;
+        lo = __float_as_int(__fmaf_rn(t, ws, mt)) - 0x4B400000;
+    }
+    __device__ __forceinline__ void scaled(float w, float& wh, float& ws) const {
+        wh = __fmul_rn(w, s_hi);
+        ws = __fmul_rn(w, scale);
     }
     __device__ __forceinline__ static unsigned long long join(int hi, int lo) {
         return (unsigned long long)((long long)hi * 524288ll + (long long)lo);
     }
     template <typename T>
-    __device__ __forceinline__ void add(size_t node, T a, T b) const {
+    __device__ __forceinline__ void add2(size_t node, T tx, T ty, T wy) const {
+        float wh, ws;
+        scaled((float)wy, wh, ws);
         int ha, la, hb, lb;
-        split((float)a, ha, la);
-        split((float)b, hb, lb);
+        split2((float)tx, wh, ws, ha, la);
+        split2((float)ty, wh, ws, hb, lb);
         atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), join(ha, la));
         atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].y), join(hb, lb));
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1f(size_t node, T t, T w) const {
+        float wh, ws;
+        scaled((float)w, wh, ws);
+        int h, l;
+        split2((float)t, wh, ws, h, l);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&J[node].x), join(h, l));
     }
     template <typename T>
     __device__ __forceinline__ void add1(size_t node, T a) const {
@@ -204,10 +225,7 @@ k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __rest
             const T tx = rmul(vxi, wx[a]), ty = rmul(vyi, wx[a]);
             const size_t row = (size_t)gi * g.ny;
 #pragma unroll
-            for (int b = 0; b <= P; ++b) {
-                const int gj = wrap_idx(iy + b, g.ny);
-                acc.add(row + gj, rmul(tx, wy[b]), rmul(ty, wy[b]));
-            }
+            for (int b = 0; b <= P; ++b) acc.add2(row + wrap_idx(iy + b, g.ny), tx, ty, wy[b]);
         }
     }
 }
@@ -243,168 +261,9 @@ k_deposit_charge(ParticleGeom g, const T* __restrict__ x, const T* __restrict__ 
 }
 
 
-// Move + deposit over particles sorted by tile and cell (see sort.cu), FP32 form.
-//
-// CTA (tile, split) deposits the particles of one tile into a shared-memory copy of the
-// tile's node region (the tile plus a halo, rows of `pitch` words) and adds the region
-// to the global grid.  Traversal: thread tid serves local cell c = tid mod t^2 and phase
-// f = tid div t^2 and takes, one per round, the particles f, f + F, f + 2F, ... of the
-// CTA's share of that cell (F = threads per cell).  The 32 lanes of a warp thus work on 32
-// consecutive local cells -- a block of 32/t x t cells -- and the row pitch is = t
-// (mod 32), so for each stencil offset their nodes fall in 32 different banks while the
-// particles sit in their sorted cells.
-//
-// Shared atomics are native for 32-bit integers, so each contribution is split exactly
-// into hi * 2^19 + lo (AccFix::split) and the parts are summed apart.  The region is
-// flushed to the global grid every kFlushRounds rounds: a round adds at most one
-// contribution per thread to a node, so between flushes a 32-bit sum holds at most
-// kFlushRounds * 256 = 2^11 terms of magnitude <= 2^19 (< 2^31).  A particle whose
-// stencil leaves the region (it drifted further than the halo) adds the nodes outside
-// straight to the global grid.  Integer sums make the result independent of the order
-// of the particles.
-constexpr int kFlushRounds = 8;
+// The binned FP32 pass keeps its 32-bit region sums in two parts of a contribution:
+// node totals are hi 2^kLoBits + lo (see AccFix::split2).
 constexpr int kLoBits = 19;
-constexpr int kRegionCap = 2560;  // largest region (rx * pitch words), 40 KB for four arrays
-
-template <typename T, int P>
-__global__ void __launch_bounds__(kThreads, 5)
-k_move_deposit_tiled(GeomT<T> g, TileGeom tg, T* __restrict__ x, T* __restrict__ y,
-                     const float4* __restrict__ p4, const int* __restrict__ off, int nsplit,
-                     AccFix acc, unsigned int* __restrict__ err) {
-    // four arrays of R = rx * pitch words: lo_x, lo_y, hi_x, hi_y (sized to the region,
-    // so that the rest of the L1 caches the scattered particle loads)
-    extern __shared__ int sacc[];
-    __shared__ int max_rounds;
-    const int pitch = tg.pitch;
-    const int R = tg.rx * pitch;
-    const int tt = tg.t * tg.t;
-    const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
-    const int cell = threadIdx.x % tt;
-    const int phases = blockDim.x / tt;   // threads per cell in this CTA
-    const int phase = threadIdx.x / tt;
-    const int key = tile * tt + cell;
-    if (threadIdx.x == 0) {  // the tile's particles come to L2 while the region is cleared
-        const int64_t a0 = off[tile * tt], a1 = off[(tile + 1) * tt];
-        prefetch_l2(p4 + a0, (size_t)(a1 - a0) * sizeof(float4));
-    }
-    const int o0 = off[key], count = off[key + 1] - o0;
-    // split s takes the contiguous share [s count / nsplit, (s+1) count / nsplit) of the
-    // cell, so the particles of one 32-byte sector are read by one CTA
-    const int lo_ = (int)((int64_t)count * split / nsplit);
-    const int hi_ = (int)((int64_t)count * (split + 1) / nsplit);
-    const int64_t cbeg = (int64_t)o0 + lo_ + phase;
-    const int streams = phases;
-    const int len = hi_ - lo_;
-    const int mine = len > phase ? (len - phase + phases - 1) / phases : 0;
-    if (threadIdx.x == 0) max_rounds = 0;
-    for (int k = threadIdx.x; k < R; k += blockDim.x) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sacc[q * R + k] = 0;
-    }
-    __syncthreads();
-    atomicMax(&max_rounds, mine);
-    __syncthreads();
-    const int rounds = max_rounds;
-    if (rounds == 0) return;  // empty tile (uniform for the CTA)
-    griddep_wait();  // particles and J come from the previous operations of the stream
-    griddep_launch();
-    const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
-    // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
-    // [0, 2n), so one correction wraps each exactly (whatever the halo)
-    int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
-    if (bi < 0) bi += g.nx;
-    if (bj < 0) bj += g.ny;
-    const T dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
-    unsigned bad = 0;
-    for (int r = 0; r < rounds; ++r) {
-        if (r < mine) {
-            const int64_t p = cbeg + (int64_t)r * streams;
-            const float4 q4 = p4[p];  // one 16-byte load: x, y, vx, vy
-            const T vxi = (T)q4.z, vyi = (T)q4.w;
-            const T xp = move_pos((T)q4.x, vxi, dt, lx);
-            const T yp = move_pos((T)q4.y, vyi, dt, ly);
-            x[p] = xp;
-            y[p] = yp;
-            const T xi = rmul(xp, idx_), yj = rmul(yp, idy);
-            if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
-                bad |= ERR_NONFINITE;
-            } else {
-                T wx[P + 1], wy[P + 1];
-                const int ix = wrap_idx(Shape<P, T>::weights(xi, wx), g.nx);
-                const int iy = wrap_idx(Shape<P, T>::weights(yj, wy), g.ny);
-                int ri0 = ix - bi, rj0 = iy - bj;
-                if (ri0 < 0) ri0 += g.nx;
-                if (rj0 < 0) rj0 += g.ny;
-                if (ri0 + P < tg.rx && rj0 + P < tg.ry) {
-                    // whole stencil in the region: rows ri0.., columns rj0.. (no wrap)
-                    int* row = sacc + ri0 * pitch + rj0;
-#pragma unroll
-                    for (int a = 0; a <= P; ++a) {
-                        const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
-#pragma unroll
-                        for (int b = 0; b <= P; ++b) {
-                            int hx, lx2, hy, ly2;
-                            acc.split((float)rmul(tx_, wy[b]), hx, lx2);
-                            acc.split((float)rmul(ty_, wy[b]), hy, ly2);
-                            atomicAdd(row + b, lx2);
-                            atomicAdd(row + R + b, ly2);
-                            atomicAdd(row + 2 * R + b, hx);
-                            atomicAdd(row + 3 * R + b, hy);
-                        }
-                        row += pitch;
-                    }
-                } else {
-#pragma unroll
-                    for (int a = 0; a <= P; ++a) {
-                        const int gi = wrap_idx(ix + a, g.nx);
-                        int ri = gi - bi;
-                        if (ri < 0) ri += g.nx;
-                        const T tx_ = rmul(vxi, wx[a]), ty_ = rmul(vyi, wx[a]);
-#pragma unroll
-                        for (int b = 0; b <= P; ++b) {
-                            const int gj = wrap_idx(iy + b, g.ny);
-                            int rj = gj - bj;
-                            if (rj < 0) rj += g.ny;
-                            const T cx = rmul(tx_, wy[b]), cy = rmul(ty_, wy[b]);
-                            if (ri < tg.rx && rj < tg.ry) {
-                                int hx, lx2, hy, ly2;
-                                acc.split((float)cx, hx, lx2);
-                                acc.split((float)cy, hy, ly2);
-                                int* c = sacc + ri * pitch + rj;
-                                atomicAdd(c, lx2);
-                                atomicAdd(c + R, ly2);
-                                atomicAdd(c + 2 * R, hx);
-                                atomicAdd(c + 3 * R, hy);
-                            } else {
-                                acc.add((size_t)gi * g.ny + gj, cx, cy);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        if ((r + 1) % kFlushRounds == 0 || r == rounds - 1) {  // uniform in the CTA
-            __syncthreads();
-            for (int k = threadIdx.x; k < R; k += blockDim.x) {
-                const int lx_ = sacc[k], ly_ = sacc[R + k];
-                const int hx = sacc[2 * R + k], hy = sacc[3 * R + k];
-                if (!(lx_ | ly_ | hx | hy)) continue;
-                sacc[k] = sacc[R + k] = sacc[2 * R + k] = sacc[3 * R + k] = 0;
-                const int ri = k / pitch, rj = k - ri * pitch;
-                int gi = bi + ri, gj = bj + rj;
-                if (gi >= g.nx) gi -= g.nx;
-                if (gj >= g.ny) gj -= g.ny;
-                const size_t node = (size_t)gi * g.ny + gj;
-                const long long sx = (long long)hx * (1ll << kLoBits) + (long long)lx_;
-                const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
-                if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
-                if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
-            }
-            __syncthreads();
-        }
-    }
-    if (bad) atomicOr(err, bad);
-}
 
 // Fixed-point (Jx, Jy) sums to complex storage values, times `unscale`.
 template <typename T>
@@ -439,26 +298,23 @@ __device__ __forceinline__ void gather_node(T w, const T* g, T* f) {
 //   u = P^{n+1} - q A,  v^{n+1} = c^2 u / sqrt(c^2 |u|^2 + (m c^2)^2)
 // f = (dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy).  v^{n+1} overwrites
 // v^{n-1}.  Written with explicit roundings, so every kernel gives the same bits.
+// The push from the particle's values (P^n, v^n, v^{n-1}): returns P^{n+1} and v^{n+1}.
 template <typename T>
-__device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t p,
-                                         T* __restrict__ px, T* __restrict__ py,
-                                         const T* __restrict__ vx, const T* __restrict__ vy,
-                                         T* __restrict__ vxo, T* __restrict__ vyo, unsigned& bad,
-                                         double& kin, T& vx_new, T& vy_new) {
-    const T vsx = rfma((T)2, vx[p], -vxo[p]);
-    const T vsy = rfma((T)2, vy[p], -vyo[p]);
+__device__ __forceinline__ void push_core(const PushT<T>& pp, const T* f, T px, T py, T vx, T vy,
+                                          T vxo, T vyo, unsigned& bad, double& kin, T& Px_new,
+                                          T& Py_new, T& vx_new, T& vy_new) {
+    const T vsx = rfma((T)2, vx, -vxo);
+    const T vsy = rfma((T)2, vy, -vyo);
     const T fx = rfma(f[6], vsy, rfma(f[4], vsx, -f[0]));
     const T fy = rfma(f[7], vsy, rfma(f[5], vsx, -f[1]));
-    const T Px = rfma(pp.qdt, fx, px[p]);
-    const T Py = rfma(pp.qdt, fy, py[p]);
+    const T Px = rfma(pp.qdt, fx, px);
+    const T Py = rfma(pp.qdt, fy, py);
     const T ux = rfma(-pp.q, f[2], Px), uy = rfma(-pp.q, f[3], Py);
     const T den = rsqrt_rn(rfma(pp.c2, rfma(ux, ux, rmul(uy, uy)), rmul(pp.mc2, pp.mc2)));
     const T rc = rdiv(pp.c2, den);
     const T vxn1 = rmul(rc, ux), vyn1 = rmul(rc, uy);
-    px[p] = Px;
-    py[p] = Py;
-    vxo[p] = vxn1;
-    vyo[p] = vyn1;
+    Px_new = Px;
+    Py_new = Py;
     vx_new = vxn1;
     vy_new = vyn1;
     if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
@@ -466,6 +322,21 @@ __device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t
         const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
         kin += sqrt(c2d * (uxd * uxd + uyd * uyd) + mc2d * mc2d) - mc2d;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void push_one(const PushT<T>& pp, const T* f, int64_t p,
+                                         T* __restrict__ px, T* __restrict__ py,
+                                         const T* __restrict__ vx, const T* __restrict__ vy,
+                                         T* __restrict__ vxo, T* __restrict__ vyo, unsigned& bad,
+                                         double& kin, T& vx_new, T& vy_new) {
+    T Px, Py;
+    push_core(pp, f, px[p], py[p], vx[p], vy[p], vxo[p], vyo[p], bad, kin, Px, Py, vx_new,
+              vy_new);
+    px[p] = Px;
+    py[p] = Py;
+    vxo[p] = vx_new;
+    vyo[p] = vy_new;
 }
 
 template <typename T>
@@ -541,7 +412,7 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
                     const float* __restrict__ y, float* __restrict__ px,
                     float* __restrict__ py, const float* __restrict__ vx,
                     const float* __restrict__ vy, float* __restrict__ vxo,
-                    float* __restrict__ vyo, float4* __restrict__ p4,
+                    float* __restrict__ vyo,
                     const int* __restrict__ off, int nsplit, const float2* __restrict__ F,
                     double* __restrict__ diag, unsigned int* __restrict__ err) {
     extern __shared__ float4 sf[];  // [rx][ry] nodes, two float4 each
@@ -615,9 +486,428 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
         }
         float vxn1, vyn1;
         push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
-        p4[p] = make_float4(xp, yp, vxn1, vyn1);  // the next deposit's packed input
     }
     push_finish(pp, bad, kin, diag, err);
+}
+
+// ------------------------------------------------------------ binned FP32 pass -----
+//
+// Move + deposit of the FP32 form over tile-sorted particles, and the same pass fused
+// with the gather + push of the step before it (kFused).
+//
+// CTA (tile, split) takes a contiguous share [p0, p1) of one tile's particles and works
+// through it in batches of at most kBinBatch:
+//   A  consecutive lanes take consecutive particles (the SoA loads and stores coalesce;
+//      each thread's next particle is loaded while it works on the current one).  Fused:
+//      gather the eight fields of the step at x^{n+1} from the tile's field region staged
+//      in shared memory, IAEM push (section 4.1) -> P^{n+1}, v^{n+1}.  Then the move
+//      x^{n+2} = x^{n+1} + v^{n+1} dt (the next step's first operation, Algorithm 1).  The
+//      moved particle (x, y, vx, vy) goes to a staging slot, keyed by the region node of its
+//      stencil base; a shared atomic on that key's count gives its rank there.
+//   B  an exclusive scan of the counts over the region's nodes.
+//   C  each staged slot is written at its key's offset plus its rank: the batch is now
+//      binned by stencil base.
+//   D  thread t takes an equal slice of the binned particles (slices spread over the
+//      threads so that the lanes of a warp work in different cells).  Consecutive
+//      particles of a slice mostly share their stencil base and so all (p+1)^2 nodes:
+//      their fixed-point contributions rne(t_a W_y,b scale) are summed exactly in
+//      registers (int32 hi and lo parts, AccFix::split2) and added to the CTA's shared
+//      node region with one set of atomics whenever the base changes, instead of
+//      4 (p+1)^2 atomics per particle.  The stencil rows are summed in passes of at most
+//      two rows (three for quadratic shapes) over the slice, which keeps the sums within
+//      the register budget of four CTAs per SM.
+//   The region is added to the global int64 grid after every batch, which keeps every
+//   32-bit sum exact: a batch adds at most kBinBatch = 2^10 contributions of magnitude
+//   <= 2^19 to a node.
+// A particle whose stencil leaves the region (it drifted further than the halo) adds its
+// contributions straight to the global grid.  The integer sums make J independent of the
+// order of the particles and of how they are grouped, so the result is the same bits as
+// every other deposit of the FP32 form.
+constexpr int kBinBatch = 1024;
+constexpr int kBinSmemMax = 100 * 1024;  // four CTAs per SM fit up to 56 KB each
+
+// Byte offsets in the binned pass's dynamic shared memory (stage first: 16-byte aligned).
+struct BinLayout {
+    int fields;   // kFused: the gather fields of the region, [rx][ry] x 2 float4
+    int kr;       // int [kBinBatch]: key | rank << 16 of each staged particle (-1: none)
+    int idx;      // uint16 [kBinBatch]: staging slots in binned order
+    int racc;     // int [4 rx ry]: lo_x, lo_y, hi_x, hi_y node sums
+    int cnt;      // int [rx ry + 1]: counts, then offsets
+    int bytes;
+};
+__host__ __device__ inline BinLayout bin_layout(const TileGeom& tg, int p, bool fused) {
+    BinLayout l;
+    int o = kBinBatch * 16;  // stage: (x, y, vx, vy) of each particle, arrival order
+    l.fields = o;
+    if (fused) o += tg.rx * tg.ry * 32;
+    l.kr = o;
+    o += kBinBatch * 4;
+    l.idx = o;
+    o += kBinBatch * 2;
+    o = (o + 15) & ~15;
+    l.racc = o;
+    o += 4 * tg.rx * tg.ry * 4;
+    l.cnt = o;
+    o += (tg.rx * tg.ry + 1) * 4;
+    l.bytes = (o + 15) & ~15;
+    return l;
+}
+
+// Exclusive scan of one value per thread over the CTA (kThreads); sets *total.
+__device__ __forceinline__ int cta_exclusive_scan(int v, int* wsum, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = lane < kThreads / 32 ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kThreads / 32) wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    *total = wsum[32];
+    return wsum[warp] + inc - v;
+}
+
+// Register sums of stencil rows A0..A1-1 of one base node: s[a][b] = (lo_x, lo_y, hi_x, hi_y).
+template <int P, int NA>
+struct RowSums {
+    int s[NA][P + 1][4];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int b = 0; b <= P; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[a][b][q] = 0;
+    }
+    // adds them to the region at node0 (rows of ry nodes; the four planes R apart)
+    __device__ __forceinline__ void flush(int* __restrict__ node0, int ry, int R) const {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            int* row = node0 + a * ry;
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                atomicAdd(row + b, s[a][b][0]);
+                atomicAdd(row + R + b, s[a][b][1]);
+                atomicAdd(row + 2 * R + b, s[a][b][2]);
+                atomicAdd(row + 3 * R + b, s[a][b][3]);
+            }
+        }
+    }
+};
+
+// Deposit of the binned particles [k0, k1) (sidx order) for stencil rows A0..A1-1: the
+// contributions are summed in registers while the key (the region node of the stencil
+// base) stays the same.
+template <int P, int A0, int A1>
+__device__ __forceinline__ void bin_slice_rows(const float4* __restrict__ stage,
+                                               const int* __restrict__ kr,
+                                               const uint16_t* __restrict__ sidx, int k0, int k1,
+                                               float idx_, float idy, const AccFix& acc,
+                                               int* __restrict__ racc, int ry, int R) {
+    RowSums<P, A1 - A0> rs;
+    rs.clear();
+    int cur = -1;
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        const int slot = sidx[k];
+        const int key = kr[slot] & 0xFFFF;
+        const float4 q4 = stage[slot];
+        if (key != cur) {
+            if (cur >= 0) {
+                rs.flush(racc + cur + A0 * ry, ry, R);
+                rs.clear();
+            }
+            cur = key;
+        }
+        float wx[P + 1], wy[P + 1];
+        Shape<P, float>::weights(rmul(q4.x, idx_), wx);
+        Shape<P, float>::weights(rmul(q4.y, idy), wy);
+#pragma unroll
+        for (int a = 0; a < A1 - A0; ++a) {
+            const float tx = rmul(q4.z, wx[A0 + a]), ty = rmul(q4.w, wx[A0 + a]);
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                float wh, ws;
+                acc.scaled(wy[b], wh, ws);
+                int hx, lx, hy, ly;
+                AccFix::split2(tx, wh, ws, hx, lx);
+                AccFix::split2(ty, wh, ws, hy, ly);
+                rs.s[a][b][0] += lx;
+                rs.s[a][b][1] += ly;
+                rs.s[a][b][2] += hx;
+                rs.s[a][b][3] += hy;
+            }
+        }
+    }
+    if (cur >= 0) rs.flush(racc + cur + A0 * ry, ry, R);
+}
+
+// Gather of the eight fields at (xi, yj) (cell units) from the region staged in shared
+// memory (sf: [rx][ry] nodes of two float4), or from the global fields F when the stencil
+// leaves the region; the node order and roundings of k_gather_push.
+template <int P>
+__device__ __forceinline__ void gather_region(const GeomT<float>& g, const float4* sf,
+                                              const float2* __restrict__ F, int bi, int bj,
+                                              int rx, int ry, float xi, float yj, float* f) {
+    float wx[P + 1], wy[P + 1];
+    const int ix = wrap_idx(Shape<P, float>::weights(xi, wx), g.nx);
+    const int iy = wrap_idx(Shape<P, float>::weights(yj, wy), g.ny);
+    int ri0 = ix - bi, rj0 = iy - bj;
+    if (ri0 < 0) ri0 += g.nx;
+    if (rj0 < 0) rj0 += g.ny;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = 0.f;
+    if (ri0 + P < rx && rj0 + P < ry) {
+        const float4* row = sf + 2 * (ri0 * ry + rj0);
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const float4 u = row[2 * b], v = row[2 * b + 1];
+                const float gv[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+                gather_node(rmul(wx[a], wy[b]), gv, f);
+            }
+            row += 2 * ry;
+        }
+    } else {
+#pragma unroll 1
+        for (int a = 0; a <= P; ++a) {
+            const int gi = wrap_idx(ix + a, g.nx);
+#pragma unroll
+            for (int b = 0; b <= P; ++b) {
+                const int gj = wrap_idx(iy + b, g.ny);
+                float gv[8];
+                load_node(F + ((size_t)gi * g.ny + gj) * 4, gv);
+                gather_node(rmul(wx[a], wy[b]), gv, f);
+            }
+        }
+    }
+}
+
+// Stencil base node (first node with a nonzero weight) of a position in cell units: the
+// node Shape<P>::weights returns.
+template <int P>
+__device__ __forceinline__ int stencil_base(float xi) {
+    if constexpr (P % 2 == 0) return (int)floor(radd(xi, 0.5f)) - P / 2;
+    return (int)floor(xi) - (P - 1) / 2;
+}
+
+template <int P, bool kFused>
+__global__ void __launch_bounds__(kThreads, kFused ? 3 : 4)
+k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, float* __restrict__ x,
+                 float* __restrict__ y, float* __restrict__ px, float* __restrict__ py,
+                 const float* __restrict__ vx, const float* __restrict__ vy,
+                 float* __restrict__ vxo, float* __restrict__ vyo, const int* __restrict__ off,
+                 int nsplit, const float2* __restrict__ F, AccFix acc,
+                 double* __restrict__ diag, unsigned int* __restrict__ err) {
+    constexpr int NF = kFused ? 8 : 4;  // values loaded per particle
+    extern __shared__ float4 bin_smem[];
+    __shared__ int wsum[33];
+    const BinLayout L = bin_layout(tg, P, kFused);
+    char* base = reinterpret_cast<char*>(bin_smem);
+    float4* stage = bin_smem;
+    const float4* sf = reinterpret_cast<const float4*>(base + L.fields);
+    int* kr = reinterpret_cast<int*>(base + L.kr);
+    uint16_t* sidx = reinterpret_cast<uint16_t*>(base + L.idx);
+    int* racc = reinterpret_cast<int*>(base + L.racc);
+    int* cnt = reinterpret_cast<int*>(base + L.cnt);
+
+    const int tt = tg.t * tg.t;
+    const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+    const int64_t t0 = off[tile * tt], tcnt = (int64_t)off[(tile + 1) * tt] - t0;
+    const int64_t p0 = t0 + tcnt * split / nsplit, p1 = t0 + tcnt * (split + 1) / nsplit;
+    if (p0 == p1) return;  // uniform for the CTA
+    const int rx = tg.rx, ry = tg.ry, R = rx * ry;
+    if (threadIdx.x < NF) {  // the CTA's particles come to L2 meanwhile
+        const float* arr[8] = {x, y, vx, vy, px, py, vxo, vyo};
+        prefetch_l2(arr[threadIdx.x] + p0, (size_t)(p1 - p0) * sizeof(float));
+    }
+    for (int k = threadIdx.x; k < 4 * R; k += kThreads) racc[k] = 0;
+    for (int k = threadIdx.x; k <= R; k += kThreads) cnt[k] = 0;
+    const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
+    // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
+    // [0, 2n), so one correction wraps each exactly (whatever the halo)
+    int bi = (tx * tg.t - tg.halo) % g.nx, bj = (ty * tg.t - tg.halo) % g.ny;
+    if (bi < 0) bi += g.nx;
+    if (bj < 0) bj += g.ny;
+    griddep_wait();  // particles, fields and J come from the previous operations
+    griddep_launch();
+    if (kFused) {
+        float4* sfw = reinterpret_cast<float4*>(base + L.fields);
+        const float4* F4 = reinterpret_cast<const float4*>(F);
+        for (int k = threadIdx.x; k < 2 * R; k += kThreads) {
+            const int node = k >> 1;
+            const int ri = node / ry, rj = node - ri * ry;
+            int gi = bi + ri, gj = bj + rj;
+            if (gi >= g.nx) gi -= g.nx;
+            if (gj >= g.ny) gj -= g.ny;
+            sfw[k] = __ldg(F4 + ((size_t)gi * g.ny + gj) * 2 + (k & 1));
+        }
+    }
+    __syncthreads();
+    const float dt = g.dt, lx = g.lx, ly = g.ly, idx_ = g.inv_dx, idy = g.inv_dy;
+    // per-thread segment of the region's nodes for the scan
+    const int seg = (R + kThreads - 1) / kThreads;
+    const int c0 = min(R, (int)threadIdx.x * seg), c1 = min(R, c0 + seg);
+    // the slice of the binned particles this thread deposits: 33 is odd, so t -> 33 t mod
+    // kThreads is a permutation, and the lanes of a warp take slices 33 apart
+    const int slice = (33 * (int)threadIdx.x) & (kThreads - 1);
+    double kin = 0.0;
+    unsigned bad = 0;
+    for (int64_t b0 = p0; b0 < p1; b0 += kBinBatch) {
+        const int nb = (int)min((int64_t)kBinBatch, p1 - b0);
+        // A: (gather + push,) move, stage and count; the next particle's loads are in flight
+        float cur[NF], nxt[NF];
+        auto load = [&](float* r, int i) {
+            if (i < nb) {
+                const int64_t p = b0 + i;
+                r[0] = x[p];
+                r[1] = y[p];
+                r[2] = vx[p];
+                r[3] = vy[p];
+                if (kFused) {
+                    r[4] = px[p];
+                    r[5] = py[p];
+                    r[6] = vxo[p];
+                    r[7] = vyo[p];
+                }
+            }
+        };
+        load(cur, threadIdx.x);
+#pragma unroll 1
+        for (int i = threadIdx.x; i < nb; i += kThreads) {
+            load(nxt, i + kThreads);
+            const int64_t p = b0 + i;
+            float xs = cur[0], ys = cur[1], vxs = cur[2], vys = cur[3];
+            int key = -1;
+            bool ok = true;
+            if (kFused) {
+                const float xi = rmul(xs, idx_), yj = rmul(ys, idy);
+                if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+                    bad |= ERR_NONFINITE;
+                    ok = false;
+                } else {
+                    float f[8];
+                    gather_region<P>(g, sf, F, bi, bj, rx, ry, xi, yj, f);
+                    float Px, Py;
+                    push_core(pp, f, cur[4], cur[5], cur[2], cur[3], cur[6], cur[7], bad, kin, Px,
+                              Py, vxs, vys);
+                    px[p] = Px;
+                    py[p] = Py;
+                    vxo[p] = vxs;
+                    vyo[p] = vys;
+                }
+            }
+            if (ok) {
+                xs = move_pos(xs, vxs, dt, lx);
+                ys = move_pos(ys, vys, dt, ly);
+                x[p] = xs;
+                y[p] = ys;
+                const float xi = rmul(xs, idx_), yj = rmul(ys, idy);
+                if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
+                    bad |= ERR_NONFINITE;
+                } else {
+                    const int ix = wrap_idx(stencil_base<P>(xi), g.nx);
+                    const int iy = wrap_idx(stencil_base<P>(yj), g.ny);
+                    int ri0 = ix - bi, rj0 = iy - bj;
+                    if (ri0 < 0) ri0 += g.nx;
+                    if (rj0 < 0) rj0 += g.ny;
+                    if (ri0 + P < rx && rj0 + P < ry) {
+                        key = ri0 * ry + rj0;
+                    } else {  // beyond the region: straight to the global grid
+                        float wx[P + 1], wy[P + 1];
+                        Shape<P, float>::weights(xi, wx);
+                        Shape<P, float>::weights(yj, wy);
+#pragma unroll 1
+                        for (int a = 0; a <= P; ++a) {
+                            const int gi = wrap_idx(ix + a, g.nx);
+                            const float tx_ = rmul(vxs, wx[a]), ty_ = rmul(vys, wx[a]);
+#pragma unroll
+                            for (int b = 0; b <= P; ++b)
+                                acc.add2((size_t)gi * g.ny + wrap_idx(iy + b, g.ny), tx_, ty_,
+                                         wy[b]);
+                        }
+                    }
+                }
+            }
+            if (key >= 0) {
+                stage[i] = make_float4(xs, ys, vxs, vys);
+                kr[i] = key | (atomicAdd(cnt + key, 1) << 16);
+            } else {
+                kr[i] = -1;
+            }
+#pragma unroll
+            for (int q = 0; q < NF; ++q) cur[q] = nxt[q];
+        }
+        __syncthreads();
+        // B: exclusive scan of the counts over the region's nodes
+        int local = 0;
+        for (int c = c0; c < c1; ++c) local += cnt[c];
+        int total;
+        int run = cta_exclusive_scan(local, wsum, &total);
+        for (int c = c0; c < c1; ++c) {
+            const int v = cnt[c];
+            cnt[c] = run;
+            run += v;
+        }
+        __syncthreads();
+        // C: binned order of the staging slots
+        for (int i = threadIdx.x; i < nb; i += kThreads) {
+            const int k = kr[i];
+            if (k >= 0) sidx[cnt[k & 0xFFFF] + (k >> 16)] = (uint16_t)i;
+        }
+        __syncthreads();
+        // D: equal slices of the binned particles, summed in registers per key
+        {
+            const int per = (total + kThreads - 1) / kThreads;
+            const int k0 = min(total, slice * per), k1 = min(total, k0 + per);
+            if constexpr (P == 2) {
+                bin_slice_rows<P, 0, 3>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
+            } else {
+                bin_slice_rows<P, 0, 2>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
+                bin_slice_rows<P, 2, 4>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
+                if constexpr (P == 4)
+                    bin_slice_rows<P, 4, 5>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
+            }
+        }
+        __syncthreads();
+        // the batch's region sums to the global grid; counts cleared for the next batch
+        for (int k = threadIdx.x; k < R; k += kThreads) {
+            const int lx_ = racc[k], ly_ = racc[R + k];
+            const int hx = racc[2 * R + k], hy = racc[3 * R + k];
+            if (!(lx_ | ly_ | hx | hy)) continue;
+            racc[k] = racc[R + k] = racc[2 * R + k] = racc[3 * R + k] = 0;
+            const int ri = k / ry, rj = k - ri * ry;
+            int gi = bi + ri, gj = bj + rj;
+            if (gi >= g.nx) gi -= g.nx;
+            if (gj >= g.ny) gj -= g.ny;
+            const size_t node = (size_t)gi * g.ny + gj;
+            const long long sx = (long long)hx * (1ll << kLoBits) + (long long)lx_;
+            const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
+            if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
+            if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
+        }
+        for (int k = threadIdx.x; k <= R; k += kThreads) cnt[k] = 0;
+        __syncthreads();
+    }
+    if (kFused) {
+        push_finish(pp, bad, kin, diag, err);
+    } else if (bad) {
+        atomicOr(err, bad);
+    }
 }
 
 template <typename T, int P>
@@ -744,7 +1034,7 @@ k_deposit_z(GeomT<T> g, const T* __restrict__ x, const T* __restrict__ y,
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
             const T tz = rmul(vzi, wx[a]);
 #pragma unroll
-            for (int b = 0; b <= P; ++b) acc.add1(row + wrap_idx(iy + b, g.ny), rmul(tz, wy[b]));
+            for (int b = 0; b <= P; ++b) acc.add1f(row + wrap_idx(iy + b, g.ny), tz, wy[b]);
         }
     }
 }
@@ -1049,39 +1339,6 @@ cudaError_t launch_init_particles3(int p, const ParticleGeom& g, const PushParam
 
 
 template <typename T>
-cudaError_t launch_move_deposit_tiled(int p, const ParticleGeom& g, const TileGeom& tg, T* x,
-                                      T* y, const float4* p4, int64_t n, const int* off,
-                                      void* j, bool fix, float scale, unsigned int* err,
-                                      cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    if (!fix) return cudaErrorInvalidValue;  // the tiled pass is the fixed-point form's
-    if (tg.t * tg.t > kThreads || kThreads % (tg.t * tg.t) != 0) return cudaErrorInvalidValue;
-    // splits per tile: about 1366 particles (5 or 6 rounds of 256) per CTA at the mean
-    // density, so that a grid of 64-per-cell tiles holds about five CTAs per SM (timed
-    // fastest of 512..2048 on a 128 x 128 grid with 2^20 particles)
-    const int ntiles = tg.ntx * tg.nty;
-    int nsplit = (int)((n + (int64_t)ntiles * 1366 - 1) / ((int64_t)ntiles * 1366));
-    if (nsplit < 1) nsplit = 1;
-    if (nsplit > 64) nsplit = 64;
-    const int blocks = ntiles * nsplit;
-    if (tg.rx * tg.pitch > kRegionCap || tg.ry > tg.pitch) return cudaErrorInvalidValue;
-    const AccFix acc = AccFix::make(j, scale);
-    const size_t smem = (size_t)4 * tg.rx * tg.pitch * sizeof(int);
-#define GPIC_TILED(PP)                                                                     \
-    e = launch_pdl(k_move_deposit_tiled<T, PP>, dim3(blocks), dim3(kThreads), smem, s,        \
-                   typed<T>(g), tg, x, y, p4, off, nsplit, acc, err);
-    cudaError_t e = cudaSuccess;
-    switch (p) {
-        case 2: GPIC_TILED(2) break;
-        case 3: GPIC_TILED(3) break;
-        case 4: GPIC_TILED(4) break;
-        default: return cudaErrorInvalidValue;
-    }
-#undef GPIC_TILED
-    return e;
-}
-
-template <typename T>
 cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,
                                cudaStream_t s) {
     k_fix_to_cplx<T><<<blocks_for(n), kThreads, 0, s>>>(j, unscale, (cplx_t<T>*)out, n);
@@ -1108,7 +1365,7 @@ cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& p
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,
                                     const TileGeom& tg, const float* x, const float* y, float* px,
                                     float* py, const float* vx, const float* vy, float* vxo,
-                                    float* vyo, float4* p4, int64_t n, const int* off,
+                                    float* vyo, int64_t n, const int* off,
                                     const void* f, double* diag, unsigned int* err,
                                     cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -1130,7 +1387,7 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
         if (e == cudaSuccess)                                                                  \
             e = launch_pdl(k_gather_push_tiled<PP>, dim3(blocks), dim3(kThreads), smem, s,     \
                            typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo,   \
-                           vyo, p4, off, nsplit, (const float2*)f, diag, err);                 \
+                           vyo, off, nsplit, (const float2*)f, diag, err);                     \
     }
     switch (p) {
         case 2: GPIC_GTILED(2) break;
@@ -1139,6 +1396,50 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
         default: return cudaErrorInvalidValue;
     }
 #undef GPIC_GTILED
+    return e;
+}
+
+bool deposit_binned_fits(const TileGeom& tg, int p, bool fused) {
+    return tg.rx > p && tg.ry > p && tg.rx * tg.ry < (1 << 16) &&
+           bin_layout(tg, p, fused).bytes <= kBinSmemMax;
+}
+
+cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
+                                  const TileGeom& tg, float* x, float* y, float* px, float* py,
+                                  const float* vx, const float* vy, float* vxo, float* vyo,
+                                  int64_t n, const int* off, const void* fields4, void* j,
+                                  float scale, double* diag, unsigned int* err, cudaStream_t s,
+                                  bool fused, int per_cta) {
+    if (n == 0) return cudaSuccess;
+    if (!deposit_binned_fits(tg, p, fused) || per_cta < 1) return cudaErrorInvalidValue;
+    const int ntiles = tg.ntx * tg.nty;
+    int nsplit = (int)((n + (int64_t)ntiles * per_cta - 1) / ((int64_t)ntiles * per_cta));
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 64) nsplit = 64;
+    const int blocks = ntiles * nsplit;
+    const size_t smem = (size_t)bin_layout(tg, p, fused).bytes;
+    const AccFix acc = AccFix::make(j, scale);
+    cudaError_t e = cudaSuccess;
+#define GPIC_BINNED(PP, FF)                                                                    \
+    {                                                                                          \
+        static const cudaError_t attr = cudaFuncSetAttribute(                                  \
+            k_deposit_binned<PP, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemMax); \
+        e = attr;                                                                              \
+        if (e == cudaSuccess)                                                                  \
+            e = launch_pdl(k_deposit_binned<PP, FF>, dim3(blocks), dim3(kThreads), smem, s,    \
+                           typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo,   \
+                           vyo, off, nsplit, (const float2*)fields4, acc, diag, err);          \
+    }
+    switch (p * 2 + (fused ? 1 : 0)) {
+        case 4: GPIC_BINNED(2, false) break;
+        case 5: GPIC_BINNED(2, true) break;
+        case 6: GPIC_BINNED(3, false) break;
+        case 7: GPIC_BINNED(3, true) break;
+        case 8: GPIC_BINNED(4, false) break;
+        case 9: GPIC_BINNED(4, true) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPIC_BINNED
     return e;
 }
 
@@ -1229,11 +1530,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                       unsigned int*, cudaStream_t,                \
                                                       const int32_t*, const SpeciesParams*);      \
     template cudaError_t launch_fix_to_cplx<T>(const longlong2*, double, void*, int64_t,          \
-                                               cudaStream_t);                                     \
-    template cudaError_t launch_move_deposit_tiled<T>(int, const ParticleGeom&, const TileGeom&,  \
-                                                      T*, T*, const float4*, int64_t,             \
-                                                      const int*, void*, bool, float,             \
-                                                      unsigned int*, cudaStream_t);
+                                               cudaStream_t);
 GPIC_INST(double)
 GPIC_INST(float)
 #undef GPIC_INST

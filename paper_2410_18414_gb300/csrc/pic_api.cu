@@ -40,7 +40,8 @@ void nvtx_push(const char* name) {
 
 const char* timer_name(int which) {
     static const char* const names[PIC_KT_COUNT] = {
-        "sort", "deposit", "field_solve", "gather_push", "adj_push", "adj_field", "adj_deposit"};
+        "sort", "deposit", "field_solve", "gather_push", "adj_push", "adj_field", "adj_deposit",
+        "gather_deposit"};
     return which >= 0 && which < PIC_KT_COUNT ? names[which] : "?";
 }
 
@@ -254,7 +255,6 @@ pic_status alloc_state(pic_handle* h) {
         const size_t nt = (size_t)h->tg.nkeys() + 1;
         CK(dalloc(h, (void**)&h->hist, nt * sizeof(int)));
         CK(cudaMemsetAsync(h->hist, 0, nt * sizeof(int), h->s));  // kept zero by the sort's scan
-        if (h->fp32) CK(dalloc(h, (void**)&h->p4, (size_t)std::max<int64_t>(h->n, 1) * sizeof(float4)));
         CK(dalloc(h, (void**)&h->off, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->cursor, nt * sizeof(int)));
         CK(dalloc(h, (void**)&h->bsum, sort_scan_chunks(h->tg.nkeys()) * sizeof(int)));
@@ -469,6 +469,21 @@ bool diag_due(const pic_handle* h) {
     return h->diag_every > 0 && ((h->step + 1) % h->diag_every) == 0;
 }
 
+// Particles per CTA of the binned FP32 deposit (one batch of its shared-memory binning).
+constexpr int kBinPerCta = 2048;
+
+// Whether the gather + push of the step now finishing (step h->step + 1) may run fused with
+// the next step's move + deposit: the sorted FP32 form, the next step does not sort (its
+// keys need the pushed velocities before the move), and the tile regions fit the fused
+// kernel's shared memory.
+bool fuse_next(const pic_handle* h) {
+    if (!(h->sorting && h->fp32) || h->vdim != 2 || h->spp.n > 0) return false;
+    if ((h->step + 1) % h->cfg.sort_interval == 0) return false;
+    return deposit_binned_fits(h->tg, h->p, true);
+}
+
+pic_status gather_push_step(pic_handle* h, bool fuse);
+
 pic_status sort_particles(pic_handle* h) {
     void** cur[8] = {&h->x, &h->y, &h->px, &h->py, &h->v[0][0], &h->v[0][1], &h->v[1][0], &h->v[1][1]};
     CK(by_prec(h, [&](auto t) {
@@ -482,7 +497,7 @@ pic_status sort_particles(pic_handle* h) {
         dst.id = h->id_alt;
         // cur[4 + 2 vcur] is v^n_x, the velocity of this step's move
         return launch_tile_sort<T>(h->tg, src, dst, h->n, 4 + 2 * h->vcur, h->keys, h->hist,
-                                   h->off, h->cursor, h->bsum, h->fp32 ? h->p4 : nullptr, h->s);
+                                   h->off, h->cursor, h->bsum, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
@@ -634,10 +649,16 @@ pic_status pic_deposit(pic_handle* h) {
     TimedScope ts(h, PIC_KT_DEPOSIT);
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
-        if (h->sorting && h->fp32)
-            return launch_move_deposit_tiled<T>(h->p, h->geom, h->tg, (T*)h->x, (T*)h->y,
-                                                h->p4, h->n, h->off, h->J, h->fp32,
-                                                h->fix_scale_j, h->err, h->s);
+        if (h->sorting && h->fp32 && deposit_binned_fits(h->tg, h->p, false)) {
+            const int vo = 1 - h->vcur;
+            return launch_deposit_binned(h->p, h->geom, h->push, h->tg, (float*)h->x,
+                                         (float*)h->y, (float*)h->px, (float*)h->py,
+                                         (const float*)h->v[h->vcur][0],
+                                         (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
+                                         (float*)h->v[vo][1], h->n, h->off, nullptr, h->J,
+                                         h->fix_scale_j, h->diag, h->err, h->s, false,
+                                         kBinPerCta);
+        }
         const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
         if (h->fp32)
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
@@ -798,18 +819,49 @@ pic_status pic_field_solve(pic_handle* h) {
     return PIC_OK;
 }
 
-pic_status pic_gather_push(pic_handle* h) {
+pic_status pic_gather_push(pic_handle* h) { return gather_push_step(h, false); }
+
+pic_status pic_step(pic_handle* h, int32_t nsteps) {
+    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
+    if (nsteps < 0) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    for (int32_t i = 0; i < nsteps; ++i) {
+        NvtxRange r("step");
+        // a step whose deposit ran fused with the previous gather starts deposited
+        pic_status st = h->phase == 1 && h->fused_deposit ? PIC_OK : pic_deposit(h);
+        if (st == PIC_OK) st = pic_field_solve(h);
+        // the last step of the call is not fused: the call returns between two steps
+        if (st == PIC_OK) st = gather_push_step(h, i + 1 < nsteps && fuse_next(h));
+        if (st != PIC_OK) return st;
+    }
+    return PIC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Gather + push of the step (a8, a9); with `fuse`, the sorted FP32 form's binned kernel
+// also moves the particles and deposits the next step's current (its a2, a3) into the
+// buffer the field solve just cleared, and the handle is left with that deposit done.
+pic_status gather_push_step(pic_handle* h, bool fuse) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (h->phase != 2) return fail(h, PIC_ERR_STATE, "pic_gather_push needs pic_field_solve first");
     PushParams pp = h->push;
     pp.diag = h->diag_now ? 1 : 0;
     const int vo = 1 - h->vcur;
-    if (h->sorting && h->fp32) {
+    if (fuse) {
+        TimedScope ts(h, PIC_KT_GATHER_DEPOSIT);
+        CK(launch_deposit_binned(h->p, h->geom, pp, h->tg, (float*)h->x, (float*)h->y,
+                                 (float*)h->px, (float*)h->py, (const float*)h->v[h->vcur][0],
+                                 (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
+                                 (float*)h->v[vo][1], h->n, h->off, h->G, h->Jalt,
+                                 h->fix_scale_j, h->diag, h->err, h->s, true, kBinPerCta));
+    } else if (h->sorting && h->fp32) {
         TimedScope ts(h, PIC_KT_GATHER);
         CK(launch_gather_push_tiled(h->p, h->geom, pp, h->tg, (const float*)h->x,
                                     (const float*)h->y, (float*)h->px, (float*)h->py,
                                     (const float*)h->v[h->vcur][0], (const float*)h->v[h->vcur][1],
-                                    (float*)h->v[vo][0], (float*)h->v[vo][1], h->p4, h->n,
+                                    (float*)h->v[vo][0], (float*)h->v[vo][1], h->n,
                                     h->off, h->G,
                                     h->diag, h->err, h->s));
     } else if (h->vdim == 3 || h->spp.n > 0) {
@@ -853,25 +905,19 @@ pic_status pic_gather_push(pic_handle* h) {
         }
     }
     h->phase = 0;
-    return PIC_OK;
-}
-
-pic_status pic_step(pic_handle* h, int32_t nsteps) {
-    if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
-    if (nsteps < 0) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 0");
-    for (int32_t i = 0; i < nsteps; ++i) {
-        NvtxRange r("step");
-        pic_status st = pic_deposit(h);
-        if (st == PIC_OK) st = pic_field_solve(h);
-        if (st == PIC_OK) st = pic_gather_push(h);
-        if (st != PIC_OK) return st;
+    h->fused_deposit = false;
+    if (fuse) {  // the next step's deposit is done: J^{n+2} sits in the buffer it reads
+        std::swap(h->J, h->Jalt);
+        h->launches_now = 0;
+        h->phase = 1;
+        h->fused_deposit = true;
     }
     return PIC_OK;
 }
 
-// ------------------------------------------------------------ ensembles ----
+}  // namespace
 
-}  // extern "C"
+// ------------------------------------------------------------ ensembles ----
 
 struct pic_ensemble {
     std::vector<pic_handle*> runs;

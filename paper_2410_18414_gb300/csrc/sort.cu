@@ -59,9 +59,11 @@ k_sort_keys(TileGeom tg, const T* __restrict__ x, const T* __restrict__ y,
         const int64_t p = b + threadIdx.x;
         int k = -1;
         if (p < n) {
-            // the cell the particle will deposit from after this step's move, so that the
-            // step right after a sort sees no drift from the sorted cells
-            k = tile_key(move_pos(x[p], vx[p], dt, lx), move_pos(y[p], vy[p], dt, ly), tg);
+            // the cell the particle will deposit from after this step's move (vx NULL: the
+            // particle has moved already), so that the deposit right after a sort sees no
+            // drift from the sorted cells
+            k = vx ? tile_key(move_pos(x[p], vx[p], dt, lx), move_pos(y[p], vy[p], dt, ly), tg)
+                   : tile_key(x[p], y[p], tg);
             keys[p] = k;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, k);
@@ -151,7 +153,7 @@ k_scan_add(int nkeys, int nchunks, const int* __restrict__ bsum, int* __restrict
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ keys, int64_t n,
-               int* __restrict__ cursor, float4* __restrict__ p4, int vidx) {
+               int* __restrict__ cursor) {
     const int lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * kScatterPer + threadIdx.x;
     griddep_wait();
@@ -186,19 +188,8 @@ k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ key
                 dst.a[a][q] = v[a];
             }
             dst.id[q] = src.id[p];
-            if (p4)  // the deposit's packed input: position and the velocity of its move
-                p4[q] = make_float4((float)v[0], (float)v[1], (float)(vidx == 4 ? v[4] : v[6]),
-                                    (float)(vidx == 4 ? v[5] : v[7]));
         }
     }
-}
-
-__global__ void k_pack_p4(const float* __restrict__ x, const float* __restrict__ y,
-                          const float* __restrict__ vx, const float* __restrict__ vy,
-                          float4* __restrict__ p4, int64_t n) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        p4[p] = make_float4(x[p], y[p], vx[p], vy[p]);
 }
 
 __global__ void k_iota(int32_t* __restrict__ id, int64_t n) {
@@ -214,14 +205,15 @@ int sort_scan_chunks(int nkeys) { return (nkeys + kScanChunk - 1) / kScanChunk; 
 template <typename T>
 cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T> dst, int64_t n,
                              int vidx, int* keys, int* hist, int* off, int* cursor, int* bsum,
-                             float4* p4, cudaStream_t s) {
-    if (vidx != 4 && vidx != 6) return cudaErrorInvalidValue;
+                             cudaStream_t s) {
+    if (vidx != 4 && vidx != 6 && vidx != -1) return cudaErrorInvalidValue;
     // hist is all zero on entry: zeroed once at allocation, then by every scan
     const int nkeys = tg.nkeys();  // number of sort keys (cells, tile-major)
     if (n == 0) return cudaMemsetAsync(off, 0, sizeof(int) * (nkeys + 1), s);
     cudaError_t e = launch_pdl(k_sort_keys<T>, dim3(blocks_for(n)), dim3(kThreads), 0, s, tg,
-                   (const T*)src.a[0], (const T*)src.a[1], (const T*)src.a[vidx],
-                   (const T*)src.a[vidx + 1], n, keys, hist);
+                   (const T*)src.a[0], (const T*)src.a[1],
+                   vidx < 0 ? nullptr : (const T*)src.a[vidx],
+                   vidx < 0 ? nullptr : (const T*)src.a[vidx + 1], n, keys, hist);
     const int nchunks = sort_scan_chunks(nkeys);
     if (e == cudaSuccess)
         e = launch_pdl(k_scan_local, dim3(nchunks), dim3(kScanThreads), 0, s, hist, nkeys, off,
@@ -232,15 +224,8 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
     const int64_t per_cta = (int64_t)kThreads * kScatterPer;
     if (e == cudaSuccess)
         e = launch_pdl(k_sort_scatter<T>, dim3((unsigned)((n + per_cta - 1) / per_cta)),
-                       dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor, p4, vidx);
+                       dim3(kThreads), 0, s, src, dst, (const int*)keys, n, cursor);
     return e;
-}
-
-cudaError_t launch_pack_p4(const float* x, const float* y, const float* vx, const float* vy,
-                           float4* p4, int64_t n, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    k_pack_p4<<<blocks_for(n), kThreads, 0, s>>>(x, y, vx, vy, p4, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {
@@ -251,9 +236,9 @@ cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s) {
 
 template cudaError_t launch_tile_sort<float>(const TileGeom&, SortArrays<float>, SortArrays<float>,
                                              int64_t, int, int*, int*, int*, int*, int*,
-                                             float4*, cudaStream_t);
+                                             cudaStream_t);
 template cudaError_t launch_tile_sort<double>(const TileGeom&, SortArrays<double>,
                                               SortArrays<double>, int64_t, int, int*, int*, int*,
-                                              int*, int*, float4*, cudaStream_t);
+                                              int*, int*, cudaStream_t);
 
 }  // namespace gpic

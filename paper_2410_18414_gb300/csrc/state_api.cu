@@ -213,14 +213,9 @@ pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
     h->diag_valid = h->e_valid = false;
     // the diagnostics log restarts: records of steps before the load are not returned
     h->ring_read = h->ring_written;
-    if (h->fp32) {
-        // the buffer the next deposit sums into starts at zero (the row transform keeps it so)
+    if (h->fp32)  // the buffer the next deposit sums into starts at zero (the row
+                  // transform keeps it so)
         CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));
-        if (h->sorting)
-            CK(launch_pack_p4((const float*)h->x, (const float*)h->y,
-                              (const float*)h->v[h->vcur][0], (const float*)h->v[h->vcur][1], h->p4,
-                              h->n, h->s));
-    }
     CK(cudaStreamSynchronize(h->s));  // src may be released on return
     return check_device_error(h);
 }

@@ -36,7 +36,7 @@ FIELDS = {"jx": 0, "jy": 1, "rho": 2, "phi": 3, "ax": 4, "ay": 5, "bz": 6, "ex":
           "daydx": 15, "daydy": 16,
           "jz": 17, "az": 18, "bx": 19, "by": 20, "dazdx": 21, "dazdy": 22}
 KERNEL_TIMERS = {"sort": 0, "deposit": 1, "field_solve": 2, "gather_push": 3,
-                 "adj_push": 4, "adj_field": 5, "adj_deposit": 6}
+                 "adj_push": 4, "adj_field": 5, "adj_deposit": 6, "gather_deposit": 7}
 
 
 class PicError(RuntimeError):

@@ -5,6 +5,8 @@ fixed-point current deposit.
     float32), on random triples and on constructed ties;
   * the float32 shape weights against the textbook B-spline polynomials (FP64) within
     float32 rounding, summing to one;
+  * a contribution is the exact product t W rounded once to the quantum: against exact
+    rational arithmetic, on random float32 pairs and on constructed half-quantum ties;
   * the integer sums are exactly independent of the order of the particles;
   * the deposited current against the FP64 oracle deposit (oracle.pic.deposit) within the
     bound set by the quantum and the float32 roundings;
@@ -69,6 +71,35 @@ def test_float32_weights_match_the_polynomials(p):
     # the first node is the one of the FP64 oracle
     ref_i0, _ = opic.bspline.node_weights(xi.astype(np.float64), p)
     assert np.array_equal(i0, ref_i0)
+
+
+def _rne(q):
+    """Exact rational q rounded to the nearest integer, ties to even."""
+    f = q.numerator // q.denominator
+    r = q - f
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and f % 2 == 1):
+        f += 1
+    return f
+
+
+def test_contribution_is_the_exact_product_rounded_once():
+    rng = np.random.default_rng(5)
+    scale = 2.0 ** 38
+    t = (rng.standard_normal(2000) * 0.7).astype(np.float32)
+    w = rng.uniform(0.0, 0.7, 2000).astype(np.float32)
+    got = fx.contribution(t, w, scale)
+    for i in range(2000):
+        q = Fraction(float(t[i])) * Fraction(float(w[i])) * Fraction(2) ** 38
+        assert got[i] == _rne(q), i
+    # products that fall exactly on half a quantum go to the even integer, and rounding the
+    # product to float32 first would move this one by a quantum
+    half = np.float32(2.0 ** -39)
+    t2 = np.array([3 * half, 5 * half, -3 * half], dtype=np.float32)
+    w2 = np.ones(3, dtype=np.float32)
+    assert list(fx.contribution(t2, w2, scale)) == [2, 2, -2]
+    a, b = np.float32(1 + 2.0 ** -23), np.float32(1 - 2.0 ** -23)   # a b = 1 - 2^-46
+    assert fx.contribution(a, b, 2.0 ** 46) == 2 ** 46 - 1
+    assert np.rint(np.float64(np.float32(a * b)) * 2.0 ** 46) == 2 ** 46
 
 
 def _inputs(n, seed, lx=1.0, ly=0.75):
