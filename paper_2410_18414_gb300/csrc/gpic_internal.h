@@ -288,19 +288,21 @@ cudaError_t launch_tile_sort(const TileGeom& tg, SortArrays<T> src, SortArrays<T
 cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 
 // Binned move + deposit of the FP32 form over tile-sorted particles (x, y, v^n = vx, vy)
-// into the int64 current j: each CTA bins its particles by deposit cell in shared memory
-// and sums each cell's contributions in registers before its shared atomics.  fused: the
-// gather + push of the step before runs first on each particle (fields4 = that step's gather
-// fields, P and v^{n+1} -> px, py, vxo, vyo; the move and deposit then use v^{n+1}), as
-// launch_gather_push_tiled does it.  per_cta: particles per CTA at the mean density.
-// deposit_binned_fits: whether the tile's regions fit the pass's shared memory.
+// into the int64 current j (the moved positions go to xo, yo, which may be x, y): each CTA
+// bins its particles by stencil base in shared memory and sums each base's contributions
+// in registers before its shared atomics.  fused: the gather + push of the step before runs
+// first on each particle (fields4 = that step's gather fields, P and v^{n+1} -> px, py,
+// vxo, vyo; the move and deposit then use v^{n+1}), as launch_gather_push_tiled does it.
+// per_cta: particles per CTA at the mean density.  deposit_binned_fits: whether the tile's
+// regions fit the pass's shared memory.
 bool deposit_binned_fits(const TileGeom& tg, int p, bool fused);
 cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
-                                  const TileGeom& tg, float* x, float* y, float* px, float* py,
-                                  const float* vx, const float* vy, float* vxo, float* vyo,
-                                  int64_t n, const int* off, const void* fields4, void* j,
-                                  float scale, double* diag, unsigned int* err, cudaStream_t s,
-                                  bool fused, int per_cta);
+                                  const TileGeom& tg, const float* x, const float* y, float* xo,
+                                  float* yo, float* px, float* py, const float* vx,
+                                  const float* vy, float* vxo, float* vyo, int64_t n,
+                                  const int* off, const void* fields4, void* j, float scale,
+                                  double* diag, unsigned int* err, cudaStream_t s, bool fused,
+                                  int per_cta);
 
 // Gather + push of particles sorted by launch_tile_sort (FP32 form), fields staged per tile.
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,

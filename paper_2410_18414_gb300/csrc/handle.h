@@ -94,6 +94,13 @@ struct pic_handle {
     int64_t step = 0;
     int phase = 0;  // 0: ready to deposit, 1: deposited, 2: fields solved
     bool fused_deposit = false;  // phase 1 reached by the fused gather + deposit of pic_step
+    // The sorted FP32 form ends a pic_step call with the fused kernel too: the next step's
+    // moved positions wait in xnext, ynext and its current in Jalt (pending); the handle's
+    // state is unchanged otherwise.  The next deposit swaps them in; anything else that
+    // changes the state drops them (drop_pending).
+    void *xnext = nullptr, *ynext = nullptr;
+    bool pending = false;
+    bool no_defer = false;  // set while an ensemble captures the run's steps
     bool stepped = false;
     std::vector<void*> allocs;
     gpic::ModeCommon mc{};
@@ -122,6 +129,9 @@ cudaError_t forward_fft(pic_handle* h, const void* in, void* out);
 cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb);
 // Waits for the stream and maps the device error word to a status.
 pic_status check_device_error(pic_handle* h);
+// Forgets a pending deposit (see pic_handle::pending): the current buffer it filled is
+// cleared for the next deposit.
+cudaError_t drop_pending(pic_handle* h);
 
 // NVTX ranges of the library, in the domain "gpic" (host-side markers for timeline and
 // profiler tools: nsys, or ncu --nvtx --nvtx-include "gpic@deposit/"); a push without an

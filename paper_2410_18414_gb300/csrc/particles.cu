@@ -707,8 +707,9 @@ __device__ __forceinline__ int stencil_base(float xi) {
 
 template <int P, bool kFused>
 __global__ void __launch_bounds__(kThreads, kFused ? 3 : 4)
-k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, float* __restrict__ x,
-                 float* __restrict__ y, float* __restrict__ px, float* __restrict__ py,
+k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __restrict__ x,
+                 const float* __restrict__ y, float* __restrict__ xo, float* __restrict__ yo,
+                 float* __restrict__ px, float* __restrict__ py,
                  const float* __restrict__ vx, const float* __restrict__ vy,
                  float* __restrict__ vxo, float* __restrict__ vyo, const int* __restrict__ off,
                  int nsplit, const float2* __restrict__ F, AccFix acc,
@@ -814,8 +815,8 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, float* __restrict
             if (ok) {
                 xs = move_pos(xs, vxs, dt, lx);
                 ys = move_pos(ys, vys, dt, ly);
-                x[p] = xs;
-                y[p] = ys;
+                xo[p] = xs;
+                yo[p] = ys;
                 const float xi = rmul(xs, idx_), yj = rmul(ys, idy);
                 if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
                     bad |= ERR_NONFINITE;
@@ -1405,11 +1406,12 @@ bool deposit_binned_fits(const TileGeom& tg, int p, bool fused) {
 }
 
 cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
-                                  const TileGeom& tg, float* x, float* y, float* px, float* py,
-                                  const float* vx, const float* vy, float* vxo, float* vyo,
-                                  int64_t n, const int* off, const void* fields4, void* j,
-                                  float scale, double* diag, unsigned int* err, cudaStream_t s,
-                                  bool fused, int per_cta) {
+                                  const TileGeom& tg, const float* x, const float* y, float* xo,
+                                  float* yo, float* px, float* py, const float* vx,
+                                  const float* vy, float* vxo, float* vyo, int64_t n,
+                                  const int* off, const void* fields4, void* j, float scale,
+                                  double* diag, unsigned int* err, cudaStream_t s, bool fused,
+                                  int per_cta) {
     if (n == 0) return cudaSuccess;
     if (!deposit_binned_fits(tg, p, fused) || per_cta < 1) return cudaErrorInvalidValue;
     const int ntiles = tg.ntx * tg.nty;
@@ -1427,8 +1429,8 @@ cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams
         e = attr;                                                                              \
         if (e == cudaSuccess)                                                                  \
             e = launch_pdl(k_deposit_binned<PP, FF>, dim3(blocks), dim3(kThreads), smem, s,    \
-                           typed<float>(g), typed<float>(pp), tg, x, y, px, py, vx, vy, vxo,   \
-                           vyo, off, nsplit, (const float2*)fields4, acc, diag, err);          \
+                           typed<float>(g), typed<float>(pp), tg, x, y, xo, yo, px, py, vx,    \
+                           vy, vxo, vyo, off, nsplit, (const float2*)fields4, acc, diag, err); \
     }
     switch (p * 2 + (fused ? 1 : 0)) {
         case 4: GPIC_BINNED(2, false) break;

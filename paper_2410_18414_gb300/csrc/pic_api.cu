@@ -79,6 +79,12 @@ cudaError_t inverse_fft(pic_handle* h, void* buf, void* out, int nb) {
     });
 }
 
+cudaError_t drop_pending(pic_handle* h) {
+    if (!h->pending) return cudaSuccess;
+    h->pending = false;
+    return cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s);
+}
+
 pic_status check_device_error(pic_handle* h) {
     unsigned int e = 0;
     CK(cudaMemcpyAsync(&e, h->err, sizeof e, cudaMemcpyDeviceToHost, h->s));
@@ -249,6 +255,10 @@ pic_status alloc_state(pic_handle* h) {
     if (h->sorting) {
         const size_t ni = (size_t)std::max<int64_t>(h->n, 1) * sizeof(int);
         for (int a = 0; a < 8; ++a) CK(dalloc(h, &h->alt[a], pn));
+        if (h->fp32) {  // the moved positions of a pending deposit
+            CK(dalloc(h, &h->xnext, pn));
+            CK(dalloc(h, &h->ynext, pn));
+        }
         CK(dalloc(h, (void**)&h->id, ni));
         CK(dalloc(h, (void**)&h->id_alt, ni));
         CK(dalloc(h, (void**)&h->keys, ni));
@@ -472,19 +482,20 @@ bool diag_due(const pic_handle* h) {
 // Particles per CTA of the binned FP32 deposit (one batch of its shared-memory binning).
 constexpr int kBinPerCta = 2048;
 
-// Whether the gather + push of the step now finishing (step h->step + 1) may run fused with
-// the next step's move + deposit: the sorted FP32 form, the next step does not sort (its
-// keys need the pushed velocities before the move), and the tile regions fit the fused
-// kernel's shared memory.
+// Whether the gather + push of the step now finishing may run fused with the next step's
+// move + deposit: the sorted FP32 form (2D-2V, one species) when the tile regions fit the
+// fused kernel's shared memory.  A sort due at the next step then follows its deposit.
 bool fuse_next(const pic_handle* h) {
     if (!(h->sorting && h->fp32) || h->vdim != 2 || h->spp.n > 0) return false;
-    if ((h->step + 1) % h->cfg.sort_interval == 0) return false;
     return deposit_binned_fits(h->tg, h->p, true);
 }
 
-pic_status gather_push_step(pic_handle* h, bool fuse);
+pic_status gather_push_step(pic_handle* h, bool fuse, bool defer);
 
-pic_status sort_particles(pic_handle* h) {
+// The tile sort.  moved = false: keyed by the positions after this step's move (the sort
+// comes before the step's deposit); true: keyed by the current positions (the step's move
+// and deposit are done).  The current sums do not depend on the order of the particles.
+pic_status sort_particles(pic_handle* h, bool moved) {
     void** cur[8] = {&h->x, &h->y, &h->px, &h->py, &h->v[0][0], &h->v[0][1], &h->v[1][0], &h->v[1][1]};
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
@@ -496,8 +507,8 @@ pic_status sort_particles(pic_handle* h) {
         src.id = h->id;
         dst.id = h->id_alt;
         // cur[4 + 2 vcur] is v^n_x, the velocity of this step's move
-        return launch_tile_sort<T>(h->tg, src, dst, h->n, 4 + 2 * h->vcur, h->keys, h->hist,
-                                   h->off, h->cursor, h->bsum, h->s);
+        return launch_tile_sort<T>(h->tg, src, dst, h->n, moved ? -1 : 4 + 2 * h->vcur,
+                                   h->keys, h->hist, h->off, h->cursor, h->bsum, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
@@ -633,9 +644,22 @@ pic_status pic_deposit(pic_handle* h) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_deposit: the previous step is not finished");
     h->launches_now = 0;
-    if (h->sorting && h->step % h->cfg.sort_interval == 0) {
+    const bool sort_due = h->sorting && h->step % h->cfg.sort_interval == 0;
+    if (h->pending) {  // the last step of the previous pic_step call did this deposit
+        std::swap(h->x, h->xnext);
+        std::swap(h->y, h->ynext);
+        std::swap(h->J, h->Jalt);
+        h->pending = false;
+        h->phase = 1;
+        if (sort_due) {
+            TimedScope ts(h, PIC_KT_SORT);
+            return sort_particles(h, true);
+        }
+        return PIC_OK;
+    }
+    if (sort_due) {
         TimedScope ts(h, PIC_KT_SORT);
-        pic_status st = sort_particles(h);
+        pic_status st = sort_particles(h, false);
         if (st != PIC_OK) return st;
     }
     if (h->fp32) {
@@ -651,8 +675,9 @@ pic_status pic_deposit(pic_handle* h) {
         using T = decltype(t);
         if (h->sorting && h->fp32 && deposit_binned_fits(h->tg, h->p, false)) {
             const int vo = 1 - h->vcur;
-            return launch_deposit_binned(h->p, h->geom, h->push, h->tg, (float*)h->x,
-                                         (float*)h->y, (float*)h->px, (float*)h->py,
+            return launch_deposit_binned(h->p, h->geom, h->push, h->tg, (const float*)h->x,
+                                         (const float*)h->y, (float*)h->x, (float*)h->y,
+                                         (float*)h->px, (float*)h->py,
                                          (const float*)h->v[h->vcur][0],
                                          (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
                                          (float*)h->v[vo][1], h->n, h->off, nullptr, h->J,
@@ -819,18 +844,31 @@ pic_status pic_field_solve(pic_handle* h) {
     return PIC_OK;
 }
 
-pic_status pic_gather_push(pic_handle* h) { return gather_push_step(h, false); }
+pic_status pic_gather_push(pic_handle* h) { return gather_push_step(h, false, false); }
 
 pic_status pic_step(pic_handle* h, int32_t nsteps) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 0) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 0");
     for (int32_t i = 0; i < nsteps; ++i) {
         NvtxRange r("step");
-        // a step whose deposit ran fused with the previous gather starts deposited
-        pic_status st = h->phase == 1 && h->fused_deposit ? PIC_OK : pic_deposit(h);
+        pic_status st = PIC_OK;
+        if (h->phase == 1 && h->fused_deposit) {
+            // this step's deposit ran fused with the previous gather; a sort due now
+            // follows it
+            h->fused_deposit = false;
+            if (h->sorting && h->step % h->cfg.sort_interval == 0) {
+                TimedScope ts(h, PIC_KT_SORT);
+                st = sort_particles(h, true);
+            }
+        } else {
+            st = pic_deposit(h);
+        }
         if (st == PIC_OK) st = pic_field_solve(h);
-        // the last step of the call is not fused: the call returns between two steps
-        if (st == PIC_OK) st = gather_push_step(h, i + 1 < nsteps && fuse_next(h));
+        // the last step of the call leaves the next deposit pending (the call still
+        // returns between two steps), or, in an ensemble's capture, is not fused
+        const bool last = i + 1 == nsteps;
+        if (st == PIC_OK)
+            st = gather_push_step(h, fuse_next(h) && !(last && h->no_defer), last);
         if (st != PIC_OK) return st;
     }
     return PIC_OK;
@@ -842,8 +880,10 @@ namespace {
 
 // Gather + push of the step (a8, a9); with `fuse`, the sorted FP32 form's binned kernel
 // also moves the particles and deposits the next step's current (its a2, a3) into the
-// buffer the field solve just cleared, and the handle is left with that deposit done.
-pic_status gather_push_step(pic_handle* h, bool fuse) {
+// buffer the field solve just cleared, and the handle is left with that deposit done; with
+// `defer` as well, the moved positions go to xnext, ynext and the deposit stays pending
+// until the next step, so the handle's particle state is that of the end of this step.
+pic_status gather_push_step(pic_handle* h, bool fuse, bool defer) {
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (h->phase != 2) return fail(h, PIC_ERR_STATE, "pic_gather_push needs pic_field_solve first");
     PushParams pp = h->push;
@@ -851,8 +891,11 @@ pic_status gather_push_step(pic_handle* h, bool fuse) {
     const int vo = 1 - h->vcur;
     if (fuse) {
         TimedScope ts(h, PIC_KT_GATHER_DEPOSIT);
-        CK(launch_deposit_binned(h->p, h->geom, pp, h->tg, (float*)h->x, (float*)h->y,
-                                 (float*)h->px, (float*)h->py, (const float*)h->v[h->vcur][0],
+        void* xo = defer ? h->xnext : h->x;
+        void* yo = defer ? h->ynext : h->y;
+        CK(launch_deposit_binned(h->p, h->geom, pp, h->tg, (const float*)h->x,
+                                 (const float*)h->y, (float*)xo, (float*)yo, (float*)h->px,
+                                 (float*)h->py, (const float*)h->v[h->vcur][0],
                                  (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
                                  (float*)h->v[vo][1], h->n, h->off, h->G, h->Jalt,
                                  h->fix_scale_j, h->diag, h->err, h->s, true, kBinPerCta));
@@ -906,7 +949,9 @@ pic_status gather_push_step(pic_handle* h, bool fuse) {
     }
     h->phase = 0;
     h->fused_deposit = false;
-    if (fuse) {  // the next step's deposit is done: J^{n+2} sits in the buffer it reads
+    if (fuse && defer) {
+        h->pending = true;
+    } else if (fuse) {  // the next step's deposit is done: its current is in the buffer it reads
         std::swap(h->J, h->Jalt);
         h->launches_now = 0;
         h->phase = 1;
@@ -993,10 +1038,14 @@ pic_status pic_ensemble_create(pic_handle* const* runs, int32_t count, void* str
         if (ce == cudaSuccess) e->ev_run.push_back(v);
     }
     if (ce != cudaSuccess) return efail(e, PIC_ERR_CUDA, "event creation failed", ce);
-    // nothing of the runs may be pending outside the capture
-    for (pic_handle* h : e->runs)
+    // nothing of the runs may be pending outside the capture (a pending deposit is redone
+    // by the graph's first step)
+    for (pic_handle* h : e->runs) {
+        if ((ce = drop_pending(h)) != cudaSuccess)
+            return efail(e, PIC_ERR_CUDA, "clearing a pending deposit failed", ce);
         if ((ce = cudaStreamSynchronize(h->s)) != cudaSuccess)
             return efail(e, PIC_ERR_CUDA, "synchronising a run failed", ce);
+    }
     if ((ce = cudaStreamSynchronize(e->s)) != cudaSuccess)
         return efail(e, PIC_ERR_CUDA, "synchronising the ensemble stream failed", ce);
     // Capturing runs the step functions on the host: their buffer rotations advance by
@@ -1019,7 +1068,9 @@ pic_status pic_ensemble_create(pic_handle* const* runs, int32_t count, void* str
         pic_handle* h = e->runs[i];
         failed = i;
         cap = cudaStreamWaitEvent(h->s, e->ev, 0);  // the run's stream joins the capture
+        h->no_defer = true;  // the captured period ends between two steps
         if (cap == cudaSuccess) st = pic_step(h, e->period);
+        h->no_defer = false;
         if (cap == cudaSuccess && st == PIC_OK) cap = cudaEventRecord(e->ev_run[i], h->s);
         if (cap == cudaSuccess && st == PIC_OK) cap = cudaStreamWaitEvent(e->s, e->ev_run[i], 0);
     }
@@ -1056,6 +1107,8 @@ pic_status pic_ensemble_step(pic_ensemble* e, int32_t nsteps) {
     }
     if (nsteps == 0) return PIC_OK;
     cudaError_t ce = cudaSuccess;
+    // a run stepped alone since may hold a pending deposit: the graph redoes it
+    for (size_t i = 0; i < n && ce == cudaSuccess; ++i) ce = drop_pending(e->runs[i]);
     for (size_t i = 0; i < n && ce == cudaSuccess; ++i) {  // after the runs' pending work
         ce = cudaEventRecord(e->ev_run[i], e->runs[i]->s);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->s, e->ev_run[i], 0);

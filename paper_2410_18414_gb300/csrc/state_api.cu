@@ -213,6 +213,7 @@ pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
     h->diag_valid = h->e_valid = false;
     // the diagnostics log restarts: records of steps before the load are not returned
     h->ring_read = h->ring_written;
+    h->pending = false;  // a pending deposit of the old state is void
     if (h->fp32)  // the buffer the next deposit sums into starts at zero (the row
                   // transform keeps it so)
         CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));

@@ -202,11 +202,11 @@ def test_fp32_tile_sort_is_bitwise_identical_to_unsorted(device, make, sort, nst
 
 
 def test_kernel_timers_count_the_launches_they_bracket(device):
-    # sort every 4 steps: a sort before steps 1, 5, 9 of 10.  Inside one pic_step call the
-    # sorted FP32 form fuses the gather + push of step n with the deposit of step n + 1
-    # unless step n + 1 sorts or step n is the call's last: fused after steps 1-3, 5-7, 9;
-    # plain gathers after 4, 8, 10; separate deposits in steps 1, 5, 9.  Launches beyond
-    # the reserved pairs go untimed.
+    # sort every 4 steps: sorts in steps 1, 5, 9 of 10.  The sorted FP32 form runs the
+    # gather + push of every step fused with the move + deposit of the next (the last step
+    # of a pic_step call leaves that deposit pending for the next call), so only the first
+    # step of the handle deposits on its own, and a sort due later follows the fused
+    # deposit.  Launches beyond the reserved pairs go untimed.
     wl = workloads.weibel(32, 32, 8, 0.5, 0.01, 96, 3)
     cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
                           precision=pic.FP32_FIX64, sort_interval=4, stepper="bdf", bdf_order=2)
@@ -215,17 +215,27 @@ def test_kernel_timers_count_the_launches_they_bracket(device):
         sim.step(10)
         got = {k: sim.kernel_time(k) for k in pic.KERNEL_TIMERS}
         assert {k: v[1] for k, v in got.items()} == {
-            "sort": 3, "deposit": 3, "field_solve": 10, "gather_push": 3,
-            "adj_push": 0, "adj_field": 0, "adj_deposit": 0, "gather_deposit": 7}
+            "sort": 3, "deposit": 1, "field_solve": 10, "gather_push": 0,
+            "adj_push": 0, "adj_field": 0, "adj_deposit": 0, "gather_deposit": 10}
         assert all(v[0] > 0 for k, v in got.items() if v[1]), got
         sim.set_kernel_timing(2)  # restart with fewer pairs than launches
-        sim.step(6)               # steps 11-16: separate deposits in 11 and 13, fused 4
-        sim.step(4)               # 17-20: a separate deposit in 17, fused 3
-        assert sim.kernel_time("deposit")[1] == 2
+        sim.step(6)               # steps 11-16: a sort in 13, six fused kernels
+        sim.step(4)               # 17-20: a sort in 17
+        assert sim.kernel_time("sort")[1] == 2
         assert sim.kernel_time("gather_deposit")[1] == 2
+        assert sim.kernel_time("deposit")[1] == 0
+        # the phases one at a time run the kernels apart (the pending deposit is used first)
+        sim.deposit()
+        sim.field_solve()
+        sim.gather_push()
+        sim.deposit()
+        assert sim.kernel_time("deposit")[1] == 1
+        assert sim.kernel_time("gather_push")[1] == 1
+        sim.field_solve()
+        sim.gather_push()
         sim.set_kernel_timing(0)
         sim.step(1)
-        assert sim.kernel_time("deposit")[1] == 2
+        assert sim.kernel_time("deposit")[1] == 1
         with pytest.raises(pic.PicError):
             sim.set_kernel_timing(-1)
         with pytest.raises(KeyError):
@@ -299,3 +309,54 @@ def test_diagnostics_history_records_every_diagnosed_step(device, precision):
         assert [h["step"] for h in wrapped] == list(range(sim.step_count - pic.DIAG_HISTORY + 1,
                                                           sim.step_count + 1))
         assert wrapped[-1] == sim.residuals()
+
+
+def test_pending_deposit_leaves_the_state_of_each_step(device):
+    # The sorted FP32 form ends each pic_step call with the next step's move and deposit
+    # done ahead (pending).  Read between calls, the particles and fields are still those
+    # of the step just finished -- bitwise those of the unsorted form, which has no pending
+    # deposit -- and one call of n steps, n calls of one step, the phases one at a time and
+    # a saved and reloaded state all step on to the same bits.
+    wl = workloads.weibel(48, 32, 8, 0.5, 0.01, 98, 3)
+    kw = dict(stepper="bdf", bdf_order=2)
+
+    def make(sort):
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                              precision=pic.FP32_FIX64, sort_interval=sort, **kw)
+        return pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device)
+
+    def snap(sim):
+        out = dict(sim.particles())
+        out.update({f: sim.field(f) for f in ("jx", "jy", "phi", "daxdy")})
+        return out
+
+    plain, one, many, phases = make(0), make(3), make(3), make(3)
+    for k in range(7):
+        plain.step(1)
+        one.step(1)
+        ref = snap(plain)
+        got = snap(one)
+        for name in ref:
+            assert np.array_equal(got[name], ref[name]), (k, name)
+    many.step(7)
+    for _ in range(7):
+        phases.deposit()
+        phases.field_solve()
+        phases.gather_push()
+    for sim in (many, phases):
+        got = snap(sim)
+        for name in ref:
+            assert np.array_equal(got[name], ref[name]), name
+    state = one.save_state()        # saved with a deposit pending
+    other = make(3)
+    other.load_state(state)
+    one.step(4)
+    other.step(4)
+    plain.step(4)
+    ref = snap(plain)
+    for sim in (one, other):
+        got = snap(sim)
+        for name in ref:
+            assert np.array_equal(got[name], ref[name]), name
+    for sim in (plain, one, many, phases, other):
+        sim.close()
