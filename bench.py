@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-extra-steppers", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint timing that the default line carries")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the ensemble timing that the default line carries")
     a = ap.parse_args()
     if a.stepper is None:
         a.stepper = WORKLOADS[a.workload]["stepper"] if a.workload in WORKLOADS else "bdf2"
@@ -178,24 +180,48 @@ def bytes_move_deposit(rsz):
     return 6 * rsz      # read x, y, v^n (4); write x, y (2)
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
-# captures (profiles/), keyed by (kernel, form); None when the kernel changed since.
+def bytes_gather_deposit(rsz):
+    # the fused kernel: read x, y, Px, Py, v^n, v^{n-1} (8); write Px, Py, v^{n+1}, x, y (6)
+    return 14 * rsz
+
+
+def flops_gather_deposit(p):
+    return flops_gather_push(p) + flops_move_deposit(p)
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on a workload, from a
+# committed ncu capture (profiles/), with the SHA-1 of the kernel's source file at capture
+# time: when the source has changed since, the bench line reports no traffic.
 TRAFFIC = {
-    # ncu --set full, 2 launches of k_move_deposit_tiled<float,3> on the 128x128 Weibel
-    # workload: dram__bytes_read 18.28 MB + dram__bytes_write 1.15 MB (mean; most of the
-    # x, y writes are still in L2 when the kernel ends)
-    ("move_deposit", "fp32"): 19.43e6,
+    # (kernel, workload): (bytes per launch, source file, its SHA-1 prefix, profile)
+    ("gather_deposit", "weibel128"): (34.43e6 + 40.19e6, "particles.cu", "e09646c7ac95",
+                                      "profiles/gather_deposit_fused_weibel128.md"),
 }
 
-# Conflict-free 32-bit shared-memory atomicAdd throughput of the whole GPU, in warp
-# instructions per ns (1.873 per SM per ns measured on GB300, x 152 SMs).
-SMEM_ATOMIC_RATE = 1.873 * 152
+
+def source_sha1(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2410_18414_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def traffic_of(kernel, workload):
+    entry = TRAFFIC.get((kernel, workload))
+    if entry is None:
+        return None, "no ncu capture of this kernel on this workload is committed"
+    nbytes, src, sha, profile = entry
+    if source_sha1(src) != sha:
+        return None, f"{src} changed since the capture in {profile}"
+    return nbytes, f"ncu capture: {profile}"
+
+
+_FP64 = {}
 
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    out = {"hbm_gbs": 6800.0, "hbm_src": "fallback", "fp64_gflops": 1250.0,
-           "fp64_src": "nominal GB300 FP64 (profiling recipe table)"}
+    out = {"hbm_gbs": 6800.0, "hbm_src": "fallback"}
     try:
         with open(path) as f:
             m = json.load(f)
@@ -203,7 +229,23 @@ def peaks():
         out["hbm_src"] = "measured"
     except Exception:
         pass
+    if "gflops" not in _FP64:   # the FP64 FMA rate, measured once on this device
+        try:
+            from paper_2410_18414_gb300 import pic
+            _FP64["gflops"] = pic.measure_fp64_fma()
+            _FP64["src"] = "measured: pic_measure_fp64_fma (FP64 FMA chains on every SM)"
+        except Exception as exc:
+            _FP64["gflops"] = 1250.0
+            _FP64["src"] = f"nominal 1.25 TFLOP/s (measurement failed: {exc})"[:200]
+    out["fp64_gflops"] = _FP64["gflops"]
+    out["fp64_src"] = _FP64["src"]
     return out
+
+
+def fp32_peak_gflops(sm_mhz):
+    """FP32 FMA peak from the unit counts and the measured clock: 152 SMs x 128 FP32 lanes
+    x 2 flops per FMA per cycle."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e9
 
 
 # ------------------------------------------------------------------ clocks --
@@ -318,9 +360,10 @@ def workload_params(workload):
                 seed=sp["seed"], stepper="bdf2")
 
 
-def run_oracle(workload, stepper_name, n, steps, warmup, budget_s=0.0):
+def run_oracle(workload, stepper_name, n, steps, warmup, budget_s=0.0, threads=1):
     """Per-step times of the oracle on the first n particles of the workload (weight
-    rescaled), after `warmup` untimed steps.  budget_s > 0: n is lowered, from a two-size
+    rescaled), after `warmup` untimed steps, with `threads` BLAS threads (the oracle's
+    transforms are dense matrix products).  budget_s > 0: n is lowered, from a two-size
     probe of the step cost, so that all the steps take about budget_s.  Returns (times, n)."""
     stepper, k = STEPPER_NAMES[stepper_name]
     dirk = dirk_tableau(stepper_name) if stepper == "dirk" else None
@@ -329,7 +372,8 @@ def run_oracle(workload, stepper_name, n, steps, warmup, budget_s=0.0):
                                  warmup=warmup, steps=steps, nx=w["n"], ppc=w["ppc"],
                                  v_drift=w["v_drift"], u_th=w["u_th"], p=w["p"],
                                  budget_s=float(budget_s))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+    nt = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt,
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
@@ -341,15 +385,18 @@ def run_oracle(workload, stepper_name, n, steps, warmup, budget_s=0.0):
     return out["times"], out["n"]
 
 
-def cpu_baseline(workload, stepper_name):
+def cpu_baseline(workload, stepper_name, threads=1):
+    """The oracle as it stands on a sample of the workload: one host thread, or `threads`
+    BLAS threads (the host's cores)."""
     n = 262144
     steps = 12
-    times, _ = run_oracle(workload, stepper_name, n, steps, 1)
+    times, _ = run_oracle(workload, stepper_name, n, steps, 1, threads=threads)
     v = n * len(times) / sum(times)
     w = WORKLOADS[workload]
     total = w["n"] * w["n"] * w["ppc"]
-    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 oracle, single thread, {w['n']}x{w['n']} grid with the first "
+    how = "single thread" if threads == 1 else f"{threads} BLAS threads (all host cores)"
+    return {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"numpy FP64 oracle, {how}, {w['n']}x{w['n']} grid with the first "
                       f"{n} of the {total:,} particles (weight rescaled), {steps} timed steps "
                       f"after 1 warm-up, {sum(times):.1f} s"}
 
@@ -445,11 +492,15 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm --
 
+KERNEL_GROUPS = ("sort", "deposit", "field_solve", "gather_push", "gather_deposit")
+
+
 def time_steps(sim, steps, warmup, stream, flush, count=None, detail=False):
-    """Per-step device times (CUDA events on the simulation's stream), L2 flushed between
-    steps outside the events.  detail=False brackets each whole step with one event pair
-    (the headline); detail=True also records the phase boundaries and the library's
-    per-kernel event pairs, which add about a dozen event records to every step."""
+    """Per-step device times (CUDA events on the simulation's stream), one pic_step call
+    per step, L2 flushed between steps outside the events.  detail=True also runs the
+    library's per-kernel event pairs (pic_set_kernel_timing) around each launch group:
+    the sort, the separate deposit, the field solve, the separate gather + push and the
+    fused gather + push + next deposit of the sorted FP32 form."""
     import torch
     for _ in range(warmup):
         sim.step(1)
@@ -457,46 +508,46 @@ def time_steps(sim, steps, warmup, stream, flush, count=None, detail=False):
     torch.cuda.synchronize()
     if detail:
         sim.set_kernel_timing(steps + 1)   # the library's per-kernel event pairs, made up front
-    nev = 4 if detail else 2
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
     for k in range(steps):
         e = ev[k]
         e[0].record(stream)
-        if detail:
-            sim.deposit()
-            e[1].record(stream)
-            sim.field_solve()
-            e[2].record(stream)
-            sim.gather_push()
-        else:
-            sim.step(1)
-        e[-1].record(stream)
+        sim.step(1)
+        e[1].record(stream)
         if count is not None:
             count[0] += sim.kernels_per_step
         flush.zero_()       # cold L2 for the next step (outside the events)
     torch.cuda.synchronize()
-    out = {"step_ms": [e[0].elapsed_time(e[-1]) for e in ev]}
+    out = {"step_ms": [e[0].elapsed_time(e[1]) for e in ev]}
     if detail:
         kt = {}
-        for name in ("sort", "deposit", "field_solve", "gather_push"):
+        for name in KERNEL_GROUPS:
             ms, nl = sim.kernel_time(name)
             kt[name] = {"launches": nl, "ms_per_launch": ms / nl if nl else None, "ms_total": ms}
         sim.set_kernel_timing(0)
-        out.update(deposit_ms=[e[0].elapsed_time(e[1]) for e in ev],
-                   field_ms=[e[1].elapsed_time(e[2]) for e in ev],
-                   push_ms=[e[2].elapsed_time(e[3]) for e in ev], kernels=kt)
+        out["kernels"] = kt
     return out
 
 
 def run_ensemble(a):
+    """The ensemble workload on its own (--workload ensemble256): one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
+    line = ensemble_line(ranks, a.steps, a.warmup)
+    ranks.close()
+    if line is not None:
+        print(json.dumps(line))
+
+
+def ensemble_line(ranks, steps, warmup):
     """256 independent Weibel runs (grid sizes, densities and drifts drawn per run; FP32
     form, BDF-2, cubic), sort intervals from the autotuner, advanced together by one
     CUDA-graph launch per period (pic_ensemble_step); the same runs stepped on their own
-    streams without the graph are timed beside it."""
+    streams without the graph are timed beside it.  Returns rank 0's line (None on the
+    other ranks)."""
     import torch
     from paper_2410_18414_gb300 import autotune, pic, workloads
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    ranks = Ranks()
     rank, world = ranks.rank, ranks.world
     pic.load_library()
     specs = workloads.ensemble_specs(seed0=1000 + 256 * rank)
@@ -529,9 +580,8 @@ def run_ensemble(a):
     ens = pic.Ensemble(sims, master.cuda_stream)
     capture_s = time.perf_counter() - t0
     P = ens.period
-    steps = a.steps
     full, rest = (steps // P) * P, steps % P
-    warm = max(1, -(-a.warmup // P)) * P       # whole periods keep the runs in phase
+    warm = max(1, -(-warmup // P)) * P         # whole periods keep the runs in phase
     ens.step(warm)
     ranks.barrier()
     clocks = ClockSampler(ranks.local)
@@ -570,9 +620,8 @@ def run_ensemble(a):
     ms_plain = ranks.max(f0.elapsed_time(f1))
     for s in sims:
         s.close()
-    ranks.close()
     if rank != 0:
-        return
+        return None
     value = whole_job_rate(n_total, world, steps, ms)
     hist = {}
     for si in sorts:
@@ -589,11 +638,12 @@ def run_ensemble(a):
                    "l2": "no flush: the ensemble's particle state (about 7 GB) is far larger "
                          "than L2", "parallelism": "single"},
         "roofline": {"kernel": "whole step, all runs", "bound": "hbm",
-                     "achieved": 72.0 * n_total * steps / (ms * 1e-3) / 1e9,
+                     "achieved": 56.0 * n_total * steps / (ms * 1e-3) / 1e9,
                      "peak": peaks()["hbm_gbs"], "unit": "GB/s",
-                     "frac": 72.0 * n_total * steps / (ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
+                     "frac": 56.0 * n_total * steps / (ms * 1e-3) / 1e9 / peaks()["hbm_gbs"],
                      "traffic": None, "peak_source": peaks()["hbm_src"],
-                     "note": "72 B algorithmic per particle-step (deposit 24 + gather 48)"},
+                     "note": "56 B algorithmic per particle-step (the fused gather + push + "
+                             "move + deposit: 8 values read, 6 written)"},
         "no_graph": {"ms_per_step": ms_plain / steps,
                      "value": whole_job_rate(n_total, world, steps, ms_plain),
                      "how": "each run's steps enqueued on its own stream, no graph"},
@@ -601,7 +651,7 @@ def run_ensemble(a):
         "cpu_baseline": None, "e2e": None,
         "gpu_launches": None, "clocks": clk,
     }
-    print(json.dumps(line))
+    return line
 
 
 def adjoint_timings(steps, reps, rank=0, stepper="bdf2"):
@@ -750,18 +800,17 @@ def flops_adj_push(p):
 
 
 def adjoint_roofline(p, n, ms):
-    """k_adj_push_gather against the FP64 pipe (nominal 1.25 TFLOP/s; the kernel's DRAM
-    traffic, 50.0 MB per launch by ncu at this size, is about 3% of the HBM roof)."""
+    """k_adj_push_gather against the FP64 pipe (its FMA rate measured on this device)."""
     if not ms:
         return None
     pk = peaks()
     achieved = flops_adj_push(p) * n / (ms * 1e-3) / 1e12
+    traffic, traffic_src = traffic_of("adj_push_gather", "adjoint128")
     return {"kernel": "k_adj_push_gather", "bound": "alu", "achieved": achieved,
             "peak": pk["fp64_gflops"] / 1e3, "unit": "TFLOP/s",
-            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": 50.0e6,
-            "peak_source": pk["fp64_src"],
-            "note": f"{flops_adj_push(p)} FP64 flops per particle (cubic: 600); traffic = "
-                    "dram read + write of one launch from ncu on this workload"}
+            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": traffic,
+            "traffic_source": traffic_src, "peak_source": pk["fp64_src"],
+            "note": f"{flops_adj_push(p)} FP64 flops per particle (cubic: 600)"}
 
 
 def main():
@@ -803,8 +852,8 @@ def main():
     total_ms = ranks.max(sum(t["step_ms"]))
     n_all = wl.n * world
     value = whole_job_rate(wl.n, world, a.steps, total_ms)
-    # phase and per-kernel breakdown: an instrumented run of the same simulation right
-    # after the timed region (its extra event records would slow the headline steps)
+    # per-kernel breakdown: an instrumented run of the same simulation right after the
+    # timed region (its extra event records would slow the headline steps)
     nd = min(a.steps, 500)
     t = time_steps(sim, nd, 3, stream, flush, detail=True)
 
@@ -814,47 +863,68 @@ def main():
     fp32 = a.precision == "fp32"
     rsz = 4 if fp32 else 8
     p = wl.p
-    dep_ms = statistics.mean(t["deposit_ms"])
-    psh_ms = statistics.mean(t["push_ms"])
-    fld_ms = statistics.mean(t["field_ms"])
     kt = t["kernels"]
-    kern = {
-        "gather_push": {"ms": kt["gather_push"]["ms_per_launch"],
-                        "flops": flops_gather_push(p) * wl.n,
-                        "bytes": bytes_gather_push(rsz) * wl.n},
-        "move_deposit": {"ms": kt["deposit"]["ms_per_launch"],
-                         "flops": flops_move_deposit(p) * wl.n,
-                         "bytes": bytes_move_deposit(rsz) * wl.n},
+    counts = {
+        "gather_deposit": (flops_gather_deposit(p), bytes_gather_deposit(rsz)),
+        "gather_push": (flops_gather_push(p), bytes_gather_push(rsz)),
+        "deposit": (flops_move_deposit(p), bytes_move_deposit(rsz)),
     }
-    for k in kern.values():
+    kern = {}
+    for name, (fl, by) in counts.items():
+        if not kt[name]["launches"]:
+            continue
+        k = {"ms": kt[name]["ms_per_launch"], "launches": kt[name]["launches"],
+             "flops": fl * wl.n, "bytes": by * wl.n}
         k["gflops"] = k["flops"] / (k["ms"] * 1e-3) / 1e9
         k["gbs"] = k["bytes"] / (k["ms"] * 1e-3) / 1e9
         k["frac_hbm"] = k["gbs"] / pk["hbm_gbs"]
         if not fp32:
             k["frac_fp64_alu"] = k["gflops"] / pk["fp64_gflops"]
-    dom_name = max(kern, key=lambda k: kern[k]["ms"])
+        kern[name] = k
+    # the dominant particle kernel: the one with the most time per step
+    dom_name = max(kern, key=lambda k: kern[k]["ms"] * kern[k]["launches"])
     dom = kern[dom_name]
+    traffic, traffic_src = traffic_of(dom_name, a.workload)
     if fp32:
+        sm_mhz = clk.get("sm_mhz") or 2070.0
         roofline = {"kernel": dom_name, "bound": "hbm", "achieved": dom["gbs"],
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dom["gbs"] / pk["hbm_gbs"],
-                    "traffic": TRAFFIC.get((dom_name, a.precision)), "peak_source": pk["hbm_src"]}
-        if dom_name == "move_deposit":
-            # what actually bounds it: 32-bit shared-memory atomics, (p+1)^2 nodes x 2
-            # components x 2 halves per particle, at the measured conflict-free rate
-            atoms = 4 * (p + 1) ** 2 * wl.n / 32
-            floor_ms = atoms / (SMEM_ATOMIC_RATE * 1e6)
-            roofline["smem_atomics"] = {
-                "warp_atomics_per_launch": atoms, "peak_warp_atomics_per_ns": SMEM_ATOMIC_RATE,
-                "floor_ms": floor_ms, "frac": floor_ms / dom["ms"],
-                "peak_source": "measured: conflict-free 32-bit shared atomicAdd, 152 SMs"}
+                    "traffic": traffic, "traffic_source": traffic_src,
+                    "peak_source": pk["hbm_src"],
+                    "bytes_per_particle": dom["bytes"] / wl.n,
+                    "fp32_alu": {"achieved_gflops": dom["gflops"],
+                                 "peak_gflops": fp32_peak_gflops(sm_mhz),
+                                 "frac": dom["gflops"] / fp32_peak_gflops(sm_mhz),
+                                 "flops_per_particle": dom["flops"] / wl.n,
+                                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 at the measured "
+                                                f"{sm_mhz:.0f} MHz"}}
     else:
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
                     "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
                     "frac": dom["gflops"] / pk["fp64_gflops"],
-                    "traffic": TRAFFIC.get((dom_name, a.precision)),
+                    "traffic": traffic, "traffic_source": traffic_src,
                     "peak_source": pk["fp64_src"],
                     "hbm": {"achieved_gbs": dom["gbs"], "peak_gbs": pk["hbm_gbs"],
                             "frac": dom["gbs"] / pk["hbm_gbs"], "peak_source": pk["hbm_src"]}}
+
+    # the configuration's whole run: every step in one pic_step call (the call's steps
+    # run back to back, so no L2 flush separates them)
+    sf = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
+    sf.step(3)
+    flush.zero_()
+    ranks.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    sf.step(a.steps)
+    f1.record(stream)
+    f1.synchronize()
+    full_ms = ranks.max(f0.elapsed_time(f1))
+    sf.sync()
+    sf.close()
+    full_run = {"steps": a.steps, "ms": full_ms, "ms_per_step": full_ms / a.steps,
+                "value": whole_job_rate(wl.n, world, a.steps, full_ms),
+                "how": "one pic_step call of all the steps after 3 warm-up steps; "
+                       "L2 not flushed between steps"}
 
     # the other precision form on the same workload (the metric's comparison)
     other = "fp64" if fp32 else "fp32"
@@ -869,10 +939,8 @@ def main():
     other_ms = statistics.mean(to["step_ms"])
     other_form = {"form": other, "ms_per_step": other_ms, "sort_interval": other_sort,
                   "value": wl.n * world / (other_ms * 1e-3),
-                  "phase_ms": {"deposit": statistics.mean(tod["deposit_ms"]),
-                               "field_solve": statistics.mean(tod["field_ms"]),
-                               "gather_push": statistics.mean(tod["push_ms"])},
-                  "kernel_ms": {k: v["ms_per_launch"] for k, v in tod["kernels"].items()}}
+                  "kernel_ms": {k: v["ms_per_launch"] for k, v in tod["kernels"].items()
+                                if v["launches"]}}
 
     # the same form with the residual and energy diagnostics (a10) on every step
     sd = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
@@ -926,13 +994,27 @@ def main():
     if not a.no_adjoint:
         adjoint = adjoint_timings(200, 1, rank)
 
-    cpu = None
+    # the batched ensemble (256 independent runs, one graph launch per period)
+    ensemble = None
+    if not a.no_ensemble:
+        eline = ensemble_line(ranks, 300, 20)
+        if eline is not None:
+            ensemble = {k: eline[k] for k in ("value", "unit", "ms_per_step", "steps", "config",
+                                              "roofline", "no_graph", "autotune_s",
+                                              "capture_s", "clocks")}
+
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        try:
-            cpu = cpu_baseline(a.workload, a.stepper)
-        except Exception as exc:  # the line still prints; the failure is stated
-            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
-                   "sample": f"failed: {exc}"[:300]}
+        for threads in (1, os.cpu_count() or 1):
+            try:
+                res = cpu_baseline(a.workload, a.stepper, threads)
+            except Exception as exc:  # the line still prints; the failure is stated
+                res = {"value": None, "unit": METRIC, "cores": threads, "kind": "oracle",
+                       "sample": f"failed: {exc}"[:300]}
+            if threads == 1:
+                cpu = res
+            else:
+                cpu_all = res
 
     if rank == 0:
         line = {
@@ -948,15 +1030,18 @@ def main():
             "roofline": roofline,
             "kernels": {k: {kk: round(vv, 6) if isinstance(vv, float) else vv
                             for kk, vv in v.items()} for k, v in kern.items()},
-            "phase_ms": {"deposit": dep_ms, "field_solve": fld_ms, "gather_push": psh_ms},
             "kernel_ms": {k: v["ms_per_launch"] for k, v in kt.items()},
             "kernel_launches": {k: v["launches"] for k, v in kt.items()},
+            "detail_steps": nd,
+            "full_run": full_run,
             "by_stepper_ms_per_step": by_stepper,
             "other_form": other_form,
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
             "with_diagnostics": with_diagnostics,
             "adjoint": adjoint,
+            "ensemble": ensemble,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
             "gpu_launches": launches[0],
             "clocks": clk,

@@ -334,6 +334,14 @@ pic_status pic_set_kernel_timing(pic_handle *h, int32_t max_launches);
  * PIC_ERR_INVALID_ARG for an unknown timer or NULL outputs. */
 pic_status pic_kernel_time(pic_handle *h, int32_t which, double *total_ms, int64_t *launches);
 
+/* Measurement aid (the paper has no counterpart): the FP64 fused multiply-add rate of the
+ * current device in GFLOP/s (an FMA counts two flops), timed with CUDA events on `stream`
+ * over a kernel of independent FMA chains filling every SM (best of three runs after a
+ * warm-up).  The FP64 path's particle kernels are bound by that rate.  Allocates and frees
+ * 8 bytes of device memory; synchronizes the stream.  PIC_ERR_INVALID_ARG for a NULL
+ * output, PIC_ERR_CUDA on a runtime failure. */
+pic_status pic_measure_fp64_fma(void *stream, double *gflops);
+
 /* One-line description of the last failure on this handle (or of the last failed
  * pic_init when h is NULL).  Valid until the next call on the handle. */
 const char *pic_last_error(const pic_handle *h);

@@ -498,9 +498,9 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
 // CTA (tile, split) takes a contiguous share [p0, p1) of one tile's particles and works
 // through it in batches of at most kBinBatch:
 //   A  consecutive lanes take consecutive particles (the SoA loads and stores coalesce;
-//      each thread's next particle is loaded while it works on the current one).  Fused:
-//      gather the eight fields of the step at x^{n+1} from the tile's field region staged
-//      in shared memory, IAEM push (section 4.1) -> P^{n+1}, v^{n+1}.  Then the move
+//      unfused, each thread's next particle is loaded while it works on the current one).
+//      Fused: gather the eight fields of the step at x^{n+1} from the tile's field region
+//      staged in shared memory, IAEM push (section 4.1) -> P^{n+1}, v^{n+1}.  Then the move
 //      x^{n+2} = x^{n+1} + v^{n+1} dt (the next step's first operation, Algorithm 1).  The
 //      moved particle (x, y, vx, vy) goes to a staging slot, keyed by the region node of its
 //      stencil base; a shared atomic on that key's count gives its rank there.
@@ -706,7 +706,7 @@ __device__ __forceinline__ int stencil_base(float xi) {
 }
 
 template <int P, bool kFused>
-__global__ void __launch_bounds__(kThreads, kFused ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, 4)
 k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __restrict__ x,
                  const float* __restrict__ y, float* __restrict__ xo, float* __restrict__ yo,
                  float* __restrict__ px, float* __restrict__ py,
@@ -770,7 +770,9 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
     unsigned bad = 0;
     for (int64_t b0 = p0; b0 < p1; b0 += kBinBatch) {
         const int nb = (int)min((int64_t)kBinBatch, p1 - b0);
-        // A: (gather + push,) move, stage and count; the next particle's loads are in flight
+        // A: (gather + push,) move, stage and count; without the gather, the next particle's
+        // loads are in flight meanwhile (the fused kernel keeps its registers for the gather)
+        constexpr bool kAhead = !kFused;
         float cur[NF], nxt[NF];
         auto load = [&](float* r, int i) {
             if (i < nb) {
@@ -787,10 +789,14 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                 }
             }
         };
-        load(cur, threadIdx.x);
+        if (kAhead) load(cur, threadIdx.x);
 #pragma unroll 1
         for (int i = threadIdx.x; i < nb; i += kThreads) {
-            load(nxt, i + kThreads);
+            if (kAhead) {
+                load(nxt, i + kThreads);
+            } else {
+                load(cur, i);
+            }
             const int64_t p = b0 + i;
             float xs = cur[0], ys = cur[1], vxs = cur[2], vys = cur[3];
             int key = -1;
@@ -850,8 +856,10 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
             } else {
                 kr[i] = -1;
             }
+            if (kAhead) {
 #pragma unroll
-            for (int q = 0; q < NF; ++q) cur[q] = nxt[q];
+                for (int q = 0; q < NF; ++q) cur[q] = nxt[q];
+            }
         }
         __syncthreads();
         // B: exclusive scan of the counts over the region's nodes

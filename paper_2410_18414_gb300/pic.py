@@ -129,6 +129,7 @@ def load_library(path=None):
         "pic_adjoint_backward": ([vp] + [vp] * 7, i32),
         "pic_adjoint_checkpoint_every": ([vp], i32),
         "pic_adjoint_destroy": ([vp], None),
+        "pic_measure_fp64_fma": ([vp, dp], i32),
         "pic_last_error": ([vp], ctypes.c_char_p),
         "pic_destroy": ([vp], None),
     }
@@ -188,6 +189,16 @@ def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, 
             cfg.dirk_b[i] = dirk["b"][i]
             cfg.dirk_c[i] = dirk["c"][i]
     return cfg
+
+
+def measure_fp64_fma(stream=None):
+    """The current device's FP64 FMA rate in GFLOP/s (pic_measure_fp64_fma)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    st = lib.pic_measure_fp64_fma(ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if st != PIC_OK:
+        raise PicError(st, "pic_measure_fp64_fma failed")
+    return out.value
 
 
 class Simulation:
