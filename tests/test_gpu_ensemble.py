@@ -151,3 +151,37 @@ def test_autotuner_picks_a_candidate_and_caches(torch_mod):
     assert autotune.density_class(20) == 16 and autotune.density_class(50) == 64
     assert autotune._cache[(32, 16, 3, pic.FP32_FIX64)] == s
     assert autotune.tune_sort_interval(32, 18) == s  # same key: from the cache
+
+
+def test_ensemble_matches_the_oracle(torch_mod):
+    # An FP64 run and an FP32-form run (sorted, with a fused kernel in every step) stepped
+    # together by the graph against the CPU oracle: FP64 to 1e-12, the FP32 form within
+    # the bounds of its stated error (3e-5 on fields, 2e-6 on particles after 10 steps).
+    from oracle import pic as opic
+    torch = torch_mod
+    specs = [
+        (lambda: workloads.weibel(24, 16, 8, 0.5, 0.01, 1011, 3, n=3001), pic.FP64, 0,
+         dict(stepper="bdf", bdf_order=2), dict(stepper="bdf", bdf_order=2), 1e-12, 1e-12),
+        (lambda: workloads.weibel(32, 24, 8, 0.5, 0.01, 1012, 2, n=6007), pic.FP32_FIX64, 2,
+         dict(stepper="cdf2"), dict(stepper="cdf2"), 3e-5, 2e-6),
+    ]
+    runs = [make(torch, (m, prec, sort, kw)) for m, prec, sort, kw, _, _, _ in specs]
+    master = torch.cuda.Stream()
+    with pic.Ensemble([r for r, _ in runs], master.cuda_stream) as ens:
+        P = ens.period
+        nsteps = P * max(1, -(-10 // P))
+        ens.step(nsteps)
+    for (r, _), (mk, prec, sort, kw, okw, ftol, ptol) in zip(runs, specs):
+        wl = mk()
+        ocfg = opic.Config(nx=wl.nx, ny=wl.ny, lx=wl.lx, ly=wl.ly, dt=wl.dt, p=wl.p,
+                           w=wl.weight, **okw)
+        st = opic.run(ocfg, wl.x, wl.y, wl.vx, wl.vy, nsteps)
+        got = r.particles()
+        for k in ("px", "py", "vx", "vy", "vx_old", "vy_old"):
+            assert rel(got[k], getattr(st, k)) < ptol, (k, rel(got[k], getattr(st, k)))
+        for k, L in (("x", wl.lx), ("y", wl.ly)):
+            d = np.mod(got[k] - getattr(st, k) + 0.5 * L, L) - 0.5 * L
+            assert np.linalg.norm(d) / np.linalg.norm(getattr(st, k)) < ptol, k
+        for f in ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "daydx"):
+            assert rel(r.field(f), st.grids[f]) < ftol, (f, rel(r.field(f), st.grids[f]))
+        r.close()
