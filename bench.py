@@ -43,7 +43,10 @@ def parse():
                     default="weibel128",
                     help="weibel128: the headline configuration; weibel512: the large one; "
                          "ensemble256: 256 independent runs in one graph launch per period; "
-                         "adjoint128: gradient of the final magnetic energy (FP64 adjoint)")
+                         "adjoint128: gradient of the final magnetic energy (the adjoint "
+                         "of --adjoint-form)")
+    ap.add_argument("--adjoint-form", choices=["fp64", "fp32"], default="fp64",
+                    help="adjoint128: the FP64 run or the (unsorted) FP32 form")
     ap.add_argument("--repeats", type=int, default=3,
                     help="adjoint128: timed gradient evaluations per checkpoint interval")
     ap.add_argument("--stepper", choices=list(STEPPER_NAMES), default=None,
@@ -654,10 +657,12 @@ def ensemble_line(ranks, steps, warmup):
     return line
 
 
-def adjoint_timings(steps, reps, rank=0, stepper="bdf2"):
+def adjoint_timings(steps, reps, rank=0, stepper="bdf2", form="fp64"):
     """Gradient of the magnetic energy W_B = 1/2 sum B_z^2 dx dy after `steps` (at most 200)
-    steps of the 128x128 Weibel run with 16 particles per cell (262,144), FP64, cubic,
-    under `stepper` (a STEPPER_NAMES key; BDF-2 by default), with respect to every initial velocity and momentum, by the library's adjoint.
+    steps of the 128x128 Weibel run with 16 particles per cell (262,144), cubic, under
+    `stepper` (a STEPPER_NAMES key; BDF-2 by default), with respect to every initial
+    velocity and momentum, by the library's adjoint of the FP64 run or (form "fp32") of the
+    unsorted FP32 form, each against its own plain forward run.
     Timed per whole run with CUDA events (L2 flushed before each run): the plain forward
     run (pic_step), the recording forward run and the reverse sweep, with checkpoints every
     20 steps -- replaying the particle states of each segment from the recorded gathered
@@ -668,7 +673,8 @@ def adjoint_timings(steps, reps, rank=0, stepper="bdf2"):
     from paper_2410_18414_gb300 import pic, workloads
     pic.load_library()
     wl = workloads.weibel_adjoint_128(seed=5 + rank)
-    cfg = make_config(wl, stepper)
+    cfg = make_config(wl, stepper, precision=form)
+    rsz = 4 if form == "fp32" else 8
     N = min(wl.nsteps, steps)
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
@@ -732,24 +738,25 @@ def adjoint_timings(steps, reps, rank=0, stepper="bdf2"):
     r20r = (med([t[0] for t in t20r]) + med([t[1] for t in t20r])) / fwd
     rall = (med([t[0] for t in tall]) + med([t[1] for t in tall])) / fwd
     seg = (N + k20 - 1) // k20
+    st = 8 * rsz * wl.n          # one particle state
+    gf = 8 * rsz * wl.nx * wl.ny  # one step's gather fields
     return {
         "workload": f"weibel_adjoint_128x128_16ppc_cubic_{stepper}", "particles": wl.n,
-        "steps_per_run": N, "form": "fp64", "objective": "W_B at the last step",
+        "steps_per_run": N, "form": form, "objective": "W_B at the last step",
         "forward_ms": fwd,
         "checkpoint_20": {"mode": "replay", "record_forward_ms": med([t[0] for t in t20]),
                           "backward_ms": med([t[1] for t in t20]), "ratio": r20,
-                          "record_bytes": int(N * (80 * wl.n + 64 * wl.nx * wl.ny)
-                                              + (seg + 1 + k20) * 64 * wl.n)},
+                          "record_bytes": int(N * (80 * wl.n + gf) + (seg + 1 + k20) * st)},
         "checkpoint_20_recompute": {"mode": "recompute",
                                     "record_forward_ms": med([t[0] for t in t20r]),
                                     "backward_ms": med([t[1] for t in t20r]), "ratio": r20r,
-                                    "record_bytes": int((seg + 1) * 64 * wl.n + k20 * (
-                                        144 * wl.n + 64 * wl.nx * wl.ny))},
+                                    "record_bytes": int((seg + 1) * st + k20 * (
+                                        80 * wl.n + st + gf))},
         "keep_all_steps": {"mode": "replay", "record_forward_ms": med([t[0] for t in tall]),
                            "backward_ms": med([t[1] for t in tall]), "ratio": rall,
-                           "record_bytes": int(N * (144 * wl.n + 64 * wl.nx * wl.ny))},
+                           "record_bytes": int(N * (80 * wl.n + st + gf))},
         "kernels": kt,
-        "roofline": adjoint_roofline(wl.p, wl.n, kt["adj_push"]["ms_per_launch"]),
+        "roofline": adjoint_roofline(wl.p, wl.n, kt["adj_push"]["ms_per_launch"], form),
     }
 
 
@@ -763,7 +770,7 @@ def run_adjoint(a):
     ranks.barrier()
     clocks = ClockSampler(ranks.local)
     clocks.start()
-    t = adjoint_timings(a.steps, max(1, a.repeats), rank, a.stepper)
+    t = adjoint_timings(a.steps, max(1, a.repeats), rank, a.stepper, a.adjoint_form)
     clk = clocks.stop()
     ranks.barrier()
     # every replica's own ratio; the line reports the slowest rank's
@@ -775,11 +782,11 @@ def run_adjoint(a):
         "metric": "adjoint/forward time", "value": ratio, "unit": "ratio",
         "n_gpus": world, "steps": t["steps_per_run"], "warmup": 1, "repeats": max(1, a.repeats),
         "ms_per_step": t["checkpoint_20"]["backward_ms"] / t["steps_per_run"],
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if t["form"] == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": t["workload"], "particles": t["particles"],
                    "steps_per_run": t["steps_per_run"], "objective": t["objective"],
-                   "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": "fp64",
+                   "gradient": "dW_B/dv0 and dW_B/dP0, every particle", "form": t["form"],
                    "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
         "forward_ms": t["forward_ms"], "checkpoint_20": t["checkpoint_20"],
         "checkpoint_20_recompute": t["checkpoint_20_recompute"],
@@ -799,18 +806,24 @@ def flops_adj_push(p):
     return 2 * (w + dw) + 48 + 29 * (p + 1) ** 2 + 4 * (p + 1) + 10
 
 
-def adjoint_roofline(p, n, ms):
-    """k_adj_push_gather against the FP64 pipe (its FMA rate measured on this device)."""
+def adjoint_roofline(p, n, ms, form="fp64"):
+    """k_adj_push_gather against the FP64 pipe (its FMA rate measured on this device); in
+    the FP32 form its particle arithmetic is FP32 (the field-adjoint sums stay FP64) and
+    the FP32 peak is the reference."""
     if not ms:
         return None
     pk = peaks()
     achieved = flops_adj_push(p) * n / (ms * 1e-3) / 1e12
-    traffic, traffic_src = traffic_of("adj_push_gather", "adjoint128")
+    if form == "fp32":
+        peak, src = fp32_peak_gflops(2070), "FP32 FMA issue rate at the 2070 MHz maximum SM clock"
+        traffic, traffic_src = None, "not captured for the FP32 form"
+    else:
+        peak, src = pk["fp64_gflops"], pk["fp64_src"]
+        traffic, traffic_src = traffic_of("adj_push_gather", "adjoint128")
     return {"kernel": "k_adj_push_gather", "bound": "alu", "achieved": achieved,
-            "peak": pk["fp64_gflops"] / 1e3, "unit": "TFLOP/s",
-            "frac": achieved * 1e3 / pk["fp64_gflops"], "traffic": traffic,
-            "traffic_source": traffic_src, "peak_source": pk["fp64_src"],
-            "note": f"{flops_adj_push(p)} FP64 flops per particle (cubic: 600)"}
+            "peak": peak / 1e3, "unit": "TFLOP/s", "frac": achieved * 1e3 / peak,
+            "traffic": traffic, "traffic_source": traffic_src, "peak_source": src,
+            "note": f"{flops_adj_push(p)} {form.upper()} flops per particle (cubic: 600)"}
 
 
 def main():
@@ -990,9 +1003,10 @@ def main():
 
     # the adjoint (the metric's "adjoint/forward time"): the gradient of W_B on the
     # 262,144-particle Weibel workload, FP64, one timed run per checkpoint setting
-    adjoint = None
+    adjoint = adjoint32 = None
     if not a.no_adjoint:
         adjoint = adjoint_timings(200, 1, rank)
+        adjoint32 = adjoint_timings(200, 1, rank, form="fp32")
 
     # the batched ensemble (256 independent runs, one graph launch per period)
     ensemble = None
@@ -1038,7 +1052,7 @@ def main():
             "other_form": other_form,
             "ratio_vs_other_form": (total_ms / a.steps) and other_ms / (total_ms / a.steps),
             "with_diagnostics": with_diagnostics,
-            "adjoint": adjoint,
+            "adjoint": adjoint, "adjoint_fp32": adjoint32,
             "ensemble": ensemble,
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,

@@ -350,8 +350,7 @@ const char *pic_last_error(const pic_handle *h);
 void pic_destroy(pic_handle *h);
 
 /* ---------------------------------------------------------------- adjoint ----
- * Discrete adjoint of the FP64 step: the exact gradient of an objective of the
- * final state,
+ * Discrete adjoint of the step: the exact gradient of an objective of the final state,
  *     J = sum_ij bz_bar(i, j) B_z(i, j) + sum_p (px_bar_p Px_p + py_bar_p Py_p),
  * B_z = dAy/dx - dAx/dy of the last level and P the last momenta, with respect to the
  * initial velocities v^0 given to pic_init (and, with P^0 = gamma m v^0 taken as the
@@ -370,21 +369,31 @@ void pic_destroy(pic_handle *h);
  *     v^{-1}) are transposed per particle.
  * The paper states the forward method only; the adjoint is a derived capability.
  *
+ * Precision: for an FP64 handle every step of the reverse sweep is FP64.  For an FP32-form
+ * handle (PIC_PREC_FP32_FIX64, unsorted) the adjoint is that of the step in exact
+ * arithmetic evaluated along the FP32 form's own trajectory: the particle adjoints are
+ * FP32 and run through the FP32 weights and push (the fixed-point rounding of the current,
+ * piecewise constant, is taken as the identity), while the field adjoints the particles
+ * deposit are summed in FP64 and the reverse field solve is FP64 with its own FP64
+ * transforms.  The records and checkpointed particle states are then FP32 (32 n bytes a
+ * state, 32 nx ny bytes of gather fields a step); seeds and results stay FP64.
+ *
  * Memory: the state (particles and field histories) is checkpointed every
  * `checkpoint_every` steps (K).  The backward pass rebuilds each segment of K steps from
- * its checkpoint -- the particle states (64 n bytes per step of the segment) and each
- * step's record (see pic_adjoint_mode) -- then runs it backwards.  PIC_ADJ_REPLAY (the
- * default) keeps every step's record from the forward pass and replays only the particle
- * move, costing about (nsteps/K + 1 + K) * 64 n + nsteps * (80 n + 64 nx ny) bytes;
- * PIC_ADJ_RECOMPUTE re-runs the segment's full steps, costing about (nsteps/K + 1) * 64 n
- * + K * (144 n + 64 nx ny) bytes.  Both hold the adjoint state besides. */
+ * its checkpoint -- the particle states (S = 64 n bytes per step of the segment in FP64,
+ * 32 n in the FP32 form) and each step's record (see pic_adjoint_mode) -- then runs it
+ * backwards.  With G = 64 nx ny bytes of gather fields a step (32 nx ny in the FP32 form):
+ * PIC_ADJ_REPLAY (the default) keeps every step's record from the forward pass and replays
+ * only the particle move, costing about (nsteps/K + 1 + K) S + nsteps (80 n + G) bytes;
+ * PIC_ADJ_RECOMPUTE re-runs the segment's full steps, costing about (nsteps/K + 1) S
+ * + K (80 n + S + G) bytes.  Both hold the adjoint state besides. */
 typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
 
 /* What the forward pass keeps between checkpoints. */
 typedef enum {
     PIC_ADJ_REPLAY = 0,    /* every step's record: its gather fields, and per particle
-                              P^{n+1}, v^{n+1} and the A, grad A its push gathered (80 n +
-                              64 nx ny bytes per step); the backward pass replays the particle
+                              P^{n+1}, v^{n+1} and the A, grad A its push gathered (80 n + G
+                              bytes per step); the backward pass replays the particle
                               states of a segment from its checkpoint with the move alone and
                               the recorded P, v (bit for bit the forward's states) */
     PIC_ADJ_RECOMPUTE = 1  /* nothing: the backward pass re-runs every segment's full forward
@@ -392,8 +401,8 @@ typedef enum {
 } pic_adjoint_mode;
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init
- * (step 0, no step started), FP64 (any stepper), PIC_CHARGE_CONTINUITY and without
- * sorting (sort_interval 0), 2D-2V with one species, else PIC_ERR_UNSUPPORTED (or
+ * (step 0, no step started), of either precision (any stepper), PIC_CHARGE_CONTINUITY and
+ * without sorting (sort_interval 0), 2D-2V with one species, else PIC_ERR_UNSUPPORTED (or
  * PIC_ERR_STATE for a handle that has stepped).  checkpoint_every is clamped to 1..nsteps.  Allocates all the
  * adjoint's device memory here (PIC_ERR_CUDA if that fails).  The adjoint keeps h:
  * destroy it before h.  PIC_ERR_INVALID_ARG for NULL pointers or nsteps < 1. */

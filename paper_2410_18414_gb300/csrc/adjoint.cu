@@ -1,4 +1,4 @@
-// Discrete adjoint of the FP64 step: the transpose of the Jacobian of one step of
+// Discrete adjoint of the step: the transpose of the Jacobian of one step of
 // Algorithm 1 (section 4.2) with the BDF-k (section 3.2), CDF-2 (section 3.1) or DIRK
 // (section 3.3) field solve, applied in reverse, for the gradient of an objective of the
 // final state with respect to the initial velocities.
@@ -26,8 +26,13 @@
 //     x^{n+1} = x^n + dt v^n:  x^n b = x^{n+1} b,  v^n b += dt x^{n+1} b
 //   t = 0 (k_adj_init): P^0 = gamma m v^0 and the Taylor start v^{-1}(v^0, E^0).
 //
-// Everything is FP64, one thread per particle or per mode.  Shape weights come from
-// Shape<P, double> (the forward's), their derivatives from the closed forms below.
+// One thread per particle or per mode.  The particle kernels run in the storage type T of
+// the forward they reverse: FP64 for the plain path, FP32 for the FP32 form (the adjoint
+// of the step in exact arithmetic, evaluated along the FP32 form's trajectory; the
+// fixed-point rounding of its current, piecewise constant, is differentiated as the
+// identity).  The field adjoints they deposit are summed in FP64, and the reverse field
+// solve is FP64 in both forms, as the forward's per-mode update is.  Shape weights come
+// from Shape<P, T> (the forward's), their derivatives from the closed forms below.
 #include <algorithm>
 
 #include "common.cuh"
@@ -48,81 +53,85 @@ inline int blocks_for(int64_t n) {
     return (int)b;
 }
 
-// d w[a] / d xi for the weights of Shape<P, double>, from the same offset d.
-template <int P> struct DShape;
-template <> struct DShape<2> {
+// d w[a] / d xi for the weights of Shape<P, T>, from the same offset d.
+template <int P, typename T> struct DShape;
+template <typename T> struct DShape<2, T> {
     // w = ((1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2)
-    static __device__ __forceinline__ void dweights(double xi, double* dw) {
-        const double d = xi - floor(xi + 0.5);
-        dw[0] = d - 0.5;
-        dw[1] = -2.0 * d;
-        dw[2] = d + 0.5;
+    static __device__ __forceinline__ void dweights(T xi, T* dw) {
+        const T d = xi - floor(xi + (T)0.5);
+        dw[0] = d - (T)0.5;
+        dw[1] = (T)-2 * d;
+        dw[2] = d + (T)0.5;
     }
 };
-template <> struct DShape<3> {
+template <typename T> struct DShape<3, T> {
     // w = (e^3/6, 2/3 - d^2 + d^3/2, 2/3 - e^2 + e^3/2, d^3/6), e = 1 - d
-    static __device__ __forceinline__ void dweights(double xi, double* dw) {
-        const double d = xi - floor(xi), e = 1.0 - d;
-        dw[0] = -0.5 * e * e;
-        dw[1] = d * (1.5 * d - 2.0);
-        dw[2] = e * (2.0 - 1.5 * e);
-        dw[3] = 0.5 * d * d;
+    static __device__ __forceinline__ void dweights(T xi, T* dw) {
+        const T d = xi - floor(xi), e = (T)1 - d;
+        dw[0] = (T)-0.5 * e * e;
+        dw[1] = d * ((T)1.5 * d - (T)2);
+        dw[2] = e * ((T)2 - (T)1.5 * e);
+        dw[3] = (T)0.5 * d * d;
     }
 };
-template <> struct DShape<4> {
+template <typename T> struct DShape<4, T> {
     // derivative of (55 + 20 t - 120 t^2 + 80 t^3 - 16 t^4)/96
-    static __device__ __forceinline__ double dmid(double t) {
-        return (20.0 + t * (-240.0 + t * (240.0 - 64.0 * t))) * (1.0 / 96.0);
+    static __device__ __forceinline__ T dmid(T t) {
+        return ((T)20 + t * ((T)-240 + t * ((T)240 - (T)64 * t))) * (T)(1.0 / 96.0);
     }
     // w = ((1-2d)^4/384, mid(1+d), (115 - 120 d^2 + 48 d^4)/192, mid(1-d), (1+2d)^4/384)
-    static __device__ __forceinline__ void dweights(double xi, double* dw) {
-        const double d = xi - floor(xi + 0.5);
-        const double a = 1.0 - 2.0 * d, b = 1.0 + 2.0 * d;
-        dw[0] = -a * a * a * (1.0 / 48.0);
-        dw[1] = dmid(1.0 + d);
-        dw[2] = d * (d * d - 1.25);
-        dw[3] = -dmid(1.0 - d);
-        dw[4] = b * b * b * (1.0 / 48.0);
+    static __device__ __forceinline__ void dweights(T xi, T* dw) {
+        const T d = xi - floor(xi + (T)0.5);
+        const T a = (T)1 - (T)2 * d, b = (T)1 + (T)2 * d;
+        dw[0] = -a * a * a * (T)(1.0 / 48.0);
+        dw[1] = dmid((T)1 + d);
+        dw[2] = d * (d * d - (T)1.25);
+        dw[3] = -dmid((T)1 - d);
+        dw[4] = b * b * b * (T)(1.0 / 48.0);
     }
 };
 
-__device__ __forceinline__ bool inside(double xi, int n) { return xi >= 0.0 && xi <= (double)n; }
+template <typename T>
+__device__ __forceinline__ bool inside(T xi, int n) { return xi >= (T)0 && xi <= (T)n; }
 
-template <int P>
+template <typename T, int P>
 __global__ void __launch_bounds__(kThreads, 3)
-k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
-                  const double* __restrict__ y1, const double* __restrict__ px1,
-                  const double* __restrict__ py1, const double* __restrict__ vx,
-                  const double* __restrict__ vy, const double* __restrict__ vxo,
-                  const double* __restrict__ vyo, const double* __restrict__ gf,
-                  const double2* __restrict__ F, AdjParticles ab, double2* __restrict__ Fb,
+k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
+                  const T* __restrict__ y1, const T* __restrict__ px1,
+                  const T* __restrict__ py1, const T* __restrict__ vx,
+                  const T* __restrict__ vy, const T* __restrict__ vxo,
+                  const T* __restrict__ vyo, const double* __restrict__ gf,
+                  const cplx_t<T>* __restrict__ F, AdjParticlesT<T> ab, double2* __restrict__ Fb,
                   int64_t n, unsigned int* __restrict__ err) {
+    using C = cplx_t<T>;
     const size_t ng = (size_t)g.nx * g.ny;
-    const double q = pp.q, qdt = pp.q * pp.dt, c2 = pp.c * pp.c, mc2 = pp.m * pp.c * pp.c;
+    const T q = (T)pp.q, qdt = (T)(pp.q * pp.dt), c2 = (T)(pp.c * pp.c),
+            mc2 = (T)(pp.m * pp.c * pp.c);
+    const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const double xi = rmul(x1[p], g.inv_dx), yj = rmul(y1[p], g.inv_dy);
+        const T xi = rmul(x1[p], idx_), yj = rmul(y1[p], idy);
         if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
         // the fields the forward push gathered at x^{n+1} (dphi/dx, dphi/dy, Ax, Ay,
         // dAx/dx, dAx/dy, dAy/dx, dAy/dy)
-        double f[8];  // f[0], f[1] (grad phi) are not needed here
-        f[0] = f[1] = 0.0;
+        T f[8];  // f[0], f[1] (grad phi) are not needed here
+        f[0] = f[1] = (T)0;
 #pragma unroll
-        for (int k = 2; k < 8; ++k) f[k] = gf[(size_t)(k + 2) * n + p];
+        for (int k = 2; k < 8; ++k) f[k] = (T)gf[(size_t)(k + 2) * n + p];
         // velocity: v = c^2 u / D
-        const double ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
-        const double D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
-        const double id = 1.0 / D;
-        const double vbx = ab.vx[p], vby = ab.vy[p];
-        const double cd = c2 * id, udv = (ux * vbx + uy * vby) * cd * id;
-        const double ubx = cd * (vbx - ux * udv), uby = cd * (vby - uy * udv);
-        const double pbx = ab.px[p] + ubx, pby = ab.py[p] + uby;
+        const T ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
+        const T D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
+        const T id = (T)1 / D;
+        const T vbx = ab.vx[p], vby = ab.vy[p];
+        const T cd = c2 * id, udv = (ux * vbx + uy * vby) * cd * id;
+        const T ubx = cd * (vbx - ux * udv), uby = cd * (vby - uy * udv);
+        const T pbx = ab.px[p] + ubx, pby = ab.py[p] + uby;
         // momentum: P^{n+1} = P^n + q dt (-grad phi + (grad A) . v*)
-        const double vsx = 2.0 * vx[p] - vxo[p], vsy = 2.0 * vy[p] - vyo[p];
-        double gb[8];
+        const T vsx = (T)2 * vx[p] - vxo[p], vsy = (T)2 * vy[p] - vyo[p];
+        T gb[8];
         gb[0] = -qdt * pbx;
         gb[1] = -qdt * pby;
         gb[2] = -q * ubx;
@@ -131,85 +140,87 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const double* __restrict__ x1,
         gb[5] = qdt * pby * vsx;
         gb[6] = qdt * pbx * vsy;
         gb[7] = qdt * pby * vsy;
-        const double vsbx = qdt * (pbx * f[4] + pby * f[5]);
-        const double vsby = qdt * (pbx * f[6] + pby * f[7]);
-        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
-        const int ix = Shape<P, double>::weights(xi, wx);
-        const int iy = Shape<P, double>::weights(yj, wy);
-        DShape<P>::dweights(xi, dwx);
-        DShape<P>::dweights(yj, dwy);
+        const T vsbx = qdt * (pbx * f[4] + pby * f[5]);
+        const T vsby = qdt * (pbx * f[6] + pby * f[7]);
+        T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        DShape<P, T>::dweights(xi, dwx);
+        DShape<P, T>::dweights(yj, dwy);
         // one pass over the stencil: s = sum_f gb_f F_f at each node gives the position
         // gradient (separable: along y in the row, then across rows), and gb is deposited
-        double xg = 0.0, yg = 0.0;
+        T xg = 0, yg = 0;
 #pragma unroll 1
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
-            const double wxa = wx[a];
-            double sx = 0.0, sy = 0.0;
+            const T wxa = wx[a];
+            T sx = 0, sy = 0;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const size_t nd = row + wrap_idx(iy + b, g.ny);
-                const double2* node = F + nd * 4;
-                double sn = 0.0;
+                const C* node = F + nd * 4;
+                T sn = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const double2 v = __ldg(node + k);
+                    const C v = __ldg(node + k);
                     sn += gb[2 * k] * v.x + gb[2 * k + 1] * v.y;
                 }
                 sx += wy[b] * sn;
                 sy += dwy[b] * sn;
-                const double w = wxa * wy[b];
+                const T w = wxa * wy[b];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    atomicAdd(&Fb[k * ng + nd].x, w * gb[2 * k]);
-                    atomicAdd(&Fb[k * ng + nd].y, w * gb[2 * k + 1]);
+                    atomicAdd(&Fb[k * ng + nd].x, (double)(w * gb[2 * k]));
+                    atomicAdd(&Fb[k * ng + nd].y, (double)(w * gb[2 * k + 1]));
                 }
             }
             xg += dwx[a] * sx;
             yg += wxa * sy;
         }
-        ab.x[p] += g.inv_dx * xg;
-        ab.y[p] += g.inv_dy * yg;
+        ab.x[p] += idx_ * xg;
+        ab.y[p] += idy * yg;
         ab.px[p] = pbx;
         ab.py[p] = pby;
-        ab.vx[p] = ab.vxo[p] + 2.0 * vsbx;
-        ab.vy[p] = ab.vyo[p] + 2.0 * vsby;
+        ab.vx[p] = ab.vxo[p] + (T)2 * vsbx;
+        ab.vy[p] = ab.vyo[p] + (T)2 * vsby;
         ab.vxo[p] = -vsbx;
         ab.vyo[p] = -vsby;
     }
 }
 
-template <int P>
+template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
-k_adj_deposit_move(ParticleGeom g, const double* __restrict__ x1, const double* __restrict__ y1,
-                   const double* __restrict__ vx, const double* __restrict__ vy,
-                   const double2* __restrict__ Jb, AdjParticles ab, int64_t n,
+k_adj_deposit_move(ParticleGeom g, const T* __restrict__ x1, const T* __restrict__ y1,
+                   const T* __restrict__ vx, const T* __restrict__ vy,
+                   const double2* __restrict__ Jb, AdjParticlesT<T> ab, int64_t n,
                    unsigned int* __restrict__ err) {
+    const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy, dt = (T)g.dt;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const double xi = rmul(x1[p], g.inv_dx), yj = rmul(y1[p], g.inv_dy);
+        const T xi = rmul(x1[p], idx_), yj = rmul(y1[p], idy);
         if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
-        double wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
-        const int ix = Shape<P, double>::weights(xi, wx);
-        const int iy = Shape<P, double>::weights(yj, wy);
-        DShape<P>::dweights(xi, dwx);
-        DShape<P>::dweights(yj, dwy);
+        T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        DShape<P, T>::dweights(xi, dwx);
+        DShape<P, T>::dweights(yj, dwy);
         // separable sums: row a first along y with wy and dwy, then across rows
-        double sx = 0, sy = 0, dxx = 0, dxy = 0, dyx = 0, dyy = 0;
+        T sx = 0, sy = 0, dxx = 0, dxy = 0, dyx = 0, dyy = 0;
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
-            double rx = 0, ry = 0, rdx = 0, rdy = 0;
+            T rx = 0, ry = 0, rdx = 0, rdy = 0;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
-                const double2 j = __ldg(Jb + row + wrap_idx(iy + b, g.ny));
-                rx += wy[b] * j.x;
-                ry += wy[b] * j.y;
-                rdx += dwy[b] * j.x;
-                rdy += dwy[b] * j.y;
+                const double2 jd = __ldg(Jb + row + wrap_idx(iy + b, g.ny));
+                const T jx = (T)jd.x, jy = (T)jd.y;
+                rx += wy[b] * jx;
+                ry += wy[b] * jy;
+                rdx += dwy[b] * jx;
+                rdy += dwy[b] * jy;
             }
             sx += wx[a] * rx;
             sy += wx[a] * ry;
@@ -218,13 +229,13 @@ k_adj_deposit_move(ParticleGeom g, const double* __restrict__ x1, const double* 
             dyx += wx[a] * rdx;
             dyy += wx[a] * rdy;
         }
-        const double vxp = vx[p], vyp = vy[p];
-        const double xb = ab.x[p] + g.inv_dx * (vxp * dxx + vyp * dxy);
-        const double yb = ab.y[p] + g.inv_dy * (vxp * dyx + vyp * dyy);
+        const T vxp = vx[p], vyp = vy[p];
+        const T xb = ab.x[p] + idx_ * (vxp * dxx + vyp * dxy);
+        const T yb = ab.y[p] + idy * (vxp * dyx + vyp * dyy);
         ab.x[p] = xb;
         ab.y[p] = yb;
-        ab.vx[p] = ab.vx[p] + sx + g.dt * xb;
-        ab.vy[p] = ab.vy[p] + sy + g.dt * yb;
+        ab.vx[p] = ab.vx[p] + sx + dt * xb;
+        ab.vy[p] = ab.vy[p] + sy + dt * yb;
     }
 }
 
@@ -510,16 +521,18 @@ k_adj_e0(ModeCommon mc, const double2* __restrict__ phi, double2* __restrict__ o
 }
 
 // dst[k n + i] = src.p[k][i] (pack) or dst.p[k][i] = src[k n + i] (unpack), k = blockIdx.y.
-__global__ void k_pack8(Ptr8 src, double* __restrict__ dst, int64_t n) {
-    const double* s = src.p[blockIdx.y];
-    double* d = dst + (size_t)blockIdx.y * n;
+template <typename T>
+__global__ void k_pack8(Ptr8T<T> src, T* __restrict__ dst, int64_t n) {
+    const T* s = src.p[blockIdx.y];
+    T* d = dst + (size_t)blockIdx.y * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         d[i] = s[i];
 }
-__global__ void k_unpack8(const double* __restrict__ src, Ptr8 dst, int64_t n) {
-    const double* s = src + (size_t)blockIdx.y * n;
-    double* d = const_cast<double*>(dst.p[blockIdx.y]);
+template <typename T>
+__global__ void k_unpack8(const T* __restrict__ src, Ptr8T<T> dst, int64_t n) {
+    const T* s = src + (size_t)blockIdx.y * n;
+    T* d = const_cast<T*>(dst.p[blockIdx.y]);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         d[i] = s[i];
@@ -535,57 +548,58 @@ __global__ void k_real_to_cplx(const double* __restrict__ src, double2* __restri
 // t = 0: P^0 = gamma m v^0 and v^{-1} = v^0 - kappa (E - v (v . E)/c^2), kappa =
 // dt q/(gamma m), E = E^0 gathered at x^0.  Gradient with respect to v^0 (gv) and, with
 // P^0 as the independent variable, with respect to P^0 (gp = (dv/dP)^T gv).
-template <int P>
+template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
-k_adj_init(ParticleGeom g, PushParams pp, const double* __restrict__ x0,
-           const double* __restrict__ y0, const double* __restrict__ vx0,
-           const double* __restrict__ vy0, const double2* __restrict__ E, AdjParticles ab,
-           double* __restrict__ gvx, double* __restrict__ gvy, double* __restrict__ gpx,
-           double* __restrict__ gpy, int64_t n, unsigned int* __restrict__ err) {
-    const double c2 = pp.c * pp.c, m = pp.m;
+k_adj_init(ParticleGeom g, PushParams pp, const T* __restrict__ x0, const T* __restrict__ y0,
+           const T* __restrict__ vx0, const T* __restrict__ vy0, const double2* __restrict__ E,
+           AdjParticlesT<T> ab, double* __restrict__ gvx, double* __restrict__ gvy,
+           double* __restrict__ gpx, double* __restrict__ gpy, int64_t n,
+           unsigned int* __restrict__ err) {
+    const T c2 = (T)(pp.c * pp.c), m = (T)pp.m;
+    const T idx_ = (T)g.inv_dx, idy = (T)g.inv_dy;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const double xi = x0[p] * g.inv_dx, yj = y0[p] * g.inv_dy;
+        const T xi = x0[p] * idx_, yj = y0[p] * idy;
         if (!inside(xi, g.nx) || !inside(yj, g.ny)) {
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
-        double wx[P + 1], wy[P + 1];
-        const int ix = Shape<P, double>::weights(xi, wx);
-        const int iy = Shape<P, double>::weights(yj, wy);
-        double ex = 0, ey = 0;
+        T wx[P + 1], wy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
+        T ex = 0, ey = 0;
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 const double2 e = E[row + wrap_idx(iy + b, g.ny)];
-                const double w = wx[a] * wy[b];
-                ex += w * e.x;
-                ey += w * e.y;
+                const T w = wx[a] * wy[b];
+                ex += w * (T)e.x;
+                ey += w * (T)e.y;
             }
         }
-        const double vx = vx0[p], vy = vy0[p];
-        const double gam = 1.0 / sqrt(1.0 - (vx * vx + vy * vy) / c2);
+        const T vx = vx0[p], vy = vy0[p];
+        const T gam = (T)1 / sqrt((T)1 - (vx * vx + vy * vy) / c2);
         // dP/dv = gamma m (I + gamma^2 v v^T / c^2)
-        const double pbx = ab.px[p], pby = ab.py[p];
-        const double pvb = vx * pbx + vy * pby;
-        double gx = ab.vx[p] + gam * m * (pbx + gam * gam * vx * pvb / c2);
-        double gy = ab.vy[p] + gam * m * (pby + gam * gam * vy * pvb / c2);
+        const T pbx = ab.px[p], pby = ab.py[p];
+        const T pvb = vx * pbx + vy * pby;
+        T gx = ab.vx[p] + gam * m * (pbx + gam * gam * vx * pvb / c2);
+        T gy = ab.vy[p] + gam * m * (pby + gam * gam * vy * pvb / c2);
         // v^{-1}: transpose of I + kappa gamma^2 T v^T / c^2 + kappa (v E^T + (v.E) I)/c^2
-        const double wxb = ab.vxo[p], wyb = ab.vyo[p];
-        const double kap = pp.dt * pp.q / (gam * m);
-        const double vde = vx * ex + vy * ey;
-        const double tx = ex - vx * vde / c2, ty = ey - vy * vde / c2;
-        const double tw = tx * wxb + ty * wyb, vw = vx * wxb + vy * wyb;
+        const T wxb = ab.vxo[p], wyb = ab.vyo[p];
+        const T kap = (T)(pp.dt * pp.q) / (gam * m);
+        const T vde = vx * ex + vy * ey;
+        const T tx = ex - vx * vde / c2, ty = ey - vy * vde / c2;
+        const T tw = tx * wxb + ty * wyb, vw = vx * wxb + vy * wyb;
         gx += wxb + kap * gam * gam * vx * tw / c2 + (kap / c2) * (ex * vw + vde * wxb);
         gy += wyb + kap * gam * gam * vy * tw / c2 + (kap / c2) * (ey * vw + vde * wyb);
-        if (gvx) gvx[p] = gx;
-        if (gvy) gvy[p] = gy;
+        if (gvx) gvx[p] = (double)gx;
+        if (gvy) gvy[p] = (double)gy;
         // dv/dP = (I - v v^T / c^2) / (gamma m)
-        const double vg = vx * gx + vy * gy;
-        if (gpx) gpx[p] = (gx - vx * vg / c2) / (gam * m);
-        if (gpy) gpy[p] = (gy - vy * vg / c2) / (gam * m);
+        const T vg = vx * gx + vy * gy;
+        if (gpx) gpx[p] = (double)((gx - vx * vg / c2) / (gam * m));
+        if (gpy) gpy[p] = (double)((gy - vy * vg / c2) / (gam * m));
     }
 }
 
@@ -597,38 +611,39 @@ inline int mode_blocks(const ModeCommon& mc) {
 
 #define GPIC_ADJ_DISPATCH(p, KERNEL, ...)                                                  \
     switch (p) {                                                                         \
-        case 2: KERNEL<2><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
-        case 3: KERNEL<3><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
-        case 4: KERNEL<4><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;       \
+        case 2: KERNEL<T, 2><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;    \
+        case 3: KERNEL<T, 3><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;    \
+        case 4: KERNEL<T, 4><<<blocks_for(n), kThreads, 0, s>>>(__VA_ARGS__); break;    \
         default: return cudaErrorInvalidValue;                                          \
     }
 
+template <typename T>
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
-                                   const double* x1, const double* y1, const double* px1,
-                                   const double* py1, const double* vx, const double* vy,
-                                   const double* vxo, const double* vyo, const double* gf,
-                                   const double2* F, AdjParticles ab, double2* Fb, int64_t n,
-                                   unsigned int* err, cudaStream_t s) {
+                                   const T* x1, const T* y1, const T* px1, const T* py1,
+                                   const T* vx, const T* vy, const T* vxo, const T* vyo,
+                                   const double* gf, const void* F, AdjParticlesT<T> ab,
+                                   double2* Fb, int64_t n, unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gf, F, ab,
-                      Fb, n, err)
+    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gf,
+                      (const cplx_t<T>*)F, ab, Fb, n, err)
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
-                                    const double* y1, const double* vx, const double* vy,
-                                    const double2* Jb, AdjParticles ab, int64_t n,
-                                    unsigned int* err, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const T* x1, const T* y1,
+                                    const T* vx, const T* vy, const double2* Jb,
+                                    AdjParticlesT<T> ab, int64_t n, unsigned int* err,
+                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     GPIC_ADJ_DISPATCH(p, k_adj_deposit_move, g, x1, y1, vx, vy, Jb, ab, n, err)
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const double* x0,
-                            const double* y0, const double* vx0, const double* vy0,
-                            const double2* E, AdjParticles ab, double* gvx, double* gvy,
-                            double* gpx, double* gpy, int64_t n, unsigned int* err,
-                            cudaStream_t s) {
+template <typename T>
+cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const T* x0,
+                            const T* y0, const T* vx0, const T* vy0, const double2* E,
+                            AdjParticlesT<T> ab, double* gvx, double* gvy, double* gpx,
+                            double* gpy, int64_t n, unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     GPIC_ADJ_DISPATCH(p, k_adj_init, g, pp, x0, y0, vx0, vy0, E, ab, gvx, gvy, gpx, gpy, n, err)
     return cudaGetLastError();
@@ -682,17 +697,19 @@ cudaError_t launch_adj_e0(const ModeCommon& mc, const double2* phi, double2* out
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack8(Ptr8 src, double* dst, int64_t n, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_pack8(Ptr8T<T> src, T* dst, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int bx = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
-    k_pack8<<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
+    k_pack8<T><<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack8(const double* src, Ptr8 dst, int64_t n, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_unpack8(const T* src, Ptr8T<T> dst, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int bx = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 2);
-    k_unpack8<<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
+    k_unpack8<T><<<dim3(bx, 8), kThreads, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 
@@ -701,5 +718,25 @@ cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cuda
     k_real_to_cplx<<<blocks_for(n), kThreads, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
+
+#define GPIC_ADJ_INST(T)                                                                    \
+    template cudaError_t launch_adj_push_gather<T>(                                         \
+        int, const ParticleGeom&, const PushParams&, const T*, const T*, const T*, const T*, \
+        const T*, const T*, const T*, const T*, const double*, const void*, AdjParticlesT<T>, \
+        double2*, int64_t, unsigned int*, cudaStream_t);                                    \
+    template cudaError_t launch_adj_deposit_move<T>(int, const ParticleGeom&, const T*,     \
+                                                    const T*, const T*, const T*,           \
+                                                    const double2*, AdjParticlesT<T>,       \
+                                                    int64_t, unsigned int*, cudaStream_t);  \
+    template cudaError_t launch_adj_init<T>(int, const ParticleGeom&, const PushParams&,    \
+                                            const T*, const T*, const T*, const T*,         \
+                                            const double2*, AdjParticlesT<T>, double*,      \
+                                            double*, double*, double*, int64_t,             \
+                                            unsigned int*, cudaStream_t);                   \
+    template cudaError_t launch_pack8<T>(Ptr8T<T>, T*, int64_t, cudaStream_t);              \
+    template cudaError_t launch_unpack8<T>(const T*, Ptr8T<T>, int64_t, cudaStream_t);
+GPIC_ADJ_INST(double)
+GPIC_ADJ_INST(float)
+#undef GPIC_ADJ_INST
 
 }  // namespace gpic

@@ -1,8 +1,8 @@
 // Host side of the adjoint API (include/pic.h): checkpoints of the forward run, the
-// segment-by-segment recomputation and the reverse sweep of the FP64 step (BDF-k, the
-// three CDF-2 forms or DIRK).
+// segment-by-segment recomputation and the reverse sweep of the step (BDF-k, the three
+// CDF-2 forms or DIRK), for the plain FP64 path and the (unsorted) FP32 form.
 //
-// Storage (all FP64, device):
+// Storage (device; particle values in the handle's storage type T, everything else FP64):
 //   state     the eight particle arrays of one time level, in the order x, y, Px, Py,
 //             v^n (x, y), v^{n-1} (x, y): 8 n values
 //   ck[c]     checkpoint c: the state at step c K and the field history (BDF: the ring
@@ -11,12 +11,13 @@
 //             fields, so the handle can be put back after the sweep
 //   rec[j]    the state after step c0 + j of the segment being swept (j = 0..K-1)
 //   records   per step (every step in the replay mode, the segment's in the recompute
-//             mode): the gather fields the step used (recg) and recf: P^{n+1}, v^{n+1} and
-//             the gathered A and grad A of each particle (10 n)
-//   adjoint   particle adjoints (8 n), the history adjoints (BDF: 3 L + k spectra, slot
+//             mode): the gather fields the step used (recg, in T) and recf (FP64): P^{n+1},
+//             v^{n+1} and the gathered A and grad A of each particle (10 n)
+//   adjoint   particle adjoints (8 n, in T), the history adjoints (BDF: 3 L + k spectra, slot
 //             of time level t = t mod L; CDF-2: 12 by role, each (cur, prev) pair swapped
 //             after every reverse step; DIRK: 9 by role, in place), field-adjoint planes
-//             and transform scratch
+//             and transform scratch, and FP64 twiddle tables for the reverse field solve
+//             (an FP32-form handle's own tables are FP32)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,21 +37,25 @@ struct pic_adjoint {
     int kind = K_BDF;  // StepperKind of the handle
     int nh = 0;        // history spectra: 3 L + Lr (BDF), 12 (CDF-2), 9 (DIRK)
     size_t n = 0, ng = 0;
+    bool f32 = false;  // the FP32 form: particle values in float
+    size_t rsz = 8;    // bytes of one particle value
     struct Ck {
-        double* state = nullptr;
+        void* state = nullptr;
         double2* hist = nullptr;  // nh spectra, slot or role order
         int head = 0, head_r = 0;
         int64_t step = 0;
     };
     std::vector<Ck> ck;
-    double2* final_j = nullptr;  // J of the last step
-    double2* final_g = nullptr;  // gather fields of the last step
-    double* rec = nullptr;       // K states
-    double2* recg = nullptr;     // K x 4 ng
+    double2* final_j = nullptr;  // J of the last step (FP64, or int64 sums)
+    void* final_g = nullptr;     // gather fields of the last step (4 ng complex of T)
+    void* rec = nullptr;         // K states
+    void* recg = nullptr;        // K x 4 ng complex of T
     double* recf = nullptr;      // per step 10 n: P^{n+1}, v^{n+1} and the gathered A, grad A
     int seg_held = -1;           // segment whose states rec holds
     int mode = 0;                // PIC_ADJ_REPLAY or PIC_ADJ_RECOMPUTE
-    double* ab = nullptr;        // particle adjoints, 8 n
+    void* ab = nullptr;          // particle adjoints, 8 n
+    double2* twx = nullptr;      // FP64 twiddles along x and y
+    double2* twy = nullptr;
     double2* hb = nullptr;       // history adjoints, nh ng
     double2* role[12] = {};      // CDF-2, DIRK: the history adjoint of each role
     double2* fb = nullptr;       // field-adjoint planes, 4 ng
@@ -109,18 +114,39 @@ std::vector<void*> ring_slots(pic_handle* h) {
     return s;
 }
 
-Ptr8 handle_ptrs(pic_handle* h) {
+template <typename T>
+Ptr8T<T> handle_ptrs(pic_handle* h) {
     void* arr[8];
     handle_arrays(h, arr);
-    Ptr8 p;
-    for (int k = 0; k < 8; ++k) p.p[k] = (const double*)arr[k];
+    Ptr8T<T> p;
+    for (int k = 0; k < 8; ++k) p.p[k] = (const T*)arr[k];
     return p;
 }
 
-pic_status save_state(pic_adjoint* a, double* dst) {
+// Byte offset of state j (or array k of a state) in a block of states.
+size_t state_bytes(const pic_adjoint* a) { return 8 * a->n * a->rsz; }
+
+pic_status save_state(pic_adjoint* a, void* dst) {
     pic_handle* h = a->h;
-    CK(launch_pack8(handle_ptrs(h), dst, (int64_t)a->n, h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        return launch_pack8<T>(handle_ptrs<T>(h), (T*)dst, (int64_t)a->n, h->s);
+    }));
     return PIC_OK;
+}
+
+// FP64 2-D transforms with the adjoint's own twiddles (whatever the handle's precision).
+cudaError_t fft64_forward(pic_adjoint* a, const double2* in, double2* out) {
+    pic_handle* h = a->h;
+    cudaError_t e = launch_fft_y<double>(in, out, h->nx, h->ny, 1, h->fy, a->twy, -1, 0, h->s);
+    if (e != cudaSuccess) return e;
+    return launch_fft_x<double>(out, out, h->nx, h->ny, 1, h->fx, a->twx, -1, h->s);
+}
+cudaError_t fft64_inverse(pic_adjoint* a, double2* buf, double2* out) {
+    pic_handle* h = a->h;
+    cudaError_t e = launch_fft_x<double>(buf, buf, h->nx, h->ny, 1, h->fx, a->twx, +1, h->s);
+    if (e != cudaSuccess) return e;
+    return launch_fft_y<double>(buf, out, h->nx, h->ny, 1, h->fy, a->twy, +1, 0, h->s);
 }
 
 pic_status save_checkpoint(pic_adjoint* a, pic_adjoint::Ck& c) {
@@ -140,7 +166,10 @@ pic_status save_checkpoint(pic_adjoint* a, pic_adjoint::Ck& c) {
 pic_status restore_checkpoint(pic_adjoint* a, const pic_adjoint::Ck& c) {
     pic_handle* h = a->h;
     h->vcur = 0;
-    CK(launch_unpack8(c.state, handle_ptrs(h), (int64_t)a->n, h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        return launch_unpack8<T>((const T*)c.state, handle_ptrs<T>(h), (int64_t)a->n, h->s);
+    }));
     const std::vector<void*> slots = ring_slots(h);
     for (size_t i = 0; i < slots.size(); ++i)
         CK(cudaMemcpyAsync(slots[i], c.hist + i * a->ng, a->ng * sizeof(double2),
@@ -173,18 +202,21 @@ pic_status step_and_record(pic_adjoint* a, int s, int state_j) {
     h->gather_out = nullptr;
     if (st != PIC_OK) return st;
     if (state_j >= 0) {
-        st = save_state(a, a->rec + (size_t)state_j * 8 * a->n);
+        st = save_state(a, (char*)a->rec + (size_t)state_j * state_bytes(a));
         if (st != PIC_OK) return st;
     }
-    CK(cudaMemcpyAsync(a->recg + r * 4 * a->ng, h->G, 4 * a->ng * sizeof(double2),
-                       cudaMemcpyDeviceToDevice, h->s));
+    const size_t gbytes = 4 * a->ng * 2 * a->rsz;
+    CK(cudaMemcpyAsync((char*)a->recg + r * gbytes, h->G, gbytes, cudaMemcpyDeviceToDevice,
+                       h->s));
     return PIC_OK;
 }
 
-AdjParticles adjoint_arrays(pic_adjoint* a) {
-    double* b = a->ab;
+template <typename T>
+AdjParticlesT<T> adjoint_arrays(pic_adjoint* a) {
+    T* b = (T*)a->ab;
     const size_t n = a->n;
-    return AdjParticles{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n, b + 7 * n};
+    return AdjParticlesT<T>{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n,
+                            b + 7 * n};
 }
 
 double2* hist_slot(pic_adjoint* a, int field, int64_t t) {
@@ -197,23 +229,28 @@ double2* hist_slot(pic_adjoint* a, int field, int64_t t) {
     return a->hb + (size_t)(field * a->L + s) * a->ng;
 }
 
-// Reverse of step n (from level n+1 to level n): s0 = state n, s1 = state n+1, g = the
-// gather fields of the step.
-pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const double* s1,
-                         const double* gf, const double2* g) {
+// Reverse of step n (from level n+1 to level n): s0 = state n, s1 = state n+1 (in T),
+// g = the gather fields of the step.
+pic_status backward_step(pic_adjoint* a, int64_t n, const void* s0v, const void* s1v,
+                         const double* gf, const void* g) {
     pic_handle* h = a->h;
     const size_t np = a->n, ng = a->ng;
-    AdjParticles ab = adjoint_arrays(a);
     CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
     TimedScope tp(h, PIC_KT_ADJ_PUSH);
-    CK(launch_adj_push_gather(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np, s1 + 3 * np,
-                              s0 + 4 * np, s0 + 5 * np, s0 + 6 * np, s0 + 7 * np, gf, g, ab, a->fb,
-                              (int64_t)np, h->err, h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        const T* s0 = (const T*)s0v;
+        const T* s1 = (const T*)s1v;
+        return launch_adj_push_gather<T>(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np,
+                                         s1 + 3 * np, s0 + 4 * np, s0 + 5 * np, s0 + 6 * np,
+                                         s0 + 7 * np, gf, g, adjoint_arrays<T>(a), a->fb,
+                                         (int64_t)np, h->err, h->s);
+    }));
     tp.end();
     TimedScope tf(h, PIC_KT_ADJ_FIELD);
-    CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, h->twy, -1, 0, h->s));
+    CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, a->twy, -1, 0, h->s));
     const bool fused = adj_columns_smem(h->nx) <= kFieldColumnsSmemMax;
-    if (!fused) CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, h->twx, -1, h->s));
+    if (!fused) CK(launch_fft_x<double>(a->zb, a->zb, h->nx, h->ny, 4, h->fx, a->twx, -1, h->s));
     AdjModeParams ap{};
     CdfParams cp{};
     DirkParams dp{};
@@ -240,20 +277,25 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const double* s0, const doub
         for (int r = 0; r < 9; ++r) *roles[r] = a->role[r];
     }
     if (fused) {
-        CK(launch_adj_columns(h->mc, a->kind, ap, cp, dp, a->zb, a->js, h->fx,
-                              (const double2*)h->twx, h->s));
-        CK(launch_fft_y<double>(a->js, a->jg, h->nx, h->ny, 1, h->fy, h->twy, +1, 0, h->s));
+        CK(launch_adj_columns(h->mc, a->kind, ap, cp, dp, a->zb, a->js, h->fx, a->twx, h->s));
+        CK(launch_fft_y<double>(a->js, a->jg, h->nx, h->ny, 1, h->fy, a->twy, +1, 0, h->s));
     } else {
         CK(launch_adj_modes(h->mc, a->kind, ap, cp, dp, a->zb, a->js, h->s));
-        CK(inverse_fft(h, a->js, a->jg, 1));
+        CK(fft64_inverse(a, a->js, a->jg));
     }
     // CDF-2: the adjoints before the step were written into the other buffer of each pair
     if (a->kind == K_CDF2)
         for (int r = 0; r < 12; r += 2) std::swap(a->role[r], a->role[r + 1]);
     tf.end();
     TimedScope td(h, PIC_KT_ADJ_DEPOSIT);
-    CK(launch_adj_deposit_move(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np, a->jg, ab,
-                               (int64_t)np, h->err, h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        const T* s0 = (const T*)s0v;
+        const T* s1 = (const T*)s1v;
+        return launch_adj_deposit_move<T>(h->p, h->geom, s1, s1 + np, s0 + 4 * np, s0 + 5 * np,
+                                          a->jg, adjoint_arrays<T>(a), (int64_t)np, h->err,
+                                          h->s);
+    }));
     return PIC_OK;
 }
 
@@ -274,11 +316,10 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     *out = nullptr;
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
     if (nsteps < 1) return fail(h, PIC_ERR_INVALID_ARG, "nsteps must be >= 1");
-    if (h->fp32 || h->cfg.charge != PIC_CHARGE_CONTINUITY || h->sorting || h->vdim == 3 ||
-        h->spp.n > 0)
+    if (h->cfg.charge != PIC_CHARGE_CONTINUITY || h->sorting || h->vdim == 3 || h->spp.n > 0)
         return fail(h, PIC_ERR_UNSUPPORTED,
-                    "the adjoint needs the FP64 path, the continuity charge, one species in "
-                    "2D-2V and no sorting");
+                    "the adjoint needs the continuity charge, one species in 2D-2V and no "
+                    "sorting");
     if (h->step != 0 || h->phase != 0)
         return fail(h, PIC_ERR_STATE, "the adjoint needs a handle fresh from pic_init");
     pic_adjoint* a = new pic_adjoint();
@@ -295,7 +336,9 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     a->nh = a->kind == K_BDF ? 3 * a->L + a->Lr : a->kind == K_CDF2 ? 12 : 9;
     a->n = (size_t)h->n;
     a->ng = h->ng;
-    const size_t sb = 8 * std::max<size_t>(a->n, 1) * sizeof(double);
+    a->f32 = h->fp32;
+    a->rsz = h->rsz;
+    const size_t sb = 8 * std::max<size_t>(a->n, 1) * a->rsz;
     const size_t hbytes = (size_t)a->nh * a->ng * sizeof(double2);
     const size_t gb = a->ng * sizeof(double2);
     cudaError_t e = cudaSuccess;
@@ -304,13 +347,18 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
         if (e == cudaSuccess) e = aalloc(a, (void**)&c.state, sb);
         if (e == cudaSuccess) e = aalloc(a, (void**)&c.hist, hbytes);
     }
+    const size_t gfb = 4 * a->ng * 2 * a->rsz;  // one step's gather fields
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_j, gb);
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_g, 4 * gb);
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->rec, (size_t)a->K * sb);
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->recg, nrec * 4 * gb);
+    if (e == cudaSuccess) e = aalloc(a, &a->final_g, gfb);
+    if (e == cudaSuccess) e = aalloc(a, &a->rec, (size_t)a->K * sb);
+    if (e == cudaSuccess) e = aalloc(a, &a->recg, nrec * gfb);
     if (e == cudaSuccess)
         e = aalloc(a, (void**)&a->recf, nrec * kRec * std::max<size_t>(a->n, 1) * sizeof(double));
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->ab, sb);
+    if (e == cudaSuccess) e = aalloc(a, &a->ab, sb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->twx, (size_t)h->nx * sizeof(double2));
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->twy, (size_t)h->ny * sizeof(double2));
+    if (e == cudaSuccess) e = launch_twiddles<double>(a->twx, h->nx, h->s);
+    if (e == cudaSuccess) e = launch_twiddles<double>(a->twy, h->ny, h->s);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->hb, hbytes);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->fb, 4 * gb);
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->zb, 4 * gb);
@@ -321,7 +369,7 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     // E^0 = -grad phi^0 on the mesh (every phi level holds phi^0 at step 0)
     const void* phi0 = a->kind == K_BDF ? h->phi_l[h->head] : a->kind == K_CDF2 ? h->cdf.phi : h->dirk.phi;
     if (e == cudaSuccess) e = launch_adj_e0(h->mc, (const double2*)phi0, a->tmp, h->s);
-    if (e == cudaSuccess) e = inverse_fft(h, a->tmp, a->e0, 1);
+    if (e == cudaSuccess) e = fft64_inverse(a, a->tmp, a->e0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) {
         release(a);
@@ -359,7 +407,7 @@ pic_status pic_adjoint_forward(pic_adjoint* a) {
     pic_status st = save_checkpoint(a, a->ck[a->nseg]);
     if (st != PIC_OK) return st;
     CK(cudaMemcpyAsync(a->final_j, h->J, a->ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
-    CK(cudaMemcpyAsync(a->final_g, h->G, 4 * a->ng * sizeof(double2), cudaMemcpyDeviceToDevice,
+    CK(cudaMemcpyAsync(a->final_g, h->G, 4 * a->ng * 2 * a->rsz, cudaMemcpyDeviceToDevice,
                        h->s));
     return PIC_OK;
 }
@@ -374,15 +422,26 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
     if (h->phase != 0) return fail(h, PIC_ERR_STATE, "pic_adjoint_backward inside a step");
     const size_t np = a->n, ng = a->ng;
     const size_t hbytes = (size_t)a->nh * ng * sizeof(double2);
-    CK(cudaMemsetAsync(a->ab, 0, 8 * std::max<size_t>(np, 1) * sizeof(double), h->s));
+    CK(cudaMemsetAsync(a->ab, 0, 8 * std::max<size_t>(np, 1) * a->rsz, h->s));
     CK(cudaMemsetAsync(a->hb, 0, hbytes, h->s));
     if (a->kind != K_BDF)
         for (int r = 0; r < a->nh; ++r) a->role[r] = a->hb + (size_t)r * ng;
-    if (px_bar && np) CK(cudaMemcpyAsync(a->ab + 2 * np, px_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
-    if (py_bar && np) CK(cudaMemcpyAsync(a->ab + 3 * np, py_bar, np * sizeof(double), cudaMemcpyDefault, h->s));
+    // momentum seeds, converted to the particle storage type (through the FP64 staging
+    // buffer of the handle)
+    const double* pbar[2] = {px_bar, py_bar};
+    for (int c = 0; c < 2; ++c) {
+        if (!pbar[c] || !np) continue;
+        void* dst = (char*)a->ab + (2 + c) * np * a->rsz;
+        if (!a->f32) {
+            CK(cudaMemcpyAsync(dst, pbar[c], np * sizeof(double), cudaMemcpyDefault, h->s));
+        } else {
+            CK(cudaMemcpyAsync(h->stage, pbar[c], np * sizeof(double), cudaMemcpyDefault, h->s));
+            CK(launch_convert<double, float>(h->stage, (float*)dst, (int64_t)np, h->s));
+        }
+    }
     if (bz_bar) {
         CK(launch_real_to_cplx(bz_bar, a->tmp, (int64_t)ng, h->s));
-        CK(forward_fft(h, a->tmp, a->js));
+        CK(fft64_forward(a, a->tmp, a->js));
         // the newest A: the BDF ring slot of the last level, else the A role (CDF-2: 4, 6;
         // DIRK: 2, 4)
         double2* sax = a->kind == K_BDF ? hist_slot(a, 1, a->nsteps)
@@ -398,9 +457,15 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
                 // the segment's particle states from its checkpoint and the recorded fields
                 for (int s = c0; s < c1; ++s) {
                     const int j = s - c0;
-                    const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
-                    CK(launch_replay_step(h->geom, s0, a->rec + (size_t)j * 8 * np,
-                                          a->recf + rec_slot(a, s) * kRec * np, (int64_t)np, h->s));
+                    const void* s0 = j == 0 ? a->ck[c].state
+                                            : (char*)a->rec + (size_t)(j - 1) * state_bytes(a);
+                    void* s1 = (char*)a->rec + (size_t)j * state_bytes(a);
+                    const double* rf = a->recf + rec_slot(a, s) * kRec * np;
+                    CK(by_prec(h, [&](auto t) {
+                        using T = decltype(t);
+                        return launch_replay_step<T>(h->geom, (const T*)s0, (T*)s1, rf,
+                                                     (int64_t)np, h->s);
+                    }));
                 }
             } else {
                 pic_status st = restore_checkpoint(a, a->ck[c]);
@@ -414,21 +479,26 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
         }
         for (int s = c1 - 1; s >= c0; --s) {
             const int j = s - c0;
-            const double* s0 = j == 0 ? a->ck[c].state : a->rec + (size_t)(j - 1) * 8 * np;
-            const double* s1 = a->rec + (size_t)j * 8 * np;
+            const void* s0 = j == 0 ? a->ck[c].state
+                                    : (char*)a->rec + (size_t)(j - 1) * state_bytes(a);
+            const void* s1 = (char*)a->rec + (size_t)j * state_bytes(a);
             pic_status st = backward_step(a, s, s0, s1, a->recf + rec_slot(a, s) * kRec * np,
-                                          a->recg + rec_slot(a, s) * 4 * ng);
+                                          (char*)a->recg + rec_slot(a, s) * 4 * ng * 2 * a->rsz);
             if (st != PIC_OK) return st;
         }
     }
-    const double* x0 = a->ck[0].state;
-    CK(launch_adj_init(h->p, h->geom, h->push, x0, x0 + np, x0 + 4 * np, x0 + 5 * np, a->e0,
-                       adjoint_arrays(a), dvx0, dvy0, dpx0, dpy0, (int64_t)np, h->err, h->s));
+    CK(by_prec(h, [&](auto t) {
+        using T = decltype(t);
+        const T* x0 = (const T*)a->ck[0].state;
+        return launch_adj_init<T>(h->p, h->geom, h->push, x0, x0 + np, x0 + 4 * np, x0 + 5 * np,
+                                  a->e0, adjoint_arrays<T>(a), dvx0, dvy0, dpx0, dpy0,
+                                  (int64_t)np, h->err, h->s);
+    }));
     // put the handle back at the end of the forward run
     pic_status st = restore_checkpoint(a, a->ck[a->nseg]);
     if (st != PIC_OK) return st;
     CK(cudaMemcpyAsync(h->J, a->final_j, ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
-    CK(cudaMemcpyAsync(h->G, a->final_g, 4 * ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->G, a->final_g, 4 * ng * 2 * a->rsz, cudaMemcpyDeviceToDevice, h->s));
     return check_device_error(h);
 }
 

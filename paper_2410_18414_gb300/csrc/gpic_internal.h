@@ -316,9 +316,11 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
 //
 // Adjoints of the eight particle arrays of one state: x, y, Px, Py, v^n (vx, vy) and
 // v^{n-1} (vxo, vyo).
-struct AdjParticles {
-    double *x, *y, *px, *py, *vx, *vy, *vxo, *vyo;
+template <typename T>
+struct AdjParticlesT {
+    T *x, *y, *px, *py, *vx, *vy, *vxo, *vyo;
 };
+using AdjParticles = AdjParticlesT<double>;
 // Reverse BDF-k field step: the history adjoints, slot of level d (time n+1-d) for
 // d = 0..2k-1 (rho: d = 0..k-1); level 0 is read first and rewritten with the new
 // oldest level, which shares its slot.
@@ -332,16 +334,21 @@ struct AdjModeParams {
     double2* ay[2 * kMaxBdf];
     double2* rho[kMaxBdf];
 };
+// The reverse particle kernels run in the forward's storage type T (double: the plain
+// path; float: the FP32 form); the field adjoints they add (Fb) and the current adjoint
+// they read (Jb) are FP64 in both.
+//
 // Reverse push + gather of one step: reads x^{n+1}, P^{n+1} (state n+1), v^n, v^{n-1}
-// (state n), the step's record (gf: the gathered A and grad A at 4 n .. 10 n, see
-// launch_gather_push) and the step's gather fields F ([node][4]); updates the particle adjoints and adds the eight
-// field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
+// (state n), the step's record (gf: the gathered A and grad A at 4 n .. 10 n, FP64, see
+// launch_gather_push) and the step's gather fields F ([node][4] complex of T); updates the
+// particle adjoints and adds the eight field adjoints into Fb (four planes [k][node] of
+// (f_2k, f_2k+1)).
+template <typename T>
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
-                                   const double* x1, const double* y1, const double* px1,
-                                   const double* py1, const double* vx, const double* vy,
-                                   const double* vxo, const double* vyo, const double* gf,
-                                   const double2* F, AdjParticles ab, double2* Fb, int64_t n,
-                                   unsigned int* err, cudaStream_t s);
+                                   const T* x1, const T* y1, const T* px1, const T* py1,
+                                   const T* vx, const T* vy, const T* vxo, const T* vyo,
+                                   const double* gf, const void* F, AdjParticlesT<T> ab,
+                                   double2* Fb, int64_t n, unsigned int* err, cudaStream_t s);
 // Reverse field solve per mode of the stepper `kind` (a StepperKind: ap, cp or dp used,
 // their pointers the history adjoints): Zb = forward transforms of the four Fb planes;
 // writes the packed adjoint current spectrum Js (unnormalised inverse transform -> mesh).
@@ -358,32 +365,38 @@ cudaError_t launch_adj_columns(const ModeCommon& mc, int kind, const AdjModePara
                                double2* Js, const FftDesc& fd, const double2* tw,
                                cudaStream_t s);
 // Reverse deposit + move: gathers the mesh current adjoint Jb ([node] (jx, jy)) at x^{n+1}.
-cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const double* x1,
-                                    const double* y1, const double* vx, const double* vy,
-                                    const double2* Jb, AdjParticles ab, int64_t n,
-                                    unsigned int* err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_deposit_move(int p, const ParticleGeom& g, const T* x1, const T* y1,
+                                    const T* vx, const T* vy, const double2* Jb,
+                                    AdjParticlesT<T> ab, int64_t n, unsigned int* err,
+                                    cudaStream_t s);
 // Objective seed sum bzb B_z at the final level, from zs = DFT(bzb).
 cudaError_t launch_adj_seed(const ModeCommon& mc, const double2* zs, double2* ax, double2* ay,
                             cudaStream_t s);
 // (Ex + i Ey)/(nx ny) of E = -grad phi (for the mesh E^0 by an inverse transform).
 cudaError_t launch_adj_e0(const ModeCommon& mc, const double2* phi, double2* out, cudaStream_t s);
 // t = 0 reverse: gradients with respect to v^0 and P^0 (any output may be NULL).
-cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const double* x0,
-                            const double* y0, const double* vx0, const double* vy0,
-                            const double2* E, AdjParticles ab, double* gvx, double* gvy,
-                            double* gpx, double* gpy, int64_t n, unsigned int* err,
-                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_init(int p, const ParticleGeom& g, const PushParams& pp, const T* x0,
+                            const T* y0, const T* vx0, const T* vy0, const double2* E,
+                            AdjParticlesT<T> ab, double* gvx, double* gvy, double* gpx,
+                            double* gpy, int64_t n, unsigned int* err, cudaStream_t s);
 cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cudaStream_t s);
-// Replay of one FP64 step's particle update from its record: state s0 -> state s1 (eight
-// arrays of n each), bit for bit the step's own.
-cudaError_t launch_replay_step(const ParticleGeom& g, const double* s0, double* s1,
-                               const double* rec, int64_t n, cudaStream_t s);
-// Eight FP64 arrays of n values <-> one contiguous block of 8 n (array k at k n).
-struct Ptr8 {
-    const double* p[8];
+// Replay of one step's particle update from its record (FP64 values): state s0 -> state s1
+// (eight arrays of n each, storage type T), bit for bit the step's own.
+template <typename T>
+cudaError_t launch_replay_step(const ParticleGeom& g, const T* s0, T* s1, const double* rec,
+                               int64_t n, cudaStream_t s);
+// Eight arrays of n values <-> one contiguous block of 8 n (array k at k n).
+template <typename T>
+struct Ptr8T {
+    const T* p[8];
 };
-cudaError_t launch_pack8(Ptr8 src, double* dst, int64_t n, cudaStream_t s);
-cudaError_t launch_unpack8(const double* src, Ptr8 dst, int64_t n, cudaStream_t s);
+using Ptr8 = Ptr8T<double>;
+template <typename T>
+cudaError_t launch_pack8(Ptr8T<T> src, T* dst, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack8(const T* src, Ptr8T<T> dst, int64_t n, cudaStream_t s);
 
 // Device error word bits.
 enum ErrBits { ERR_NONFINITE = 1u, ERR_OVERFLOW = 2u, ERR_TIMEOUT = 4u };

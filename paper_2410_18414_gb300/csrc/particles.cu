@@ -1281,12 +1281,17 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_replay_step(const ParticleGeom& g, const double* s0, double* s1,
-                               const double* rec, int64_t n, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_replay_step(const ParticleGeom& g, const T* s0, T* s1, const double* rec,
+                               int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_replay_step<double><<<blocks_for(n), kThreads, 0, s>>>(typed<double>(g), s0, s1, rec, n);
+    k_replay_step<T><<<blocks_for(n), kThreads, 0, s>>>(typed<T>(g), s0, s1, rec, n);
     return cudaGetLastError();
 }
+template cudaError_t launch_replay_step<double>(const ParticleGeom&, const double*, double*,
+                                                const double*, int64_t, cudaStream_t);
+template cudaError_t launch_replay_step<float>(const ParticleGeom&, const float*, float*,
+                                               const double*, int64_t, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_deposit_z(int p, const ParticleGeom& g, const T* x, const T* y, const T* vz,

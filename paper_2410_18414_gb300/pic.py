@@ -383,8 +383,9 @@ class Ensemble:
 
 
 class Adjoint:
-    """Discrete adjoint of the next `nsteps` steps of a fresh FP64 Simulation (any stepper)
-    (pic_adjoint_*): run forward() once, then backward(...) for the gradient of
+    """Discrete adjoint of the next `nsteps` steps of a fresh unsorted Simulation (either
+    precision, any stepper) (pic_adjoint_*): run forward() once, then backward(...) for the
+    gradient of
     J = sum bz_bar B_z + sum (px_bar Px + py_bar Py) of the final state with respect to
     v^0 and, with P^0 = gamma m v^0 independent, to P^0.  Seeds and results are CUDA
     float64 tensors (the library reads and writes device memory)."""

@@ -1,4 +1,4 @@
-"""GPU checks of the discrete adjoint (pic_adjoint_*) of the FP64 run.
+"""GPU checks of the discrete adjoint (pic_adjoint_*) of the FP64 run and the FP32 form.
 
 - Against the oracle's adjoint (oracle.adjoint, pinned on CPU by finite differences
   and transpose identities): small grids, several spline orders and BDF orders, both
@@ -22,6 +22,14 @@
   1e-6 |g| + sigma W_B / h with sigma = 4e-12 (about 1e-4 of a typical component).
 - The handle is left at the end of the forward run; torch.autograd returns the same
   gradient as the library call.
+- The FP32 form's adjoint (unsorted handles) against the oracle's FP64 gradient, for
+  BDF-1/2, CDF-2 and DIRK-2, both seeds and both record modes: measured <= 1.4e-6
+  relative on GB300, bound 1e-5; its two record modes agree to 1e-6.  On the 128 x 128
+  Weibel run (200 steps) against the FP64 adjoint: 1.7e-5 over the whole gradient and
+  1.0e-6 along the drift (bounds 2e-4 and 1e-5), the difference of the two trajectories;
+  and against central differences of the FP32 run itself (h = 1e-3, the truncation
+  error removed by the same difference of the FP64 run, allowance 4e-6 W_B / h for the
+  FP32 run's noise floor).
 """
 import numpy as np
 import pytest
@@ -52,7 +60,8 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-def _case(p, k, nx, ny, n, seed, stepper="bdf", dirk=None, cdf_form="implicit"):
+def _case(p, k, nx, ny, n, seed, stepper="bdf", dirk=None, cdf_form="implicit",
+          precision=None):
     rng = np.random.default_rng(seed)
     lx, ly = 1.0, 0.8
     x = rng.uniform(0, lx, n)
@@ -64,7 +73,7 @@ def _case(p, k, nx, ny, n, seed, stepper="bdf", dirk=None, cdf_form="implicit"):
     w = lx * ly / n
     name = stepper if cdf_form == "implicit" else f"cdf2_{cdf_form}"
     cfg = pic.make_config(nx, ny, lx, ly, dt, p=p, stepper=name, bdf_order=k, dirk=dirk,
-                          weight=w)
+                          weight=w, precision=pic.FP64 if precision is None else precision)
     ocfg = opic.Config(nx=nx, ny=ny, lx=lx, ly=ly, dt=dt, p=p, stepper=stepper, bdf_order=k,
                        w=w, dirk=dirk, cdf_form=cdf_form)
     return cfg, ocfg, x, y, vx, vy
@@ -183,7 +192,7 @@ def test_handle_left_at_end_of_forward_run(device, kw, mode):
 
 def test_adjoint_rejects_unsupported_handles(device):
     cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 512, seed=5)
-    for kw in (dict(precision=pic.FP32_FIX64), dict(sort_interval=4),
+    for kw in (dict(precision=pic.FP32_FIX64, sort_interval=4), dict(sort_interval=4),
                dict(charge=pic.CHARGE_DEPOSIT)):
         args = dict(p=3, stepper="bdf", bdf_order=2, weight=cfg.weight)
         args.update(kw)
@@ -197,6 +206,59 @@ def test_adjoint_rejects_unsupported_handles(device):
         with pytest.raises(pic.PicError) as e:
             pic.Adjoint(sim, 5)
         assert e.value.status == 7
+
+
+# The FP32 form's adjoint (the step's adjoint in exact arithmetic along the FP32 trajectory,
+# particle adjoints in FP32, field adjoints and the reverse field solve in FP64) against the
+# oracle's FP64 gradient: the difference is the FP32 trajectory's own departure from the
+# FP64 one plus FP32 rounding in the reverse particle arithmetic.
+FP32_CASES = [
+    ("p2-bdf1", dict(p=2, k=1, nx=24, ny=16, n=3000, seed=2), {}, 6, 3, "replay"),
+    ("p3-bdf2", dict(p=3, k=2, nx=32, ny=32, n=4096, seed=3), {}, 6, 4, "recompute"),
+    ("p3-cdf2", dict(p=3, k=1, nx=32, ny=24, n=4096, seed=4), dict(stepper="cdf2"), 5, 5,
+     "replay"),
+    ("p4-dirk2", dict(p=4, k=1, nx=16, ny=24, n=2000, seed=5),
+     dict(stepper="dirk", dirk=osteps.DIRK2_QIN_ZHANG), 4, 2, "replay"),
+]
+FP32_GRAD_TOL = 1e-5
+
+
+@pytest.mark.parametrize("name,case,kw,nsteps,K,mode", FP32_CASES,
+                         ids=[c[0] for c in FP32_CASES])
+def test_fp32_form_adjoint_matches_oracle(device, name, case, kw, nsteps, K, mode):
+    cfg, ocfg, x, y, vx, vy = _case(**case, **kw, precision=pic.FP32_FIX64)
+    tape = oadj.record(ocfg, x, y, vx, vy, nsteps)
+    expect = oadj.gradient(tape)
+    wb, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, mode=mode)
+    ewb = oadj.magnetic_energy(ocfg, tape.final)
+    print(f"{name}: W_B {wb / ewb - 1:.2e}", end="")
+    assert abs(wb / ewb - 1.0) <= 1e-5
+    # W_B and a final-momentum objective
+    rng = np.random.default_rng(30 + case["p"])
+    pb = (rng.standard_normal(case["n"]), rng.standard_normal(case["n"]))
+    for obj in ("wb", "p"):
+        if obj == "p":
+            expect = oadj.gradient(tape, px_bar=pb[0], py_bar=pb[1])
+            _, got = _gpu_gradient(device, cfg, x, y, vx, vy, nsteps, K, pb=pb, mode=mode)
+        for key, ref in (("vx", expect["v0"][0]), ("vy", expect["v0"][1]),
+                         ("px", expect["p0"][0]), ("py", expect["p0"][1])):
+            r = rel(got[key], ref)
+            print(f"  {obj}:{key} {r:.2e}", end="")
+            assert r <= FP32_GRAD_TOL, (obj, key, r)
+    print()
+
+
+def test_fp32_form_adjoint_modes_agree(device):
+    # replay (recorded P, v and gathered fields) and recompute (the segment's FP32 steps
+    # re-run; the fixed-point current is bit-exact) reverse the same trajectory: they differ
+    # only by the order of the FP64 field-adjoint atomics
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=7, precision=pic.FP32_FIX64)
+    _, a = _gpu_gradient(device, cfg, x, y, vx, vy, 9, 4, mode="replay")
+    _, b = _gpu_gradient(device, cfg, x, y, vx, vy, 9, 4, mode="recompute")
+    _, c = _gpu_gradient(device, cfg, x, y, vx, vy, 9, 9, mode="replay")
+    for key in a:
+        assert rel(a[key], b[key]) <= 1e-6, key
+        assert rel(a[key], c[key]) <= 1e-6, key
 
 
 def test_autograd_matches_library(device):
@@ -266,6 +328,62 @@ def test_c5_direction_gradients_match_finite_differences(device, c5):
         fd = (_wb(device, wl, cfg, wl.vx + h * d[0], wl.vy + h * d[1])
               - _wb(device, wl, cfg, wl.vx - h * d[0], wl.vy - h * d[1])) / (2 * h)
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+@pytest.fixture(scope="module")
+def c5_32(device, c5):
+    wl = c5[0]
+    cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, stepper="bdf",
+                          bdf_order=2, weight=wl.weight, precision=pic.FP32_FIX64)
+    wb32, g32 = _gpu_gradient(device, cfg, wl.x, wl.y, wl.vx, wl.vy, wl.nsteps, 20)
+    return cfg, wb32, g32
+
+
+def test_c5_fp32_form_adjoint_matches_fp64(device, c5, c5_32):
+    # the FP32 form's adjoint of the same 200-step run against the FP64 adjoint: the whole
+    # gradient and its projection on the drift direction
+    wl, _, wb, g = c5
+    _, wb32, g32 = c5_32
+    sgn = np.where(np.arange(wl.n) % 2 == 0, 1.0, -1.0)
+    d64, d32 = float(np.sum(sgn * g["py"])), float(np.sum(sgn * g32["py"]))
+    r = {key: rel(g32[key], g[key]) for key in g}
+    print(f"W_B {wb32 / wb - 1:.2e} drift {d32 / d64 - 1:.2e} " +
+          " ".join(f"{k} {v:.2e}" for k, v in r.items()))
+    assert abs(wb32 / wb - 1.0) <= 1e-5
+    assert abs(d32 / d64 - 1.0) <= 1e-5
+    for key, v in r.items():
+        assert v <= 2e-4, (key, v)
+
+
+def test_c5_fp32_form_finite_differences(device, c5, c5_32):
+    # Central differences of the FP32 form's own forward run against its adjoint.  The FP32
+    # run's W_B carries a noise floor sigma relative (FP32 roundoff through 200 steps of the
+    # instability; from the spread of central differences over h = 1e-6 .. 1e-3: 1e-7 to
+    # 3e-7 along the drift, about 1e-6 along a random direction, which moves every
+    # particle's roundoff), so h is 1e-3, and the truncation error of that h is taken out by
+    # the same difference of the FP64 run: (fd32 - fd64) must match (adj32 - adj64) within
+    # the noise allowance 4e-6 W_B / h (2.3e-9; measured 1.3e-10 along the drift and
+    # 5.7e-10 along the direction).
+    wl, cfg64, wb, g = c5
+    cfg32, wb32, g32 = c5_32
+    h = 1e-3
+    sgn = np.where(np.arange(wl.n) % 2 == 0, 1.0, -1.0)
+    gd = (1.0 / np.sqrt(0.75)) ** 3
+    d = np.random.default_rng(13).standard_normal((2, wl.n))
+    probes = [
+        (lambda s: _v_of_vd(wl, 0.5 + s * h), lambda gr: gd * float(np.sum(sgn * gr["py"]))),
+        (lambda s: (wl.vx + s * h * d[0], wl.vy + s * h * d[1]),
+         lambda gr: float(np.dot(gr["vx"], d[0]) + np.dot(gr["vy"], d[1]))),
+    ]
+    for v_at, proj in probes:
+        fd = {}
+        for name, cfg in (("32", cfg32), ("64", cfg64)):
+            fd[name] = (_wb(device, wl, cfg, *v_at(1.0)) - _wb(device, wl, cfg, *v_at(-1.0))) / (2 * h)
+        a32, a64 = proj(g32), proj(g)
+        err = abs((fd["32"] - fd["64"]) - (a32 - a64))
+        print(f"fd32 {fd['32']:.8e} adj32 {a32:.8e} fd64 {fd['64']:.8e} adj64 {a64:.8e} "
+              f"residual {err:.2e} (sigma {err * h / wb32:.1e})")
+        assert err <= 4e-6 * wb32 / h, (fd, a32, a64)
 
 
 def test_c5_momentum_components_match_finite_differences(device, c5):
