@@ -545,7 +545,8 @@ def run_ensemble(a):
 
 def ensemble_line(ranks, steps, warmup):
     """256 independent Weibel runs (grid sizes, densities and drifts drawn per run; FP32
-    form, BDF-2, cubic), sort intervals from the autotuner, advanced together by one
+    form, BDF-2, cubic), tile widths and sort intervals from the autotuner, advanced
+    together by one
     CUDA-graph launch per period (pic_ensemble_step); the same runs stepped on their own
     streams without the graph are timed beside it.  Returns rank 0's line (None on the
     other ranks)."""
@@ -555,16 +556,16 @@ def ensemble_line(ranks, steps, warmup):
     pic.load_library()
     specs = workloads.ensemble_specs(seed0=1000 + 256 * rank)
     t0 = time.perf_counter()
-    sorts = [autotune.tune_sort_interval(sp["n"], sp["ppc"]) for sp in specs]
+    tuned = [autotune.tune(sp["n"], sp["ppc"])[:2] for sp in specs]
     tune_s = time.perf_counter() - t0
 
     def build():
         sims, streams = [], []
-        for sp, si in zip(specs, sorts):
+        for sp, (ti, si) in zip(specs, tuned):
             wl = workloads.ensemble_run(sp)
             cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf",
                                   bdf_order=2, weight=wl.weight, precision=pic.FP32_FIX64,
-                                  sort_interval=si)
+                                  sort_interval=si, tile=ti)
             st = torch.cuda.Stream()
             sims.append(pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=st.cuda_stream))
             streams.append(st)
@@ -627,8 +628,8 @@ def ensemble_line(ranks, steps, warmup):
         return None
     value = whole_job_rate(n_total, world, steps, ms)
     hist = {}
-    for si in sorts:
-        hist[str(si)] = hist.get(str(si), 0) + 1
+    for ti, si in tuned:
+        hist[f"T{ti}_S{si}"] = hist.get(f"T{ti}_S{si}", 0) + 1
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
@@ -636,7 +637,7 @@ def ensemble_line(ranks, steps, warmup):
         "config": {"workload": "ensemble_256_weibel_cubic_bdf2", "runs": len(specs),
                    "particles_total": n_total, "grid_sizes": sorted({sp["n"] for sp in specs}),
                    "ppc_range": [min(sp["ppc"] for sp in specs), max(sp["ppc"] for sp in specs)],
-                   "sort_intervals": hist, "period": P, "graph_steps": full,
+                   "tile_and_sort_interval": hist, "period": P, "graph_steps": full,
                    "steps_outside_graph": rest, "form": "fp32_fix64",
                    "l2": "no flush: the ensemble's particle state (about 7 GB) is far larger "
                          "than L2", "parallelism": "single"},
@@ -650,6 +651,7 @@ def ensemble_line(ranks, steps, warmup):
         "no_graph": {"ms_per_step": ms_plain / steps,
                      "value": whole_job_rate(n_total, world, steps, ms_plain),
                      "how": "each run's steps enqueued on its own stream, no graph"},
+        "ps_per_particle_step": ms * 1e9 / (n_total * steps),
         "autotune_s": tune_s, "capture_s": capture_s,
         "cpu_baseline": None, "e2e": None,
         "gpu_launches": None, "clocks": clk,

@@ -116,7 +116,10 @@ typedef struct {
                                 carries a species index into species_q/m/w (section 2.1
                                 sums the densities over species; section 2.2 writes the
                                 equations with each particle's own charge and mass)        */
-    int32_t reserved[5];     /* must be zero                                                */
+    int32_t tile;            /* tile width T (cells) of the sorted form's tiles: 4, 8 or 16;
+                                0 = from the mean particle density (about 4096 particles a
+                                tile); only used with sort_interval > 0                    */
+    int32_t reserved[4];     /* must be zero                                                */
     double species_q[4];     /* charge, mass and macro-particle weight of each species     */
     double species_m[4];
     double species_w[4];
@@ -165,7 +168,9 @@ typedef struct {
  * step back in E^0 = -grad phi^0, and every history level at its t = 0 value.
  * On success *out receives the handle.  The stream must outlive the handle.
  * 2D-3V and species tables run on the unsorted kernels: with sort_interval > 0 they are
- * PIC_ERR_UNSUPPORTED. */
+ * PIC_ERR_UNSUPPORTED.  PIC_ERR_INVALID_ARG for a field out of its stated range (tile not
+ * 0, 4, 8 or 16; reserved fields not zero; ...).  A tile wider than half the grid is
+ * narrowed to fit. */
 pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,
                     pic_handle **out);
 

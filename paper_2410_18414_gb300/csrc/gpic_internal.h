@@ -66,8 +66,9 @@ struct BdfParams {
     int k;
     double a[kMaxBdf + 1];
     double C[2 * kMaxBdf + 1];
-    double g;    // (c beta dt)^2
-    double bdt;  // beta dt
+    double g;       // (c beta dt)^2
+    double bdt;     // beta dt
+    double inv_a0;  // 1 / a[0] (host-computed, so no mode divides)
     // history, newest first: hist[d-1] is level n+1-d
     void* phi[2 * kMaxBdf];
     void* ax[2 * kMaxBdf];

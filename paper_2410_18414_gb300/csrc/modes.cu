@@ -187,25 +187,40 @@ __device__ __forceinline__ zd deposited_rho(const ModeCommon& mc, const ModeIn& 
     return zscale(mc.jscale, zload(reinterpret_cast<const C*>(mc.zq) + m.idx));
 }
 
+// The BDF order a kernel is compiled for: K in 1..kMaxBdf fixes it (loops unroll and every
+// history load of a mode is issued at once), K = 0 takes it from the parameters.
+template <int K> struct BdfOrder {
+    BdfParams p;
+};
+template <int K>
+__device__ __forceinline__ int bdf_k(const BdfParams& bp) {
+    return K > 0 ? K : bp.k;
+}
+
 // The BDF-k recurrences of one mode: continuity and the phi wave update; the A wave
 // updates.
+template <int K = 0>
 __device__ __forceinline__ void bdf_rho_phi(const ModeCommon& mc, const BdfParams& bp,
                                             const ModeIn& m, zd& rho_new, zd& phi_new,
                                             const zd* rho_dep = nullptr) {
-    const int idx = m.idx, k = bp.k;
+    const int idx = m.idx, k = bdf_k<K>(bp);
     rho_new = zscale(-bp.bdt, m.divj);
+#pragma unroll
     for (int d = 1; d <= k; ++d) rho_new = zfms(rho_new, bp.a[d], hload(bp.rho[d - 1], idx));
-    rho_new = zscale(1.0 / bp.a[0], rho_new);
+    rho_new = zscale(bp.inv_a0, rho_new);
     if (rho_dep) rho_new = *rho_dep;  // the naive update: the deposited charge
     zd sphi = zscale(bp.g / mc.eps0, rho_new);
+#pragma unroll
     for (int d = 1; d <= 2 * k; ++d) sphi = zfms(sphi, bp.C[d], hload(bp.phi[d - 1], idx));
     phi_new = zscale(mc.invd[idx], sphi);  // 1/(C_0 + g K)
 }
+template <int K = 0>
 __device__ __forceinline__ void bdf_a(const ModeCommon& mc, const BdfParams& bp, const ModeIn& m,
                                       zd& ax_new, zd& ay_new) {
-    const int idx = m.idx, k = bp.k;
+    const int idx = m.idx, k = bdf_k<K>(bp);
     zd sax = zscale(bp.g * mc.mu0, m.jx);
     zd say = zscale(bp.g * mc.mu0, m.jy);
+#pragma unroll
     for (int d = 1; d <= 2 * k; ++d) {
         sax = zfms(sax, bp.C[d], hload(bp.ax[d - 1], idx));
         say = zfms(say, bp.C[d], hload(bp.ay[d - 1], idx));
@@ -215,20 +230,36 @@ __device__ __forceinline__ void bdf_a(const ModeCommon& mc, const BdfParams& bp,
     ay_new = zscale(inv, say);
 }
 
+template <int K, typename C>
+__device__ __forceinline__ void bdf_mode_update(const ModeCommon& mc, const BdfParams& bp,
+                                                const ModeIn& m, double* acc, C* epk, C* out);
+
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfParams& bp,
                                             const ModeIn& m, double* acc, C* epk, C* out) {
-    const int idx = m.idx, k = bp.k;
+    bdf_mode_update<0>(mc, bp, m, acc, epk, out);
+}
+template <int K, typename C>
+__device__ __forceinline__ void mode_update(const ModeCommon& mc, const BdfOrder<K>& bo,
+                                            const ModeIn& m, double* acc, C* epk, C* out) {
+    bdf_mode_update<K>(mc, bo.p, m, acc, epk, out);
+}
+
+template <int K, typename C>
+__device__ __forceinline__ void bdf_mode_update(const ModeCommon& mc, const BdfParams& bp,
+                                                const ModeIn& m, double* acc, C* epk, C* out) {
+    const int idx = m.idx, k = bdf_k<K>(bp);
     zd rho_new, phi_new, ax_new, ay_new;
     zd rho_dep;
     if (mc.zq) rho_dep = deposited_rho<C>(mc, m);
-    bdf_rho_phi(mc, bp, m, rho_new, phi_new, mc.zq ? &rho_dep : nullptr);
-    bdf_a(mc, bp, m, ax_new, ay_new);
+    bdf_rho_phi<K>(mc, bp, m, rho_new, phi_new, mc.zq ? &rho_dep : nullptr);
+    bdf_a<K>(mc, bp, m, ax_new, ay_new);
     if (mc.diag) {
         // section 3.2: gauge eps_1, continuity eps_2, and Gauss with
         // E^{n+1} = -grad phi^{n+1} - (1/(beta dt)) sum_j a_j A^{n+1-j}
         zd dphi = bp.a[0] * phi_new, dax = bp.a[0] * ax_new, day = bp.a[0] * ay_new;
         zd drho = bp.a[0] * rho_new;
+#pragma unroll
         for (int d = 1; d <= k; ++d) {
             dphi = dphi + bp.a[d] * hload(bp.phi[d - 1], idx);
             dax = dax + bp.a[d] * hload(bp.ax[d - 1], idx);
@@ -445,6 +476,11 @@ __device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const Bdf
         }
         for (int d = 0; d < bp.k; ++d) prefetch_l2(bp.rho[d], idx);
     }
+}
+template <int K>
+__device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const BdfOrder<K>& bo,
+                                                 int j) {
+    prefetch_history(mc, bo.p, j);
 }
 __device__ __forceinline__ void prefetch_history(const ModeCommon& mc, const CdfParams& cp, int j) {
     const void* const arr[10] = {cp.phi, cp.phi_prev, cp.rho, cp.rho_prev, cp.ax,
@@ -684,7 +720,17 @@ cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams
                                  void* f4, void* e, double* diag, const FftDesc& fd,
                                  const void* tw, cudaStream_t s) {
     using C = cplx_t<T>;
-    if (kind == K_BDF) return launch_columns_generic<C>(mc, bp, z, f4, e, diag, fd, tw, s);
+    if (kind == K_BDF) {
+        static_assert(kMaxBdf == 6, "one column kernel per BDF order");
+        switch (bp.k) {
+            case 1: return launch_columns_generic<C>(mc, BdfOrder<1>{bp}, z, f4, e, diag, fd, tw, s);
+            case 2: return launch_columns_generic<C>(mc, BdfOrder<2>{bp}, z, f4, e, diag, fd, tw, s);
+            case 3: return launch_columns_generic<C>(mc, BdfOrder<3>{bp}, z, f4, e, diag, fd, tw, s);
+            case 4: return launch_columns_generic<C>(mc, BdfOrder<4>{bp}, z, f4, e, diag, fd, tw, s);
+            case 5: return launch_columns_generic<C>(mc, BdfOrder<5>{bp}, z, f4, e, diag, fd, tw, s);
+            default: return launch_columns_generic<C>(mc, BdfOrder<6>{bp}, z, f4, e, diag, fd, tw, s);
+        }
+    }
     if (kind == K_CDF2) return launch_columns_generic<C>(mc, cp, z, f4, e, diag, fd, tw, s);
     return launch_columns_generic<C>(mc, dp, z, f4, e, diag, fd, tw, s);
 }

@@ -129,8 +129,10 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 pic_status validate(const pic_config* c, const pic_particles_in* in) {
     pic_handle* h = nullptr;
     if (!c || !in) return fail(h, PIC_ERR_INVALID_ARG, "cfg and init must not be NULL");
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c->reserved[i] != 0) return fail(h, PIC_ERR_INVALID_ARG, "reserved fields must be 0");
+    if (c->tile != 0 && c->tile != 4 && c->tile != 8 && c->tile != 16)
+        return fail(h, PIC_ERR_INVALID_ARG, "tile must be 0, 4, 8 or 16");
     if (c->vdim != 0 && c->vdim != 2 && c->vdim != 3)
         return fail(h, PIC_ERR_INVALID_ARG, "vdim must be 0, 2 or 3");
     if (c->nspecies < 0 || c->nspecies > kMaxSpecies)
@@ -358,6 +360,7 @@ pic_status alloc_state(pic_handle* h) {
             h->bdf.C[d] = s;
         }
         h->bdf.bdt = beta * c.dt;
+        h->bdf.inv_a0 = 1.0 / h->bdf.a[0];
         h->bdf.g = (c.c * beta * c.dt) * (c.c * beta * c.dt);
     } else if (c.stepper == PIC_STEPPER_CDF2) {
         void** slots[] = {&h->cdf.phi, &h->cdf.phi_prev, &h->cdf.rho, &h->cdf.rho_prev,
@@ -585,9 +588,13 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         tg.ny = cfg->ny;
         const double ppc = (double)std::max<int64_t>(h->n, 1) / ((double)cfg->nx * cfg->ny);
         tg.t = 4;
-        while (tg.t < 16 && (double)(2 * tg.t) * (2 * tg.t) * ppc <= 8192.0 &&
-               2 * tg.t <= std::min(cfg->nx, cfg->ny))
-            tg.t *= 2;
+        if (cfg->tile > 0) {  // the caller's (an autotuner's) choice, within the grid
+            while (tg.t < cfg->tile && 2 * tg.t <= std::min(cfg->nx, cfg->ny)) tg.t *= 2;
+        } else {
+            while (tg.t < 16 && (double)(2 * tg.t) * (2 * tg.t) * ppc <= 8192.0 &&
+                   2 * tg.t <= std::min(cfg->nx, cfg->ny))
+                tg.t *= 2;
+        }
         tg.ntx = (cfg->nx + tg.t - 1) / tg.t;
         tg.nty = (cfg->ny + tg.t - 1) / tg.t;
         const double drift = cfg->c * cfg->dt * cfg->sort_interval / std::fmin(dx, dy);

@@ -26,7 +26,7 @@ namespace {
 struct StateHeader {
     char magic[8];
     int32_t nx, ny, p, stepper, cdf_form, bdf_order, dirk_stages, precision;
-    int32_t sort_interval, vdim, nspecies, charge;
+    int32_t sort_interval, vdim, nspecies, charge, tile, pad;
     int64_t n, step;
     int32_t vcur, head, head_r, stepped;
     uint64_t payload;
@@ -34,7 +34,7 @@ struct StateHeader {
     double dirk_a[16], dirk_b[4], dirk_c[4];
     double species_q[4], species_m[4], species_w[4];
 };
-constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '2'};
+constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '3'};
 
 struct Seg {
     void* p;
@@ -98,6 +98,7 @@ StateHeader header_of(pic_handle* h, uint64_t payload) {
     hd.vdim = h->vdim;
     hd.nspecies = h->spp.n;
     hd.charge = c.charge;
+    hd.tile = h->sorting ? h->tg.t : 0;  // the tiles the saved order and offsets belong to
     hd.n = h->n;
     hd.step = h->step;
     hd.vcur = h->vcur;
@@ -191,7 +192,8 @@ pic_status pic_load_state(pic_handle* h, const void* src, size_t size) {
                       hd.bdf_order == mine.bdf_order && hd.dirk_stages == mine.dirk_stages &&
                       hd.precision == mine.precision && hd.sort_interval == mine.sort_interval &&
                       hd.vdim == mine.vdim && hd.nspecies == mine.nspecies &&
-                      hd.charge == mine.charge && hd.n == mine.n && hd.payload == payload &&
+                      hd.charge == mine.charge && hd.tile == mine.tile && hd.n == mine.n &&
+                      hd.payload == payload &&
                       same_parameters(hd, mine);
     if (!same)
         return fail(h, PIC_ERR_INVALID_ARG,

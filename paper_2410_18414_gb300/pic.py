@@ -58,7 +58,7 @@ class PicConfig(ctypes.Structure):
         ("dirk_c", ctypes.c_double * 4),
         ("charge", ctypes.c_int32),
         ("vdim", ctypes.c_int32), ("nspecies", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
         ("species_q", ctypes.c_double * 4), ("species_m", ctypes.c_double * 4),
         ("species_w", ctypes.c_double * 4),
     ]
@@ -163,9 +163,10 @@ CHARGE_CONTINUITY, CHARGE_DEPOSIT = 0, 1
 
 def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, c=1.0, eps0=1.0,
                 q=-1.0, m=1.0, weight=1.0, precision=FP64, sort_interval=0,
-                charge=CHARGE_CONTINUITY, vdim=2, species=None):
+                charge=CHARGE_CONTINUITY, vdim=2, species=None, tile=0):
     """species: optional ((q, m, w), ...) per species (at most 4); particles then carry a
-    species index (Simulation(..., species=...))."""
+    species index (Simulation(..., species=...)).  tile: the sorted form's tile width T
+    (4, 8 or 16; 0 = chosen from the particle density)."""
     cfg = PicConfig()
     cfg.nx, cfg.ny, cfg.lx, cfg.ly, cfg.dt = nx, ny, lx, ly, dt
     cfg.spline_order = p
@@ -174,6 +175,7 @@ def make_config(nx, ny, lx, ly, dt, p=2, stepper="bdf", bdf_order=1, dirk=None, 
     cfg.c, cfg.eps0, cfg.q, cfg.m, cfg.weight = c, eps0, q, m, weight
     cfg.precision = precision
     cfg.sort_interval = sort_interval
+    cfg.tile = tile
     cfg.charge = charge
     cfg.vdim = vdim
     if species is not None:

@@ -84,7 +84,7 @@ def _bad(lib, **kw):
     dict(nx=7), dict(nx=10), dict(ny=2048), dict(nx=14), dict(p=5), dict(p=1), dict(dt=-1.0),
     dict(dt=2.0), dict(bdf_order=7), dict(bdf_order=0), dict(stepper=9), dict(lx=float("nan")),
     dict(stepper="dirk"),  # zero stages
-    dict(charge=2),
+    dict(charge=2), dict(tile=3), dict(tile=32), dict(tile=-4),
 ])
 def test_invalid_config_is_rejected_without_a_device(lib, kw):
     err = _bad(lib, **kw)

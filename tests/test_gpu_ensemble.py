@@ -144,13 +144,37 @@ def test_ensemble_rejects_misuse(torch_mod):
     r1.close()
 
 
-def test_autotuner_picks_a_candidate_and_caches(torch_mod):
+def test_autotuner_picks_the_fastest_pair_and_caches(torch_mod):
     from paper_2410_18414_gb300 import autotune
-    s = autotune.tune_sort_interval(32, 20)
-    assert s in autotune.CANDIDATES
+    t, s, ms = autotune.tune(32, 20)
+    # every tile up to half the grid with every sort interval was probed
+    assert set(ms) == {(a, b) for a in (4, 8, 16) for b in (1, 2, 4, 8, 16)}
+    assert (t, s) == min(ms, key=ms.get)
     assert autotune.density_class(20) == 16 and autotune.density_class(50) == 64
-    assert autotune._cache[(32, 16, 3, pic.FP32_FIX64)] == s
-    assert autotune.tune_sort_interval(32, 18) == s  # same key: from the cache
+    assert autotune._cache[(32, 16, 3, pic.FP32_FIX64)] == (t, s)
+    assert autotune.tune(32, 18) == (t, s, {})  # same key: from the cache
+    assert autotune.candidates(16) == [(a, b) for a in (4, 8) for b in (1, 2, 4, 8, 16)]
+
+
+def test_tile_width_changes_no_result(torch_mod):
+    # the sorted FP32 form sums its current exactly in integers, so the tiling (which
+    # regroups the sums) leaves every bit unchanged: tiles 4, 8, 16 and the derived one
+    torch = torch_mod
+    wl = workloads.weibel(64, 48, 24, 0.5, 0.01, 1021, 3)
+    out = []
+    for tile in (0, 4, 8, 16):
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf",
+                              bdf_order=2, weight=wl.weight, precision=pic.FP32_FIX64,
+                              sort_interval=4, tile=tile)
+        with pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy,
+                            stream=torch.cuda.Stream().cuda_stream) as sim:
+            sim.step(13)
+            out.append((sim.particles(), {f: sim.field(f) for f in ("jx", "jy", "phi", "ay")}))
+    for parts, fields in out[1:]:
+        for k in parts:
+            assert np.array_equal(parts[k], out[0][0][k]), k
+        for f in fields:
+            assert np.array_equal(fields[f], out[0][1][f]), f
 
 
 def test_ensemble_matches_the_oracle(torch_mod):

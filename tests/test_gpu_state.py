@@ -141,6 +141,25 @@ def test_load_refuses_other_fp64_parameters(device):
         s.close()
 
 
+def test_load_refuses_another_tile_width(device):
+    # the saved sort order and tile offsets belong to the tiles they were made for
+    a = _make_cfg(device, 3, precision=pic.FP32_FIX64, sort_interval=4, tile=4)
+    a.step(3)
+    state = a.save_state()
+    b = _make_cfg(device, 3, precision=pic.FP32_FIX64, sort_interval=4, tile=8)
+    with pytest.raises(pic.PicError) as e:
+        b.load_state(state)
+    assert e.value.status == 1
+    c = _make_cfg(device, 4, precision=pic.FP32_FIX64, sort_interval=4, tile=4)
+    c.load_state(state)
+    a.step(2)
+    c.step(2)
+    for k, v in a.particles().items():
+        assert np.array_equal(c.particles()[k], v), k
+    for s in (a, b, c):
+        s.close()
+
+
 def test_diagnostics_log_restarts_at_a_load(device):
     # Records logged before a load are not returned after it, so step numbers never repeat
     # or go backwards.
