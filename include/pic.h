@@ -200,8 +200,8 @@ pic_status pic_step(pic_handle *h, int32_t nsteps);
  * buffer rotations (history rings, velocity and current buffers, sort buffers: the
  * least common multiple of 2, the BDF ring lengths and twice each sort interval), so
  * every replay finds every buffer where the captured launches expect it.  The results
- * are those of pic_step on each run, bit for bit (the FP32 form; the FP64 path sums the
- * current with FP64 atomics in no fixed order, so its runs agree to roundoff).
+ * are those of pic_step on each run, bit for bit (both forms sum their deposits as
+ * integers, so the order of the additions does not matter).
  *
  * Not a step of the paper: a batching of its step (no counterpart there). */
 typedef struct pic_ensemble pic_ensemble; /* opaque, owned by the library */

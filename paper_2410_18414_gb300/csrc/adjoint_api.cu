@@ -46,7 +46,7 @@ struct pic_adjoint {
         int64_t step = 0;
     };
     std::vector<Ck> ck;
-    double2* final_j = nullptr;  // J of the last step (FP64, or int64 sums)
+    double2* final_j = nullptr;  // J of the last step (the handle's sums, jbytes)
     void* final_g = nullptr;     // gather fields of the last step (4 ng complex of T)
     void* rec = nullptr;         // K states
     void* recg = nullptr;        // K x 4 ng complex of T
@@ -348,7 +348,7 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
         if (e == cudaSuccess) e = aalloc(a, (void**)&c.hist, hbytes);
     }
     const size_t gfb = 4 * a->ng * 2 * a->rsz;  // one step's gather fields
-    if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_j, gb);
+    if (e == cudaSuccess) e = aalloc(a, (void**)&a->final_j, h->jbytes);
     if (e == cudaSuccess) e = aalloc(a, &a->final_g, gfb);
     if (e == cudaSuccess) e = aalloc(a, &a->rec, (size_t)a->K * sb);
     if (e == cudaSuccess) e = aalloc(a, &a->recg, nrec * gfb);
@@ -406,7 +406,7 @@ pic_status pic_adjoint_forward(pic_adjoint* a) {
     a->seg_held = replay ? -1 : a->nseg - 1;
     pic_status st = save_checkpoint(a, a->ck[a->nseg]);
     if (st != PIC_OK) return st;
-    CK(cudaMemcpyAsync(a->final_j, h->J, a->ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(a->final_j, h->J, h->jbytes, cudaMemcpyDeviceToDevice, h->s));
     CK(cudaMemcpyAsync(a->final_g, h->G, 4 * a->ng * 2 * a->rsz, cudaMemcpyDeviceToDevice,
                        h->s));
     return PIC_OK;
@@ -497,7 +497,7 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
     // put the handle back at the end of the forward run
     pic_status st = restore_checkpoint(a, a->ck[a->nseg]);
     if (st != PIC_OK) return st;
-    CK(cudaMemcpyAsync(h->J, a->final_j, ng * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->J, a->final_j, h->jbytes, cudaMemcpyDeviceToDevice, h->s));
     CK(cudaMemcpyAsync(h->G, a->final_g, 4 * ng * 2 * a->rsz, cudaMemcpyDeviceToDevice, h->s));
     return check_device_error(h);
 }

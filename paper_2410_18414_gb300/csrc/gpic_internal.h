@@ -200,12 +200,27 @@ cudaError_t launch_deposit_charge_fix(int p, const ParticleGeom& g, const T* x, 
                                       int64_t n, longlong2* j, float scale, unsigned int* err,
                                       cudaStream_t s, const int32_t* sp = nullptr,
                                       const SpeciesParams* spp = nullptr);
-// 2D-3V: J_z of the moved particles (x^{n+1}, v_z^n) into the .x parts of jz (FP64 sums,
-// or int64 with `scale` when fix).
+// FP64 path, deterministic: contribution = round(value * scale) summed exactly as 128-bit
+// integers; j holds 2 ng longlong2, the low words (x, y) of each node, then the high words.
+cudaError_t launch_move_deposit_fix128(int p, const ParticleGeom& g, double* x, double* y,
+                                       const double* vx, const double* vy, int64_t n,
+                                       longlong2* j, size_t ng, double scale, unsigned int* err,
+                                       cudaStream_t s, const int32_t* sp = nullptr,
+                                       const SpeciesParams* spp = nullptr);
+cudaError_t launch_deposit_charge_fix128(int p, const ParticleGeom& g, const double* x,
+                                         const double* y, int64_t n, longlong2* j, size_t ng,
+                                         double scale, unsigned int* err, cudaStream_t s,
+                                         const int32_t* sp = nullptr,
+                                         const SpeciesParams* spp = nullptr);
+// out[k] = the 128-bit sums (x, y) of node k times unscale, as complex FP64.
+cudaError_t launch_fix128_to_cplx(const longlong2* j, size_t ng, double unscale, double2* out,
+                                  cudaStream_t s);
+// 2D-3V: J_z of the moved particles (x^{n+1}, v_z^n) into the .x parts of jz: int64 sums
+// (FP32 form, float `scale`) or 128-bit sums (FP64, layout of launch_move_deposit_fix128).
 template <typename T>
 cudaError_t launch_deposit_z(int p, const ParticleGeom& g, const T* x, const T* y, const T* vz,
                              int64_t n, const int32_t* sp, const SpeciesParams& spp, void* jz,
-                             bool fix, float scale, unsigned int* err, cudaStream_t s);
+                             size_t ng, double scale, unsigned int* err, cudaStream_t s);
 // out[k] = (J[k].x, J[k].y) * unscale in complex storage type T.
 template <typename T>
 cudaError_t launch_fix_to_cplx(const longlong2* j, double unscale, void* out, int64_t n,

@@ -42,11 +42,16 @@ struct pic_handle {
     int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
     int launches_now = 0, launches_last = 0;
     // grid buffers
-    double2* J = nullptr;    // deposit accumulator (sum_p v W): FP64, or int64 pairs (FP32 form)
+    double2* J = nullptr;    // deposit accumulator (sum_p v W): 128-bit sums (FP64 path:
+                             // longlong2 low words, then high words), or int64 pairs (FP32 form)
     double2* Jalt = nullptr; // FP32 form: the other int64 buffer, zeroed by the row transform
     // FP32 form: a contribution a is summed as round(a * fix_scale_*) in int64
     float fix_scale_j = 0.f, fix_scale_q = 0.f;
     double fix_unscale_j = 0.0, fix_unscale_q = 0.0;
+    // FP64 path: round(a * fix64_scale_*) summed as 128-bit integers (two words a value)
+    double fix64_scale_j = 0.0, fix64_scale_q = 0.0;
+    double fix64_unscale_j = 0.0, fix64_unscale_q = 0.0;
+    size_t jbytes = 0;  // bytes of one current, charge or J_z buffer: 16 or 32 a node
     void* Z = nullptr;       // spectrum of J (complex)
     void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
     void* G = nullptr;       // [node][4] complex: the eight real gather fields

@@ -119,6 +119,8 @@ __device__ __forceinline__ bool in_domain(T xi, int n) {
 // atomics, so the grid total does not depend on the order of the additions.
 struct AccF64 {
     double2* J;
+    template <typename T>
+    __device__ __forceinline__ T pre(T v) const { return v; }
     // (tx wy, ty wy) to node: the two current components of one stencil node
     template <typename T>
     __device__ __forceinline__ void add2(size_t node, T tx, T ty, T wy) const {
@@ -139,6 +141,8 @@ struct AccFix {
     longlong2* J;
     float scale;     // 1 / quantum, a power of two
     float s_hi;      // scale 2^-19
+    template <typename T>
+    __device__ __forceinline__ T pre(T v) const { return v; }
     static AccFix make(void* j, float scale) {
         return AccFix{(longlong2*)j, scale, scale * (1.0f / 524288.0f)};
     }
@@ -193,6 +197,58 @@ struct AccFix {
     }
 };
 
+// FP64 path: each contribution is rounded once to an integer multiple of the quantum
+// 1/scale (|x| <= 2^60 by the choice of scale, a power of two) and summed exactly as a
+// 128-bit integer per node and component: a low word (unsigned, modulo 2^64) and a high
+// word.  The atomic on the low word returns the word it added to, so the carry out of
+// each addition is known exactly; the carry and the sign extension of x go to the high
+// word, which changes only when the low word wraps.  Integer sums do not depend on the
+// order of the additions, so the deposit is bit-for-bit deterministic.
+struct AccFix128 {
+    longlong2* J;  // [node]: the low words (x, y); [ng + node]: the high words
+    size_t ng;
+    double scale;
+    // the velocity factor carries the scale (exact: a power of two), so each contribution
+    // is rounded to an integer once
+    template <typename T>
+    __device__ __forceinline__ T pre(T v) const { return v * (T)scale; }
+    __device__ __forceinline__ void add_word(size_t node, int comp, long long x) const {
+        unsigned long long* lo = reinterpret_cast<unsigned long long*>(J + node) + comp;
+        const unsigned long long ux = (unsigned long long)x;
+        const unsigned long long old = atomicAdd(lo, ux);
+        const long long dh = (x < 0 ? -1ll : 0ll) + (old + ux < old ? 1ll : 0ll);
+        if (dh != 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(J + ng + node) + comp,
+                      (unsigned long long)dh);
+    }
+    template <typename T>
+    __device__ __forceinline__ void add2(size_t node, T tx, T ty, T wy) const {
+        add_word(node, 0, __double2ll_rn((double)rmul(tx, wy)));
+        add_word(node, 1, __double2ll_rn((double)rmul(ty, wy)));
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1f(size_t node, T t, T w) const {
+        add_word(node, 0, __double2ll_rn((double)rmul(t, w)));
+    }
+    template <typename T>
+    __device__ __forceinline__ void add1(size_t node, T a) const {
+        add_word(node, 0, __double2ll_rn((double)a * scale));
+    }
+};
+
+// hi 2^64 + lo (two's complement over 128 bits) times unscale, rounded to FP64: the
+// magnitude is exact below 2^64 before its one rounding, and rounded twice above.
+__device__ __forceinline__ double fix128_value(long long hi, unsigned long long lo,
+                                               double unscale) {
+    const bool neg = hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ll : 0ll);
+    }
+    const double m = fma((double)hi, 18446744073709551616.0, (double)lo);
+    return (neg ? -m : m) * unscale;
+}
+
 template <typename T, int P, typename Acc>
 __global__ void __launch_bounds__(kThreads)
 k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __restrict__ vx,
@@ -216,6 +272,8 @@ k_move_deposit(GeomT<T> g, T* __restrict__ x, T* __restrict__ y, const T* __rest
             vxi = rmul(vxi, fq);
             vyi = rmul(vyi, fq);
         }
+        vxi = acc.pre(vxi);
+        vyi = acc.pre(vyi);
         T wx[P + 1], wy[P + 1];
         const int ix = Shape<P, T>::weights(xi, wx);
         const int iy = Shape<P, T>::weights(yj, wy);
@@ -273,6 +331,17 @@ __global__ void k_fix_to_cplx(const longlong2* __restrict__ J, double unscale,
          k += (int64_t)gridDim.x * blockDim.x) {
         const longlong2 v = J[k];
         out[k] = mk<cplx_t<T>>((double)v.x * unscale, (double)v.y * unscale);
+    }
+}
+
+// FP64 path: the 128-bit sums of AccFix128 to complex FP64 values, times `unscale`.
+__global__ void k_fix128_to_cplx(const longlong2* __restrict__ J, size_t ng, double unscale,
+                                 double2* __restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)ng;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const longlong2 lo = J[k], hi = J[ng + k];
+        out[k] = make_double2(fix128_value(hi.x, (unsigned long long)lo.x, unscale),
+                              fix128_value(hi.y, (unsigned long long)lo.y, unscale));
     }
 }
 
@@ -1037,7 +1106,7 @@ k_deposit_z(GeomT<T> g, const T* __restrict__ x, const T* __restrict__ y,
         T wx[P + 1], wy[P + 1];
         const int ix = Shape<P, T>::weights(xi, wx);
         const int iy = Shape<P, T>::weights(yj, wy);
-        const T vzi = sp ? rmul(vz[p], fq) : vz[p];
+        const T vzi = acc.pre(sp ? rmul(vz[p], fq) : vz[p]);
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
             const size_t row = (size_t)wrap_idx(ix + a, g.nx) * g.ny;
@@ -1250,6 +1319,35 @@ cudaError_t launch_move_deposit(int p, const ParticleGeom& g, T* x, T* y, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_move_deposit_fix128(int p, const ParticleGeom& g, double* x, double* y,
+                                       const double* vx, const double* vy, int64_t n,
+                                       longlong2* j, size_t ng, double scale, unsigned int* err,
+                                       cudaStream_t s, const int32_t* sp,
+                                       const SpeciesParams* spp) {
+    using T = double;
+    if (n == 0) return cudaSuccess;
+    GPIC_DISPATCH_PA(p, k_move_deposit, AccFix128, typed<T>(g), x, y, vx, vy, n,
+                     (AccFix128{j, ng, scale}), err, sp, typed_species<T>(spp))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_charge_fix128(int p, const ParticleGeom& g, const double* x,
+                                         const double* y, int64_t n, longlong2* j, size_t ng,
+                                         double scale, unsigned int* err, cudaStream_t s,
+                                         const int32_t* sp, const SpeciesParams* spp) {
+    using T = double;
+    if (n == 0) return cudaSuccess;
+    GPIC_DISPATCH_PA(p, k_deposit_charge, AccFix128, g, x, y, n, (AccFix128{j, ng, scale}), err,
+                     sp, typed_species<T>(spp))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix128_to_cplx(const longlong2* j, size_t ng, double unscale, double2* out,
+                                  cudaStream_t s) {
+    k_fix128_to_cplx<<<blocks_for((int64_t)ng), kThreads, 0, s>>>(j, ng, unscale, out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_deposit_charge(int p, const ParticleGeom& g, const T* x, const T* y, int64_t n,
                                   double2* j, unsigned int* err, cudaStream_t s,
@@ -1296,15 +1394,15 @@ template cudaError_t launch_replay_step<float>(const ParticleGeom&, const float*
 template <typename T>
 cudaError_t launch_deposit_z(int p, const ParticleGeom& g, const T* x, const T* y, const T* vz,
                              int64_t n, const int32_t* sp, const SpeciesParams& spp, void* jz,
-                             bool fix, float scale, unsigned int* err, cudaStream_t s) {
+                             size_t ng, double scale, unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int32_t* spi = spp.n > 0 ? sp : nullptr;
-    if (fix) {
+    if constexpr (sizeof(T) == 4) {
         GPIC_DISPATCH_PA(p, k_deposit_z, AccFix, typed<T>(g), x, y, vz, n, spi,
-                         typed_species<T>(&spp), (AccFix::make(jz, scale)), err)
+                         typed_species<T>(&spp), (AccFix::make(jz, (float)scale)), err)
     } else {
-        GPIC_DISPATCH_PA(p, k_deposit_z, AccF64, typed<T>(g), x, y, vz, n, spi,
-                         typed_species<T>(&spp), AccF64{(double2*)jz}, err)
+        GPIC_DISPATCH_PA(p, k_deposit_z, AccFix128, typed<T>(g), x, y, vz, n, spi,
+                         typed_species<T>(&spp), (AccFix128{(longlong2*)jz, ng, scale}), err)
     }
     return cudaGetLastError();
 }
@@ -1510,7 +1608,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
                                                   const SpeciesParams*);                        \
     template cudaError_t launch_deposit_z<T>(int, const ParticleGeom&, const T*, const T*,      \
                                              const T*, int64_t, const int32_t*,                 \
-                                             const SpeciesParams&, void*, bool, float,          \
+                                             const SpeciesParams&, void*, size_t, double,       \
                                              unsigned int*, cudaStream_t);                      \
     template cudaError_t launch_gather_push3<T>(int, const ParticleGeom&, const PushParams&,    \
                                                 const T*, const T*, T*, T*, const T*, const T*, \

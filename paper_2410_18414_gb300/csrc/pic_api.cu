@@ -276,21 +276,21 @@ pic_status alloc_state(pic_handle* h) {
         CK(dalloc(h, &h->pz, pn));
         CK(dalloc(h, &h->vz[0], pn));
         CK(dalloc(h, &h->vz[1], pn));
-        CK(dalloc(h, &h->Jz, h->ng * sizeof(double2)));
+        CK(dalloc(h, &h->Jz, h->jbytes));
         CK(dalloc(h, &h->Zz, h->ng * cs));
         CK(dalloc(h, &h->F2, 2 * h->ng * cs));
         CK(dalloc(h, &h->Gz, 2 * h->ng * cs));
     }
     if (h->spp.n > 0)
         CK(dalloc(h, (void**)&h->species, (size_t)std::max<int64_t>(h->n, 1) * sizeof(int32_t)));
-    CK(dalloc(h, (void**)&h->J, h->ng * sizeof(double2)));
+    CK(dalloc(h, (void**)&h->J, h->jbytes));
     if (h->fp32) {
         CK(dalloc(h, (void**)&h->Jalt, h->ng * sizeof(double2)));
         CK(cudaMemsetAsync(h->Jalt, 0, h->ng * sizeof(double2), h->s));
     }
     CK(dalloc(h, &h->Z, h->ng * cs));
     if (h->cfg.charge == PIC_CHARGE_DEPOSIT) {
-        CK(dalloc(h, &h->rhoq, h->ng * sizeof(double2)));
+        CK(dalloc(h, &h->rhoq, h->jbytes));
         CK(dalloc(h, &h->ZQ, h->ng * cs));
         h->mc.zq = h->ZQ;
     }
@@ -427,7 +427,7 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
 
     void* rho0 = newest(h, 3);
     void* phi0 = newest(h, 0);
-    CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+    CK(cudaMemsetAsync(h->J, 0, h->jbytes, h->s));
     CK(by_prec(h, [&](auto t) -> cudaError_t {
         using T = decltype(t);
         cudaError_t r = launch_wrap_positions<T>((T*)h->x, (T*)h->y, n, c.lx, c.ly, h->s);
@@ -441,10 +441,14 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
             if (r != cudaSuccess) return r;
             r = forward_fft(h, h->tmp, h->Z);
         } else {
-            r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, n, h->J,
-                                         h->err, h->s, sp, &h->spp);
+            r = launch_deposit_charge_fix128(h->p, h->geom, (const double*)h->x,
+                                             (const double*)h->y, n, (longlong2*)h->J, h->ng,
+                                             h->fix64_scale_q, h->err, h->s, sp, &h->spp);
             if (r != cudaSuccess) return r;
-            r = forward_fft(h, h->J, h->Z);
+            r = launch_fix128_to_cplx((const longlong2*)h->J, h->ng, h->fix64_unscale_q,
+                                      (double2*)h->tmp, h->s);
+            if (r != cudaSuccess) return r;
+            r = forward_fft(h, h->tmp, h->Z);
         }
         if (r != cudaSuccess) return r;
         r = launch_mode_init<T>(h->mc, h->Z, rho0, phi0, h->F4, h->s);
@@ -633,7 +637,19 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         k -= (int)std::ceil(std::log2(rmax));
         h->fix_scale_q = (float)std::ldexp(1.0, k);
         h->fix_unscale_q = std::ldexp(1.0, -k);
+    } else {
+        // FP64 path: |v W_x W_y| < c and |W_x W_y| <= 1 (times max |q_s w_s|), so quanta of
+        // 2^-60 of those bounds keep every contribution below 2^60 (one int64 word); the
+        // 128-bit sums have room for any number of them.  The quantum (8.7e-19 c for the
+        // current) is far below FP64 rounding of a node's total.
+        const int kc = (int)std::ceil(std::log2(cfg->c)) + (int)std::ceil(std::log2(rmax));
+        h->fix64_scale_j = std::ldexp(1.0, 60 - kc);
+        h->fix64_unscale_j = std::ldexp(1.0, kc - 60);
+        const int kq = (int)std::ceil(std::log2(rmax));
+        h->fix64_scale_q = std::ldexp(1.0, 60 - kq);
+        h->fix64_unscale_q = std::ldexp(1.0, kq - 60);
     }
+    h->jbytes = h->ng * (h->fp32 ? sizeof(longlong2) : 2 * sizeof(longlong2));
     st = alloc_state(h);
     if (st == PIC_OK) st = setup(h, init);
     if (st != PIC_OK) {
@@ -674,7 +690,7 @@ pic_status pic_deposit(pic_handle* h) {
         // of dependent launches); J^n stays readable until then
         std::swap(h->J, h->Jalt);
     } else {
-        CK(cudaMemsetAsync(h->J, 0, h->ng * sizeof(double2), h->s));
+        CK(cudaMemsetAsync(h->J, 0, h->jbytes, h->s));
     }
     h->launches_now += 1;
     TimedScope ts(h, PIC_KT_DEPOSIT);
@@ -692,22 +708,26 @@ pic_status pic_deposit(pic_handle* h) {
                                          kBinPerCta);
         }
         const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
-        if (h->fp32)
+        if constexpr (sizeof(T) == 4) {
             return launch_move_deposit_fix<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
                                               (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1],
                                               h->n, (longlong2*)h->J, h->fix_scale_j, h->err, h->s,
                                               sp, &h->spp);
-        return launch_move_deposit<T>(h->p, h->geom, (T*)h->x, (T*)h->y,
-                                      (const T*)h->v[h->vcur][0], (const T*)h->v[h->vcur][1], h->n,
-                                      h->J, h->err, h->s, sp, &h->spp);
+        } else {
+            return launch_move_deposit_fix128(h->p, h->geom, (T*)h->x, (T*)h->y,
+                                              (const T*)h->v[h->vcur][0],
+                                              (const T*)h->v[h->vcur][1], h->n, (longlong2*)h->J,
+                                              h->ng, h->fix64_scale_j, h->err, h->s, sp, &h->spp);
+        }
     }));
     if (h->vdim == 3) {  // J_z of the moved particles
-        CK(cudaMemsetAsync(h->Jz, 0, h->ng * sizeof(double2), h->s));
+        CK(cudaMemsetAsync(h->Jz, 0, h->jbytes, h->s));
         CK(by_prec(h, [&](auto t) {
             using T = decltype(t);
             return launch_deposit_z<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y,
                                        (const T*)h->vz[h->vcur], h->n, h->species, h->spp, h->Jz,
-                                       h->fp32, h->fix_scale_j, h->err, h->s);
+                                       h->ng, h->fp32 ? (double)h->fix_scale_j : h->fix64_scale_j,
+                                       h->err, h->s);
         }));
         h->launches_now += 1;
     }
@@ -728,8 +748,11 @@ pic_status pic_field_solve(pic_handle* h) {
     if (h->fp32) {
         CK(launch_fft_y_from_fix<float>((const longlong2*)h->J, h->fix_unscale_j, h->Z, h->nx,
                                         h->ny, h->fy, h->twy, (longlong2*)h->Jalt, h->s));
-    } else {
-        CK(launch_fft_y<double>(h->J, h->Z, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s));
+    } else {  // the 128-bit sums to FP64, then the transform
+        CK(launch_fix128_to_cplx((const longlong2*)h->J, h->ng, h->fix64_unscale_j,
+                                 (double2*)h->tmp, h->s));
+        CK(launch_fft_y<double>(h->tmp, h->Z, h->nx, h->ny, 1, h->fy, h->twy, -1, 0, h->s));
+        h->launches_now += 1;
     }
     if (!fused) CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
@@ -740,7 +763,7 @@ pic_status pic_field_solve(pic_handle* h) {
     // like the t = 0 charge
     const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
     if (h->cfg.charge == PIC_CHARGE_DEPOSIT) {
-        CK(cudaMemsetAsync(h->rhoq, 0, h->ng * sizeof(double2), h->s));
+        CK(cudaMemsetAsync(h->rhoq, 0, h->jbytes, h->s));
         CK(by_prec(h, [&](auto t) -> cudaError_t {
             using T = decltype(t);
             cudaError_t r;
@@ -753,9 +776,13 @@ pic_status pic_field_solve(pic_handle* h) {
                                               h->ng, h->s);
                 return r == cudaSuccess ? forward_fft(h, h->tmp, h->ZQ) : r;
             }
-            r = launch_deposit_charge<T>(h->p, h->geom, (const T*)h->x, (const T*)h->y, h->n,
-                                         (double2*)h->rhoq, h->err, h->s, sp, &h->spp);
-            return r == cudaSuccess ? forward_fft(h, h->rhoq, h->ZQ) : r;
+            r = launch_deposit_charge_fix128(h->p, h->geom, (const double*)h->x,
+                                             (const double*)h->y, h->n, (longlong2*)h->rhoq,
+                                             h->ng, h->fix64_scale_q, h->err, h->s, sp, &h->spp);
+            if (r == cudaSuccess)
+                r = launch_fix128_to_cplx((const longlong2*)h->rhoq, h->ng, h->fix64_unscale_q,
+                                          (double2*)h->tmp, h->s);
+            return r == cudaSuccess ? forward_fft(h, h->tmp, h->ZQ) : r;
         }));
     }
 
@@ -831,8 +858,10 @@ pic_status pic_field_solve(pic_handle* h) {
                 r = launch_fix_to_cplx<T>((const longlong2*)h->Jz, h->fix_unscale_j, h->tmp, h->ng,
                                           h->s);
                 if (r == cudaSuccess) r = forward_fft(h, h->tmp, h->Zz);
-            } else {
-                r = forward_fft(h, h->Jz, h->Zz);  // J_z in the real parts
+            } else {  // J_z in the real parts
+                r = launch_fix128_to_cplx((const longlong2*)h->Jz, h->ng, h->fix64_unscale_j,
+                                          (double2*)h->tmp, h->s);
+                if (r == cudaSuccess) r = forward_fft(h, h->tmp, h->Zz);
             }
             if (r != cudaSuccess) return r;
             r = launch_zfield<T>(h->mc, bp, h->dirk, zp, h->Zz, h->F2, h->diag, h->s);
@@ -1236,18 +1265,26 @@ pic_status pic_get_field(pic_handle* h, int32_t which, double* dst) {
     cudaError_t e = by_prec(h, [&](auto t) -> cudaError_t {
         using T = decltype(t);
         const size_t cs = sizeof(T) * 2;
+        cudaError_t r0;
         switch (which) {
             case PIC_FIELD_JX:
             case PIC_FIELD_JY:
                 if (h->fp32)
                     return launch_extract_fix((const longlong2*)h->J, which == PIC_FIELD_JY,
                                               h->fix_unscale_j * h->mc.jscale, h->tmpd, n, h->s);
-                return launch_extract<double>(h->J, 1, which == PIC_FIELD_JY, h->mc.jscale, h->tmpd, n, h->s);
+                r0 = launch_fix128_to_cplx((const longlong2*)h->J, h->ng, h->fix64_unscale_j,
+                                           (double2*)h->tmp, h->s);
+                if (r0 != cudaSuccess) return r0;
+                return launch_extract<double>(h->tmp, 1, which == PIC_FIELD_JY, h->mc.jscale,
+                                              h->tmpd, n, h->s);
             case PIC_FIELD_JZ:
                 if (h->fp32)
                     return launch_extract_fix((const longlong2*)h->Jz, 0,
                                               h->fix_unscale_j * h->mc.jscale, h->tmpd, n, h->s);
-                return launch_extract<double>(h->Jz, 1, 0, h->mc.jscale, h->tmpd, n, h->s);
+                r0 = launch_fix128_to_cplx((const longlong2*)h->Jz, h->ng, h->fix64_unscale_j,
+                                           (double2*)h->tmp, h->s);
+                if (r0 != cudaSuccess) return r0;
+                return launch_extract<double>(h->tmp, 1, 0, h->mc.jscale, h->tmpd, n, h->s);
             case PIC_FIELD_DAZDX: case PIC_FIELD_DAZDY:  // Gz: [node][2], (dAz/dx, dAz/dy) first
                 return launch_extract<T>(h->Gz, 2, which == PIC_FIELD_DAZDY, 1.0, h->tmpd, n, h->s);
             case PIC_FIELD_DPHIDX: case PIC_FIELD_DPHIDY: case PIC_FIELD_GAX: case PIC_FIELD_GAY:

@@ -34,7 +34,7 @@ struct StateHeader {
     double dirk_a[16], dirk_b[4], dirk_c[4];
     double species_q[4], species_m[4], species_w[4];
 };
-constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '3'};
+constexpr char kMagic[8] = {'G', 'P', 'I', 'C', 'S', 'T', 'A', '4'};
 
 struct Seg {
     void* p;
@@ -57,10 +57,10 @@ std::vector<Seg> segments(pic_handle* h) {
         add(h->id, (size_t)h->n * sizeof(int32_t));
         add(h->off, ((size_t)h->tg.nkeys() + 1) * sizeof(int));
     }
-    add(h->J, sb);  // last step's current (double2, or longlong2 sums)
+    add(h->J, h->jbytes);  // last step's current (128-bit sums, or int64 sums)
     add(h->G, 4 * ng * cs);
     if (h->vdim == 3) {
-        add(h->Jz, sb);
+        add(h->Jz, h->jbytes);
         add(h->Gz, 2 * ng * cs);
     }
     switch (h->cfg.stepper) {

@@ -7,19 +7,20 @@
   The same for the three CDF-2 forms and DIRK (Qin-Zhang 2-stage, implicit-midpoint
   3-stage), in both record modes, with the fused column pass and the separate mode
   kernel (a grid whose x extent is too large for the column pass's shared memory).
-- Checkpoint-interval invariance: K = 1, 3, N give the same gradient (to the FP64
-  atomic-order roundoff of the forward's current deposit).
+- Checkpoint-interval invariance: K = 1, 3, N give the same gradient (to the roundoff of
+  the reverse pass's FP64 field-adjoint atomics, which sum in no fixed order).
 - The 128 x 128 Weibel configuration (262,144 particles, v_d = 0.5c, BDF-2, cubic, 200
   steps): the gradient of W_B against central finite differences of the forward run with
   h = 1e-6 along v_d (through u_d = gamma_d v_d) and along 4 random directions in v^0;
   bound 1e-6 relative (measured <= 1.5e-7).  Along 32 random single components of P^0
   the forward's own roundoff limits the finite difference: W_B carries FP64 roundoff
-  amplified by 200 steps of the unstable dynamics (identical runs differ by 1e-14 to
-  2.6e-13 relative, since the current sums FP64 atomics in no fixed order; a perturbed
-  input reshuffles the roundoff the same way), while one particle's derivative is only
-  ~1e-10 against W_B = 5.8e-7.  The finite difference then carries an error of about
-  sigma W_B / h; values up to sigma = 1.1e-12 were seen.  There h = 1e-4 and the bound is
-  1e-6 |g| + sigma W_B / h with sigma = 4e-12 (about 1e-4 of a typical component).
+  amplified by 200 steps of the unstable dynamics (identical runs are bit-identical, the
+  deposit summing integers, but a perturbed input reshuffles the roundoff of every later
+  transform and push), while one particle's derivative is only ~1e-10 against
+  W_B = 5.8e-7.  The finite difference then carries an error of about sigma W_B / h;
+  measured sigma <= 1.9e-13 at h = 1e-6 and <= 1.3e-12 at h = 1e-4 (truncation
+  included).  There h = 1e-4 and the bound is 1e-6 |g| + sigma W_B / h with
+  sigma = 4e-12 (about 1e-4 of a typical component).
 - The handle is left at the end of the forward run; torch.autograd returns the same
   gradient as the library call.
 - The FP32 form's adjoint (unsorted handles) against the oracle's FP64 gradient, for

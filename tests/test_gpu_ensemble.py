@@ -1,7 +1,6 @@
 """GPU checks of ensembles (pic_ensemble_*): independent runs captured into one CUDA
-graph and advanced by replaying it must give the results of pic_step on each run --
-bit for bit in the FP32 form, whose current is an integer sum; to roundoff in the FP64
-path, whose FP64 current atomics have no fixed order."""
+graph and advanced by replaying it must give the results of pic_step on each run, bit for
+bit in both forms, whose currents are integer sums."""
 import numpy as np
 import pytest
 
@@ -56,16 +55,9 @@ def make(torch, spec, stream=None):
 def assert_same(a, b, prec):
     pa, pb = a.particles(), b.particles()
     for k in pa:
-        if prec == pic.FP32_FIX64:
-            assert np.array_equal(pa[k], pb[k]), k
-        else:
-            assert rel(pa[k], pb[k]) < 1e-13, k
+        assert np.array_equal(pa[k], pb[k]), (k, prec)
     for f in ("jx", "phi", "ay", "daxdy"):
-        u, v = a.field(f), b.field(f)
-        if prec == pic.FP32_FIX64:
-            assert np.array_equal(u, v), f
-        else:
-            assert rel(u, v) < 1e-12, f
+        assert np.array_equal(a.field(f), b.field(f)), (f, prec)
 
 
 def test_ensemble_matches_runs_stepped_alone(torch_mod):

@@ -247,9 +247,8 @@ def test_kernel_timers_count_the_launches_they_bracket(device):
                                         ("cdf2", {})], ids=["bdf2", "bdf3", "cdf2"])
 def test_diagnostics_do_not_change_the_trajectory(device, precision, stepper, kw):
     # diagnosed steps take a different (one thread per mode) path through the per-mode
-    # update; the arithmetic must be the same.  The FP32 form sums the current in
-    # integers, so its trajectories are bitwise equal; the FP64 path sums it with FP64
-    # atomics in no fixed order, so two of its runs agree to roundoff only.
+    # update; the arithmetic must be the same.  Both forms sum the current in integers,
+    # so the trajectories are bitwise equal.
     wl = workloads.weibel(48, 32, 8, 0.5, 0.01, 97, 3)
     sims = []
     for diag in (0, 3):
@@ -262,16 +261,10 @@ def test_diagnostics_do_not_change_the_trajectory(device, precision, stepper, kw
         sims.append(sim)
     a, b = sims[0].particles(), sims[1].particles()
     fields = [(sims[0].field(f), sims[1].field(f)) for f in ("phi", "ax", "ay", "rho", "daxdy")]
-    if precision == pic.FP32_FIX64:
-        for k in a:
-            assert np.array_equal(a[k], b[k]), k
-        for u, v in fields:
-            assert np.array_equal(u, v)
-    else:
-        for k in a:
-            assert rel(a[k], b[k]) < 1e-13, k
-        for u, v in fields:
-            assert rel(u, v) < 1e-12
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    for u, v in fields:
+        assert np.array_equal(u, v)
     for s in sims:
         s.close()
 

@@ -307,6 +307,35 @@ def test_parity_with_tile_sort(device, name, make, nsteps, sort, kw):
     sim.close()
 
 
+@pytest.mark.parametrize("kw", [dict(stepper="bdf", bdf_order=2),
+                                dict(stepper="bdf", bdf_order=1, charge=pic.CHARGE_DEPOSIT),
+                                dict(stepper="cdf2", vdim=3)],
+                         ids=["bdf2", "bdf1-naive-charge", "cdf2-3v"])
+def test_fp64_deposit_is_deterministic(device, kw):
+    # The FP64 path sums every deposit (current, J_z, the charge at t = 0 and the naive
+    # charge) as 128-bit integers, so the order of the additions cannot change a bit: two
+    # runs of one handle configuration, and a run whose tile sort reorders the particles
+    # (and so the order of the atomics) every 3 steps, give identical particles and fields.
+    wl = workloads.weibel(48, 32, 12, 0.5, 0.01, 33, 3)
+    extra = {}
+    if kw.get("vdim") == 3:
+        extra["vz"] = np.random.default_rng(5).uniform(-0.2, 0.2, wl.n)
+    runs = []
+    for sort in ((0, 0) if kw.get("vdim") == 3 else (0, 0, 3)):  # 2D-3V runs unsorted
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=wl.p, weight=wl.weight,
+                              sort_interval=sort, **kw)
+        with pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=device, **extra) as sim:
+            sim.step(11)
+            f = ("jx", "jy", "rho", "phi", "ax", "ay", "dphidx", "daydy") + \
+                (("jz", "az") if kw.get("vdim") == 3 else ())
+            runs.append((sim.particles(), {k: sim.field(k) for k in f}))
+    for parts, fields in runs[1:]:
+        for k, v in runs[0][0].items():
+            assert np.array_equal(parts[k], v), k
+        for k, v in runs[0][1].items():
+            assert np.array_equal(fields[k], v), k
+
+
 def test_tile_sort_full_size_weibel_128(device):
     wl = workloads.weibel_128(stepper="bdf", bdf_order=2)
     cfg = pic.make_config(128, 128, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf", bdf_order=2,

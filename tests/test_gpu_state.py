@@ -1,7 +1,7 @@
 """Checkpoint and resume (pic_save_state / pic_load_state): a handle loaded with the state
-of another steps on exactly as the other does -- bit for bit in the FP32 form, whose
-current sums are order-independent integers; to FP64 roundoff in the FP64 path, whose
-atomics sum in no fixed order.  Saved mid sort interval (the sort's order and tile
+of another steps on exactly as the other does -- bit for bit in both forms, whose current
+sums are order-independent integers (int64 in the FP32 form, 128-bit in the FP64 path).
+Saved mid sort interval (the sort's order and tile
 offsets), after an odd number of CDF-2 steps (its swapped levels), with BDF rings whose
 head has moved, and in 2D-3V with species.  Loading into another configuration or from a
 truncated string is refused."""
@@ -40,6 +40,8 @@ CASES = [
                                   species=((-1.0, 1.0, 1.0 / 8192), (1.0, 4.0, 1.0 / 8192))),
      3, 5),
     ("fp64-cdf2", dict(stepper="cdf2"), 3, 5),
+    ("fp64-bdf2-sorted", dict(stepper="bdf", bdf_order=2, sort_interval=3), 2, 4),
+    ("fp64-bdf2-3v", dict(stepper="bdf", bdf_order=2, vdim=3), 2, 4),
 ]
 
 
@@ -77,13 +79,8 @@ def test_resume_steps_on_like_the_source(device, name, kw, before, after):
     b.step(after)
     got = _snapshot(b, three)
     b.close()
-    exact = kw.get("precision") == pic.FP32_FIX64
     for k, v in ref.items():
-        if exact:
-            assert np.array_equal(got[k], v), k
-        else:
-            err = np.linalg.norm(got[k] - v) / max(np.linalg.norm(v), 1e-300)
-            assert err <= 1e-12, (k, err)
+        assert np.array_equal(got[k], v), k
 
 
 def test_load_refuses_other_configurations(device):
