@@ -167,8 +167,9 @@ typedef struct {
  * Poisson's equation, A^0 = 0, P^0 = gamma m v^0, v^{-1} by a first-order Taylor
  * step back in E^0 = -grad phi^0, and every history level at its t = 0 value.
  * On success *out receives the handle.  The stream must outlive the handle.
- * 2D-3V and species tables run on the unsorted kernels: with sort_interval > 0 they are
- * PIC_ERR_UNSUPPORTED.  PIC_ERR_INVALID_ARG for a field out of its stated range (tile not
+ * With sort_interval > 0 a species table (2D-2V, FP32 form) runs in the fused binned
+ * kernel; 2D-3V runs, and FP64 runs, step their sorted particles with the general kernels.
+ * PIC_ERR_INVALID_ARG for a field out of its stated range (tile not
  * 0, 4, 8 or 16; reserved fields not zero; ...).  A tile wider than half the grid is
  * narrowed to fit. */
 pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,

@@ -271,6 +271,9 @@ cudaError_t launch_convert(const Tsrc* src, Tdst* dst, int64_t n, cudaStream_t s
 template <typename T>
 cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, int64_t n,
                                  cudaStream_t s);
+// dst[id[k]] = src[k] for int32 values (the species indices of a sorted handle).
+cudaError_t launch_scatter_by_id_i32(const int32_t* src, const int32_t* id, int32_t* dst,
+                                     int64_t n, cudaStream_t s);
 
 // Tiles for the particle sort and the shared-memory deposit: t x t cells per tile,
 // ntx x nty tiles; a CTA accumulates into an rx x ry node region starting `halo` nodes
@@ -292,6 +295,8 @@ template <typename T>
 struct SortArrays {
     T* a[8];
     int32_t* id;
+    int32_t* sp = nullptr;                  // species indices (a species table), else NULL
+    T* z[3] = {nullptr, nullptr, nullptr};  // 2D-3V: P_z, v_z (both buffers), else NULL
 };
 
 int sort_scan_chunks(int nkeys);  // chunk totals the scan keeps (size of its bsum array)
@@ -310,15 +315,19 @@ cudaError_t launch_iota(int32_t* id, int64_t n, cudaStream_t s);
 // first on each particle (fields4 = that step's gather fields, P and v^{n+1} -> px, py,
 // vxo, vyo; the move and deposit then use v^{n+1}), as launch_gather_push_tiled does it.
 // per_cta: particles per CTA at the mean density.  deposit_binned_fits: whether the tile's
-// regions fit the pass's shared memory.
-bool deposit_binned_fits(const TileGeom& tg, int p, bool fused);
+// regions fit the pass's shared memory.  sp/spp: a species table (each contribution times
+// q_s w_s; the fused push with each species' charge and mass).  vz/jz (2D-3V, not fused):
+// v_z^n of the particles and the int64 J_z sums (.x parts), deposited in the same pass.
+bool deposit_binned_fits(const TileGeom& tg, int p, bool fused, bool z = false);
 cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
                                   const TileGeom& tg, const float* x, const float* y, float* xo,
                                   float* yo, float* px, float* py, const float* vx,
                                   const float* vy, float* vxo, float* vyo, int64_t n,
                                   const int* off, const void* fields4, void* j, float scale,
                                   double* diag, unsigned int* err, cudaStream_t s, bool fused,
-                                  int per_cta);
+                                  int per_cta, const int32_t* sp = nullptr,
+                                  const SpeciesParams* spp = nullptr, const float* vz = nullptr,
+                                  void* jz = nullptr);
 
 // Gather + push of particles sorted by launch_tile_sort (FP32 form), fields staged per tile.
 cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushParams& pp,

@@ -39,6 +39,8 @@ struct pic_handle {
     gpic::TileGeom tg{};
     void* alt[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t *id = nullptr, *id_alt = nullptr;
+    int32_t* species_alt = nullptr;                 // species indices (a species table)
+    void* z_alt[3] = {nullptr, nullptr, nullptr};   // 2D-3V: P_z, v_z[0], v_z[1]
     int *keys = nullptr, *hist = nullptr, *off = nullptr, *cursor = nullptr, *bsum = nullptr;
     int launches_now = 0, launches_last = 0;
     // grid buffers

@@ -596,26 +596,39 @@ constexpr int kBinBatch = 1024;
 constexpr int kBinSmemMax = 100 * 1024;  // four CTAs per SM fit up to 56 KB each
 
 // Byte offsets in the binned pass's dynamic shared memory (stage first: 16-byte aligned).
+// The species constants of the binned pass (FP32 form): the deposit factor q_s w_s, the
+// push constants of k_gather_push3 (q_s, q_s dt, m_s c^2 in FP32) and the FP64 mass and
+// weight of the kinetic-energy diagnostic.
+struct BinSpecies {
+    int n;
+    float qw[kMaxSpecies], q[kMaxSpecies], qdt[kMaxSpecies], mc2[kMaxSpecies];
+    double m[kMaxSpecies], w[kMaxSpecies];
+};
+
 struct BinLayout {
     int fields;   // kFused: the gather fields of the region, [rx][ry] x 2 float4
+    int stz;      // 2D-3V: float [kBinBatch]: v_z of each staged particle
     int kr;       // int [kBinBatch]: key | rank << 16 of each staged particle (-1: none)
     int idx;      // uint16 [kBinBatch]: staging slots in binned order
-    int racc;     // int [4 rx ry]: lo_x, lo_y, hi_x, hi_y node sums
+    int racc;     // int [4 rx ry] (2D-3V: 6): lo_x, lo_y, hi_x, hi_y (lo_z, hi_z) node sums
     int cnt;      // int [rx ry + 1]: counts, then offsets
     int bytes;
 };
-__host__ __device__ inline BinLayout bin_layout(const TileGeom& tg, int p, bool fused) {
+__host__ __device__ inline BinLayout bin_layout(const TileGeom& tg, int p, bool fused,
+                                                bool z = false) {
     BinLayout l;
     int o = kBinBatch * 16;  // stage: (x, y, vx, vy) of each particle, arrival order
     l.fields = o;
     if (fused) o += tg.rx * tg.ry * 32;
+    l.stz = o;
+    if (z) o += kBinBatch * 4;
     l.kr = o;
     o += kBinBatch * 4;
     l.idx = o;
     o += kBinBatch * 2;
     o = (o + 15) & ~15;
     l.racc = o;
-    o += 4 * tg.rx * tg.ry * 4;
+    o += (z ? 6 : 4) * tg.rx * tg.ry * 4;
     l.cnt = o;
     o += (tg.rx * tg.ry + 1) * 4;
     l.bytes = (o + 15) & ~15;
@@ -649,30 +662,28 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int* wsum, int* total) 
     return wsum[warp] + inc - v;
 }
 
-// Register sums of stencil rows A0..A1-1 of one base node: s[a][b] = (lo_x, lo_y, hi_x, hi_y).
-template <int P, int NA>
+// Register sums of stencil rows A0..A1-1 of one base node: s[a][b] = (lo_x, lo_y, hi_x,
+// hi_y) and, in 2D-3V (NQ = 6), (lo_z, hi_z).
+template <int P, int NA, int NQ = 4>
 struct RowSums {
-    int s[NA][P + 1][4];
+    int s[NA][P + 1][NQ];
     __device__ __forceinline__ void clear() {
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
             for (int b = 0; b <= P; ++b)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) s[a][b][q] = 0;
+                for (int q = 0; q < NQ; ++q) s[a][b][q] = 0;
     }
-    // adds them to the region at node0 (rows of ry nodes; the four planes R apart)
+    // adds them to the region at node0 (rows of ry nodes; the NQ planes R apart)
     __device__ __forceinline__ void flush(int* __restrict__ node0, int ry, int R) const {
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
             int* row = node0 + a * ry;
 #pragma unroll
-            for (int b = 0; b <= P; ++b) {
-                atomicAdd(row + b, s[a][b][0]);
-                atomicAdd(row + R + b, s[a][b][1]);
-                atomicAdd(row + 2 * R + b, s[a][b][2]);
-                atomicAdd(row + 3 * R + b, s[a][b][3]);
-            }
+            for (int b = 0; b <= P; ++b)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) atomicAdd(row + q * R + b, s[a][b][q]);
         }
     }
 };
@@ -680,13 +691,14 @@ struct RowSums {
 // Deposit of the binned particles [k0, k1) (sidx order) for stencil rows A0..A1-1: the
 // contributions are summed in registers while the key (the region node of the stencil
 // base) stays the same.
-template <int P, int A0, int A1>
+template <int P, int A0, int A1, bool kZ = false>
 __device__ __forceinline__ void bin_slice_rows(const float4* __restrict__ stage,
                                                const int* __restrict__ kr,
                                                const uint16_t* __restrict__ sidx, int k0, int k1,
                                                float idx_, float idy, const AccFix& acc,
-                                               int* __restrict__ racc, int ry, int R) {
-    RowSums<P, A1 - A0> rs;
+                                               int* __restrict__ racc, int ry, int R,
+                                               const float* __restrict__ stz = nullptr) {
+    RowSums<P, A1 - A0, kZ ? 6 : 4> rs;
     rs.clear();
     int cur = -1;
 #pragma unroll 1
@@ -704,9 +716,13 @@ __device__ __forceinline__ void bin_slice_rows(const float4* __restrict__ stage,
         float wx[P + 1], wy[P + 1];
         Shape<P, float>::weights(rmul(q4.x, idx_), wx);
         Shape<P, float>::weights(rmul(q4.y, idy), wy);
+        float vzs = 0.f;
+        if (kZ) vzs = stz[slot];
 #pragma unroll
         for (int a = 0; a < A1 - A0; ++a) {
             const float tx = rmul(q4.z, wx[A0 + a]), ty = rmul(q4.w, wx[A0 + a]);
+            float tz = 0.f;
+            if (kZ) tz = rmul(vzs, wx[A0 + a]);
 #pragma unroll
             for (int b = 0; b <= P; ++b) {
                 float wh, ws;
@@ -718,6 +734,12 @@ __device__ __forceinline__ void bin_slice_rows(const float4* __restrict__ stage,
                 rs.s[a][b][1] += ly;
                 rs.s[a][b][2] += hx;
                 rs.s[a][b][3] += hy;
+                if constexpr (kZ) {
+                    int hz, lz;
+                    AccFix::split2(tz, wh, ws, hz, lz);
+                    rs.s[a][b][4] += lz;
+                    rs.s[a][b][5] += hz;
+                }
             }
         }
     }
@@ -774,7 +796,7 @@ __device__ __forceinline__ int stencil_base(float xi) {
     return (int)floor(xi) - (P - 1) / 2;
 }
 
-template <int P, bool kFused>
+template <int P, bool kFused, bool kSpecies, bool kZ>
 __global__ void __launch_bounds__(kThreads, 4)
 k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __restrict__ x,
                  const float* __restrict__ y, float* __restrict__ xo, float* __restrict__ yo,
@@ -782,11 +804,15 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                  const float* __restrict__ vx, const float* __restrict__ vy,
                  float* __restrict__ vxo, float* __restrict__ vyo, const int* __restrict__ off,
                  int nsplit, const float2* __restrict__ F, AccFix acc,
-                 double* __restrict__ diag, unsigned int* __restrict__ err) {
-    constexpr int NF = kFused ? 8 : 4;  // values loaded per particle
+                 double* __restrict__ diag, unsigned int* __restrict__ err,
+                 const int32_t* __restrict__ sp, BinSpecies bs, const float* __restrict__ vz,
+                 AccFix accz) {
+    static_assert(!(kZ && kFused), "2D-3V runs the binned deposit on its own");
+    constexpr int NF = kFused ? 8 : (kZ ? 5 : 4);  // values loaded per particle
+    constexpr int NQ = kZ ? 6 : 4;                 // region planes
     extern __shared__ float4 bin_smem[];
     __shared__ int wsum[33];
-    const BinLayout L = bin_layout(tg, P, kFused);
+    const BinLayout L = bin_layout(tg, P, kFused, kZ);
     char* base = reinterpret_cast<char*>(bin_smem);
     float4* stage = bin_smem;
     const float4* sf = reinterpret_cast<const float4*>(base + L.fields);
@@ -794,6 +820,7 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
     uint16_t* sidx = reinterpret_cast<uint16_t*>(base + L.idx);
     int* racc = reinterpret_cast<int*>(base + L.racc);
     int* cnt = reinterpret_cast<int*>(base + L.cnt);
+    float* stz = reinterpret_cast<float*>(base + L.stz);
 
     const int tt = tg.t * tg.t;
     const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
@@ -802,10 +829,10 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
     if (p0 == p1) return;  // uniform for the CTA
     const int rx = tg.rx, ry = tg.ry, R = rx * ry;
     if (threadIdx.x < NF) {  // the CTA's particles come to L2 meanwhile
-        const float* arr[8] = {x, y, vx, vy, px, py, vxo, vyo};
+        const float* arr[8] = {x, y, vx, vy, kZ ? vz : px, py, vxo, vyo};
         prefetch_l2(arr[threadIdx.x] + p0, (size_t)(p1 - p0) * sizeof(float));
     }
-    for (int k = threadIdx.x; k < 4 * R; k += kThreads) racc[k] = 0;
+    for (int k = threadIdx.x; k < NQ * R; k += kThreads) racc[k] = 0;
     for (int k = threadIdx.x; k <= R; k += kThreads) cnt[k] = 0;
     const int tx = tile / tg.nty, ty = tile - tx * tg.nty;
     // region origin, reduced into [0, n): then gi - bi lies in (-n, n) and bi + ri in
@@ -855,6 +882,8 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                     r[5] = py[p];
                     r[6] = vxo[p];
                     r[7] = vyo[p];
+                } else if (kZ) {
+                    r[NF - 1] = vz[p];
                 }
             }
         };
@@ -870,7 +899,15 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
             float xs = cur[0], ys = cur[1], vxs = cur[2], vys = cur[3];
             int key = -1;
             bool ok = true;
-            if (kFused) {
+            int sidx_p = 0;  // the particle's species (kSpecies)
+            if (kSpecies) {
+                sidx_p = sp[p];
+                if ((unsigned)sidx_p >= (unsigned)bs.n) {
+                    bad |= ERR_NONFINITE;
+                    ok = false;
+                }
+            }
+            if (kFused && ok) {
                 const float xi = rmul(xs, idx_), yj = rmul(ys, idy);
                 if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
                     bad |= ERR_NONFINITE;
@@ -879,8 +916,20 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                     float f[8];
                     gather_region<P>(g, sf, F, bi, bj, rx, ry, xi, yj, f);
                     float Px, Py;
-                    push_core(pp, f, cur[4], cur[5], cur[2], cur[3], cur[6], cur[7], bad, kin, Px,
-                              Py, vxs, vys);
+                    if (kSpecies) {  // the species' charge and mass, its weight on the energy
+                        PushT<float> ps = pp;
+                        ps.q = bs.q[sidx_p];
+                        ps.qdt = bs.qdt[sidx_p];
+                        ps.mc2 = bs.mc2[sidx_p];
+                        ps.m = bs.m[sidx_p];
+                        double ks = 0.0;
+                        push_core(ps, f, cur[4], cur[5], cur[2], cur[3], cur[6], cur[7], bad, ks,
+                                  Px, Py, vxs, vys);
+                        kin += bs.w[sidx_p] * ks;
+                    } else {
+                        push_core(pp, f, cur[4], cur[5], cur[2], cur[3], cur[6], cur[7], bad,
+                                  kin, Px, Py, vxs, vys);
+                    }
                     px[p] = Px;
                     py[p] = Py;
                     vxo[p] = vxs;
@@ -892,6 +941,13 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                 ys = move_pos(ys, vys, dt, ly);
                 xo[p] = xs;
                 yo[p] = ys;
+                float vzs = kZ ? cur[NF - 1] : 0.f;
+                if (kSpecies) {  // each contribution carries the particle's q_s w_s
+                    vxs = rmul(vxs, bs.qw[sidx_p]);
+                    vys = rmul(vys, bs.qw[sidx_p]);
+                    if (kZ) vzs = rmul(vzs, bs.qw[sidx_p]);
+                }
+                if (kZ) stz[i] = vzs;
                 const float xi = rmul(xs, idx_), yj = rmul(ys, idy);
                 if (!in_domain(xi, g.nx) || !in_domain(yj, g.ny)) {
                     bad |= ERR_NONFINITE;
@@ -915,6 +971,13 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                             for (int b = 0; b <= P; ++b)
                                 acc.add2((size_t)gi * g.ny + wrap_idx(iy + b, g.ny), tx_, ty_,
                                          wy[b]);
+                            if (kZ) {
+                                const float tz_ = rmul(vzs, wx[a]);
+#pragma unroll
+                                for (int b = 0; b <= P; ++b)
+                                    accz.add1f((size_t)gi * g.ny + wrap_idx(iy + b, g.ny), tz_,
+                                               wy[b]);
+                            }
                         }
                     }
                 }
@@ -952,7 +1015,15 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
         {
             const int per = (total + kThreads - 1) / kThreads;
             const int k0 = min(total, slice * per), k1 = min(total, k0 + per);
-            if constexpr (P == 2) {
+            if constexpr (kZ) {  // six planes: one stencil row a pass
+                bin_slice_rows<P, 0, 1, true>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R, stz);
+                bin_slice_rows<P, 1, 2, true>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R, stz);
+                bin_slice_rows<P, 2, 3, true>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R, stz);
+                if constexpr (P >= 3)
+                    bin_slice_rows<P, 3, 4, true>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R, stz);
+                if constexpr (P == 4)
+                    bin_slice_rows<P, 4, 5, true>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R, stz);
+            } else if constexpr (P == 2) {
                 bin_slice_rows<P, 0, 3>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
             } else {
                 bin_slice_rows<P, 0, 2>(stage, kr, sidx, k0, k1, idx_, idy, acc, racc, ry, R);
@@ -966,8 +1037,14 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
         for (int k = threadIdx.x; k < R; k += kThreads) {
             const int lx_ = racc[k], ly_ = racc[R + k];
             const int hx = racc[2 * R + k], hy = racc[3 * R + k];
-            if (!(lx_ | ly_ | hx | hy)) continue;
+            int lz = 0, hz = 0;
+            if (kZ) {
+                lz = racc[4 * R + k];
+                hz = racc[5 * R + k];
+            }
+            if (!(lx_ | ly_ | hx | hy | lz | hz)) continue;
             racc[k] = racc[R + k] = racc[2 * R + k] = racc[3 * R + k] = 0;
+            if (kZ) racc[4 * R + k] = racc[5 * R + k] = 0;
             const int ri = k / ry, rj = k - ri * ry;
             int gi = bi + ri, gj = bj + rj;
             if (gi >= g.nx) gi -= g.nx;
@@ -977,6 +1054,10 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
             const long long sy = (long long)hy * (1ll << kLoBits) + (long long)ly_;
             if (sx) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].x), (unsigned long long)sx);
             if (sy) atomicAdd(reinterpret_cast<unsigned long long*>(&acc.J[node].y), (unsigned long long)sy);
+            if (kZ) {
+                const long long sz = (long long)hz * (1ll << kLoBits) + (long long)lz;
+                if (sz) atomicAdd(reinterpret_cast<unsigned long long*>(&accz.J[node].x), (unsigned long long)sz);
+            }
         }
         for (int k = threadIdx.x; k <= R; k += kThreads) cnt[k] = 0;
         __syncthreads();
@@ -1511,9 +1592,9 @@ cudaError_t launch_gather_push_tiled(int p, const ParticleGeom& g, const PushPar
     return e;
 }
 
-bool deposit_binned_fits(const TileGeom& tg, int p, bool fused) {
-    return tg.rx > p && tg.ry > p && tg.rx * tg.ry < (1 << 16) &&
-           bin_layout(tg, p, fused).bytes <= kBinSmemMax;
+bool deposit_binned_fits(const TileGeom& tg, int p, bool fused, bool z) {
+    return tg.rx > p && tg.ry > p && tg.rx * tg.ry < (1 << 16) && !(fused && z) &&
+           bin_layout(tg, p, fused, z).bytes <= kBinSmemMax;
 }
 
 cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams& pp,
@@ -1522,36 +1603,63 @@ cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams
                                   const float* vy, float* vxo, float* vyo, int64_t n,
                                   const int* off, const void* fields4, void* j, float scale,
                                   double* diag, unsigned int* err, cudaStream_t s, bool fused,
-                                  int per_cta) {
+                                  int per_cta, const int32_t* sp, const SpeciesParams* spp,
+                                  const float* vz, void* jz) {
     if (n == 0) return cudaSuccess;
-    if (!deposit_binned_fits(tg, p, fused) || per_cta < 1) return cudaErrorInvalidValue;
+    const bool z = vz != nullptr;
+    if (z && (fused || !jz)) return cudaErrorInvalidValue;
+    const bool species = sp && spp && spp->n > 0;
+    BinSpecies bs{};
+    PushT<float> ptyped = typed<float>(pp);
+    if (species) {
+        bs.n = spp->n;
+        for (int k = 0; k < spp->n; ++k) {
+            bs.qw[k] = (float)spp->qw[k];
+            bs.q[k] = (float)spp->q[k];
+            bs.qdt[k] = (float)(spp->q[k] * pp.dt);
+            bs.mc2[k] = (float)(spp->m[k] * pp.c * pp.c);
+            bs.m[k] = spp->m[k];
+            bs.w[k] = spp->w[k];
+        }
+        ptyped.weight = 1.0;  // the energy sum carries each particle's w_s already
+    }
+    if (!deposit_binned_fits(tg, p, fused, z) || per_cta < 1) return cudaErrorInvalidValue;
     const int ntiles = tg.ntx * tg.nty;
     int nsplit = (int)((n + (int64_t)ntiles * per_cta - 1) / ((int64_t)ntiles * per_cta));
     if (nsplit < 1) nsplit = 1;
     if (nsplit > 64) nsplit = 64;
     const int blocks = ntiles * nsplit;
-    const size_t smem = (size_t)bin_layout(tg, p, fused).bytes;
+    const size_t smem = (size_t)bin_layout(tg, p, fused, z).bytes;
     const AccFix acc = AccFix::make(j, scale);
+    const AccFix accz = AccFix::make(jz, scale);
     cudaError_t e = cudaSuccess;
-#define GPIC_BINNED(PP, FF)                                                                    \
+#define GPIC_BINNED(PP, FF, SS, ZZ)                                                            \
     {                                                                                          \
         static const cudaError_t attr = cudaFuncSetAttribute(                                  \
-            k_deposit_binned<PP, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemMax); \
+            k_deposit_binned<PP, FF, SS, ZZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+            kBinSmemMax);                                                                      \
         e = attr;                                                                              \
         if (e == cudaSuccess)                                                                  \
-            e = launch_pdl(k_deposit_binned<PP, FF>, dim3(blocks), dim3(kThreads), smem, s,    \
-                           typed<float>(g), typed<float>(pp), tg, x, y, xo, yo, px, py, vx,    \
-                           vy, vxo, vyo, off, nsplit, (const float2*)fields4, acc, diag, err); \
+            e = launch_pdl(k_deposit_binned<PP, FF, SS, ZZ>, dim3(blocks), dim3(kThreads),     \
+                           smem, s, typed<float>(g), ptyped, tg, x, y, xo, yo, px, py, vx, vy, \
+                           vxo, vyo, off, nsplit, (const float2*)fields4, acc, diag, err,      \
+                           species ? sp : nullptr, bs, vz, accz);                              \
     }
+#define GPIC_BINNED_S(PP, FF)                       \
+    if (species && z) GPIC_BINNED(PP, false, true, true) \
+    else if (z) GPIC_BINNED(PP, false, false, true)     \
+    else if (species) GPIC_BINNED(PP, FF, true, false)  \
+    else GPIC_BINNED(PP, FF, false, false)
     switch (p * 2 + (fused ? 1 : 0)) {
-        case 4: GPIC_BINNED(2, false) break;
-        case 5: GPIC_BINNED(2, true) break;
-        case 6: GPIC_BINNED(3, false) break;
-        case 7: GPIC_BINNED(3, true) break;
-        case 8: GPIC_BINNED(4, false) break;
-        case 9: GPIC_BINNED(4, true) break;
+        case 4: GPIC_BINNED_S(2, false) break;
+        case 5: GPIC_BINNED_S(2, true) break;
+        case 6: GPIC_BINNED_S(3, false) break;
+        case 7: GPIC_BINNED_S(3, true) break;
+        case 8: GPIC_BINNED_S(4, false) break;
+        case 9: GPIC_BINNED_S(4, true) break;
         default: return cudaErrorInvalidValue;
     }
+#undef GPIC_BINNED_S
 #undef GPIC_BINNED
     return e;
 }
@@ -1586,6 +1694,20 @@ cudaError_t launch_scatter_by_id(const T* src, const int32_t* id, double* dst, i
                                  cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_scatter_by_id<T><<<blocks_for(n), kThreads, 0, s>>>(src, id, dst, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_by_id_i32(const int32_t* __restrict__ src, const int32_t* __restrict__ id,
+                                    int32_t* __restrict__ dst, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        dst[id[k]] = src[k];
+}
+
+cudaError_t launch_scatter_by_id_i32(const int32_t* src, const int32_t* id, int32_t* dst,
+                                     int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_scatter_by_id_i32<<<blocks_for(n), kThreads, 0, s>>>(src, id, dst, n);
     return cudaGetLastError();
 }
 

@@ -142,9 +142,6 @@ pic_status validate(const pic_config* c, const pic_particles_in* in) {
             !std::isfinite(c->species_w[i]) || c->species_w[i] < 0)
             return fail(h, PIC_ERR_INVALID_ARG,
                         "species %d: q finite, m finite and > 0, weight finite and >= 0", i);
-    if ((c->vdim == 3 || c->nspecies > 0) && c->sort_interval > 0)
-        return fail(h, PIC_ERR_UNSUPPORTED,
-                    "2D-3V and species tables run on the unsorted kernels (sort_interval 0)");
     if (c->charge != PIC_CHARGE_CONTINUITY && c->charge != PIC_CHARGE_DEPOSIT)
         return fail(h, PIC_ERR_INVALID_ARG, "unknown charge source %d", c->charge);
     if (c->charge == PIC_CHARGE_DEPOSIT &&
@@ -283,6 +280,11 @@ pic_status alloc_state(pic_handle* h) {
     }
     if (h->spp.n > 0)
         CK(dalloc(h, (void**)&h->species, (size_t)std::max<int64_t>(h->n, 1) * sizeof(int32_t)));
+    if (h->sorting && h->spp.n > 0)  // the sort's second set
+        CK(dalloc(h, (void**)&h->species_alt,
+                  (size_t)std::max<int64_t>(h->n, 1) * sizeof(int32_t)));
+    if (h->sorting && h->vdim == 3)
+        for (int a = 0; a < 3; ++a) CK(dalloc(h, &h->z_alt[a], pn));
     CK(dalloc(h, (void**)&h->J, h->jbytes));
     if (h->fp32) {
         CK(dalloc(h, (void**)&h->Jalt, h->ng * sizeof(double2)));
@@ -492,8 +494,14 @@ constexpr int kBinPerCta = 2048;
 // Whether the gather + push of the step now finishing may run fused with the next step's
 // move + deposit: the sorted FP32 form (2D-2V, one species) when the tile regions fit the
 // fused kernel's shared memory.  A sort due at the next step then follows its deposit.
+// The sorted FP32 form's deposit runs in the binned pass (with J_z in 2D-3V) when the
+// tiles' regions fit its shared memory.
+bool binned_deposit(const pic_handle* h) {
+    return h->sorting && h->fp32 && deposit_binned_fits(h->tg, h->p, false, h->vdim == 3);
+}
+
 bool fuse_next(const pic_handle* h) {
-    if (!(h->sorting && h->fp32) || h->vdim != 2 || h->spp.n > 0) return false;
+    if (!(h->sorting && h->fp32) || h->vdim != 2) return false;
     return deposit_binned_fits(h->tg, h->p, true);
 }
 
@@ -504,6 +512,8 @@ pic_status gather_push_step(pic_handle* h, bool fuse, bool defer);
 // and deposit are done).  The current sums do not depend on the order of the particles.
 pic_status sort_particles(pic_handle* h, bool moved) {
     void** cur[8] = {&h->x, &h->y, &h->px, &h->py, &h->v[0][0], &h->v[0][1], &h->v[1][0], &h->v[1][1]};
+    void** curz[3] = {&h->pz, &h->vz[0], &h->vz[1]};
+    const bool z3 = h->vdim == 3, spec = h->spp.n > 0;
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
         SortArrays<T> src, dst;
@@ -513,12 +523,24 @@ pic_status sort_particles(pic_handle* h, bool moved) {
         }
         src.id = h->id;
         dst.id = h->id_alt;
+        if (spec) {
+            src.sp = h->species;
+            dst.sp = h->species_alt;
+        }
+        if (z3)
+            for (int a = 0; a < 3; ++a) {
+                src.z[a] = (T*)*curz[a];
+                dst.z[a] = (T*)h->z_alt[a];
+            }
         // cur[4 + 2 vcur] is v^n_x, the velocity of this step's move
         return launch_tile_sort<T>(h->tg, src, dst, h->n, moved ? -1 : 4 + 2 * h->vcur,
                                    h->keys, h->hist, h->off, h->cursor, h->bsum, h->s);
     }));
     for (int a = 0; a < 8; ++a) std::swap(*cur[a], h->alt[a]);
     std::swap(h->id, h->id_alt);
+    if (spec) std::swap(h->species, h->species_alt);
+    if (z3)
+        for (int a = 0; a < 3; ++a) std::swap(*curz[a], h->z_alt[a]);
     h->launches_now += 4;
     return PIC_OK;
 }
@@ -692,12 +714,15 @@ pic_status pic_deposit(pic_handle* h) {
     } else {
         CK(cudaMemsetAsync(h->J, 0, h->jbytes, h->s));
     }
+    if (h->vdim == 3 && binned_deposit(h))  // the binned pass adds J_z to it
+        CK(cudaMemsetAsync(h->Jz, 0, h->jbytes, h->s));
     h->launches_now += 1;
     TimedScope ts(h, PIC_KT_DEPOSIT);
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
-        if (h->sorting && h->fp32 && deposit_binned_fits(h->tg, h->p, false)) {
+        if (binned_deposit(h)) {  // 2D-3V: J_z in the same pass
             const int vo = 1 - h->vcur;
+            const bool z3 = h->vdim == 3;
             return launch_deposit_binned(h->p, h->geom, h->push, h->tg, (const float*)h->x,
                                          (const float*)h->y, (float*)h->x, (float*)h->y,
                                          (float*)h->px, (float*)h->py,
@@ -705,7 +730,9 @@ pic_status pic_deposit(pic_handle* h) {
                                          (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
                                          (float*)h->v[vo][1], h->n, h->off, nullptr, h->J,
                                          h->fix_scale_j, h->diag, h->err, h->s, false,
-                                         kBinPerCta);
+                                         kBinPerCta, h->species, &h->spp,
+                                         z3 ? (const float*)h->vz[h->vcur] : nullptr,
+                                         z3 ? h->Jz : nullptr);
         }
         const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
         if constexpr (sizeof(T) == 4) {
@@ -720,7 +747,7 @@ pic_status pic_deposit(pic_handle* h) {
                                               h->ng, h->fix64_scale_j, h->err, h->s, sp, &h->spp);
         }
     }));
-    if (h->vdim == 3) {  // J_z of the moved particles
+    if (h->vdim == 3 && !binned_deposit(h)) {  // J_z of the moved particles
         CK(cudaMemsetAsync(h->Jz, 0, h->jbytes, h->s));
         CK(by_prec(h, [&](auto t) {
             using T = decltype(t);
@@ -934,8 +961,9 @@ pic_status gather_push_step(pic_handle* h, bool fuse, bool defer) {
                                  (float*)h->py, (const float*)h->v[h->vcur][0],
                                  (const float*)h->v[h->vcur][1], (float*)h->v[vo][0],
                                  (float*)h->v[vo][1], h->n, h->off, h->G, h->Jalt,
-                                 h->fix_scale_j, h->diag, h->err, h->s, true, kBinPerCta));
-    } else if (h->sorting && h->fp32) {
+                                 h->fix_scale_j, h->diag, h->err, h->s, true, kBinPerCta,
+                                 h->species, &h->spp));
+    } else if (h->sorting && h->fp32 && h->vdim == 2 && h->spp.n == 0) {
         TimedScope ts(h, PIC_KT_GATHER);
         CK(launch_gather_push_tiled(h->p, h->geom, pp, h->tg, (const float*)h->x,
                                     (const float*)h->y, (float*)h->px, (float*)h->py,
@@ -1366,6 +1394,15 @@ pic_status pic_read_particles_z(pic_handle* h, double* pz, double* vz, double* v
     double* dst[3] = {pz, vz, vz_old};
     for (int i = 0; i < 3 && h->n > 0; ++i) {
         if (!dst[i]) continue;
+        if (h->sorting) {  // restore the order given to pic_init
+            CK(by_prec(h, [&](auto t) {
+                using T = decltype(t);
+                return launch_scatter_by_id<T>((const T*)src[i], h->id, h->stage, h->n, h->s);
+            }));
+            CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            continue;
+        }
         if (h->fp32) {
             CK(launch_convert<float, double>((const float*)src[i], h->stage, h->n, h->s));
             CK(cudaMemcpyAsync(dst[i], h->stage, nb, cudaMemcpyDefault, h->s));
@@ -1374,9 +1411,15 @@ pic_status pic_read_particles_z(pic_handle* h, double* pz, double* vz, double* v
             CK(cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyDefault, h->s));
         }
     }
-    if (species && h->n > 0)
-        CK(cudaMemcpyAsync(species, h->species, (size_t)h->n * sizeof(int32_t), cudaMemcpyDefault,
+    if (species && h->n > 0) {
+        const int32_t* from = h->species;
+        if (h->sorting) {  // restore the order given to pic_init (in the staging buffer)
+            CK(launch_scatter_by_id_i32(h->species, h->id, (int32_t*)h->stage, h->n, h->s));
+            from = (const int32_t*)h->stage;
+        }
+        CK(cudaMemcpyAsync(species, from, (size_t)h->n * sizeof(int32_t), cudaMemcpyDefault,
                            h->s));
+    }
     return check_device_error(h);
 }
 

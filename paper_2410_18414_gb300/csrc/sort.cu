@@ -188,6 +188,11 @@ k_sort_scatter(SortArrays<T> src, SortArrays<T> dst, const int* __restrict__ key
                 dst.a[a][q] = v[a];
             }
             dst.id[q] = src.id[p];
+            if (src.sp) dst.sp[q] = src.sp[p];
+            if (src.z[0]) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) dst.z[a][q] = src.z[a][p];
+            }
         }
     }
 }

@@ -10,7 +10,11 @@
 - P_z is never updated (d/dz = 0): bit for bit its t = 0 value.  Gauge and continuity
   residuals stay at roundoff.  The diagnostics' W_B, W_E (with B_x, B_y and E_z) and the
   per-species kinetic energy equal the oracle's energies.
-- Sorting with 2D-3V or a species table is PIC_ERR_UNSUPPORTED.
+- Sorted runs (tile sort every 3 steps) with 2D-3V and/or a species table, in both forms,
+  equal the unsorted runs bit for bit (both forms sum their deposits as integers, and
+  every particle's arithmetic is the same whatever kernel runs it): the FP32 form's
+  2D-2V species runs take the fused binned kernel, 2D-3V runs the general particle
+  kernels on the sorted order.  A sorted FP64 run also matches the oracle at 1e-12.
 """
 import numpy as np
 import pytest
@@ -171,9 +175,43 @@ def test_3v_pz_constant_residuals_and_energies(device, stepper, kw, okw):
         assert abs(d[k] / e[ko] - 1.0) <= 1e-11, (k, d[k], e[ko])
 
 
-def test_3v_and_species_need_the_unsorted_kernels(device):
-    c = _case(n=256, seed=5)
-    for vdim in (3, 2):
-        with pytest.raises(pic.PicError) as e:
-            _gpu(device, c, "bdf", dict(bdf_order=2), vdim=vdim, sort=4)
-        assert e.value.status == 2
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_FIX64], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("vdim", [2, 3], ids=["2v", "3v"])
+def test_sorted_species_runs_equal_unsorted(device, precision, vdim):
+    c = _case(n=24000, seed=6, nx=48, ny=48)
+    out = []
+    for sort in (0, 3):
+        with _gpu(device, c, "bdf", dict(bdf_order=2), vdim=vdim, precision=precision,
+                  sort=sort) as sim:
+            sim.set_kernel_timing(64)
+            sim.step(13)
+            fused = sim.kernel_time("gather_deposit")[1]
+            sim.set_kernel_timing(0)
+            parts = dict(sim.particles())  # with the z arrays and species indices
+            fields = {f: sim.field(f) for f in FIELDS + (Z_FIELDS if vdim == 3 else ())}
+            out.append((parts, fields, fused))
+    (pa, fa, fused0), (pb, fb, fused1) = out
+    # the sorted FP32 2D-2V run steps through the fused binned kernel with its species
+    assert fused0 == 0
+    assert (fused1 > 0) == (precision == pic.FP32_FIX64 and vdim == 2)
+    for k, v in pa.items():
+        assert np.array_equal(pb[k], v), k
+    for f, v in fa.items():
+        assert np.array_equal(fb[f], v), f
+
+
+def test_sorted_3v_species_fp64_matches_oracle(device):
+    c = _case(seed=7)
+    ocfg, st = _oracle(c, "bdf", dict(bdf_order=2))
+    with _gpu(device, c, "bdf", dict(bdf_order=2), sort=3) as sim:
+        sim.step(10)
+        got = sim.particles()
+        fields = {f: sim.field(f) for f in FIELDS + Z_FIELDS}
+    assert np.array_equal(got["species"], c["sp"])
+    errs = {"x": wrapped_rel(got["x"], st.x, c["lx"]), "y": wrapped_rel(got["y"], st.y, c["ly"])}
+    for k in PARTICLE_KEYS + Z_KEYS:
+        errs[k] = rel(got[k], getattr(st, k))
+    for f in FIELDS + Z_FIELDS:
+        errs[f] = rel(fields[f], st.grids[f])
+    bad = {k: v for k, v in errs.items() if not v <= 1e-12}
+    assert not bad, bad

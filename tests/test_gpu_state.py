@@ -41,6 +41,12 @@ CASES = [
      3, 5),
     ("fp64-cdf2", dict(stepper="cdf2"), 3, 5),
     ("fp64-bdf2-sorted", dict(stepper="bdf", bdf_order=2, sort_interval=3), 2, 4),
+    ("fp32-bdf2-sorted-species", dict(stepper="bdf", bdf_order=2, precision=pic.FP32_FIX64,
+                                      sort_interval=3,
+                                      species=((-1.0, 1.0, 1.0 / 8192), (1.0, 4.0, 1.0 / 8192))),
+     2, 5),
+    ("fp32-cdf2-sorted-3v", dict(stepper="cdf2", precision=pic.FP32_FIX64, sort_interval=2,
+                                 vdim=3), 2, 5),
     ("fp64-bdf2-3v", dict(stepper="bdf", bdf_order=2, vdim=3), 2, 4),
 ]
 
