@@ -175,6 +175,30 @@ typedef struct {
 pic_status pic_init(const pic_config *cfg, const pic_particles_in *init, void *cuda_stream,
                     pic_handle **out);
 
+/* Caller-owned particle state (pic_init_bound): eight device arrays of n values each in
+ * the storage type of cfg->precision (double for PIC_FP64, float for PIC_FP32_FIX64),
+ * for example torch tensors.  On entry x, y, vx, vy hold x^0 and v^0; px, py, vx_old and
+ * vy_old are written by the t = 0 set-up (P^0 and v^{-1}). */
+typedef struct {
+    void *x, *y, *px, *py, *vx, *vy, *vx_old, *vy_old;
+    int64_t n;
+} pic_particles_bound;
+
+/* As pic_init, but the handle steps the caller's arrays in place: no copy in, no copy
+ * out.  The library never frees them; they must stay allocated until pic_destroy.  Each
+ * step writes v^{n+1} over the pair holding v^{n-1}, so the two velocity pairs exchange
+ * roles every step: pic_velocity_slot says which pair holds v^n.  Only for unsorted
+ * (sort_interval 0), 2D-2V, single-species configurations, else PIC_ERR_UNSUPPORTED;
+ * PIC_ERR_INVALID_ARG for NULL arrays (n > 0) or arrays that are not device memory.
+ * pic_read_particles, checkpoints, ensembles and the adjoint work as for pic_init. */
+pic_status pic_init_bound(const pic_config *cfg, const pic_particles_bound *particles,
+                          void *cuda_stream, pic_handle **out);
+
+/* 0 when (vx, vy) of pic_init_bound hold v^n (and (vx_old, vy_old) v^{n-1}), 1 when the
+ * roles are exchanged; the same index for handles of pic_init (internal buffers).  -1 for
+ * NULL. */
+int32_t pic_velocity_slot(const pic_handle *h);
+
 /* Algorithm 1, the position update and deposit: move every particle with v^n
  * (wrapping into the domain) and deposit J^{n+1} with the new positions and v^n.
  * Re-sorts the particles first when sort_interval says so. */

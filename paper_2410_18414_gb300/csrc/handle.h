@@ -33,6 +33,7 @@ struct pic_handle {
     void *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr;
     void* v[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int vcur = 0;             // v[vcur] holds v^n, v[1 - vcur] holds v^{n-1}
+    bool bound = false;       // x, y, px, py, v are the caller's arrays (pic_init_bound)
     double* stage = nullptr;  // FP64 staging for conversions (n values)
     // tile sort (sort_interval > 0): second set of particle arrays, original indices, keys
     bool sorting = false;

@@ -244,12 +244,14 @@ pic_status alloc_state(pic_handle* h) {
     const pic_config& c = h->cfg;
     const size_t cs = 2 * h->rsz;
     const size_t pn = (size_t)std::max<int64_t>(h->n, 1) * h->rsz;
-    CK(dalloc(h, &h->x, pn));
-    CK(dalloc(h, &h->y, pn));
-    CK(dalloc(h, &h->px, pn));
-    CK(dalloc(h, &h->py, pn));
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->v[b][k], pn));
+    if (!h->bound) {  // else the caller's arrays, set by pic_init_bound
+        CK(dalloc(h, &h->x, pn));
+        CK(dalloc(h, &h->y, pn));
+        CK(dalloc(h, &h->px, pn));
+        CK(dalloc(h, &h->py, pn));
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->v[b][k], pn));
+    }
     CK(dalloc(h, (void**)&h->stage, (size_t)std::max<int64_t>(h->n, 1) * sizeof(double)));
     if (h->sorting) {
         const size_t ni = (size_t)std::max<int64_t>(h->n, 1) * sizeof(int);
@@ -418,7 +420,7 @@ pic_status setup(pic_handle* h, const pic_particles_in* in) {
         CK(cudaMemcpyAsync(h->species, in->species, (size_t)n * sizeof(int32_t), cudaMemcpyDefault,
                            h->s));
     const int32_t* sp = h->spp.n > 0 ? h->species : nullptr;
-    for (int i = 0; i < narr && n > 0; ++i) {
+    for (int i = 0; i < narr && n > 0 && !h->bound; ++i) {  // bound: in place already
         if (h->fp32) {
             CK(cudaMemcpyAsync(h->stage, src[i], nb64, cudaMemcpyDefault, h->s));
             CK(launch_convert<double, float>(h->stage, (float*)dst[i], n, h->s));
@@ -549,8 +551,40 @@ pic_status sort_particles(pic_handle* h, bool moved) {
 
 extern "C" {
 
+static pic_status init_impl(const pic_config* cfg, const pic_particles_in* init,
+                            const pic_particles_bound* bound, void* stream, pic_handle** out);
+
 pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* stream,
                     pic_handle** out) {
+    return init_impl(cfg, init, nullptr, stream, out);
+}
+
+pic_status pic_init_bound(const pic_config* cfg, const pic_particles_bound* p, void* stream,
+                          pic_handle** out) {
+    if (out) *out = nullptr;
+    if (!cfg || !p) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfg and particles must not be NULL");
+    if (cfg->sort_interval != 0 || (cfg->vdim != 0 && cfg->vdim != 2) || cfg->nspecies != 0)
+        return fail(nullptr, PIC_ERR_UNSUPPORTED,
+                    "bound particle arrays need an unsorted 2D-2V single-species configuration");
+    void* const arr[8] = {p->x, p->y, p->px, p->py, p->vx, p->vy, p->vx_old, p->vy_old};
+    for (int a = 0; a < 8 && p->n > 0; ++a) {
+        if (!arr[a]) return fail(nullptr, PIC_ERR_INVALID_ARG, "bound particle array %d is NULL", a);
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, arr[a]) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();  // a host pointer is not an error of the context
+            return fail(nullptr, PIC_ERR_INVALID_ARG, "bound particle array %d is not device memory",
+                        a);
+        }
+    }
+    // the positions and velocities are read in place; the descriptor only carries n
+    const pic_particles_in in{(const double*)p->x, (const double*)p->y, (const double*)p->vx,
+                              (const double*)p->vy, p->n, nullptr, nullptr};
+    return init_impl(cfg, &in, p, stream, out);
+}
+
+static pic_status init_impl(const pic_config* cfg, const pic_particles_in* init,
+                            const pic_particles_bound* bound, void* stream, pic_handle** out) {
     if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out must not be NULL");
     *out = nullptr;
     pic_status st = validate(cfg, init);
@@ -672,6 +706,17 @@ pic_status pic_init(const pic_config* cfg, const pic_particles_in* init, void* s
         h->fix64_unscale_q = std::ldexp(1.0, kq - 60);
     }
     h->jbytes = h->ng * (h->fp32 ? sizeof(longlong2) : 2 * sizeof(longlong2));
+    if (bound) {
+        h->bound = true;
+        h->x = bound->x;
+        h->y = bound->y;
+        h->px = bound->px;
+        h->py = bound->py;
+        h->v[0][0] = bound->vx;
+        h->v[0][1] = bound->vy;
+        h->v[1][0] = bound->vx_old;
+        h->v[1][1] = bound->vy_old;
+    }
     st = alloc_state(h);
     if (st == PIC_OK) st = setup(h, init);
     if (st != PIC_OK) {
@@ -1430,6 +1475,8 @@ pic_status pic_sync(pic_handle* h) {
 }
 
 int64_t pic_step_count(const pic_handle* h) { return h ? h->step : -1; }
+
+int32_t pic_velocity_slot(const pic_handle* h) { return h ? h->vcur : -1; }
 
 int32_t pic_kernels_per_step(const pic_handle* h) {
     if (!h) return 0;

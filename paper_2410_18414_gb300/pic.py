@@ -70,6 +70,11 @@ class PicParticlesIn(ctypes.Structure):
                 ("species", ctypes.c_void_p)]
 
 
+class PicParticlesBound(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("x", "y", "px", "py", "vx", "vy", "vx_old",
+                                               "vy_old")] + [("n", ctypes.c_int64)]
+
+
 DIAG_HISTORY = 4096  # PIC_DIAG_HISTORY: records the device ring holds
 
 
@@ -101,6 +106,9 @@ def load_library(path=None):
     sig = {
         "pic_init": ([ctypes.POINTER(PicConfig), ctypes.POINTER(PicParticlesIn), vp,
                       ctypes.POINTER(vp)], i32),
+        "pic_init_bound": ([ctypes.POINTER(PicConfig), ctypes.POINTER(PicParticlesBound), vp,
+                            ctypes.POINTER(vp)], i32),
+        "pic_velocity_slot": ([vp], i32),
         "pic_deposit": ([vp], i32),
         "pic_field_solve": ([vp], i32),
         "pic_gather_push": ([vp], i32),
@@ -222,6 +230,50 @@ class Simulation:
             raise PicError(st, self.lib.pic_last_error(None).decode())
         self.h = handle
         self._keep = None
+
+    BOUND_KEYS = ("x", "y", "px", "py", "vx", "vy", "vx_old", "vy_old")
+
+    @classmethod
+    def bound(cls, cfg, arrays, stream=None):
+        """A simulation that steps the caller's CUDA tensors in place (pic_init_bound):
+        `arrays` maps BOUND_KEYS to contiguous CUDA tensors of n values (float64, or
+        float32 for the FP32 form); x, y, vx, vy hold x^0 and v^0.  The tensors must live
+        as long as the simulation (it keeps references).  velocities() names the pair that
+        holds v^n after each step."""
+        import torch
+        sim = cls.__new__(cls)
+        sim.lib = load_library()
+        sim.cfg = cfg
+        dtype = torch.float32 if cfg.precision == FP32_FIX64 else torch.float64
+        n = arrays["x"].numel()
+        for k in cls.BOUND_KEYS:
+            t = arrays[k]
+            if t.dtype != dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise TypeError(f"{k}: a contiguous CUDA {dtype} tensor of {n} values")
+        sim.n = n
+        sim.arrays = dict(arrays)
+        desc = PicParticlesBound(*[arrays[k].data_ptr() for k in cls.BOUND_KEYS], n)
+        handle = ctypes.c_void_p()
+        st = sim.lib.pic_init_bound(ctypes.byref(cfg), ctypes.byref(desc),
+                                    ctypes.c_void_p(stream or 0), ctypes.byref(handle))
+        if st != PIC_OK:
+            raise PicError(st, sim.lib.pic_last_error(None).decode())
+        sim.h = handle
+        sim._keep = None
+        return sim
+
+    @property
+    def velocity_slot(self):
+        """0 while (vx, vy) hold v^n, 1 while (vx_old, vy_old) do (pic_velocity_slot)."""
+        return int(self.lib.pic_velocity_slot(self.h))
+
+    def velocities(self):
+        """Bound simulations: ((vx^n, vy^n), (vx^{n-1}, vy^{n-1})) as the caller's tensors."""
+        a = self.arrays
+        now, old = (("vx", "vy"), ("vx_old", "vy_old"))
+        if self.velocity_slot:
+            now, old = old, now
+        return (a[now[0]], a[now[1]]), (a[old[0]], a[old[1]])
 
     def _check(self, st):
         if st != PIC_OK:

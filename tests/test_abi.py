@@ -58,7 +58,7 @@ def test_struct_layout_matches_header(tmp_path):
         "int main(){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_config),"
         " offsetof(pic_config, lx), offsetof(pic_config, dirk_a), offsetof(pic_config, reserved),"
         " sizeof(pic_diagnostics), sizeof(pic_particles_in), offsetof(pic_diagnostics, step),"
-        " offsetof(pic_config, charge));"
+        " offsetof(pic_config, charge)); printf(\"%zu\\n\", sizeof(pic_particles_bound));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -67,7 +67,7 @@ def test_struct_layout_matches_header(tmp_path):
     py_vals = [ctypes.sizeof(pic.PicConfig), pic.PicConfig.lx.offset, pic.PicConfig.dirk_a.offset,
                pic.PicConfig.reserved.offset, ctypes.sizeof(pic.PicDiagnostics),
                ctypes.sizeof(pic.PicParticlesIn), pic.PicDiagnostics.step.offset,
-               pic.PicConfig.charge.offset]
+               pic.PicConfig.charge.offset, ctypes.sizeof(pic.PicParticlesBound)]
     assert c_vals == py_vals
 
 
@@ -180,3 +180,23 @@ def test_new_struct_fields_match_header(tmp_path):
     assert c_vals == [pic.PicConfig.vdim.offset, pic.PicConfig.nspecies.offset,
                       pic.PicConfig.species_q.offset, pic.PicConfig.species_w.offset,
                       pic.PicParticlesIn.vz.offset, pic.PicParticlesIn.species.offset]
+
+
+def test_bound_arrays_rejected_without_a_device(lib):
+    # pic_init_bound checks its configuration and arrays before any device work: sorted,
+    # 2D-3V and species configurations are unsupported, NULL and host arrays refused
+    base = dict(nx=16, ny=16, lx=1.0, ly=1.0, dt=0.01, p=2, stepper="bdf", bdf_order=2)
+    x = np.zeros(4)
+    host = pic.PicParticlesBound(*([x.ctypes.data] * 8), 4)
+    nulls = pic.PicParticlesBound(*([None] * 8), 4)
+
+    def status(cfg, desc):
+        h = ctypes.c_void_p()
+        return lib.pic_init_bound(ctypes.byref(cfg), ctypes.byref(desc), None, ctypes.byref(h))
+
+    assert status(pic.make_config(**base, sort_interval=4), host) == 2
+    assert status(pic.make_config(**base, vdim=3), host) == 2
+    assert status(pic.make_config(**base, species=((-1.0, 1.0, 1.0),)), host) == 2
+    assert status(pic.make_config(**base), nulls) == 1
+    assert status(pic.make_config(**base), host) == 1
+    assert lib.pic_velocity_slot(None) == -1
