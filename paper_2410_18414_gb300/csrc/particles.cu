@@ -367,6 +367,24 @@ __device__ __forceinline__ void gather_node(T w, const T* g, T* f) {
 //   u = P^{n+1} - q A,  v^{n+1} = c^2 u / sqrt(c^2 |u|^2 + (m c^2)^2)
 // f = (dphi/dx, dphi/dy, Ax, Ay, dAx/dx, dAx/dy, dAy/dx, dAy/dy).  v^{n+1} overwrites
 // v^{n-1}.  Written with explicit roundings, so every kernel gives the same bits.
+// m c^2 (gamma - 1) per unit weight from |u|^2 (u = P - q A), accumulated in FP64.  FP64
+// storage: in FP64 from the identity gamma m c^2 = sqrt(c^2 |u|^2 + (m c^2)^2).  FP32
+// form: in FP32 as c^2 |u|^2 / (m c^2 (gamma + 1)), gamma = sqrt(1 + c^2 |u|^2 / (m c^2)^2),
+// which has no cancellation at small |u| (the FP32 momenta carry 2^-24 relative error
+// already, and the FP64 sqrt per particle would cost the FP32 kernels more than their
+// whole push).
+template <typename T>
+__device__ __forceinline__ double kinetic(T c2, T mc2, double c, double m, T u2) {
+    if constexpr (sizeof(T) == 4) {
+        const float t = __fmul_rn(c2, u2);
+        const float g = __fsqrt_rn(__fadd_rn(1.0f, __fdiv_rn(t, __fmul_rn(mc2, mc2))));
+        return (double)__fdiv_rn(t, __fmul_rn(mc2, __fadd_rn(g, 1.0f)));
+    } else {
+        const double c2d = c * c, mc2d = m * c2d;
+        return sqrt(c2d * (double)u2 + mc2d * mc2d) - mc2d;
+    }
+}
+
 // The push from the particle's values (P^n, v^n, v^{n-1}): returns P^{n+1} and v^{n+1}.
 template <typename T>
 __device__ __forceinline__ void push_core(const PushT<T>& pp, const T* f, T px, T py, T vx, T vy,
@@ -387,10 +405,7 @@ __device__ __forceinline__ void push_core(const PushT<T>& pp, const T* f, T px, 
     vx_new = vxn1;
     vy_new = vyn1;
     if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
-    if (pp.diag) {  // m c^2 (gamma - 1) per unit weight, in FP64 for either storage type
-        const double uxd = ux, uyd = uy, c2d = pp.c * pp.c, mc2d = pp.m * c2d;
-        kin += sqrt(c2d * (uxd * uxd + uyd * uyd) + mc2d * mc2d) - mc2d;
-    }
+    if (pp.diag) kin += kinetic(pp.c2, pp.mc2, pp.c, pp.m, rfma(ux, ux, rmul(uy, uy)));
 }
 
 template <typename T>
@@ -1297,11 +1312,7 @@ k_gather_push3(GeomT<T> g, PushParams pp, const T* __restrict__ x, const T* __re
         vyo[p] = vyn1;
         if (Z3) vzo[p] = rmul(rc, uz);
         if (!isfinite(vxn1) || !isfinite(vyn1)) bad |= ERR_NONFINITE;
-        if (pp.diag) {  // w m c^2 (gamma - 1) in FP64
-            const double c2d = pp.c * pp.c, mc2d = k.m * c2d;
-            const double ud2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-            kin += k.w * (sqrt(c2d * ud2 + mc2d * mc2d) - mc2d);
-        }
+        if (pp.diag) kin += k.w * kinetic(c2, k.mc2, pp.c, k.m, u2);  // w m c^2 (gamma - 1)
     }
     if (bad) atomicOr(err, bad);
     if (pp.diag) {
