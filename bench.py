@@ -197,7 +197,7 @@ def flops_gather_deposit(p):
 # time: when the source has changed since, the bench line reports no traffic.
 TRAFFIC = {
     # (kernel, workload): (bytes per launch, source file, its SHA-1 prefix, profile)
-    ("gather_deposit", "weibel128"): (34.43e6 + 47.36e6, "particles.cu", "ca9dfcabcdc3",
+    ("gather_deposit", "weibel128"): (34.43e6 + 47.36e6, "particles.cu", "69b9977ccf6e",
                                       "profiles/gather_deposit_fused_weibel128.md"),
 }
 
