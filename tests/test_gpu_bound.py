@@ -112,3 +112,20 @@ def test_bound_rejects_sorting_and_wrong_tensors(torch_mod):
               for k in pic.Simulation.BOUND_KEYS}
     with pytest.raises(TypeError):
         pic.Simulation.bound(cfg, arrays)  # FP32 form: float32 tensors
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_FIX64], ids=["fp64", "fp32"])
+def test_bound_empty_particle_set(torch_mod, precision):
+    torch = torch_mod
+    dtype = torch.float32 if precision == pic.FP32_FIX64 else torch.float64
+    cfg = pic.make_config(16, 16, 1.0, 1.0, 0.01, p=3, stepper="bdf", bdf_order=2, weight=1.0,
+                          precision=precision)
+    arrays = {k: torch.zeros(0, dtype=dtype, device="cuda") for k in pic.Simulation.BOUND_KEYS}
+    with pic.Simulation.bound(cfg, arrays,
+                              stream=torch.cuda.current_stream().cuda_stream) as sim:
+        sim.set_diagnostics(1)
+        sim.step(3)
+        for f in ("jx", "phi", "ax", "dphidx"):
+            assert np.max(np.abs(sim.field(f))) == 0.0
+        assert sim.residuals()["kinetic"] == 0.0
+        assert all(len(v) == 0 for v in sim.particles().values())
