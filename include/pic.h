@@ -400,12 +400,11 @@ void pic_destroy(pic_handle *h);
  * The paper states the forward method only; the adjoint is a derived capability.
  *
  * Precision: for an FP64 handle every step of the reverse sweep is FP64.  For an FP32-form
- * handle (PIC_PREC_FP32_FIX64, unsorted) the adjoint is that of the step in exact
- * arithmetic evaluated along the FP32 form's own trajectory: the particle adjoints are
- * FP32 and run through the FP32 weights and push (the fixed-point rounding of the current,
- * piecewise constant, is taken as the identity), while the field adjoints the particles
- * deposit are summed in FP64 and the reverse field solve is FP64 with its own FP64
- * transforms.  The records and checkpointed particle states are then FP32 (32 n bytes a
+ * handle (PIC_FP32_FIX64, unsorted) the adjoint is that of the step in exact arithmetic
+ * evaluated along the FP32 form's own trajectory: the particle adjoints are FP32 and run
+ * through the FP32 weights and push (the fixed-point rounding of the current, piecewise
+ * constant, is taken as the identity), and the field adjoints the particles deposit are
+ * summed in FP32, while the reverse field solve is FP64 with its own FP64 transforms.  The records and checkpointed particle states are then FP32 (32 n bytes a
  * state, 32 nx ny bytes of gather fields a step); seeds and results stay FP64.
  *
  * Memory: the state (particles and field histories) is checkpointed every

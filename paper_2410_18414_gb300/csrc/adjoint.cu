@@ -30,7 +30,8 @@
 // the forward they reverse: FP64 for the plain path, FP32 for the FP32 form (the adjoint
 // of the step in exact arithmetic, evaluated along the FP32 form's trajectory; the
 // fixed-point rounding of its current, piecewise constant, is differentiated as the
-// identity).  The field adjoints they deposit are summed in FP64, and the reverse field
+// identity).  The field adjoints they deposit are summed in FP64 (FP32 form: in FP32, the
+// eight values of a node in two vector atomics, then converted), and the reverse field
 // solve is FP64 in both forms, as the forward's per-mode update is.  Shape weights come
 // from Shape<P, T> (the forward's), their derivatives from the closed forms below.
 #include <algorithm>
@@ -102,7 +103,7 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
                   const T* __restrict__ vy, const T* __restrict__ vxo,
                   const T* __restrict__ vyo, const double* __restrict__ gf,
                   const cplx_t<T>* __restrict__ F, AdjParticlesT<T> ab, double2* __restrict__ Fb,
-                  int64_t n, unsigned int* __restrict__ err) {
+                  float4* __restrict__ Fb32, int64_t n, unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
     const size_t ng = (size_t)g.nx * g.ny;
     const T q = (T)pp.q, qdt = (T)(pp.q * pp.dt), c2 = (T)(pp.c * pp.c),
@@ -168,10 +169,17 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
                 sx += wy[b] * sn;
                 sy += dwy[b] * sn;
                 const T w = wxa * wy[b];
+                if constexpr (sizeof(T) == 4) {  // the node's eight values, four an atomic
+                    atomicAdd(Fb32 + 2 * nd,
+                              make_float4(w * gb[0], w * gb[1], w * gb[2], w * gb[3]));
+                    atomicAdd(Fb32 + 2 * nd + 1,
+                              make_float4(w * gb[4], w * gb[5], w * gb[6], w * gb[7]));
+                } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    atomicAdd(&Fb[k * ng + nd].x, (double)(w * gb[2 * k]));
-                    atomicAdd(&Fb[k * ng + nd].y, (double)(w * gb[2 * k + 1]));
+                    for (int k = 0; k < 4; ++k) {
+                        atomicAdd(&Fb[k * ng + nd].x, (double)(w * gb[2 * k]));
+                        atomicAdd(&Fb[k * ng + nd].y, (double)(w * gb[2 * k + 1]));
+                    }
                 }
             }
             xg += dwx[a] * sx;
@@ -603,6 +611,20 @@ k_adj_init(ParticleGeom g, PushParams pp, const T* __restrict__ x0, const T* __r
     }
 }
 
+// The FP32 form's field adjoints, [node][2] float4 (fields 0-3, 4-7), to the four FP64
+// planes of the reverse field solve: plane k holds fields (2k, 2k + 1) of each node.
+__global__ void k_fb32_to_planes(const float4* __restrict__ fb32, double2* __restrict__ Fb,
+                                 int64_t ng) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ng;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = fb32[2 * k], b = fb32[2 * k + 1];
+        Fb[k] = make_double2(a.x, a.y);
+        Fb[ng + k] = make_double2(a.z, a.w);
+        Fb[2 * ng + k] = make_double2(b.x, b.y);
+        Fb[3 * ng + k] = make_double2(b.z, b.w);
+    }
+}
+
 inline int mode_blocks(const ModeCommon& mc) {
     return (mc.nx * mc.ny + kModeThreads - 1) / kModeThreads;
 }
@@ -622,10 +644,17 @@ cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParam
                                    const T* x1, const T* y1, const T* px1, const T* py1,
                                    const T* vx, const T* vy, const T* vxo, const T* vyo,
                                    const double* gf, const void* F, AdjParticlesT<T> ab,
-                                   double2* Fb, int64_t n, unsigned int* err, cudaStream_t s) {
+                                   double2* Fb, void* fb32, int64_t n, unsigned int* err,
+                                   cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    if (sizeof(T) == 4 && !fb32) return cudaErrorInvalidValue;
     GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gf,
-                      (const cplx_t<T>*)F, ab, Fb, n, err)
+                      (const cplx_t<T>*)F, ab, Fb, (float4*)fb32, n, err)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fb32_to_planes(const void* fb32, double2* Fb, int64_t ng, cudaStream_t s) {
+    k_fb32_to_planes<<<blocks_for(ng), kThreads, 0, s>>>((const float4*)fb32, Fb, ng);
     return cudaGetLastError();
 }
 
@@ -723,7 +752,7 @@ cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cuda
     template cudaError_t launch_adj_push_gather<T>(                                         \
         int, const ParticleGeom&, const PushParams&, const T*, const T*, const T*, const T*, \
         const T*, const T*, const T*, const T*, const double*, const void*, AdjParticlesT<T>, \
-        double2*, int64_t, unsigned int*, cudaStream_t);                                    \
+        double2*, void*, int64_t, unsigned int*, cudaStream_t);                             \
     template cudaError_t launch_adj_deposit_move<T>(int, const ParticleGeom&, const T*,     \
                                                     const T*, const T*, const T*,           \
                                                     const double2*, AdjParticlesT<T>,       \

@@ -56,6 +56,7 @@ struct pic_adjoint {
     void* ab = nullptr;          // particle adjoints, 8 n
     double2* twx = nullptr;      // FP64 twiddles along x and y
     double2* twy = nullptr;
+    void* fb32 = nullptr;        // FP32 form: the field adjoints as summed, [node][8] float
     double2* hb = nullptr;       // history adjoints, nh ng
     double2* role[12] = {};      // CDF-2, DIRK: the history adjoint of each role
     double2* fb = nullptr;       // field-adjoint planes, 4 ng
@@ -235,7 +236,10 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const void* s0v, const void*
                          const double* gf, const void* g) {
     pic_handle* h = a->h;
     const size_t np = a->n, ng = a->ng;
-    CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
+    if (a->f32)
+        CK(cudaMemsetAsync(a->fb32, 0, ng * 8 * sizeof(float), h->s));
+    else
+        CK(cudaMemsetAsync(a->fb, 0, 4 * ng * sizeof(double2), h->s));
     TimedScope tp(h, PIC_KT_ADJ_PUSH);
     CK(by_prec(h, [&](auto t) {
         using T = decltype(t);
@@ -244,8 +248,9 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const void* s0v, const void*
         return launch_adj_push_gather<T>(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np,
                                          s1 + 3 * np, s0 + 4 * np, s0 + 5 * np, s0 + 6 * np,
                                          s0 + 7 * np, gf, g, adjoint_arrays<T>(a), a->fb,
-                                         (int64_t)np, h->err, h->s);
+                                         a->fb32, (int64_t)np, h->err, h->s);
     }));
+    if (a->f32) CK(launch_fb32_to_planes(a->fb32, a->fb, (int64_t)ng, h->s));
     tp.end();
     TimedScope tf(h, PIC_KT_ADJ_FIELD);
     CK(launch_fft_y<double>(a->fb, a->zb, h->nx, h->ny, 4, h->fy, a->twy, -1, 0, h->s));
@@ -355,6 +360,7 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     if (e == cudaSuccess)
         e = aalloc(a, (void**)&a->recf, nrec * kRec * std::max<size_t>(a->n, 1) * sizeof(double));
     if (e == cudaSuccess) e = aalloc(a, &a->ab, sb);
+    if (e == cudaSuccess && a->f32) e = aalloc(a, &a->fb32, a->ng * 8 * sizeof(float));
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->twx, (size_t)h->nx * sizeof(double2));
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->twy, (size_t)h->ny * sizeof(double2));
     if (e == cudaSuccess) e = launch_twiddles<double>(a->twx, h->nx, h->s);

@@ -373,7 +373,11 @@ cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParam
                                    const T* x1, const T* y1, const T* px1, const T* py1,
                                    const T* vx, const T* vy, const T* vxo, const T* vyo,
                                    const double* gf, const void* F, AdjParticlesT<T> ab,
-                                   double2* Fb, int64_t n, unsigned int* err, cudaStream_t s);
+                                   double2* Fb, void* fb32, int64_t n, unsigned int* err,
+                                   cudaStream_t s);
+// The FP32 form's field adjoints (fb32: [node][2] float4, fields 0-3 and 4-7, summed by
+// launch_adj_push_gather<float>) to the four FP64 planes Fb of the reverse field solve.
+cudaError_t launch_fb32_to_planes(const void* fb32, double2* Fb, int64_t ng, cudaStream_t s);
 // Reverse field solve per mode of the stepper `kind` (a StepperKind: ap, cp or dp used,
 // their pointers the history adjoints): Zb = forward transforms of the four Fb planes;
 // writes the packed adjoint current spectrum Js (unnormalised inverse transform -> mesh).
