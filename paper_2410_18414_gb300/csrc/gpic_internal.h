@@ -57,6 +57,9 @@ struct ModeCommon {
     const double* kxt;
     const double* kyt;
     const double* invd;
+    // DIRK: the step as one real 2 x 4 matrix per mode, (u', v') = M (u, v, S^n, S^{n+1}),
+    // dirkm[8 mode + 4 r + k] (built from the stage recurrence on unit inputs); else NULL
+    const double* dirkm;
     // naive update (PIC_CHARGE_DEPOSIT): spectrum of the charge deposited at x^{n+1}
     // (raw shape-weight sums, storage type of the form); NULL: continuity
     const void* zq;
@@ -166,7 +169,7 @@ cudaError_t launch_zfield(const ModeCommon& mc, const BdfParams& bp, const DirkP
 // Fill the wavenumber and inverse-denominator tables of mc (kind: StepperKind).
 cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& bp,
                                const DirkParams& dp, double* kxt, double* kyt, double* invd,
-                               cudaStream_t s);
+                               double* dirkm, cudaStream_t s);
 // Pack two spectra a + i b (scaled by inv_n) for an inverse transform to two real fields.
 template <typename T>
 cudaError_t launch_mode_pack2(const ModeCommon& mc, const void* a, const void* b, int op,

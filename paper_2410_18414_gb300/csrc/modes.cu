@@ -378,6 +378,20 @@ __device__ __forceinline__ void dirk_mode(const DirkParams& dp, double K, double
     }
 }
 
+// The DIRK step of one mode as its matrix (mc.dirkm): u' = M_0 . (u, v, sn, snew),
+// v' = M_1 . (u, v, sn, snew).  The stage recurrence is linear in those four inputs with
+// real coefficients that depend on K alone, so the matrix, built once per mode from the
+// recurrence on unit inputs, is the step (to the rounding of its build).
+__device__ __forceinline__ void dirk_apply(const double* __restrict__ M, zd u, zd v, zd sn,
+                                           zd snew, zd& uo, zd& vo) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(M)),
+                  b = __ldg(reinterpret_cast<const double2*>(M) + 1),
+                  c = __ldg(reinterpret_cast<const double2*>(M) + 2),
+                  d = __ldg(reinterpret_cast<const double2*>(M) + 3);
+    uo = a.x * u + a.y * v + b.x * sn + b.y * snew;
+    vo = c.x * u + c.y * v + d.x * sn + d.y * snew;
+}
+
 template <typename C>
 __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkParams& dp,
                                             const ModeIn& m, double* acc, C* epk, C* out) {
@@ -389,17 +403,16 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkPara
     const zd rho = hload(dp.rho, idx);
     const zd jxn = hload(dp.jx, idx), jyn = hload(dp.jy, idx);
     const zd divjn = div2(m.kx, m.ky, jxn, jyn);
-    zd rho_new = rho;
-    for (int i = 0; i < dp.s; ++i)
-        rho_new = rho_new - (h * dp.b[i]) * ((1.0 - dp.c[i]) * divjn + dp.c[i] * m.divj);
+    // continuity: the stages' sum of b_i ((1 - c_i) div J^n + c_i div J^{n+1}) in closed
+    // form, r0 = sum b_i (1 - c_i), r1 = sum b_i c_i
+    zd rho_new = rho - (h * dp.r0) * divjn - (h * dp.r1) * m.divj;
     if (mc.zq) rho_new = deposited_rho<C>(mc, m);  // the naive update
     zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
     const double ie = 1.0 / mc.eps0;
-    const double* dinv = mc.invd + idx;
-    const size_t stride = (size_t)mc.nx * mc.ny;
-    dirk_mode(dp, m.K, mc.c, h, dinv, stride, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
-    dirk_mode(dp, m.K, mc.c, h, dinv, stride, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
-    dirk_mode(dp, m.K, mc.c, h, dinv, stride, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
+    const double* M = mc.dirkm + (size_t)idx * 8;
+    dirk_apply(M, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
+    dirk_apply(M, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);
+    dirk_apply(M, ay, vay, mc.mu0 * jyn, mc.mu0 * m.jy, ay_new, vay_new);
     if (mc.diag) {
         // section 3.3.2: eps_1, eps_2 and eps_3; Gauss with E = -grad phi - v_A (reported only)
         const double c2h = mc.c * mc.c * h;
@@ -586,8 +599,8 @@ k_zmode(ModeCommon mc, BdfParams bp, DirkParams dp, ZParams zp, const C* __restr
         } else {
             const zd az = hload(zp.az_n, idx), vaz = hload(zp.vaz, idx);
             zd vaz_new;
-            dirk_mode(dp, K, mc.c, mc.dt, mc.invd + idx, (size_t)nmodes, az, vaz,
-                      mc.mu0 * hload(zp.jz_n, idx), mc.mu0 * jz, az_new, vaz_new);
+            dirk_apply(mc.dirkm + (size_t)idx * 8, az, vaz, mc.mu0 * hload(zp.jz_n, idx),
+                       mc.mu0 * jz, az_new, vaz_new);
             ez = -vaz_new;
             hstore(zp.az_n, idx, az_new);
             hstore(zp.vaz, idx, vaz_new);
@@ -605,7 +618,7 @@ k_zmode(ModeCommon mc, BdfParams bp, DirkParams dp, ZParams zp, const C* __restr
 
 __global__ void k_mode_tables(ModeCommon mc, int kind, BdfParams bp, DirkParams dp,
                               double* __restrict__ kxt, double* __restrict__ kyt,
-                              double* __restrict__ invd) {
+                              double* __restrict__ invd, double* __restrict__ dirkm) {
     const int nmodes = mc.nx * mc.ny;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < mc.nx) kxt[idx] = wavenumber(idx, mc.nx, mc.kx_scale);
@@ -620,9 +633,20 @@ __global__ void k_mode_tables(ModeCommon mc, int kind, BdfParams bp, DirkParams 
         const double th = 0.5 * mc.c * mc.c * mc.dt * mc.dt;
         invd[idx] = 1.0 / (1.0 + th * K);
     } else {
+        double dl[kMaxDirk];
         for (int st = 0; st < dp.s; ++st) {
             const double gc = mc.dt * dp.a[st * kMaxDirk + st] * mc.c;
-            invd[(size_t)st * nmodes + idx] = 1.0 / (1.0 + gc * gc * K);
+            dl[st] = 1.0 / (1.0 + gc * gc * K);
+            invd[(size_t)st * nmodes + idx] = dl[st];
+        }
+        // the step matrix: the stage recurrence on the four unit inputs
+        for (int k = 0; k < 4; ++k) {
+            const zd e1{1.0, 0.0}, e0{0.0, 0.0};
+            zd uo, vo;
+            dirk_mode(dp, K, mc.c, mc.dt, dl, 1, k == 0 ? e1 : e0, k == 1 ? e1 : e0,
+                      k == 2 ? e1 : e0, k == 3 ? e1 : e0, uo, vo);
+            dirkm[(size_t)idx * 8 + k] = uo.re;
+            dirkm[(size_t)idx * 8 + 4 + k] = vo.re;
         }
     }
 }
@@ -736,10 +760,11 @@ cudaError_t launch_field_columns(const ModeCommon& mc, int kind, const BdfParams
 }
 cudaError_t launch_mode_tables(const ModeCommon& mc, int kind, const BdfParams& bp,
                                const DirkParams& dp, double* kxt, double* kyt, double* invd,
-                               cudaStream_t s) {
+                               double* dirkm, cudaStream_t s) {
+    if (kind == K_DIRK && !dirkm) return cudaErrorInvalidValue;
     const int n = mc.nx * mc.ny > mc.nx ? mc.nx * mc.ny : mc.nx;
     k_mode_tables<<<(n + kModeThreads - 1) / kModeThreads, kModeThreads, 0, s>>>(
-        mc, kind, bp, dp, kxt, kyt, invd);
+        mc, kind, bp, dp, kxt, kyt, invd, dirkm);
     return cudaGetLastError();
 }
 

@@ -315,6 +315,12 @@ pic_status alloc_state(pic_handle* h) {
         h->mc.kxt = kxt;
         h->mc.kyt = kyt;
         h->mc.invd = invd;
+        h->mc.dirkm = nullptr;
+        if (c.stepper == PIC_STEPPER_DIRK) {  // the per-mode step matrices
+            double* dirkm = nullptr;
+            CK(dalloc(h, (void**)&dirkm, 8 * h->ng * sizeof(double)));
+            h->mc.dirkm = dirkm;
+        }
     }
     CK(dalloc(h, (void**)&h->err, sizeof(unsigned int)));
     CK(cudaMemsetAsync(h->err, 0, sizeof(unsigned int), h->s));
@@ -395,7 +401,8 @@ pic_status alloc_state(pic_handle* h) {
     {
         const int kind = c.stepper == PIC_STEPPER_BDF ? K_BDF : (c.stepper == PIC_STEPPER_CDF2 ? K_CDF2 : K_DIRK);
         CK(launch_mode_tables(h->mc, kind, h->bdf, h->dirk, const_cast<double*>(h->mc.kxt),
-                              const_cast<double*>(h->mc.kyt), const_cast<double*>(h->mc.invd), h->s));
+                              const_cast<double*>(h->mc.kyt), const_cast<double*>(h->mc.invd),
+                              const_cast<double*>(h->mc.dirkm), h->s));
     }
     return PIC_OK;
 }
