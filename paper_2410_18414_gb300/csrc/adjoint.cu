@@ -17,8 +17,8 @@
 //     and x^{n+1} b gets sum_f gb_f grad(sum_node F_f W)
 //   field solve (k_adj_modes / k_adj_columns), per mode, after forward transforms of the
 //     deposited field adjoints: conj(i k) = -i k for the spectral gradients, then the
-//     stepper's recurrences run backwards with their real per-mode multipliers (DIRK's
-//     2 x 4 stage matrix from the forward stage loop on unit inputs), ending in the
+//     stepper's recurrences run backwards with their real per-mode multipliers (DIRK:
+//     the transpose of the forward's per-mode 2 x 4 step matrix), ending in the
 //     adjoint of the current spectrum, inverse-transformed to the mesh
 //   deposit + move (k_adj_deposit_move), per particle:
 //     J = q_p v^n W(x^{n+1}) / (dx dy):  v^n b += gather(Jb),
@@ -372,40 +372,6 @@ __device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const CdfParams& cp
     return mc.jscale * (jxn + zi(jyn));
 }
 
-// The real 2 x 4 matrix of one DIRK wave step of a mode: (u', v') = M (u, v, S^n, S^{n+1}),
-// by running the forward stage recurrence (section 3.3.1, the same closed-form stage
-// solve as the forward) on the four unit inputs; the map is linear with real
-// coefficients, so this is its Jacobian exactly.
-__device__ __forceinline__ void dirk_matrix(const DirkParams& dp, double K, double c, double h,
-                                            const double* dinv, size_t stride, double M[2][4]) {
-    const double c2 = c * c;
-#pragma unroll 1
-    for (int col = 0; col < 4; ++col) {
-        const double u = col == 0, v = col == 1, sn = col == 2, snew = col == 3;
-        double ku[kMaxDirk], kv[kMaxDirk];
-        double uo = u, vo = v;
-        for (int i = 0; i < dp.s; ++i) {
-            double ub = u, vb = v;
-            for (int j = 0; j < i; ++j) {
-                ub += (h * dp.a[i * kMaxDirk + j]) * ku[j];
-                vb += (h * dp.a[i * kMaxDirk + j]) * kv[j];
-            }
-            const double src = (1.0 - dp.c[i]) * sn + dp.c[i] * snew;
-            const double gam = h * dp.a[i * kMaxDirk + i];
-            const double d = dinv[i * stride];
-            const double force = c2 * (src - K * ub);
-            ku[i] = d * (vb + gam * force);
-            kv[i] = d * (force - (gam * c2 * K) * vb);
-        }
-        for (int i = 0; i < dp.s; ++i) {
-            uo += (h * dp.b[i]) * ku[i];
-            vo += (h * dp.b[i]) * kv[i];
-        }
-        M[0][col] = uo;
-        M[1][col] = vo;
-    }
-}
-
 // Reverse DIRK field step of mode idx (section 3.3): dp's state pointers hold the
 // adjoints of the state after the step (phi, v_phi, A, v_A, rho, J^{n+1}), overwritten in
 // place with those of the state before it (J^n in the J slots).
@@ -415,8 +381,15 @@ __device__ __forceinline__ zd adj_mode(const ModeCommon& mc, const DirkParams& d
     auto S = [&](void* p, zd v) { zs(reinterpret_cast<double2*>(p) + idx, v); };
     zd phic, axc, ayc;
     gathered_adjoints(mc, kx, ky, za, zb, phic, axc, ayc);
+    // the forward's step matrix of this mode (mc.dirkm, built once from the stage
+    // recurrence on unit inputs): the step is that linear map, so its transpose is exact
     double M[2][4];
-    dirk_matrix(dp, kx * kx + ky * ky, mc.c, mc.dt, mc.invd + idx, (size_t)mc.nx * mc.ny, M);
+    const double* Mf = mc.dirkm + (size_t)idx * 8;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        M[0][k] = __ldg(Mf + k);
+        M[1][k] = __ldg(Mf + 4 + k);
+    }
     const zd phiu = L(dp.phi) + phic, phiv = L(dp.vphi);
     const zd axu = L(dp.ax) + axc, axv = L(dp.vax);
     const zd ayu = L(dp.ay) + ayc, ayv = L(dp.vay);
