@@ -1,6 +1,7 @@
 """GPU checks of ensembles (pic_ensemble_*): independent runs captured into one CUDA
 graph and advanced by replaying it must give the results of pic_step on each run, bit for
-bit in both forms, whose currents are integer sums."""
+bit in both forms, whose currents are integer sums; at the benchmarked size (256 runs,
+7.0e7 particles) on sampled runs."""
 import numpy as np
 import pytest
 
@@ -200,4 +201,36 @@ def test_ensemble_matches_the_oracle(torch_mod):
             assert np.linalg.norm(d) / np.linalg.norm(getattr(st, k)) < ptol, k
         for f in ("jx", "jy", "rho", "phi", "ax", "ay", "bz", "daydx"):
             assert rel(r.field(f), st.grids[f]) < ftol, (f, rel(r.field(f), st.grids[f]))
+        r.close()
+
+
+def test_full_size_ensemble_matches_solo_runs(torch_mod):
+    # The benchmarked ensemble at its full size: 256 runs drawn as the benchmark draws them
+    # (7.0e7 particles), tile widths and sort intervals from the autotuner, one period
+    # replayed as one graph launch; seeded sample runs stepped alone must give the same bits.
+    from paper_2410_18414_gb300 import autotune
+    torch = torch_mod
+    specs = workloads.ensemble_specs()
+    tuned = [autotune.tune(sp["n"], sp["ppc"])[:2] for sp in specs]
+
+    def make_run(sp, t_s):
+        wl = workloads.ensemble_run(sp)
+        cfg = pic.make_config(wl.nx, wl.ny, wl.lx, wl.ly, wl.dt, p=3, stepper="bdf",
+                              bdf_order=2, weight=wl.weight, precision=pic.FP32_FIX64,
+                              sort_interval=t_s[1], tile=t_s[0])
+        return pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy,
+                              stream=torch.cuda.Stream().cuda_stream)
+
+    runs = [make_run(sp, ts) for sp, ts in zip(specs, tuned)]
+    assert sum(r.n for r in runs) > 6e7
+    with pic.Ensemble(runs, torch.cuda.Stream().cuda_stream) as ens:
+        P = ens.period
+        ens.step(P)
+    sample = np.random.default_rng(7).choice(len(specs), 4, replace=False)
+    for k in sample:
+        solo = make_run(specs[k], tuned[k])
+        solo.step(P)
+        assert_same(runs[k], solo, pic.FP32_FIX64)
+        solo.close()
+    for r in runs:
         r.close()
