@@ -50,6 +50,10 @@ struct ModeCommon {
     double jscale;              // q_p / (dx dy): raw deposit sums -> current density
     double inv_n;               // 1 / (nx ny): inverse-FFT normalisation folded in
     double eps0, mu0, c, dt;
+    // host-computed constants of the per-mode updates (the same roundings as the device
+    // expressions they replace, so no mode divides): 1/eps0 and CDF-2's th/eps0 with
+    // th = 0.5 c^2 dt^2
+    double inv_eps0, cdf_th_eps0;
     int diag;                   // accumulate diagnostics this step
     // precomputed FP64 tables (pic_init): wavenumbers per axis and the inverse implicit-
     // solve denominator per mode (BDF: 1/(C_0 + g K); CDF: 1/(1 + th K); DIRK stage i:
@@ -72,6 +76,7 @@ struct BdfParams {
     double g;       // (c beta dt)^2
     double bdt;     // beta dt
     double inv_a0;  // 1 / a[0] (host-computed, so no mode divides)
+    double g_eps0;  // g / eps0 (host-computed)
     // history, newest first: hist[d-1] is level n+1-d
     void* phi[2 * kMaxBdf];
     void* ax[2 * kMaxBdf];

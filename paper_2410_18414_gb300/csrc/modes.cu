@@ -209,7 +209,7 @@ __device__ __forceinline__ void bdf_rho_phi(const ModeCommon& mc, const BdfParam
     for (int d = 1; d <= k; ++d) rho_new = zfms(rho_new, bp.a[d], hload(bp.rho[d - 1], idx));
     rho_new = zscale(bp.inv_a0, rho_new);
     if (rho_dep) rho_new = *rho_dep;  // the naive update: the deposited charge
-    zd sphi = zscale(bp.g / mc.eps0, rho_new);
+    zd sphi = zscale(bp.g_eps0, rho_new);
 #pragma unroll
     for (int d = 1; d <= 2 * k; ++d) sphi = zfms(sphi, bp.C[d], hload(bp.phi[d - 1], idx));
     phi_new = zscale(mc.invd[idx], sphi);  // 1/(C_0 + g K)
@@ -272,7 +272,7 @@ __device__ __forceinline__ void bdf_mode_update(const ModeCommon& mc, const BdfP
         const zd cont = ibdt * drho + m.divj;
         const zd ex = -zi(m.kx * phi_new) - ibdt * dax;
         const zd ey = -zi(m.ky * phi_new) - ibdt * day;
-        const zd rs = (1.0 / mc.eps0) * rho_new;
+        const zd rs = mc.inv_eps0 * rho_new;
         const zd gauss = div2(m.kx, m.ky, ex, ey) - rs;
         acc[D_GAUGE] += znorm2(gauge);
         acc[D_CONT] += znorm2(cont);
@@ -305,13 +305,13 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParam
     const zd rho_new = rho - dt * m.divj;  // rho^{n+3/2}
     zd phi_new, ax_new, ay_new;
     if (cp.form == 0) {  // implicit: sources averaged over the new and the oldest level
-        phi_new = inv * (2.0 * phi + (th / mc.eps0) * (rho_new + rho_prev)) - phi_prev;
+        phi_new = inv * (2.0 * phi + mc.cdf_th_eps0 * (rho_new + rho_prev)) - phi_prev;
         ax_new = inv * (2.0 * ax + (th * mc.mu0) * (m.jx + jx_prev)) - ax_prev;
         ay_new = inv * (2.0 * ay + (th * mc.mu0) * (m.jy + jy_prev)) - ay_prev;
     } else {  // sources at the middle level: rho^{n+1/2} and J^n
         const double h2 = mc.c * mc.c * dt * dt;
         const zd jx_n = hload(cp.jx, idx), jy_n = hload(cp.jy, idx);
-        const zd sphi = (1.0 / mc.eps0) * rho, sax = mc.mu0 * jx_n, say = mc.mu0 * jy_n;
+        const zd sphi = mc.inv_eps0 * rho, sax = mc.mu0 * jx_n, say = mc.mu0 * jy_n;
         if (cp.form == 1) {  // semi-implicit: Laplacian averaged over levels n+1, n-1
             phi_new = inv * (2.0 * phi + h2 * sphi) - phi_prev;
             ax_new = inv * (2.0 * ax + h2 * sax) - ax_prev;
@@ -335,7 +335,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const CdfParam
         acc[D_GAUGE] += znorm2(gauge);
         acc[D_CONT] += znorm2(cont);
         acc[D_GAUSS] += znorm2(gauss);
-        acc[D_RHO] += znorm2((1.0 / mc.eps0) * rho_new);
+        acc[D_RHO] += znorm2(mc.inv_eps0 * rho_new);
         diag_fields(acc, m.kx, m.ky, ex, ey, ax_new, ay_new);
         zstore(epk + idx, mc.inv_n * (ex + zi(ey)));
     }
@@ -408,7 +408,7 @@ __device__ __forceinline__ void mode_update(const ModeCommon& mc, const DirkPara
     zd rho_new = rho - (h * dp.r0) * divjn - (h * dp.r1) * m.divj;
     if (mc.zq) rho_new = deposited_rho<C>(mc, m);  // the naive update
     zd phi_new, vphi_new, ax_new, vax_new, ay_new, vay_new;
-    const double ie = 1.0 / mc.eps0;
+    const double ie = mc.inv_eps0;
     const double* M = mc.dirkm + (size_t)idx * 8;
     dirk_apply(M, phi, vphi, ie * rho, ie * rho_new, phi_new, vphi_new);
     dirk_apply(M, ax, vax, mc.mu0 * jxn, mc.mu0 * m.jx, ax_new, vax_new);

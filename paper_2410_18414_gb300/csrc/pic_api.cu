@@ -372,6 +372,7 @@ pic_status alloc_state(pic_handle* h) {
         h->bdf.bdt = beta * c.dt;
         h->bdf.inv_a0 = 1.0 / h->bdf.a[0];
         h->bdf.g = (c.c * beta * c.dt) * (c.c * beta * c.dt);
+        h->bdf.g_eps0 = h->bdf.g / c.eps0;
     } else if (c.stepper == PIC_STEPPER_CDF2) {
         void** slots[] = {&h->cdf.phi, &h->cdf.phi_prev, &h->cdf.rho, &h->cdf.rho_prev,
                           &h->cdf.ax,  &h->cdf.ax_prev,  &h->cdf.ay,  &h->cdf.ay_prev,
@@ -639,6 +640,8 @@ static pic_status init_impl(const pic_config* cfg, const pic_particles_in* init,
     }
     h->mc.inv_n = 1.0 / (double)h->ng;
     h->mc.eps0 = cfg->eps0;
+    h->mc.inv_eps0 = 1.0 / cfg->eps0;
+    h->mc.cdf_th_eps0 = (0.5 * cfg->c * cfg->c * cfg->dt * cfg->dt) / cfg->eps0;
     h->mc.mu0 = 1.0 / (cfg->eps0 * cfg->c * cfg->c);
     h->mc.c = cfg->c;
     h->mc.dt = cfg->dt;
