@@ -712,7 +712,8 @@ def adjoint_timings(steps, reps, rank=0, stepper="bdf2", form="fp64"):
         return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
 
     k20 = min(20, N)
-    for K, mode in ((0, "replay"), (k20, "replay"), (k20, "recompute"), (N, "replay")):
+    for K, mode in ((0, "replay"), (k20, "replay"), (k20, "recompute"), (k20, "replay_lean"),
+                    (N, "replay")):
         once(K, mode)          # warm-up: one of each
     # one instrumented reverse sweep (every step kept): the library's per-kernel event
     # pairs around the three reverse launch groups of every step
@@ -735,9 +736,11 @@ def adjoint_timings(steps, reps, rank=0, stepper="bdf2", form="fp64"):
     fwd = med([once(0)[0] for _ in range(reps)])
     t20 = [once(k20) for _ in range(reps)]
     t20r = [once(k20, "recompute") for _ in range(reps)]
+    t20l = [once(k20, "replay_lean") for _ in range(reps)]
     tall = [once(N) for _ in range(reps)]
     r20 = (med([t[0] for t in t20]) + med([t[1] for t in t20])) / fwd
     r20r = (med([t[0] for t in t20r]) + med([t[1] for t in t20r])) / fwd
+    r20l = (med([t[0] for t in t20l]) + med([t[1] for t in t20l])) / fwd
     rall = (med([t[0] for t in tall]) + med([t[1] for t in tall])) / fwd
     seg = (N + k20 - 1) // k20
     st = 8 * rsz * wl.n          # one particle state
@@ -754,6 +757,10 @@ def adjoint_timings(steps, reps, rank=0, stepper="bdf2", form="fp64"):
                                     "backward_ms": med([t[1] for t in t20r]), "ratio": r20r,
                                     "record_bytes": int((seg + 1) * st + k20 * (
                                         80 * wl.n + st + gf))},
+        "checkpoint_20_lean": {"mode": "replay_lean",
+                               "record_forward_ms": med([t[0] for t in t20l]),
+                               "backward_ms": med([t[1] for t in t20l]), "ratio": r20l,
+                               "record_bytes": int(N * (32 * wl.n + gf) + (seg + 1 + k20) * st)},
         "keep_all_steps": {"mode": "replay", "record_forward_ms": med([t[0] for t in tall]),
                            "backward_ms": med([t[1] for t in tall]), "ratio": rall,
                            "record_bytes": int(N * (80 * wl.n + st + gf))},
@@ -792,6 +799,7 @@ def run_adjoint(a):
                    "l2": "flushed (256 MiB write) before each timed run", "parallelism": "replicas"},
         "forward_ms": t["forward_ms"], "checkpoint_20": t["checkpoint_20"],
         "checkpoint_20_recompute": t["checkpoint_20_recompute"],
+        "checkpoint_20_lean": t["checkpoint_20_lean"],
         "keep_all_steps": t["keep_all_steps"], "kernels": t["kernels"], "roofline": t["roofline"],
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }

@@ -413,9 +413,10 @@ void pic_destroy(pic_handle *h);
  * 32 n in the FP32 form) and each step's record (see pic_adjoint_mode) -- then runs it
  * backwards.  With G = 64 nx ny bytes of gather fields a step (32 nx ny in the FP32 form):
  * PIC_ADJ_REPLAY (the default) keeps every step's record from the forward pass and replays
- * only the particle move, costing about (nsteps/K + 1 + K) S + nsteps (80 n + G) bytes;
- * PIC_ADJ_RECOMPUTE re-runs the segment's full steps, costing about (nsteps/K + 1) S
- * + K (80 n + S + G) bytes.  Both hold the adjoint state besides. */
+ * only the particle move, costing about (nsteps/K + 1 + K) S + nsteps (80 n + G) bytes
+ * (PIC_ADJ_REPLAY_LEAN: 32 n in place of 80 n); PIC_ADJ_RECOMPUTE re-runs the segment's
+ * full steps, costing about (nsteps/K + 1) S + K (80 n + S + G) bytes.  All hold the
+ * adjoint state besides. */
 typedef struct pic_adjoint pic_adjoint; /* opaque, owned by the library */
 
 /* What the forward pass keeps between checkpoints. */
@@ -425,8 +426,12 @@ typedef enum {
                               bytes per step); the backward pass replays the particle
                               states of a segment from its checkpoint with the move alone and
                               the recorded P, v (bit for bit the forward's states) */
-    PIC_ADJ_RECOMPUTE = 1  /* nothing: the backward pass re-runs every segment's full forward
+    PIC_ADJ_RECOMPUTE = 1, /* nothing: the backward pass re-runs every segment's full forward
                               steps from its checkpoint (least memory) */
+    PIC_ADJ_REPLAY_LEAN = 2 /* as PIC_ADJ_REPLAY with per particle only P^{n+1}, v^{n+1}
+                              (32 n + G bytes per step): the reverse push gathers A and
+                              grad A again from the recorded fields (the same bits, a second
+                              pass over the stencil) */
 } pic_adjoint_mode;
 
 /* Prepare the adjoint of the next `nsteps` steps of h.  h must be fresh from pic_init

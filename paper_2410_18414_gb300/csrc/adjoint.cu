@@ -101,7 +101,7 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
                   const T* __restrict__ y1, const T* __restrict__ px1,
                   const T* __restrict__ py1, const T* __restrict__ vx,
                   const T* __restrict__ vy, const T* __restrict__ vxo,
-                  const T* __restrict__ vyo, const double* __restrict__ gf,
+                  const T* __restrict__ vyo, const double* __restrict__ gfa,
                   const cplx_t<T>* __restrict__ F, AdjParticlesT<T> ab, double2* __restrict__ Fb,
                   float4* __restrict__ Fb32, int64_t n, unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
@@ -116,12 +116,34 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
             atomicOr(err, (unsigned)ERR_NONFINITE);
             continue;
         }
+        T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
+        const int ix = Shape<P, T>::weights(xi, wx);
+        const int iy = Shape<P, T>::weights(yj, wy);
         // the fields the forward push gathered at x^{n+1} (dphi/dx, dphi/dy, Ax, Ay,
-        // dAx/dx, dAx/dy, dAy/dx, dAy/dy)
-        T f[8];  // f[0], f[1] (grad phi) are not needed here
-        f[0] = f[1] = (T)0;
+        // dAx/dx, dAx/dy, dAy/dx, dAy/dy): from the record, or (gfa == NULL, the lean
+        // record) gathered again from the step's fields F in the forward gather's node
+        // order and roundings, which gives the same bits
+        T f[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // f[0], f[1] (grad phi) are not needed here
+        if (gfa) {
 #pragma unroll
-        for (int k = 2; k < 8; ++k) f[k] = (T)gf[(size_t)(k + 2) * n + p];
+            for (int k = 2; k < 8; ++k) f[k] = (T)gfa[(size_t)(k - 2) * n + p];
+        } else {
+#pragma unroll 1
+            for (int a = 0; a <= P; ++a) {
+                const C* row = F + (size_t)wrap_idx(ix + a, g.nx) * g.ny * 4;
+#pragma unroll
+                for (int b = 0; b <= P; ++b) {
+                    const C* node = row + (size_t)wrap_idx(iy + b, g.ny) * 4;
+                    const T w = rmul(wx[a], wy[b]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const C v = __ldg(node + k);
+                        f[2 * k] = rfma(w, v.x, f[2 * k]);
+                        f[2 * k + 1] = rfma(w, v.y, f[2 * k + 1]);
+                    }
+                }
+            }
+        }
         // velocity: v = c^2 u / D
         const T ux = px1[p] - q * f[2], uy = py1[p] - q * f[3];
         const T D = sqrt(c2 * (ux * ux + uy * uy) + mc2 * mc2);
@@ -143,9 +165,6 @@ k_adj_push_gather(ParticleGeom g, PushParams pp, const T* __restrict__ x1,
         gb[7] = qdt * pby * vsy;
         const T vsbx = qdt * (pbx * f[4] + pby * f[5]);
         const T vsby = qdt * (pbx * f[6] + pby * f[7]);
-        T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];
-        const int ix = Shape<P, T>::weights(xi, wx);
-        const int iy = Shape<P, T>::weights(yj, wy);
         DShape<P, T>::dweights(xi, dwx);
         DShape<P, T>::dweights(yj, dwy);
         // one pass over the stencil: s = sum_f gb_f F_f at each node gives the position
@@ -616,12 +635,13 @@ template <typename T>
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
                                    const T* x1, const T* y1, const T* px1, const T* py1,
                                    const T* vx, const T* vy, const T* vxo, const T* vyo,
-                                   const double* gf, const void* F, AdjParticlesT<T> ab,
-                                   double2* Fb, void* fb32, int64_t n, unsigned int* err,
-                                   cudaStream_t s) {
+                                   const double* gf, bool lean, const void* F,
+                                   AdjParticlesT<T> ab, double2* Fb, void* fb32, int64_t n,
+                                   unsigned int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     if (sizeof(T) == 4 && !fb32) return cudaErrorInvalidValue;
-    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gf,
+    const double* gfa = lean ? nullptr : gf + 4 * n;  // the gathered values of the record
+    GPIC_ADJ_DISPATCH(p, k_adj_push_gather, g, pp, x1, y1, px1, py1, vx, vy, vxo, vyo, gfa,
                       (const cplx_t<T>*)F, ab, Fb, (float4*)fb32, n, err)
     return cudaGetLastError();
 }
@@ -724,8 +744,8 @@ cudaError_t launch_real_to_cplx(const double* src, double2* dst, int64_t n, cuda
 #define GPIC_ADJ_INST(T)                                                                    \
     template cudaError_t launch_adj_push_gather<T>(                                         \
         int, const ParticleGeom&, const PushParams&, const T*, const T*, const T*, const T*, \
-        const T*, const T*, const T*, const T*, const double*, const void*, AdjParticlesT<T>, \
-        double2*, void*, int64_t, unsigned int*, cudaStream_t);                             \
+        const T*, const T*, const T*, const T*, const double*, bool, const void*,            \
+        AdjParticlesT<T>, double2*, void*, int64_t, unsigned int*, cudaStream_t);           \
     template cudaError_t launch_adj_deposit_move<T>(int, const ParticleGeom&, const T*,     \
                                                     const T*, const T*, const T*,           \
                                                     const double2*, AdjParticlesT<T>,       \

@@ -52,7 +52,8 @@ struct pic_adjoint {
     void* recg = nullptr;        // K x 4 ng complex of T
     double* recf = nullptr;      // per step 10 n: P^{n+1}, v^{n+1} and the gathered A, grad A
     int seg_held = -1;           // segment whose states rec holds
-    int mode = 0;                // PIC_ADJ_REPLAY or PIC_ADJ_RECOMPUTE
+    int mode = 0;                // PIC_ADJ_REPLAY, PIC_ADJ_RECOMPUTE or PIC_ADJ_REPLAY_LEAN
+    bool lean = false;           // records without the gathered values (re-gathered)
     void* ab = nullptr;          // particle adjoints, 8 n
     double2* twx = nullptr;      // FP64 twiddles along x and y
     double2* twy = nullptr;
@@ -182,7 +183,9 @@ pic_status restore_checkpoint(pic_adjoint* a, const pic_adjoint::Ck& c) {
     return PIC_OK;
 }
 
-constexpr size_t kRec = 10;  // arrays of n in one step's record
+// Arrays of n in one step's record: P^{n+1} (2), v^{n+1} (2) and the gathered A, grad A
+// (6); the lean record keeps the first four.
+size_t rec_width(const pic_adjoint* a) { return a->lean ? 4 : 10; }
 
 int seg_begin(const pic_adjoint* a, int c) { return c * a->K; }
 int seg_end(const pic_adjoint* a, int c) { return std::min(a->nsteps, (c + 1) * a->K); }
@@ -190,7 +193,7 @@ int seg_end(const pic_adjoint* a, int c) { return std::min(a->nsteps, (c + 1) * 
 // Record slot of step s: every step has its own in the replay mode; in the recompute mode
 // the slots are reused by each segment.
 size_t rec_slot(const pic_adjoint* a, int s) {
-    return a->mode == PIC_ADJ_REPLAY ? (size_t)s : (size_t)(s % a->K);
+    return a->mode != PIC_ADJ_RECOMPUTE ? (size_t)s : (size_t)(s % a->K);
 }
 
 // One forward step of h (step s of the run), keeping the step's gather fields and the
@@ -198,9 +201,11 @@ size_t rec_slot(const pic_adjoint* a, int s) {
 pic_status step_and_record(pic_adjoint* a, int s, int state_j) {
     pic_handle* h = a->h;
     const size_t r = rec_slot(a, s);
-    h->gather_out = a->recf + r * kRec * a->n;
+    h->gather_out = a->recf + r * rec_width(a) * a->n;
+    h->gather_out_short = a->lean;
     pic_status st = pic_step(h, 1);
     h->gather_out = nullptr;
+    h->gather_out_short = false;
     if (st != PIC_OK) return st;
     if (state_j >= 0) {
         st = save_state(a, (char*)a->rec + (size_t)state_j * state_bytes(a));
@@ -247,8 +252,8 @@ pic_status backward_step(pic_adjoint* a, int64_t n, const void* s0v, const void*
         const T* s1 = (const T*)s1v;
         return launch_adj_push_gather<T>(h->p, h->geom, h->push, s1, s1 + np, s1 + 2 * np,
                                          s1 + 3 * np, s0 + 4 * np, s0 + 5 * np, s0 + 6 * np,
-                                         s0 + 7 * np, gf, g, adjoint_arrays<T>(a), a->fb,
-                                         a->fb32, (int64_t)np, h->err, h->s);
+                                         s0 + 7 * np, gf, a->lean, g, adjoint_arrays<T>(a),
+                                         a->fb, a->fb32, (int64_t)np, h->err, h->s);
     }));
     if (a->f32) CK(launch_fb32_to_planes(a->fb32, a->fb, (int64_t)ng, h->s));
     tp.end();
@@ -316,7 +321,7 @@ pic_status pic_adjoint_create(pic_handle* h, int32_t nsteps, int32_t checkpoint_
 pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoint_every,
                                  int32_t mode, pic_adjoint** out) {
     if (!out) return fail(h, PIC_ERR_INVALID_ARG, "out must not be NULL");
-    if (mode != PIC_ADJ_REPLAY && mode != PIC_ADJ_RECOMPUTE)
+    if (mode != PIC_ADJ_REPLAY && mode != PIC_ADJ_RECOMPUTE && mode != PIC_ADJ_REPLAY_LEAN)
         return fail(h, PIC_ERR_INVALID_ARG, "unknown adjoint record mode %d", mode);
     *out = nullptr;
     if (!h) return fail(nullptr, PIC_ERR_INVALID_ARG, "NULL handle");
@@ -333,7 +338,8 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     a->K = std::max(1, std::min(checkpoint_every, nsteps));
     a->nseg = (nsteps + a->K - 1) / a->K;
     a->mode = mode;
-    const size_t nrec = mode == PIC_ADJ_REPLAY ? (size_t)nsteps : (size_t)a->K;
+    a->lean = mode == PIC_ADJ_REPLAY_LEAN;
+    const size_t nrec = mode != PIC_ADJ_RECOMPUTE ? (size_t)nsteps : (size_t)a->K;
     a->L = h->L;
     a->Lr = h->Lr;
     a->kind = h->cfg.stepper == PIC_STEPPER_BDF ? K_BDF
@@ -358,7 +364,8 @@ pic_status pic_adjoint_create_ex(pic_handle* h, int32_t nsteps, int32_t checkpoi
     if (e == cudaSuccess) e = aalloc(a, &a->rec, (size_t)a->K * sb);
     if (e == cudaSuccess) e = aalloc(a, &a->recg, nrec * gfb);
     if (e == cudaSuccess)
-        e = aalloc(a, (void**)&a->recf, nrec * kRec * std::max<size_t>(a->n, 1) * sizeof(double));
+        e = aalloc(a, (void**)&a->recf,
+                   nrec * rec_width(a) * std::max<size_t>(a->n, 1) * sizeof(double));
     if (e == cudaSuccess) e = aalloc(a, &a->ab, sb);
     if (e == cudaSuccess && a->f32) e = aalloc(a, &a->fb32, a->ng * 8 * sizeof(float));
     if (e == cudaSuccess) e = aalloc(a, (void**)&a->twx, (size_t)h->nx * sizeof(double2));
@@ -394,7 +401,7 @@ pic_status pic_adjoint_forward(pic_adjoint* a) {
     if (h->step != 0 || h->phase != 0)
         return fail(h, PIC_ERR_STATE, "the handle has stepped since pic_adjoint_create");
     a->forward_done = true;
-    const bool replay = a->mode == PIC_ADJ_REPLAY;
+    const bool replay = a->mode != PIC_ADJ_RECOMPUTE;
     for (int c = 0; c < a->nseg; ++c) {
         pic_status st = save_checkpoint(a, a->ck[c]);
         if (st != PIC_OK) return st;
@@ -459,14 +466,14 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
     for (int c = a->nseg - 1; c >= 0; --c) {
         const int c0 = seg_begin(a, c), c1 = seg_end(a, c);
         if (a->seg_held != c) {
-            if (a->mode == PIC_ADJ_REPLAY) {
+            if (a->mode != PIC_ADJ_RECOMPUTE) {
                 // the segment's particle states from its checkpoint and the recorded fields
                 for (int s = c0; s < c1; ++s) {
                     const int j = s - c0;
                     const void* s0 = j == 0 ? a->ck[c].state
                                             : (char*)a->rec + (size_t)(j - 1) * state_bytes(a);
                     void* s1 = (char*)a->rec + (size_t)j * state_bytes(a);
-                    const double* rf = a->recf + rec_slot(a, s) * kRec * np;
+                    const double* rf = a->recf + rec_slot(a, s) * rec_width(a) * np;
                     CK(by_prec(h, [&](auto t) {
                         using T = decltype(t);
                         return launch_replay_step<T>(h->geom, (const T*)s0, (T*)s1, rf,
@@ -488,7 +495,8 @@ pic_status pic_adjoint_backward(pic_adjoint* a, const double* bz_bar, const doub
             const void* s0 = j == 0 ? a->ck[c].state
                                     : (char*)a->rec + (size_t)(j - 1) * state_bytes(a);
             const void* s1 = (char*)a->rec + (size_t)j * state_bytes(a);
-            pic_status st = backward_step(a, s, s0, s1, a->recf + rec_slot(a, s) * kRec * np,
+            pic_status st = backward_step(a, s, s0, s1,
+                                          a->recf + rec_slot(a, s) * rec_width(a) * np,
                                           (char*)a->recg + rec_slot(a, s) * 4 * ng * 2 * a->rsz);
             if (st != PIC_OK) return st;
         }

@@ -252,7 +252,8 @@ template <typename T>
 cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vx_old,
                                T* vy_old, int64_t n, const void* fields4, double* gout,
-                               double* diag, unsigned int* err, cudaStream_t s);
+                               double* diag, unsigned int* err, cudaStream_t s,
+                               bool gout_short = false);
 // Gather + push with a species table and/or three velocity components (vz == NULL: 2D-2V):
 // fz holds the A_z fields as [node][2] complex ((dAz/dx, dAz/dy), (Az, 0)); P_z is constant.
 template <typename T>
@@ -368,21 +369,21 @@ struct AdjModeParams {
     double2* rho[kMaxBdf];
 };
 // The reverse particle kernels run in the forward's storage type T (double: the plain
-// path; float: the FP32 form); the field adjoints they add (Fb) and the current adjoint
-// they read (Jb) are FP64 in both.
+// path; float: the FP32 form); the current adjoint they read (Jb) is FP64 in both, the
+// field adjoints they add are FP64 (Fb) or, for T = float, FP32 sums (fb32).
 //
 // Reverse push + gather of one step: reads x^{n+1}, P^{n+1} (state n+1), v^n, v^{n-1}
 // (state n), the step's record (gf: the gathered A and grad A at 4 n .. 10 n, FP64, see
-// launch_gather_push) and the step's gather fields F ([node][4] complex of T); updates the
-// particle adjoints and adds the eight field adjoints into Fb (four planes [k][node] of
-// (f_2k, f_2k+1)).
+// launch_gather_push; lean: the record stops at 4 n and they are gathered again from F)
+// and the step's gather fields F ([node][4] complex of T); updates the particle adjoints
+// and adds the eight field adjoints into Fb (four planes [k][node] of (f_2k, f_2k+1)).
 template <typename T>
 cudaError_t launch_adj_push_gather(int p, const ParticleGeom& g, const PushParams& pp,
                                    const T* x1, const T* y1, const T* px1, const T* py1,
                                    const T* vx, const T* vy, const T* vxo, const T* vyo,
-                                   const double* gf, const void* F, AdjParticlesT<T> ab,
-                                   double2* Fb, void* fb32, int64_t n, unsigned int* err,
-                                   cudaStream_t s);
+                                   const double* gf, bool lean, const void* F,
+                                   AdjParticlesT<T> ab, double2* Fb, void* fb32, int64_t n,
+                                   unsigned int* err, cudaStream_t s);
 // The FP32 form's field adjoints (fb32: [node][2] float4, fields 0-3 and 4-7, summed by
 // launch_adj_push_gather<float>) to the four FP64 planes Fb of the reverse field solve.
 cudaError_t launch_fb32_to_planes(const void* fb32, double2* Fb, int64_t ng, cudaStream_t s);

@@ -58,8 +58,9 @@ struct pic_handle {
     void* Z = nullptr;       // spectrum of J (complex)
     void* F4 = nullptr;      // 4 packed field spectra, inverse-transformed in place
     void* G = nullptr;       // [node][4] complex: the eight real gather fields
-    double* gather_out = nullptr;  // FP64 path: where gather_push also writes the gathered
-                                   // fields (the adjoint's recording steps), else NULL
+    double* gather_out = nullptr;  // where gather_push also writes the adjoint's record of
+                                   // the step (its recording steps), else NULL
+    bool gather_out_short = false; // the record without the gathered values (P, v only)
     void* E = nullptr;       // packed E spectrum of the last diagnosed step
     void* tmp = nullptr;     // complex scratch (ng)
     // naive update (PIC_CHARGE_DEPOSIT): the deposited charge (FP64 pairs, or int64 sums

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads)
 k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restrict__ y,
               T* __restrict__ px, T* __restrict__ py, const T* __restrict__ vx,
               const T* __restrict__ vy, T* __restrict__ vxo, T* __restrict__ vyo, int64_t n,
-              const cplx_t<T>* __restrict__ F, double* __restrict__ gout,
+              const cplx_t<T>* __restrict__ F, double* __restrict__ gout, int gout_short,
               double* __restrict__ diag, unsigned int* __restrict__ err) {
     using C = cplx_t<T>;
     const T idx_ = g.inv_dx, idy = g.inv_dy;
@@ -470,13 +470,15 @@ k_gather_push(GeomT<T> g, PushT<T> pp, const T* __restrict__ x, const T* __restr
         }
         T vxn1, vyn1;
         push_one(pp, f, p, px, py, vx, vy, vxo, vyo, bad, kin, vxn1, vyn1);
-        if (gout) {  // the adjoint's record of this step (ten arrays of n, see launcher)
+        if (gout) {  // the adjoint's record of this step (see launcher)
             gout[p] = (double)px[p];
             gout[(size_t)n + p] = (double)py[p];
             gout[2 * (size_t)n + p] = (double)vxn1;
             gout[3 * (size_t)n + p] = (double)vyn1;
+            if (!gout_short) {
 #pragma unroll
-            for (int k = 2; k < 8; ++k) gout[(size_t)(k + 2) * n + p] = (double)f[k];
+                for (int k = 2; k < 8; ++k) gout[(size_t)(k + 2) * n + p] = (double)f[k];
+            }
         }
     }
     push_finish(pp, bad, kin, diag, err);
@@ -1559,10 +1561,10 @@ template <typename T>
 cudaError_t launch_gather_push(int p, const ParticleGeom& g, const PushParams& pp, const T* x,
                                const T* y, T* px, T* py, const T* vx, const T* vy, T* vxo,
                                T* vyo, int64_t n, const void* f, double* gout, double* diag,
-                               unsigned int* err, cudaStream_t s) {
+                               unsigned int* err, cudaStream_t s, bool gout_short) {
     if (n == 0) return cudaSuccess;
     GPIC_DISPATCH_P(p, k_gather_push, typed<T>(g), typed<T>(pp), x, y, px, py, vx, vy, vxo, vyo, n,
-                    (const cplx_t<T>*)f, gout, diag, err)
+                    (const cplx_t<T>*)f, gout, gout_short ? 1 : 0, diag, err)
     return cudaGetLastError();
 }
 
@@ -1757,7 +1759,7 @@ cudaError_t launch_extract(const void* src, int stride, int comp, double scale, 
     template cudaError_t launch_gather_push<T>(int, const ParticleGeom&, const PushParams&,     \
                                                const T*, const T*, T*, T*, const T*, const T*,  \
                                                T*, T*, int64_t, const void*, double*, double*,  \
-                                               unsigned int*, cudaStream_t);                    \
+                                               unsigned int*, cudaStream_t, bool);                    \
     template cudaError_t launch_init_particles<T>(int, const ParticleGeom&, const PushParams&,  \
                                                   T*, T*, T*, T*, const T*, const T*, T*, T*,   \
                                                   int64_t, const void*, unsigned int*,          \

@@ -1046,7 +1046,7 @@ pic_status gather_push_step(pic_handle* h, bool fuse, bool defer) {
                                          (T*)h->px, (T*)h->py, (const T*)h->v[h->vcur][0],
                                          (const T*)h->v[h->vcur][1], (T*)h->v[vo][0],
                                          (T*)h->v[vo][1], h->n, h->G, h->gather_out, h->diag,
-                                         h->err, h->s);
+                                         h->err, h->s, h->gather_out_short);
         }));
     }
     h->vcur = vo;

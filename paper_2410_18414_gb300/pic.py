@@ -444,12 +444,13 @@ class Adjoint:
     v^0 and, with P^0 = gamma m v^0 independent, to P^0.  Seeds and results are CUDA
     float64 tensors (the library reads and writes device memory)."""
 
-    MODES = {"replay": 0, "recompute": 1}
+    MODES = {"replay": 0, "recompute": 1, "replay_lean": 2}
 
     def __init__(self, sim, nsteps, checkpoint_every=None, mode="replay"):
         """mode "replay": the forward pass keeps every step's gathered fields and the backward
-        pass replays particle states between checkpoints; "recompute": it re-runs each
-        segment's full steps (least memory)."""
+        pass replays particle states between checkpoints; "replay_lean": the same with per
+        particle only P and v kept (the reverse push gathers the fields again);
+        "recompute": it re-runs each segment's full steps (least memory)."""
         self.lib = load_library()
         self.sim = sim
         self.nsteps = int(nsteps)

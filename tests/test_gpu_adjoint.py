@@ -249,6 +249,26 @@ def test_fp32_form_adjoint_matches_oracle(device, name, case, kw, nsteps, K, mod
     print()
 
 
+@pytest.mark.parametrize("p,k,precision", [(2, 1, pic.FP64), (3, 2, pic.FP64), (4, 3, pic.FP64),
+                                           (3, 2, pic.FP32_FIX64)],
+                         ids=["p2-fp64", "p3-fp64", "p4-fp64", "p3-fp32"])
+def test_lean_replay_gives_the_replay_gradient(device, p, k, precision):
+    # The lean records keep P and v only; the reverse push gathers A and grad A again from
+    # the recorded fields with the forward gather's own operations, so the gradient is the
+    # replay mode's up to the order of the field-adjoint atomics; FP64 also against the
+    # oracle at the parity bound.
+    cfg, ocfg, x, y, vx, vy = _case(p, k, 32, 24, 3001, seed=40 + p, precision=precision)
+    _, full = _gpu_gradient(device, cfg, x, y, vx, vy, 7, 3, mode="replay")
+    _, lean = _gpu_gradient(device, cfg, x, y, vx, vy, 7, 3, mode="replay_lean")
+    tol = 1e-13 if precision == pic.FP64 else 1e-6
+    for key in full:
+        assert rel(lean[key], full[key]) <= tol, (key, rel(lean[key], full[key]))
+    if precision == pic.FP64:
+        expect = oadj.gradient(oadj.record(ocfg, x, y, vx, vy, 7))
+        assert rel(lean["vx"], expect["v0"][0]) <= 1e-11
+        assert rel(lean["py"], expect["p0"][1]) <= 1e-11
+
+
 def test_fp32_form_adjoint_modes_agree(device):
     # replay (recorded P, v and gathered fields) and recompute (the segment's FP32 steps
     # re-run; the fixed-point current is bit-exact) reverse the same trajectory: they differ
