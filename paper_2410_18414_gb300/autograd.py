@@ -1,4 +1,5 @@
-"""torch.autograd interface to the discrete adjoint of the FP64 run (any stepper).
+"""torch.autograd interface to the discrete adjoint of the run (any stepper; the FP64 path
+or the unsorted FP32 form).
 
 magnetic_energy(cfg, x0, y0, vx0, vy0, nsteps) returns the magnetic energy
 W_B = 1/2 sum B_z^2 dx dy of the last level (section 5) after `nsteps` steps of
@@ -14,12 +15,12 @@ from . import pic
 
 class _MagneticEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, vx0, vy0, cfg, x0, y0, nsteps, checkpoint_every, stream):
+    def forward(ctx, vx0, vy0, cfg, x0, y0, nsteps, checkpoint_every, stream, mode):
         vx0 = vx0.detach().contiguous()
         vy0 = vy0.detach().contiguous()
         sim = pic.Simulation(cfg, x0, y0, vx0, vy0, stream=stream)
         try:
-            adj = pic.Adjoint(sim, nsteps, checkpoint_every)
+            adj = pic.Adjoint(sim, nsteps, checkpoint_every, mode=mode)
             adj.forward()
         except Exception:
             sim.close()
@@ -36,12 +37,14 @@ class _MagneticEnergy(torch.autograd.Function):
         g = ctx.adj.backward(bz_bar=bz_bar.contiguous())
         ctx.adj.close()
         ctx.sim.close()
-        return g["vx"], g["vy"], None, None, None, None, None, None
+        return g["vx"], g["vy"], None, None, None, None, None, None, None
 
 
-def magnetic_energy(cfg, x0, y0, vx0, vy0, nsteps, checkpoint_every=None, stream=None):
-    """W_B after nsteps (FP64, continuity charge, no sorting); differentiable in vx0, vy0 (CUDA
-    float64 tensors).  x0, y0: CUDA float64 tensors or numpy arrays."""
+def magnetic_energy(cfg, x0, y0, vx0, vy0, nsteps, checkpoint_every=None, stream=None,
+                    mode="replay"):
+    """W_B after nsteps (either precision, continuity charge, no sorting); differentiable in
+    vx0, vy0 (CUDA float64 tensors).  x0, y0: CUDA float64 tensors or numpy arrays.  mode:
+    the adjoint's record mode ("replay", "replay_lean" or "recompute", see pic.Adjoint)."""
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    return _MagneticEnergy.apply(vx0, vy0, cfg, x0, y0, nsteps, checkpoint_every, stream)
+    return _MagneticEnergy.apply(vx0, vy0, cfg, x0, y0, nsteps, checkpoint_every, stream, mode)

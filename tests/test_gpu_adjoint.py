@@ -282,17 +282,21 @@ def test_fp32_form_adjoint_modes_agree(device):
         assert rel(a[key], c[key]) <= 1e-6, key
 
 
-def test_autograd_matches_library(device):
+@pytest.mark.parametrize("precision,mode,tol", [(pic.FP64, "replay", 1e-12),
+                                                (pic.FP64, "replay_lean", 1e-12),
+                                                (pic.FP32_FIX64, "replay", 1e-6)],
+                         ids=["fp64", "fp64-lean", "fp32"])
+def test_autograd_matches_library(device, precision, mode, tol):
     import torch
     from paper_2410_18414_gb300 import autograd
-    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=6)
+    cfg, _, x, y, vx, vy = _case(3, 2, 32, 32, 4096, seed=6, precision=precision)
     vx0 = torch.tensor(vx, device="cuda", requires_grad=True)
     vy0 = torch.tensor(vy, device="cuda", requires_grad=True)
-    wb = autograd.magnetic_energy(cfg, x, y, vx0, vy0, 12, checkpoint_every=5)
+    wb = autograd.magnetic_energy(cfg, x, y, vx0, vy0, 12, checkpoint_every=5, mode=mode)
     (2.5 * wb).backward()
     _, ref = _gpu_gradient(device, cfg, x, y, vx, vy, 12, 12)
-    assert rel(vx0.grad.cpu().numpy(), 2.5 * ref["vx"]) <= 1e-12
-    assert rel(vy0.grad.cpu().numpy(), 2.5 * ref["vy"]) <= 1e-12
+    assert rel(vx0.grad.cpu().numpy(), 2.5 * ref["vx"]) <= tol
+    assert rel(vy0.grad.cpu().numpy(), 2.5 * ref["vy"]) <= tol
 
 
 # ------------------------------------------------------------ 128 x 128 Weibel --
