@@ -717,7 +717,10 @@ cudaError_t launch_columns_generic(const ModeCommon& mc, const Params& prm, cons
                                               (int)smem);
         if (e2 != cudaSuccess) return e2;
     }
-    return launch_pdl(kern, dim3(mc.ny), dim3(kModeThreads), smem, s, mc, prm, (const C*)z,
+    // one thread per mode of the column: grids up to 128 wide take 128-thread CTAs (one
+    // step 1 us shorter at 128 x 128 than with 256, half of whose threads idle)
+    const int threads = mc.nx <= 128 ? 128 : kModeThreads;
+    return launch_pdl(kern, dim3(mc.ny), dim3(threads), smem, s, mc, prm, (const C*)z,
                       (C*)f4, (C*)e, diag, fd, (const C*)tw);
 }
 
