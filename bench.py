@@ -197,9 +197,9 @@ def flops_gather_deposit(p):
 # time: when the source has changed since, the bench line reports no traffic.
 TRAFFIC = {
     # (kernel, workload): (bytes per launch, source file, its SHA-1 prefix, profile)
-    ("gather_deposit", "weibel128"): (34.43e6 + 0.016e6, "particles.cu", "6235639ff411",
+    ("gather_deposit", "weibel128"): (34.43e6 + 0.017e6, "particles.cu", "9ba05500f8ad",
                                       "profiles/gather_deposit_fused_weibel128.md"),
-    ("gather_deposit", "weibel512"): (852.54e6 + 594.43e6, "particles.cu", "6235639ff411",
+    ("gather_deposit", "weibel512"): (853.19e6 + 592.23e6, "particles.cu", "9ba05500f8ad",
                                       "profiles/gather_deposit_fused_weibel512.md"),
 }
 

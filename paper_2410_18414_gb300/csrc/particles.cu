@@ -582,7 +582,9 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
 // with the gather + push of the step before it (kFused).
 //
 // CTA (tile, split) takes a contiguous share [p0, p1) of one tile's particles and works
-// through it in batches of at most kBinBatch:
+// through it in the fewest batches of at most `cap` particles, of equal sizes (a batch
+// costs the same barriers, scan and region flush whatever its size, so a share of
+// cap + 20 runs as two halves, not as cap and 20):
 //   A  consecutive lanes take consecutive particles (the SoA loads and stores coalesce;
 //      unfused, each thread's next particle is loaded while it works on the current one).
 //      Fused: gather the eight fields of the step at x^{n+1} from the tile's field region
@@ -603,13 +605,18 @@ k_gather_push_tiled(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* _
 //      two rows (three for quadratic shapes) over the slice, which keeps the sums within
 //      the register budget of four CTAs per SM.
 //   The region is added to the global int64 grid after every batch, which keeps every
-//   32-bit sum exact: a batch adds at most kBinBatch = 2^10 contributions of magnitude
-//   <= 2^19 to a node.
+//   32-bit sum exact: a batch adds at most cap <= kBinBatchMax = 1152 contributions of
+//   magnitude <= 2^19 to a node, less than 2^30 in all.
 // A particle whose stencil leaves the region (it drifted further than the halo) adds its
 // contributions straight to the global grid.  The integer sums make J independent of the
 // order of the particles and of how they are grouped, so the result is the same bits as
 // every other deposit of the FP32 form.
-constexpr int kBinBatch = 1024;
+// Batch capacity: kBinBatchMax where four CTAs per SM still fit (a tile share of about
+// 1024 particles then runs as one batch even when sampling noise puts it a little above
+// 1024), else kBinBatchMin; whether a tiling can use the pass at all is judged at the
+// smaller one.
+constexpr int kBinBatchMin = 1024;
+constexpr int kBinBatchMax = 1152;
 constexpr int kBinSmemMax = 100 * 1024;  // four CTAs per SM fit up to 56 KB each
 
 // Byte offsets in the binned pass's dynamic shared memory (stage first: 16-byte aligned).
@@ -624,25 +631,25 @@ struct BinSpecies {
 
 struct BinLayout {
     int fields;   // kFused: the gather fields of the region, [rx][ry] x 2 float4
-    int stz;      // 2D-3V: float [kBinBatch]: v_z of each staged particle
-    int kr;       // int [kBinBatch]: key | rank << 16 of each staged particle (-1: none)
-    int idx;      // uint16 [kBinBatch]: staging slots in binned order
+    int stz;      // 2D-3V: float [cap]: v_z of each staged particle
+    int kr;       // int [cap]: key | rank << 16 of each staged particle (-1: none)
+    int idx;      // uint16 [cap]: staging slots in binned order
     int racc;     // int [4 rx ry] (2D-3V: 6): lo_x, lo_y, hi_x, hi_y (lo_z, hi_z) node sums
     int cnt;      // int [rx ry + 1]: counts, then offsets
     int bytes;
 };
 __host__ __device__ inline BinLayout bin_layout(const TileGeom& tg, int p, bool fused,
-                                                bool z = false) {
+                                                bool z = false, int cap = kBinBatchMin) {
     BinLayout l;
-    int o = kBinBatch * 16;  // stage: (x, y, vx, vy) of each particle, arrival order
+    int o = cap * 16;  // stage: (x, y, vx, vy) of each particle, arrival order
     l.fields = o;
     if (fused) o += tg.rx * tg.ry * 32;
     l.stz = o;
-    if (z) o += kBinBatch * 4;
+    if (z) o += cap * 4;
     l.kr = o;
-    o += kBinBatch * 4;
+    o += cap * 4;
     l.idx = o;
-    o += kBinBatch * 2;
+    o += cap * 2;
     o = (o + 15) & ~15;
     l.racc = o;
     o += (z ? 6 : 4) * tg.rx * tg.ry * 4;
@@ -823,13 +830,13 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
                  int nsplit, const float2* __restrict__ F, AccFix acc,
                  double* __restrict__ diag, unsigned int* __restrict__ err,
                  const int32_t* __restrict__ sp, BinSpecies bs, const float* __restrict__ vz,
-                 AccFix accz) {
+                 AccFix accz, int cap) {
     static_assert(!(kZ && kFused), "2D-3V runs the binned deposit on its own");
     constexpr int NF = kFused ? 8 : (kZ ? 5 : 4);  // values loaded per particle
     constexpr int NQ = kZ ? 6 : 4;                 // region planes
     extern __shared__ float4 bin_smem[];
     __shared__ int wsum[33];
-    const BinLayout L = bin_layout(tg, P, kFused, kZ);
+    const BinLayout L = bin_layout(tg, P, kFused, kZ, cap);
     char* base = reinterpret_cast<char*>(bin_smem);
     float4* stage = bin_smem;
     const float4* sf = reinterpret_cast<const float4*>(base + L.fields);
@@ -881,8 +888,10 @@ k_deposit_binned(GeomT<float> g, PushT<float> pp, TileGeom tg, const float* __re
     const int slice = (33 * (int)threadIdx.x) & (kThreads - 1);
     double kin = 0.0;
     unsigned bad = 0;
-    for (int64_t b0 = p0; b0 < p1; b0 += kBinBatch) {
-        const int nb = (int)min((int64_t)kBinBatch, p1 - b0);
+    const int64_t nbat = (p1 - p0 + cap - 1) / cap;
+    for (int64_t bq = 0; bq < nbat; ++bq) {
+        const int64_t b0 = p0 + (p1 - p0) * bq / nbat;
+        const int nb = (int)(p0 + (p1 - p0) * (bq + 1) / nbat - b0);
         // A: (gather + push,) move, stage and count; without the gather, the next particle's
         // loads are in flight meanwhile (the fused kernel keeps its registers for the gather)
         constexpr bool kAhead = !kFused;
@@ -1642,21 +1651,29 @@ cudaError_t launch_deposit_binned(int p, const ParticleGeom& g, const PushParams
     if (nsplit < 1) nsplit = 1;
     if (nsplit > 64) nsplit = 64;
     const int blocks = ntiles * nsplit;
-    const size_t smem = (size_t)bin_layout(tg, p, fused, z).bytes;
     const AccFix acc = AccFix::make(j, scale);
     const AccFix accz = AccFix::make(jz, scale);
     cudaError_t e = cudaSuccess;
+    // the larger batch capacity where the occupancy calculator still puts four CTAs on an
+    // SM (shared memory is what limits it), else the smaller one
 #define GPIC_BINNED(PP, FF, SS, ZZ)                                                            \
     {                                                                                          \
         static const cudaError_t attr = cudaFuncSetAttribute(                                  \
             k_deposit_binned<PP, FF, SS, ZZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
             kBinSmemMax);                                                                      \
         e = attr;                                                                              \
+        int cap = kBinBatchMin, per_sm = 0;                                                    \
+        const size_t big = (size_t)bin_layout(tg, p, fused, z, kBinBatchMax).bytes;            \
+        if (e == cudaSuccess && big <= (size_t)kBinSmemMax)                                    \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
+                &per_sm, k_deposit_binned<PP, FF, SS, ZZ>, kThreads, big);                     \
+        if (per_sm >= 4) cap = kBinBatchMax;                                                   \
+        const size_t smem = (size_t)bin_layout(tg, p, fused, z, cap).bytes;                    \
         if (e == cudaSuccess)                                                                  \
             e = launch_pdl(k_deposit_binned<PP, FF, SS, ZZ>, dim3(blocks), dim3(kThreads),     \
                            smem, s, typed<float>(g), ptyped, tg, x, y, xo, yo, px, py, vx, vy, \
                            vxo, vyo, off, nsplit, (const float2*)fields4, acc, diag, err,      \
-                           species ? sp : nullptr, bs, vz, accz);                              \
+                           species ? sp : nullptr, bs, vz, accz, cap);                         \
     }
 #define GPIC_BINNED_S(PP, FF)                       \
     if (species && z) GPIC_BINNED(PP, false, true, true) \

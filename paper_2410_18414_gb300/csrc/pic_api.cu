@@ -498,8 +498,11 @@ bool diag_due(const pic_handle* h) {
     return h->diag_every > 0 && ((h->step + 1) % h->diag_every) == 0;
 }
 
-// Particles per CTA of the binned FP32 deposit (one batch of its shared-memory binning).
-constexpr int kBinPerCta = 2048;
+// Particles per CTA of the binned FP32 deposit at the mean density: one batch of its
+// shared-memory binning.  Measured on the 128 x 128 workload (2^20 particles, tiles of
+// about 4096): 1024 a CTA (one batch each) 51 us for the fused kernel, 2048 (two batches)
+// 58 us.
+constexpr int kBinPerCta = 1024;
 
 // Whether the gather + push of the step now finishing may run fused with the next step's
 // move + deposit: the sorted FP32 form (2D-2V, one species) when the tile regions fit the
