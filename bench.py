@@ -204,6 +204,16 @@ TRAFFIC = {
 }
 
 
+# Shared-memory wavefronts per launch (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum) of the
+# fused FP32 kernel, from the same kind of committed capture: the pipe that bounds it.  One
+# wavefront per SM clock is the pipe's peak (128 B a clock).
+SMEM_WAVEFRONTS = {
+    # (kernel, workload): (wavefronts per launch, source file, its SHA-1 prefix, profile)
+    ("gather_deposit", "weibel128"): (9.40e6, "particles.cu", "9ba05500f8ad",
+                                      "profiles/gather_deposit_fused_weibel128.md"),
+}
+
+
 def source_sha1(name):
     import hashlib
     path = os.path.join(ROOT, "paper_2410_18414_gb300", "csrc", name)
@@ -219,6 +229,21 @@ def traffic_of(kernel, workload):
     if source_sha1(src) != sha:
         return None, f"{src} changed since the capture in {profile}"
     return nbytes, f"ncu capture: {profile}"
+
+
+def smem_pipe_of(kernel, workload, ms, sm_mhz, nsm):
+    """The kernel's shared-memory pipe use: committed wavefronts per launch over the
+    event-timed launch, per SM clock at the sampled clock (peak 1.0), or None."""
+    entry = SMEM_WAVEFRONTS.get((kernel, workload))
+    if entry is None:
+        return None
+    wf, src, sha, profile = entry
+    if source_sha1(src) != sha:
+        return {"wavefronts": None, "source": f"{src} changed since the capture in {profile}"}
+    per_clk = wf / (ms * 1e-3 * nsm * sm_mhz * 1e6)
+    return {"wavefronts": wf, "achieved": per_clk, "peak": 1.0,
+            "unit": "wavefronts per SM clock", "frac": per_clk,
+            "source": f"ncu capture: {profile}; {nsm} SMs at the measured {sm_mhz:.0f} MHz"}
 
 
 _FP64 = {}
@@ -923,6 +948,10 @@ def main():
                                  "flops_per_particle": dom["flops"] / wl.n,
                                  "peak_source": f"152 SMs x 128 FP32 lanes x 2 at the measured "
                                                 f"{sm_mhz:.0f} MHz"}}
+        nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        smem = smem_pipe_of(dom_name, a.workload, dom["ms"], sm_mhz, nsm)
+        if smem is not None:
+            roofline["smem_pipe"] = smem
     else:
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dom["gflops"],
                     "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
@@ -932,24 +961,26 @@ def main():
                     "hbm": {"achieved_gbs": dom["gbs"], "peak_gbs": pk["hbm_gbs"],
                             "frac": dom["gbs"] / pk["hbm_gbs"], "peak_source": pk["hbm_src"]}}
 
-    # the configuration's whole run: every step in one pic_step call (the call's steps
-    # run back to back, so no L2 flush separates them)
+    # the configuration's whole run (its own step count, whatever --steps says): every
+    # step in one pic_step call (the call's steps run back to back, so no L2 flush
+    # separates them)
+    full_steps = wl.nsteps
     sf = pic.Simulation(cfg, wl.x, wl.y, wl.vx, wl.vy, stream=sp)
     sf.step(3)
     flush.zero_()
     ranks.barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    sf.step(a.steps)
+    sf.step(full_steps)
     f1.record(stream)
     f1.synchronize()
     full_ms = ranks.max(f0.elapsed_time(f1))
     sf.sync()
     sf.close()
-    full_run = {"steps": a.steps, "ms": full_ms, "ms_per_step": full_ms / a.steps,
-                "value": whole_job_rate(wl.n, world, a.steps, full_ms),
-                "how": "one pic_step call of all the steps after 3 warm-up steps; "
-                       "L2 not flushed between steps"}
+    full_run = {"steps": full_steps, "ms": full_ms, "ms_per_step": full_ms / full_steps,
+                "value": whole_job_rate(wl.n, world, full_steps, full_ms),
+                "how": f"the configuration's {full_steps} steps in one pic_step call after 3 "
+                       "warm-up steps; L2 not flushed between steps"}
 
     # the other precision form on the same workload (the metric's comparison)
     other = "fp64" if fp32 else "fp32"
